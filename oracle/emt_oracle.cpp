@@ -1,0 +1,501 @@
+// Plain FP64 CPU oracle of the EMTP-type time loop -- TEST INFRASTRUCTURE.
+//
+// Only the tests, the package smoke check and the benchmark's CPU-baseline
+// leg load this file's library.  It shares nothing with the CUDA path.
+//
+// What it computes (the four basic processes of the EMTP-type algorithm,
+// CloudPSS paper Sec. III-A, with the textbook formulas of its ref. [2]):
+//
+//   companion conductances (trapezoidal rule)
+//     R: g = 1/R        L: g = dt/(2L)        C: g = 2C/dt
+//     closed switch: g = 1/R_sw               line end: g = 1/Z_c
+//   branch b from node k to node m, v_b = V(k) - V(m), V(ground) = 0,
+//   V(source s) = A_s sin(2 pi f_s t_n + phi_s), t_n = n dt:
+//     current k->m:  i_b(n) = g v_b(n) + h_b(n-1)      (h = 0 for R)
+//     L: h_b(n) = h_b(n-1) + 2 g v_b(n)
+//     C: h_b(n) = -h_b(n-1) - 2 g v_b(n)
+//   lossless line (k, m), Z_c, travel time d steps (Bergeron):
+//     current k->line: v_k(n)/Z_c + I_k(n)
+//     I_m(n+d) = -(2/Z_c) v_k(n) - I_k(n),  I_k(n+d) = -(2/Z_c) v_m(n) - I_m(n)
+//   nodal equations per step:  G v_n = u_n - A h_{n-1} - L I_n
+//
+// The time loop starts de-energised: v_0 = 0, h_0 = 0, I(n) = 0 for n <= d,
+// and the first solved step is n = 1.  Each conductance matrix is factorised
+// by LU with partial pivoting whenever the switch state changes (process 3)
+// and every step is a forward/backward substitution (process 4).
+//
+// The scalar type is a template parameter so the same loop runs in complex
+// arithmetic for complex-step derivatives.
+#include "emt_oracle.h"
+
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+using cplx = std::complex<double>;
+
+inline double re(double x) { return x; }
+inline double re(const cplx& x) { return x.real(); }
+
+const double kPi = 3.14159265358979323846;
+
+// ---------------------------------------------------------------- dense LU
+
+// In-place LU with partial pivoting (Doolittle), row-major n x n.
+// Pivots on the magnitude of the real part so that a complex-step run takes
+// the same pivot sequence as the real run.
+template <class T>
+bool lu_factor(int n, std::vector<T>& a, std::vector<int>& piv) {
+  piv.resize(n);
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    double best = std::fabs(re(a[(size_t)k * n + k]));
+    for (int i = k + 1; i < n; ++i) {
+      double m = std::fabs(re(a[(size_t)i * n + k]));
+      if (m > best) { best = m; p = i; }
+    }
+    if (!(best > 0.0)) return false;
+    piv[k] = p;
+    if (p != k)
+      for (int j = 0; j < n; ++j) std::swap(a[(size_t)k * n + j], a[(size_t)p * n + j]);
+    for (int i = k + 1; i < n; ++i) {
+      T f = a[(size_t)i * n + k] / a[(size_t)k * n + k];
+      a[(size_t)i * n + k] = f;
+      for (int j = k + 1; j < n; ++j) a[(size_t)i * n + j] -= f * a[(size_t)k * n + j];
+    }
+  }
+  return true;
+}
+
+// Solve with the factors: apply the row swaps, then L y = Pb, then U x = y.
+template <class T>
+void lu_solve(int n, const std::vector<T>& lu, const std::vector<int>& piv, T* x) {
+  for (int k = 0; k < n; ++k)
+    if (piv[k] != k) std::swap(x[k], x[piv[k]]);
+  for (int i = 0; i < n; ++i) {
+    T s = x[i];
+    for (int j = 0; j < i; ++j) s -= lu[(size_t)i * n + j] * x[j];
+    x[i] = s;
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    T s = x[i];
+    for (int j = i + 1; j < n; ++j) s -= lu[(size_t)i * n + j] * x[j];
+    x[i] = s / lu[(size_t)i * n + i];
+  }
+}
+
+// Solve A^T x = b with the factors of P A = L U:  A^T = U^T L^T P,
+// so U^T z = b, L^T y = z, x = P^T y.
+template <class T>
+void lu_solve_transposed(int n, const std::vector<T>& lu, const std::vector<int>& piv, T* x) {
+  for (int i = 0; i < n; ++i) {
+    T s = x[i];
+    for (int j = 0; j < i; ++j) s -= lu[(size_t)j * n + i] * x[j];
+    x[i] = s / lu[(size_t)i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    T s = x[i];
+    for (int j = i + 1; j < n; ++j) s -= lu[(size_t)j * n + i] * x[j];
+    x[i] = s;
+  }
+  for (int k = n - 1; k >= 0; --k)
+    if (piv[k] != k) std::swap(x[k], x[piv[k]]);
+}
+
+// ---------------------------------------------------------------- network
+
+bool valid(const orc_net* net) {
+  if (!net || !(net->dt > 0.0) || net->n_nodes < 0) return false;
+  auto node_ok = [&](int32_t x) { return x >= -1 - net->n_src && x < net->n_nodes; };
+  for (int64_t b = 0; b < net->n_br; ++b) {
+    int32_t k = net->br_k[b], m = net->br_m[b];
+    if (!node_ok(k) || !node_ok(m) || k == m) return false;
+    if (k < 0 && m < 0) return false;
+    if (net->br_kind[b] > 2 || !(net->br_val[b] > 0.0) || !std::isfinite(net->br_val[b])) return false;
+  }
+  for (int64_t l = 0; l < net->n_ln; ++l) {
+    if (net->ln_k[l] < 0 || net->ln_m[l] < 0 || net->ln_k[l] >= net->n_nodes || net->ln_m[l] >= net->n_nodes) return false;
+    if (net->ln_k[l] == net->ln_m[l] || net->ln_d[l] < 1 || !(net->ln_zc[l] > 0.0)) return false;
+  }
+  for (int64_t s = 0; s < net->n_sw; ++s) {
+    int32_t k = net->sw_k[s], m = net->sw_m[s];
+    if (k < -1 || m < -1 || k >= net->n_nodes || m >= net->n_nodes || k == m || (k < 0 && m < 0)) return false;
+    if (!(net->sw_r[s] > 0.0)) return false;
+  }
+  return true;
+}
+
+// Connected components of unknown nodes over branches and switches
+// (ground and source nodes do not join anything; lines are cuts).
+int find(std::vector<int>& p, int x) {
+  while (p[x] != x) { p[x] = p[p[x]]; x = p[x]; }
+  return x;
+}
+
+void components(const orc_net* net, std::vector<int>& sub, int& n_sub) {
+  int n = (int)net->n_nodes;
+  std::vector<int> p(n);
+  for (int i = 0; i < n; ++i) p[i] = i;
+  auto join = [&](int a, int b) {
+    if (a < 0 || b < 0) return;
+    a = find(p, a); b = find(p, b);
+    if (a != b) p[std::max(a, b)] = std::min(a, b);
+  };
+  for (int64_t b = 0; b < net->n_br; ++b) join(net->br_k[b], net->br_m[b]);
+  for (int64_t s = 0; s < net->n_sw; ++s) join(net->sw_k[s], net->sw_m[s]);
+  sub.assign(n, -1);
+  n_sub = 0;
+  std::vector<int> label(n, -1);
+  for (int i = 0; i < n; ++i) {
+    int r = find(p, i);
+    if (label[r] < 0) label[r] = n_sub++;
+    sub[i] = label[r];
+  }
+}
+
+template <class T>
+T conductance(uint8_t kind, const T& value, double dt) {
+  if (kind == 0) return T(1.0) / value;
+  if (kind == 1) return T(dt) / (T(2.0) * value);
+  return T(2.0) * value / T(dt);
+}
+
+bool switch_closed(const orc_net* net, int64_t s, int64_t n) {
+  return net->sw_on[s] >= 0 && n >= net->sw_on[s] && (net->sw_off[s] < 0 || n < net->sw_off[s]);
+}
+
+// One simulation.  Parameters (branch values, source amplitudes) are given
+// in the scalar type T so that complex-step runs can perturb one of them.
+template <class T>
+struct Sim {
+  const orc_net* net;
+  int n_nodes;
+  std::vector<T> g;          // companion conductance per branch
+  std::vector<T> amp;        // source amplitudes
+  std::vector<int> sub;      // subsystem of each unknown node
+  int n_sub = 0;
+  std::vector<std::vector<int>> nodes;   // nodes of each subsystem
+  std::vector<int> local;                // local index of each node
+  std::vector<std::vector<T>> lu;        // factors per subsystem (current switch state)
+  std::vector<std::vector<int>> piv;
+  std::vector<std::vector<char>> state;  // switch state the factors belong to
+  std::vector<T> h;                      // history current per branch
+  // line history rings: I value consumed at end k (slot 0) / end m (slot 1)
+  // of line l at step n lives at ring[l][end][n mod (d+1)]
+  std::vector<std::vector<T>> ring_k, ring_m;
+  std::vector<T> vsrc;   // source voltages at the current step
+  std::vector<T> v;      // node voltages at the current step
+
+  bool init(const T* br_value, const T* src_amp, bool monolithic) {
+    n_nodes = (int)net->n_nodes;
+    g.resize(net->n_br);
+    for (int64_t b = 0; b < net->n_br; ++b) g[b] = conductance<T>(net->br_kind[b], br_value[b], net->dt);
+    amp.assign(src_amp, src_amp + net->n_src);
+    if (monolithic) {
+      sub.assign(n_nodes, 0);
+      n_sub = n_nodes > 0 ? 1 : 0;
+    } else {
+      components(net, sub, n_sub);
+    }
+    nodes.assign(n_sub, {});
+    local.assign(n_nodes, -1);
+    for (int i = 0; i < n_nodes; ++i) {
+      local[i] = (int)nodes[sub[i]].size();
+      nodes[sub[i]].push_back(i);
+    }
+    lu.assign(n_sub, {});
+    piv.assign(n_sub, {});
+    state.assign(n_sub, {});
+    h.assign(net->n_br, T(0.0));
+    ring_k.assign(net->n_ln, {});
+    ring_m.assign(net->n_ln, {});
+    for (int64_t l = 0; l < net->n_ln; ++l) {
+      ring_k[l].assign(net->ln_d[l] + 1, T(0.0));
+      ring_m[l].assign(net->ln_d[l] + 1, T(0.0));
+    }
+    vsrc.assign(net->n_src, T(0.0));
+    v.assign(n_nodes, T(0.0));
+    return true;
+  }
+
+  // Process 3: assemble the subsystem's conductance matrix for the switch
+  // state of step n and factorise it, if that state differs from the one
+  // the current factors belong to.
+  bool refactor_if_needed(int s, int64_t n) {
+    std::vector<char> st(net->n_sw, 0);
+    for (int64_t w = 0; w < net->n_sw; ++w) {
+      int a = net->sw_k[w] >= 0 ? net->sw_k[w] : net->sw_m[w];
+      if (sub[a] == s) st[w] = switch_closed(net, w, n) ? 1 : 0;
+    }
+    if (!lu[s].empty() && st == state[s]) return true;
+    state[s] = st;
+    int ns = (int)nodes[s].size();
+    std::vector<T> G((size_t)ns * ns, T(0.0));
+    auto stamp = [&](int32_t k, int32_t m, const T& gg) {
+      int a = (k >= 0) ? local[k] : -1;
+      int b = (m >= 0) ? local[m] : -1;
+      if (a >= 0) G[(size_t)a * ns + a] += gg;
+      if (b >= 0) G[(size_t)b * ns + b] += gg;
+      if (a >= 0 && b >= 0) {
+        G[(size_t)a * ns + b] -= gg;
+        G[(size_t)b * ns + a] -= gg;
+      }
+    };
+    for (int64_t b = 0; b < net->n_br; ++b) {
+      int32_t k = net->br_k[b], m = net->br_m[b];
+      int a = k >= 0 ? k : m;
+      if (sub[a] != s) continue;
+      stamp(k, m, g[b]);   // a source end acts like ground in G
+    }
+    for (int64_t l = 0; l < net->n_ln; ++l) {
+      T y = T(1.0) / T(net->ln_zc[l]);
+      if (sub[net->ln_k[l]] == s) G[(size_t)local[net->ln_k[l]] * ns + local[net->ln_k[l]]] += y;
+      if (sub[net->ln_m[l]] == s) G[(size_t)local[net->ln_m[l]] * ns + local[net->ln_m[l]]] += y;
+    }
+    for (int64_t w = 0; w < net->n_sw; ++w)
+      if (st[w]) stamp(net->sw_k[w], net->sw_m[w], T(1.0) / T(net->sw_r[w]));
+    lu[s] = G;
+    return lu_factor(ns, lu[s], piv[s]);
+  }
+
+  T node_voltage(int32_t x) const {
+    if (x >= 0) return v[x];
+    if (x == -1) return T(0.0);
+    return vsrc[-2 - x];
+  }
+
+  // One time step n >= 1.  Returns false if a matrix is singular.
+  bool step(int64_t n) {
+    const double t = (double)n * net->dt;
+    for (int64_t s = 0; s < net->n_src; ++s)
+      vsrc[s] = amp[s] * std::sin(2.0 * kPi * net->src_freq[s] * t + net->src_phase[s]);
+    // process 2: nodal injections u_n - A h_{n-1} - L I_n
+    std::vector<T> rhs(n_nodes, T(0.0));
+    for (int64_t b = 0; b < net->n_br; ++b) {
+      int32_t k = net->br_k[b], m = net->br_m[b];
+      if (k >= 0 && m <= -2) rhs[k] += g[b] * vsrc[-2 - m];
+      if (m >= 0 && k <= -2) rhs[m] += g[b] * vsrc[-2 - k];
+      if (net->br_kind[b] != 0) {
+        if (k >= 0) rhs[k] -= h[b];
+        if (m >= 0) rhs[m] += h[b];
+      }
+    }
+    for (int64_t l = 0; l < net->n_ln; ++l) {
+      int64_t d1 = net->ln_d[l] + 1;
+      rhs[net->ln_k[l]] -= ring_k[l][n % d1];
+      rhs[net->ln_m[l]] -= ring_m[l][n % d1];
+    }
+    // processes 3 and 4 per subsystem
+    for (int s = 0; s < n_sub; ++s) {
+      if (!refactor_if_needed(s, n)) return false;
+      int ns = (int)nodes[s].size();
+      std::vector<T> x(ns);
+      for (int i = 0; i < ns; ++i) x[i] = rhs[nodes[s][i]];
+      lu_solve(ns, lu[s], piv[s], x.data());
+      for (int i = 0; i < ns; ++i) v[nodes[s][i]] = x[i];
+    }
+    // process 1: history currents of L and C branches
+    for (int64_t b = 0; b < net->n_br; ++b) {
+      if (net->br_kind[b] == 0) continue;
+      T vb = node_voltage(net->br_k[b]) - node_voltage(net->br_m[b]);
+      if (net->br_kind[b] == 1) h[b] = h[b] + T(2.0) * g[b] * vb;
+      else h[b] = -h[b] - T(2.0) * g[b] * vb;
+    }
+    // process 1 for lines: values consumed d steps later at the far ends
+    for (int64_t l = 0; l < net->n_ln; ++l) {
+      int64_t d = net->ln_d[l], d1 = d + 1;
+      T y2 = T(2.0) / T(net->ln_zc[l]);
+      T ik = ring_k[l][n % d1], im = ring_m[l][n % d1];
+      ring_m[l][(n + d) % d1] = -y2 * v[net->ln_k[l]] - ik;
+      ring_k[l][(n + d) % d1] = -y2 * v[net->ln_m[l]] - im;
+    }
+    return true;
+  }
+};
+
+template <class T>
+int run_loss(const orc_net* net, bool monolithic, int64_t n_steps, const T* br_value, const T* src_amp,
+             const int32_t* rec, int64_t n_rec, double* v_out, const double* v_target, T* loss) {
+  Sim<T> sim;
+  sim.net = net;
+  sim.init(br_value, src_amp, monolithic);
+  T J = T(0.0);
+  for (int64_t n = 1; n <= n_steps; ++n) {
+    if (!sim.step(n)) return -2;
+    if (v_out) {
+      double* row = v_out + (size_t)(n - 1) * (rec ? n_rec : net->n_nodes);
+      if (rec)
+        for (int64_t c = 0; c < n_rec; ++c) row[c] = re(sim.v[rec[c]]);
+      else
+        for (int64_t k = 0; k < net->n_nodes; ++k) row[k] = re(sim.v[k]);
+    }
+    if (v_target && loss) {
+      const double* tg = v_target + (size_t)(n - 1) * net->n_nodes;
+      for (int64_t k = 0; k < net->n_nodes; ++k) {
+        T e = sim.v[k] - T(tg[k]);
+        J += e * e;
+      }
+    }
+  }
+  if (loss) *loss = J;
+  return 0;
+}
+
+}  // namespace
+
+extern "C" int orc_run(const orc_net* net, int monolithic, int64_t n_steps, const int32_t* rec, int64_t n_rec,
+                       double* v_out, const double* v_target, double* loss) {
+  if (!valid(net) || n_steps < 0) return -1;
+  if (rec)
+    for (int64_t c = 0; c < n_rec; ++c)
+      if (rec[c] < 0 || rec[c] >= net->n_nodes) return -1;
+  return run_loss<double>(net, monolithic != 0, n_steps, net->br_val, net->src_amp, rec, n_rec, v_out,
+                          v_target, loss);
+}
+
+extern "C" int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_target, int64_t param, double h,
+                           double* loss, double* dloss) {
+  if (!valid(net) || !v_target || param < 0 || param >= net->n_br + net->n_src) return -1;
+  std::vector<cplx> bv(net->br_val, net->br_val + net->n_br);
+  std::vector<cplx> am(net->src_amp, net->src_amp + net->n_src);
+  if (param < net->n_br) bv[param] += cplx(0.0, h);
+  else am[param - net->n_br] += cplx(0.0, h);
+  cplx J;
+  int rc = run_loss<cplx>(net, false, n_steps, bv.data(), am.data(), nullptr, 0, nullptr, v_target, &J);
+  if (rc) return rc;
+  *loss = J.real();
+  *dloss = J.imag() / h;
+  return 0;
+}
+
+// Reverse-mode (discrete adjoint) of the loop above for
+//   J = sum_{n=1..N} sum_k (v_n[k] - v*_n[k])^2.
+// With w_n = G_n^{-T} vbar_n, the reverse recursion for n = N..1 is
+//   vbar_n      = 2 (v_n - v*_n) + A E hbar_n + (line terms from I(n+d))
+//   hbar_{n-1}  = D hbar_n - A^T w_n
+//   Ibar_e(n)   = -w_n[k_e] - Ibar_f(n+d)        (f = far end of e)
+// where h_n = D h_{n-1} + E v_b(n), D = +1 (L) / -1 (C), E = 2g (L) / -2g (C).
+// Parameter terms per step:
+//   dJ/dg_b += -(a_b^T w_n) v_b(n) + hbar_n[b] (dE_b/dg_b) v_b(n)
+//   dJ/dv_s += g_b w_n[unknown end] + (-/+) E_b hbar_n[b]   (source branches)
+//   dJ/dA_s += sin(2 pi f t_n + phi) dJ/dv_s
+// and finally dg/dR = -1/R^2, dg/dL = -dt/(2L^2), dg/dC = 2/dt.
+extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad,
+                           double* loss) {
+  if (!valid(net) || !v_target || !grad || n_steps < 0) return -1;
+  const int64_t nn = net->n_nodes, nb = net->n_br, ns = net->n_src, nl = net->n_ln;
+  Sim<double> sim;
+  sim.net = net;
+  sim.init(net->br_val, net->src_amp, false);
+  std::vector<double> tape((size_t)n_steps * nn);
+  double J = 0.0;
+  for (int64_t n = 1; n <= n_steps; ++n) {
+    if (!sim.step(n)) return -2;
+    double* row = tape.data() + (size_t)(n - 1) * nn;
+    const double* tg = v_target + (size_t)(n - 1) * nn;
+    for (int64_t k = 0; k < nn; ++k) {
+      row[k] = sim.v[k];
+      double e = sim.v[k] - tg[k];
+      J += e * e;
+    }
+  }
+  if (loss) *loss = J;
+
+  std::vector<double> dg(nb, 0.0), dA(ns, 0.0), hbar(nb, 0.0), vbar(nn), w(nn), vs(ns);
+  std::vector<std::vector<double>> ibar_k(nl), ibar_m(nl);   // rings, slot n mod (d+1)
+  for (int64_t l = 0; l < nl; ++l) {
+    ibar_k[l].assign(net->ln_d[l] + 1, 0.0);
+    ibar_m[l].assign(net->ln_d[l] + 1, 0.0);
+  }
+  auto V = [&](const double* vn, int32_t x) { return x >= 0 ? vn[x] : (x == -1 ? 0.0 : vs[-2 - x]); };
+  for (int64_t n = n_steps; n >= 1; --n) {
+    const double* vn = tape.data() + (size_t)(n - 1) * nn;
+    const double* tg = v_target + (size_t)(n - 1) * nn;
+    const double t = (double)n * net->dt;
+    for (int64_t s = 0; s < ns; ++s)
+      vs[s] = net->src_amp[s] * std::sin(2.0 * kPi * net->src_freq[s] * t + net->src_phase[s]);
+    for (int64_t k = 0; k < nn; ++k) vbar[k] = 2.0 * (vn[k] - tg[k]);
+    for (int64_t b = 0; b < nb; ++b) {
+      if (net->br_kind[b] == 0) continue;
+      double E = (net->br_kind[b] == 1 ? 2.0 : -2.0) * sim.g[b];
+      if (net->br_k[b] >= 0) vbar[net->br_k[b]] += E * hbar[b];
+      if (net->br_m[b] >= 0) vbar[net->br_m[b]] -= E * hbar[b];
+    }
+    for (int64_t l = 0; l < nl; ++l) {
+      int64_t d = net->ln_d[l], d1 = d + 1;
+      double y2 = 2.0 / net->ln_zc[l];
+      vbar[net->ln_k[l]] += -y2 * ibar_m[l][(n + d) % d1];
+      vbar[net->ln_m[l]] += -y2 * ibar_k[l][(n + d) % d1];
+    }
+    // w_n = G_n^{-T} vbar_n, per subsystem with the factors of step n
+    for (int s = 0; s < sim.n_sub; ++s) {
+      if (!sim.refactor_if_needed(s, n)) return -2;
+      int m = (int)sim.nodes[s].size();
+      std::vector<double> x(m);
+      for (int i = 0; i < m; ++i) x[i] = vbar[sim.nodes[s][i]];
+      lu_solve_transposed(m, sim.lu[s], sim.piv[s], x.data());
+      for (int i = 0; i < m; ++i) w[sim.nodes[s][i]] = x[i];
+    }
+    for (int64_t b = 0; b < nb; ++b) {
+      int32_t k = net->br_k[b], m = net->br_m[b];
+      double aw = (k >= 0 ? w[k] : 0.0) - (m >= 0 ? w[m] : 0.0);
+      double vb = V(vn, k) - V(vn, m);
+      dg[b] += -aw * vb;
+      double E = 0.0;
+      if (net->br_kind[b] != 0) {
+        E = (net->br_kind[b] == 1 ? 2.0 : -2.0) * sim.g[b];
+        dg[b] += hbar[b] * (net->br_kind[b] == 1 ? 2.0 : -2.0) * vb;
+      }
+      // source amplitude terms
+      if (k <= -2 || m <= -2) {
+        int64_t s = k <= -2 ? (-2 - k) : (-2 - m);
+        int32_t u = k <= -2 ? m : k;
+        double dv = sim.g[b] * (u >= 0 ? w[u] : 0.0);
+        if (net->br_kind[b] != 0) dv += (k <= -2 ? E : -E) * hbar[b];
+        dA[s] += std::sin(2.0 * kPi * net->src_freq[s] * t + net->src_phase[s]) * dv;
+      }
+    }
+    for (int64_t b = 0; b < nb; ++b) {
+      if (net->br_kind[b] == 0) continue;
+      int32_t k = net->br_k[b], m = net->br_m[b];
+      double aw = (k >= 0 ? w[k] : 0.0) - (m >= 0 ? w[m] : 0.0);
+      hbar[b] = (net->br_kind[b] == 1 ? 1.0 : -1.0) * hbar[b] - aw;
+    }
+    for (int64_t l = 0; l < nl; ++l) {
+      int64_t d = net->ln_d[l], d1 = d + 1;
+      double far_m = ibar_m[l][(n + d) % d1], far_k = ibar_k[l][(n + d) % d1];
+      ibar_k[l][n % d1] = -w[net->ln_k[l]] - far_m;
+      ibar_m[l][n % d1] = -w[net->ln_m[l]] - far_k;
+    }
+  }
+  for (int64_t b = 0; b < nb; ++b) {
+    double x = net->br_val[b];
+    double dgdp = net->br_kind[b] == 0 ? -1.0 / (x * x) : (net->br_kind[b] == 1 ? -net->dt / (2.0 * x * x) : 2.0 / net->dt);
+    grad[b] = dg[b] * dgdp;
+  }
+  for (int64_t s = 0; s < ns; ++s) grad[nb + s] = dA[s];
+  return 0;
+}
+
+extern "C" int orc_partition(const orc_net* net, int32_t* sub_of_node, int64_t* n_sub) {
+  if (!valid(net)) return -1;
+  std::vector<int> sub;
+  int ns = 0;
+  components(net, sub, ns);
+  for (int64_t i = 0; i < net->n_nodes; ++i) sub_of_node[i] = sub[i];
+  *n_sub = ns;
+  return 0;
+}
+
+extern "C" int orc_lu_solve(int64_t n, const double* A, const double* b, double* x) {
+  if (n <= 0) return -1;
+  std::vector<double> a(A, A + n * n);
+  std::vector<int> piv;
+  if (!lu_factor<double>((int)n, a, piv)) return -2;
+  for (int64_t i = 0; i < n; ++i) x[i] = b[i];
+  lu_solve<double>((int)n, a, piv, x);
+  return 0;
+}

@@ -1,0 +1,82 @@
+/*
+ * Plain FP64 CPU oracle for the EMTP-type time loop (test infrastructure).
+ *
+ * This library exists to check the CUDA path; only tests, the package's
+ * smoke entry and the benchmark's CPU-baseline leg may load it.  It shares
+ * no code, header or table with the CUDA library.
+ *
+ * Method (Sec. III-A of the CloudPSS paper lists the four basic processes of
+ * the EMTP-type algorithm, ref. [2] gives the formulas):
+ *   1. update Norton equivalent conductance / history current per element
+ *      (trapezoidal companion models of R, L, C; Bergeron lossless lines),
+ *   2. update nodal injected currents,
+ *   3. factorise the conductance matrix (whenever it changes),
+ *   4. forward / backward substitution for the node voltages.
+ * Node codes: k >= 0 unknown node, -1 ground, -2-s known node of source s.
+ */
+#ifndef EMT_ORACLE_H
+#define EMT_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  double dt;
+  int64_t n_nodes;
+  int64_t n_br;
+  const int32_t* br_k;
+  const int32_t* br_m;
+  const uint8_t* br_kind;   /* 0 = R, 1 = L, 2 = C */
+  const double* br_val;     /* ohm, henry, farad */
+  int64_t n_src;
+  const double* src_amp;
+  const double* src_phase;
+  const double* src_freq;
+  int64_t n_ln;
+  const int32_t* ln_k;
+  const int32_t* ln_m;
+  const double* ln_zc;
+  const int32_t* ln_d;      /* travel time in steps, >= 1 */
+  int64_t n_sw;
+  const int32_t* sw_k;
+  const int32_t* sw_m;
+  const double* sw_r;
+  const int64_t* sw_on;     /* closed for sw_on <= n < sw_off */
+  const int64_t* sw_off;    /* -1 = never opens */
+} orc_net;
+
+/* Run n_steps steps from the de-energised state.
+ *   monolithic = 1: one conductance matrix over all unknown nodes;
+ *   monolithic = 0: one matrix per subsystem (components joined by
+ *                   branches and switches; lines cut them).
+ *   rec / n_rec: recorded nodes (rec = NULL: all nodes in order);
+ *   v_out: [n_steps][n_rec] node voltages of steps 1..n_steps (may be NULL);
+ *   v_target / loss: if both non-NULL, loss = sum_n sum_k (v_n[k]-v*_n[k])^2
+ *   over all nodes, v_target laid out [n_steps][n_nodes].
+ * Returns 0, or a negative code: -1 invalid input, -2 singular matrix. */
+int orc_run(const orc_net* net, int monolithic, int64_t n_steps, const int32_t* rec, int64_t n_rec,
+            double* v_out, const double* v_target, double* loss);
+
+/* Complex-step derivative of the loss with respect to parameter `param`
+ * (0..n_br-1: branch value; n_br..n_br+n_src-1: source amplitude):
+ * runs the same loop in complex arithmetic with p -> p + i*h.
+ * loss = Re J, dloss = Im J / h. */
+int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_target, int64_t param, double h,
+                double* loss, double* dloss);
+
+/* Discrete adjoint of the loss over the full stored trajectory.
+ * grad: [n_br + n_src] = dJ/d(branch value) then dJ/d(source amplitude). */
+int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad, double* loss);
+
+/* Subsystem of each unknown node (components over branches and switches). */
+int orc_partition(const orc_net* net, int32_t* sub_of_node, int64_t* n_sub);
+
+/* Dense LU with partial pivoting: solve A x = b, A row-major n x n. */
+int orc_lu_solve(int64_t n, const double* A, const double* b, double* x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

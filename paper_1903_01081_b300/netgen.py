@@ -1,0 +1,545 @@
+"""Seeded synthetic network generator.
+
+This module only draws inputs: topology, element values, sources, lines,
+switches and per-scenario overrides.  It holds none of the simulation's
+arithmetic (no companion conductances, no partitioning, no solves), so both
+the CUDA path and the CPU oracle can take its output as their common input.
+
+Node codes follow one convention everywhere:
+  * ``k >= 0``   an unknown node,
+  * ``k == -1``  ground,
+  * ``k == -2-s`` the known-voltage node of source ``s``.
+
+Element value ranges are those of the paper's test-case family as stated for
+the synthetic workloads: R ~ U[0.1, 10] ohm, L ~ U[1, 100] mH,
+C ~ U[1, 100] uF, sources of 1 kV peak at 60 Hz, lossless lines with
+Z_c ~ U[200, 500] ohm and integer travel times of 1..20 steps.  The paper's
+own test feeder (Sec. IV-A, Fig. 5) is not available, so these networks
+stand in for its large-scale and multi-scenario cases (Sec. IV-B, IV-C).
+"""
+from __future__ import annotations
+
+import dataclasses
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+R_RANGE = (0.1, 10.0)          # ohm
+L_RANGE = (1e-3, 100e-3)       # henry
+C_RANGE = (1e-6, 100e-6)       # farad
+ZC_RANGE = (200.0, 500.0)      # ohm
+DELAY_RANGE = (1, 20)          # steps, inclusive
+V_PEAK = 1000.0                # volt (1 kV peak = 1 p.u.)
+F_HZ = 60.0
+R_FAULT = 0.01                 # ohm
+
+KIND_R, KIND_L, KIND_C = 0, 1, 2
+GROUND = -1
+
+
+def source_node(s: int) -> int:
+    """Node code of the known-voltage node of source ``s``."""
+    return -2 - s
+
+
+@dataclass
+class Network:
+    """Plain arrays describing one network (all numpy, C-contiguous)."""
+    dt: float
+    n_nodes: int
+    br_k: np.ndarray            # int32 [n_br]
+    br_m: np.ndarray            # int32 [n_br]
+    br_kind: np.ndarray         # uint8 [n_br]  0=R 1=L 2=C
+    br_value: np.ndarray        # float64 [n_br] ohm / henry / farad
+    src_amp: np.ndarray         # float64 [n_src] peak volts
+    src_phase: np.ndarray       # float64 [n_src] rad
+    src_freq: np.ndarray        # float64 [n_src] Hz
+    ln_k: np.ndarray            # int32 [n_ln]
+    ln_m: np.ndarray            # int32 [n_ln]
+    ln_zc: np.ndarray           # float64 [n_ln] ohm
+    ln_delay: np.ndarray        # int32 [n_ln] steps >= 1
+    sw_k: np.ndarray            # int32 [n_sw]
+    sw_m: np.ndarray            # int32 [n_sw]
+    sw_r: np.ndarray            # float64 [n_sw] ohm (closed resistance)
+    sw_close_step: np.ndarray   # int64 [n_sw]; closed for close <= n < open
+    sw_open_step: np.ndarray    # int64 [n_sw]; -1 = never opens
+    n_steps: int = 0            # suggested run length
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_branches(self) -> int:
+        return int(self.br_k.shape[0])
+
+    @property
+    def n_sources(self) -> int:
+        return int(self.src_amp.shape[0])
+
+    @property
+    def n_lines(self) -> int:
+        return int(self.ln_k.shape[0])
+
+    @property
+    def n_switches(self) -> int:
+        return int(self.sw_k.shape[0])
+
+    def copy(self) -> "Network":
+        kw = {}
+        for f in dataclasses.fields(self):
+            v = getattr(self, f.name)
+            kw[f.name] = v.copy() if isinstance(v, np.ndarray) else (dict(v) if isinstance(v, dict) else v)
+        return Network(**kw)
+
+    def with_params(self, br_value: Optional[np.ndarray] = None, src_amp: Optional[np.ndarray] = None) -> "Network":
+        net = self.copy()
+        if br_value is not None:
+            net.br_value = np.ascontiguousarray(br_value, dtype=np.float64)
+        if src_amp is not None:
+            net.src_amp = np.ascontiguousarray(src_amp, dtype=np.float64)
+        return net
+
+
+@dataclass
+class Scenarios:
+    """Per-scenario overrides of a base network.
+
+    * ``src_amp`` / ``src_phase``: [S, n_src] or None (base values).
+    * removed branches / lines: CSR lists (``*_ptr`` has S+1 entries).
+    * extra switches (faults): CSR over scenarios of (k, m, r, close, open).
+    """
+    n_scenarios: int
+    src_amp: Optional[np.ndarray] = None
+    src_phase: Optional[np.ndarray] = None
+    rm_branch_ptr: Optional[np.ndarray] = None
+    rm_branch: Optional[np.ndarray] = None
+    rm_line_ptr: Optional[np.ndarray] = None
+    rm_line: Optional[np.ndarray] = None
+    sw_ptr: Optional[np.ndarray] = None
+    sw_k: Optional[np.ndarray] = None
+    sw_m: Optional[np.ndarray] = None
+    sw_r: Optional[np.ndarray] = None
+    sw_close_step: Optional[np.ndarray] = None
+    sw_open_step: Optional[np.ndarray] = None
+    meta: dict = field(default_factory=dict)
+
+    def subset(self, idx) -> "Scenarios":
+        """The scenarios ``idx`` (a sequence of indices) as a new set."""
+        idx = [int(i) for i in idx]
+        out = Scenarios(n_scenarios=len(idx), meta=dict(self.meta))
+        if self.src_amp is not None:
+            out.src_amp = np.ascontiguousarray(self.src_amp[idx])
+        if self.src_phase is not None:
+            out.src_phase = np.ascontiguousarray(self.src_phase[idx])
+
+        def sub_csr(ptr, *cols):
+            if ptr is None:
+                return (None,) * (len(cols) + 1)
+            new_ptr = [0]
+            parts = [[] for _ in cols]
+            for i in idx:
+                a, b = int(ptr[i]), int(ptr[i + 1])
+                for p, c in zip(parts, cols):
+                    p.append(c[a:b])
+                new_ptr.append(new_ptr[-1] + (b - a))
+            res = [np.asarray(new_ptr, dtype=np.int64)]
+            for p, c in zip(parts, cols):
+                res.append(np.ascontiguousarray(np.concatenate(p) if p else c[:0]).astype(c.dtype))
+            return tuple(res)
+
+        out.rm_branch_ptr, out.rm_branch = sub_csr(self.rm_branch_ptr, self.rm_branch) if self.rm_branch_ptr is not None else (None, None)
+        out.rm_line_ptr, out.rm_line = sub_csr(self.rm_line_ptr, self.rm_line) if self.rm_line_ptr is not None else (None, None)
+        if self.sw_ptr is not None:
+            (out.sw_ptr, out.sw_k, out.sw_m, out.sw_r, out.sw_close_step, out.sw_open_step) = sub_csr(
+                self.sw_ptr, self.sw_k, self.sw_m, self.sw_r, self.sw_close_step, self.sw_open_step)
+        return out
+
+    def expand(self, base: Network, s: int) -> Network:
+        """Scenario ``s`` written out as a plain network.
+
+        Removed branches and lines are dropped, extra switches appended and
+        source overrides substituted.  This is input bookkeeping only.
+        """
+        net = base.copy()
+        if self.src_amp is not None:
+            net.src_amp = np.ascontiguousarray(self.src_amp[s], dtype=np.float64)
+        if self.src_phase is not None:
+            net.src_phase = np.ascontiguousarray(self.src_phase[s], dtype=np.float64)
+        if self.rm_branch_ptr is not None:
+            rm = set(int(x) for x in self.rm_branch[self.rm_branch_ptr[s]:self.rm_branch_ptr[s + 1]])
+            keep = np.array([i not in rm for i in range(base.n_branches)], dtype=bool)
+            for f in ("br_k", "br_m", "br_kind", "br_value"):
+                setattr(net, f, np.ascontiguousarray(getattr(net, f)[keep]))
+            net.meta["kept_branches"] = np.nonzero(keep)[0]
+        if self.rm_line_ptr is not None:
+            rm = set(int(x) for x in self.rm_line[self.rm_line_ptr[s]:self.rm_line_ptr[s + 1]])
+            keep = np.array([i not in rm for i in range(base.n_lines)], dtype=bool)
+            for f in ("ln_k", "ln_m", "ln_zc", "ln_delay"):
+                setattr(net, f, np.ascontiguousarray(getattr(net, f)[keep]))
+        if self.sw_ptr is not None:
+            a, b = int(self.sw_ptr[s]), int(self.sw_ptr[s + 1])
+            net.sw_k = np.ascontiguousarray(np.concatenate([net.sw_k, self.sw_k[a:b]]).astype(np.int32))
+            net.sw_m = np.ascontiguousarray(np.concatenate([net.sw_m, self.sw_m[a:b]]).astype(np.int32))
+            net.sw_r = np.ascontiguousarray(np.concatenate([net.sw_r, self.sw_r[a:b]]).astype(np.float64))
+            net.sw_close_step = np.ascontiguousarray(
+                np.concatenate([net.sw_close_step, self.sw_close_step[a:b]]).astype(np.int64))
+            net.sw_open_step = np.ascontiguousarray(
+                np.concatenate([net.sw_open_step, self.sw_open_step[a:b]]).astype(np.int64))
+        return net
+
+
+# ----------------------------------------------------------------------------
+# helpers
+
+def _value(rng: np.random.Generator, kind: int) -> float:
+    lo, hi = (R_RANGE, L_RANGE, C_RANGE)[kind]
+    return float(rng.uniform(lo, hi))
+
+
+class NetworkBuilder:
+    def __init__(self):
+        self.br = []     # (k, m, kind, value)
+        self.src = []    # (amp, phase, freq)
+        self.ln = []     # (k, m, zc, d)
+        self.sw = []     # (k, m, r, close, open)
+
+    def branch(self, k, m, kind, value):
+        self.br.append((int(k), int(m), int(kind), float(value)))
+        return len(self.br) - 1
+
+    def source(self, amp, phase, freq=F_HZ):
+        self.src.append((float(amp), float(phase), float(freq)))
+        return len(self.src) - 1
+
+    def line(self, k, m, zc, d):
+        self.ln.append((int(k), int(m), float(zc), int(d)))
+        return len(self.ln) - 1
+
+    def switch(self, k, m, r, close, open_=-1):
+        self.sw.append((int(k), int(m), float(r), int(close), int(open_)))
+
+    def build(self, dt, n_nodes, n_steps=0, meta=None) -> Network:
+        def col(lst, i, dt_):
+            return np.ascontiguousarray(np.array([x[i] for x in lst], dtype=dt_))
+        return Network(
+            dt=float(dt), n_nodes=int(n_nodes),
+            br_k=col(self.br, 0, np.int32), br_m=col(self.br, 1, np.int32),
+            br_kind=col(self.br, 2, np.uint8), br_value=col(self.br, 3, np.float64),
+            src_amp=col(self.src, 0, np.float64), src_phase=col(self.src, 1, np.float64),
+            src_freq=col(self.src, 2, np.float64),
+            ln_k=col(self.ln, 0, np.int32), ln_m=col(self.ln, 1, np.int32),
+            ln_zc=col(self.ln, 2, np.float64), ln_delay=col(self.ln, 3, np.int32),
+            sw_k=col(self.sw, 0, np.int32), sw_m=col(self.sw, 1, np.int32),
+            sw_r=col(self.sw, 2, np.float64), sw_close_step=col(self.sw, 3, np.int64),
+            sw_open_step=col(self.sw, 4, np.int64), n_steps=int(n_steps), meta=dict(meta or {}))
+
+
+# ----------------------------------------------------------------------------
+# single-subsystem random RLC network (config 1 shape)
+
+def single_rlc(seed: int = 1001, n_nodes: int = 12, n_branches: int = 20, dt: float = 50e-6,
+               n_steps: int = 20000, fault_step: Optional[int] = 2000) -> Network:
+    """Random single-phase RLC network with one 60 Hz source of 1 kV peak.
+
+    Topology: a random spanning tree over {ground, source node, unknown
+    nodes} plus random extra edges up to ``n_branches`` (never ground to
+    source, never a self loop, no duplicate pair).  Each branch holds one
+    element whose kind is uniform over {R, L, C}.  A 0.01 ohm fault switch to
+    ground at a random unknown node closes at ``fault_step``.
+    """
+    rng = np.random.default_rng(seed)
+    b = NetworkBuilder()
+    b.source(V_PEAK, 0.0)
+    # vertices: 0 = ground, 1 = source, 2.. = unknown nodes
+    nv = n_nodes + 2
+    code = lambda v: GROUND if v == 0 else (source_node(0) if v == 1 else v - 2)
+    edges = []
+    seen = set()
+
+    def add(a, c):
+        key = (min(a, c), max(a, c))
+        if a == c or key == (0, 1) or key in seen:
+            return False
+        seen.add(key)
+        edges.append(key)
+        return True
+
+    # spanning tree over {ground, unknown nodes} by random attachment,
+    # then the source vertex hangs off a random unknown node
+    order = [0] + [int(x) + 2 for x in rng.permutation(n_nodes)]
+    for i in range(1, len(order)):
+        add(order[i], order[int(rng.integers(0, i))])
+    add(1, int(rng.integers(2, nv)))
+    while len(edges) < n_branches:
+        a, c = (int(x) for x in rng.integers(0, nv, size=2))
+        add(a, c)
+    for (a, c) in edges:
+        kind = int(rng.integers(0, 3))
+        k, m = code(c), code(a)   # c > a, so k is never ground
+        if m >= 0 and rng.random() < 0.5:
+            k, m = m, k
+        b.branch(k, m, kind, _value(rng, kind))
+    if fault_step is not None:
+        node = int(rng.integers(0, n_nodes))
+        b.switch(node, GROUND, R_FAULT, fault_step, -1)
+    return b.build(dt, n_nodes, n_steps, meta={"kind": "single_rlc", "seed": seed})
+
+
+# ----------------------------------------------------------------------------
+# multi-subsystem three-phase networks cut by Bergeron lines (configs 2-5)
+
+def multi_subsystem(seed: int, bus_counts, n_lines: int, n_sources: int, dt: float,
+                    n_steps: int = 0, phases: int = 3, p2p_frac: float = 0.2,
+                    n_series_extra: int = 0, source_phase_random: bool = True,
+                    shunt_kinds=(KIND_R, KIND_L, KIND_C), shuffle_nodes: bool = True,
+                    delay_range=DELAY_RANGE, zc_range=ZC_RANGE) -> Network:
+    """Three-phase (or single-phase) network made of subsystems cut by lines.
+
+    * ``bus_counts[j]`` buses in subsystem j; each bus has ``phases`` nodes.
+    * inside a subsystem: a random spanning tree of series connections over
+      its buses plus ``n_series_extra`` extra connections network-wide; a
+      series connection is one branch per phase, kind uniform over {R, L, C}
+      per connection, value drawn per phase.
+    * every node has one shunt branch to ground (kind from ``shunt_kinds``).
+    * every subsystem gets phase-to-phase branches (a-b, b-c) at one random
+      bus, and ``p2p_frac`` of all buses get one more phase-to-phase branch.
+    * ``n_lines`` lines: first a random spanning tree over the subsystems,
+      then random pairs of distinct subsystems; a line joins a random bus of
+      each side, one lossless conductor per phase, with one Z_c and one delay
+      per line.
+    * ``n_sources`` sources: one known node per phase at 1 kV peak, phase
+      shifts 0, -2pi/3, +2pi/3 on top of a random (or zero) angle, each
+      joined to its bus's phase node by an R or L branch.
+    Unknown node numbers are randomly permuted when ``shuffle_nodes``.
+    """
+    rng = np.random.default_rng(seed)
+    bus_counts = [int(x) for x in bus_counts]
+    n_sub = len(bus_counts)
+    n_bus = sum(bus_counts)
+    n_nodes = n_bus * phases
+    perm = rng.permutation(n_nodes) if shuffle_nodes else np.arange(n_nodes)
+    node = lambda bus, p: int(perm[bus * phases + p])
+    sub_of_bus = np.repeat(np.arange(n_sub), bus_counts)
+    first_bus = np.concatenate([[0], np.cumsum(bus_counts)[:-1]]).astype(int)
+    b = NetworkBuilder()
+
+    def series(ba, bb, kind=None):
+        kind = int(rng.integers(0, 3)) if kind is None else kind
+        for p in range(phases):
+            b.branch(node(ba, p), node(bb, p), kind, _value(rng, kind))
+
+    conn = []  # inter-bus three-phase connections: ("br", [branch ids]) or ("ln", [line ids])
+    for j in range(n_sub):
+        f, nb = first_bus[j], bus_counts[j]
+        for i in range(1, nb):
+            a = f + i
+            c = f + int(rng.integers(0, i))
+            start = len(b.br)
+            series(a, c)
+            conn.append(("br", list(range(start, len(b.br)))))
+    for _ in range(n_series_extra):
+        j = int(rng.integers(0, n_sub))
+        if bus_counts[j] < 2:
+            continue
+        a, c = rng.choice(bus_counts[j], size=2, replace=False) + first_bus[j]
+        start = len(b.br)
+        series(int(a), int(c))
+        conn.append(("br", list(range(start, len(b.br)))))
+    for bus in range(n_bus):
+        for p in range(phases):
+            kind = int(rng.choice(shunt_kinds))
+            b.branch(node(bus, p), GROUND, kind, _value(rng, kind))
+    if phases >= 2:
+        # couple the phases of every subsystem at one random bus so that a
+        # subsystem is one electrical component, not one per phase
+        for j in range(n_sub):
+            bus = first_bus[j] + int(rng.integers(0, bus_counts[j]))
+            for p in range(phases - 1):
+                kind = int(rng.integers(0, 3))
+                b.branch(node(bus, p), node(bus, p + 1), kind, _value(rng, kind))
+        for bus in range(n_bus):
+            if rng.random() < p2p_frac:
+                p, q = rng.choice(phases, size=2, replace=False)
+                kind = int(rng.integers(0, 3))
+                b.branch(node(bus, int(p)), node(bus, int(q)), kind, _value(rng, kind))
+    # lines
+    pairs = []
+    order = rng.permutation(n_sub)
+    for i in range(1, n_sub):
+        pairs.append((int(order[i]), int(order[rng.integers(0, i)])))
+    while len(pairs) < n_lines and n_sub >= 2:
+        a, c = rng.choice(n_sub, size=2, replace=False)
+        pairs.append((int(a), int(c)))
+    for (sa, sb) in pairs[:n_lines]:
+        ba = first_bus[sa] + int(rng.integers(0, bus_counts[sa]))
+        bb = first_bus[sb] + int(rng.integers(0, bus_counts[sb]))
+        zc = float(rng.uniform(*zc_range))
+        d = int(rng.integers(delay_range[0], delay_range[1] + 1))
+        start = len(b.ln)
+        for p in range(phases):
+            b.line(node(ba, p), node(bb, p), zc, d)
+        conn.append(("ln", list(range(start, len(b.ln)))))
+    # sources
+    shifts = [0.0, -2.0 * np.pi / 3.0, 2.0 * np.pi / 3.0][:phases]
+    src_bus = []
+    for _ in range(n_sources):
+        bus = int(rng.integers(0, n_bus))
+        src_bus.append(bus)
+        phi0 = float(rng.uniform(0.0, 2.0 * np.pi)) if source_phase_random else 0.0
+        kind = int(rng.integers(0, 2))   # R or L source impedance
+        for p in range(phases):
+            s = b.source(V_PEAK, phi0 + shifts[p])
+            b.branch(source_node(s), node(bus, p), kind, _value(rng, kind))
+    meta = {"kind": "multi_subsystem", "seed": seed, "bus_counts": bus_counts, "phases": phases,
+            "n_subsystems": n_sub, "connections": conn, "source_bus": src_bus,
+            "bus_nodes": [[node(bus, p) for p in range(phases)] for bus in range(n_bus)]}
+    return b.build(dt, n_nodes, n_steps, meta=meta)
+
+
+def _sizes_uniform_to_total(rng, total, lo, hi):
+    """Draw sizes ~ U{lo..hi} until they sum to ``total`` (last one clipped/merged)."""
+    sizes = []
+    left = total
+    while left > 0:
+        s = int(rng.integers(lo, hi + 1))
+        if left - s < lo and left - s != 0:
+            s = left if left <= hi else left - lo
+        s = min(s, left)
+        sizes.append(s)
+        left -= s
+    return sizes
+
+
+def _sizes_fixed_count(rng, total, count, lo, hi):
+    """``count`` sizes in [lo, hi] summing to ``total``: start at ``lo``, add units at random."""
+    sizes = np.full(count, lo, dtype=int)
+    left = total - lo * count
+    assert 0 <= left <= (hi - lo) * count
+    while left > 0:
+        j = int(rng.integers(0, count))
+        if sizes[j] < hi:
+            sizes[j] += 1
+            left -= 1
+    return [int(x) for x in sizes]
+
+
+def large_scale(seed: int = 1002, n_buses: int = 1000, n_lines: int = 700, n_sources: int = 50,
+                dt: float = 20e-6, n_steps: int = 50000, target_branches: int = 6000,
+                strict_500: bool = False) -> Network:
+    """Large-scale three-phase network: 1,000 buses (3,000 nodes), ~6,000
+    branches, 700 three-phase Bergeron lines, 50 three-phase sources.
+
+    Subsystem sizes are 3*U{2..20} nodes drawn until the 1,000 buses are used
+    (the subsystem count falls out, about a hundred).  ``strict_500`` instead
+    makes 500 subsystems of 2 buses (6 nodes) each.
+    """
+    rng = np.random.default_rng(seed)
+    if strict_500:
+        bus_counts = [2] * (n_buses // 2)
+    else:
+        bus_counts = _sizes_uniform_to_total(rng, n_buses, 2, 20)
+    tree = n_buses - len(bus_counts)
+    p2p = int(round(0.2 * n_buses)) + 2 * len(bus_counts)
+    extra = max(0, (target_branches - 3 * n_buses - p2p - 3 * n_sources - 3 * tree) // 3)
+    sub_seed = int(rng.integers(0, 2**31))
+    net = multi_subsystem(sub_seed, bus_counts, n_lines, n_sources, dt, n_steps=n_steps,
+                          n_series_extra=extra)
+    net.meta.update({"config": "large_scale_strict500" if strict_500 else "large_scale", "seed": seed})
+    return net
+
+
+def n1_contingency(seed: int = 1003, n_scenarios: int = 1024, n_buses: int = 200, n_sub: int = 40,
+                   n_lines: int = 56, n_sources: int = 10, dt: float = 20e-6, n_steps: int = 10000,
+                   fault_step: int = 2500, target_branches: int = 1200):
+    """Multi-scenario N-1 workload: a 200-bus (600-node) network in 40
+    subsystems of 2..15 buses; scenario s removes one random three-phase
+    connection (series branch triplet or line) and applies a three-phase
+    fault (three 0.01 ohm phase-to-ground resistors) at a random bus at
+    ``fault_step``.  Scenario s draws from ``default_rng([seed, s])``.
+    """
+    rng = np.random.default_rng(seed)
+    bus_counts = _sizes_fixed_count(rng, n_buses, n_sub, 2, 15)
+    tree = n_buses - n_sub
+    p2p = int(round(0.2 * n_buses)) + 2 * n_sub
+    extra = max(0, (target_branches - 3 * n_buses - p2p - 3 * n_sources - 3 * tree) // 3)
+    net = multi_subsystem(int(rng.integers(0, 2**31)), bus_counts, n_lines, n_sources, dt,
+                          n_steps=n_steps, n_series_extra=extra)
+    net.meta.update({"config": "n1_contingency", "seed": seed})
+    conns = net.meta["connections"]
+    n_bus = n_buses
+    rm_b_ptr, rm_b, rm_l_ptr, rm_l = [0], [], [0], []
+    sw_ptr, swk, swm, swr, swc, swo = [0], [], [], [], [], []
+    removed = []
+    for s in range(n_scenarios):
+        srng = np.random.default_rng([seed, s])
+        kind, ids = conns[int(srng.integers(0, len(conns)))]
+        removed.append((kind, list(ids)))
+        if kind == "br":
+            rm_b.extend(ids)
+        else:
+            rm_l.extend(ids)
+        rm_b_ptr.append(len(rm_b))
+        rm_l_ptr.append(len(rm_l))
+        bus = int(srng.integers(0, n_bus))
+        for nd in net.meta["bus_nodes"][bus]:
+            swk.append(nd); swm.append(GROUND); swr.append(R_FAULT); swc.append(fault_step); swo.append(-1)
+        sw_ptr.append(len(swk))
+    sc = Scenarios(
+        n_scenarios=n_scenarios,
+        rm_branch_ptr=np.asarray(rm_b_ptr, np.int64), rm_branch=np.asarray(rm_b, np.int32),
+        rm_line_ptr=np.asarray(rm_l_ptr, np.int64), rm_line=np.asarray(rm_l, np.int32),
+        sw_ptr=np.asarray(sw_ptr, np.int64), sw_k=np.asarray(swk, np.int32), sw_m=np.asarray(swm, np.int32),
+        sw_r=np.asarray(swr, np.float64), sw_close_step=np.asarray(swc, np.int64),
+        sw_open_step=np.asarray(swo, np.int64), meta={"removed": removed, "fault_step": fault_step})
+    return net, sc
+
+
+def shared_g(seed: int = 1004, n_scenarios: int = 4096, dt: float = 20e-6, n_steps: int = 10000,
+             fault_step: int = 2500, base: Optional[Network] = None):
+    """Shared-G multi-scenario workload on the large-scale topology.
+
+    Scenario s: each three-phase source gets amplitude 1 kV * U[0.9, 1.1]
+    and angle U[0, 2pi) (phases keep their -2pi/3, +2pi/3 shifts); a
+    three-phase fault of resistance R_f ~ U[0.01, 10] ohm per phase to
+    ground at one seeded bus (the same bus for all scenarios) closes at
+    ``fault_step``.
+    """
+    if base is None:
+        base = large_scale(n_steps=n_steps, dt=dt)
+    net = base.copy()
+    net.dt = dt
+    net.n_steps = n_steps
+    rng = np.random.default_rng(seed)
+    n_bus = len(net.meta["bus_nodes"])
+    phases = net.meta["phases"]
+    fault_bus = int(rng.integers(0, n_bus))
+    n_src = net.n_sources
+    n3 = n_src // phases
+    shifts = np.array([0.0, -2.0 * np.pi / 3.0, 2.0 * np.pi / 3.0][:phases])
+    amp = np.empty((n_scenarios, n_src))
+    ph = np.empty((n_scenarios, n_src))
+    sw_ptr, swk, swm, swr, swc, swo = [0], [], [], [], [], []
+    for s in range(n_scenarios):
+        srng = np.random.default_rng([seed, s])
+        a = srng.uniform(0.9, 1.1, size=n3) * V_PEAK
+        phi = srng.uniform(0.0, 2.0 * np.pi, size=n3)
+        amp[s] = np.repeat(a, phases)
+        ph[s] = (phi[:, None] + shifts[None, :]).reshape(-1)
+        rf = float(srng.uniform(0.01, 10.0))
+        for nd in net.meta["bus_nodes"][fault_bus]:
+            swk.append(nd); swm.append(GROUND); swr.append(rf); swc.append(fault_step); swo.append(-1)
+        sw_ptr.append(len(swk))
+    sc = Scenarios(n_scenarios=n_scenarios, src_amp=amp, src_phase=ph,
+                   sw_ptr=np.asarray(sw_ptr, np.int64), sw_k=np.asarray(swk, np.int32),
+                   sw_m=np.asarray(swm, np.int32), sw_r=np.asarray(swr, np.float64),
+                   sw_close_step=np.asarray(swc, np.int64), sw_open_step=np.asarray(swo, np.int64),
+                   meta={"fault_bus": fault_bus, "fault_step": fault_step})
+    return net, sc
+
+
+def adjoint_target(net: Network, seed: int = 1005, rel: float = 0.05):
+    """Perturbed parameters p* = p (1 + delta), delta ~ U[-rel, rel], for
+    every branch value and every source amplitude (the target run)."""
+    rng = np.random.default_rng(seed)
+    br = net.br_value * (1.0 + rng.uniform(-rel, rel, size=net.n_branches))
+    amp = net.src_amp * (1.0 + rng.uniform(-rel, rel, size=net.n_sources))
+    return br, amp
