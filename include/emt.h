@@ -1,0 +1,180 @@
+/*
+ * libemt -- EMTP-type electromagnetic-transient time loop on one B300 GPU.
+ *
+ * C ABI.  All arguments are plain pointers and sizes; no C++ or PyTorch
+ * types cross this boundary.  Every call returns an emt_status; no
+ * exception or abort crosses it.  One context per host thread.
+ *
+ * The computation is the fixed-step nodal-analysis loop of the EMTP-type
+ * algorithm the CloudPSS paper builds on (Sec. III-A, its four basic
+ * processes: update Norton equivalents, update nodal injections, factorise
+ * the conductance matrix, solve for the node voltages; formulas from its
+ * ref. [2]).  Here the factorisation is an explicit inverse G^-1 computed
+ * once per subsystem and switch state, and lossless Bergeron lines cut the
+ * network into subsystems that exchange history currents one or more steps
+ * late.
+ *
+ * Node codes in every node argument:
+ *   k >= 0       unknown node k (0 <= k < n_nodes)
+ *   k == -1      ground
+ *   k == -2 - s  known-voltage node of source s: v = A_s sin(2 pi f_s t + phi_s)
+ *
+ * Time: step n = 1, 2, ... is at t_n = n dt.  The loop starts de-energised
+ * (all voltages, history currents and line histories zero; source voltages
+ * count as zero at n = 0).
+ */
+#ifndef EMT_H
+#define EMT_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EMT_OK = 0,
+  EMT_EINVAL = 1,     /* invalid argument or network description */
+  EMT_ESINGULAR = 2,  /* a subsystem conductance matrix is singular */
+  EMT_ENOMEM = 3,     /* device or host allocation failed */
+  EMT_ECUDA = 4,      /* a CUDA runtime call failed (message in emt_last_error) */
+  EMT_ETIMEOUT = 5,   /* a device wait for another subsystem's line values ran out */
+  EMT_ERESOURCE = 6,  /* the persistent launch cannot be co-resident / too large */
+  EMT_ESTATE = 7      /* call out of order (e.g. step before prefactor) */
+} emt_status;
+
+typedef struct emt_ctx emt_ctx;  /* opaque; owns all device memory it allocates */
+
+/* Network description.  All arrays are caller-owned and COPIED by
+ * emt_build_network; they may be freed afterwards.
+ *
+ * Branches (R, L or C, one element each; trapezoidal companion model):
+ *   br_k, br_m: end nodes (node codes; not both known, k != m)
+ *   br_kind: 0 = R (ohm), 1 = L (henry), 2 = C (farad); br_value > 0
+ * Sources: src_amp (peak volts), src_phase (rad), src_freq (Hz).
+ * Lossless Bergeron lines: ln_k, ln_m unknown nodes, ln_zc > 0 (ohm),
+ *   ln_delay >= 1 (travel time in whole steps).
+ * Switches (ideal resistors while closed): sw_k, sw_m (unknown node or
+ *   ground), sw_r > 0 (ohm); closed for sw_close_step <= n < sw_open_step,
+ *   sw_open_step = -1 never opens, sw_close_step = -1 never closes. */
+typedef struct {
+  double dt;
+  int64_t n_nodes;
+  int64_t n_branches;
+  const int32_t* br_k;
+  const int32_t* br_m;
+  const uint8_t* br_kind;
+  const double* br_value;
+  int64_t n_sources;
+  const double* src_amp;
+  const double* src_phase;
+  const double* src_freq;
+  int64_t n_lines;
+  const int32_t* ln_k;
+  const int32_t* ln_m;
+  const double* ln_zc;
+  const int32_t* ln_delay;
+  int64_t n_switches;
+  const int32_t* sw_k;
+  const int32_t* sw_m;
+  const double* sw_r;
+  const int64_t* sw_close_step;
+  const int64_t* sw_open_step;
+} emt_network_desc;
+
+/* Optional per-scenario overrides of one base network (the paper's
+ * multi-scenario studies, Sec. III-B / IV-C).  NULL pointer fields mean
+ * "same as the base network".  All arrays are caller-owned and copied.
+ *   src_amp, src_phase: [n_scenarios][n_sources] row-major
+ *   rm_branch_ptr[n_scenarios+1], rm_branch[]: branches removed per scenario
+ *   rm_line_ptr[n_scenarios+1], rm_line[]:     lines removed per scenario
+ *   sw_ptr[n_scenarios+1], sw_k[], sw_m[], sw_r[], sw_close_step[],
+ *     sw_open_step[]: switches added per scenario (same rules as above). */
+typedef struct {
+  int64_t n_scenarios;
+  const double* src_amp;
+  const double* src_phase;
+  const int64_t* rm_branch_ptr;
+  const int32_t* rm_branch;
+  const int64_t* rm_line_ptr;
+  const int32_t* rm_line;
+  const int64_t* sw_ptr;
+  const int32_t* sw_k;
+  const int32_t* sw_m;
+  const double* sw_r;
+  const int64_t* sw_close_step;
+  const int64_t* sw_open_step;
+} emt_scenario_desc;
+
+/* Validate the description, split the network into subsystems (connected
+ * components over branches and switches; lines are the cuts), number the
+ * nodes subsystem by subsystem and upload the network to the current CUDA
+ * device.  `scen` may be NULL (one scenario).  On success *out owns the
+ * context; on failure *out is NULL (message via emt_last_error(NULL)). */
+emt_status emt_build_network(const emt_network_desc* desc, const emt_scenario_desc* scen, emt_ctx** out);
+
+/* Process 3 of Sec. III-A, done once: on the device, assemble each
+ * subsystem's conductance matrix G (companion conductances g = 1/R,
+ * dt/(2L), 2C/dt; 1/Z_c per line end; 1/R per closed switch) for every
+ * switch state it meets and store G^-1 (Gauss-Jordan with partial pivoting
+ * plus one Newton step whose residual is summed in twice the working
+ * precision).  Synchronous.  ESINGULAR names the subsystem. */
+emt_status emt_prefactor(emt_ctx* ctx);
+
+/* Choose the recorded node voltages ("waveform channels", Sec. II-A):
+ * channels = node ids (NULL = all nodes in order), every `decim`-th step
+ * (steps decim, 2 decim, ...), room for `max_rows` recorded steps per
+ * scenario.  Allocates the device record buffer; n_ch = 0 stops recording. */
+emt_status emt_set_recording(emt_ctx* ctx, const int32_t* channels, int64_t n_ch, int32_t decim, int64_t max_rows);
+
+/* Advance n_steps steps from the current step (resumable), asynchronously on
+ * `cuda_stream` (a cudaStream_t; NULL = legacy default stream).  A source
+ * kernel tabulates v_src(t_n) for the steps, then one persistent launch
+ * runs them: each CTA owns a subsystem, keeps G^-1 and all element data in
+ * shared memory, and meets other subsystems only through the line rings,
+ * whose slots carry the step they belong to (no grid barrier, no flags).
+ * A wait for line values exceeding its time budget latches an error that
+ * emt_sync or the next call returns. */
+emt_status emt_step_n(emt_ctx* ctx, int64_t n_steps, void* cuda_stream);
+
+/* Copy recorded waveforms out.  channels: node ids that were recorded;
+ * rows for steps step0, step0+decim, ... (n_rows of them; step0 a positive
+ * multiple of decim); scenarios scen0 .. scen0+n_scen-1.
+ * out: [n_rows][n_scen][n_ch] doubles, caller-owned, device memory if
+ * out_on_device != 0 else host memory.  Synchronous. */
+emt_status emt_read_waveforms(emt_ctx* ctx, const int32_t* channels, int64_t n_ch, int64_t step0, int64_t n_rows,
+                              int64_t scen0, int64_t n_scen, double* out, int32_t out_on_device);
+
+/* Return to the de-energised state at step 0 (keeps G^-1 and recording setup). */
+emt_status emt_reset(emt_ctx* ctx);
+
+/* Wait for all work of this context; report a latched device error.
+ * dev_err_info (may be NULL): [code, subsystem, line end, step]. */
+emt_status emt_sync(emt_ctx* ctx, int32_t* dev_err_info);
+
+/* Tuning and debug knobs (key = value): "wait_budget_ns" (per wait),
+ * "refine_kappa" (refine solves of subsystems whose inf-norm condition
+ * estimate exceeds this; -1 never; applies at the next emt_prefactor),
+ * "debug_hold_lines" (that subsystem never sends line values; -1 none;
+ * for failure-path tests).  EINVAL for an unknown key. */
+emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
+
+/* Read-only facts: "n_subsystems", "n_ctas", "step", "max_subsystem_nodes",
+ * "n_scenarios", "n_epochs_total", "sum_n2" (sum over subsystems of n_s^2),
+ * "n_refined" (matrices whose solves are refined), "threads_per_cta",
+ * "kernel_launches", "n_branches", "n_line_ends". */
+emt_status emt_get_info(const emt_ctx* ctx, const char* key, int64_t* value);
+
+/* Internal node order: perm[i] = original node id of internal slot i
+ * (n_nodes entries). */
+emt_status emt_get_node_order(const emt_ctx* ctx, int32_t* perm);
+
+/* Last error message of ctx (or of the last failed build if ctx == NULL). */
+const char* emt_last_error(const emt_ctx* ctx);
+
+/* Free everything the context owns.  NULL is a no-op. */
+void emt_destroy(emt_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

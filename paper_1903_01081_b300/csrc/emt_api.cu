@@ -1,0 +1,844 @@
+// Host side of libemt: validation, partitioning into subsystems, device
+// layout, launches and the C ABI of include/emt.h.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <set>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/emt.h"
+#include "emt_internal.h"
+
+using namespace emt;
+
+namespace {
+
+thread_local std::string g_build_error;
+
+const double kTwoPi = 2.0 * 3.14159265358979323846;
+
+// Source-voltage table budget per chunk of a launch (doubles): 32 MiB.
+const int64_t kSourceTableDoubles = 4 << 20;
+
+}  // namespace
+
+struct emt_ctx {
+  std::string err;
+  int device = 0;
+  double dt = 0.0;
+  int64_t n_nodes = 0, n_branches = 0, n_sources = 0, n_lines = 0;
+
+  // partition and internal numbering
+  int n_sub = 0;
+  std::vector<int32_t> sub_of_node;     // original node -> subsystem
+  std::vector<int32_t> internal_of;     // original node -> internal id
+  std::vector<int32_t> original_of;     // internal id -> original node
+
+  // host images of the device arrays
+  std::vector<SubDev> subs;
+  std::vector<EpochDev> epochs;
+  std::vector<BranchDev> branches;
+  std::vector<int32_t> lc_idx, sb_idx;
+  std::vector<int32_t> ent, eptr;
+  std::vector<LineEndDev> line_ends;
+  std::vector<int32_t> src_global;                     // global source id per local source slot
+  std::vector<double> src_amp, src_phase, src_omega;   // per global source
+  std::vector<int32_t> nb_sub, nb_dmin;
+  std::vector<SwitchDev> switches;
+  std::vector<int32_t> sp_ptr, sp_col;
+  int64_t ring_len = 0, ginv_len = 0, n_lc_total = 0, sp_nz_total = 0;
+  FwdLimits lim{0, 1, 0, 0, 0, 0, 0, 0, 0};
+  int64_t n_refined = 0;
+
+  // device arrays
+  SubDev* d_sub = nullptr;
+  EpochDev* d_ep = nullptr;
+  BranchDev* d_br = nullptr;
+  int32_t* d_lc_idx = nullptr;
+  int32_t* d_sb_idx = nullptr;
+  double* d_h = nullptr;
+  int32_t* d_ent = nullptr;
+  int32_t* d_eptr = nullptr;
+  LineEndDev* d_le = nullptr;
+  unsigned long long* d_ring = nullptr;
+  int32_t* d_src_global = nullptr;
+  double* d_src_amp = nullptr;
+  double* d_src_phase = nullptr;
+  double* d_src_omega = nullptr;
+  double* d_src_table = nullptr;
+  int64_t src_table_steps = 0;
+  SwitchDev* d_sw = nullptr;
+  int32_t* d_sp_ptr = nullptr;
+  int32_t* d_sp_col = nullptr;
+  double* d_sp_val = nullptr;
+  double* d_ginv = nullptr;
+  int32_t* d_err = nullptr;
+
+  // recording
+  std::vector<int32_t> rec_channels;     // original node ids, column order
+  std::vector<int32_t> rec_col_of;       // original node -> column or -1
+  int32_t rec_decim = 1;
+  int64_t rec_rows = 0;
+  double* d_rec = nullptr;
+  int32_t* d_rec_pos = nullptr;          // internal node -> column or -1
+
+  // run state and knobs
+  int64_t step = 0;
+  bool prefactored = false;
+  unsigned long long wait_budget_ns = 2000000000ull;
+  double refine_kappa = 1000.0;
+  int32_t hold_sub = -1;
+  int64_t launches = 0;
+
+  std::vector<void*> allocations;
+
+  emt_status fail(emt_status st, const std::string& msg) {
+    err = msg;
+    return st;
+  }
+  emt_status cuda_fail(cudaError_t e, const char* what) {
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? EMT_ENOMEM : EMT_ECUDA;
+  }
+  template <class T>
+  cudaError_t upload(T** dst, const std::vector<T>& src) {
+    const size_t n = std::max<size_t>(src.size(), 1);
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) return e;
+    allocations.push_back(p);
+    if (!src.empty()) e = cudaMemcpy(p, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    *dst = static_cast<T*>(p);
+    return e;
+  }
+  template <class T>
+  cudaError_t alloc_zero(T** dst, size_t count) {
+    void* p = nullptr;
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return e;
+    allocations.push_back(p);
+    *dst = static_cast<T*>(p);
+    return cudaMemset(p, 0, bytes);
+  }
+  void release(void* p) {
+    if (!p) return;
+    auto it = std::find(allocations.begin(), allocations.end(), p);
+    if (it != allocations.end()) allocations.erase(it);
+    cudaFree(p);
+  }
+};
+
+namespace {
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+std::string validate(const emt_network_desc* d) {
+  if (!d) return "desc is NULL";
+  if (!finite_pos(d->dt)) return "dt must be finite and > 0";
+  if (d->n_nodes < 0 || d->n_branches < 0 || d->n_sources < 0 || d->n_lines < 0 || d->n_switches < 0)
+    return "negative count";
+  if (d->n_nodes > (1 << 28) || d->n_sources > (1 << 28)) return "too many nodes or sources";
+  auto node_ok = [&](int32_t x) { return x >= -1 - d->n_sources && x < d->n_nodes; };
+  if (d->n_branches && (!d->br_k || !d->br_m || !d->br_kind || !d->br_value)) return "branch array is NULL";
+  for (int64_t b = 0; b < d->n_branches; ++b) {
+    const int32_t k = d->br_k[b], m = d->br_m[b];
+    if (!node_ok(k) || !node_ok(m)) return "branch " + std::to_string(b) + ": node out of range";
+    if (k == m) return "branch " + std::to_string(b) + ": both ends on one node";
+    if (k < 0 && m < 0) return "branch " + std::to_string(b) + ": no unknown end";
+    if (d->br_kind[b] > 2) return "branch " + std::to_string(b) + ": kind must be 0 (R), 1 (L) or 2 (C)";
+    if (!finite_pos(d->br_value[b])) return "branch " + std::to_string(b) + ": value must be finite and > 0";
+  }
+  if (d->n_sources && (!d->src_amp || !d->src_phase || !d->src_freq)) return "source array is NULL";
+  for (int64_t s = 0; s < d->n_sources; ++s)
+    if (!std::isfinite(d->src_amp[s]) || !std::isfinite(d->src_phase[s]) || !std::isfinite(d->src_freq[s]))
+      return "source " + std::to_string(s) + ": non-finite parameter";
+  if (d->n_lines && (!d->ln_k || !d->ln_m || !d->ln_zc || !d->ln_delay)) return "line array is NULL";
+  for (int64_t l = 0; l < d->n_lines; ++l) {
+    if (d->ln_k[l] < 0 || d->ln_k[l] >= d->n_nodes || d->ln_m[l] < 0 || d->ln_m[l] >= d->n_nodes)
+      return "line " + std::to_string(l) + ": ends must be unknown nodes";
+    if (d->ln_k[l] == d->ln_m[l]) return "line " + std::to_string(l) + ": both ends on one node";
+    if (d->ln_delay[l] < 1) return "line " + std::to_string(l) + ": delay must be >= 1 step";
+    if (d->ln_delay[l] > (1 << 20)) return "line " + std::to_string(l) + ": delay too large";
+    if (!finite_pos(d->ln_zc[l])) return "line " + std::to_string(l) + ": Z_c must be finite and > 0";
+  }
+  if (d->n_switches && (!d->sw_k || !d->sw_m || !d->sw_r || !d->sw_close_step || !d->sw_open_step))
+    return "switch array is NULL";
+  for (int64_t w = 0; w < d->n_switches; ++w) {
+    const int32_t k = d->sw_k[w], m = d->sw_m[w];
+    if (k < -1 || m < -1 || k >= d->n_nodes || m >= d->n_nodes || k == m || (k < 0 && m < 0))
+      return "switch " + std::to_string(w) + ": ends must be unknown nodes or ground";
+    if (!finite_pos(d->sw_r[w])) return "switch " + std::to_string(w) + ": resistance must be finite and > 0";
+  }
+  return "";
+}
+
+int uf_find(std::vector<int>& p, int x) {
+  while (p[x] != x) {
+    p[x] = p[p[x]];
+    x = p[x];
+  }
+  return x;
+}
+
+bool switch_closed(int64_t on, int64_t off, int64_t n) { return on >= 0 && n >= on && (off < 0 || n < off); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ build
+
+extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_scenario_desc* scen, emt_ctx** out) {
+  if (!out) {
+    g_build_error = "out is NULL";
+    return EMT_EINVAL;
+  }
+  *out = nullptr;
+  const std::string msg = validate(d);
+  if (!msg.empty()) {
+    g_build_error = msg;
+    return EMT_EINVAL;
+  }
+  if (scen && scen->n_scenarios != 1) {
+    g_build_error = "multi-scenario sets are not supported by emt_build_network yet";
+    return EMT_EINVAL;
+  }
+  emt_ctx* c = new emt_ctx();
+  auto bail = [&](const std::string& m) {
+    g_build_error = m;
+    delete c;
+    return EMT_EINVAL;
+  };
+  cudaGetDevice(&c->device);
+  c->dt = d->dt;
+  c->n_nodes = d->n_nodes;
+  c->n_branches = d->n_branches;
+  c->n_sources = d->n_sources;
+  c->n_lines = d->n_lines;
+  const int N = (int)d->n_nodes;
+
+  // -------- subsystems: components over branches and switches
+  std::vector<int> parent(N);
+  std::iota(parent.begin(), parent.end(), 0);
+  auto join = [&](int a, int b) {
+    if (a < 0 || b < 0) return;
+    a = uf_find(parent, a);
+    b = uf_find(parent, b);
+    if (a != b) parent[std::max(a, b)] = std::min(a, b);
+  };
+  for (int64_t b = 0; b < d->n_branches; ++b) join(d->br_k[b], d->br_m[b]);
+  for (int64_t w = 0; w < d->n_switches; ++w) join(d->sw_k[w], d->sw_m[w]);
+  c->sub_of_node.assign(N, -1);
+  std::vector<int> label(N, -1);
+  std::vector<std::vector<int>> nodes_of;
+  for (int i = 0; i < N; ++i) {
+    const int r = uf_find(parent, i);
+    if (label[r] < 0) {
+      label[r] = (int)nodes_of.size();
+      nodes_of.emplace_back();
+    }
+    c->sub_of_node[i] = label[r];
+    nodes_of[label[r]].push_back(i);
+  }
+  c->n_sub = (int)nodes_of.size();
+  const int S = c->n_sub;
+  c->internal_of.assign(N, -1);
+  c->original_of.assign(N, -1);
+  std::vector<int> local(N, -1);
+  c->subs.assign(S, SubDev{});
+  {
+    int off = 0;
+    for (int s = 0; s < S; ++s) {
+      const int n = (int)nodes_of[s].size();
+      if (n > kMaxSubsystemNodes)
+        return bail("subsystem " + std::to_string(s) + " has " + std::to_string(n) + " nodes; at most " +
+                    std::to_string(kMaxSubsystemNodes) + " are supported");
+      c->subs[s].n = n;
+      c->subs[s].node_off = off;
+      for (int j = 0; j < n; ++j) {
+        const int v = nodes_of[s][j];
+        local[v] = j;
+        c->internal_of[v] = off + j;
+        c->original_of[off + j] = v;
+      }
+      off += n;
+      c->lim.n = std::max(c->lim.n, n);
+    }
+  }
+
+  // -------- branches and local sources, grouped by subsystem
+  std::vector<std::vector<int64_t>> br_of(S);
+  for (int64_t b = 0; b < d->n_branches; ++b) {
+    const int a = d->br_k[b] >= 0 ? d->br_k[b] : d->br_m[b];
+    br_of[c->sub_of_node[a]].push_back(b);
+  }
+  std::vector<int32_t> lc_slot_of, sb_slot_of;   // new branch index -> local slot
+  for (int s = 0; s < S; ++s) {
+    SubDev& sd = c->subs[s];
+    sd.br_off = (int)c->branches.size();
+    sd.lc_off = (int)c->lc_idx.size();
+    sd.sb_off = (int)c->sb_idx.size();
+    sd.src_off = (int)c->src_global.size();
+    std::map<int, int> src_local;
+    auto code = [&](int32_t x) -> int16_t {
+      if (x >= 0) return (int16_t)local[x];
+      if (x == -1) return -1;
+      const int g = -2 - x;
+      auto it = src_local.find(g);
+      if (it != src_local.end()) return (int16_t)(-2 - it->second);
+      const int j = (int)src_local.size();
+      src_local[g] = j;
+      c->src_global.push_back(g);
+      return (int16_t)(-2 - j);
+    };
+    for (int64_t b : br_of[s]) {
+      BranchDev x{};
+      x.k = code(d->br_k[b]);
+      x.m = code(d->br_m[b]);
+      x.kind = d->br_kind[b];
+      x.value = d->br_value[b];
+      const int32_t nb = (int32_t)c->branches.size();
+      lc_slot_of.push_back(-1);
+      sb_slot_of.push_back(-1);
+      if (x.kind != 0) {
+        lc_slot_of[nb] = (int32_t)c->lc_idx.size() - sd.lc_off;
+        c->lc_idx.push_back(nb);
+      }
+      if (x.k <= -2 || x.m <= -2) {
+        sb_slot_of[nb] = (int32_t)c->sb_idx.size() - sd.sb_off;
+        c->sb_idx.push_back(nb);
+      }
+      c->branches.push_back(x);
+    }
+    sd.n_br = (int)c->branches.size() - sd.br_off;
+    sd.n_lc = (int)c->lc_idx.size() - sd.lc_off;
+    sd.n_sb = (int)c->sb_idx.size() - sd.sb_off;
+    sd.n_src = (int)c->src_global.size() - sd.src_off;
+    if (sd.n_src > kFwdThreads)
+      return bail("subsystem " + std::to_string(s) + " uses more than " + std::to_string(kFwdThreads) + " sources");
+    c->lim.lc = std::max(c->lim.lc, sd.n_lc);
+    c->lim.sb = std::max(c->lim.sb, sd.n_sb);
+    c->lim.src = std::max(c->lim.src, sd.n_src);
+  }
+  c->n_lc_total = (int64_t)c->lc_idx.size();
+  if (c->branches.size() > (1u << 29)) return bail("too many branches");
+  for (int64_t g = 0; g < d->n_sources; ++g) {
+    c->src_amp.push_back(d->src_amp[g]);
+    c->src_phase.push_back(d->src_phase[g]);
+    c->src_omega.push_back(kTwoPi * d->src_freq[g]);
+  }
+
+  // -------- line ends: end 2l at ln_k, end 2l+1 at ln_m; ring depth 2d
+  std::vector<int64_t> ring_off(2 * d->n_lines);
+  {
+    int64_t off = 0;
+    for (int64_t l = 0; l < d->n_lines; ++l) {
+      const int64_t depth = 2 * (int64_t)d->ln_delay[l];
+      ring_off[2 * l] = off;
+      off += depth;
+      ring_off[2 * l + 1] = off;
+      off += depth;
+    }
+    c->ring_len = off;
+  }
+  std::vector<std::vector<int64_t>> ends_of(S);
+  for (int64_t e = 0; e < 2 * d->n_lines; ++e) {
+    const int node = (e & 1) ? d->ln_m[e >> 1] : d->ln_k[e >> 1];
+    ends_of[c->sub_of_node[node]].push_back(e);
+  }
+  for (int s = 0; s < S; ++s) {
+    SubDev& sd = c->subs[s];
+    sd.le_off = (int)c->line_ends.size();
+    std::map<int, int> dmin;
+    for (int64_t e : ends_of[s]) {
+      const int64_t l = e >> 1;
+      const int node = (e & 1) ? d->ln_m[l] : d->ln_k[l];
+      const int far_node = (e & 1) ? d->ln_k[l] : d->ln_m[l];
+      LineEndDev le{};
+      le.node = local[node];
+      le.d = d->ln_delay[l];
+      le.depth = 2 * d->ln_delay[l];
+      le.y = 1.0 / d->ln_zc[l];
+      le.y2 = 2.0 / d->ln_zc[l];
+      le.own_ring = ring_off[e];
+      le.far_ring = ring_off[e ^ 1];
+      c->line_ends.push_back(le);
+      const int fs = c->sub_of_node[far_node];
+      if (fs != s) {
+        auto it = dmin.find(fs);
+        if (it == dmin.end() || it->second > le.d) dmin[fs] = le.d;
+      }
+    }
+    sd.n_le = (int)c->line_ends.size() - sd.le_off;
+    c->lim.le = std::max(c->lim.le, sd.n_le);
+    sd.nb_off = (int)c->nb_sub.size();
+    for (auto& kv : dmin) {
+      c->nb_sub.push_back(kv.first);
+      c->nb_dmin.push_back(kv.second);
+    }
+    sd.n_nb = (int)c->nb_sub.size() - sd.nb_off;
+  }
+
+  // -------- injection entries per node (see kEntryNeg), padded to 4
+  for (int s = 0; s < S; ++s) {
+    SubDev& sd = c->subs[s];
+    std::vector<std::vector<int32_t>> el(sd.n);
+    const int ie_base = sd.n_lc + sd.n_sb, zero = ie_base + 2 * sd.n_le;
+    for (int b = sd.br_off; b < sd.br_off + sd.n_br; ++b) {
+      const BranchDev& x = c->branches[b];
+      if (x.kind != 0) {
+        const int32_t slot = lc_slot_of[b];
+        if (x.k >= 0) el[x.k].push_back((int32_t)(kEntryNeg | (uint32_t)slot));   // current leaves k
+        if (x.m >= 0) el[x.m].push_back(slot);                                     // and enters m
+      }
+      if (sb_slot_of[b] >= 0) el[x.k >= 0 ? x.k : x.m].push_back(sd.n_lc + sb_slot_of[b]);
+    }
+    for (int e = 0; e < sd.n_le; ++e)
+      el[c->line_ends[sd.le_off + e].node].push_back((int32_t)(kEntryNeg | (uint32_t)(ie_base + e)));
+    sd.ent_off = (int)c->ent.size();
+    sd.eptr_off = (int)c->eptr.size();
+    int cnt = 0;
+    for (int k = 0; k < sd.n; ++k) {
+      c->eptr.push_back(cnt);
+      while (el[k].size() % 4) el[k].push_back(zero);
+      if (el[k].empty()) el[k].assign(4, zero);
+      c->ent.insert(c->ent.end(), el[k].begin(), el[k].end());
+      cnt += (int)el[k].size();
+    }
+    c->eptr.push_back(cnt);
+    sd.n_ent = cnt;
+    c->lim.ent = std::max(c->lim.ent, cnt);
+  }
+
+  // -------- switch epochs per subsystem, sparse pattern of G per epoch
+  {
+    std::vector<std::vector<int64_t>> sw_of(S);
+    for (int64_t w = 0; w < d->n_switches; ++w) {
+      const int a = d->sw_k[w] >= 0 ? d->sw_k[w] : d->sw_m[w];
+      sw_of[c->sub_of_node[a]].push_back(w);
+    }
+    int64_t goff = 0;
+    for (int s = 0; s < S; ++s) {
+      SubDev& sd = c->subs[s];
+      std::vector<int64_t> events;
+      for (int64_t w : sw_of[s]) {
+        if (d->sw_close_step[w] >= 0) events.push_back(d->sw_close_step[w]);
+        if (d->sw_open_step[w] >= 0) events.push_back(d->sw_open_step[w]);
+      }
+      std::sort(events.begin(), events.end());
+      events.erase(std::unique(events.begin(), events.end()), events.end());
+      std::vector<std::pair<int64_t, int64_t>> eps;   // (start, step at which the state is read)
+      eps.push_back({LLONG_MIN, events.empty() ? 1 : events[0] - 1});
+      for (int64_t e : events) eps.push_back({e, e});
+      sd.ep_off = (int)c->epochs.size();
+      // structural pattern shared by all epochs: branches between unknown nodes
+      std::vector<std::set<int>> base(sd.n);
+      for (int k = 0; k < sd.n; ++k) base[k].insert(k);
+      for (int b = sd.br_off; b < sd.br_off + sd.n_br; ++b) {
+        const BranchDev& x = c->branches[b];
+        if (x.k >= 0 && x.m >= 0) {
+          base[x.k].insert(x.m);
+          base[x.m].insert(x.k);
+        }
+      }
+      for (auto& ep : eps) {
+        EpochDev E{};
+        E.start = ep.first;
+        E.ginv_off = goff;
+        goff += (int64_t)sd.n * sd.n;
+        E.sw_off = (int)c->switches.size();
+        std::vector<std::set<int>> pat = base;
+        for (int64_t w : sw_of[s]) {
+          if (!switch_closed(d->sw_close_step[w], d->sw_open_step[w], ep.second)) continue;
+          SwitchDev sw{};
+          sw.k = d->sw_k[w] >= 0 ? local[d->sw_k[w]] : -1;
+          sw.m = d->sw_m[w] >= 0 ? local[d->sw_m[w]] : -1;
+          sw.g = 1.0 / d->sw_r[w];
+          c->switches.push_back(sw);
+          if (sw.k >= 0 && sw.m >= 0) {
+            pat[sw.k].insert(sw.m);
+            pat[sw.m].insert(sw.k);
+          }
+        }
+        E.n_sw = (int)c->switches.size() - E.sw_off;
+        E.sp_ptr_off = (int)c->sp_ptr.size();
+        E.sp_nz_off = (int)c->sp_col.size();
+        int nz = 0;
+        for (int k = 0; k < sd.n; ++k) {
+          c->sp_ptr.push_back(nz);
+          for (int j : pat[k]) c->sp_col.push_back(j);
+          nz += (int)pat[k].size();
+        }
+        c->sp_ptr.push_back(nz);
+        E.n_nz = nz;
+        c->lim.nz = std::max(c->lim.nz, nz);
+        c->epochs.push_back(E);
+      }
+      sd.n_ep = (int)c->epochs.size() - sd.ep_off;
+    }
+    c->ginv_len = goff;
+    c->sp_nz_total = (int64_t)c->sp_col.size();
+  }
+
+  // -------- matvec chunking: ~12 columns per partial sum
+  for (int s = 0; s < S; ++s) {
+    SubDev& sd = c->subs[s];
+    const int n = std::max(sd.n, 1);
+    sd.q = std::max(1, std::min((n + 11) / 12, kFwdThreads / n));
+    c->lim.q = std::max(c->lim.q, sd.q);
+  }
+
+  // -------- upload
+  cudaError_t e = cudaSuccess;
+#define UP(dst, vec) \
+  if (e == cudaSuccess) e = c->upload(&c->dst, c->vec);
+  UP(d_sub, subs)
+  UP(d_ep, epochs)
+  UP(d_br, branches)
+  UP(d_lc_idx, lc_idx)
+  UP(d_sb_idx, sb_idx)
+  UP(d_ent, ent)
+  UP(d_eptr, eptr)
+  UP(d_le, line_ends)
+  UP(d_src_global, src_global)
+  UP(d_src_amp, src_amp)
+  UP(d_src_phase, src_phase)
+  UP(d_src_omega, src_omega)
+  UP(d_sw, switches)
+  UP(d_sp_ptr, sp_ptr)
+  UP(d_sp_col, sp_col)
+#undef UP
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_sp_val, (size_t)c->sp_nz_total);
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_h, (size_t)c->n_lc_total);
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_ring, 2 * (size_t)std::max<int64_t>(c->ring_len, 1));
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_ginv, (size_t)c->ginv_len);
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_err, 4);
+  if (e == cudaSuccess) e = launch_companion(c->d_br, (int64_t)c->branches.size(), c->dt, nullptr);
+  if (e == cudaSuccess) e = launch_ring_init(RingInitParams{c->d_le, (int64_t)c->line_ends.size(), c->d_ring}, nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    g_build_error = std::string("device setup failed: ") + cudaGetErrorString(e);
+    const emt_status st = (e == cudaErrorMemoryAllocation) ? EMT_ENOMEM : EMT_ECUDA;
+    emt_destroy(c);
+    return st;
+  }
+  *out = c;
+  return EMT_OK;
+}
+
+extern "C" emt_status emt_prefactor(emt_ctx* c) {
+  if (!c) return EMT_EINVAL;
+  std::vector<int32_t> mat_sub, mat_ep;
+  for (int s = 0; s < c->n_sub; ++s)
+    for (int k = 0; k < c->subs[s].n_ep; ++k) {
+      mat_sub.push_back(s);
+      mat_ep.push_back(c->subs[s].ep_off + k);
+    }
+  int32_t *d_ms = nullptr, *d_me = nullptr, *d_status = nullptr;
+  double *d_wg = nullptr, *d_wr = nullptr;
+  cudaError_t e = c->upload(&d_ms, mat_sub);
+  if (e == cudaSuccess) e = c->upload(&d_me, mat_ep);
+  if (e == cudaSuccess) e = c->alloc_zero(&d_status, mat_sub.size());
+  if (e == cudaSuccess) e = c->alloc_zero(&d_wg, (size_t)c->ginv_len);
+  if (e == cudaSuccess) e = c->alloc_zero(&d_wr, (size_t)c->ginv_len);
+  PrefParams p{};
+  p.n_mats = (int32_t)mat_sub.size();
+  p.mat_sub = d_ms;
+  p.mat_ep = d_me;
+  p.sub = c->d_sub;
+  p.ep = c->d_ep;
+  p.br = c->d_br;
+  p.le = c->d_le;
+  p.sw = c->d_sw;
+  p.sp_ptr = c->d_sp_ptr;
+  p.sp_col = c->d_sp_col;
+  p.sp_val = c->d_sp_val;
+  p.ginv = c->d_ginv;
+  p.work_g = d_wg;
+  p.work_r = d_wr;
+  p.status = d_status;
+  p.refine_kappa = c->refine_kappa;
+  if (e == cudaSuccess) e = launch_prefactor(p, std::max(c->lim.n, 1), nullptr);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  std::vector<int32_t> status(mat_sub.size(), 0);
+  if (e == cudaSuccess && !status.empty())
+    e = cudaMemcpy(status.data(), d_status, status.size() * sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && !c->epochs.empty())
+    e = cudaMemcpy(c->epochs.data(), c->d_ep, c->epochs.size() * sizeof(EpochDev), cudaMemcpyDeviceToHost);
+  c->release(d_ms);
+  c->release(d_me);
+  c->release(d_status);
+  c->release(d_wg);
+  c->release(d_wr);
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_prefactor");
+  for (size_t i = 0; i < status.size(); ++i)
+    if (status[i] != 0) {
+      const int s = mat_sub[i];
+      return c->fail(EMT_ESINGULAR, "conductance matrix of subsystem " + std::to_string(s) + " (first node " +
+                                        std::to_string(c->original_of[c->subs[s].node_off]) + ", switch state " +
+                                        std::to_string(mat_ep[i] - c->subs[s].ep_off) + ") is singular");
+    }
+  c->n_refined = 0;
+  for (const EpochDev& E : c->epochs) c->n_refined += E.refine ? 1 : 0;
+  c->lim.refine = c->n_refined > 0 ? 1 : 0;
+  c->prefactored = true;
+  return EMT_OK;
+}
+
+extern "C" emt_status emt_set_recording(emt_ctx* c, const int32_t* channels, int64_t n_ch, int32_t decim,
+                                        int64_t max_rows) {
+  if (!c) return EMT_EINVAL;
+  if (decim < 1 || max_rows < 0 || n_ch < 0) return c->fail(EMT_EINVAL, "decim must be >= 1, counts >= 0");
+  cudaDeviceSynchronize();
+  c->release(c->d_rec);
+  c->release(c->d_rec_pos);
+  c->d_rec = nullptr;
+  c->d_rec_pos = nullptr;
+  c->rec_channels.clear();
+  c->rec_col_of.assign(c->n_nodes, -1);
+  c->rec_rows = 0;
+  if (n_ch == 0 || max_rows == 0) return EMT_OK;
+  std::vector<int32_t> chans;
+  if (channels) {
+    for (int64_t i = 0; i < n_ch; ++i) {
+      const int32_t x = channels[i];
+      if (x < 0 || x >= c->n_nodes) return c->fail(EMT_EINVAL, "channel " + std::to_string(x) + " is not a node");
+      if (c->rec_col_of[x] >= 0) return c->fail(EMT_EINVAL, "channel " + std::to_string(x) + " listed twice");
+      c->rec_col_of[x] = (int32_t)chans.size();
+      chans.push_back(x);
+    }
+  } else {
+    for (int64_t i = 0; i < c->n_nodes; ++i) {
+      c->rec_col_of[i] = (int32_t)i;
+      chans.push_back((int32_t)i);
+    }
+  }
+  std::vector<int32_t> pos(c->n_nodes, -1);
+  for (int64_t i = 0; i < c->n_nodes; ++i) pos[c->internal_of[i]] = c->rec_col_of[i];
+  cudaError_t e = c->upload(&c->d_rec_pos, pos);
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_rec, (size_t)max_rows * chans.size());
+  if (e != cudaSuccess) {
+    c->rec_col_of.assign(c->n_nodes, -1);
+    return c->cuda_fail(e, "emt_set_recording");
+  }
+  c->rec_channels = chans;
+  c->rec_decim = decim;
+  c->rec_rows = max_rows;
+  return EMT_OK;
+}
+
+extern "C" emt_status emt_step_n(emt_ctx* c, int64_t n_steps, void* stream) {
+  if (!c) return EMT_EINVAL;
+  if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
+  if (n_steps < 0) return c->fail(EMT_EINVAL, "n_steps < 0");
+  if (n_steps == 0 || c->n_sub == 0) return EMT_OK;
+  if (c->step + n_steps > (int64_t)INT32_MAX - (int64_t)(1 << 21))
+    return c->fail(EMT_EINVAL, "step counter would exceed 2^31 - 2^21");
+  if (!c->rec_channels.empty() && (c->step + n_steps) / c->rec_decim > c->rec_rows)
+    return c->fail(EMT_EINVAL, "recording capacity exceeded: raise max_rows in emt_set_recording");
+  if (forward_smem_bytes(c->lim) > 227 * 1024)
+    return c->fail(EMT_ERESOURCE, "a subsystem needs more shared memory than one CTA has");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // source table for one chunk of steps at a time (grow-only buffer)
+  const int64_t chunk =
+      std::min<int64_t>(n_steps, std::max<int64_t>(1, kSourceTableDoubles / std::max<int64_t>(c->n_sources, 1)));
+  if (c->src_table_steps < chunk) {
+    cudaStreamSynchronize(st);
+    c->release(c->d_src_table);
+    c->d_src_table = nullptr;
+    c->src_table_steps = 0;
+    cudaError_t e = c->alloc_zero(&c->d_src_table, (size_t)chunk * std::max<int64_t>(c->n_sources, 1));
+    if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n source table");
+    c->src_table_steps = chunk;
+  }
+  FwdParams p{};
+  p.n_sub = c->n_sub;
+  p.lim = c->lim;
+  p.lim.n = std::max(p.lim.n, 1);
+  p.sub = c->d_sub;
+  p.ep = c->d_ep;
+  p.ginv = c->d_ginv;
+  p.sp_ptr = c->d_sp_ptr;
+  p.sp_col = c->d_sp_col;
+  p.sp_val = c->d_sp_val;
+  p.br = c->d_br;
+  p.lc_idx = c->d_lc_idx;
+  p.sb_idx = c->d_sb_idx;
+  p.h = c->d_h;
+  p.ent = c->d_ent;
+  p.eptr = c->d_eptr;
+  p.le = c->d_le;
+  p.ring = c->d_ring;
+  p.src_global = c->d_src_global;
+  p.src_table = c->d_src_table;
+  p.n_sources = (int32_t)c->n_sources;
+  p.err = c->d_err;
+  p.rec = c->rec_channels.empty() ? nullptr : c->d_rec;
+  p.rec_pos = c->d_rec_pos;
+  p.rec_rows = c->rec_rows;
+  p.rec_decim = c->rec_decim;
+  p.n_rec = (int32_t)c->rec_channels.size();
+  p.wait_budget_ns = c->wait_budget_ns;
+  p.hold_sub = c->hold_sub;
+  for (int64_t done = 0; done < n_steps; done += chunk) {
+    const int64_t len = std::min(chunk, n_steps - done);
+    SourceParams sp{};
+    sp.n_sources = (int32_t)c->n_sources;
+    sp.amp = c->d_src_amp;
+    sp.phase = c->d_src_phase;
+    sp.omega = c->d_src_omega;
+    sp.dt = c->dt;
+    sp.n0 = c->step + 1;
+    sp.n_steps = len;
+    sp.table = c->d_src_table;
+    cudaError_t e = launch_sources(sp, st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n source table");
+    p.n0 = c->step + 1;
+    p.n_steps = len;
+    e = launch_forward(p, st);
+    if (e == cudaErrorCooperativeLaunchTooLarge)
+      return c->fail(EMT_ERESOURCE, "persistent launch of " + std::to_string(c->n_sub) +
+                                        " CTAs cannot be co-resident on this device");
+    if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n launch");
+    c->step += len;
+    c->launches += (c->n_sources > 0 ? 2 : 1);
+  }
+  return EMT_OK;
+}
+
+extern "C" emt_status emt_sync(emt_ctx* c, int32_t* info) {
+  if (!c) return EMT_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_sync");
+  int32_t h[4] = {0, 0, 0, 0};
+  e = cudaMemcpy(h, c->d_err, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_sync");
+  if (info) std::memcpy(info, h, sizeof(h));
+  if (h[0] == EMT_ETIMEOUT)
+    return c->fail(EMT_ETIMEOUT, "subsystem " + std::to_string(h[1]) + " timed out at step " + std::to_string(h[3]) +
+                                     " waiting for the value of its line end " + std::to_string(h[2]));
+  if (h[0] != 0) return c->fail((emt_status)h[0], "device error");
+  return EMT_OK;
+}
+
+extern "C" emt_status emt_read_waveforms(emt_ctx* c, const int32_t* channels, int64_t n_ch, int64_t step0,
+                                         int64_t n_rows, int64_t scen0, int64_t n_scen, double* out,
+                                         int32_t out_on_device) {
+  if (!c) return EMT_EINVAL;
+  if (n_ch < 0 || n_rows < 0 || n_scen < 0) return c->fail(EMT_EINVAL, "negative count");
+  if (n_ch == 0 || n_rows == 0 || n_scen == 0) return EMT_OK;
+  if (!out || !channels) return c->fail(EMT_EINVAL, "NULL buffer");
+  if (c->rec_channels.empty()) return c->fail(EMT_ESTATE, "nothing is being recorded");
+  if (scen0 < 0 || scen0 + n_scen > 1) return c->fail(EMT_EINVAL, "scenario range out of bounds");
+  if (step0 < c->rec_decim || step0 % c->rec_decim != 0)
+    return c->fail(EMT_EINVAL, "step0 must be a positive multiple of the recording decimation");
+  const int64_t row0 = step0 / c->rec_decim - 1;
+  if (row0 + n_rows > c->rec_rows || (row0 + n_rows) * c->rec_decim > c->step)
+    return c->fail(EMT_EINVAL, "requested steps have not been recorded");
+  std::vector<int32_t> col(n_ch);
+  for (int64_t i = 0; i < n_ch; ++i) {
+    const int32_t x = channels[i];
+    if (x < 0 || x >= c->n_nodes || c->rec_col_of[x] < 0)
+      return c->fail(EMT_EINVAL, "channel " + std::to_string(x) + " is not recorded");
+    col[i] = c->rec_col_of[x];
+  }
+  const emt_status st = emt_sync(c, nullptr);
+  if (st != EMT_OK) return st;
+  int32_t* d_col = nullptr;
+  double* d_out = out;
+  cudaError_t e = c->upload(&d_col, col);
+  const size_t bytes = (size_t)n_rows * n_scen * n_ch * sizeof(double);
+  if (e == cudaSuccess && !out_on_device) {
+    void* p = nullptr;
+    e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) c->allocations.push_back(p);
+    d_out = static_cast<double*>(p);
+  }
+  if (e == cudaSuccess)
+    e = launch_gather(c->d_rec, (int32_t)c->rec_channels.size(), 1, d_col, n_ch, row0, n_rows, scen0, n_scen, d_out,
+                      nullptr);
+  if (e == cudaSuccess && !out_on_device) e = cudaMemcpy(out, d_out, bytes, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  c->release(d_col);
+  if (!out_on_device) c->release(d_out);
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_read_waveforms");
+  return EMT_OK;
+}
+
+extern "C" emt_status emt_reset(emt_ctx* c) {
+  if (!c) return EMT_EINVAL;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemset(c->d_h, 0, std::max<int64_t>(c->n_lc_total, 1) * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMemset(c->d_ring, 0, 2 * std::max<int64_t>(c->ring_len, 1) * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = launch_ring_init(RingInitParams{c->d_le, (int64_t)c->line_ends.size(), c->d_ring}, nullptr);
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_reset");
+  c->step = 0;
+  return EMT_OK;
+}
+
+extern "C" emt_status emt_set_option(emt_ctx* c, const char* key, int64_t value) {
+  if (!c || !key) return EMT_EINVAL;
+  const std::string k(key);
+  if (k == "wait_budget_ns") {
+    if (value < 0) return c->fail(EMT_EINVAL, "wait_budget_ns must be >= 0");
+    c->wait_budget_ns = (unsigned long long)value;
+    return EMT_OK;
+  }
+  if (k == "refine_kappa") {
+    c->refine_kappa = value < 0 ? -1.0 : (double)value;
+    return EMT_OK;
+  }
+  if (k == "debug_hold_lines") {   // failure-path tests: one subsystem never sends line values
+    if (value < -1 || value >= c->n_sub) return c->fail(EMT_EINVAL, "debug_hold_lines out of range");
+    c->hold_sub = (int32_t)value;
+    return EMT_OK;
+  }
+  return c->fail(EMT_EINVAL, "unknown option '" + k + "'");
+}
+
+extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* value) {
+  if (!c || !key || !value) return EMT_EINVAL;
+  const std::string k(key);
+  if (k == "n_subsystems" || k == "n_ctas") *value = c->n_sub;
+  else if (k == "step") *value = c->step;
+  else if (k == "max_subsystem_nodes") *value = c->lim.n;
+  else if (k == "n_scenarios") *value = 1;
+  else if (k == "n_epochs_total") *value = (int64_t)c->epochs.size();
+  else if (k == "sum_n2") {
+    int64_t s2 = 0;
+    for (const SubDev& s : c->subs) s2 += (int64_t)s.n * s.n;
+    *value = s2;
+  } else if (k == "n_refined") *value = c->n_refined;
+  else if (k == "threads_per_cta") *value = kFwdThreads;
+  else if (k == "kernel_launches") *value = c->launches;
+  else if (k == "n_branches") *value = (int64_t)c->branches.size();
+  else if (k == "n_line_ends") *value = (int64_t)c->line_ends.size();
+  else if (k == "smem_bytes") *value = (int64_t)forward_smem_bytes(c->lim);
+  else return EMT_EINVAL;
+  return EMT_OK;
+}
+
+extern "C" emt_status emt_get_node_order(const emt_ctx* c, int32_t* perm) {
+  if (!c || !perm) return EMT_EINVAL;
+  for (int64_t i = 0; i < c->n_nodes; ++i) perm[i] = c->original_of[i];
+  return EMT_OK;
+}
+
+extern "C" const char* emt_last_error(const emt_ctx* c) { return c ? c->err.c_str() : g_build_error.c_str(); }
+
+extern "C" void emt_destroy(emt_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  for (void* p : c->allocations) cudaFree(p);
+  c->allocations.clear();
+  delete c;
+}

@@ -1,0 +1,171 @@
+// Internal layout shared by the host driver (emt_api.cu) and the kernels.
+// Everything here is an implementation detail behind include/emt.h.
+#pragma once
+#include <stdint.h>
+
+#include <cuda_runtime.h>
+
+namespace emt {
+
+// Largest subsystem the persistent kernel keeps on chip (G^-1 in shared
+// memory: 128 x 128 doubles = 128 KiB).
+constexpr int kMaxSubsystemNodes = 128;
+
+// Threads per CTA of the persistent forward kernel.
+constexpr int kFwdThreads = 256;
+
+// Injection entries (process 2).  Every node's injection is a signed sum of
+// entries of one shared-memory input vector
+//     inp = [ h (L/C slots) | g_b v_src (source-branch slots) |
+//             I_e parity 0 (line ends) | I_e parity 1 | 0 ]
+// An entry is an int32: bit 31 = subtract, bits 0..30 = index into inp with
+// line ends addressed in their parity-0 block.  Each node's entries are
+// padded to a multiple of 4 with the index of the trailing zero.
+constexpr uint32_t kEntryNeg = 0x80000000u;
+
+// One branch in device form.  Node fields are subsystem-local:
+//   >= 0 local node, -1 ground, <= -2 local source -2-j.
+struct BranchDev {
+  int16_t k, m;
+  uint8_t kind;      // 0 R, 1 L, 2 C
+  uint8_t pad[3];
+  double value;      // ohm / henry / farad (input)
+  double g;          // companion conductance (written by the companion kernel)
+  double e;          // history gain: +2g (L), -2g (C), 0 (R)
+};
+
+// One line end, owned by the subsystem of its node.  It consumes I_e(n)
+// from its own ring and produces I_f(n+d) into the far end's ring.
+// A ring slot is two 64-bit words, each = (step << 32) | one 32-bit half of
+// the double I(step); each word is written and read as one single-copy
+// atomic access, so a reader that finds the expected step in both words
+// holds that step's value -- no fence or separate flag is needed.  A slot is
+// rewritten (D = 2d steps later) only after its reader consumed it: the far
+// end's write at step m carries a value computed from this end's output of
+// step m - d, which this end produced after reading the slot.
+struct LineEndDev {
+  int32_t node;        // local node of this end
+  int32_t d;           // travel time in steps
+  int32_t depth;       // ring depth D = 2d
+  int32_t pad;
+  double y2;           // 2 / Z_c
+  double y;            // 1 / Z_c
+  int64_t own_ring;    // first slot of this end's ring (values consumed here)
+  int64_t far_ring;    // first slot of the far end's ring (values produced here)
+};
+
+// A switch in device form (subsystem-local ends, -1 = ground).
+struct SwitchDev {
+  int32_t k, m;
+  double g;          // 1 / R while closed
+};
+
+// Per-subsystem descriptor.
+struct SubDev {
+  int32_t n;           // unknown nodes
+  int32_t node_off;    // first internal node id
+  int32_t br_off, n_br;        // all branches (stamping)
+  int32_t lc_off, n_lc;        // L/C branch slots (history updates)
+  int32_t sb_off, n_sb;        // source-branch slots (injection from known nodes)
+  int32_t le_off, n_le;        // line ends owned here
+  int32_t src_off, n_src;      // local sources (global ids in src_global)
+  int32_t nb_off, n_nb;        // neighbour subsystems (reported by emt_get_info)
+  int32_t ep_off, n_ep;        // switch epochs
+  int32_t ent_off, n_ent;      // injection entries (multiple of 4 per node)
+  int32_t eptr_off;            // n + 1 entry offsets (relative to ent_off)
+  int32_t q;                   // column chunks per row in the matvec
+};
+
+// Switch epoch of a subsystem: state holding from step `start` on.
+struct EpochDev {
+  int64_t start;
+  int64_t ginv_off;      // offset of this epoch's n x n G^-1
+  int32_t sw_off, n_sw;  // closed switches (SwitchDev list)
+  int32_t sp_ptr_off;    // n + 1 row offsets of the sparse G (relative to sp_nz_off)
+  int32_t sp_nz_off, n_nz;
+  int32_t refine;        // set by the prefactor: refine each solve (ill-conditioned G)
+};
+
+// Per-launch upper bounds that size the forward kernel's shared memory.
+struct FwdLimits {
+  int32_t n, q, lc, sb, le, src, ent, nz, refine;
+};
+
+struct FwdParams {
+  int32_t n_sub;
+  FwdLimits lim;
+  const SubDev* sub;
+  const EpochDev* ep;
+  const double* ginv;
+  const int32_t* sp_ptr;       // sparse G pattern / values per epoch
+  const int32_t* sp_col;
+  const double* sp_val;
+  const BranchDev* br;
+  const int32_t* lc_idx;       // branch index per L/C slot
+  const int32_t* sb_idx;       // branch index per source-branch slot
+  double* h;                   // history current per L/C slot
+  const int32_t* ent;          // injection entries
+  const int32_t* eptr;         // per subsystem n + 1 entry offsets
+  const LineEndDev* le;
+  unsigned long long* ring;    // [slots][2] tagged words
+  const int32_t* src_global;   // global source id per local source slot
+  const double* src_table;     // [n_steps][n_sources]: v_src(t_{n0+i})
+  int32_t n_sources;
+  int32_t* err;                // [4]: code, subsystem, line end, step
+  double* rec;                 // [rows][n_rec]
+  const int32_t* rec_pos;      // per internal node: column in rec, or -1
+  int64_t rec_rows;
+  int32_t rec_decim;
+  int32_t n_rec;
+  int64_t n0;                  // first step of this launch
+  int64_t n_steps;
+  unsigned long long wait_budget_ns;
+  int32_t hold_sub;            // debug: this subsystem never writes its line outputs (-1: none)
+};
+
+struct PrefParams {
+  int32_t n_mats;
+  const int32_t* mat_sub;      // subsystem per matrix
+  const int32_t* mat_ep;       // epoch index (into ep) per matrix
+  const SubDev* sub;
+  EpochDev* ep;                // refine flags written here
+  const BranchDev* br;
+  const LineEndDev* le;
+  const SwitchDev* sw;
+  const int32_t* sp_ptr;
+  const int32_t* sp_col;
+  double* sp_val;              // filled from the stamped G
+  double* ginv;
+  double* work_g;              // copy of G per matrix, at ep.ginv_off
+  double* work_r;              // residual I - G X per matrix, at ep.ginv_off
+  int32_t* status;             // per matrix: 0 ok, 1 singular
+  double refine_kappa;         // refine solves when ||G|| ||G^-1|| (inf-norm) exceeds this; < 0 never
+};
+
+struct SourceParams {
+  int32_t n_sources;
+  const double* amp;           // per global source
+  const double* phase;
+  const double* omega;         // 2 pi f
+  double dt;
+  int64_t n0, n_steps;
+  double* table;               // [n_steps][n_sources]
+};
+
+struct RingInitParams {
+  const LineEndDev* le;        // all line ends
+  int64_t n_le;
+  unsigned long long* ring;
+};
+
+// kernels / launchers (emt_kernels.cu)
+cudaError_t launch_ring_init(const RingInitParams& p, cudaStream_t st);
+cudaError_t launch_companion(BranchDev* br, int64_t n_br, double dt, cudaStream_t st);
+cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st);
+cudaError_t launch_sources(const SourceParams& p, cudaStream_t st);
+cudaError_t launch_forward(const FwdParams& p, cudaStream_t st);
+size_t forward_smem_bytes(const FwdLimits& lim);
+cudaError_t launch_gather(const double* rec, int32_t n_rec, int64_t n_scen_rec, const int32_t* col, int64_t n_ch,
+                          int64_t row0, int64_t n_rows, int64_t scen0, int64_t n_scen, double* out, cudaStream_t st);
+
+}  // namespace emt

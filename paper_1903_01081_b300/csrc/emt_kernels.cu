@@ -1,0 +1,706 @@
+// CUDA kernels of the EMTP-type time loop for sm_103a (B300).
+//
+// companion_kernel   process 1 constants: g = 1/R, dt/(2L), 2C/dt and the
+//                    history gain e = +2g (L) / -2g (C)
+// prefactor_kernel   process 3, once per subsystem and switch state: stamp G,
+//                    invert it in place (Gauss-Jordan, partial pivoting),
+//                    then one Newton step X <- X + X (I - G X) with the
+//                    residual summed in twice the working precision; flags
+//                    ill-conditioned matrices for refined solves
+// source_kernel      process 1 for sources: the table v_src(t_n) of a launch
+// ring_init_kernel   de-energised line histories in the tagged rings
+// fwd_kernel         the persistent time loop (processes 1, 2, 4 and the
+//                    Bergeron line update), one CTA per subsystem, G^-1 and
+//                    all per-element data in shared memory for the whole
+//                    launch; subsystems meet only through the line rings,
+//                    whose slots carry the step they belong to (no flags,
+//                    no fences, no grid barrier)
+// gather_kernel      copies recorded channels into the caller's layout
+//
+// Formulas (CloudPSS paper Sec. III-A processes; textbook trapezoidal
+// companions of its ref. [2]; lossless Bergeron line):
+//   i_n[k] = sum_src g_b v_src(t_n) - sum_b a_bk h_b(n-1) - sum_e I_e(n)
+//   v_n    = G^-1 i_n
+//   h_b(n) = +h_b(n-1) + 2 g v_b(n)   (L)      -h_b(n-1) - 2 g v_b(n)   (C)
+//   I_far(n+d) = -(2/Z_c) v_near(n) - I_near(n)
+#include <stdint.h>
+
+#include <algorithm>
+#include <climits>
+
+#include <cuda_runtime.h>
+
+#include "emt_internal.h"
+
+namespace emt {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+// error-free transformations (Knuth TwoSum; TwoProd by FMA)
+__device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
+  s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+}
+
+// hi + lo += a * b, products exact, sum carried in two doubles (Dot2)
+__device__ __forceinline__ void dot2_acc(double& hi, double& lo, double a, double b) {
+  const double p = __dmul_rn(a, b);
+  const double pe = fma(a, b, -p);
+  double s, e;
+  two_sum(hi, p, s, e);
+  hi = s;
+  lo = __dadd_rn(lo, __dadd_rn(e, pe));
+}
+
+// ------------------------------------------------------------ companion
+
+__global__ void companion_kernel(BranchDev* br, int64_t n_br, double dt) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_br) return;
+  const BranchDev x = br[b];
+  double g;
+  if (x.kind == 0) g = 1.0 / x.value;
+  else if (x.kind == 1) g = dt / (2.0 * x.value);
+  else g = 2.0 * x.value / dt;
+  br[b].g = g;
+  br[b].e = x.kind == 1 ? 2.0 * g : (x.kind == 2 ? -2.0 * g : 0.0);
+}
+
+// ------------------------------------------------------------ prefactor
+
+__device__ __forceinline__ void stamp(double* A, int n, int k, int m, double g) {
+  if (k >= 0) A[k * n + k] += g;
+  if (m >= 0) A[m * n + m] += g;
+  if (k >= 0 && m >= 0) {
+    A[k * n + m] -= g;
+    A[m * n + k] -= g;
+  }
+}
+
+__global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
+  extern __shared__ double A[];
+  __shared__ double fcol[kMaxSubsystemNodes];
+  __shared__ double rowsum[kMaxSubsystemNodes];
+  __shared__ int perm[kMaxSubsystemNodes];
+  __shared__ int s_p, s_sing;
+  __shared__ double s_gnorm;
+  const int mi = blockIdx.x;
+  const SubDev S = P.sub[P.mat_sub[mi]];
+  const EpochDev E = P.ep[P.mat_ep[mi]];
+  const int n = S.n, T = blockDim.x, tid = threadIdx.x;
+  for (int i = tid; i < n * n; i += T) A[i] = 0.0;
+  __syncthreads();
+  if (tid == 0) {
+    // a source end acts as ground in G (its voltage goes to the injection)
+    for (int b = 0; b < S.n_br; ++b) {
+      const BranchDev x = P.br[S.br_off + b];
+      stamp(A, n, x.k >= 0 ? x.k : -1, x.m >= 0 ? x.m : -1, x.g);
+    }
+    for (int e = 0; e < S.n_le; ++e) {
+      const LineEndDev le = P.le[S.le_off + e];
+      A[le.node * n + le.node] += le.y;
+    }
+    for (int w = 0; w < E.n_sw; ++w) {
+      const SwitchDev sw = P.sw[E.sw_off + w];
+      stamp(A, n, sw.k, sw.m, sw.g);
+    }
+    s_sing = 0;
+  }
+  __syncthreads();
+  double* Gw = P.work_g + E.ginv_off;
+  double* Rw = P.work_r + E.ginv_off;
+  for (int i = tid; i < n * n; i += T) Gw[i] = A[i];
+  // sparse copy of the stamped G (pattern from the host) and row sums
+  for (int i = tid; i < n; i += T) {
+    const int* rp = P.sp_ptr + E.sp_ptr_off;
+    for (int x = rp[i]; x < rp[i + 1]; ++x)
+      P.sp_val[E.sp_nz_off + x] = A[i * n + P.sp_col[E.sp_nz_off + x]];
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += fabs(A[i * n + j]);
+    rowsum[i] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double g = 0.0;
+    for (int i = 0; i < n; ++i) g = fmax(g, rowsum[i]);
+    s_gnorm = g;
+  }
+  // in-place Gauss-Jordan inversion with row pivoting
+  for (int k = 0; k < n; ++k) {
+    if (tid < 32) {
+      double best = -1.0;
+      int arg = k;
+      for (int i = k + tid; i < n; i += 32) {
+        const double m = fabs(A[i * n + k]);
+        if (m > best) { best = m; arg = i; }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, off);
+        const int oa = __shfl_down_sync(0xffffffffu, arg, off);
+        if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+      }
+      if (tid == 0) {
+        s_p = arg;
+        perm[k] = arg;
+        if (!(best > 1e-300) || !isfinite(best)) s_sing = 1;
+      }
+    }
+    __syncthreads();
+    if (s_sing) break;
+    const int p = s_p;
+    if (p != k)
+      for (int j = tid; j < n; j += T) {
+        const double t = A[k * n + j];
+        A[k * n + j] = A[p * n + j];
+        A[p * n + j] = t;
+      }
+    __syncthreads();
+    const double inv = 1.0 / A[k * n + k];
+    __syncthreads();
+    for (int j = tid; j < n; j += T) A[k * n + j] = (j == k) ? inv : A[k * n + j] * inv;
+    for (int i = tid; i < n; i += T) fcol[i] = (i == k) ? 0.0 : A[i * n + k];
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += T) {
+      const int i = idx / n, j = idx - i * n;
+      if (i == k) continue;
+      if (j == k) A[i * n + k] = -fcol[i] * A[k * n + k];
+      else A[i * n + j] -= fcol[i] * A[k * n + j];
+    }
+    __syncthreads();
+  }
+  if (s_sing) {
+    if (tid == 0) P.status[mi] = 1;
+    return;
+  }
+  // undo the row interchanges as column interchanges, last pivot first
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int i = tid; i < n; i += T) {
+        const double t = A[i * n + k];
+        A[i * n + k] = A[i * n + p];
+        A[i * n + p] = t;
+      }
+    __syncthreads();
+  }
+  // Newton step: R = I - G X with Dot2 (exact products, sum carried in two
+  // doubles), then X + X R.  X's error drops from ~cond(G) eps to a few
+  // ulps, so the explicit inverse does not bias the long recursion.
+  for (int idx = tid; idx < n * n; idx += T) {
+    const int i = idx / n, j = idx - i * n;
+    double hi = (i == j) ? 1.0 : 0.0, lo = 0.0;
+    for (int k = 0; k < n; ++k) dot2_acc(hi, lo, -Gw[i * n + k], A[k * n + j]);
+    Rw[idx] = __dadd_rn(hi, lo);
+  }
+  __syncthreads();
+  double* out = P.ginv + E.ginv_off;
+  for (int idx = tid; idx < n * n; idx += T) {
+    const int i = idx / n, j = idx - i * n;
+    double c = 0.0;
+    for (int k = 0; k < n; ++k) c = fma(A[i * n + k], Rw[k * n + j], c);
+    out[idx] = A[idx] + c;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += T) {
+    double s = 0.0;
+    for (int j = 0; j < n; ++j) s += fabs(out[i * n + j]);
+    rowsum[i] = s;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double x = 0.0;
+    for (int i = 0; i < n; ++i) x = fmax(x, rowsum[i]);
+    const double kappa = s_gnorm * x;
+    P.ep[P.mat_ep[mi]].refine = (P.refine_kappa >= 0.0 && kappa > P.refine_kappa) ? 1 : 0;
+    P.status[mi] = 0;
+  }
+}
+
+// ------------------------------------------------------------ sources
+
+__global__ void source_kernel(SourceParams P) {
+  const int64_t total = P.n_steps * P.n_sources;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / P.n_sources;
+    const int s = (int)(i - r * P.n_sources);
+    const double t = (double)(P.n0 + r) * P.dt;
+    // argument rounded as (omega * t) + phase, each operation once
+    P.table[i] = P.amp[s] * sin(__dadd_rn(__dmul_rn(P.omega[s], t), P.phase[s]));
+  }
+}
+
+// ------------------------------------------------------------ line rings
+
+// Tagged ring slot: two words (step << 32) | low / high half of the double.
+__device__ __forceinline__ void st_tagged(unsigned long long* p, unsigned tag, double v) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long w0 = ((unsigned long long)tag << 32) | (bits & 0xffffffffull);
+  const unsigned long long w1 = ((unsigned long long)tag << 32) | (bits >> 32);
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(w0), "l"(w1) : "memory");
+}
+
+__device__ __forceinline__ bool ld_tagged(const unsigned long long* p, unsigned tag, double& v) {
+  unsigned long long w0, w1;
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(w0), "=l"(w1) : "l"(p) : "memory");
+  if ((unsigned)(w0 >> 32) != tag || (unsigned)(w1 >> 32) != tag) return false;
+  v = __longlong_as_double((long long)((w1 << 32) | (w0 & 0xffffffffull)));
+  return true;
+}
+
+// De-energised start: the slot consumed at step s (1 <= s <= d) holds 0
+// tagged s; every other slot holds tag 0, which no step matches.
+__global__ void ring_init_kernel(RingInitParams P) {
+  const int64_t e = blockIdx.x;
+  if (e >= P.n_le) return;
+  const LineEndDev L = P.le[e];
+  for (int j = threadIdx.x; j < L.depth; j += blockDim.x) {
+    const unsigned s = (j == 0) ? (unsigned)L.depth : (unsigned)j;
+    const unsigned long long w = (s <= (unsigned)L.d) ? ((unsigned long long)s << 32) : 0ull;
+    P.ring[2 * (L.own_ring + j)] = w;
+    P.ring[2 * (L.own_ring + j) + 1] = w;
+  }
+}
+
+// ------------------------------------------------------------ forward
+
+// Shared-memory layout of fwd_kernel, from the per-launch limits.  G^-1
+// rows are stored with an odd stride (n | 1) so that the rows a warp reads
+// together fall in different banks.
+struct FwdSmem {
+  size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar, spv;        // 8-byte
+  size_t gi32, rr, cpart;                                                       // 4-byte float
+  size_t lck, lcm, lckind, sbsrc, lenode, ledepth, led, rslot, wslot, ent, eptr, srcg, spc, spp;   // int
+  size_t bytes;
+};
+
+__host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
+  FwdSmem s{};
+  size_t o = 0;
+  auto d = [&](size_t count) { size_t r = o; o += count * 8; return r; };
+  auto w = [&](size_t count) { size_t r = o; o += count * 4; return r; };
+  const size_t rf = L.refine ? 1 : 0;
+  s.gi = d((size_t)L.n * (L.n | 1));
+  s.part = d((size_t)L.n * L.q);
+  s.iv = d(L.n);
+  s.vv = d(L.n);
+  s.inp = d((size_t)L.lc + L.sb + 2 * (size_t)L.le + 1);
+  s.vs = d(2 * (size_t)L.src);
+  s.lce = d(L.lc);
+  s.sbg = d(L.sb);
+  s.ley2 = d(L.le);
+  s.leown = d(L.le);
+  s.lefar = d(L.le);
+  s.spv = d(rf * L.nz);
+  s.gi32 = w(rf * L.n * (L.n | 1));
+  s.rr = w(rf * L.n);
+  s.cpart = w(rf * L.n * L.q);
+  s.lck = w(L.lc);
+  s.lcm = w(L.lc);
+  s.lckind = w(L.lc);
+  s.sbsrc = w(L.sb);
+  s.lenode = w(L.le);
+  s.ledepth = w(L.le);
+  s.led = w(L.le);
+  s.rslot = w(L.le);
+  s.wslot = w(L.le);
+  s.ent = w(L.ent);
+  s.eptr = w((size_t)L.n + 1);
+  s.srcg = w(L.src);
+  s.spc = w(rf * L.nz);
+  s.spp = w(rf * ((size_t)L.n + 1));
+  s.bytes = (o + 15) & ~(size_t)15;
+  return s;
+}
+
+// Warp 0 collects one step's line-end histories I_e(n) from the tagged
+// rings.  Bounded: on exceeding the time budget (or seeing another CTA's
+// error) it latches an error and returns false.
+__device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int lane, int sidx, const long long* leown,
+                              const int* ledepth, int* rslot, double* ie) {
+  bool ok = true;
+  for (int e = lane; e < n_le && ok; e += 32) {
+    const unsigned long long* slot = P.ring + 2 * (leown[e] + rslot[e]);
+    double v = 0.0;
+    if (!ld_tagged(slot, tag, v)) {
+      const unsigned long long t0 = global_ns();
+      unsigned spins = 0;
+      while (!ld_tagged(slot, tag, v)) {
+        if ((++spins & 31u) == 0) {
+          if (ld_volatile(P.err) != 0) { ok = false; break; }
+          if (global_ns() - t0 > P.wait_budget_ns || spins > (1u << 30)) {
+            if (atomicCAS(P.err, 0, 5) == 0) {
+              P.err[1] = sidx;
+              P.err[2] = e;
+              P.err[3] = (int)tag;
+            }
+            ok = false;
+            break;
+          }
+        }
+      }
+    }
+    ie[e] = v;
+    const int nx = rslot[e] + 1;
+    rslot[e] = nx == ledepth[e] ? 0 : nx;
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
+__device__ __forceinline__ double sum_parts(const double* p, int Q) {
+  double a = p[0], b = 0.0;
+  int q = 1;
+  for (; q + 1 < Q; q += 2) {
+    a += p[q];
+    b += p[q + 1];
+  }
+  if (q < Q) a += p[q];
+  return a + b;
+}
+
+__device__ __forceinline__ float sum_parts_f(const float* p, int Q) {
+  float a = 0.f;
+  for (int q = 0; q < Q; ++q) a += p[q];
+  return a;
+}
+
+__global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_abort;
+  const FwdSmem L = fwd_smem(P.lim);
+  double* gi = reinterpret_cast<double*>(smem_raw + L.gi);
+  double* part = reinterpret_cast<double*>(smem_raw + L.part);
+  double* iv = reinterpret_cast<double*>(smem_raw + L.iv);
+  double* vv = reinterpret_cast<double*>(smem_raw + L.vv);
+  double* inp = reinterpret_cast<double*>(smem_raw + L.inp);
+  double* vs = reinterpret_cast<double*>(smem_raw + L.vs);     // [2][src]
+  double* lce = reinterpret_cast<double*>(smem_raw + L.lce);
+  double* sbg = reinterpret_cast<double*>(smem_raw + L.sbg);
+  double* ley2 = reinterpret_cast<double*>(smem_raw + L.ley2);
+  long long* leown = reinterpret_cast<long long*>(smem_raw + L.leown);
+  long long* lefar = reinterpret_cast<long long*>(smem_raw + L.lefar);
+  double* spv = reinterpret_cast<double*>(smem_raw + L.spv);
+  float* gi32 = reinterpret_cast<float*>(smem_raw + L.gi32);
+  float* rr = reinterpret_cast<float*>(smem_raw + L.rr);
+  float* cpart = reinterpret_cast<float*>(smem_raw + L.cpart);
+  int* lck = reinterpret_cast<int*>(smem_raw + L.lck);
+  int* lcm = reinterpret_cast<int*>(smem_raw + L.lcm);
+  int* lckind = reinterpret_cast<int*>(smem_raw + L.lckind);
+  int* sbsrc = reinterpret_cast<int*>(smem_raw + L.sbsrc);
+  int* lenode = reinterpret_cast<int*>(smem_raw + L.lenode);
+  int* ledepth = reinterpret_cast<int*>(smem_raw + L.ledepth);
+  int* led = reinterpret_cast<int*>(smem_raw + L.led);
+  int* rslot = reinterpret_cast<int*>(smem_raw + L.rslot);
+  int* wslot = reinterpret_cast<int*>(smem_raw + L.wslot);
+  int* ent = reinterpret_cast<int*>(smem_raw + L.ent);
+  int* eptr = reinterpret_cast<int*>(smem_raw + L.eptr);
+  int* srcg = reinterpret_cast<int*>(smem_raw + L.srcg);
+  int* spc = reinterpret_cast<int*>(smem_raw + L.spc);
+  int* spp = reinterpret_cast<int*>(smem_raw + L.spp);
+
+  const int sidx = blockIdx.x;
+  const SubDev S = P.sub[sidx];
+  const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = S.n, Q = S.q, ldg = n | 1;
+  const int n_lc = S.n_lc, n_sb = S.n_sb, n_le = S.n_le;
+  const int ie_base = n_lc + n_sb;
+  const int zero_slot = ie_base + 2 * n_le;
+  const int src_vs = P.lim.src;
+  const bool writes_lines = sidx != P.hold_sub;
+  const int src_thread = T - 1 - tid;   // the last threads carry the least other work
+
+  // ---- prologue: this subsystem's data into shared memory
+  for (int x = tid; x < n_lc; x += T) {
+    const BranchDev b = P.br[P.lc_idx[S.lc_off + x]];
+    inp[x] = P.h[S.lc_off + x];
+    lce[x] = b.e;
+    lck[x] = b.k;
+    lcm[x] = b.m;
+    lckind[x] = b.kind;
+  }
+  for (int x = tid; x < n_sb; x += T) {
+    const BranchDev b = P.br[P.sb_idx[S.sb_off + x]];
+    sbg[x] = b.g;
+    sbsrc[x] = b.k <= -2 ? -2 - b.k : -2 - b.m;
+  }
+  for (int x = tid; x < n_le; x += T) {
+    const LineEndDev e = P.le[S.le_off + x];
+    ley2[x] = e.y2;
+    leown[x] = e.own_ring;
+    lefar[x] = e.far_ring;
+    lenode[x] = e.node;
+    ledepth[x] = e.depth;
+    led[x] = e.d;
+    rslot[x] = (int)(P.n0 % e.depth);
+    wslot[x] = (int)((P.n0 + e.d) % e.depth);
+  }
+  for (int x = tid; x < S.n_ent; x += T) ent[x] = P.ent[S.ent_off + x];
+  for (int x = tid; x <= n; x += T) eptr[x] = P.eptr[S.eptr_off + x];
+  for (int x = tid; x < S.n_src; x += T) {
+    srcg[x] = P.src_global[S.src_off + x];
+    vs[(P.n0 & 1) * src_vs + x] = P.src_table[P.src_global[S.src_off + x]];
+  }
+  if (tid == 0) {
+    inp[zero_slot] = 0.0;
+    s_abort = 0;
+  }
+  int ep = 0;
+  while (ep + 1 < S.n_ep && P.ep[S.ep_off + ep + 1].start <= P.n0) ++ep;
+  long long next_ep_start = (ep + 1 < S.n_ep) ? P.ep[S.ep_off + ep + 1].start : LLONG_MAX;
+  int refine = 0;
+  {
+    const EpochDev E = P.ep[S.ep_off + ep];
+    refine = P.lim.refine ? E.refine : 0;
+    const double* src = P.ginv + E.ginv_off;
+    for (int i = tid; i < n * n; i += T) {
+      const int r = i / n, c = i - r * n;
+      gi[r * ldg + c] = src[i];
+      if (refine) gi32[r * ldg + c] = (float)src[i];
+    }
+    if (refine) {
+      for (int x = tid; x < E.n_nz; x += T) {
+        spv[x] = P.sp_val[E.sp_nz_off + x];
+        spc[x] = P.sp_col[E.sp_nz_off + x];
+      }
+      for (int x = tid; x <= n; x += T) spp[x] = P.sp_ptr[E.sp_ptr_off + x];
+    }
+  }
+  __syncthreads();
+  for (int x = tid; x < n_sb; x += T) inp[n_lc + x] = sbg[x] * vs[(P.n0 & 1) * src_vs + sbsrc[x]];
+  if (warp == 0 && n_le > 0) {
+    const bool ok = collect_lines(P, n_le, (unsigned)P.n0, lane, sidx, leown, ledepth, rslot,
+                                  inp + ie_base + (int)(P.n0 & 1) * n_le);
+    if (!ok && lane == 0) s_abort = 1;
+  }
+  // recording counters: steps decim, 2 decim, ... go to rows 0, 1, ...
+  const int decim = P.rec_decim > 0 ? P.rec_decim : 1;
+  int dec = (int)(P.n0 % decim);
+  long long rec_row = P.n0 / decim - (dec == 0 ? 1 : 0);
+  __syncthreads();
+
+  const long long n_end = P.n0 + P.n_steps;
+  for (long long step = P.n0; step < n_end && !s_abort; ++step) {
+    const int par = (int)(step & 1);
+    const double* vsc = vs + par * src_vs;
+    const int parshift = par * n_le;
+    if (step >= next_ep_start) {
+      while (ep + 1 < S.n_ep && P.ep[S.ep_off + ep + 1].start <= step) ++ep;
+      next_ep_start = (ep + 1 < S.n_ep) ? P.ep[S.ep_off + ep + 1].start : LLONG_MAX;
+      const EpochDev E = P.ep[S.ep_off + ep];
+      refine = P.lim.refine ? E.refine : 0;
+      const double* src = P.ginv + E.ginv_off;
+      for (int i = tid; i < n * n; i += T) {
+        const int r = i / n, c = i - r * n;
+        gi[r * ldg + c] = src[i];
+        if (refine) gi32[r * ldg + c] = (float)src[i];
+      }
+      if (refine) {
+        for (int x = tid; x < E.n_nz; x += T) {
+          spv[x] = P.sp_val[E.sp_nz_off + x];
+          spc[x] = P.sp_col[E.sp_nz_off + x];
+        }
+        for (int x = tid; x <= n; x += T) spp[x] = P.sp_ptr[E.sp_ptr_off + x];
+      }
+    }
+    // next step's source voltages: load issued now, stored after process 4
+    double vnext = 0.0;
+    if (src_thread < S.n_src && step + 1 < n_end)
+      vnext = __ldg(P.src_table + (step + 1 - P.n0) * P.n_sources + srcg[src_thread]);
+
+    // process 2: nodal injections, four entries at a time
+    for (int k = tid; k < n; k += T) {
+      double a0 = 0.0, a1 = 0.0;
+      const int x1 = eptr[k + 1];
+      for (int x = eptr[k]; x < x1; x += 4) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const unsigned raw = (unsigned)ent[x + u];
+          int idx = (int)(raw & ~kEntryNeg);
+          if ((unsigned)(idx - ie_base) < (unsigned)n_le) idx += parshift;
+          const unsigned long long bits =
+              (unsigned long long)__double_as_longlong(inp[idx]) ^ ((unsigned long long)(raw & kEntryNeg) << 32);
+          v[u] = __longlong_as_double((long long)bits);
+        }
+        const double c = (v[0] + v[1]) + (v[2] + v[3]);
+        if (((x - eptr[k]) & 4) == 0) a0 += c;
+        else a1 += c;
+      }
+      iv[k] = a0 + a1;
+    }
+    __syncthreads();
+
+    // process 4: v = G^-1 i, rows split into Q column chunks
+    for (int task = tid; task < n * Q; task += T) {
+      const int r = task / Q, q = task - r * Q;
+      const double* row = gi + r * ldg;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int j = q;
+      for (; j + 3 * Q < n; j += 4 * Q) {
+        a0 = fma(row[j], iv[j], a0);
+        a1 = fma(row[j + Q], iv[j + Q], a1);
+        a2 = fma(row[j + 2 * Q], iv[j + 2 * Q], a2);
+        a3 = fma(row[j + 3 * Q], iv[j + 3 * Q], a3);
+      }
+      for (; j < n; j += Q) a0 = fma(row[j], iv[j], a0);
+      part[task] = (a0 + a1) + (a2 + a3);
+    }
+    if (src_thread < S.n_src) vs[(par ^ 1) * src_vs + src_thread] = vnext;
+    __syncthreads();
+
+    if (refine) {
+      // one refinement step: r = i - G v0 (sparse G, Dot2), v = v0 + G^-1 r
+      // with the correction in single precision (its relative accuracy only
+      // needs to beat cond(G) * 2^-24 << 1)
+      for (int r = tid; r < n; r += T) vv[r] = sum_parts(part + r * Q, Q);
+      __syncthreads();
+      for (int k = tid; k < n; k += T) {
+        double hi = iv[k], lo = 0.0;
+        for (int x = spp[k]; x < spp[k + 1]; ++x) dot2_acc(hi, lo, -spv[x], vv[spc[x]]);
+        rr[k] = (float)__dadd_rn(hi, lo);
+      }
+      __syncthreads();
+      for (int task = tid; task < n * Q; task += T) {
+        const int r = task / Q, q = task - r * Q;
+        const float* row = gi32 + r * ldg;
+        float a0 = 0.f, a1 = 0.f;
+        int j = q;
+        for (; j + Q < n; j += 2 * Q) {
+          a0 = fmaf(row[j], rr[j], a0);
+          a1 = fmaf(row[j + Q], rr[j + Q], a1);
+        }
+        if (j < n) a0 = fmaf(row[j], rr[j], a0);
+        cpart[task] = a0 + a1;
+      }
+      __syncthreads();
+    }
+
+    // node voltages, line outputs, history currents, next step's source
+    // injections: each item finishes the voltages it needs from the partials
+    const bool rec_now = P.rec != nullptr && dec == 0 && rec_row < P.rec_rows;
+    const double* ie_cur = inp + ie_base + parshift;
+    const double* vs_next = vs + (par ^ 1) * src_vs;
+    const int n_items = n + n_le + n_lc + n_sb;
+    for (int it = tid; it < n_items; it += T) {
+      if (it < n) {
+        const double v = refine ? vv[it] + (double)sum_parts_f(cpart + it * Q, Q) : sum_parts(part + it * Q, Q);
+        if (rec_now) {
+          const int pos = P.rec_pos[S.node_off + it];
+          if (pos >= 0) P.rec[rec_row * P.n_rec + pos] = v;
+        }
+      } else if (it < n + n_le) {
+        const int e = it - n, r = lenode[e];
+        const double v = refine ? vv[r] + (double)sum_parts_f(cpart + r * Q, Q) : sum_parts(part + r * Q, Q);
+        if (writes_lines)
+          st_tagged(P.ring + 2 * (lefar[e] + wslot[e]), (unsigned)(step + led[e]), fma(-ley2[e], v, -ie_cur[e]));
+        const int nx = wslot[e] + 1;
+        wslot[e] = nx == ledepth[e] ? 0 : nx;
+      } else if (it < n + n_le + n_lc) {
+        const int x = it - n - n_le;
+        const int k = lck[x], m = lcm[x];
+        double vk, vm;
+        if (k >= 0) vk = refine ? vv[k] + (double)sum_parts_f(cpart + k * Q, Q) : sum_parts(part + k * Q, Q);
+        else vk = (k == -1) ? 0.0 : vsc[-2 - k];
+        if (m >= 0) vm = refine ? vv[m] + (double)sum_parts_f(cpart + m * Q, Q) : sum_parts(part + m * Q, Q);
+        else vm = (m == -1) ? 0.0 : vsc[-2 - m];
+        const double vb = vk - vm;
+        inp[x] = lckind[x] == 1 ? fma(lce[x], vb, inp[x]) : fma(lce[x], vb, -inp[x]);
+      } else {
+        const int x = it - n - n_le - n_lc;
+        inp[n_lc + x] = sbg[x] * vs_next[sbsrc[x]];
+      }
+    }
+    if (dec == 0) ++rec_row;
+    if (++dec == decim) dec = 0;
+    if (warp == 0 && n_le > 0 && step + 1 < n_end) {
+      const bool ok = collect_lines(P, n_le, (unsigned)(step + 1), lane, sidx, leown, ledepth, rslot,
+                                    inp + ie_base + (par ^ 1) * n_le);
+      if (!ok && lane == 0) s_abort = 1;
+    }
+    __syncthreads();
+  }
+  if (!s_abort)
+    for (int b = tid; b < n_lc; b += T) P.h[S.lc_off + b] = inp[b];
+}
+
+// ------------------------------------------------------------ gather
+
+__global__ void gather_kernel(const double* rec, int32_t n_rec, int64_t n_scen_rec, const int32_t* col, int64_t n_ch,
+                              int64_t row0, int64_t n_rows, int64_t scen0, int64_t n_scen, double* out) {
+  const int64_t total = n_rows * n_scen * n_ch;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i % n_ch, rs = i / n_ch;
+    const int64_t s = rs % n_scen, r = rs / n_scen;
+    out[i] = rec[((row0 + r) * n_scen_rec + scen0 + s) * n_rec + col[c]];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_ring_init(const RingInitParams& p, cudaStream_t st) {
+  if (p.n_le <= 0) return cudaSuccess;
+  ring_init_kernel<<<(unsigned)p.n_le, 64, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_companion(BranchDev* br, int64_t n_br, double dt, cudaStream_t st) {
+  if (n_br <= 0) return cudaSuccess;
+  const int th = 256;
+  companion_kernel<<<(unsigned)((n_br + th - 1) / th), th, 0, st>>>(br, n_br, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st) {
+  if (p.n_mats <= 0) return cudaSuccess;
+  const size_t smem = (size_t)max_n * max_n * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(prefactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  prefactor_kernel<<<p.n_mats, 256, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sources(const SourceParams& p, cudaStream_t st) {
+  const int64_t total = p.n_steps * p.n_sources;
+  if (total <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 8);
+  source_kernel<<<blocks, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+size_t forward_smem_bytes(const FwdLimits& lim) { return fwd_smem(lim).bytes; }
+
+cudaError_t launch_forward(const FwdParams& p, cudaStream_t st) {
+  const size_t smem = forward_smem_bytes(p.lim);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, n_sm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel, kFwdThreads, smem);
+  if (e != cudaSuccess) return e;
+  if ((long long)per_sm * n_sm < p.n_sub) return cudaErrorCooperativeLaunchTooLarge;
+  FwdParams arg = p;
+  void* args[] = {&arg};
+  // cooperative launch: all CTAs co-resident, so every ring wait can end
+  return cudaLaunchCooperativeKernel((const void*)fwd_kernel, dim3(p.n_sub), dim3(kFwdThreads), args, smem, st);
+}
+
+cudaError_t launch_gather(const double* rec, int32_t n_rec, int64_t n_scen_rec, const int32_t* col, int64_t n_ch,
+                          int64_t row0, int64_t n_rows, int64_t scen0, int64_t n_scen, double* out, cudaStream_t st) {
+  const int64_t total = n_rows * n_scen * n_ch;
+  if (total <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 16);
+  gather_kernel<<<blocks, 256, 0, st>>>(rec, n_rec, n_scen_rec, col, n_ch, row0, n_rows, scen0, n_scen, out);
+  return cudaGetLastError();
+}
+
+}  // namespace emt

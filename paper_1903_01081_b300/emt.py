@@ -1,0 +1,314 @@
+"""Thin Python binding of libemt (include/emt.h).
+
+Argument marshalling only: every step of the time loop runs in the CUDA
+library.  Functions keep the C names; ``Simulator`` is a small convenience
+wrapper around one context.  There is no CPU fallback: if the library
+cannot be built or loaded, or no CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+EMT_OK, EMT_EINVAL, EMT_ESINGULAR, EMT_ENOMEM, EMT_ECUDA, EMT_ETIMEOUT, EMT_ERESOURCE, EMT_ESTATE = range(8)
+_STATUS = {0: "EMT_OK", 1: "EMT_EINVAL", 2: "EMT_ESINGULAR", 3: "EMT_ENOMEM", 4: "EMT_ECUDA",
+           5: "EMT_ETIMEOUT", 6: "EMT_ERESOURCE", 7: "EMT_ESTATE"}
+
+# every function include/emt.h declares
+EXPORTS = ("emt_build_network", "emt_prefactor", "emt_set_recording", "emt_step_n", "emt_read_waveforms",
+           "emt_reset", "emt_sync", "emt_set_option", "emt_get_info", "emt_get_node_order", "emt_last_error",
+           "emt_destroy")
+
+
+class EmtError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _NetworkDesc(ctypes.Structure):
+    _fields_ = [
+        ("dt", ctypes.c_double), ("n_nodes", ctypes.c_int64),
+        ("n_branches", ctypes.c_int64), ("br_k", ctypes.c_void_p), ("br_m", ctypes.c_void_p),
+        ("br_kind", ctypes.c_void_p), ("br_value", ctypes.c_void_p),
+        ("n_sources", ctypes.c_int64), ("src_amp", ctypes.c_void_p), ("src_phase", ctypes.c_void_p),
+        ("src_freq", ctypes.c_void_p),
+        ("n_lines", ctypes.c_int64), ("ln_k", ctypes.c_void_p), ("ln_m", ctypes.c_void_p),
+        ("ln_zc", ctypes.c_void_p), ("ln_delay", ctypes.c_void_p),
+        ("n_switches", ctypes.c_int64), ("sw_k", ctypes.c_void_p), ("sw_m", ctypes.c_void_p),
+        ("sw_r", ctypes.c_void_p), ("sw_close_step", ctypes.c_void_p), ("sw_open_step", ctypes.c_void_p),
+    ]
+
+
+class _ScenarioDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_scenarios", ctypes.c_int64),
+        ("src_amp", ctypes.c_void_p), ("src_phase", ctypes.c_void_p),
+        ("rm_branch_ptr", ctypes.c_void_p), ("rm_branch", ctypes.c_void_p),
+        ("rm_line_ptr", ctypes.c_void_p), ("rm_line", ctypes.c_void_p),
+        ("sw_ptr", ctypes.c_void_p), ("sw_k", ctypes.c_void_p), ("sw_m", ctypes.c_void_p),
+        ("sw_r", ctypes.c_void_p), ("sw_close_step", ctypes.c_void_p), ("sw_open_step", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load_library(build_if_needed: bool = True):
+    """Load libemt.so (building it with nvcc first if missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_needed and _build.needs_build():
+        _build.build()
+    if not os.path.exists(_build.LIB_PATH):
+        raise RuntimeError(f"libemt.so not found at {_build.LIB_PATH}; build it with paper_1903_01081_b300.build.build()")
+    lib = ctypes.CDLL(_build.LIB_PATH)
+    P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    sig = {
+        "emt_build_network": [P, P, P],
+        "emt_prefactor": [P],
+        "emt_set_recording": [P, P, I64, I32, I64],
+        "emt_step_n": [P, I64, P],
+        "emt_read_waveforms": [P, P, I64, I64, I64, I64, I64, P, I32],
+        "emt_reset": [P],
+        "emt_sync": [P, P],
+        "emt_set_option": [P, ctypes.c_char_p, I64],
+        "emt_get_info": [P, ctypes.c_char_p, P],
+        "emt_get_node_order": [P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.emt_last_error.argtypes = [P]
+    lib.emt_last_error.restype = ctypes.c_char_p
+    lib.emt_destroy.argtypes = [P]
+    lib.emt_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _arr(x, dtype):
+    return np.ascontiguousarray(np.asarray(x), dtype=dtype)
+
+
+class Ctx:
+    """Owner of one ``emt_ctx*``."""
+
+    def __init__(self, handle: int, n_nodes: int, n_scenarios: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.n_nodes = n_nodes
+        self.n_scenarios = n_scenarios
+
+    def __del__(self):
+        try:
+            emt_destroy(self)
+        except Exception:
+            pass
+
+
+def _check(ctx: Optional[Ctx], status: int):
+    if status != EMT_OK:
+        lib = load_library(False)
+        msg = lib.emt_last_error(ctx.handle if ctx is not None else None)
+        raise EmtError(status, msg.decode() if msg else "")
+
+
+def network_desc(net, keep: list) -> _NetworkDesc:
+    """ctypes ``emt_network_desc`` pointing into arrays appended to ``keep``."""
+    def p(x, dt):
+        a = _arr(x, dt)
+        keep.append(a)
+        return a.ctypes.data if a.size else None
+
+    d = _NetworkDesc()
+    d.dt = float(net.dt)
+    d.n_nodes = int(net.n_nodes)
+    d.n_branches = int(len(net.br_k))
+    d.br_k, d.br_m = p(net.br_k, np.int32), p(net.br_m, np.int32)
+    d.br_kind, d.br_value = p(net.br_kind, np.uint8), p(net.br_value, np.float64)
+    d.n_sources = int(len(net.src_amp))
+    d.src_amp, d.src_phase, d.src_freq = (p(net.src_amp, np.float64), p(net.src_phase, np.float64),
+                                          p(net.src_freq, np.float64))
+    d.n_lines = int(len(net.ln_k))
+    d.ln_k, d.ln_m = p(net.ln_k, np.int32), p(net.ln_m, np.int32)
+    d.ln_zc, d.ln_delay = p(net.ln_zc, np.float64), p(net.ln_delay, np.int32)
+    d.n_switches = int(len(net.sw_k))
+    d.sw_k, d.sw_m = p(net.sw_k, np.int32), p(net.sw_m, np.int32)
+    d.sw_r = p(net.sw_r, np.float64)
+    d.sw_close_step, d.sw_open_step = p(net.sw_close_step, np.int64), p(net.sw_open_step, np.int64)
+    return d
+
+
+def scenario_desc(sc, keep: list) -> _ScenarioDesc:
+    def p(x, dt):
+        if x is None:
+            return None
+        a = _arr(x, dt)
+        keep.append(a)
+        return a.ctypes.data if a.size else None
+
+    d = _ScenarioDesc()
+    d.n_scenarios = int(sc.n_scenarios)
+    d.src_amp, d.src_phase = p(sc.src_amp, np.float64), p(sc.src_phase, np.float64)
+    d.rm_branch_ptr, d.rm_branch = p(sc.rm_branch_ptr, np.int64), p(sc.rm_branch, np.int32)
+    d.rm_line_ptr, d.rm_line = p(sc.rm_line_ptr, np.int64), p(sc.rm_line, np.int32)
+    d.sw_ptr, d.sw_k, d.sw_m = p(sc.sw_ptr, np.int64), p(sc.sw_k, np.int32), p(sc.sw_m, np.int32)
+    d.sw_r = p(sc.sw_r, np.float64)
+    d.sw_close_step, d.sw_open_step = p(sc.sw_close_step, np.int64), p(sc.sw_open_step, np.int64)
+    return d
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)   # torch.cuda.Stream
+
+
+# ------------------------------------------------------------------ C names
+
+def emt_build_network(net, scenarios=None) -> Ctx:
+    lib = load_library()
+    keep: list = []
+    d = network_desc(net, keep)
+    sd = scenario_desc(scenarios, keep) if scenarios is not None else None
+    out = ctypes.c_void_p()
+    st = lib.emt_build_network(ctypes.byref(d), ctypes.byref(sd) if sd is not None else None, ctypes.byref(out))
+    _check(None, st)
+    return Ctx(out.value, int(net.n_nodes), 1 if scenarios is None else int(scenarios.n_scenarios))
+
+
+def emt_prefactor(ctx: Ctx) -> None:
+    _check(ctx, load_library().emt_prefactor(ctx.handle))
+
+
+def emt_set_recording(ctx: Ctx, channels: Optional[Sequence[int]] = None, decim: int = 1, max_rows: int = 0) -> None:
+    lib = load_library()
+    if channels is None:
+        _check(ctx, lib.emt_set_recording(ctx.handle, None, ctx.n_nodes, int(decim), int(max_rows)))
+    else:
+        ch = _arr(channels, np.int32)
+        _check(ctx, lib.emt_set_recording(ctx.handle, ch.ctypes.data if ch.size else None, int(ch.size),
+                                          int(decim), int(max_rows)))
+
+
+def emt_step_n(ctx: Ctx, n_steps: int, stream=None) -> None:
+    _check(ctx, load_library().emt_step_n(ctx.handle, int(n_steps), _stream_handle(stream)))
+
+
+def emt_read_waveforms(ctx: Ctx, channels, step0: int, n_rows: int, scen0: int = 0, n_scen: int = 1, out=None):
+    """Recorded waveforms [n_rows][n_scen][n_ch].  ``out`` may be a CUDA
+    torch tensor (filled on the device) or a numpy array; by default a new
+    numpy array is returned."""
+    lib = load_library()
+    ch = _arr(channels, np.int32)
+    shape = (int(n_rows), int(n_scen), int(ch.size))
+    on_device = 0
+    if out is None:
+        out = np.zeros(shape, dtype=np.float64)
+        ptr = out.ctypes.data
+    elif isinstance(out, np.ndarray):
+        if out.dtype != np.float64 or not out.flags.c_contiguous or out.size != int(np.prod(shape)):
+            raise ValueError("out must be a C-contiguous float64 array of shape " + str(shape))
+        ptr = out.ctypes.data
+    else:   # torch tensor
+        if not out.is_contiguous() or out.numel() != int(np.prod(shape)) or str(out.dtype) != "torch.float64":
+            raise ValueError("out must be a contiguous float64 tensor of shape " + str(shape))
+        ptr = out.data_ptr()
+        on_device = 1 if out.is_cuda else 0
+    if int(np.prod(shape)) == 0:
+        return out
+    _check(ctx, lib.emt_read_waveforms(ctx.handle, ch.ctypes.data, int(ch.size), int(step0), int(n_rows),
+                                       int(scen0), int(n_scen), ptr, on_device))
+    return out
+
+
+def emt_reset(ctx: Ctx) -> None:
+    _check(ctx, load_library().emt_reset(ctx.handle))
+
+
+def emt_sync(ctx: Ctx):
+    info = (ctypes.c_int32 * 4)()
+    _check(ctx, load_library().emt_sync(ctx.handle, info))
+    return list(info)
+
+
+def emt_set_option(ctx: Ctx, key: str, value: int) -> None:
+    _check(ctx, load_library().emt_set_option(ctx.handle, key.encode(), int(value)))
+
+
+def emt_get_info(ctx: Ctx, key: str) -> int:
+    v = ctypes.c_int64(0)
+    _check(ctx, load_library().emt_get_info(ctx.handle, key.encode(), ctypes.byref(v)))
+    return v.value
+
+
+def emt_get_node_order(ctx: Ctx) -> np.ndarray:
+    perm = np.zeros(ctx.n_nodes, dtype=np.int32)
+    _check(ctx, load_library().emt_get_node_order(ctx.handle, perm.ctypes.data if perm.size else None))
+    return perm
+
+
+def emt_last_error(ctx: Optional[Ctx] = None) -> str:
+    msg = load_library().emt_last_error(ctx.handle if ctx is not None else None)
+    return msg.decode() if msg else ""
+
+
+def emt_destroy(ctx: Ctx) -> None:
+    if ctx is not None and ctx.handle:
+        load_library(False).emt_destroy(ctx.handle)
+        ctx.handle = ctypes.c_void_p(None)
+
+
+# ------------------------------------------------------------------ wrapper
+
+class Simulator:
+    """One network (optionally with scenarios) on the current CUDA device."""
+
+    def __init__(self, net, scenarios=None, record: bool = True, n_steps: Optional[int] = None,
+                 channels=None, decim: int = 1, options: Optional[dict] = None):
+        self.net = net
+        self.ctx = emt_build_network(net, scenarios)
+        for k, v in (options or {}).items():
+            emt_set_option(self.ctx, k, v)
+        emt_prefactor(self.ctx)
+        self.channels = np.arange(net.n_nodes, dtype=np.int32) if channels is None else _arr(channels, np.int32)
+        self.decim = int(decim)
+        if record:
+            rows = int(n_steps if n_steps is not None else net.n_steps) // self.decim
+            emt_set_recording(self.ctx, None if channels is None else self.channels, self.decim, rows)
+
+    def run(self, n_steps: int, stream=None):
+        emt_step_n(self.ctx, n_steps, stream)
+
+    def waveforms(self, n_rows: Optional[int] = None, step0: Optional[int] = None, scen0: int = 0,
+                  n_scen: Optional[int] = None, out=None):
+        step0 = self.decim if step0 is None else step0
+        if n_rows is None:
+            n_rows = emt_get_info(self.ctx, "step") // self.decim - (step0 // self.decim - 1)
+        n_scen = self.ctx.n_scenarios if n_scen is None else n_scen
+        return emt_read_waveforms(self.ctx, self.channels, step0, n_rows, scen0, n_scen, out)
+
+    def sync(self):
+        return emt_sync(self.ctx)
+
+    def reset(self):
+        emt_reset(self.ctx)
+
+    def info(self, key: str) -> int:
+        return emt_get_info(self.ctx, key)
+
+    def close(self):
+        emt_destroy(self.ctx)

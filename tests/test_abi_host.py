@@ -1,0 +1,75 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every function include/emt.h declares, and rejects invalid
+network descriptions before touching the device."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1903_01081_b300 import emt, netgen as g
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(emt_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = emt.load_library()
+    names = declared_functions()
+    assert "emt_build_network" in names and "emt_step_n" in names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert set(emt.EXPORTS) <= names
+
+
+def bad(net, **changes):
+    net = net.copy()
+    for k, v in changes.items():
+        setattr(net, k, v)
+    with pytest.raises(emt.EmtError) as ei:
+        emt.emt_build_network(net)
+    assert ei.value.status == emt.EMT_EINVAL
+    return str(ei.value)
+
+
+def test_rejects_invalid_descriptions():
+    net = g.single_rlc(n_steps=10)
+    assert "value" in bad(net, br_value=np.where(np.arange(net.n_branches) == 3, -1.0, net.br_value))
+    k = net.br_k.copy(); k[0] = net.n_nodes
+    assert "out of range" in bad(net, br_k=k)
+    kind = net.br_kind.copy(); kind[1] = 7
+    assert "kind" in bad(net, br_kind=kind)
+    m = net.br_m.copy(); m[2] = net.br_k[2]
+    assert "one node" in bad(net, br_m=m)
+    assert "dt" in bad(net, dt=0.0)
+    b = g.NetworkBuilder(); b.source(1.0, 0.0); b.branch(g.source_node(0), g.GROUND, 0, 1.0)
+    assert "unknown end" in bad(b.build(1e-5, 0))
+
+
+def test_rejects_bad_lines_and_switches():
+    net = g.multi_subsystem(3, [2, 2], n_lines=1, n_sources=1, dt=20e-6)
+    assert "delay" in bad(net, ln_delay=np.zeros_like(net.ln_delay))
+    assert "Z_c" in bad(net, ln_zc=-net.ln_zc)
+    lk = net.ln_k.copy(); lk[0] = -1
+    assert "unknown nodes" in bad(net, ln_k=lk)
+    net2 = g.single_rlc(n_steps=10)
+    assert "resistance" in bad(net2, sw_r=np.zeros_like(net2.sw_r))
+
+
+def test_rejects_oversized_subsystem():
+    b = g.NetworkBuilder()
+    b.source(1.0, 0.0)
+    n = 129
+    b.branch(g.source_node(0), 0, 0, 1.0)
+    for i in range(n - 1):
+        b.branch(i, i + 1, 0, 1.0)
+    assert "at most 128" in bad(b.build(1e-5, n))
