@@ -116,8 +116,10 @@ emt_status emt_build_network(const emt_network_desc* desc, const emt_scenario_de
  * subsystem's conductance matrix G (companion conductances g = 1/R,
  * dt/(2L), 2C/dt; 1/Z_c per line end; 1/R per closed switch) for every
  * switch state it meets and store G^-1 (Gauss-Jordan with partial pivoting
- * plus one Newton step whose residual is summed in twice the working
- * precision).  Synchronous.  ESINGULAR names the subsystem. */
+ * plus a Newton step whose residual is summed in twice the working
+ * precision) as a double matrix plus its single-precision remainder, so
+ * each solve applies G^-1 to well beyond double rounding.  Synchronous.
+ * ESINGULAR names the subsystem. */
 emt_status emt_prefactor(emt_ctx* ctx);
 
 /* Choose the recorded node voltages ("waveform channels", Sec. II-A):
@@ -152,16 +154,14 @@ emt_status emt_reset(emt_ctx* ctx);
 emt_status emt_sync(emt_ctx* ctx, int32_t* dev_err_info);
 
 /* Tuning and debug knobs (key = value): "wait_budget_ns" (per wait),
- * "refine_kappa" (refine solves of subsystems whose inf-norm condition
- * estimate exceeds this; -1 never; applies at the next emt_prefactor),
  * "debug_hold_lines" (that subsystem never sends line values; -1 none;
  * for failure-path tests).  EINVAL for an unknown key. */
 emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
 
 /* Read-only facts: "n_subsystems", "n_ctas", "step", "max_subsystem_nodes",
  * "n_scenarios", "n_epochs_total", "sum_n2" (sum over subsystems of n_s^2),
- * "n_refined" (matrices whose solves are refined), "threads_per_cta",
- * "kernel_launches", "n_branches", "n_line_ends". */
+ * "threads_per_cta", "kernel_launches", "n_branches", "n_line_ends",
+ * "smem_bytes" (dynamic shared memory per CTA of the persistent kernel). */
 emt_status emt_get_info(const emt_ctx* ctx, const char* key, int64_t* value);
 
 /* Internal node order: perm[i] = original node id of internal slot i

@@ -46,16 +46,14 @@ struct emt_ctx {
   std::vector<EpochDev> epochs;
   std::vector<BranchDev> branches;
   std::vector<int32_t> lc_idx, sb_idx;
-  std::vector<int32_t> ent, eptr;
+  std::vector<int32_t> ent, il_node, il_cnt;
   std::vector<LineEndDev> line_ends;
   std::vector<int32_t> src_global;                     // global source id per local source slot
   std::vector<double> src_amp, src_phase, src_omega;   // per global source
   std::vector<int32_t> nb_sub, nb_dmin;
   std::vector<SwitchDev> switches;
-  std::vector<int32_t> sp_ptr, sp_col;
-  int64_t ring_len = 0, ginv_len = 0, n_lc_total = 0, sp_nz_total = 0;
-  FwdLimits lim{0, 1, 0, 0, 0, 0, 0, 0, 0};
-  int64_t n_refined = 0;
+  int64_t ring_len = 0, ginv_len = 0, n_lc_total = 0;
+  FwdLimits lim{0, 1, 0, 0, 0, 0, 0};
 
   // device arrays
   SubDev* d_sub = nullptr;
@@ -65,7 +63,8 @@ struct emt_ctx {
   int32_t* d_sb_idx = nullptr;
   double* d_h = nullptr;
   int32_t* d_ent = nullptr;
-  int32_t* d_eptr = nullptr;
+  int32_t* d_il_node = nullptr;
+  int32_t* d_il_cnt = nullptr;
   LineEndDev* d_le = nullptr;
   unsigned long long* d_ring = nullptr;
   int32_t* d_src_global = nullptr;
@@ -75,10 +74,8 @@ struct emt_ctx {
   double* d_src_table = nullptr;
   int64_t src_table_steps = 0;
   SwitchDev* d_sw = nullptr;
-  int32_t* d_sp_ptr = nullptr;
-  int32_t* d_sp_col = nullptr;
-  double* d_sp_val = nullptr;
   double* d_ginv = nullptr;
+  float* d_ginv_lo = nullptr;
   int32_t* d_err = nullptr;
 
   // recording
@@ -93,7 +90,6 @@ struct emt_ctx {
   int64_t step = 0;
   bool prefactored = false;
   unsigned long long wait_budget_ns = 2000000000ull;
-  double refine_kappa = 1000.0;
   int32_t hold_sub = -1;
   int64_t launches = 0;
 
@@ -385,7 +381,8 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     sd.n_nb = (int)c->nb_sub.size() - sd.nb_off;
   }
 
-  // -------- injection entries per node (see kEntryNeg), padded to 4
+  // -------- injection lanes (see kEntryNeg): 4 entries each, a node's
+  // lanes consecutive and inside one warp
   for (int s = 0; s < S; ++s) {
     SubDev& sd = c->subs[s];
     std::vector<std::vector<int32_t>> el(sd.n);
@@ -401,19 +398,30 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     }
     for (int e = 0; e < sd.n_le; ++e)
       el[c->line_ends[sd.le_off + e].node].push_back((int32_t)(kEntryNeg | (uint32_t)(ie_base + e)));
-    sd.ent_off = (int)c->ent.size();
-    sd.eptr_off = (int)c->eptr.size();
-    int cnt = 0;
+    sd.il_off = (int)c->il_node.size();
+    int lanes = 0;
     for (int k = 0; k < sd.n; ++k) {
-      c->eptr.push_back(cnt);
-      while (el[k].size() % 4) el[k].push_back(zero);
-      if (el[k].empty()) el[k].assign(4, zero);
-      c->ent.insert(c->ent.end(), el[k].begin(), el[k].end());
-      cnt += (int)el[k].size();
+      while (el[k].size() % 4 || el[k].empty()) el[k].push_back(zero);
+      const int cnt = (int)el[k].size() / 4;
+      if (cnt > kMaxLanesPerNode)
+        return bail("node " + std::to_string(nodes_of[s][k]) + " has more than " +
+                    std::to_string(4 * kMaxLanesPerNode) + " branch and line incidences");
+      if (lanes % 32 + cnt > 32)
+        while (lanes % 32) {   // pad to the next warp
+          for (int u = 0; u < 4; ++u) c->ent.push_back(zero);
+          c->il_node.push_back(-1);
+          c->il_cnt.push_back(0);
+          ++lanes;
+        }
+      for (int j = 0; j < cnt; ++j) {
+        for (int u = 0; u < 4; ++u) c->ent.push_back(el[k][4 * j + u]);
+        c->il_node.push_back(k);
+        c->il_cnt.push_back(j == 0 ? cnt : 0);
+        ++lanes;
+      }
     }
-    c->eptr.push_back(cnt);
-    sd.n_ent = cnt;
-    c->lim.ent = std::max(c->lim.ent, cnt);
+    sd.n_il = lanes;
+    c->lim.il = std::max(c->lim.il, lanes);
   }
 
   // -------- switch epochs per subsystem, sparse pattern of G per epoch
@@ -437,23 +445,12 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       eps.push_back({LLONG_MIN, events.empty() ? 1 : events[0] - 1});
       for (int64_t e : events) eps.push_back({e, e});
       sd.ep_off = (int)c->epochs.size();
-      // structural pattern shared by all epochs: branches between unknown nodes
-      std::vector<std::set<int>> base(sd.n);
-      for (int k = 0; k < sd.n; ++k) base[k].insert(k);
-      for (int b = sd.br_off; b < sd.br_off + sd.n_br; ++b) {
-        const BranchDev& x = c->branches[b];
-        if (x.k >= 0 && x.m >= 0) {
-          base[x.k].insert(x.m);
-          base[x.m].insert(x.k);
-        }
-      }
       for (auto& ep : eps) {
         EpochDev E{};
         E.start = ep.first;
         E.ginv_off = goff;
         goff += (int64_t)sd.n * sd.n;
         E.sw_off = (int)c->switches.size();
-        std::vector<std::set<int>> pat = base;
         for (int64_t w : sw_of[s]) {
           if (!switch_closed(d->sw_close_step[w], d->sw_open_step[w], ep.second)) continue;
           SwitchDev sw{};
@@ -461,36 +458,22 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
           sw.m = d->sw_m[w] >= 0 ? local[d->sw_m[w]] : -1;
           sw.g = 1.0 / d->sw_r[w];
           c->switches.push_back(sw);
-          if (sw.k >= 0 && sw.m >= 0) {
-            pat[sw.k].insert(sw.m);
-            pat[sw.m].insert(sw.k);
-          }
         }
         E.n_sw = (int)c->switches.size() - E.sw_off;
-        E.sp_ptr_off = (int)c->sp_ptr.size();
-        E.sp_nz_off = (int)c->sp_col.size();
-        int nz = 0;
-        for (int k = 0; k < sd.n; ++k) {
-          c->sp_ptr.push_back(nz);
-          for (int j : pat[k]) c->sp_col.push_back(j);
-          nz += (int)pat[k].size();
-        }
-        c->sp_ptr.push_back(nz);
-        E.n_nz = nz;
-        c->lim.nz = std::max(c->lim.nz, nz);
         c->epochs.push_back(E);
       }
       sd.n_ep = (int)c->epochs.size() - sd.ep_off;
     }
     c->ginv_len = goff;
-    c->sp_nz_total = (int64_t)c->sp_col.size();
   }
 
-  // -------- matvec chunking: ~12 columns per partial sum
+  // -------- matvec blocking: a task's n/q FMAs and a node's q-1 adds are
+  // both FP64 instructions on one warp, so q ~ sqrt(n), within the CTA
   for (int s = 0; s < S; ++s) {
     SubDev& sd = c->subs[s];
     const int n = std::max(sd.n, 1);
-    sd.q = std::max(1, std::min((n + 11) / 12, kFwdThreads / n));
+    const int q = (int)std::lround(std::sqrt((double)n));
+    sd.q = std::max(1, std::min(q, kFwdThreads / n));
     c->lim.q = std::max(c->lim.q, sd.q);
   }
 
@@ -504,20 +487,19 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   UP(d_lc_idx, lc_idx)
   UP(d_sb_idx, sb_idx)
   UP(d_ent, ent)
-  UP(d_eptr, eptr)
+  UP(d_il_node, il_node)
+  UP(d_il_cnt, il_cnt)
   UP(d_le, line_ends)
   UP(d_src_global, src_global)
   UP(d_src_amp, src_amp)
   UP(d_src_phase, src_phase)
   UP(d_src_omega, src_omega)
   UP(d_sw, switches)
-  UP(d_sp_ptr, sp_ptr)
-  UP(d_sp_col, sp_col)
 #undef UP
-  if (e == cudaSuccess) e = c->alloc_zero(&c->d_sp_val, (size_t)c->sp_nz_total);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_h, (size_t)c->n_lc_total);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ring, 2 * (size_t)std::max<int64_t>(c->ring_len, 1));
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ginv, (size_t)c->ginv_len);
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_ginv_lo, (size_t)c->ginv_len);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_err, 4);
   if (e == cudaSuccess) e = launch_companion(c->d_br, (int64_t)c->branches.size(), c->dt, nullptr);
   if (e == cudaSuccess) e = launch_ring_init(RingInitParams{c->d_le, (int64_t)c->line_ends.size(), c->d_ring}, nullptr);
@@ -556,21 +538,16 @@ extern "C" emt_status emt_prefactor(emt_ctx* c) {
   p.br = c->d_br;
   p.le = c->d_le;
   p.sw = c->d_sw;
-  p.sp_ptr = c->d_sp_ptr;
-  p.sp_col = c->d_sp_col;
-  p.sp_val = c->d_sp_val;
   p.ginv = c->d_ginv;
+  p.ginv_lo = c->d_ginv_lo;
   p.work_g = d_wg;
   p.work_r = d_wr;
   p.status = d_status;
-  p.refine_kappa = c->refine_kappa;
   if (e == cudaSuccess) e = launch_prefactor(p, std::max(c->lim.n, 1), nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   std::vector<int32_t> status(mat_sub.size(), 0);
   if (e == cudaSuccess && !status.empty())
     e = cudaMemcpy(status.data(), d_status, status.size() * sizeof(int32_t), cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && !c->epochs.empty())
-    e = cudaMemcpy(c->epochs.data(), c->d_ep, c->epochs.size() * sizeof(EpochDev), cudaMemcpyDeviceToHost);
   c->release(d_ms);
   c->release(d_me);
   c->release(d_status);
@@ -584,9 +561,6 @@ extern "C" emt_status emt_prefactor(emt_ctx* c) {
                                         std::to_string(c->original_of[c->subs[s].node_off]) + ", switch state " +
                                         std::to_string(mat_ep[i] - c->subs[s].ep_off) + ") is singular");
     }
-  c->n_refined = 0;
-  for (const EpochDev& E : c->epochs) c->n_refined += E.refine ? 1 : 0;
-  c->lim.refine = c->n_refined > 0 ? 1 : 0;
   c->prefactored = true;
   return EMT_OK;
 }
@@ -664,15 +638,14 @@ extern "C" emt_status emt_step_n(emt_ctx* c, int64_t n_steps, void* stream) {
   p.sub = c->d_sub;
   p.ep = c->d_ep;
   p.ginv = c->d_ginv;
-  p.sp_ptr = c->d_sp_ptr;
-  p.sp_col = c->d_sp_col;
-  p.sp_val = c->d_sp_val;
+  p.ginv_lo = c->d_ginv_lo;
   p.br = c->d_br;
   p.lc_idx = c->d_lc_idx;
   p.sb_idx = c->d_sb_idx;
   p.h = c->d_h;
   p.ent = c->d_ent;
-  p.eptr = c->d_eptr;
+  p.il_node = c->d_il_node;
+  p.il_cnt = c->d_il_cnt;
   p.le = c->d_le;
   p.ring = c->d_ring;
   p.src_global = c->d_src_global;
@@ -793,10 +766,6 @@ extern "C" emt_status emt_set_option(emt_ctx* c, const char* key, int64_t value)
     c->wait_budget_ns = (unsigned long long)value;
     return EMT_OK;
   }
-  if (k == "refine_kappa") {
-    c->refine_kappa = value < 0 ? -1.0 : (double)value;
-    return EMT_OK;
-  }
   if (k == "debug_hold_lines") {   // failure-path tests: one subsystem never sends line values
     if (value < -1 || value >= c->n_sub) return c->fail(EMT_EINVAL, "debug_hold_lines out of range");
     c->hold_sub = (int32_t)value;
@@ -817,8 +786,7 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
     int64_t s2 = 0;
     for (const SubDev& s : c->subs) s2 += (int64_t)s.n * s.n;
     *value = s2;
-  } else if (k == "n_refined") *value = c->n_refined;
-  else if (k == "threads_per_cta") *value = kFwdThreads;
+  } else if (k == "threads_per_cta") *value = kFwdThreads;
   else if (k == "kernel_launches") *value = c->launches;
   else if (k == "n_branches") *value = (int64_t)c->branches.size();
   else if (k == "n_line_ends") *value = (int64_t)c->line_ends.size();

@@ -19,9 +19,12 @@ constexpr int kFwdThreads = 256;
 //     inp = [ h (L/C slots) | g_b v_src (source-branch slots) |
 //             I_e parity 0 (line ends) | I_e parity 1 | 0 ]
 // An entry is an int32: bit 31 = subtract, bits 0..30 = index into inp with
-// line ends addressed in their parity-0 block.  Each node's entries are
-// padded to a multiple of 4 with the index of the trailing zero.
+// line ends addressed in their parity-0 block.  A node's entries are split
+// into "injection lanes" of 4 entries (padded with the trailing zero); the
+// lanes of one node are consecutive and never straddle a warp, so the
+// node's first lane can add the others' partial sums by warp shuffles.
 constexpr uint32_t kEntryNeg = 0x80000000u;
+constexpr int kMaxLanesPerNode = 32;
 
 // One branch in device form.  Node fields are subsystem-local:
 //   >= 0 local node, -1 ground, <= -2 local source -2-j.
@@ -71,9 +74,9 @@ struct SubDev {
   int32_t src_off, n_src;      // local sources (global ids in src_global)
   int32_t nb_off, n_nb;        // neighbour subsystems (reported by emt_get_info)
   int32_t ep_off, n_ep;        // switch epochs
-  int32_t ent_off, n_ent;      // injection entries (multiple of 4 per node)
-  int32_t eptr_off;            // n + 1 entry offsets (relative to ent_off)
-  int32_t q;                   // column chunks per row in the matvec
+  int32_t il_off, n_il;        // injection lanes (4 entries each; il_node / il_cnt per lane)
+  int32_t q;                   // column blocks per row in the matvec
+  int32_t pad;
 };
 
 // Switch epoch of a subsystem: state holding from step `start` on.
@@ -81,14 +84,11 @@ struct EpochDev {
   int64_t start;
   int64_t ginv_off;      // offset of this epoch's n x n G^-1
   int32_t sw_off, n_sw;  // closed switches (SwitchDev list)
-  int32_t sp_ptr_off;    // n + 1 row offsets of the sparse G (relative to sp_nz_off)
-  int32_t sp_nz_off, n_nz;
-  int32_t refine;        // set by the prefactor: refine each solve (ill-conditioned G)
 };
 
 // Per-launch upper bounds that size the forward kernel's shared memory.
 struct FwdLimits {
-  int32_t n, q, lc, sb, le, src, ent, nz, refine;
+  int32_t n, q, lc, sb, le, src, il;
 };
 
 struct FwdParams {
@@ -96,16 +96,15 @@ struct FwdParams {
   FwdLimits lim;
   const SubDev* sub;
   const EpochDev* ep;
-  const double* ginv;
-  const int32_t* sp_ptr;       // sparse G pattern / values per epoch
-  const int32_t* sp_col;
-  const double* sp_val;
+  const double* ginv;          // G^-1 rounded to double, per epoch
+  const float* ginv_lo;        // G^-1 minus that rounding, in single precision
   const BranchDev* br;
   const int32_t* lc_idx;       // branch index per L/C slot
   const int32_t* sb_idx;       // branch index per source-branch slot
   double* h;                   // history current per L/C slot
-  const int32_t* ent;          // injection entries
-  const int32_t* eptr;         // per subsystem n + 1 entry offsets
+  const int32_t* ent;          // injection entries, 4 per injection lane
+  const int32_t* il_node;      // node of each injection lane (-1: padding)
+  const int32_t* il_cnt;       // lanes of the node on its first lane, else 0
   const LineEndDev* le;
   unsigned long long* ring;    // [slots][2] tagged words
   const int32_t* src_global;   // global source id per local source slot
@@ -128,18 +127,15 @@ struct PrefParams {
   const int32_t* mat_sub;      // subsystem per matrix
   const int32_t* mat_ep;       // epoch index (into ep) per matrix
   const SubDev* sub;
-  EpochDev* ep;                // refine flags written here
+  const EpochDev* ep;
   const BranchDev* br;
   const LineEndDev* le;
   const SwitchDev* sw;
-  const int32_t* sp_ptr;
-  const int32_t* sp_col;
-  double* sp_val;              // filled from the stamped G
-  double* ginv;
+  double* ginv;                // X_hi: G^-1 rounded to double
+  float* ginv_lo;              // X_lo: G^-1 - X_hi in single precision
   double* work_g;              // copy of G per matrix, at ep.ginv_off
   double* work_r;              // residual I - G X per matrix, at ep.ginv_off
   int32_t* status;             // per matrix: 0 ok, 1 singular
-  double refine_kappa;         // refine solves when ||G|| ||G^-1|| (inf-norm) exceeds this; < 0 never
 };
 
 struct SourceParams {

@@ -4,9 +4,9 @@
 //                    history gain e = +2g (L) / -2g (C)
 // prefactor_kernel   process 3, once per subsystem and switch state: stamp G,
 //                    invert it in place (Gauss-Jordan, partial pivoting),
-//                    then one Newton step X <- X + X (I - G X) with the
-//                    residual summed in twice the working precision; flags
-//                    ill-conditioned matrices for refined solves
+//                    then a Newton step with the residual summed in twice
+//                    the working precision, giving G^-1 = X_hi + X_lo
+//                    (double + single-precision remainder)
 // source_kernel      process 1 for sources: the table v_src(t_n) of a launch
 // ring_init_kernel   de-energised line histories in the tagged rings
 // fwd_kernel         the persistent time loop (processes 1, 2, 4 and the
@@ -89,10 +89,8 @@ __device__ __forceinline__ void stamp(double* A, int n, int k, int m, double g) 
 __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
   extern __shared__ double A[];
   __shared__ double fcol[kMaxSubsystemNodes];
-  __shared__ double rowsum[kMaxSubsystemNodes];
   __shared__ int perm[kMaxSubsystemNodes];
   __shared__ int s_p, s_sing;
-  __shared__ double s_gnorm;
   const int mi = blockIdx.x;
   const SubDev S = P.sub[P.mat_sub[mi]];
   const EpochDev E = P.ep[P.mat_ep[mi]];
@@ -119,21 +117,6 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
   double* Gw = P.work_g + E.ginv_off;
   double* Rw = P.work_r + E.ginv_off;
   for (int i = tid; i < n * n; i += T) Gw[i] = A[i];
-  // sparse copy of the stamped G (pattern from the host) and row sums
-  for (int i = tid; i < n; i += T) {
-    const int* rp = P.sp_ptr + E.sp_ptr_off;
-    for (int x = rp[i]; x < rp[i + 1]; ++x)
-      P.sp_val[E.sp_nz_off + x] = A[i * n + P.sp_col[E.sp_nz_off + x]];
-    double s = 0.0;
-    for (int j = 0; j < n; ++j) s += fabs(A[i * n + j]);
-    rowsum[i] = s;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double g = 0.0;
-    for (int i = 0; i < n; ++i) g = fmax(g, rowsum[i]);
-    s_gnorm = g;
-  }
   // in-place Gauss-Jordan inversion with row pivoting
   for (int k = 0; k < n; ++k) {
     if (tid < 32) {
@@ -192,9 +175,12 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
       }
     __syncthreads();
   }
-  // Newton step: R = I - G X with Dot2 (exact products, sum carried in two
-  // doubles), then X + X R.  X's error drops from ~cond(G) eps to a few
-  // ulps, so the explicit inverse does not bias the long recursion.
+  // Newton step: R0 = I - G X0 with Dot2 (exact products, sum carried in
+  // two doubles), X_hi = X0 + X0 R0, which is G^-1 to about an ulp.  Then
+  // the remainder X_lo = X_hi (I - G X_hi) in single precision: a rounded
+  // inverse is the exact inverse of a matrix off from G by ~cond(G) eps,
+  // a systematic error the long recursion would integrate; X_hi + X_lo
+  // removes it at the cost of single-precision work per solve.
   for (int idx = tid; idx < n * n; idx += T) {
     const int i = idx / n, j = idx - i * n;
     double hi = (i == j) ? 1.0 : 0.0, lo = 0.0;
@@ -210,19 +196,23 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
     out[idx] = A[idx] + c;
   }
   __syncthreads();
-  for (int i = tid; i < n; i += T) {
-    double s = 0.0;
-    for (int j = 0; j < n; ++j) s += fabs(out[i * n + j]);
-    rowsum[i] = s;
+  for (int idx = tid; idx < n * n; idx += T) A[idx] = out[idx];
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += T) {
+    const int i = idx / n, j = idx - i * n;
+    double hi = (i == j) ? 1.0 : 0.0, lo = 0.0;
+    for (int k = 0; k < n; ++k) dot2_acc(hi, lo, -Gw[i * n + k], A[k * n + j]);
+    Rw[idx] = __dadd_rn(hi, lo);
   }
   __syncthreads();
-  if (tid == 0) {
-    double x = 0.0;
-    for (int i = 0; i < n; ++i) x = fmax(x, rowsum[i]);
-    const double kappa = s_gnorm * x;
-    P.ep[P.mat_ep[mi]].refine = (P.refine_kappa >= 0.0 && kappa > P.refine_kappa) ? 1 : 0;
-    P.status[mi] = 0;
+  float* out_lo = P.ginv_lo + E.ginv_off;
+  for (int idx = tid; idx < n * n; idx += T) {
+    const int i = idx / n, j = idx - i * n;
+    double c = 0.0;
+    for (int k = 0; k < n; ++k) c = fma(A[i * n + k], Rw[k * n + j], c);
+    out_lo[idx] = (float)c;
   }
+  if (tid == 0) P.status[mi] = 0;
 }
 
 // ------------------------------------------------------------ sources
@@ -271,14 +261,26 @@ __global__ void ring_init_kernel(RingInitParams P) {
 }
 
 // ------------------------------------------------------------ forward
+//
+// On B300 a warp issues at most one FP64 instruction per ~64 cycles however
+// many of its lanes are active, and two warps on one SM sub-partition share
+// that rate.  The step is therefore laid out to keep the FP64 instruction
+// count of the busiest warp small: four-entry injection lanes joined by
+// shuffles, one FMA chain per matvec task over a contiguous block of
+// columns (plus a single-precision chain for X_lo), node sums in their own
+// phase, and update items of one kind per warp.  The last warp only
+// collects the next step's line values.
+
+constexpr int kPollWarp = kFwdThreads / 32 - 1;
+constexpr int kItemThreads = kFwdThreads - 32;
 
 // Shared-memory layout of fwd_kernel, from the per-launch limits.  G^-1
 // rows are stored with an odd stride (n | 1) so that the rows a warp reads
 // together fall in different banks.
 struct FwdSmem {
-  size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar, spv;        // 8-byte
-  size_t gi32, rr, cpart;                                                       // 4-byte float
-  size_t lck, lcm, lckind, sbsrc, lenode, ledepth, led, rslot, wslot, ent, eptr, srcg, spc, spp;   // int
+  size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar;   // 8-byte
+  size_t gilo, ivf;                                                 // float
+  size_t lck, lcm, lckind, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg;   // int
   size_t bytes;
 };
 
@@ -287,8 +289,8 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   size_t o = 0;
   auto d = [&](size_t count) { size_t r = o; o += count * 8; return r; };
   auto w = [&](size_t count) { size_t r = o; o += count * 4; return r; };
-  const size_t rf = L.refine ? 1 : 0;
-  s.gi = d((size_t)L.n * (L.n | 1));
+  const size_t ldg = (size_t)(L.n | 1);
+  s.gi = d((size_t)L.n * ldg);
   s.part = d((size_t)L.n * L.q);
   s.iv = d(L.n);
   s.vv = d(L.n);
@@ -299,10 +301,8 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.ley2 = d(L.le);
   s.leown = d(L.le);
   s.lefar = d(L.le);
-  s.spv = d(rf * L.nz);
-  s.gi32 = w(rf * L.n * (L.n | 1));
-  s.rr = w(rf * L.n);
-  s.cpart = w(rf * L.n * L.q);
+  s.gilo = w((size_t)L.n * ldg);
+  s.ivf = w(L.n);
   s.lck = w(L.lc);
   s.lcm = w(L.lc);
   s.lckind = w(L.lc);
@@ -312,16 +312,15 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.led = w(L.le);
   s.rslot = w(L.le);
   s.wslot = w(L.le);
-  s.ent = w(L.ent);
-  s.eptr = w((size_t)L.n + 1);
+  s.ent = w(4 * (size_t)L.il);
+  s.ilnode = w(L.il);
+  s.ilcnt = w(L.il);
   s.srcg = w(L.src);
-  s.spc = w(rf * L.nz);
-  s.spp = w(rf * ((size_t)L.n + 1));
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
 }
 
-// Warp 0 collects one step's line-end histories I_e(n) from the tagged
+// One warp collects one step's line-end histories I_e(n) from the tagged
 // rings.  Bounded: on exceeding the time budget (or seeing another CTA's
 // error) it latches an error and returns false.
 __device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int lane, int sidx, const long long* leown,
@@ -355,21 +354,12 @@ __device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int la
   return __all_sync(0xffffffffu, ok);
 }
 
-__device__ __forceinline__ double sum_parts(const double* p, int Q) {
-  double a = p[0], b = 0.0;
-  int q = 1;
-  for (; q + 1 < Q; q += 2) {
-    a += p[q];
-    b += p[q + 1];
-  }
-  if (q < Q) a += p[q];
-  return a + b;
-}
-
-__device__ __forceinline__ float sum_parts_f(const float* p, int Q) {
-  float a = 0.f;
-  for (int q = 0; q < Q; ++q) a += p[q];
-  return a;
+__device__ __forceinline__ double signed_entry(const double* inp, unsigned raw, int ie_base, int n_le, int parshift) {
+  int idx = (int)(raw & ~kEntryNeg);
+  if ((unsigned)(idx - ie_base) < (unsigned)n_le) idx += parshift;
+  const unsigned long long bits =
+      (unsigned long long)__double_as_longlong(inp[idx]) ^ ((unsigned long long)(raw & kEntryNeg) << 32);
+  return __longlong_as_double((long long)bits);
 }
 
 __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
@@ -387,10 +377,8 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   double* ley2 = reinterpret_cast<double*>(smem_raw + L.ley2);
   long long* leown = reinterpret_cast<long long*>(smem_raw + L.leown);
   long long* lefar = reinterpret_cast<long long*>(smem_raw + L.lefar);
-  double* spv = reinterpret_cast<double*>(smem_raw + L.spv);
-  float* gi32 = reinterpret_cast<float*>(smem_raw + L.gi32);
-  float* rr = reinterpret_cast<float*>(smem_raw + L.rr);
-  float* cpart = reinterpret_cast<float*>(smem_raw + L.cpart);
+  float* gilo = reinterpret_cast<float*>(smem_raw + L.gilo);
+  float* ivf = reinterpret_cast<float*>(smem_raw + L.ivf);
   int* lck = reinterpret_cast<int*>(smem_raw + L.lck);
   int* lcm = reinterpret_cast<int*>(smem_raw + L.lcm);
   int* lckind = reinterpret_cast<int*>(smem_raw + L.lckind);
@@ -401,21 +389,26 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   int* rslot = reinterpret_cast<int*>(smem_raw + L.rslot);
   int* wslot = reinterpret_cast<int*>(smem_raw + L.wslot);
   int* ent = reinterpret_cast<int*>(smem_raw + L.ent);
-  int* eptr = reinterpret_cast<int*>(smem_raw + L.eptr);
+  int* ilnode = reinterpret_cast<int*>(smem_raw + L.ilnode);
+  int* ilcnt = reinterpret_cast<int*>(smem_raw + L.ilcnt);
   int* srcg = reinterpret_cast<int*>(smem_raw + L.srcg);
-  int* spc = reinterpret_cast<int*>(smem_raw + L.spc);
-  int* spp = reinterpret_cast<int*>(smem_raw + L.spp);
 
   const int sidx = blockIdx.x;
   const SubDev S = P.sub[sidx];
   const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = S.n, Q = S.q, ldg = n | 1;
-  const int n_lc = S.n_lc, n_sb = S.n_sb, n_le = S.n_le;
+  const int blk = (n + Q - 1) / Q;   // columns per matvec task
+  const int n_lc = S.n_lc, n_sb = S.n_sb, n_le = S.n_le, n_il = S.n_il;
   const int ie_base = n_lc + n_sb;
   const int zero_slot = ie_base + 2 * n_le;
   const int src_vs = P.lim.src;
   const bool writes_lines = sidx != P.hold_sub;
-  const int src_thread = T - 1 - tid;   // the last threads carry the least other work
+  const int src_thread = T - 1 - tid;
+  // update items: L/C branches, then line ends, then source branches, each
+  // block starting on a warp boundary so that a warp runs one kind
+  const int it_le = (n_lc + 31) & ~31;
+  const int it_sb = it_le + ((n_le + 31) & ~31);
+  const int it_end = it_sb + n_sb;
 
   // ---- prologue: this subsystem's data into shared memory
   for (int x = tid; x < n_lc; x += T) {
@@ -442,8 +435,11 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     rslot[x] = (int)(P.n0 % e.depth);
     wslot[x] = (int)((P.n0 + e.d) % e.depth);
   }
-  for (int x = tid; x < S.n_ent; x += T) ent[x] = P.ent[S.ent_off + x];
-  for (int x = tid; x <= n; x += T) eptr[x] = P.eptr[S.eptr_off + x];
+  for (int x = tid; x < 4 * n_il; x += T) ent[x] = P.ent[4 * (size_t)S.il_off + x];
+  for (int x = tid; x < n_il; x += T) {
+    ilnode[x] = P.il_node[S.il_off + x];
+    ilcnt[x] = P.il_cnt[S.il_off + x];
+  }
   for (int x = tid; x < S.n_src; x += T) {
     srcg[x] = P.src_global[S.src_off + x];
     vs[(P.n0 & 1) * src_vs + x] = P.src_table[P.src_global[S.src_off + x]];
@@ -455,27 +451,17 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   int ep = 0;
   while (ep + 1 < S.n_ep && P.ep[S.ep_off + ep + 1].start <= P.n0) ++ep;
   long long next_ep_start = (ep + 1 < S.n_ep) ? P.ep[S.ep_off + ep + 1].start : LLONG_MAX;
-  int refine = 0;
   {
-    const EpochDev E = P.ep[S.ep_off + ep];
-    refine = P.lim.refine ? E.refine : 0;
-    const double* src = P.ginv + E.ginv_off;
+    const int64_t off = P.ep[S.ep_off + ep].ginv_off;
     for (int i = tid; i < n * n; i += T) {
       const int r = i / n, c = i - r * n;
-      gi[r * ldg + c] = src[i];
-      if (refine) gi32[r * ldg + c] = (float)src[i];
-    }
-    if (refine) {
-      for (int x = tid; x < E.n_nz; x += T) {
-        spv[x] = P.sp_val[E.sp_nz_off + x];
-        spc[x] = P.sp_col[E.sp_nz_off + x];
-      }
-      for (int x = tid; x <= n; x += T) spp[x] = P.sp_ptr[E.sp_ptr_off + x];
+      gi[r * ldg + c] = P.ginv[off + i];
+      gilo[r * ldg + c] = P.ginv_lo[off + i];
     }
   }
   __syncthreads();
   for (int x = tid; x < n_sb; x += T) inp[n_lc + x] = sbg[x] * vs[(P.n0 & 1) * src_vs + sbsrc[x]];
-  if (warp == 0 && n_le > 0) {
+  if (warp == kPollWarp && n_le > 0) {
     const bool ok = collect_lines(P, n_le, (unsigned)P.n0, lane, sidx, leown, ledepth, rslot,
                                   inp + ie_base + (int)(P.n0 & 1) * n_le);
     if (!ok && lane == 0) s_abort = 1;
@@ -494,20 +480,11 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     if (step >= next_ep_start) {
       while (ep + 1 < S.n_ep && P.ep[S.ep_off + ep + 1].start <= step) ++ep;
       next_ep_start = (ep + 1 < S.n_ep) ? P.ep[S.ep_off + ep + 1].start : LLONG_MAX;
-      const EpochDev E = P.ep[S.ep_off + ep];
-      refine = P.lim.refine ? E.refine : 0;
-      const double* src = P.ginv + E.ginv_off;
+      const int64_t off = P.ep[S.ep_off + ep].ginv_off;
       for (int i = tid; i < n * n; i += T) {
         const int r = i / n, c = i - r * n;
-        gi[r * ldg + c] = src[i];
-        if (refine) gi32[r * ldg + c] = (float)src[i];
-      }
-      if (refine) {
-        for (int x = tid; x < E.n_nz; x += T) {
-          spv[x] = P.sp_val[E.sp_nz_off + x];
-          spc[x] = P.sp_col[E.sp_nz_off + x];
-        }
-        for (int x = tid; x <= n; x += T) spp[x] = P.sp_ptr[E.sp_ptr_off + x];
+        gi[r * ldg + c] = P.ginv[off + i];
+        gilo[r * ldg + c] = P.ginv_lo[off + i];
       }
     }
     // next step's source voltages: load issued now, stored after process 4
@@ -515,115 +492,99 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     if (src_thread < S.n_src && step + 1 < n_end)
       vnext = __ldg(P.src_table + (step + 1 - P.n0) * P.n_sources + srcg[src_thread]);
 
-    // process 2: nodal injections, four entries at a time
-    for (int k = tid; k < n; k += T) {
-      double a0 = 0.0, a1 = 0.0;
-      const int x1 = eptr[k + 1];
-      for (int x = eptr[k]; x < x1; x += 4) {
-        double v[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const unsigned raw = (unsigned)ent[x + u];
-          int idx = (int)(raw & ~kEntryNeg);
-          if ((unsigned)(idx - ie_base) < (unsigned)n_le) idx += parshift;
-          const unsigned long long bits =
-              (unsigned long long)__double_as_longlong(inp[idx]) ^ ((unsigned long long)(raw & kEntryNeg) << 32);
-          v[u] = __longlong_as_double((long long)bits);
-        }
-        const double c = (v[0] + v[1]) + (v[2] + v[3]);
-        if (((x - eptr[k]) & 4) == 0) a0 += c;
-        else a1 += c;
+    // process 2: nodal injections; each lane sums four entries, the node's
+    // first lane adds its other lanes' sums
+    for (int base = 0; base < n_il; base += T) {
+      const int l = base + tid;
+      double s = 0.0;
+      int node = -1, cnt = 0;
+      if (l < n_il) {
+        node = ilnode[l];
+        cnt = ilcnt[l];
+        const int* e4 = ent + 4 * l;
+        s = (signed_entry(inp, (unsigned)e4[0], ie_base, n_le, parshift) +
+             signed_entry(inp, (unsigned)e4[1], ie_base, n_le, parshift)) +
+            (signed_entry(inp, (unsigned)e4[2], ie_base, n_le, parshift) +
+             signed_entry(inp, (unsigned)e4[3], ie_base, n_le, parshift));
       }
-      iv[k] = a0 + a1;
+      const int wmax = __reduce_max_sync(0xffffffffu, cnt);
+      double acc = s;
+      for (int j = 1; j < wmax; ++j) {
+        const double o = __shfl_down_sync(0xffffffffu, s, j);
+        if (j < cnt) acc += o;
+      }
+      if (cnt > 0) {
+        iv[node] = acc;
+        ivf[node] = (float)acc;
+      }
     }
     __syncthreads();
 
-    // process 4: v = G^-1 i, rows split into Q column chunks
+    // process 4: v = (X_hi + X_lo) i; task (r, q) runs one FMA chain over
+    // the contiguous column block q (the warp issue rate, not the FMA
+    // latency, is the limit; contiguous blocks keep the rounding of the
+    // partial sums small, measured over long runs)
     for (int task = tid; task < n * Q; task += T) {
       const int r = task / Q, q = task - r * Q;
       const double* row = gi + r * ldg;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int j = q;
-      for (; j + 3 * Q < n; j += 4 * Q) {
-        a0 = fma(row[j], iv[j], a0);
-        a1 = fma(row[j + Q], iv[j + Q], a1);
-        a2 = fma(row[j + 2 * Q], iv[j + 2 * Q], a2);
-        a3 = fma(row[j + 3 * Q], iv[j + 3 * Q], a3);
+      const float* rowl = gilo + r * ldg;
+      const int j1 = min(n, (q + 1) * blk);
+      double a = 0.0;
+      float b = 0.f;
+      for (int j = q * blk; j < j1; ++j) {
+        a = fma(row[j], iv[j], a);
+        b = fmaf(rowl[j], ivf[j], b);
       }
-      for (; j < n; j += Q) a0 = fma(row[j], iv[j], a0);
-      part[task] = (a0 + a1) + (a2 + a3);
+      part[task] = a + (double)b;
     }
     if (src_thread < S.n_src) vs[(par ^ 1) * src_vs + src_thread] = vnext;
     __syncthreads();
 
-    if (refine) {
-      // one refinement step: r = i - G v0 (sparse G, Dot2), v = v0 + G^-1 r
-      // with the correction in single precision (its relative accuracy only
-      // needs to beat cond(G) * 2^-24 << 1)
-      for (int r = tid; r < n; r += T) vv[r] = sum_parts(part + r * Q, Q);
-      __syncthreads();
-      for (int k = tid; k < n; k += T) {
-        double hi = iv[k], lo = 0.0;
-        for (int x = spp[k]; x < spp[k + 1]; ++x) dot2_acc(hi, lo, -spv[x], vv[spc[x]]);
-        rr[k] = (float)__dadd_rn(hi, lo);
-      }
-      __syncthreads();
-      for (int task = tid; task < n * Q; task += T) {
-        const int r = task / Q, q = task - r * Q;
-        const float* row = gi32 + r * ldg;
-        float a0 = 0.f, a1 = 0.f;
-        int j = q;
-        for (; j + Q < n; j += 2 * Q) {
-          a0 = fmaf(row[j], rr[j], a0);
-          a1 = fmaf(row[j + Q], rr[j + Q], a1);
-        }
-        if (j < n) a0 = fmaf(row[j], rr[j], a0);
-        cpart[task] = a0 + a1;
-      }
-      __syncthreads();
-    }
-
-    // node voltages, line outputs, history currents, next step's source
-    // injections: each item finishes the voltages it needs from the partials
+    // node voltages
     const bool rec_now = P.rec != nullptr && dec == 0 && rec_row < P.rec_rows;
-    const double* ie_cur = inp + ie_base + parshift;
-    const double* vs_next = vs + (par ^ 1) * src_vs;
-    const int n_items = n + n_le + n_lc + n_sb;
-    for (int it = tid; it < n_items; it += T) {
-      if (it < n) {
-        const double v = refine ? vv[it] + (double)sum_parts_f(cpart + it * Q, Q) : sum_parts(part + it * Q, Q);
-        if (rec_now) {
-          const int pos = P.rec_pos[S.node_off + it];
-          if (pos >= 0) P.rec[rec_row * P.n_rec + pos] = v;
-        }
-      } else if (it < n + n_le) {
-        const int e = it - n, r = lenode[e];
-        const double v = refine ? vv[r] + (double)sum_parts_f(cpart + r * Q, Q) : sum_parts(part + r * Q, Q);
-        if (writes_lines)
-          st_tagged(P.ring + 2 * (lefar[e] + wslot[e]), (unsigned)(step + led[e]), fma(-ley2[e], v, -ie_cur[e]));
-        const int nx = wslot[e] + 1;
-        wslot[e] = nx == ledepth[e] ? 0 : nx;
-      } else if (it < n + n_le + n_lc) {
-        const int x = it - n - n_le;
-        const int k = lck[x], m = lcm[x];
-        double vk, vm;
-        if (k >= 0) vk = refine ? vv[k] + (double)sum_parts_f(cpart + k * Q, Q) : sum_parts(part + k * Q, Q);
-        else vk = (k == -1) ? 0.0 : vsc[-2 - k];
-        if (m >= 0) vm = refine ? vv[m] + (double)sum_parts_f(cpart + m * Q, Q) : sum_parts(part + m * Q, Q);
-        else vm = (m == -1) ? 0.0 : vsc[-2 - m];
-        const double vb = vk - vm;
-        inp[x] = lckind[x] == 1 ? fma(lce[x], vb, inp[x]) : fma(lce[x], vb, -inp[x]);
-      } else {
-        const int x = it - n - n_le - n_lc;
-        inp[n_lc + x] = sbg[x] * vs_next[sbsrc[x]];
+    for (int r = tid; r < n; r += T) {
+      double v = part[r * Q];
+      for (int q = 1; q < Q; ++q) v += part[r * Q + q];
+      vv[r] = v;
+      if (rec_now) {
+        const int pos = P.rec_pos[S.node_off + r];
+        if (pos >= 0) P.rec[rec_row * P.n_rec + pos] = v;
       }
     }
     if (dec == 0) ++rec_row;
     if (++dec == decim) dec = 0;
-    if (warp == 0 && n_le > 0 && step + 1 < n_end) {
-      const bool ok = collect_lines(P, n_le, (unsigned)(step + 1), lane, sidx, leown, ledepth, rslot,
-                                    inp + ie_base + (par ^ 1) * n_le);
-      if (!ok && lane == 0) s_abort = 1;
+    __syncthreads();
+
+    // process 1: history currents, line outputs, next step's source
+    // injections; the poll warp meanwhile collects next step's line values
+    if (warp == kPollWarp) {
+      if (n_le > 0 && step + 1 < n_end) {
+        const bool ok = collect_lines(P, n_le, (unsigned)(step + 1), lane, sidx, leown, ledepth, rslot,
+                                      inp + ie_base + (par ^ 1) * n_le);
+        if (!ok && lane == 0) s_abort = 1;
+      }
+    } else {
+      const double* ie_cur = inp + ie_base + parshift;
+      const double* vs_next = vs + (par ^ 1) * src_vs;
+      for (int it = tid; it < it_end; it += kItemThreads) {
+        if (it < n_lc) {
+          const int k = lck[it], m = lcm[it];
+          const double vk = k >= 0 ? vv[k] : (k == -1 ? 0.0 : vsc[-2 - k]);
+          const double vm = m >= 0 ? vv[m] : (m == -1 ? 0.0 : vsc[-2 - m]);
+          const double vb = vk - vm;
+          inp[it] = lckind[it] == 1 ? fma(lce[it], vb, inp[it]) : fma(lce[it], vb, -inp[it]);
+        } else if (it >= it_le && it < it_le + n_le) {
+          const int e = it - it_le;
+          if (writes_lines)
+            st_tagged(P.ring + 2 * (lefar[e] + wslot[e]), (unsigned)(step + led[e]),
+                      fma(-ley2[e], vv[lenode[e]], -ie_cur[e]));
+          const int nx = wslot[e] + 1;
+          wslot[e] = nx == ledepth[e] ? 0 : nx;
+        } else if (it >= it_sb) {
+          const int x = it - it_sb;
+          inp[n_lc + x] = sbg[x] * vs_next[sbsrc[x]];
+        }
+      }
     }
     __syncthreads();
   }

@@ -5,8 +5,9 @@ seeded network and compares all recorded node voltages element by element.
 Tolerance: the peak-normalised error
     max_{n,k} |v_gpu - v_oracle| / max_{n,k} |v_oracle|  <=  1e-10,
 the bar the method is held to (explicit G^-1 against per-step LU differ only
-by rounding, amplified at most by the matrices' condition numbers; solves of
-ill-conditioned subsystems are refined to keep that amplification small).
+by rounding, amplified at most by the matrices' condition numbers; G^-1 is
+kept as a double plus its single-precision remainder so that the rounded
+inverse does not act as a systematically perturbed conductance matrix).
 """
 import numpy as np
 import pytest
@@ -72,19 +73,6 @@ def test_large_scale_full_size():
     assert rel_err(got, ref) <= TOL
     per_node = np.max(np.abs(got - ref), axis=0) / np.maximum(np.max(np.abs(ref), axis=0), 1e-300)
     assert np.max(per_node) <= 1e-8
-
-
-def test_refinement_is_what_keeps_ill_conditioned_subsystems_in_tolerance():
-    net = g.large_scale(n_steps=20000)
-    N = 20000
-    sim = emt.Simulator(net, n_steps=N)
-    assert sim.info("n_refined") > 0
-    sim.close()
-    ref = oracle.simulate(net, N)
-    refined = gpu_run(net, N)
-    assert rel_err(refined, ref) <= TOL
-    plain = gpu_run(net, N, options={"refine_kappa": -1})
-    assert rel_err(plain, ref) >= rel_err(refined, ref)
 
 
 def test_strict_500_subsystems():
