@@ -161,7 +161,8 @@ emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
 /* Read-only facts: "n_subsystems", "n_ctas", "step", "max_subsystem_nodes",
  * "n_scenarios", "n_epochs_total", "sum_n2" (sum over subsystems of n_s^2),
  * "threads_per_cta", "kernel_launches", "n_branches", "n_line_ends",
- * "smem_bytes" (dynamic shared memory per CTA of the persistent kernel). */
+ * "smem_bytes" (dynamic shared memory per CTA of the persistent kernel),
+ * "n_strong_branches" (L/C branches applied through extra solve columns). */
 emt_status emt_get_info(const emt_ctx* ctx, const char* key, int64_t* value);
 
 /* Internal node order: perm[i] = original node id of internal slot i

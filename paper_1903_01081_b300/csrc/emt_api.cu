@@ -46,14 +46,14 @@ struct emt_ctx {
   std::vector<EpochDev> epochs;
   std::vector<BranchDev> branches;
   std::vector<int32_t> lc_idx, sb_idx;
-  std::vector<int32_t> ent, il_node, il_cnt;
+  std::vector<int32_t> ent, il_node, il_cnt, str_slot;
   std::vector<LineEndDev> line_ends;
   std::vector<int32_t> src_global;                     // global source id per local source slot
   std::vector<double> src_amp, src_phase, src_omega;   // per global source
   std::vector<int32_t> nb_sub, nb_dmin;
   std::vector<SwitchDev> switches;
   int64_t ring_len = 0, ginv_len = 0, n_lc_total = 0;
-  FwdLimits lim{0, 1, 0, 0, 0, 0, 0};
+  FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0};
 
   // device arrays
   SubDev* d_sub = nullptr;
@@ -65,6 +65,7 @@ struct emt_ctx {
   int32_t* d_ent = nullptr;
   int32_t* d_il_node = nullptr;
   int32_t* d_il_cnt = nullptr;
+  int32_t* d_str_slot = nullptr;
   LineEndDev* d_le = nullptr;
   unsigned long long* d_ring = nullptr;
   int32_t* d_src_global = nullptr;
@@ -381,15 +382,46 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     sd.n_nb = (int)c->nb_sub.size() - sd.nb_off;
   }
 
+  // -------- strong L/C branches (see kStrongRatio), from the companion
+  // conductances and the line-end conductances at each node
+  auto companion = [&](const BranchDev& x) {
+    return x.kind == 0 ? 1.0 / x.value : (x.kind == 1 ? c->dt / (2.0 * x.value) : 2.0 * x.value / c->dt);
+  };
+  std::vector<char> strong(c->branches.size(), 0);
+  for (int s = 0; s < S; ++s) {
+    SubDev& sd = c->subs[s];
+    std::vector<double> diag(sd.n, 0.0);
+    for (int b = sd.br_off; b < sd.br_off + sd.n_br; ++b) {
+      const BranchDev& x = c->branches[b];
+      const double g = companion(x);
+      if (x.k >= 0) diag[x.k] += g;
+      if (x.m >= 0) diag[x.m] += g;
+    }
+    for (int e = sd.le_off; e < sd.le_off + sd.n_le; ++e) diag[c->line_ends[e].node] += c->line_ends[e].y;
+    sd.str_off = (int)c->str_slot.size();
+    for (int b = sd.br_off; b < sd.br_off + sd.n_br; ++b) {
+      const BranchDev& x = c->branches[b];
+      if (x.kind == 0 || x.k < 0 || x.m < 0) continue;
+      const double g = companion(x);
+      if (g >= kStrongRatio * std::min(diag[x.k] - g, diag[x.m] - g)) {
+        strong[b] = 1;
+        c->str_slot.push_back(lc_slot_of[b]);
+      }
+    }
+    sd.n_str = (int)c->str_slot.size() - sd.str_off;
+    c->lim.str = std::max(c->lim.str, sd.n_str);
+    c->lim.nc = std::max(c->lim.nc, sd.n + sd.n_str);
+  }
+
   // -------- injection lanes (see kEntryNeg): 4 entries each, a node's
-  // lanes consecutive and inside one warp
+  // lanes consecutive and inside one warp; strong branches stay out
   for (int s = 0; s < S; ++s) {
     SubDev& sd = c->subs[s];
     std::vector<std::vector<int32_t>> el(sd.n);
     const int ie_base = sd.n_lc + sd.n_sb, zero = ie_base + 2 * sd.n_le;
     for (int b = sd.br_off; b < sd.br_off + sd.n_br; ++b) {
       const BranchDev& x = c->branches[b];
-      if (x.kind != 0) {
+      if (x.kind != 0 && !strong[b]) {
         const int32_t slot = lc_slot_of[b];
         if (x.k >= 0) el[x.k].push_back((int32_t)(kEntryNeg | (uint32_t)slot));   // current leaves k
         if (x.m >= 0) el[x.m].push_back(slot);                                     // and enters m
@@ -449,7 +481,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
         EpochDev E{};
         E.start = ep.first;
         E.ginv_off = goff;
-        goff += (int64_t)sd.n * sd.n;
+        goff += (int64_t)sd.n * (sd.n + sd.n_str);
         E.sw_off = (int)c->switches.size();
         for (int64_t w : sw_of[s]) {
           if (!switch_closed(d->sw_close_step[w], d->sw_open_step[w], ep.second)) continue;
@@ -472,7 +504,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   for (int s = 0; s < S; ++s) {
     SubDev& sd = c->subs[s];
     const int n = std::max(sd.n, 1);
-    const int q = (int)std::lround(std::sqrt((double)n));
+    const int q = (int)std::lround(std::sqrt((double)(n + sd.n_str)));
     sd.q = std::max(1, std::min(q, kFwdThreads / n));
     c->lim.q = std::max(c->lim.q, sd.q);
   }
@@ -489,6 +521,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   UP(d_ent, ent)
   UP(d_il_node, il_node)
   UP(d_il_cnt, il_cnt)
+  UP(d_str_slot, str_slot)
   UP(d_le, line_ends)
   UP(d_src_global, src_global)
   UP(d_src_amp, src_amp)
@@ -538,6 +571,8 @@ extern "C" emt_status emt_prefactor(emt_ctx* c) {
   p.br = c->d_br;
   p.le = c->d_le;
   p.sw = c->d_sw;
+  p.lc_idx = c->d_lc_idx;
+  p.str_slot = c->d_str_slot;
   p.ginv = c->d_ginv;
   p.ginv_lo = c->d_ginv_lo;
   p.work_g = d_wg;
@@ -635,6 +670,7 @@ extern "C" emt_status emt_step_n(emt_ctx* c, int64_t n_steps, void* stream) {
   p.n_sub = c->n_sub;
   p.lim = c->lim;
   p.lim.n = std::max(p.lim.n, 1);
+  p.lim.nc = std::max(p.lim.nc, 1);
   p.sub = c->d_sub;
   p.ep = c->d_ep;
   p.ginv = c->d_ginv;
@@ -646,6 +682,7 @@ extern "C" emt_status emt_step_n(emt_ctx* c, int64_t n_steps, void* stream) {
   p.ent = c->d_ent;
   p.il_node = c->d_il_node;
   p.il_cnt = c->d_il_cnt;
+  p.str_slot = c->d_str_slot;
   p.le = c->d_le;
   p.ring = c->d_ring;
   p.src_global = c->d_src_global;
@@ -790,6 +827,7 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "kernel_launches") *value = c->launches;
   else if (k == "n_branches") *value = (int64_t)c->branches.size();
   else if (k == "n_line_ends") *value = (int64_t)c->line_ends.size();
+  else if (k == "n_strong_branches") *value = (int64_t)c->str_slot.size();
   else if (k == "smem_bytes") *value = (int64_t)forward_smem_bytes(c->lim);
   else return EMT_EINVAL;
   return EMT_OK;

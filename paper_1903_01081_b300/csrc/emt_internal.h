@@ -75,20 +75,31 @@ struct SubDev {
   int32_t nb_off, n_nb;        // neighbour subsystems (reported by emt_get_info)
   int32_t ep_off, n_ep;        // switch epochs
   int32_t il_off, n_il;        // injection lanes (4 entries each; il_node / il_cnt per lane)
+  int32_t str_off, n_str;      // strong L/C branches (L/C slots in str_slot)
   int32_t q;                   // column blocks per row in the matvec
   int32_t pad;
 };
 
-// Switch epoch of a subsystem: state holding from step `start` on.
+// Strong L/C branches.  When a branch's conductance dwarfs the rest of
+// what its two end nodes see, its history current h enters the injections
+// of k and m with opposite signs and G^-1 i cancels two nearly equal large
+// products.  Such a branch is kept out of the injections; its effect
+// -(G^-1[:,k] - G^-1[:,m]) h is applied through an extra matvec column whose
+// entries are formed without cancellation when G^-1 is built.  Criterion:
+// g_b >= kStrongRatio * min(G_kk - g_b, G_mm - g_b).
+constexpr double kStrongRatio = 3.0;
+
+// Switch epoch of a subsystem: state holding from step `start` on.  Its
+// solve matrix is n x nc, nc = n + n_str: [G^-1 | strong-branch columns].
 struct EpochDev {
   int64_t start;
-  int64_t ginv_off;      // offset of this epoch's n x n G^-1
+  int64_t ginv_off;      // offset of this epoch's n x nc solve matrix
   int32_t sw_off, n_sw;  // closed switches (SwitchDev list)
 };
 
 // Per-launch upper bounds that size the forward kernel's shared memory.
 struct FwdLimits {
-  int32_t n, q, lc, sb, le, src, il;
+  int32_t n, nc, q, lc, sb, le, src, il, str;
 };
 
 struct FwdParams {
@@ -105,6 +116,7 @@ struct FwdParams {
   const int32_t* ent;          // injection entries, 4 per injection lane
   const int32_t* il_node;      // node of each injection lane (-1: padding)
   const int32_t* il_cnt;       // lanes of the node on its first lane, else 0
+  const int32_t* str_slot;     // L/C slot of each strong branch
   const LineEndDev* le;
   unsigned long long* ring;    // [slots][2] tagged words
   const int32_t* src_global;   // global source id per local source slot
@@ -131,6 +143,8 @@ struct PrefParams {
   const BranchDev* br;
   const LineEndDev* le;
   const SwitchDev* sw;
+  const int32_t* lc_idx;       // branch index per L/C slot
+  const int32_t* str_slot;     // L/C slot of each strong branch
   double* ginv;                // X_hi: G^-1 rounded to double
   float* ginv_lo;              // X_lo: G^-1 - X_hi in single precision
   double* work_g;              // copy of G per matrix, at ep.ginv_off

@@ -188,15 +188,16 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
     Rw[idx] = __dadd_rn(hi, lo);
   }
   __syncthreads();
+  const int nc = n + S.n_str;
   double* out = P.ginv + E.ginv_off;
   for (int idx = tid; idx < n * n; idx += T) {
     const int i = idx / n, j = idx - i * n;
     double c = 0.0;
     for (int k = 0; k < n; ++k) c = fma(A[i * n + k], Rw[k * n + j], c);
-    out[idx] = A[idx] + c;
+    out[i * nc + j] = A[idx] + c;
   }
   __syncthreads();
-  for (int idx = tid; idx < n * n; idx += T) A[idx] = out[idx];
+  for (int idx = tid; idx < n * n; idx += T) A[idx] = out[(idx / n) * nc + idx % n];
   __syncthreads();
   for (int idx = tid; idx < n * n; idx += T) {
     const int i = idx / n, j = idx - i * n;
@@ -210,7 +211,21 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
     const int i = idx / n, j = idx - i * n;
     double c = 0.0;
     for (int k = 0; k < n; ++k) c = fma(A[i * n + k], Rw[k * n + j], c);
-    out_lo[idx] = (float)c;
+    out_lo[i * nc + j] = (float)c;
+  }
+  __syncthreads();
+  // strong-branch columns (G^-1[:,k] - G^-1[:,m]) from X_hi + X_lo with
+  // error-free differences, split again into double + single remainder
+  for (int idx = tid; idx < n * S.n_str; idx += T) {
+    const int i = idx / S.n_str, t = idx - i * S.n_str;
+    const BranchDev b = P.br[P.lc_idx[S.lc_off + P.str_slot[S.str_off + t]]];
+    double d1, e1;
+    two_sum(out[i * nc + b.k], -out[i * nc + b.m], d1, e1);
+    const double rest = e1 + ((double)out_lo[i * nc + b.k] - (double)out_lo[i * nc + b.m]);
+    double s, e;
+    two_sum(d1, rest, s, e);
+    out[i * nc + n + t] = s;
+    out_lo[i * nc + n + t] = (float)e;
   }
   if (tid == 0) P.status[mi] = 0;
 }
@@ -280,7 +295,7 @@ constexpr int kItemThreads = kFwdThreads - 32;
 struct FwdSmem {
   size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar;   // 8-byte
   size_t gilo, ivf;                                                 // float
-  size_t lck, lcm, lckind, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg;   // int
+  size_t lck, lcm, lckind, lcstr, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg;   // int
   size_t bytes;
 };
 
@@ -289,10 +304,10 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   size_t o = 0;
   auto d = [&](size_t count) { size_t r = o; o += count * 8; return r; };
   auto w = [&](size_t count) { size_t r = o; o += count * 4; return r; };
-  const size_t ldg = (size_t)(L.n | 1);
+  const size_t ldg = (size_t)(L.nc | 1);
   s.gi = d((size_t)L.n * ldg);
   s.part = d((size_t)L.n * L.q);
-  s.iv = d(L.n);
+  s.iv = d(L.nc);
   s.vv = d(L.n);
   s.inp = d((size_t)L.lc + L.sb + 2 * (size_t)L.le + 1);
   s.vs = d(2 * (size_t)L.src);
@@ -302,7 +317,8 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.leown = d(L.le);
   s.lefar = d(L.le);
   s.gilo = w((size_t)L.n * ldg);
-  s.ivf = w(L.n);
+  s.ivf = w(L.nc);
+  s.lcstr = w(L.lc);
   s.lck = w(L.lc);
   s.lcm = w(L.lc);
   s.lckind = w(L.lc);
@@ -382,6 +398,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   int* lck = reinterpret_cast<int*>(smem_raw + L.lck);
   int* lcm = reinterpret_cast<int*>(smem_raw + L.lcm);
   int* lckind = reinterpret_cast<int*>(smem_raw + L.lckind);
+  int* lcstr = reinterpret_cast<int*>(smem_raw + L.lcstr);
   int* sbsrc = reinterpret_cast<int*>(smem_raw + L.sbsrc);
   int* lenode = reinterpret_cast<int*>(smem_raw + L.lenode);
   int* ledepth = reinterpret_cast<int*>(smem_raw + L.ledepth);
@@ -396,8 +413,8 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   const int sidx = blockIdx.x;
   const SubDev S = P.sub[sidx];
   const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int n = S.n, Q = S.q, ldg = n | 1;
-  const int blk = (n + Q - 1) / Q;   // columns per matvec task
+  const int n = S.n, Q = S.q, n_str = S.n_str, nc = n + n_str, ldg = nc | 1;
+  const int blk = (nc + Q - 1) / Q;   // columns per matvec task
   const int n_lc = S.n_lc, n_sb = S.n_sb, n_le = S.n_le, n_il = S.n_il;
   const int ie_base = n_lc + n_sb;
   const int zero_slot = ie_base + 2 * n_le;
@@ -418,6 +435,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     lck[x] = b.k;
     lcm[x] = b.m;
     lckind[x] = b.kind;
+    lcstr[x] = -1;
   }
   for (int x = tid; x < n_sb; x += T) {
     const BranchDev b = P.br[P.sb_idx[S.sb_off + x]];
@@ -453,14 +471,20 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   long long next_ep_start = (ep + 1 < S.n_ep) ? P.ep[S.ep_off + ep + 1].start : LLONG_MAX;
   {
     const int64_t off = P.ep[S.ep_off + ep].ginv_off;
-    for (int i = tid; i < n * n; i += T) {
-      const int r = i / n, c = i - r * n;
+    for (int i = tid; i < n * nc; i += T) {
+      const int r = i / nc, c = i - r * nc;
       gi[r * ldg + c] = P.ginv[off + i];
       gilo[r * ldg + c] = P.ginv_lo[off + i];
     }
   }
   __syncthreads();
   for (int x = tid; x < n_sb; x += T) inp[n_lc + x] = sbg[x] * vs[(P.n0 & 1) * src_vs + sbsrc[x]];
+  for (int t = tid; t < n_str; t += T) {
+    const int x = P.str_slot[S.str_off + t];
+    lcstr[x] = t;
+    iv[n + t] = -inp[x];
+    ivf[n + t] = (float)(-inp[x]);
+  }
   if (warp == kPollWarp && n_le > 0) {
     const bool ok = collect_lines(P, n_le, (unsigned)P.n0, lane, sidx, leown, ledepth, rslot,
                                   inp + ie_base + (int)(P.n0 & 1) * n_le);
@@ -481,8 +505,8 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       while (ep + 1 < S.n_ep && P.ep[S.ep_off + ep + 1].start <= step) ++ep;
       next_ep_start = (ep + 1 < S.n_ep) ? P.ep[S.ep_off + ep + 1].start : LLONG_MAX;
       const int64_t off = P.ep[S.ep_off + ep].ginv_off;
-      for (int i = tid; i < n * n; i += T) {
-        const int r = i / n, c = i - r * n;
+      for (int i = tid; i < n * nc; i += T) {
+        const int r = i / nc, c = i - r * nc;
         gi[r * ldg + c] = P.ginv[off + i];
         gilo[r * ldg + c] = P.ginv_lo[off + i];
       }
@@ -528,7 +552,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       const int r = task / Q, q = task - r * Q;
       const double* row = gi + r * ldg;
       const float* rowl = gilo + r * ldg;
-      const int j1 = min(n, (q + 1) * blk);
+      const int j1 = min(nc, (q + 1) * blk);
       double a = 0.0;
       float b = 0.f;
       for (int j = q * blk; j < j1; ++j) {
@@ -572,7 +596,13 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
           const double vk = k >= 0 ? vv[k] : (k == -1 ? 0.0 : vsc[-2 - k]);
           const double vm = m >= 0 ? vv[m] : (m == -1 ? 0.0 : vsc[-2 - m]);
           const double vb = vk - vm;
-          inp[it] = lckind[it] == 1 ? fma(lce[it], vb, inp[it]) : fma(lce[it], vb, -inp[it]);
+          const double hn = lckind[it] == 1 ? fma(lce[it], vb, inp[it]) : fma(lce[it], vb, -inp[it]);
+          inp[it] = hn;
+          const int t = lcstr[it];
+          if (t >= 0) {   // strong branch: its current drives the extra matvec column
+            iv[n + t] = -hn;
+            ivf[n + t] = (float)(-hn);
+          }
         } else if (it >= it_le && it < it_le + n_le) {
           const int e = it - it_le;
           if (writes_lines)
