@@ -24,6 +24,10 @@ thread_local std::string g_build_error;
 
 const double kTwoPi = 2.0 * 3.14159265358979323846;
 
+// Shared memory given to the solve matrix [G^-1 | strong columns] of one
+// subsystem (double + single-precision parts).
+const double kSolveSmemBytes = 150.0 * 1024;
+
 // Source-voltage table budget per chunk of a launch (doubles): 32 MiB.
 const int64_t kSourceTableDoubles = 4 << 20;
 
@@ -399,14 +403,26 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     }
     for (int e = sd.le_off; e < sd.le_off + sd.n_le; ++e) diag[c->line_ends[e].node] += c->line_ends[e].y;
     sd.str_off = (int)c->str_slot.size();
+    std::vector<std::pair<double, int>> cand;   // (ratio, branch), strongest first
     for (int b = sd.br_off; b < sd.br_off + sd.n_br; ++b) {
       const BranchDev& x = c->branches[b];
       if (x.kind == 0 || x.k < 0 || x.m < 0) continue;
       const double g = companion(x);
-      if (g >= kStrongRatio * std::min(diag[x.k] - g, diag[x.m] - g)) {
-        strong[b] = 1;
-        c->str_slot.push_back(lc_slot_of[b]);
-      }
+      const double rest = std::min(diag[x.k] - g, diag[x.m] - g);
+      if (g >= kStrongRatio * rest) cand.push_back({rest > 0.0 ? g / rest : 1e300, b});
+    }
+    std::sort(cand.begin(), cand.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+      return a.first > b.first || (a.first == b.first && a.second < b.second);
+    });
+    // the n x (n + n_str) solve matrix (double + float) must fit on chip
+    const int max_nc = std::max(sd.n, (int)(kSolveSmemBytes / (12.0 * std::max(sd.n, 1))) - 1);
+    const int keep = std::min((int)cand.size(), max_nc - sd.n);
+    std::vector<int> chosen;
+    for (int i = 0; i < keep; ++i) chosen.push_back(cand[i].second);
+    std::sort(chosen.begin(), chosen.end());
+    for (int b : chosen) {
+      strong[b] = 1;
+      c->str_slot.push_back(lc_slot_of[b]);
     }
     sd.n_str = (int)c->str_slot.size() - sd.str_off;
     c->lim.str = std::max(c->lim.str, sd.n_str);
