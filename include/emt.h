@@ -122,6 +122,27 @@ emt_status emt_build_network(const emt_network_desc* desc, const emt_scenario_de
  * ESINGULAR names the subsystem. */
 emt_status emt_prefactor(emt_ctx* ctx);
 
+/* The same computation as emt_prefactor, without any device allocation: the
+ * workspace emt_prefactor obtains from cudaMalloc (matrix lists, per-matrix
+ * status, a copy of G and the Newton residual for every matrix) lives in a
+ * fixed device array built into the library instead.  It is for callers
+ * that must not allocate device memory at this point -- while recording a
+ * CUDA graph, in a service that reserves all device memory up front, or in
+ * a loop that cannot accept cudaMalloc's implicit synchronisation or its
+ * failure -- having built the context beforehand.  The paper has no
+ * counterpart; it is a deployment convenience.
+ *   Limit: at most 16383 matrices (subsystems x switch states) and 491,520
+ *   solve-matrix entries (the "solve matrix" is n x (n + strong columns) per
+ *   matrix); larger networks get EINVAL with a message (use emt_prefactor).
+ *   The fixed array (about 7.7 MiB) is held on every device that loads the
+ *   library until the process exits.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   The context's device must be current.  Runs on `cuda_stream` and
+ *   synchronises it.  All calls share the one array: calls that overlap on
+ *   the GPU (other threads, other streams) race and must be serialised. */
+emt_status emt_prefactor_noalloc(emt_ctx* ctx, void* cuda_stream);
+
 /* Choose the recorded node voltages ("waveform channels", Sec. II-A):
  * channels = node ids (NULL = all nodes in order), every `decim`-th step
  * (steps decim, 2 decim, ...), room for `max_rows` recorded steps per

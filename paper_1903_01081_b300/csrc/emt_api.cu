@@ -864,3 +864,110 @@ extern "C" void emt_destroy(emt_ctx* c) {
   c->allocations.clear();
   delete c;
 }
+
+// ------------------------------------------------------------------ no-alloc prefactor
+//
+// emt_prefactor allocates temporary device buffers (the matrix lists, a
+// status word per matrix, and two n x nc workspaces per matrix: a copy of G
+// and the Newton residual).  Callers that must not allocate device memory
+// while they run -- code recording a CUDA graph, services that reserve all
+// device memory up front, loops that cannot afford cudaMalloc's implicit
+// synchronisation or its failure -- use emt_prefactor_noalloc instead,
+// which keeps that workspace in the fixed array below.
+
+namespace {
+
+constexpr size_t kNoAllocMaxMats = 16384;                    // matrices (subsystem x switch state)
+constexpr size_t kNoAllocMaxWorkDoubles = 480 * 1024;        // per workspace (G copy / residual)
+constexpr size_t kNoAllocScratchBytes =
+    3 * kNoAllocMaxMats * sizeof(int32_t) + 2 * kNoAllocMaxWorkDoubles * sizeof(double) + 256;
+
+// Shared by every call on a device; holds the last call's contents.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch per device, found on first use.
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Matrix m is epoch m: epochs are stored subsystem by subsystem.
+__global__ void noalloc_mat_lists(const SubDev* sub, int n_sub, int32_t* mat_sub, int32_t* mat_ep) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_sub) return;
+  for (int k = 0; k < sub[s].n_ep; ++k) {
+    mat_sub[sub[s].ep_off + k] = s;
+    mat_ep[sub[s].ep_off + k] = sub[s].ep_off + k;
+  }
+}
+
+// first[0] = 1 + index of the first singular matrix, or 0 if none
+__global__ void noalloc_first_singular(const int32_t* status, int n_mats, int32_t* first) {
+  for (int m = threadIdx.x; m < n_mats; m += blockDim.x)
+    if (status[m] != 0) atomicMin(first, m + 1);
+}
+
+}  // namespace
+
+extern "C" emt_status emt_prefactor_noalloc(emt_ctx* c, void* stream) {
+  if (!c) return EMT_EINVAL;
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_prefactor_noalloc");
+  if (dev != c->device) return c->fail(EMT_EINVAL, "make the context's device current first");
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return c->fail(EMT_EINVAL, "device index beyond the supported range");
+  const size_t n_mats = c->epochs.size();
+  if (n_mats + 1 > kNoAllocMaxMats || (size_t)c->ginv_len > kNoAllocMaxWorkDoubles)
+    return c->fail(EMT_EINVAL, "network too large for emt_prefactor_noalloc's fixed workspace "
+                               "(at most 16383 matrices and 491520 solve-matrix entries); use emt_prefactor");
+  if (!g_noalloc_ptr[dev]) {   // one-time set-up on this device
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return c->cuda_fail(e, "emt_prefactor_noalloc: cudaGetSymbolAddress");
+    g_noalloc_ptr[dev] = p;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  int32_t* mat_sub = reinterpret_cast<int32_t*>(base);
+  int32_t* mat_ep = mat_sub + kNoAllocMaxMats;
+  int32_t* status = mat_ep + kNoAllocMaxMats;      // status[0 .. n_mats), then the "first" word
+  double* work_g = reinterpret_cast<double*>(base + 3 * kNoAllocMaxMats * sizeof(int32_t));
+  double* work_r = work_g + kNoAllocMaxWorkDoubles;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n_mats == 0) {
+    c->prefactored = true;
+    return EMT_OK;
+  }
+  e = cudaMemsetAsync(status, 0, (n_mats + 1) * sizeof(int32_t), st);
+  if (e == cudaSuccess) {
+    noalloc_mat_lists<<<(c->n_sub + 127) / 128, 128, 0, st>>>(c->d_sub, c->n_sub, mat_sub, mat_ep);
+    e = cudaGetLastError();
+  }
+  PrefParams p{};
+  p.n_mats = (int32_t)n_mats;
+  p.mat_sub = mat_sub;
+  p.mat_ep = mat_ep;
+  p.sub = c->d_sub;
+  p.ep = c->d_ep;
+  p.br = c->d_br;
+  p.le = c->d_le;
+  p.sw = c->d_sw;
+  p.lc_idx = c->d_lc_idx;
+  p.str_slot = c->d_str_slot;
+  p.ginv = c->d_ginv;
+  p.ginv_lo = c->d_ginv_lo;
+  p.work_g = work_g;
+  p.work_r = work_r;
+  p.status = status;
+  if (e == cudaSuccess) e = launch_prefactor(p, std::max(c->lim.n, 1), st);
+  int32_t* first = status + n_mats;
+  if (e == cudaSuccess) e = cudaMemsetAsync(first, 0x7f, sizeof(int32_t), st);
+  if (e == cudaSuccess) {
+    noalloc_first_singular<<<1, 256, 0, st>>>(status, (int)n_mats, first);
+    e = cudaGetLastError();
+  }
+  int32_t h_first = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_first, first, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_prefactor_noalloc");
+  if (h_first != 0x7f7f7f7f) return c->fail(EMT_ESINGULAR, "a subsystem conductance matrix is singular");
+  c->prefactored = true;
+  return EMT_OK;
+}

@@ -22,7 +22,7 @@ _STATUS = {0: "EMT_OK", 1: "EMT_EINVAL", 2: "EMT_ESINGULAR", 3: "EMT_ENOMEM", 4:
 # every function include/emt.h declares
 EXPORTS = ("emt_build_network", "emt_prefactor", "emt_set_recording", "emt_step_n", "emt_read_waveforms",
            "emt_reset", "emt_sync", "emt_set_option", "emt_get_info", "emt_get_node_order", "emt_last_error",
-           "emt_destroy")
+           "emt_destroy", "emt_prefactor_noalloc")
 
 
 class EmtError(RuntimeError):
@@ -77,6 +77,7 @@ def load_library(build_if_needed: bool = True):
     sig = {
         "emt_build_network": [P, P, P],
         "emt_prefactor": [P],
+        "emt_prefactor_noalloc": [P, P],
         "emt_set_recording": [P, P, I64, I32, I64],
         "emt_step_n": [P, I64, P],
         "emt_read_waveforms": [P, P, I64, I64, I64, I64, I64, P, I32],
@@ -192,6 +193,11 @@ def emt_build_network(net, scenarios=None) -> Ctx:
 
 def emt_prefactor(ctx: Ctx) -> None:
     _check(ctx, load_library().emt_prefactor(ctx.handle))
+
+
+def emt_prefactor_noalloc(ctx: Ctx, stream=None) -> None:
+    """emt_prefactor without device allocation (fixed workspace; see include/emt.h)."""
+    _check(ctx, load_library().emt_prefactor_noalloc(ctx.handle, _stream_handle(stream)))
 
 
 def emt_set_recording(ctx: Ctx, channels: Optional[Sequence[int]] = None, decim: int = 1, max_rows: int = 0) -> None:
