@@ -8,6 +8,10 @@ benchmark "step" is one full run of those 50,000 time steps from the
 de-energised state (emt_step_n), i.e. one pass of the whole hot path.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--time-steps T] [--skip-extras]
+
+--time-steps shortens each run (for profiling small cases); --skip-extras
+leaves out the end-to-end leg, the CPU baseline and the parity check.
 
 N > 1 runs N independent replicas (the single-network path does not shard;
 see the design doc), launched by torch.distributed.run.  `--impl reference`
@@ -160,6 +164,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     net = g.large_scale()
     n = net.n_nodes
+    N_STEPS = args.time_steps
 
     def barrier():
         if world > 1:
@@ -198,10 +203,17 @@ def run_ours(args):
     value = world * n * N_STEPS * args.steps / t_max
 
     # parity of the timed configuration against the oracle on sampled steps
-    w = sim.waveforms(n_rows=2000)[:, 0, :]
+    w = sim.waveforms(n_rows=min(2000, N_STEPS))[:, 0, :]
     flops = algorithmic_flops_per_step(net, sim) * N_STEPS
     n_sub = sim.info("n_subsystems")
     sim.close()
+
+    if args.skip_extras:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                              "ms_per_step": 1e3 * t_max / args.steps, "time_steps": N_STEPS,
+                              "note": "profiling run: extras skipped"}), flush=True)
+        return 0
 
     # ---------------- end to end through the C ABI with host buffers
     e2e_times = []
@@ -231,7 +243,7 @@ def run_ours(args):
 
     if rank == 0:
         import oracle
-        ref = oracle.simulate(net, 2000)
+        ref = oracle.simulate(net, min(2000, N_STEPS))
         parity = float(np.max(np.abs(w - ref)) / np.max(np.abs(ref)))
         per_launch_s = t_max / args.steps
         achieved = flops / per_launch_s / 1e9
@@ -274,6 +286,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--time-steps", type=int, default=N_STEPS)
+    ap.add_argument("--skip-extras", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
