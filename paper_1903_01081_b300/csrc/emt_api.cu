@@ -8,6 +8,7 @@
 #include <map>
 #include <numeric>
 #include <set>
+#include <array>
 #include <string>
 #include <vector>
 
@@ -97,6 +98,40 @@ struct emt_ctx {
   unsigned long long wait_budget_ns = 2000000000ull;
   int32_t hold_sub = -1;
   int64_t launches = 0;
+
+  // multi-scenario mode (emt_build_network with a scenario set)
+  bool batched = false;
+  int64_t S = 1;
+  int S_t = 1;
+  int max_nc = 1;
+  int64_t n_base_epochs = 0;
+  std::vector<int32_t> node_l0, node_nl;
+  std::vector<int64_t> le_bring, le_bfar;
+  int64_t bring_len = 0;
+  std::vector<double> bsrc_amp, bsrc_phase;            // [S][n_sources]
+  std::vector<uint8_t> keep_lc, keep_sb, keep_le;      // [slot][S], empty if nothing is removed
+  std::vector<int64_t> msel_ptr, msel_start;
+  std::vector<int32_t> msel_mat;
+  std::vector<int32_t> var_sub;                        // subsystem of each variant matrix
+  std::vector<int32_t> rm_ptr_br, rm_br, rm_ptr_le, rm_le;
+  int64_t* d_msel_ptr = nullptr;
+  int64_t* d_msel_start = nullptr;
+  int32_t* d_msel_mat = nullptr;
+  int32_t* d_node_l0 = nullptr;
+  int32_t* d_node_nl = nullptr;
+  int64_t* d_le_bring = nullptr;
+  int64_t* d_le_bfar = nullptr;
+  double* d_bsrc_amp = nullptr;
+  double* d_bsrc_phase = nullptr;
+  uint8_t* d_keep_lc = nullptr;
+  uint8_t* d_keep_sb = nullptr;
+  uint8_t* d_keep_le = nullptr;
+  double* d_bh = nullptr;
+  double* d_bring = nullptr;
+  int32_t* d_rm_ptr_br = nullptr;
+  int32_t* d_rm_br = nullptr;
+  int32_t* d_rm_ptr_le = nullptr;
+  int32_t* d_rm_le = nullptr;
 
   std::vector<void*> allocations;
 
@@ -191,7 +226,211 @@ int uf_find(std::vector<int>& p, int x) {
 
 bool switch_closed(int64_t on, int64_t off, int64_t n) { return on >= 0 && n >= on && (off < 0 || n < off); }
 
+std::string validate_scenarios(const emt_network_desc* d, const emt_scenario_desc* sc) {
+  if (sc->n_scenarios < 1 || sc->n_scenarios > (1 << 24)) return "n_scenarios must be in 1 .. 2^24";
+  const int64_t S = sc->n_scenarios;
+  for (int64_t i = 0; sc->src_amp && i < S * d->n_sources; ++i)
+    if (!std::isfinite(sc->src_amp[i])) return "scenario source amplitude is not finite";
+  for (int64_t i = 0; sc->src_phase && i < S * d->n_sources; ++i)
+    if (!std::isfinite(sc->src_phase[i])) return "scenario source phase is not finite";
+  auto csr = [&](const int64_t* ptr, const void* data, const char* what) -> std::string {
+    if (!ptr) return "";
+    if (!data && ptr[S] > 0) return std::string(what) + " list is NULL";
+    if (ptr[0] != 0) return std::string(what) + " pointer must start at 0";
+    for (int64_t s = 0; s < S; ++s)
+      if (ptr[s + 1] < ptr[s]) return std::string(what) + " pointer must not decrease";
+    return "";
+  };
+  std::string m = csr(sc->rm_branch_ptr, sc->rm_branch, "removed-branch");
+  if (m.empty()) m = csr(sc->rm_line_ptr, sc->rm_line, "removed-line");
+  if (m.empty()) m = csr(sc->sw_ptr, sc->sw_k, "scenario-switch");
+  if (!m.empty()) return m;
+  if (sc->rm_branch_ptr)
+    for (int64_t i = 0; i < sc->rm_branch_ptr[S]; ++i)
+      if (sc->rm_branch[i] < 0 || sc->rm_branch[i] >= d->n_branches) return "removed branch out of range";
+  if (sc->rm_line_ptr)
+    for (int64_t i = 0; i < sc->rm_line_ptr[S]; ++i)
+      if (sc->rm_line[i] < 0 || sc->rm_line[i] >= d->n_lines) return "removed line out of range";
+  if (sc->sw_ptr) {
+    if (!sc->sw_m || !sc->sw_r || !sc->sw_close_step || !sc->sw_open_step) return "scenario-switch array is NULL";
+    for (int64_t w = 0; w < sc->sw_ptr[S]; ++w) {
+      const int32_t k = sc->sw_k[w], m2 = sc->sw_m[w];
+      if (k < -1 || m2 < -1 || k >= d->n_nodes || m2 >= d->n_nodes || k == m2 || (k < 0 && m2 < 0))
+        return "scenario switch " + std::to_string(w) + ": ends must be unknown nodes or ground";
+      if (!finite_pos(sc->sw_r[w])) return "scenario switch " + std::to_string(w) + ": resistance must be > 0";
+    }
+  }
+  return "";
+}
+
 }  // namespace
+
+// ------------------------------------------------------------------ scenarios
+
+// Multi-scenario set: per (scenario, subsystem) the switch epochs and the
+// solve-matrix variant of each (deduplicated by content: subsystem, removed
+// branches and line ends, closed switches with their conductances), the
+// removal masks, per-scenario sources and the batched line rings.
+std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_scenario_desc* sc,
+                            const std::vector<int>& local, const std::vector<int32_t>& new_of_orig,
+                            const std::vector<int64_t>& le_of_end, const std::vector<int32_t>& lc_slot_of,
+                            const std::vector<int32_t>& sb_slot_of) {
+  c->batched = true;
+  const int64_t S = sc->n_scenarios;
+  c->S = S;
+  const int nsub = c->n_sub;
+  const int64_t nsrc = d->n_sources;
+  c->bsrc_amp.resize(S * nsrc);
+  c->bsrc_phase.resize(S * nsrc);
+  for (int64_t q = 0; q < S; ++q)
+    for (int64_t j = 0; j < nsrc; ++j) {
+      c->bsrc_amp[q * nsrc + j] = sc->src_amp ? sc->src_amp[q * nsrc + j] : d->src_amp[j];
+      c->bsrc_phase[q * nsrc + j] = sc->src_phase ? sc->src_phase[q * nsrc + j] : d->src_phase[j];
+    }
+  std::vector<int> sub_of_br(c->branches.size()), sub_of_le(c->line_ends.size());
+  std::vector<int64_t> end_of_le(c->line_ends.size());
+  for (int q = 0; q < nsub; ++q) {
+    const SubDev& sd = c->subs[q];
+    for (int b = sd.br_off; b < sd.br_off + sd.n_br; ++b) sub_of_br[b] = q;
+    for (int e = sd.le_off; e < sd.le_off + sd.n_le; ++e) sub_of_le[e] = q;
+  }
+  for (int64_t e = 0; e < (int64_t)le_of_end.size(); ++e) end_of_le[le_of_end[e]] = e;
+  const bool any_rm = (sc->rm_branch_ptr && sc->rm_branch_ptr[S] > 0) || (sc->rm_line_ptr && sc->rm_line_ptr[S] > 0);
+  if (any_rm) {
+    c->keep_lc.assign((size_t)c->lc_idx.size() * S, 1);
+    c->keep_sb.assign((size_t)c->sb_idx.size() * S, 1);
+    c->keep_le.assign((size_t)c->line_ends.size() * S, 1);
+  }
+  std::vector<std::vector<int64_t>> base_sw_of(nsub);
+  for (int64_t w = 0; w < d->n_switches; ++w) {
+    const int a = d->sw_k[w] >= 0 ? d->sw_k[w] : d->sw_m[w];
+    base_sw_of[c->sub_of_node[a]].push_back(w);
+  }
+  struct Sw {
+    int32_t k, m;
+    double r;
+    int64_t on, off;
+  };
+  std::map<std::vector<int64_t>, int> variants;
+  c->n_base_epochs = (int64_t)c->epochs.size();
+  int64_t goff = c->ginv_len;
+  c->rm_ptr_br.assign(1, 0);
+  c->rm_ptr_le.assign(1, 0);
+  c->msel_ptr.assign(1, 0);
+  std::vector<std::vector<int32_t>> rb(nsub), rl(nsub);
+  std::vector<std::vector<Sw>> ssw(nsub);
+  for (int64_t q = 0; q < S; ++q) {
+    for (int k = 0; k < nsub; ++k) {
+      rb[k].clear();
+      rl[k].clear();
+      ssw[k].clear();
+    }
+    if (sc->rm_branch_ptr)
+      for (int64_t i = sc->rm_branch_ptr[q]; i < sc->rm_branch_ptr[q + 1]; ++i) {
+        const int32_t nb = new_of_orig[sc->rm_branch[i]];
+        const int k = sub_of_br[nb];
+        rb[k].push_back(nb);
+        if (lc_slot_of[nb] >= 0) c->keep_lc[(size_t)(c->subs[k].lc_off + lc_slot_of[nb]) * S + q] = 0;
+        if (sb_slot_of[nb] >= 0) c->keep_sb[(size_t)(c->subs[k].sb_off + sb_slot_of[nb]) * S + q] = 0;
+      }
+    if (sc->rm_line_ptr)
+      for (int64_t i = sc->rm_line_ptr[q]; i < sc->rm_line_ptr[q + 1]; ++i)
+        for (int end = 0; end < 2; ++end) {
+          const int64_t ge = le_of_end[2 * (int64_t)sc->rm_line[i] + end];
+          rl[sub_of_le[ge]].push_back((int32_t)ge);
+          c->keep_le[(size_t)ge * S + q] = 0;
+        }
+    for (int k = 0; k < nsub; ++k)
+      for (int64_t w : base_sw_of[k])
+        ssw[k].push_back({d->sw_k[w], d->sw_m[w], d->sw_r[w], d->sw_close_step[w], d->sw_open_step[w]});
+    if (sc->sw_ptr)
+      for (int64_t w = sc->sw_ptr[q]; w < sc->sw_ptr[q + 1]; ++w) {
+        const int a = sc->sw_k[w] >= 0 ? sc->sw_k[w] : sc->sw_m[w];
+        ssw[c->sub_of_node[a]].push_back({sc->sw_k[w], sc->sw_m[w], sc->sw_r[w], sc->sw_close_step[w], sc->sw_open_step[w]});
+      }
+    for (int k = 0; k < nsub; ++k) {
+      const SubDev& sd = c->subs[k];
+      std::sort(rb[k].begin(), rb[k].end());
+      std::sort(rl[k].begin(), rl[k].end());
+      std::vector<int64_t> events;
+      for (const Sw& w : ssw[k]) {
+        if (w.on >= 0) events.push_back(w.on);
+        if (w.off >= 0) events.push_back(w.off);
+      }
+      std::sort(events.begin(), events.end());
+      events.erase(std::unique(events.begin(), events.end()), events.end());
+      std::vector<std::pair<int64_t, int64_t>> eps;
+      eps.push_back({LLONG_MIN, events.empty() ? 1 : events[0] - 1});
+      for (int64_t ev : events) eps.push_back({ev, ev});
+      for (auto& ep : eps) {
+        std::vector<std::array<int64_t, 3>> closed;
+        for (const Sw& w : ssw[k]) {
+          if (!switch_closed(w.on, w.off, ep.second)) continue;
+          const double g = 1.0 / w.r;
+          int64_t gb;
+          std::memcpy(&gb, &g, sizeof(gb));
+          closed.push_back({w.k >= 0 ? local[w.k] : -1, w.m >= 0 ? local[w.m] : -1, gb});
+        }
+        std::sort(closed.begin(), closed.end());
+        std::vector<int64_t> key{k, (int64_t)rb[k].size()};
+        key.insert(key.end(), rb[k].begin(), rb[k].end());
+        key.push_back((int64_t)rl[k].size());
+        key.insert(key.end(), rl[k].begin(), rl[k].end());
+        for (auto& cl : closed) key.insert(key.end(), cl.begin(), cl.end());
+        auto it = variants.find(key);
+        int vid;
+        if (it == variants.end()) {
+          vid = (int)variants.size();
+          variants.emplace(key, vid);
+          EpochDev E{};
+          E.start = 0;
+          E.ginv_off = goff;
+          goff += (int64_t)sd.n * (sd.n + sd.n_str);
+          E.sw_off = (int)c->switches.size();
+          for (auto& cl : closed) {
+            SwitchDev sw{};
+            sw.k = (int32_t)cl[0];
+            sw.m = (int32_t)cl[1];
+            std::memcpy(&sw.g, &cl[2], sizeof(sw.g));
+            c->switches.push_back(sw);
+          }
+          E.n_sw = (int)closed.size();
+          c->epochs.push_back(E);
+          c->var_sub.push_back(k);
+          c->rm_br.insert(c->rm_br.end(), rb[k].begin(), rb[k].end());
+          c->rm_ptr_br.push_back((int32_t)c->rm_br.size());
+          c->rm_le.insert(c->rm_le.end(), rl[k].begin(), rl[k].end());
+          c->rm_ptr_le.push_back((int32_t)c->rm_le.size());
+        } else {
+          vid = it->second;
+        }
+        c->msel_start.push_back(ep.first);
+        c->msel_mat.push_back((int32_t)(c->n_base_epochs + vid));
+      }
+      c->msel_ptr.push_back((int64_t)c->msel_start.size());
+    }
+  }
+  if (c->epochs.size() > (size_t)INT32_MAX / 2) return "too many scenario matrix variants";
+  c->ginv_len = goff;
+  // batched rings: depth d + 1, scenario-contiguous
+  c->le_bring.assign(c->line_ends.size(), 0);
+  c->le_bfar.assign(c->line_ends.size(), 0);
+  int64_t off = 0;
+  for (size_t e = 0; e < c->line_ends.size(); ++e) {
+    c->le_bring[e] = off;
+    off += c->line_ends[e].d + 1;
+  }
+  for (size_t e = 0; e < c->line_ends.size(); ++e) c->le_bfar[e] = c->le_bring[le_of_end[end_of_le[e] ^ 1]];
+  c->bring_len = off;
+  c->max_nc = 1;
+  for (const SubDev& sd : c->subs) c->max_nc = std::max(c->max_nc, sd.n + sd.n_str);
+  c->S_t = 1;
+  while (c->S_t < 32 && S / (2 * c->S_t) >= 128) c->S_t *= 2;
+  auto smem = [&](int st) { return (double)nsrc * st * 8 + (double)c->max_nc * st * 20; };
+  while (c->S_t > 1 && smem(c->S_t) > 200.0 * 1024) c->S_t /= 2;
+  if (smem(c->S_t) > 200.0 * 1024) return "network too large for the multi-scenario kernel's shared memory";
+  return "";
+}
 
 // ------------------------------------------------------------------ build
 
@@ -206,9 +445,12 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     g_build_error = msg;
     return EMT_EINVAL;
   }
-  if (scen && scen->n_scenarios != 1) {
-    g_build_error = "multi-scenario sets are not supported by emt_build_network yet";
-    return EMT_EINVAL;
+  if (scen) {
+    const std::string sm = validate_scenarios(d, scen);
+    if (!sm.empty()) {
+      g_build_error = sm;
+      return EMT_EINVAL;
+    }
   }
   emt_ctx* c = new emt_ctx();
   auto bail = [&](const std::string& m) {
@@ -235,6 +477,8 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   };
   for (int64_t b = 0; b < d->n_branches; ++b) join(d->br_k[b], d->br_m[b]);
   for (int64_t w = 0; w < d->n_switches; ++w) join(d->sw_k[w], d->sw_m[w]);
+  if (scen && scen->sw_ptr)   // scenario switches may join nodes too
+    for (int64_t w = 0; w < scen->sw_ptr[scen->n_scenarios]; ++w) join(scen->sw_k[w], scen->sw_m[w]);
   c->sub_of_node.assign(N, -1);
   std::vector<int> label(N, -1);
   std::vector<std::vector<int>> nodes_of;
@@ -280,6 +524,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     br_of[c->sub_of_node[a]].push_back(b);
   }
   std::vector<int32_t> lc_slot_of, sb_slot_of;   // new branch index -> local slot
+  std::vector<int32_t> new_of_orig(d->n_branches, -1);
   for (int s = 0; s < S; ++s) {
     SubDev& sd = c->subs[s];
     sd.br_off = (int)c->branches.size();
@@ -305,6 +550,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       x.kind = d->br_kind[b];
       x.value = d->br_value[b];
       const int32_t nb = (int32_t)c->branches.size();
+      new_of_orig[b] = nb;
       lc_slot_of.push_back(-1);
       sb_slot_of.push_back(-1);
       if (x.kind != 0) {
@@ -349,6 +595,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     c->ring_len = off;
   }
   std::vector<std::vector<int64_t>> ends_of(S);
+  std::vector<int64_t> le_of_end(2 * d->n_lines, -1);
   for (int64_t e = 0; e < 2 * d->n_lines; ++e) {
     const int node = (e & 1) ? d->ln_m[e >> 1] : d->ln_k[e >> 1];
     ends_of[c->sub_of_node[node]].push_back(e);
@@ -369,6 +616,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       le.y2 = 2.0 / d->ln_zc[l];
       le.own_ring = ring_off[e];
       le.far_ring = ring_off[e ^ 1];
+      le_of_end[e] = (int64_t)c->line_ends.size();
       c->line_ends.push_back(le);
       const int fs = c->sub_of_node[far_node];
       if (fs != s) {
@@ -525,6 +773,26 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     c->lim.q = std::max(c->lim.q, sd.q);
   }
 
+  // -------- injection-lane range of every internal node
+  c->node_l0.assign(N, 0);
+  c->node_nl.assign(N, 0);
+  for (int s = 0; s < S; ++s) {
+    const SubDev& sd = c->subs[s];
+    for (int l = 0; l < sd.n_il; ++l) {
+      const int cnt = c->il_cnt[sd.il_off + l];
+      if (cnt > 0) {
+        c->node_l0[sd.node_off + c->il_node[sd.il_off + l]] = l;
+        c->node_nl[sd.node_off + c->il_node[sd.il_off + l]] = cnt;
+      }
+    }
+  }
+
+  // -------- multi-scenario set
+  if (scen) {
+    const std::string bm = build_scenarios(c, d, scen, local, new_of_orig, le_of_end, lc_slot_of, sb_slot_of);
+    if (!bm.empty()) return bail(bm);
+  }
+
   // -------- upload
   cudaError_t e = cudaSuccess;
 #define UP(dst, vec) \
@@ -550,6 +818,28 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ginv, (size_t)c->ginv_len);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ginv_lo, (size_t)c->ginv_len);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_err, 4);
+  if (e == cudaSuccess) e = c->upload(&c->d_node_l0, c->node_l0);
+  if (e == cudaSuccess) e = c->upload(&c->d_node_nl, c->node_nl);
+  if (c->batched) {
+    if (e == cudaSuccess) e = c->upload(&c->d_msel_ptr, c->msel_ptr);
+    if (e == cudaSuccess) e = c->upload(&c->d_msel_start, c->msel_start);
+    if (e == cudaSuccess) e = c->upload(&c->d_msel_mat, c->msel_mat);
+    if (e == cudaSuccess) e = c->upload(&c->d_le_bring, c->le_bring);
+    if (e == cudaSuccess) e = c->upload(&c->d_le_bfar, c->le_bfar);
+    if (e == cudaSuccess) e = c->upload(&c->d_bsrc_amp, c->bsrc_amp);
+    if (e == cudaSuccess) e = c->upload(&c->d_bsrc_phase, c->bsrc_phase);
+    if (e == cudaSuccess) e = c->upload(&c->d_rm_ptr_br, c->rm_ptr_br);
+    if (e == cudaSuccess) e = c->upload(&c->d_rm_br, c->rm_br);
+    if (e == cudaSuccess) e = c->upload(&c->d_rm_ptr_le, c->rm_ptr_le);
+    if (e == cudaSuccess) e = c->upload(&c->d_rm_le, c->rm_le);
+    if (!c->keep_lc.empty()) {
+      if (e == cudaSuccess) e = c->upload(&c->d_keep_lc, c->keep_lc);
+      if (e == cudaSuccess) e = c->upload(&c->d_keep_sb, c->keep_sb);
+      if (e == cudaSuccess) e = c->upload(&c->d_keep_le, c->keep_le);
+    }
+    if (e == cudaSuccess) e = c->alloc_zero(&c->d_bh, (size_t)c->n_lc_total * c->S);
+    if (e == cudaSuccess) e = c->alloc_zero(&c->d_bring, (size_t)std::max<int64_t>(c->bring_len, 1) * c->S);
+  }
   if (e == cudaSuccess) e = launch_companion(c->d_br, (int64_t)c->branches.size(), c->dt, nullptr);
   if (e == cudaSuccess) e = launch_ring_init(RingInitParams{c->d_le, (int64_t)c->line_ends.size(), c->d_ring}, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -566,11 +856,18 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
 extern "C" emt_status emt_prefactor(emt_ctx* c) {
   if (!c) return EMT_EINVAL;
   std::vector<int32_t> mat_sub, mat_ep;
-  for (int s = 0; s < c->n_sub; ++s)
-    for (int k = 0; k < c->subs[s].n_ep; ++k) {
-      mat_sub.push_back(s);
-      mat_ep.push_back(c->subs[s].ep_off + k);
+  if (c->batched) {
+    for (size_t v = 0; v < c->var_sub.size(); ++v) {
+      mat_sub.push_back(c->var_sub[v]);
+      mat_ep.push_back((int32_t)(c->n_base_epochs + v));
     }
+  } else {
+    for (int s = 0; s < c->n_sub; ++s)
+      for (int k = 0; k < c->subs[s].n_ep; ++k) {
+        mat_sub.push_back(s);
+        mat_ep.push_back(c->subs[s].ep_off + k);
+      }
+  }
   int32_t *d_ms = nullptr, *d_me = nullptr, *d_status = nullptr;
   double *d_wg = nullptr, *d_wr = nullptr;
   cudaError_t e = c->upload(&d_ms, mat_sub);
@@ -594,6 +891,12 @@ extern "C" emt_status emt_prefactor(emt_ctx* c) {
   p.work_g = d_wg;
   p.work_r = d_wr;
   p.status = d_status;
+  if (c->batched) {
+    p.rm_ptr_br = c->d_rm_ptr_br;
+    p.rm_br = c->d_rm_br;
+    p.rm_ptr_le = c->d_rm_ptr_le;
+    p.rm_le = c->d_rm_le;
+  }
   if (e == cudaSuccess) e = launch_prefactor(p, std::max(c->lim.n, 1), nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   std::vector<int32_t> status(mat_sub.size(), 0);
@@ -647,7 +950,7 @@ extern "C" emt_status emt_set_recording(emt_ctx* c, const int32_t* channels, int
   std::vector<int32_t> pos(c->n_nodes, -1);
   for (int64_t i = 0; i < c->n_nodes; ++i) pos[c->internal_of[i]] = c->rec_col_of[i];
   cudaError_t e = c->upload(&c->d_rec_pos, pos);
-  if (e == cudaSuccess) e = c->alloc_zero(&c->d_rec, (size_t)max_rows * chans.size());
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_rec, (size_t)max_rows * c->S * chans.size());
   if (e != cudaSuccess) {
     c->rec_col_of.assign(c->n_nodes, -1);
     return c->cuda_fail(e, "emt_set_recording");
@@ -667,9 +970,56 @@ extern "C" emt_status emt_step_n(emt_ctx* c, int64_t n_steps, void* stream) {
     return c->fail(EMT_EINVAL, "step counter would exceed 2^31 - 2^21");
   if (!c->rec_channels.empty() && (c->step + n_steps) / c->rec_decim > c->rec_rows)
     return c->fail(EMT_EINVAL, "recording capacity exceeded: raise max_rows in emt_set_recording");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (c->batched) {
+    BatchParams b{};
+    b.n_sub = c->n_sub;
+    b.S = (int32_t)c->S;
+    b.S_t = c->S_t;
+    b.n_sources = (int32_t)c->n_sources;
+    b.max_nc = c->max_nc;
+    b.sub = c->d_sub;
+    b.ep = c->d_ep;
+    b.ginv = c->d_ginv;
+    b.ginv_lo = c->d_ginv_lo;
+    b.msel_ptr = c->d_msel_ptr;
+    b.msel_start = c->d_msel_start;
+    b.msel_mat = c->d_msel_mat;
+    b.br = c->d_br;
+    b.lc_idx = c->d_lc_idx;
+    b.sb_idx = c->d_sb_idx;
+    b.ent = c->d_ent;
+    b.node_l0 = c->d_node_l0;
+    b.node_nl = c->d_node_nl;
+    b.str_slot = c->d_str_slot;
+    b.le = c->d_le;
+    b.le_bring = c->d_le_bring;
+    b.le_bfar = c->d_le_bfar;
+    b.src_global = c->d_src_global;
+    b.src_amp = c->d_bsrc_amp;
+    b.src_phase = c->d_bsrc_phase;
+    b.src_omega = c->d_src_omega;
+    b.keep_lc = c->d_keep_lc;
+    b.keep_sb = c->d_keep_sb;
+    b.keep_le = c->d_keep_le;
+    b.h = c->d_bh;
+    b.ring = c->d_bring;
+    b.rec = c->rec_channels.empty() ? nullptr : c->d_rec;
+    b.rec_pos = c->d_rec_pos;
+    b.rec_rows = c->rec_rows;
+    b.rec_decim = c->rec_decim;
+    b.n_rec = (int32_t)c->rec_channels.size();
+    b.n0 = c->step + 1;
+    b.n_steps = n_steps;
+    b.dt = c->dt;
+    cudaError_t e = launch_batch(b, st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n multi-scenario launch");
+    c->step += n_steps;
+    c->launches += 1;
+    return EMT_OK;
+  }
   if (forward_smem_bytes(c->lim) > 227 * 1024)
     return c->fail(EMT_ERESOURCE, "a subsystem needs more shared memory than one CTA has");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   // source table for one chunk of steps at a time (grow-only buffer)
   const int64_t chunk =
       std::min<int64_t>(n_steps, std::max<int64_t>(1, kSourceTableDoubles / std::max<int64_t>(c->n_sources, 1)));
@@ -761,7 +1111,7 @@ extern "C" emt_status emt_read_waveforms(emt_ctx* c, const int32_t* channels, in
   if (n_ch == 0 || n_rows == 0 || n_scen == 0) return EMT_OK;
   if (!out || !channels) return c->fail(EMT_EINVAL, "NULL buffer");
   if (c->rec_channels.empty()) return c->fail(EMT_ESTATE, "nothing is being recorded");
-  if (scen0 < 0 || scen0 + n_scen > 1) return c->fail(EMT_EINVAL, "scenario range out of bounds");
+  if (scen0 < 0 || scen0 + n_scen > c->S) return c->fail(EMT_EINVAL, "scenario range out of bounds");
   if (step0 < c->rec_decim || step0 % c->rec_decim != 0)
     return c->fail(EMT_EINVAL, "step0 must be a positive multiple of the recording decimation");
   const int64_t row0 = step0 / c->rec_decim - 1;
@@ -787,7 +1137,7 @@ extern "C" emt_status emt_read_waveforms(emt_ctx* c, const int32_t* channels, in
     d_out = static_cast<double*>(p);
   }
   if (e == cudaSuccess)
-    e = launch_gather(c->d_rec, (int32_t)c->rec_channels.size(), 1, d_col, n_ch, row0, n_rows, scen0, n_scen, d_out,
+    e = launch_gather(c->d_rec, (int32_t)c->rec_channels.size(), c->S, d_col, n_ch, row0, n_rows, scen0, n_scen, d_out,
                       nullptr);
   if (e == cudaSuccess && !out_on_device) e = cudaMemcpy(out, d_out, bytes, cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -805,6 +1155,11 @@ extern "C" emt_status emt_reset(emt_ctx* c) {
     e = cudaMemset(c->d_ring, 0, 2 * std::max<int64_t>(c->ring_len, 1) * sizeof(unsigned long long));
   if (e == cudaSuccess) e = launch_ring_init(RingInitParams{c->d_le, (int64_t)c->line_ends.size(), c->d_ring}, nullptr);
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 4 * sizeof(int32_t));
+  if (c->batched) {
+    if (e == cudaSuccess) e = cudaMemset(c->d_bh, 0, std::max<size_t>((size_t)c->n_lc_total * c->S, 1) * sizeof(double));
+    if (e == cudaSuccess)
+      e = cudaMemset(c->d_bring, 0, std::max<size_t>((size_t)std::max<int64_t>(c->bring_len, 1) * c->S, 1) * sizeof(double));
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return c->cuda_fail(e, "emt_reset");
   c->step = 0;
@@ -833,7 +1188,9 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   if (k == "n_subsystems" || k == "n_ctas") *value = c->n_sub;
   else if (k == "step") *value = c->step;
   else if (k == "max_subsystem_nodes") *value = c->lim.n;
-  else if (k == "n_scenarios") *value = 1;
+  else if (k == "n_scenarios") *value = c->S;
+  else if (k == "n_matrix_variants") *value = c->batched ? (int64_t)c->var_sub.size() : (int64_t)c->epochs.size();
+  else if (k == "scenarios_per_cta") *value = c->batched ? c->S_t : 1;
   else if (k == "n_epochs_total") *value = (int64_t)c->epochs.size();
   else if (k == "sum_n2") {
     int64_t s2 = 0;
@@ -913,6 +1270,7 @@ extern "C" emt_status emt_prefactor_noalloc(emt_ctx* c, void* stream) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return c->cuda_fail(e, "emt_prefactor_noalloc");
   if (dev != c->device) return c->fail(EMT_EINVAL, "make the context's device current first");
+  if (c->batched) return c->fail(EMT_EINVAL, "emt_prefactor_noalloc serves single-scenario contexts; use emt_prefactor");
   if (dev < 0 || dev >= kNoAllocMaxDevices) return c->fail(EMT_EINVAL, "device index beyond the supported range");
   const size_t n_mats = c->epochs.size();
   if (n_mats + 1 > kNoAllocMaxMats || (size_t)c->ginv_len > kNoAllocMaxWorkDoubles)

@@ -150,6 +150,56 @@ struct PrefParams {
   double* work_g;              // copy of G per matrix, at ep.ginv_off
   double* work_r;              // residual I - G X per matrix, at ep.ginv_off
   int32_t* status;             // per matrix: 0 ok, 1 singular
+  // optional per-matrix removals (scenario variants): CSR over matrices of
+  // branch indices / line-end indices left out of G (nullptr: none)
+  const int32_t* rm_ptr_br;
+  const int32_t* rm_br;
+  const int32_t* rm_ptr_le;
+  const int32_t* rm_le;
+};
+
+// Multi-scenario run (the paper's multi-scenario strategy, Sec. III-B):
+// one CTA per tile of S_t scenarios runs the whole network for them; a
+// warp's lanes are (item, scenario) with the scenario fastest, so every
+// solve-matrix load is shared by the scenarios of a warp.  Per-scenario
+// state is scenario-contiguous in global memory: h[lc][S], ring[slot][S]
+// (ring depth d+1: one CTA runs a scenario's subsystems in step order).
+struct BatchParams {
+  int32_t n_sub, S, S_t;       // subsystems, scenarios, scenarios per CTA
+  int32_t n_sources;
+  int32_t max_nc;              // largest n + strong columns
+  const SubDev* sub;
+  const EpochDev* ep;          // solve matrices (variants) by index
+  const double* ginv;
+  const float* ginv_lo;
+  const int64_t* msel_ptr;     // [S * n_sub + 1]: selections of (scenario, subsystem)
+  const int64_t* msel_start;   // first step of each selection
+  const int32_t* msel_mat;     // solve matrix (index into ep) of each selection
+  const BranchDev* br;
+  const int32_t* lc_idx;
+  const int32_t* sb_idx;
+  const int32_t* ent;          // injection entries (4 per injection lane)
+  const int32_t* node_l0;      // per internal node: first injection lane
+  const int32_t* node_nl;      // per internal node: number of injection lanes
+  const int32_t* str_slot;
+  const LineEndDev* le;
+  const int64_t* le_bring;     // per line end: first slot of its own ring (depth d+1)
+  const int64_t* le_bfar;      // per line end: first slot of the far end's ring
+  const int32_t* src_global;
+  const double* src_amp;       // [S][n_sources]
+  const double* src_phase;     // [S][n_sources]
+  const double* src_omega;     // [n_sources]
+  const uint8_t* keep_lc;      // [n_lc][S] 1 = present (nullptr: all present)
+  const uint8_t* keep_sb;      // [n_sb][S]
+  const uint8_t* keep_le;      // [n_le][S]
+  double* h;                   // [n_lc][S]
+  double* ring;                // [slots][S]
+  double* rec;                 // [rows][S][n_rec]
+  const int32_t* rec_pos;
+  int64_t rec_rows;
+  int32_t rec_decim, n_rec;
+  int64_t n0, n_steps;
+  double dt;
 };
 
 struct SourceParams {
@@ -175,6 +225,9 @@ cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st);
 cudaError_t launch_sources(const SourceParams& p, cudaStream_t st);
 cudaError_t launch_forward(const FwdParams& p, cudaStream_t st);
 size_t forward_smem_bytes(const FwdLimits& lim);
+cudaError_t launch_batch(const BatchParams& p, cudaStream_t st);
+size_t batch_smem_bytes(const BatchParams& p);
+int batch_threads();
 cudaError_t launch_gather(const double* rec, int32_t n_rec, int64_t n_scen_rec, const int32_t* col, int64_t n_ch,
                           int64_t row0, int64_t n_rows, int64_t scen0, int64_t n_scen, double* out, cudaStream_t st);
 

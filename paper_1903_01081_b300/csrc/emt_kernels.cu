@@ -98,12 +98,21 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
   for (int i = tid; i < n * n; i += T) A[i] = 0.0;
   __syncthreads();
   if (tid == 0) {
-    // a source end acts as ground in G (its voltage goes to the injection)
+    // a source end acts as ground in G (its voltage goes to the injection);
+    // elements a scenario variant removes are left out
+    const int rb0 = P.rm_ptr_br ? P.rm_ptr_br[mi] : 0, rb1 = P.rm_ptr_br ? P.rm_ptr_br[mi + 1] : 0;
+    const int rl0 = P.rm_ptr_le ? P.rm_ptr_le[mi] : 0, rl1 = P.rm_ptr_le ? P.rm_ptr_le[mi + 1] : 0;
     for (int b = 0; b < S.n_br; ++b) {
+      bool removed = false;
+      for (int x = rb0; x < rb1; ++x) removed |= (P.rm_br[x] == S.br_off + b);
+      if (removed) continue;
       const BranchDev x = P.br[S.br_off + b];
       stamp(A, n, x.k >= 0 ? x.k : -1, x.m >= 0 ? x.m : -1, x.g);
     }
     for (int e = 0; e < S.n_le; ++e) {
+      bool removed = false;
+      for (int x = rl0; x < rl1; ++x) removed |= (P.rm_le[x] == S.le_off + e);
+      if (removed) continue;
       const LineEndDev le = P.le[S.le_off + e];
       A[le.node * n + le.node] += le.y;
     }

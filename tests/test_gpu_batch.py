@@ -1,0 +1,85 @@
+"""GPU parity of the multi-scenario path against the CPU oracle.
+
+Each scenario of a set is written out as a plain network (removed elements
+dropped, fault switches added, sources overridden) and run by the oracle;
+the batched CUDA run of the whole set must match every checked scenario to
+the same peak-normalised 1e-10 as the single-network path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_01081_b300 import emt, netgen as g
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def rel_err(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+def batch_run(net, sc, n_steps, channels=None, decim=1, check=None):
+    sim = emt.Simulator(net, sc, n_steps=n_steps, channels=channels, decim=decim)
+    sim.run(n_steps)
+    sim.sync()
+    out = {}
+    for s in (range(sc.n_scenarios) if check is None else check):
+        out[s] = sim.waveforms(scen0=s, n_scen=1)[:, 0, :]
+    info = {k: sim.info(k) for k in ("n_scenarios", "n_matrix_variants", "scenarios_per_cta")}
+    sim.close()
+    return out, info
+
+
+def test_small_n1_contingency_all_scenarios():
+    net, sc = g.n1_contingency(seed=77, n_scenarios=12, n_buses=40, n_sub=8, n_lines=12, n_sources=3,
+                               n_steps=1500, fault_step=500, target_branches=240)
+    N = 1500
+    got, info = batch_run(net, sc, N)
+    assert info["n_scenarios"] == 12 and info["n_matrix_variants"] > 8
+    for s in range(12):
+        ref = oracle.simulate(sc.expand(net, s), N)
+        assert rel_err(got[s], ref) <= TOL, s
+
+
+def test_small_shared_g_all_scenarios():
+    base = g.multi_subsystem(91, [3, 5, 2, 4, 6], n_lines=9, n_sources=3, dt=20e-6, n_series_extra=2)
+    net, sc = g.shared_g(seed=92, n_scenarios=10, n_steps=1200, fault_step=400, base=base)
+    N = 1200
+    got, info = batch_run(net, sc, N)
+    for s in range(10):
+        ref = oracle.simulate(sc.expand(net, s), N)
+        assert rel_err(got[s], ref) <= TOL, s
+
+
+def test_one_scenario_set_equals_the_plain_network():
+    net = g.multi_subsystem(93, [4, 3, 5], n_lines=5, n_sources=2, dt=20e-6)
+    sc = g.Scenarios(n_scenarios=1)
+    N = 800
+    got, _ = batch_run(net, sc, N)
+    assert rel_err(got[0], oracle.simulate(net, N)) <= TOL
+
+
+def test_scenario_tiles_with_a_ragged_tail():
+    # 300 scenarios: tiles of 2, the last tile holds a ragged count only if S_t does not divide S
+    net, sc = g.n1_contingency(seed=78, n_scenarios=300, n_buses=30, n_sub=6, n_lines=8, n_sources=2,
+                               n_steps=600, fault_step=200, target_branches=180)
+    N = 600
+    check = [0, 1, 149, 298, 299]
+    got, info = batch_run(net, sc, N, check=check)
+    for s in check:
+        assert rel_err(got[s], oracle.simulate(sc.expand(net, s), N)) <= TOL, s
+
+
+def test_n1_full_size_sampled_scenarios():
+    """1,024 N-1 scenarios of the 200-bus network, 10,000 steps, in one launch;
+    sixteen scenarios checked against the oracle on every 10th step."""
+    net, sc = g.n1_contingency()
+    N = net.n_steps
+    rng = np.random.default_rng(5)
+    check = sorted(rng.choice(sc.n_scenarios, size=16, replace=False).tolist())
+    got, info = batch_run(net, sc, N, decim=10, check=check)
+    assert info["n_scenarios"] == 1024
+    for s in check:
+        ref = oracle.simulate(sc.expand(net, s), N)[9::10]
+        assert rel_err(got[s], ref) <= TOL, s
