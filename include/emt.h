@@ -167,6 +167,35 @@ emt_status emt_step_n(emt_ctx* ctx, int64_t n_steps, void* cuda_stream);
 emt_status emt_read_waveforms(emt_ctx* ctx, const int32_t* channels, int64_t n_ch, int64_t step0, int64_t n_rows,
                               int64_t scen0, int64_t n_scen, double* out, int32_t out_on_device);
 
+/* Discrete adjoint: the loss J = sum_{n=1..N} sum_k (v_n[k] - v*_n[k])^2
+ * over all node voltages of steps 1..N from the de-energised state, and
+ * its exact gradient (reverse-mode of the discrete time loop, not of the
+ * continuous equations) with respect to every branch value and source
+ * amplitude.  Switch times, Z_c and line delays are fixed, not parameters.
+ * The paper's fixed-step loop (Sec. III-A, processes 1-4) is run backwards:
+ * w_n = G_n^-T vbar_n with G symmetric, so the same prefactored G^-1 serves
+ * both directions.
+ *   v_target:   [n_steps][n_nodes] doubles, caller's node order (v*_n in
+ *               row n-1); treated as constant.
+ *   ckpt_every: K >= 1: the forward state (history currents and line
+ *               rings) is stored every K steps and each segment is run
+ *               forward again before its reverse sweep (memory ~ N/K
+ *               states + K x n_nodes tape); K = 0: the whole tape v_n is
+ *               kept (N x n_nodes doubles), nothing is recomputed.  Both
+ *               give bit-identical results.
+ *   grad:       [n_branches + n_sources] doubles, or NULL: dJ/d(br_value[b])
+ *               in the caller's branch order, then dJ/d(src_amp[s]).
+ *   loss:       host double, or NULL (not both NULL).
+ *   on_device:  non-zero: v_target and grad are device memory; else host.
+ *   cuda_stream: stream for the launches (NULL: legacy default stream).
+ * Requires emt_prefactor; a context built with a scenario set returns
+ * EINVAL.  Resets the context to step 0 before and after (the recording
+ * buffer is not written).  Allocates its work buffers (about 8 N n_nodes
+ * bytes for a host v_target, N/K checkpoints, the tape) and frees them
+ * before returning.  Synchronous.  ETIMEOUT as for emt_step_n. */
+emt_status emt_adjoint(emt_ctx* ctx, const double* v_target, int64_t n_steps, int32_t ckpt_every, double* grad,
+                       double* loss, int32_t on_device, void* cuda_stream);
+
 /* Return to the de-energised state at step 0 (keeps G^-1 and recording setup). */
 emt_status emt_reset(emt_ctx* ctx);
 
@@ -175,13 +204,16 @@ emt_status emt_reset(emt_ctx* ctx);
 emt_status emt_sync(emt_ctx* ctx, int32_t* dev_err_info);
 
 /* Tuning and debug knobs (key = value): "wait_budget_ns" (per wait),
+ * "adjoint_overlap" (default 1: emt_adjoint re-runs segment j-1 forward on
+ * a second stream while the reverse sweep of segment j runs, when both
+ * persistent grids fit on the device together; 0: one stream),
  * "debug_hold_lines" (that subsystem never sends line values; -1 none;
  * for failure-path tests).  EINVAL for an unknown key. */
 emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
 
 /* Read-only facts: "n_subsystems", "n_ctas", "step", "max_subsystem_nodes",
  * "n_scenarios", "n_epochs_total", "sum_n2" (sum over subsystems of n_s^2),
- * "threads_per_cta", "kernel_launches", "n_branches", "n_line_ends",
+ * "threads_per_cta", "kernel_launches", "n_nodes", "n_branches", "n_sources", "n_line_ends",
  * "smem_bytes" (dynamic shared memory per CTA of the persistent kernel),
  * "n_strong_branches" (L/C branches applied through extra solve columns). */
 emt_status emt_get_info(const emt_ctx* ctx, const char* key, int64_t* value);

@@ -15,7 +15,7 @@ def sources():
 
 
 def headers():
-    return sorted(glob.glob(os.path.join(HERE, "csrc", "*.h")) +
+    return sorted(glob.glob(os.path.join(HERE, "csrc", "*.h")) + glob.glob(os.path.join(HERE, "csrc", "*.cuh")) +
                   glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h")))
 
 

@@ -1,0 +1,498 @@
+// Discrete adjoint of the time loop for sm_103a (B300): the reverse sweep.
+//
+// Loss J = sum_{n=1..N} sum_k (v_n[k] - v*_n[k])^2.  Per subsystem the
+// forward step is (trapezoidal companions, Bergeron lines)
+//   v_n = G_n^-1 (u_n - A h_{n-1} - L I_n),    h_n = D h_{n-1} + E A^T v_n
+//   I_far(n+d) = -(2/Z_c) v_near(n) - I_near(n)
+// with D = +1 (L) / -1 (C), E = +2g (L) / -2g (C).  Its reverse, n = N..1,
+// with hbar_N = 0 and Ibar(n) = 0 for n > N:
+//   vbar_n  = 2 (v_n - v*_n) + A E hbar_n - sum_e (2/Z_c) Ibar_far(e)(n+d) e_node(e)
+//   w_n     = G_n^-T vbar_n = G_n^-1 vbar_n          (G is symmetric)
+//   hbar_{n-1} = D hbar_n - A^T w_n
+//   Ibar_e(n)  = -w_n[node(e)] - Ibar_far(e)(n+d)
+// and the parameter terms of step n
+//   dJ/dg_b += -(a_b^T w_n) v_b(n) + hbar_n[b] (dE_b/dg_b) v_b(n)
+//   dJ/dA_s += sin(omega t_n + phase) (g_b w_n[u] +/- E_b hbar_n[b])   (b joins source s to u)
+//
+// adj_kernel mirrors fwd_kernel: one CTA per subsystem, the solve matrix
+// [X_hi | strong columns] and X_lo in shared memory, the same injection
+// lanes assembling vbar (the lane inputs hold -E hbar for L/C slots, 0 for
+// source branches and (2/Z_c) Ibar for line ends, so the forward's entry
+// signs give A E hbar and -(2/Z_c) Ibar), the same matvec, and tagged rings
+// carrying Ibar between subsystems with the tag N + 1 - n.  A strong branch
+// enters through its extra column with the input +E hbar (the forward uses
+// -h), since that column is G^-1 (e_k - e_m).  The forward tape v_n and the
+// target v*_n are read one step ahead.
+#include <stdint.h>
+
+#include <algorithm>
+#include <climits>
+
+#include <cuda_runtime.h>
+
+#include "emt_device.cuh"
+#include "emt_internal.h"
+
+namespace emt {
+
+namespace {
+
+constexpr int kAdjThreads = kFwdThreads;
+constexpr int kAdjPollWarp = kAdjThreads / 32 - 1;
+constexpr int kAdjItemThreads = kAdjThreads - 32;
+
+struct AdjSmem {
+  size_t gi, part, iv, ww, vn, ev, inp, xr, hb, lce, brg, bre, dga, dsa, ley2, leown, lefar, amp, sn, vsrc;   // 8-byte
+  size_t gilo, ivf;                                                                                      // float
+  size_t brk, brm, brlc, brkind, lcstr, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, orig;   // int
+  size_t bytes;
+};
+
+__host__ __device__ inline AdjSmem adj_smem(const AdjLimits& L) {
+  AdjSmem s{};
+  size_t o = 0;
+  auto d = [&](size_t count) { size_t r = o; o += count * 8; return r; };
+  auto w = [&](size_t count) { size_t r = o; o += count * 4; return r; };
+  const size_t ldg = (size_t)(L.nc | 1);
+  s.gi = d((size_t)L.n * ldg);
+  s.part = d((size_t)L.n * L.q);
+  s.iv = d(L.nc);
+  s.ww = d(L.n);
+  s.vn = d(2 * (size_t)L.n);
+  s.ev = d(2 * (size_t)L.n);
+  s.inp = d((size_t)L.lc + L.sb + 2 * (size_t)L.le + 1);
+  s.xr = d(2 * (size_t)L.le);
+  s.hb = d(L.lc);
+  s.lce = d(L.lc);
+  s.brg = d(L.br);
+  s.bre = d(L.br);
+  s.dga = d(L.br);
+  s.dsa = d(L.br);
+  s.ley2 = d(L.le);
+  s.leown = d(L.le);
+  s.lefar = d(L.le);
+  s.amp = d(L.src);
+  s.sn = d(2 * (size_t)L.src);
+  s.vsrc = d(2 * (size_t)L.src);
+  s.gilo = w((size_t)L.n * ldg);
+  s.ivf = w(L.nc);
+  s.brk = w(L.br);
+  s.brm = w(L.br);
+  s.brlc = w(L.br);
+  s.brkind = w(L.br);
+  s.lcstr = w(L.lc);
+  s.lenode = w(L.le);
+  s.ledepth = w(L.le);
+  s.led = w(L.le);
+  s.rslot = w(L.le);
+  s.wslot = w(L.le);
+  s.ent = w(4 * (size_t)L.il);
+  s.ilnode = w(L.il);
+  s.ilcnt = w(L.il);
+  s.srcg = w(L.src);
+  s.orig = w(L.n);
+  s.bytes = (o + 15) & ~(size_t)15;
+  return s;
+}
+
+// One warp collects one reverse step's adjoint line values Ibar_far(n+d)
+// (raw into xr, times 2/Z_c into the lane inputs).  Bounded like the
+// forward's collection: on exceeding the time budget (or seeing another
+// CTA's error) it latches an error and returns false.
+__device__ bool collect_adj(const AdjParams& P, int n_le, unsigned tag, int lane, int sidx, const long long* leown,
+                            const int* ledepth, int* rslot, const double* ley2, double* xr, double* inp_le) {
+  bool ok = true;
+  for (int e = lane; e < n_le && ok; e += 32) {
+    const unsigned long long* slot = P.ring + 2 * (leown[e] + rslot[e]);
+    double v = 0.0;
+    if (!ld_tagged(slot, tag, v)) {
+      const unsigned long long t0 = global_ns();
+      unsigned spins = 0;
+      while (!ld_tagged(slot, tag, v)) {
+        if ((++spins & 31u) == 0) {
+          if (ld_volatile(P.err) != 0) { ok = false; break; }
+          if (global_ns() - t0 > P.wait_budget_ns || spins > (1u << 30)) {
+            if (atomicCAS(P.err, 0, 5) == 0) {
+              P.err[1] = sidx;
+              P.err[2] = e;
+              P.err[3] = (int)tag;
+            }
+            ok = false;
+            break;
+          }
+        }
+      }
+    }
+    xr[e] = v;
+    inp_le[e] = ley2[e] * v;
+    const int nx = rslot[e] + 1;
+    rslot[e] = nx == ledepth[e] ? 0 : nx;
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
+__global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_abort;
+  const AdjSmem L = adj_smem(P.lim);
+  double* gi = reinterpret_cast<double*>(smem_raw + L.gi);
+  double* part = reinterpret_cast<double*>(smem_raw + L.part);
+  double* iv = reinterpret_cast<double*>(smem_raw + L.iv);
+  double* ww = reinterpret_cast<double*>(smem_raw + L.ww);
+  double* vn = reinterpret_cast<double*>(smem_raw + L.vn);     // [2][n]: v_n by tag parity
+  double* ev = reinterpret_cast<double*>(smem_raw + L.ev);     // [2][n]: v_n - v*_n
+  double* inp = reinterpret_cast<double*>(smem_raw + L.inp);
+  double* xr = reinterpret_cast<double*>(smem_raw + L.xr);     // [2][le]
+  double* hb = reinterpret_cast<double*>(smem_raw + L.hb);
+  double* lce = reinterpret_cast<double*>(smem_raw + L.lce);
+  double* brg = reinterpret_cast<double*>(smem_raw + L.brg);
+  double* bre = reinterpret_cast<double*>(smem_raw + L.bre);
+  double* dga = reinterpret_cast<double*>(smem_raw + L.dga);
+  double* dsa = reinterpret_cast<double*>(smem_raw + L.dsa);
+  double* ley2 = reinterpret_cast<double*>(smem_raw + L.ley2);
+  long long* leown = reinterpret_cast<long long*>(smem_raw + L.leown);
+  long long* lefar = reinterpret_cast<long long*>(smem_raw + L.lefar);
+  double* amp = reinterpret_cast<double*>(smem_raw + L.amp);
+  double* sn = reinterpret_cast<double*>(smem_raw + L.sn);     // [2][src]
+  double* vsrc = reinterpret_cast<double*>(smem_raw + L.vsrc); // [2][src]
+  float* gilo = reinterpret_cast<float*>(smem_raw + L.gilo);
+  float* ivf = reinterpret_cast<float*>(smem_raw + L.ivf);
+  int* brk = reinterpret_cast<int*>(smem_raw + L.brk);
+  int* brm = reinterpret_cast<int*>(smem_raw + L.brm);
+  int* brlc = reinterpret_cast<int*>(smem_raw + L.brlc);
+  int* brkind = reinterpret_cast<int*>(smem_raw + L.brkind);
+  int* lcstr = reinterpret_cast<int*>(smem_raw + L.lcstr);
+  int* lenode = reinterpret_cast<int*>(smem_raw + L.lenode);
+  int* ledepth = reinterpret_cast<int*>(smem_raw + L.ledepth);
+  int* led = reinterpret_cast<int*>(smem_raw + L.led);
+  int* rslot = reinterpret_cast<int*>(smem_raw + L.rslot);
+  int* wslot = reinterpret_cast<int*>(smem_raw + L.wslot);
+  int* ent = reinterpret_cast<int*>(smem_raw + L.ent);
+  int* ilnode = reinterpret_cast<int*>(smem_raw + L.ilnode);
+  int* ilcnt = reinterpret_cast<int*>(smem_raw + L.ilcnt);
+  int* srcg = reinterpret_cast<int*>(smem_raw + L.srcg);
+  int* orig = reinterpret_cast<int*>(smem_raw + L.orig);
+
+  const int sidx = blockIdx.x;
+  const SubDev S = P.sub[sidx];
+  const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = S.n, Q = S.q, n_str = S.n_str, nc = n + n_str, ldg = nc | 1;
+  const int blk = (nc + Q - 1) / Q;
+  const int n_br = S.n_br, n_lc = S.n_lc, n_sb = S.n_sb, n_le = S.n_le, n_il = S.n_il, n_src = S.n_src;
+  const int ie_base = n_lc + n_sb;
+  const int zero_slot = ie_base + 2 * n_le;
+  const int nv = P.lim.n, sv = P.lim.src, lv = P.lim.le;   // strides of the parity-doubled arrays
+  const int src_thread = T - 1 - tid;
+  const int it_le = (n_br + 31) & ~31;   // branch items, then line ends on their own warps
+  const int it_end = it_le + n_le;
+  const long long tau0 = P.n_total + 1 - P.n_hi;
+  const int64_t nn = P.n_nodes;
+
+  // ---- prologue
+  for (int x = tid; x < n_br; x += T) {
+    const BranchDev b = P.br[S.br_off + x];
+    brk[x] = b.k;
+    brm[x] = b.m;
+    brkind[x] = b.kind;
+    brg[x] = b.g;
+    bre[x] = b.e;
+    brlc[x] = P.br_lc[S.br_off + x];
+    dga[x] = P.dg[S.br_off + x];
+    dsa[x] = P.dsrc[S.br_off + x];
+  }
+  for (int x = tid; x < n_lc; x += T) {
+    const double e = P.br[P.lc_idx[S.lc_off + x]].e;
+    const double h = P.hbar[S.lc_off + x];
+    lce[x] = e;
+    hb[x] = h;
+    inp[x] = -e * h;
+    lcstr[x] = -1;
+  }
+  for (int x = tid; x < n_sb; x += T) inp[n_lc + x] = 0.0;
+  for (int x = tid; x < n_le; x += T) {
+    const LineEndDev e = P.le[S.le_off + x];
+    ley2[x] = e.y2;
+    leown[x] = e.own_ring;
+    lefar[x] = e.far_ring;
+    lenode[x] = e.node;
+    ledepth[x] = e.depth;
+    led[x] = e.d;
+    rslot[x] = (int)(tau0 % e.depth);
+    wslot[x] = (int)((tau0 + e.d) % e.depth);
+  }
+  for (int x = tid; x < 4 * n_il; x += T) ent[x] = P.ent[4 * (size_t)S.il_off + x];
+  for (int x = tid; x < n_il; x += T) {
+    ilnode[x] = P.il_node[S.il_off + x];
+    ilcnt[x] = P.il_cnt[S.il_off + x];
+  }
+  const int par0 = (int)(tau0 & 1);
+  for (int x = tid; x < n_src; x += T) {
+    const int g = P.src_global[S.src_off + x];
+    srcg[x] = g;
+    amp[x] = P.src_amp[g];
+    const double s = P.sin_table[(P.n_hi - 1) * P.n_sources + g];
+    sn[par0 * sv + x] = s;
+    vsrc[par0 * sv + x] = P.src_amp[g] * s;
+  }
+  for (int r = tid; r < n; r += T) {
+    const int o = P.orig_of[S.node_off + r];
+    orig[r] = o;
+    const double v = P.tape[(P.n_hi - 1 - P.tape_row0) * nn + S.node_off + r];
+    vn[par0 * nv + r] = v;
+    ev[par0 * nv + r] = v - P.target[(P.n_hi - 1) * nn + o];
+  }
+  if (tid == 0) {
+    inp[zero_slot] = 0.0;
+    s_abort = 0;
+  }
+  int ep = 0;
+  while (ep + 1 < S.n_ep && P.ep[S.ep_off + ep + 1].start <= P.n_hi) ++ep;
+  long long ep_start = P.ep[S.ep_off + ep].start;
+  {
+    const int64_t off = P.ep[S.ep_off + ep].ginv_off;
+    for (int i = tid; i < n * nc; i += T) {
+      const int r = i / nc, c = i - r * nc;
+      gi[r * ldg + c] = P.ginv[off + i];
+      gilo[r * ldg + c] = P.ginv_lo[off + i];
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < n_str; t += T) {
+    const int x = P.str_slot[S.str_off + t];
+    lcstr[x] = t;
+    const double e = lce[x] * hb[x];
+    iv[n + t] = e;
+    ivf[n + t] = (float)e;
+  }
+  if (warp == kAdjPollWarp && n_le > 0) {
+    const bool ok = collect_adj(P, n_le, (unsigned)tau0, lane, sidx, leown, ledepth, rslot, ley2, xr + par0 * lv,
+                                inp + ie_base + par0 * n_le);
+    if (!ok && lane == 0) s_abort = 1;
+  }
+  double jacc = P.loss_part[(int64_t)sidx * T + tid];
+  __syncthreads();
+
+  for (long long i = 0; i < P.n_steps && !s_abort; ++i) {
+    const long long nstep = P.n_hi - i;
+    const long long tau = tau0 + i;
+    const int par = (int)(tau & 1);
+    const int parshift = par * n_le;
+    const bool more = i + 1 < P.n_steps;
+    if (nstep < ep_start) {   // switch state of the earlier epoch
+      while (ep > 0 && P.ep[S.ep_off + ep].start > nstep) --ep;
+      ep_start = P.ep[S.ep_off + ep].start;
+      const int64_t off = P.ep[S.ep_off + ep].ginv_off;
+      for (int x = tid; x < n * nc; x += T) {
+        const int r = x / nc, c = x - r * nc;
+        gi[r * ldg + c] = P.ginv[off + x];
+        gilo[r * ldg + c] = P.ginv_lo[off + x];
+      }
+    }
+    // step n-1's tape, target and source values: loads issued now, stored after the solve
+    double vnx = 0.0, tnx = 0.0, snx = 0.0;
+    if (more) {
+      if (tid < n) {
+        vnx = __ldg(P.tape + (nstep - 2 - P.tape_row0) * nn + S.node_off + tid);
+        tnx = __ldg(P.target + (nstep - 2) * nn + orig[tid]);
+      }
+      if (src_thread < n_src) snx = __ldg(P.sin_table + (nstep - 2) * P.n_sources + srcg[src_thread]);
+    }
+
+    // vbar_n = 2 (v_n - v*_n) + A E hbar_n - sum_e (2/Z_c) Ibar_far(n+d), by injection lanes
+    for (int base = 0; base < n_il; base += T) {
+      const int l = base + tid;
+      double s = 0.0;
+      int node = -1, cnt = 0;
+      if (l < n_il) {
+        node = ilnode[l];
+        cnt = ilcnt[l];
+        const int* e4 = ent + 4 * l;
+        s = (signed_entry(inp, (unsigned)e4[0], ie_base, n_le, parshift) +
+             signed_entry(inp, (unsigned)e4[1], ie_base, n_le, parshift)) +
+            (signed_entry(inp, (unsigned)e4[2], ie_base, n_le, parshift) +
+             signed_entry(inp, (unsigned)e4[3], ie_base, n_le, parshift));
+      }
+      const int wmax = __reduce_max_sync(0xffffffffu, cnt);
+      double acc = s;
+      for (int j = 1; j < wmax; ++j) {
+        const double o = __shfl_down_sync(0xffffffffu, s, j);
+        if (j < cnt) acc += o;
+      }
+      if (cnt > 0) {
+        const double vb = 2.0 * ev[par * nv + node] + acc;
+        iv[node] = vb;
+        ivf[node] = (float)vb;
+      }
+    }
+    __syncthreads();
+
+    // w_n = (X_hi + X_lo) [vbar; E hbar_strong], task (r, q) over column block q
+    for (int task = tid; task < n * Q; task += T) {
+      const int r = task / Q, q = task - r * Q;
+      const double* row = gi + r * ldg;
+      const float* rowl = gilo + r * ldg;
+      const int j1 = min(nc, (q + 1) * blk);
+      double a = 0.0;
+      float b = 0.f;
+      for (int j = q * blk; j < j1; ++j) {
+        a = fma(row[j], iv[j], a);
+        b = fmaf(rowl[j], ivf[j], b);
+      }
+      part[task] = a + (double)b;
+    }
+    if (more) {
+      if (tid < n) {
+        vn[(par ^ 1) * nv + tid] = vnx;
+        ev[(par ^ 1) * nv + tid] = vnx - tnx;
+      }
+      if (src_thread < n_src) {
+        sn[(par ^ 1) * sv + src_thread] = snx;
+        vsrc[(par ^ 1) * sv + src_thread] = amp[src_thread] * snx;
+      }
+    }
+    __syncthreads();
+
+    for (int r = tid; r < n; r += T) {
+      double w = part[r * Q];
+      for (int q = 1; q < Q; ++q) w += part[r * Q + q];
+      ww[r] = w;
+      const double e = ev[par * nv + r];
+      jacc = fma(e, e, jacc);
+    }
+    __syncthreads();
+
+    // parameter terms, hbar_{n-1}, Ibar_e(n); the poll warp collects step n-1's line values
+    if (warp == kAdjPollWarp) {
+      if (n_le > 0 && more) {
+        const bool ok = collect_adj(P, n_le, (unsigned)(tau + 1), lane, sidx, leown, ledepth, rslot, ley2,
+                                    xr + (par ^ 1) * lv, inp + ie_base + (par ^ 1) * n_le);
+        if (!ok && lane == 0) s_abort = 1;
+      }
+    } else {
+      const double* vnc = vn + par * nv;
+      const double* vsc = vsrc + par * sv;
+      for (int it = tid; it < it_end; it += kAdjItemThreads) {
+        if (it < n_br) {
+          const int k = brk[it], m = brm[it];
+          const double vk = k >= 0 ? vnc[k] : (k == -1 ? 0.0 : vsc[-2 - k]);
+          const double vm = m >= 0 ? vnc[m] : (m == -1 ? 0.0 : vsc[-2 - m]);
+          const double vb = vk - vm;
+          const double aw = (k >= 0 ? ww[k] : 0.0) - (m >= 0 ? ww[m] : 0.0);
+          double dg = fma(-aw, vb, dga[it]);
+          const int x = brlc[it];
+          const double E = bre[it];
+          double hbn = 0.0;
+          if (x >= 0) {
+            hbn = hb[x];
+            const bool is_l = brkind[it] == 1;
+            dg = fma(is_l ? 2.0 * hbn : -2.0 * hbn, vb, dg);
+            const double hnew = (is_l ? hbn : -hbn) - aw;
+            hb[x] = hnew;
+            inp[x] = -E * hnew;
+            const int t = lcstr[x];
+            if (t >= 0) {
+              const double e = E * hnew;
+              iv[n + t] = e;
+              ivf[n + t] = (float)e;
+            }
+          }
+          dga[it] = dg;
+          if (k <= -2 || m <= -2) {
+            const int j = k <= -2 ? -2 - k : -2 - m;
+            const int u = k <= -2 ? m : k;
+            double dv = brg[it] * (u >= 0 ? ww[u] : 0.0);
+            if (x >= 0) dv += (k <= -2 ? E : -E) * hbn;
+            dsa[it] = fma(sn[par * sv + j], dv, dsa[it]);
+          }
+        } else if (it >= it_le) {
+          const int e = it - it_le;
+          st_tagged(P.ring + 2 * (lefar[e] + wslot[e]), (unsigned)(tau + led[e]),
+                    -ww[lenode[e]] - xr[par * lv + e]);
+          const int nx = wslot[e] + 1;
+          wslot[e] = nx == ledepth[e] ? 0 : nx;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (!s_abort) {
+    for (int x = tid; x < n_lc; x += T) P.hbar[S.lc_off + x] = hb[x];
+    for (int x = tid; x < n_br; x += T) {
+      P.dg[S.br_off + x] = dga[x];
+      P.dsrc[S.br_off + x] = dsa[x];
+    }
+    P.loss_part[(int64_t)sidx * T + tid] = jacc;
+  }
+}
+
+// Chain rule to the element values and per-source sums, in a fixed order:
+//   dJ/dR = -dJ/dg / R^2,  dJ/dL = -dJ/dg dt / (2 L^2),  dJ/dC = dJ/dg 2 / dt
+//   dJ/dA_s = sum over branches b of source s (internal order) of dsrc[b]
+//   J = sum of the per-thread partial sums (CTA order, then thread order)
+__global__ void adj_finalize_kernel(const BranchDev* br, const int32_t* br_orig, const int32_t* br_src, int64_t n_br,
+                                    const double* dg, const double* dsrc, int64_t n_sources, double dt,
+                                    const double* loss_part, int64_t n_loss, double* grad, double* loss) {
+  const int64_t total = n_br + n_sources + 1;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n_br) {
+      const BranchDev b = br[i];
+      const double x = b.value;
+      const double dgdp = b.kind == 0 ? -1.0 / (x * x) : (b.kind == 1 ? -dt / (2.0 * x * x) : 2.0 / dt);
+      grad[br_orig[i]] = dg[i] * dgdp;
+    } else if (i < n_br + n_sources) {
+      const int32_t s = (int32_t)(i - n_br);
+      double acc = 0.0;
+      for (int64_t b = 0; b < n_br; ++b)
+        if (br_src[b] == s) acc += dsrc[b];
+      grad[i] = acc;
+    } else if (loss) {
+      double acc = 0.0;
+      for (int64_t j = 0; j < n_loss; ++j) acc += loss_part[j];
+      *loss = acc;
+    }
+  }
+}
+
+}  // namespace
+
+int adjoint_threads() { return kAdjThreads; }
+
+size_t adjoint_smem_bytes(const AdjLimits& lim) { return adj_smem(lim).bytes; }
+
+int adjoint_blocks_per_sm(const AdjLimits& lim) {
+  const size_t smem = adjoint_smem_bytes(lim);
+  if (smem > 227 * 1024) return 0;
+  if (cudaFuncSetAttribute(adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_kernel, kAdjThreads, smem) != cudaSuccess) return 0;
+  return per_sm;
+}
+
+cudaError_t launch_adjoint(const AdjParams& p, cudaStream_t st) {
+  const size_t smem = adjoint_smem_bytes(p.lim);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(adj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, n_sm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_kernel, kAdjThreads, smem);
+  if (e != cudaSuccess) return e;
+  if ((long long)per_sm * n_sm < p.n_sub) return cudaErrorCooperativeLaunchTooLarge;
+  AdjParams arg = p;
+  void* args[] = {&arg};
+  // cooperative launch: all CTAs co-resident, so every ring wait can end
+  return cudaLaunchCooperativeKernel((const void*)adj_kernel, dim3(p.n_sub), dim3(kAdjThreads), args, smem, st);
+}
+
+cudaError_t launch_adj_finalize(const BranchDev* br, const int32_t* br_orig, const int32_t* br_src, int64_t n_br,
+                                const double* dg, const double* dsrc, int64_t n_sources, double dt,
+                                const double* loss_part, int64_t n_loss, double* grad, double* loss, cudaStream_t st) {
+  const int64_t total = n_br + n_sources + 1;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 4);
+  adj_finalize_kernel<<<blocks, 256, 0, st>>>(br, br_orig, br_src, n_br, dg, dsrc, n_sources, dt, loss_part, n_loss,
+                                              grad, loss);
+  return cudaGetLastError();
+}
+
+}  // namespace emt

@@ -53,6 +53,9 @@ struct emt_ctx {
   std::vector<int32_t> lc_idx, sb_idx;
   std::vector<int32_t> ent, il_node, il_cnt, str_slot;
   std::vector<LineEndDev> line_ends;
+  std::vector<int32_t> br_orig;                        // internal branch -> caller's branch index
+  std::vector<int32_t> br_lc;                          // internal branch -> subsystem-local L/C slot or -1
+  std::vector<int32_t> br_src;                         // internal branch -> global source at one end or -1
   std::vector<int32_t> src_global;                     // global source id per local source slot
   std::vector<double> src_amp, src_phase, src_omega;   // per global source
   std::vector<int32_t> nb_sub, nb_dmin;
@@ -74,6 +77,10 @@ struct emt_ctx {
   LineEndDev* d_le = nullptr;
   unsigned long long* d_ring = nullptr;
   int32_t* d_src_global = nullptr;
+  int32_t* d_br_orig = nullptr;
+  int32_t* d_br_lc = nullptr;
+  int32_t* d_br_src = nullptr;
+  int32_t* d_original_of = nullptr;
   double* d_src_amp = nullptr;
   double* d_src_phase = nullptr;
   double* d_src_omega = nullptr;
@@ -95,6 +102,7 @@ struct emt_ctx {
   // run state and knobs
   int64_t step = 0;
   bool prefactored = false;
+  bool overlap_adjoint = true;
   unsigned long long wait_budget_ns = 2000000000ull;
   int32_t hold_sub = -1;
   int64_t launches = 0;
@@ -557,6 +565,10 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
         lc_slot_of[nb] = (int32_t)c->lc_idx.size() - sd.lc_off;
         c->lc_idx.push_back(nb);
       }
+      c->br_orig.push_back((int32_t)b);
+      c->br_lc.push_back(lc_slot_of[nb]);
+      c->br_src.push_back(x.k <= -2 ? c->src_global[sd.src_off + (-2 - x.k)]
+                                    : (x.m <= -2 ? c->src_global[sd.src_off + (-2 - x.m)] : -1));
       if (x.k <= -2 || x.m <= -2) {
         sb_slot_of[nb] = (int32_t)c->sb_idx.size() - sd.sb_off;
         c->sb_idx.push_back(nb);
@@ -812,6 +824,10 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   UP(d_src_phase, src_phase)
   UP(d_src_omega, src_omega)
   UP(d_sw, switches)
+  UP(d_br_orig, br_orig)
+  UP(d_br_lc, br_lc)
+  UP(d_br_src, br_src)
+  UP(d_original_of, original_of)
 #undef UP
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_h, (size_t)c->n_lc_total);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ring, 2 * (size_t)std::max<int64_t>(c->ring_len, 1));
@@ -961,6 +977,91 @@ extern "C" emt_status emt_set_recording(emt_ctx* c, const int32_t* channels, int
   return EMT_OK;
 }
 
+// Where a forward launch writes node voltages: rows of rec for steps
+// decim, 2 decim, ..., row r (step (r + 1) decim) at rec + (r - row0) * n_rec.
+struct RecSpec {
+  double* rec = nullptr;
+  const int32_t* pos = nullptr;
+  int32_t n_rec = 0;
+  int32_t decim = 1;
+  int64_t rows = 0;
+  int64_t row0 = 0;
+};
+
+// Single-network forward run of n_steps steps from the context's step.
+static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, const RecSpec& rs) {
+  if (forward_smem_bytes(c->lim) > 227 * 1024)
+    return c->fail(EMT_ERESOURCE, "a subsystem needs more shared memory than one CTA has");
+  // source table for one chunk of steps at a time (grow-only buffer)
+  const int64_t chunk =
+      std::min<int64_t>(n_steps, std::max<int64_t>(1, kSourceTableDoubles / std::max<int64_t>(c->n_sources, 1)));
+  if (c->src_table_steps < chunk) {
+    cudaStreamSynchronize(st);
+    c->release(c->d_src_table);
+    c->d_src_table = nullptr;
+    c->src_table_steps = 0;
+    cudaError_t e = c->alloc_zero(&c->d_src_table, (size_t)chunk * std::max<int64_t>(c->n_sources, 1));
+    if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n source table");
+    c->src_table_steps = chunk;
+  }
+  FwdParams p{};
+  p.n_sub = c->n_sub;
+  p.lim = c->lim;
+  p.lim.n = std::max(p.lim.n, 1);
+  p.lim.nc = std::max(p.lim.nc, 1);
+  p.sub = c->d_sub;
+  p.ep = c->d_ep;
+  p.ginv = c->d_ginv;
+  p.ginv_lo = c->d_ginv_lo;
+  p.br = c->d_br;
+  p.lc_idx = c->d_lc_idx;
+  p.sb_idx = c->d_sb_idx;
+  p.h = c->d_h;
+  p.ent = c->d_ent;
+  p.il_node = c->d_il_node;
+  p.il_cnt = c->d_il_cnt;
+  p.str_slot = c->d_str_slot;
+  p.le = c->d_le;
+  p.ring = c->d_ring;
+  p.src_global = c->d_src_global;
+  p.src_table = c->d_src_table;
+  p.n_sources = (int32_t)c->n_sources;
+  p.err = c->d_err;
+  p.rec = rs.rec;
+  p.rec_pos = rs.pos;
+  p.rec_rows = rs.rows;
+  p.rec_row0 = rs.row0;
+  p.rec_decim = rs.decim;
+  p.n_rec = rs.n_rec;
+  p.wait_budget_ns = c->wait_budget_ns;
+  p.hold_sub = c->hold_sub;
+  for (int64_t done = 0; done < n_steps; done += chunk) {
+    const int64_t len = std::min(chunk, n_steps - done);
+    SourceParams sp{};
+    sp.n_sources = (int32_t)c->n_sources;
+    sp.amp = c->d_src_amp;
+    sp.phase = c->d_src_phase;
+    sp.omega = c->d_src_omega;
+    sp.dt = c->dt;
+    sp.n0 = c->step + 1;
+    sp.n_steps = len;
+    sp.table = c->d_src_table;
+    cudaError_t e = launch_sources(sp, st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n source table");
+    p.n0 = c->step + 1;
+    p.n_steps = len;
+    e = launch_forward(p, st);
+    if (e == cudaErrorCooperativeLaunchTooLarge)
+      return c->fail(EMT_ERESOURCE, "persistent launch of " + std::to_string(c->n_sub) +
+                                        " CTAs cannot be co-resident on this device");
+    if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n launch");
+    c->step += len;
+    c->launches += (c->n_sources > 0 ? 2 : 1);
+  }
+  return EMT_OK;
+}
+
+
 extern "C" emt_status emt_step_n(emt_ctx* c, int64_t n_steps, void* stream) {
   if (!c) return EMT_EINVAL;
   if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
@@ -1018,74 +1119,15 @@ extern "C" emt_status emt_step_n(emt_ctx* c, int64_t n_steps, void* stream) {
     c->launches += 1;
     return EMT_OK;
   }
-  if (forward_smem_bytes(c->lim) > 227 * 1024)
-    return c->fail(EMT_ERESOURCE, "a subsystem needs more shared memory than one CTA has");
-  // source table for one chunk of steps at a time (grow-only buffer)
-  const int64_t chunk =
-      std::min<int64_t>(n_steps, std::max<int64_t>(1, kSourceTableDoubles / std::max<int64_t>(c->n_sources, 1)));
-  if (c->src_table_steps < chunk) {
-    cudaStreamSynchronize(st);
-    c->release(c->d_src_table);
-    c->d_src_table = nullptr;
-    c->src_table_steps = 0;
-    cudaError_t e = c->alloc_zero(&c->d_src_table, (size_t)chunk * std::max<int64_t>(c->n_sources, 1));
-    if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n source table");
-    c->src_table_steps = chunk;
+  RecSpec rs;
+  if (!c->rec_channels.empty()) {
+    rs.rec = c->d_rec;
+    rs.pos = c->d_rec_pos;
+    rs.n_rec = (int32_t)c->rec_channels.size();
+    rs.decim = c->rec_decim;
+    rs.rows = c->rec_rows;
   }
-  FwdParams p{};
-  p.n_sub = c->n_sub;
-  p.lim = c->lim;
-  p.lim.n = std::max(p.lim.n, 1);
-  p.lim.nc = std::max(p.lim.nc, 1);
-  p.sub = c->d_sub;
-  p.ep = c->d_ep;
-  p.ginv = c->d_ginv;
-  p.ginv_lo = c->d_ginv_lo;
-  p.br = c->d_br;
-  p.lc_idx = c->d_lc_idx;
-  p.sb_idx = c->d_sb_idx;
-  p.h = c->d_h;
-  p.ent = c->d_ent;
-  p.il_node = c->d_il_node;
-  p.il_cnt = c->d_il_cnt;
-  p.str_slot = c->d_str_slot;
-  p.le = c->d_le;
-  p.ring = c->d_ring;
-  p.src_global = c->d_src_global;
-  p.src_table = c->d_src_table;
-  p.n_sources = (int32_t)c->n_sources;
-  p.err = c->d_err;
-  p.rec = c->rec_channels.empty() ? nullptr : c->d_rec;
-  p.rec_pos = c->d_rec_pos;
-  p.rec_rows = c->rec_rows;
-  p.rec_decim = c->rec_decim;
-  p.n_rec = (int32_t)c->rec_channels.size();
-  p.wait_budget_ns = c->wait_budget_ns;
-  p.hold_sub = c->hold_sub;
-  for (int64_t done = 0; done < n_steps; done += chunk) {
-    const int64_t len = std::min(chunk, n_steps - done);
-    SourceParams sp{};
-    sp.n_sources = (int32_t)c->n_sources;
-    sp.amp = c->d_src_amp;
-    sp.phase = c->d_src_phase;
-    sp.omega = c->d_src_omega;
-    sp.dt = c->dt;
-    sp.n0 = c->step + 1;
-    sp.n_steps = len;
-    sp.table = c->d_src_table;
-    cudaError_t e = launch_sources(sp, st);
-    if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n source table");
-    p.n0 = c->step + 1;
-    p.n_steps = len;
-    e = launch_forward(p, st);
-    if (e == cudaErrorCooperativeLaunchTooLarge)
-      return c->fail(EMT_ERESOURCE, "persistent launch of " + std::to_string(c->n_sub) +
-                                        " CTAs cannot be co-resident on this device");
-    if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n launch");
-    c->step += len;
-    c->launches += (c->n_sources > 0 ? 2 : 1);
-  }
-  return EMT_OK;
+  return forward_steps(c, n_steps, st, rs);
 }
 
 extern "C" emt_status emt_sync(emt_ctx* c, int32_t* info) {
@@ -1174,6 +1216,10 @@ extern "C" emt_status emt_set_option(emt_ctx* c, const char* key, int64_t value)
     c->wait_budget_ns = (unsigned long long)value;
     return EMT_OK;
   }
+  if (k == "adjoint_overlap") {   // 0: the adjoint re-runs segments on the caller's stream only
+    c->overlap_adjoint = value != 0;
+    return EMT_OK;
+  }
   if (k == "debug_hold_lines") {   // failure-path tests: one subsystem never sends line values
     if (value < -1 || value >= c->n_sub) return c->fail(EMT_EINVAL, "debug_hold_lines out of range");
     c->hold_sub = (int32_t)value;
@@ -1199,6 +1245,8 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   } else if (k == "threads_per_cta") *value = kFwdThreads;
   else if (k == "kernel_launches") *value = c->launches;
   else if (k == "n_branches") *value = (int64_t)c->branches.size();
+  else if (k == "n_sources") *value = c->n_sources;
+  else if (k == "n_nodes") *value = c->n_nodes;
   else if (k == "n_line_ends") *value = (int64_t)c->line_ends.size();
   else if (k == "n_strong_branches") *value = (int64_t)c->str_slot.size();
   else if (k == "smem_bytes") *value = (int64_t)forward_smem_bytes(c->lim);
@@ -1220,6 +1268,285 @@ extern "C" void emt_destroy(emt_ctx* c) {
   for (void* p : c->allocations) cudaFree(p);
   c->allocations.clear();
   delete c;
+}
+
+// ---------------------------------------------------------------- adjoint
+//
+// Forward pass from the de-energised state, saving (h, line rings) before
+// every segment of K steps but the last; the last segment records its tape
+// v_n directly.  Reverse pass, segments last to first: restore the
+// segment's checkpoint, run it forward again recording the tape, then run
+// the reverse kernel over it.  K = 0 keeps the whole tape (one segment).
+extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_steps, int32_t ckpt_every,
+                                  double* grad, double* loss, int32_t on_device, void* stream) {
+  if (!c) return EMT_EINVAL;
+  if (c->batched) return c->fail(EMT_EINVAL, "emt_adjoint: a context built with a scenario set has no adjoint");
+  if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
+  if (n_steps < 1) return c->fail(EMT_EINVAL, "emt_adjoint: n_steps must be >= 1");
+  if (n_steps > (int64_t)INT32_MAX - (int64_t)(1 << 21))
+    return c->fail(EMT_EINVAL, "emt_adjoint: n_steps exceeds 2^31 - 2^21");
+  if (ckpt_every < 0) return c->fail(EMT_EINVAL, "emt_adjoint: ckpt_every must be >= 0");
+  if (!v_target) return c->fail(EMT_EINVAL, "emt_adjoint: v_target is NULL");
+  if (!grad && !loss) return c->fail(EMT_EINVAL, "emt_adjoint: grad and loss are both NULL");
+  AdjLimits al{};
+  al.n = std::max(c->lim.n, 1);
+  al.nc = std::max(c->lim.nc, 1);
+  al.q = c->lim.q;
+  for (const SubDev& sd : c->subs) al.br = std::max(al.br, sd.n_br);
+  al.lc = c->lim.lc;
+  al.sb = c->lim.sb;
+  al.le = c->lim.le;
+  al.src = c->lim.src;
+  al.il = c->lim.il;
+  if (adjoint_smem_bytes(al) > 227 * 1024)
+    return c->fail(EMT_ERESOURCE, "emt_adjoint: a subsystem needs more shared memory than one CTA has");
+  emt_status rs0 = emt_reset(c);
+  if (rs0 != EMT_OK) return rs0;
+  if (c->n_sub == 0) {
+    if (grad) {
+      if (on_device) cudaMemset(grad, 0, (size_t)(c->n_branches + c->n_sources) * sizeof(double));
+      else std::fill(grad, grad + c->n_branches + c->n_sources, 0.0);
+    }
+    if (loss) *loss = 0.0;
+    return EMT_OK;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t N = n_steps, nn = c->n_nodes, ns = c->n_sources, nbr = (int64_t)c->branches.size();
+  const int64_t K = ckpt_every > 0 ? std::min<int64_t>(ckpt_every, N) : N;
+  const int64_t n_seg = (N + K - 1) / K;
+  const int64_t n_lc = std::max<int64_t>(c->n_lc_total, 1);
+  const int64_t ring_words = 2 * std::max<int64_t>(c->ring_len, 1);
+  const int T = adjoint_threads();
+
+  // The forward re-run of segment j-1 overlaps the reverse sweep of
+  // segment j (second stream, two tapes) when both persistent grids fit on
+  // the device together: every SM holds at least min(per-SM residency) CTAs
+  // of either kernel, so 2 n_sub <= n_SM * that is enough.
+  bool overlap = false;
+  if (K < N) {
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    FwdLimits fl = c->lim;
+    fl.n = std::max(fl.n, 1);
+    fl.nc = std::max(fl.nc, 1);
+    const int m = std::min(forward_blocks_per_sm(fl), adjoint_blocks_per_sm(al));
+    overlap = m > 0 && 2 * (int64_t)c->n_sub <= (int64_t)n_sm * m && c->overlap_adjoint;
+  }
+  std::vector<void*> mine;   // this call's buffers, released before returning
+  const double* d_tgt = v_target;
+  double *d_tgt_copy = nullptr, *d_sin = nullptr, *d_ones = nullptr, *d_ck_h = nullptr, *d_tape = nullptr;
+  double *d_hbar = nullptr, *d_dg = nullptr, *d_dsrc = nullptr, *d_lp = nullptr, *d_grad = grad, *d_loss = nullptr;
+  unsigned long long *d_ck_ring = nullptr, *d_aring = nullptr;
+  int32_t* d_pos = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {
+    e = c->alloc_zero(&d_tgt_copy, (size_t)(N * nn));
+    if (e == cudaSuccess) {
+      mine.push_back(d_tgt_copy);
+      e = cudaMemcpyAsync(d_tgt_copy, v_target, (size_t)(N * nn) * sizeof(double), cudaMemcpyHostToDevice, st);
+    }
+    d_tgt = d_tgt_copy;
+  }
+#define ADJ_ALLOC(ptr, count) \
+  if (e == cudaSuccess) {     \
+    e = c->alloc_zero(&ptr, (size_t)(count)); \
+    if (e == cudaSuccess) mine.push_back(ptr); \
+  }
+  ADJ_ALLOC(d_sin, std::max<int64_t>(N * ns, 1))
+  ADJ_ALLOC(d_ones, std::max<int64_t>(ns, 1))
+  ADJ_ALLOC(d_ck_h, std::max<int64_t>((n_seg - 1) * n_lc, 1))
+  ADJ_ALLOC(d_ck_ring, std::max<int64_t>((n_seg - 1) * ring_words, 1))
+  ADJ_ALLOC(d_tape, (overlap ? 2 : 1) * K * nn)
+  ADJ_ALLOC(d_aring, ring_words)
+  ADJ_ALLOC(d_hbar, n_lc)
+  ADJ_ALLOC(d_dg, std::max<int64_t>(nbr, 1))
+  ADJ_ALLOC(d_dsrc, std::max<int64_t>(nbr, 1))
+  ADJ_ALLOC(d_lp, (int64_t)c->n_sub * T)
+  ADJ_ALLOC(d_loss, 1)
+  if (!on_device || !grad) ADJ_ALLOC(d_grad, nbr + ns)
+#undef ADJ_ALLOC
+  if (e == cudaSuccess) {
+    std::vector<int32_t> pos(nn);
+    std::iota(pos.begin(), pos.end(), 0);
+    e = c->upload(&d_pos, pos);
+    if (e == cudaSuccess) mine.push_back(d_pos);
+  }
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(st);
+    for (void* p : mine) c->release(p);
+  };
+  if (e != cudaSuccess) {
+    cleanup();
+    return c->cuda_fail(e, "emt_adjoint allocation");
+  }
+  // sin(omega t_n + phase) for n = 1..N: the source table with unit amplitudes
+  if (ns > 0) {
+    std::vector<double> ones(ns, 1.0);
+    e = cudaMemcpyAsync(d_ones, ones.data(), ns * sizeof(double), cudaMemcpyHostToDevice, st);
+    SourceParams sp{};
+    sp.n_sources = (int32_t)ns;
+    sp.amp = d_ones;
+    sp.phase = c->d_src_phase;
+    sp.omega = c->d_src_omega;
+    sp.dt = c->dt;
+    sp.n0 = 1;
+    sp.n_steps = N;
+    sp.table = d_sin;
+    if (e == cudaSuccess) e = launch_sources(sp, st);
+    if (e == cudaSuccess) cudaStreamSynchronize(st);   // ones[] leaves scope
+    c->launches += 1;
+  }
+  if (e != cudaSuccess) {
+    cleanup();
+    return c->cuda_fail(e, "emt_adjoint sin table");
+  }
+  auto tape_of = [&](int64_t j) { return d_tape + (overlap ? (j & 1) : 0) * K * nn; };
+  auto tape_spec = [&](int64_t j, int64_t seg0, int64_t len) {
+    RecSpec r;
+    r.rec = tape_of(j);
+    r.pos = d_pos;
+    r.n_rec = (int32_t)nn;
+    r.decim = 1;
+    r.rows = seg0 + len;
+    r.row0 = seg0;
+    return r;
+  };
+  // forward pass with checkpoints
+  emt_status stt = EMT_OK;
+  for (int64_t j = 0; j < n_seg && stt == EMT_OK; ++j) {
+    const int64_t s0 = j * K, len = std::min(K, N - s0);
+    if (j < n_seg - 1) {
+      e = cudaMemcpyAsync(d_ck_h + j * n_lc, c->d_h, n_lc * sizeof(double), cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_ck_ring + j * ring_words, c->d_ring, ring_words * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) break;
+    }
+    stt = forward_steps(c, len, st, j == n_seg - 1 ? tape_spec(j, s0, len) : RecSpec());
+  }
+  // reverse pass
+  if (e == cudaSuccess && stt == EMT_OK)
+    e = launch_ring_init(RingInitParams{c->d_le, (int64_t)c->line_ends.size(), d_aring}, st);
+  AdjParams a{};
+  a.n_sub = c->n_sub;
+  a.lim = al;
+  a.sub = c->d_sub;
+  a.ep = c->d_ep;
+  a.ginv = c->d_ginv;
+  a.ginv_lo = c->d_ginv_lo;
+  a.br = c->d_br;
+  a.br_lc = c->d_br_lc;
+  a.lc_idx = c->d_lc_idx;
+  a.ent = c->d_ent;
+  a.il_node = c->d_il_node;
+  a.il_cnt = c->d_il_cnt;
+  a.str_slot = c->d_str_slot;
+  a.le = c->d_le;
+  a.ring = d_aring;
+  a.src_global = c->d_src_global;
+  a.src_amp = c->d_src_amp;
+  a.sin_table = d_sin;
+  a.n_sources = (int32_t)ns;
+  a.target = d_tgt;
+  a.orig_of = c->d_original_of;
+  a.n_nodes = nn;
+  a.hbar = d_hbar;
+  a.dg = d_dg;
+  a.dsrc = d_dsrc;
+  a.loss_part = d_lp;
+  a.err = c->d_err;
+  a.n_total = N;
+  a.wait_budget_ns = c->wait_budget_ns;
+  // Re-run of segment j from its checkpoint, recording its tape, on `rs`.
+  auto rerun = [&](int64_t j, cudaStream_t rs) -> emt_status {
+    const int64_t s0 = j * K, len = std::min(K, N - s0);
+    e = cudaMemcpyAsync(c->d_h, d_ck_h + j * n_lc, n_lc * sizeof(double), cudaMemcpyDeviceToDevice, rs);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->d_ring, d_ck_ring + j * ring_words, ring_words * sizeof(unsigned long long),
+                          cudaMemcpyDeviceToDevice, rs);
+    if (e != cudaSuccess) return c->cuda_fail(e, "emt_adjoint checkpoint restore");
+    c->step = s0;
+    return forward_steps(c, len, rs, tape_spec(j, s0, len));
+  };
+  // Host order of the overlapped schedule (each event is recorded before
+  // any wait on it is enqueued):
+  //   st:  ... reverse(j) [waits rerun_done(j)], records rev_done(j)
+  //   st2: rerun(j-1) [waits rev_done(j+1), the last user of its tape], records rerun_done(j-1)
+  cudaStream_t st2 = nullptr;
+  cudaEvent_t ev_fwd = nullptr, ev_rerun[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
+  if (overlap && e == cudaSuccess && stt == EMT_OK) {
+    e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_fwd, cudaEventDisableTiming);
+    for (int q = 0; q < 2 && e == cudaSuccess; ++q) {
+      e = cudaEventCreateWithFlags(&ev_rerun[q], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_rev[q], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev_fwd, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st2, ev_fwd, 0);
+  }
+  for (int64_t j = n_seg - 1; j >= 0 && e == cudaSuccess && stt == EMT_OK; --j) {
+    const int64_t s0 = j * K, len = std::min(K, N - s0);
+    if (j < n_seg - 1) {
+      if (overlap) {
+        e = cudaStreamWaitEvent(st, ev_rerun[j & 1], 0);
+      } else {
+        stt = rerun(j, st);
+      }
+      if (e != cudaSuccess || stt != EMT_OK) break;
+    }
+    a.tape = tape_of(j);
+    a.tape_row0 = s0;
+    a.n_hi = s0 + len;
+    a.n_steps = len;
+    e = launch_adjoint(a, st);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+      stt = c->fail(EMT_ERESOURCE, "adjoint launch of " + std::to_string(c->n_sub) +
+                                       " CTAs cannot be co-resident on this device");
+      break;
+    }
+    c->launches += 1;
+    if (overlap && e == cudaSuccess) e = cudaEventRecord(ev_rev[j & 1], st);
+    if (overlap && e == cudaSuccess && j >= 1) {
+      if (j + 1 <= n_seg - 1) e = cudaStreamWaitEvent(st2, ev_rev[(j + 1) & 1], 0);
+      if (e == cudaSuccess) stt = rerun(j - 1, st2);
+      if (e == cudaSuccess && stt == EMT_OK) e = cudaEventRecord(ev_rerun[(j - 1) & 1], st2);
+    }
+  }
+  if (st2) {
+    cudaStreamSynchronize(st2);
+    cudaStreamDestroy(st2);
+  }
+  if (ev_fwd) cudaEventDestroy(ev_fwd);
+  for (int q = 0; q < 2; ++q) {
+    if (ev_rerun[q]) cudaEventDestroy(ev_rerun[q]);
+    if (ev_rev[q]) cudaEventDestroy(ev_rev[q]);
+  }
+  if (e == cudaSuccess && stt == EMT_OK) {
+    e = launch_adj_finalize(c->d_br, c->d_br_orig, c->d_br_src, nbr, d_dg, d_dsrc, ns, c->dt, d_lp,
+                            (int64_t)c->n_sub * T, d_grad, d_loss, st);
+    c->launches += 1;
+  }
+  double h_loss = 0.0;
+  if (e == cudaSuccess && stt == EMT_OK) {
+    if (grad && !on_device)
+      e = cudaMemcpyAsync(grad, d_grad, (size_t)(nbr + ns) * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_loss, d_loss, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  cleanup();
+  if (stt != EMT_OK) return stt;
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_adjoint");
+  int32_t info[4] = {0, 0, 0, 0};
+  e = cudaMemcpy(info, c->d_err, sizeof(info), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_adjoint");
+  if (info[0] == EMT_ETIMEOUT)
+    return c->fail(EMT_ETIMEOUT, "emt_adjoint: subsystem " + std::to_string(info[1]) + " timed out at tag " +
+                                     std::to_string(info[3]) + " waiting for the value of its line end " +
+                                     std::to_string(info[2]));
+  if (info[0] != 0) return c->fail((emt_status)info[0], "emt_adjoint: device error");
+  if (loss) *loss = h_loss;
+  return emt_reset(c);
 }
 
 // ------------------------------------------------------------------ no-alloc prefactor

@@ -1,0 +1,46 @@
+// Device helpers shared by the persistent kernels (forward and adjoint).
+#pragma once
+#include <stdint.h>
+
+#include <cuda_runtime.h>
+
+#include "emt_internal.h"
+
+namespace emt {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
+
+// Tagged ring slot: two words (tag << 32) | low / high half of the double,
+// written and read as one 16-byte single-copy-atomic access each.
+__device__ __forceinline__ void st_tagged(unsigned long long* p, unsigned tag, double v) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long w0 = ((unsigned long long)tag << 32) | (bits & 0xffffffffull);
+  const unsigned long long w1 = ((unsigned long long)tag << 32) | (bits >> 32);
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(w0), "l"(w1) : "memory");
+}
+
+__device__ __forceinline__ bool ld_tagged(const unsigned long long* p, unsigned tag, double& v) {
+  unsigned long long w0, w1;
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(w0), "=l"(w1) : "l"(p) : "memory");
+  if ((unsigned)(w0 >> 32) != tag || (unsigned)(w1 >> 32) != tag) return false;
+  v = __longlong_as_double((long long)((w1 << 32) | (w0 & 0xffffffffull)));
+  return true;
+}
+
+// Signed injection entry (see kEntryNeg): the input value with the entry's
+// sign bit applied; line-end entries are shifted to the current parity block.
+__device__ __forceinline__ double signed_entry(const double* inp, unsigned raw, int ie_base, int n_le, int parshift) {
+  int idx = (int)(raw & ~kEntryNeg);
+  if ((unsigned)(idx - ie_base) < (unsigned)n_le) idx += parshift;
+  const unsigned long long bits =
+      (unsigned long long)__double_as_longlong(inp[idx]) ^ ((unsigned long long)(raw & kEntryNeg) << 32);
+  return __longlong_as_double((long long)bits);
+}
+
+}  // namespace emt

@@ -123,9 +123,10 @@ struct FwdParams {
   const double* src_table;     // [n_steps][n_sources]: v_src(t_{n0+i})
   int32_t n_sources;
   int32_t* err;                // [4]: code, subsystem, line end, step
-  double* rec;                 // [rows][n_rec]
+  double* rec;                 // [rows][n_rec], row r at rec + (r - rec_row0) * n_rec
   const int32_t* rec_pos;      // per internal node: column in rec, or -1
-  int64_t rec_rows;
+  int64_t rec_rows;            // rows below this are written
+  int64_t rec_row0;            // first row held by rec (0 for a whole recording)
   int32_t rec_decim;
   int32_t n_rec;
   int64_t n0;                  // first step of this launch
@@ -202,6 +203,52 @@ struct BatchParams {
   double dt;
 };
 
+// Per-launch upper bounds that size the adjoint kernel's shared memory.
+struct AdjLimits {
+  int32_t n, nc, q, br, lc, sb, le, src, il;
+};
+
+// Reverse sweep of the discrete adjoint over steps n = n_hi, n_hi - 1, ...,
+// n_hi - n_steps + 1 (one CTA per subsystem, like the forward kernel).
+// Adjoint line values travel through tagged rings with the forward's slot
+// layout; the tag of step n is n_total + 1 - n, so tags grow as the sweep
+// runs backwards in time and the forward's de-energised ring start serves
+// as the adjoint's zero final condition.
+struct AdjParams {
+  int32_t n_sub;
+  AdjLimits lim;
+  const SubDev* sub;
+  const EpochDev* ep;
+  const double* ginv;
+  const float* ginv_lo;
+  const BranchDev* br;
+  const int32_t* br_lc;        // per branch: subsystem-local L/C slot, or -1
+  const int32_t* lc_idx;
+  const int32_t* ent;
+  const int32_t* il_node;
+  const int32_t* il_cnt;
+  const int32_t* str_slot;
+  const LineEndDev* le;
+  unsigned long long* ring;    // adjoint rings
+  const int32_t* src_global;
+  const double* src_amp;       // per global source
+  const double* sin_table;     // [n_total][n_sources]: sin(omega t_n + phase), row n - 1
+  int32_t n_sources;
+  const double* tape;          // [rows][n_nodes] internal order: v_n in row n - 1 - tape_row0
+  int64_t tape_row0;
+  const double* target;        // [n_total][n_nodes] caller's node order: v*_n in row n - 1
+  const int32_t* orig_of;      // internal node -> caller's node
+  int64_t n_nodes;
+  double* hbar;                // per L/C slot: adjoint of h (carried across launches)
+  double* dg;                  // per branch: dJ/dg accumulated
+  double* dsrc;                // per branch: dJ/dA of its source accumulated
+  double* loss_part;           // [n_sub][threads]: partial sums of (v - v*)^2
+  int32_t* err;
+  int64_t n_total;
+  int64_t n_hi, n_steps;
+  unsigned long long wait_budget_ns;
+};
+
 struct SourceParams {
   int32_t n_sources;
   const double* amp;           // per global source
@@ -225,9 +272,17 @@ cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st);
 cudaError_t launch_sources(const SourceParams& p, cudaStream_t st);
 cudaError_t launch_forward(const FwdParams& p, cudaStream_t st);
 size_t forward_smem_bytes(const FwdLimits& lim);
+int forward_blocks_per_sm(const FwdLimits& lim);   // resident CTAs per SM (0 on error)
 cudaError_t launch_batch(const BatchParams& p, cudaStream_t st);
 size_t batch_smem_bytes(const BatchParams& p);
 int batch_threads();
+cudaError_t launch_adjoint(const AdjParams& p, cudaStream_t st);
+size_t adjoint_smem_bytes(const AdjLimits& lim);
+int adjoint_blocks_per_sm(const AdjLimits& lim);
+int adjoint_threads();
+cudaError_t launch_adj_finalize(const BranchDev* br, const int32_t* br_orig, const int32_t* br_src, int64_t n_br,
+                                const double* dg, const double* dsrc, int64_t n_sources, double dt,
+                                const double* loss_part, int64_t n_loss, double* grad, double* loss, cudaStream_t st);
 cudaError_t launch_gather(const double* rec, int32_t n_rec, int64_t n_scen_rec, const int32_t* col, int64_t n_ch,
                           int64_t row0, int64_t n_rows, int64_t scen0, int64_t n_scen, double* out, cudaStream_t st);
 

@@ -31,18 +31,11 @@
 #include <cuda_runtime.h>
 
 #include "emt_internal.h"
+#include "emt_device.cuh"
 
 namespace emt {
 
 namespace {
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ int ld_volatile(const int* p) { return *reinterpret_cast<const volatile int*>(p); }
 
 // error-free transformations (Knuth TwoSum; TwoProd by FMA)
 __device__ __forceinline__ void two_sum(double a, double b, double& s, double& e) {
@@ -254,22 +247,6 @@ __global__ void source_kernel(SourceParams P) {
 
 // ------------------------------------------------------------ line rings
 
-// Tagged ring slot: two words (step << 32) | low / high half of the double.
-__device__ __forceinline__ void st_tagged(unsigned long long* p, unsigned tag, double v) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-  const unsigned long long w0 = ((unsigned long long)tag << 32) | (bits & 0xffffffffull);
-  const unsigned long long w1 = ((unsigned long long)tag << 32) | (bits >> 32);
-  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(w0), "l"(w1) : "memory");
-}
-
-__device__ __forceinline__ bool ld_tagged(const unsigned long long* p, unsigned tag, double& v) {
-  unsigned long long w0, w1;
-  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(w0), "=l"(w1) : "l"(p) : "memory");
-  if ((unsigned)(w0 >> 32) != tag || (unsigned)(w1 >> 32) != tag) return false;
-  v = __longlong_as_double((long long)((w1 << 32) | (w0 & 0xffffffffull)));
-  return true;
-}
-
 // De-energised start: the slot consumed at step s (1 <= s <= d) holds 0
 // tagged s; every other slot holds tag 0, which no step matches.
 __global__ void ring_init_kernel(RingInitParams P) {
@@ -377,14 +354,6 @@ __device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int la
     rslot[e] = nx == ledepth[e] ? 0 : nx;
   }
   return __all_sync(0xffffffffu, ok);
-}
-
-__device__ __forceinline__ double signed_entry(const double* inp, unsigned raw, int ie_base, int n_le, int parshift) {
-  int idx = (int)(raw & ~kEntryNeg);
-  if ((unsigned)(idx - ie_base) < (unsigned)n_le) idx += parshift;
-  const unsigned long long bits =
-      (unsigned long long)__double_as_longlong(inp[idx]) ^ ((unsigned long long)(raw & kEntryNeg) << 32);
-  return __longlong_as_double((long long)bits);
 }
 
 __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
@@ -581,7 +550,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       vv[r] = v;
       if (rec_now) {
         const int pos = P.rec_pos[S.node_off + r];
-        if (pos >= 0) P.rec[rec_row * P.n_rec + pos] = v;
+        if (pos >= 0) P.rec[(rec_row - P.rec_row0) * P.n_rec + pos] = v;
       }
     }
     if (dec == 0) ++rec_row;
@@ -676,6 +645,15 @@ cudaError_t launch_sources(const SourceParams& p, cudaStream_t st) {
 }
 
 size_t forward_smem_bytes(const FwdLimits& lim) { return fwd_smem(lim).bytes; }
+
+int forward_blocks_per_sm(const FwdLimits& lim) {
+  const size_t smem = forward_smem_bytes(lim);
+  if (smem > 227 * 1024) return 0;
+  if (cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel, kFwdThreads, smem) != cudaSuccess) return 0;
+  return per_sm;
+}
 
 cudaError_t launch_forward(const FwdParams& p, cudaStream_t st) {
   const size_t smem = forward_smem_bytes(p.lim);

@@ -22,7 +22,7 @@ _STATUS = {0: "EMT_OK", 1: "EMT_EINVAL", 2: "EMT_ESINGULAR", 3: "EMT_ENOMEM", 4:
 # every function include/emt.h declares
 EXPORTS = ("emt_build_network", "emt_prefactor", "emt_set_recording", "emt_step_n", "emt_read_waveforms",
            "emt_reset", "emt_sync", "emt_set_option", "emt_get_info", "emt_get_node_order", "emt_last_error",
-           "emt_destroy", "emt_prefactor_noalloc")
+           "emt_destroy", "emt_prefactor_noalloc", "emt_adjoint")
 
 
 class EmtError(RuntimeError):
@@ -86,6 +86,7 @@ def load_library(build_if_needed: bool = True):
         "emt_set_option": [P, ctypes.c_char_p, I64],
         "emt_get_info": [P, ctypes.c_char_p, P],
         "emt_get_node_order": [P, P],
+        "emt_adjoint": [P, P, I64, I32, P, P, I32, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -239,6 +240,45 @@ def emt_read_waveforms(ctx: Ctx, channels, step0: int, n_rows: int, scen0: int =
     _check(ctx, lib.emt_read_waveforms(ctx.handle, ch.ctypes.data, int(ch.size), int(step0), int(n_rows),
                                        int(scen0), int(n_scen), ptr, on_device))
     return out
+
+
+def emt_adjoint(ctx: Ctx, v_target, n_steps: int, ckpt_every: int = 256, stream=None, grad=None):
+    """Loss J = sum_n ||v_n - v*_n||^2 over steps 1..n_steps and dJ/dp for
+    p = [branch values..., source amplitudes...] (include/emt.h).
+
+    ``v_target`` is [n_steps][n_nodes] float64: a numpy array (host path) or
+    a CUDA torch tensor (device path; the gradient is then a CUDA tensor,
+    written into ``grad`` if given).  Returns (loss, grad)."""
+    lib = load_library()
+    n_steps = int(n_steps)
+    shape = (n_steps, ctx.n_nodes)
+    if isinstance(v_target, np.ndarray):
+        tg = _arr(v_target, np.float64)
+        if tg.shape != shape:
+            raise ValueError(f"v_target must have shape {shape}")
+        n_par = _n_params(ctx)
+        g = np.zeros(n_par, dtype=np.float64) if grad is None else grad
+        if not isinstance(g, np.ndarray) or g.dtype != np.float64 or g.size != n_par or not g.flags.c_contiguous:
+            raise ValueError(f"grad must be a C-contiguous float64 array of {n_par} entries")
+        tptr, gptr, on_device = tg.ctypes.data, g.ctypes.data if g.size else None, 0
+    else:   # torch tensor on the device
+        import torch
+        if not v_target.is_cuda or v_target.dtype != torch.float64 or tuple(v_target.shape) != shape:
+            raise ValueError(f"v_target must be a CUDA float64 tensor of shape {shape}")
+        tg = v_target.contiguous()
+        n_par = _n_params(ctx)
+        g = torch.empty(n_par, dtype=torch.float64, device=tg.device) if grad is None else grad
+        if not g.is_cuda or g.dtype != torch.float64 or g.numel() != n_par or not g.is_contiguous():
+            raise ValueError(f"grad must be a contiguous CUDA float64 tensor of {n_par} entries")
+        tptr, gptr, on_device = tg.data_ptr(), g.data_ptr() if n_par else None, 1
+    loss = ctypes.c_double(0.0)
+    _check(ctx, lib.emt_adjoint(ctx.handle, tptr, n_steps, int(ckpt_every), gptr, ctypes.byref(loss), on_device,
+                                _stream_handle(stream)))
+    return loss.value, g
+
+
+def _n_params(ctx: Ctx) -> int:
+    return emt_get_info(ctx, "n_branches") + emt_get_info(ctx, "n_sources")
 
 
 def emt_reset(ctx: Ctx) -> None:
