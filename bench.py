@@ -11,7 +11,15 @@ de-energised state (emt_step_n), i.e. one pass of the whole hot path.
                   [--time-steps T] [--skip-extras]
 
 --time-steps shortens each run (for profiling small cases); --skip-extras
-leaves out the end-to-end leg, the CPU baseline and the parity check.
+leaves out the end-to-end leg, the CPU baseline, the parity check and the
+two further legs the metric names, reported as extra keys of the line:
+  "scenarios": multi-scenario throughput (scenario-steps/s) of the N-1 study
+      (1,024 scenarios of a 600-node network, 10,000 steps, one launch) and
+      of the shared-G study (4,096 scenarios of the large-scale network;
+      3,000 of its 10,000 steps timed, across the fault at step 2,500);
+  "adjoint": emt_adjoint time over the forward time for the gradient of
+      sum_n ||v_n - v*_n||^2 over 20,000 steps of the large-scale network
+      with checkpoints every 256 steps (and with the whole tape kept).
 
 N > 1 runs N independent replicas (the single-network path does not shard;
 see the design doc), launched by torch.distributed.run.  `--impl reference`
@@ -123,6 +131,116 @@ def cpu_baseline(net, n_steps: int):
     return {"value": net.n_nodes * n_steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"large-scale network, {n_steps} of the 50,000 steps, all nodes recorded, 1 thread",
             "seconds": round(dt, 3), "host_cores_available": os.cpu_count()}
+
+
+def scenario_leg(name, net, sc, n_steps, n_check, rec_channels, decim, warm_steps=500):
+    """Throughput of one multi-scenario study: one emt_step_n launch over all
+    scenarios, CUDA events on the launching stream, after a short warm-up
+    run; parity of `n_check` sampled scenarios against the oracle on the
+    recorded (decimated) rows."""
+    import torch
+    import oracle
+    from paper_1903_01081_b300 import emt
+    t0 = time.perf_counter()
+    sim = emt.Simulator(net, sc, n_steps=n_steps, channels=rec_channels, decim=decim)
+    build_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    sim.run(warm_steps, stream)
+    sim.sync()
+    sim.reset()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.run(n_steps, stream)
+    e1.record(stream)
+    sim.sync()
+    ms = e0.elapsed_time(e1)
+    S = sc.n_scenarios
+    flops_per_scen_step = 2.0 * sim.info("sum_n2")
+    rng = np.random.default_rng(7)
+    check = sorted(rng.choice(S, size=n_check, replace=False).tolist())
+    worst = 0.0
+    ch = np.arange(net.n_nodes) if rec_channels is None else np.asarray(rec_channels)
+    for s_ in check:
+        got = sim.waveforms(scen0=s_, n_scen=1)[:, 0, :]
+        ref = oracle.simulate(sc.expand(net, s_), n_steps, rec=ch)[decim - 1::decim]
+        worst = max(worst, float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))))
+    out = {"scenarios": S, "nodes": int(net.n_nodes), "time_steps": n_steps, "ms": ms,
+           "scenario_steps_per_s": S * n_steps / (ms / 1e3),
+           "node_steps_per_s": S * net.n_nodes * n_steps / (ms / 1e3),
+           "solve_gflops": flops_per_scen_step * S * n_steps / (ms / 1e3) / 1e9,
+           "solve_frac_of_fp64_peak": flops_per_scen_step * S * n_steps / (ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
+           "n_matrix_variants": sim.info("n_matrix_variants"), "scenarios_per_cta": sim.info("scenarios_per_cta"),
+           "build_prefactor_s": round(build_s, 3), "kernel_launches": 1,
+           "parity_rel_err_sampled": worst, "parity_scenarios": check,
+           "recorded": f"{len(ch)} nodes every {decim} steps"}
+    sim.close()
+    return out
+
+
+def scenario_legs():
+    from paper_1903_01081_b300 import netgen as g
+    net, sc = g.n1_contingency()
+    n1 = scenario_leg("n1", net, sc, 10000, 4, None, 100)
+    net, sc = g.shared_g()
+    sg = scenario_leg("shared_g", net, sc, 3000, 2, list(range(0, net.n_nodes, 50)), 10)
+    return {"n1_contingency": dict(workload="N-1: 600-node three-phase network, 40 subsystems, one connection "
+                                            "removed + three-phase fault at step 2,500 per scenario", **n1),
+            "shared_g": dict(workload="large-scale network, per-scenario source amplitude/phase and fault "
+                                      "resistance at step 2,500; 3,000 of 10,000 steps timed", **sg)}
+
+
+def adjoint_leg():
+    """emt_adjoint (loss + gradient for all branch values and source
+    amplitudes) over the forward run, 20,000 steps of the large-scale
+    network; wall time of the call (it allocates and synchronises)."""
+    import torch
+    from paper_1903_01081_b300 import emt, netgen as g
+    net = g.large_scale()
+    N = 20000
+    br, amp = g.adjoint_target(net, seed=1005)
+    pert = net.copy()
+    pert.br_value, pert.src_amp = br, amp
+    tsim = emt.Simulator(pert, n_steps=N)
+    tsim.run(N)
+    tsim.sync()
+    tgt = torch.empty((N, 1, net.n_nodes), dtype=torch.float64, device="cuda")
+    tsim.waveforms(out=tgt)
+    tsim.close()
+    tgt = tgt.view(N, net.n_nodes)
+    ctx = emt.emt_build_network(net)
+    emt.emt_prefactor(ctx)
+    stream = torch.cuda.current_stream()
+    fwd = []
+    for _ in range(3):
+        emt.emt_reset(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        emt.emt_step_n(ctx, N, stream)
+        e1.record(stream)
+        emt.emt_sync(ctx)
+        fwd.append(e0.elapsed_time(e1))
+    t_fwd = float(np.median(fwd))
+    res = {}
+    for K in (256, 0):
+        ts = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            J, _ = emt.emt_adjoint(ctx, tgt, N, K, stream)
+            torch.cuda.synchronize()
+            ts.append(1e3 * (time.perf_counter() - t0))
+        res[K] = float(np.median(ts))
+    emt.emt_destroy(ctx)
+    return {"workload": "gradient of sum_n ||v_n - v*_n||^2 over all 3,000 nodes of the large-scale network, "
+                        "20,000 steps, w.r.t. all branch values and source amplitudes",
+            "n_params": int(net.n_branches + net.n_sources), "forward_ms": t_fwd,
+            "adjoint_ms_ckpt256": res[256], "ratio_ckpt256": res[256] / t_fwd,
+            "adjoint_ms_full_tape": res[0], "ratio_full_tape": res[0] / t_fwd,
+            "timing": "wall time of the emt_adjoint call (allocations, forward with checkpoints, re-runs, reverse "
+                      "sweep, gradient copy) over the CUDA-event time of emt_step_n for the same 20,000 steps",
+            "loss": J}
 
 
 def run_reference(args):
@@ -272,6 +390,8 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
             "parity_rel_err_first_2000_steps": parity,
+            "scenarios": scenario_legs(),
+            "adjoint": adjoint_leg(),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
