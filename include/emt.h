@@ -156,7 +156,11 @@ emt_status emt_set_recording(emt_ctx* ctx, const int32_t* channels, int64_t n_ch
  * shared memory, and meets other subsystems only through the line rings,
  * whose slots carry the step they belong to (no grid barrier, no flags).
  * A wait for line values exceeding its time budget latches an error that
- * emt_sync or the next call returns. */
+ * emt_sync or the next call returns.
+ * With a scenario set the whole study advances in one launch of the
+ * multi-scenario kernel (one CTA per tile of scenarios, no waits between
+ * CTAs), issued through a CUDA graph that is built once per launch shape
+ * and whose kernel arguments are updated per call. */
 emt_status emt_step_n(emt_ctx* ctx, int64_t n_steps, void* cuda_stream);
 
 /* Copy recorded waveforms out.  channels: node ids that were recorded;
@@ -166,6 +170,17 @@ emt_status emt_step_n(emt_ctx* ctx, int64_t n_steps, void* cuda_stream);
  * out_on_device != 0 else host memory.  Synchronous. */
 emt_status emt_read_waveforms(emt_ctx* ctx, const int32_t* channels, int64_t n_ch, int64_t step0, int64_t n_rows,
                               int64_t scen0, int64_t n_scen, double* out, int32_t out_on_device);
+
+/* Pick the launch shape of the multi-scenario kernel by measurement: for
+ * scenarios per CTA S_t (about k CTAs per SM for k = 1..6, and the powers
+ * of two up to 32, where the subsystem groups fit in shared memory) and
+ * 256, 512 or 1024 threads per CTA, run `trial_steps` steps from the
+ * de-energised state on `cuda_stream` and keep the fastest.  Resets the
+ * context to step 0 afterwards.  A context without a scenario set has no
+ * tunable shape (EMT_OK, nothing changes).  The chosen shape is reported by
+ * emt_get_info ("scenarios_per_cta", "batch_threads"); it can also be set
+ * with emt_set_option.  Synchronous. */
+emt_status emt_autotune(emt_ctx* ctx, int64_t trial_steps, void* cuda_stream);
 
 /* Discrete adjoint: the loss J = sum_{n=1..N} sum_k (v_n[k] - v*_n[k])^2
  * over all node voltages of steps 1..N from the de-energised state, and
@@ -204,6 +219,9 @@ emt_status emt_reset(emt_ctx* ctx);
 emt_status emt_sync(emt_ctx* ctx, int32_t* dev_err_info);
 
 /* Tuning and debug knobs (key = value): "wait_budget_ns" (per wait),
+ * "batch_graph" (default 1: multi-scenario launches go through a CUDA
+ * graph; 0: straight to the stream), "scenarios_per_cta" and
+ * "batch_threads" (multi-scenario launch shape; see emt_autotune),
  * "adjoint_overlap" (default 1: emt_adjoint re-runs segment j-1 forward on
  * a second stream while the reverse sweep of segment j runs, when both
  * persistent grids fit on the device together; 0: one stream),
@@ -215,7 +233,10 @@ emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
  * "n_scenarios", "n_epochs_total", "sum_n2" (sum over subsystems of n_s^2),
  * "threads_per_cta", "kernel_launches", "n_nodes", "n_branches", "n_sources", "n_line_ends",
  * "smem_bytes" (dynamic shared memory per CTA of the persistent kernel),
- * "n_strong_branches" (L/C branches applied through extra solve columns). */
+ * "n_strong_branches" (L/C branches applied through extra solve columns),
+ * "n_matrix_variants", "scenarios_per_cta", "batch_threads", "batch_groups"
+ * (subsystem groups per step of the multi-scenario kernel),
+ * "graph_launches", "autotuned". */
 emt_status emt_get_info(const emt_ctx* ctx, const char* key, int64_t* value);
 
 /* Internal node order: perm[i] = original node id of internal slot i

@@ -122,9 +122,26 @@ struct emt_ctx {
   std::vector<int32_t> msel_mat;
   std::vector<int32_t> var_sub;                        // subsystem of each variant matrix
   std::vector<int32_t> rm_ptr_br, rm_br, rm_ptr_le, rm_le;
-  int64_t* d_msel_ptr = nullptr;
-  int64_t* d_msel_start = nullptr;
-  int32_t* d_msel_mat = nullptr;
+  // flat per-slot arrays of the multi-scenario kernel (see BatchParams)
+  std::vector<int32_t> b_col_code, b_node_sub, b_node_r, b_sub_nc, b_sub_col_off, b_ent_ptr, b_bent;
+  std::vector<int32_t> b_lc_nk, b_lc_nm, b_sb_src, b_le_nd, b_le_d1, b_ev_sub;
+  std::vector<double> b_lc_e, b_sb_g, b_le_y2;
+  std::vector<int8_t> b_lc_isl;
+  std::vector<int64_t> b_ev_ptr, b_ev_step, b_ev_off;
+  int32_t *d_col_code = nullptr, *d_node_sub = nullptr, *d_node_r = nullptr, *d_sub_nc = nullptr,
+          *d_sub_col_off = nullptr, *d_ent_ptr = nullptr, *d_bent = nullptr, *d_lc_nk = nullptr,
+          *d_lc_nm = nullptr, *d_sb_src = nullptr, *d_le_nd = nullptr, *d_le_d1 = nullptr, *d_ev_sub = nullptr;
+  double *d_lc_e = nullptr, *d_sb_g = nullptr, *d_le_y2 = nullptr, *d_src_ac = nullptr, *d_src_as = nullptr;
+  int8_t* d_lc_isl = nullptr;
+  int64_t *d_ev_ptr = nullptr, *d_ev_step = nullptr, *d_ev_off = nullptr;
+  // launch configuration: scenarios per CTA, threads, subsystem groups
+  int batch_threads = 512;
+  std::vector<BatchGroupDev> groups;
+  int max_cols = 0, max_nodes = 0;
+  BatchGroupDev* d_grp = nullptr;
+  BatchGraph graph;
+  bool use_graph = true;
+  bool tuned = false;
   int32_t* d_node_l0 = nullptr;
   int32_t* d_node_nl = nullptr;
   int64_t* d_le_bring = nullptr;
@@ -279,6 +296,58 @@ std::string validate_scenarios(const emt_network_desc* d, const emt_scenario_des
 // solve-matrix variant of each (deduplicated by content: subsystem, removed
 // branches and line ends, closed switches with their conductances), the
 // removal masks, per-scenario sources and the batched line rings.
+// Group consecutive subsystems so that one group's solve columns and nodes
+// fit in the multi-scenario kernel's shared memory for S_t scenarios per
+// CTA; upload the groups when `upload`.  False if one subsystem alone does
+// not fit.
+bool batch_configure(emt_ctx* c, int S_t, bool upload) {
+  const size_t fixed = batch_smem_bytes(S_t, (int)c->n_sources, c->n_sub, 0, 0);
+  if (fixed >= 227 * 1024) return false;
+  const size_t budget = 227 * 1024 - fixed - 16;
+  std::vector<BatchGroupDev> groups;
+  int max_cols = 0, max_nodes = 0;
+  int s0 = 0;
+  while (s0 < c->n_sub) {
+    int s1 = s0, cols = 0, nodes = 0;
+    while (s1 < c->n_sub) {
+      const SubDev& sd = c->subs[s1];
+      const int nc2 = cols + sd.n + sd.n_str, n2 = nodes + sd.n;
+      if (((size_t)nc2 * 12 + (size_t)n2 * 8) * S_t > budget) break;
+      cols = nc2;
+      nodes = n2;
+      ++s1;
+    }
+    if (s1 == s0) return false;
+    const SubDev& a = c->subs[s0];
+    const SubDev& b = c->subs[s1 - 1];
+    BatchGroupDev G{};
+    G.node0 = a.node_off;
+    G.node1 = b.node_off + b.n;
+    G.col0 = c->b_sub_col_off[s0];
+    G.col1 = c->b_sub_col_off[s1 - 1] + b.n + b.n_str;
+    G.lc0 = a.lc_off;
+    G.lc1 = b.lc_off + b.n_lc;
+    G.le0 = a.le_off;
+    G.le1 = b.le_off + b.n_le;
+    groups.push_back(G);
+    max_cols = std::max(max_cols, cols);
+    max_nodes = std::max(max_nodes, nodes);
+    s0 = s1;
+  }
+  if (!upload) return true;
+  if (c->d_grp) {
+    cudaDeviceSynchronize();
+    c->release(c->d_grp);
+    c->d_grp = nullptr;
+  }
+  if (c->upload(&c->d_grp, groups) != cudaSuccess) return false;
+  c->groups = groups;
+  c->max_cols = std::max(max_cols, 1);
+  c->max_nodes = std::max(max_nodes, 1);
+  c->S_t = S_t;
+  return true;
+}
+
 std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_scenario_desc* sc,
                             const std::vector<int>& local, const std::vector<int32_t>& new_of_orig,
                             const std::vector<int64_t>& le_of_end, const std::vector<int32_t>& lc_slot_of,
@@ -432,11 +501,86 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
   c->bring_len = off;
   c->max_nc = 1;
   for (const SubDev& sd : c->subs) c->max_nc = std::max(c->max_nc, sd.n + sd.n_str);
-  c->S_t = 1;
-  while (c->S_t < 32 && S / (2 * c->S_t) >= 128) c->S_t *= 2;
-  auto smem = [&](int st) { return (double)nsrc * st * 8 + (double)c->max_nc * st * 20; };
-  while (c->S_t > 1 && smem(c->S_t) > 200.0 * 1024) c->S_t /= 2;
-  if (smem(c->S_t) > 200.0 * 1024) return "network too large for the multi-scenario kernel's shared memory";
+
+  // flat per-slot arrays (global numbering of columns, lanes and slots)
+  if (c->lc_idx.size() >= kBentIndexMask || c->sb_idx.size() >= kBentIndexMask ||
+      c->line_ends.size() >= kBentIndexMask)
+    return "too many element slots for the multi-scenario kernel";
+  const int N = (int)c->original_of.size();
+  c->b_node_sub.assign(N, 0);
+  c->b_node_r.assign(N, 0);
+  c->b_ent_ptr.assign(1, 0);
+  int64_t col = 0;
+  for (int q = 0; q < nsub; ++q) {
+    const SubDev& sd = c->subs[q];
+    const int nc = sd.n + sd.n_str;
+    c->b_sub_nc.push_back(nc);
+    if (col + nc > INT32_MAX / 2) return "too many solve columns";
+    c->b_sub_col_off.push_back((int32_t)col);
+    const int ie_base = sd.n_lc + sd.n_sb;
+    for (int k = 0; k < sd.n; ++k) {
+      c->b_col_code.push_back(sd.node_off + k);
+      c->b_node_sub[sd.node_off + k] = q;
+      c->b_node_r[sd.node_off + k] = k;
+      // the node's entries in lane order, padding left out
+      const int l0 = c->node_l0[sd.node_off + k], nl = c->node_nl[sd.node_off + k];
+      for (int l = l0; l < l0 + nl; ++l)
+        for (int u = 0; u < 4; ++u) {
+          const uint32_t raw = (uint32_t)c->ent[4 * (size_t)(sd.il_off + l) + u];
+          const int idx = (int)(raw & ~kEntryNeg);
+          uint32_t code;
+          if (idx < sd.n_lc) code = (0u << kBentKindShift) | (uint32_t)(sd.lc_off + idx);
+          else if (idx < ie_base) code = (1u << kBentKindShift) | (uint32_t)(sd.sb_off + idx - sd.n_lc);
+          else if (idx < ie_base + sd.n_le) code = (2u << kBentKindShift) | (uint32_t)(sd.le_off + idx - ie_base);
+          else continue;
+          c->b_bent.push_back((int32_t)(code | (raw & kEntryNeg)));
+        }
+      c->b_ent_ptr.push_back((int32_t)c->b_bent.size());
+    }
+    for (int t = 0; t < sd.n_str; ++t) c->b_col_code.push_back(-1 - (sd.lc_off + c->str_slot[sd.str_off + t]));
+    col += nc;
+    auto gnode = [&](int16_t x) -> int32_t {
+      if (x >= 0) return sd.node_off + x;
+      if (x == -1) return -1;
+      return -2 - c->src_global[sd.src_off + (-2 - x)];
+    };
+    for (int x = 0; x < sd.n_lc; ++x) {
+      const BranchDev& b = c->branches[c->lc_idx[sd.lc_off + x]];
+      c->b_lc_nk.push_back(gnode(b.k));
+      c->b_lc_nm.push_back(gnode(b.m));
+      c->b_lc_isl.push_back(b.kind == 1 ? 1 : 0);
+    }
+    for (int x = 0; x < sd.n_sb; ++x) {
+      const BranchDev& b = c->branches[c->sb_idx[sd.sb_off + x]];
+      c->b_sb_src.push_back(c->src_global[sd.src_off + (b.k <= -2 ? -2 - b.k : -2 - b.m)]);
+    }
+    for (int e = 0; e < sd.n_le; ++e) {
+      const LineEndDev& L = c->line_ends[sd.le_off + e];
+      c->b_le_nd.push_back(sd.node_off + L.node);
+      c->b_le_d1.push_back(L.d + 1);
+      c->b_le_y2.push_back(L.y2);
+    }
+  }
+  // solve-matrix selections as per-scenario events sorted by step
+  c->b_ev_ptr.assign(1, 0);
+  for (int64_t q = 0; q < S; ++q) {
+    std::vector<std::array<int64_t, 3>> ev;   // (first step, subsystem, offset)
+    for (int k = 0; k < nsub; ++k)
+      for (int64_t x = c->msel_ptr[q * nsub + k]; x < c->msel_ptr[q * nsub + k + 1]; ++x)
+        ev.push_back({std::max<int64_t>(c->msel_start[x], 0), k, c->epochs[c->msel_mat[x]].ginv_off});
+    std::stable_sort(ev.begin(), ev.end(),
+                     [](const std::array<int64_t, 3>& a, const std::array<int64_t, 3>& b) { return a[0] < b[0]; });
+    for (auto& x : ev) {
+      c->b_ev_step.push_back(x[0]);
+      c->b_ev_sub.push_back((int32_t)x[1]);
+      c->b_ev_off.push_back(x[2]);
+    }
+    c->b_ev_ptr.push_back((int64_t)c->b_ev_step.size());
+  }
+  // default launch shape: about one CTA per SM
+  c->S_t = (int)std::min<int64_t>(32, std::max<int64_t>(1, (S + 147) / 148));
+  while (c->S_t > 1 && !batch_configure(c, c->S_t, false)) c->S_t = std::max(1, c->S_t / 2);
+  if (!batch_configure(c, c->S_t, false)) return "network too large for the multi-scenario kernel's shared memory";
   return "";
 }
 
@@ -828,7 +972,6 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   UP(d_br_lc, br_lc)
   UP(d_br_src, br_src)
   UP(d_original_of, original_of)
-#undef UP
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_h, (size_t)c->n_lc_total);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ring, 2 * (size_t)std::max<int64_t>(c->ring_len, 1));
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ginv, (size_t)c->ginv_len);
@@ -837,9 +980,24 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   if (e == cudaSuccess) e = c->upload(&c->d_node_l0, c->node_l0);
   if (e == cudaSuccess) e = c->upload(&c->d_node_nl, c->node_nl);
   if (c->batched) {
-    if (e == cudaSuccess) e = c->upload(&c->d_msel_ptr, c->msel_ptr);
-    if (e == cudaSuccess) e = c->upload(&c->d_msel_start, c->msel_start);
-    if (e == cudaSuccess) e = c->upload(&c->d_msel_mat, c->msel_mat);
+    UP(d_col_code, b_col_code)
+    UP(d_node_sub, b_node_sub)
+    UP(d_node_r, b_node_r)
+    UP(d_sub_nc, b_sub_nc)
+    UP(d_sub_col_off, b_sub_col_off)
+    UP(d_ent_ptr, b_ent_ptr)
+    UP(d_bent, b_bent)
+    UP(d_lc_nk, b_lc_nk)
+    UP(d_lc_nm, b_lc_nm)
+    UP(d_lc_isl, b_lc_isl)
+    UP(d_sb_src, b_sb_src)
+    UP(d_le_nd, b_le_nd)
+    UP(d_le_d1, b_le_d1)
+    UP(d_le_y2, b_le_y2)
+    UP(d_ev_ptr, b_ev_ptr)
+    UP(d_ev_step, b_ev_step)
+    UP(d_ev_sub, b_ev_sub)
+    UP(d_ev_off, b_ev_off)
     if (e == cudaSuccess) e = c->upload(&c->d_le_bring, c->le_bring);
     if (e == cudaSuccess) e = c->upload(&c->d_le_bfar, c->le_bfar);
     if (e == cudaSuccess) e = c->upload(&c->d_bsrc_amp, c->bsrc_amp);
@@ -855,8 +1013,20 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     }
     if (e == cudaSuccess) e = c->alloc_zero(&c->d_bh, (size_t)c->n_lc_total * c->S);
     if (e == cudaSuccess) e = c->alloc_zero(&c->d_bring, (size_t)std::max<int64_t>(c->bring_len, 1) * c->S);
+    if (e == cudaSuccess) e = c->alloc_zero(&c->d_src_ac, (size_t)c->S * c->n_sources);
+    if (e == cudaSuccess) e = c->alloc_zero(&c->d_src_as, (size_t)c->S * c->n_sources);
+    if (e == cudaSuccess) e = c->alloc_zero(&c->d_lc_e, (size_t)c->lc_idx.size());
+    if (e == cudaSuccess) e = c->alloc_zero(&c->d_sb_g, (size_t)c->sb_idx.size());
   }
+#undef UP
+  if (e == cudaSuccess && c->batched && !batch_configure(c, c->S_t, true)) e = cudaErrorMemoryAllocation;
   if (e == cudaSuccess) e = launch_companion(c->d_br, (int64_t)c->branches.size(), c->dt, nullptr);
+  if (e == cudaSuccess && c->batched)
+    e = launch_source_coefficients(c->d_bsrc_amp, c->d_bsrc_phase, c->S * c->n_sources, c->d_src_ac, c->d_src_as,
+                                   nullptr);
+  if (e == cudaSuccess && c->batched)
+    e = launch_slot_constants(c->d_br, c->d_lc_idx, (int64_t)c->lc_idx.size(), c->d_sb_idx, (int64_t)c->sb_idx.size(),
+                              c->d_lc_e, c->d_sb_g, nullptr);
   if (e == cudaSuccess) e = launch_ring_init(RingInitParams{c->d_le, (int64_t)c->line_ends.size(), c->d_ring}, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -988,6 +1158,60 @@ struct RecSpec {
   int64_t row0 = 0;
 };
 
+// The one multi-scenario launch for steps n0 .. n0 + n_steps - 1.
+static cudaError_t batch_launch(emt_ctx* c, int64_t n0, int64_t n_steps, cudaStream_t st, bool record) {
+  BatchParams b{};
+  b.n_sub = c->n_sub;
+  b.S = (int32_t)c->S;
+  b.S_t = c->S_t;
+  b.n_sources = (int32_t)c->n_sources;
+  b.n_groups = (int32_t)c->groups.size();
+  b.max_cols = c->max_cols;
+  b.max_nodes = c->max_nodes;
+  b.grp = c->d_grp;
+  b.ginv = c->d_ginv;
+  b.ginv_lo = c->d_ginv_lo;
+  b.col_code = c->d_col_code;
+  b.node_sub = c->d_node_sub;
+  b.node_r = c->d_node_r;
+  b.sub_nc = c->d_sub_nc;
+  b.sub_col_off = c->d_sub_col_off;
+  b.ent_ptr = c->d_ent_ptr;
+  b.bent = c->d_bent;
+  b.lc_nk = c->d_lc_nk;
+  b.lc_nm = c->d_lc_nm;
+  b.lc_e = c->d_lc_e;
+  b.lc_isl = c->d_lc_isl;
+  b.sb_g = c->d_sb_g;
+  b.sb_src = c->d_sb_src;
+  b.le_nd = c->d_le_nd;
+  b.le_d1 = c->d_le_d1;
+  b.le_y2 = c->d_le_y2;
+  b.le_bring = c->d_le_bring;
+  b.le_bfar = c->d_le_bfar;
+  b.ev_ptr = c->d_ev_ptr;
+  b.ev_step = c->d_ev_step;
+  b.ev_sub = c->d_ev_sub;
+  b.ev_off = c->d_ev_off;
+  b.src_ac = c->d_src_ac;
+  b.src_as = c->d_src_as;
+  b.src_omega = c->d_src_omega;
+  b.keep_lc = c->d_keep_lc;
+  b.keep_sb = c->d_keep_sb;
+  b.keep_le = c->d_keep_le;
+  b.h = c->d_bh;
+  b.ring = c->d_bring;
+  b.rec = record ? c->d_rec : nullptr;
+  b.rec_pos = c->d_rec_pos;
+  b.rec_rows = c->rec_rows;
+  b.rec_decim = c->rec_decim;
+  b.n_rec = (int32_t)c->rec_channels.size();
+  b.n0 = n0;
+  b.n_steps = n_steps;
+  b.dt = c->dt;
+  return launch_batch(b, c->batch_threads, st, c->use_graph ? &c->graph : nullptr);
+}
+
 // Single-network forward run of n_steps steps from the context's step.
 static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, const RecSpec& rs) {
   if (forward_smem_bytes(c->lim) > 227 * 1024)
@@ -1073,47 +1297,7 @@ extern "C" emt_status emt_step_n(emt_ctx* c, int64_t n_steps, void* stream) {
     return c->fail(EMT_EINVAL, "recording capacity exceeded: raise max_rows in emt_set_recording");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (c->batched) {
-    BatchParams b{};
-    b.n_sub = c->n_sub;
-    b.S = (int32_t)c->S;
-    b.S_t = c->S_t;
-    b.n_sources = (int32_t)c->n_sources;
-    b.max_nc = c->max_nc;
-    b.sub = c->d_sub;
-    b.ep = c->d_ep;
-    b.ginv = c->d_ginv;
-    b.ginv_lo = c->d_ginv_lo;
-    b.msel_ptr = c->d_msel_ptr;
-    b.msel_start = c->d_msel_start;
-    b.msel_mat = c->d_msel_mat;
-    b.br = c->d_br;
-    b.lc_idx = c->d_lc_idx;
-    b.sb_idx = c->d_sb_idx;
-    b.ent = c->d_ent;
-    b.node_l0 = c->d_node_l0;
-    b.node_nl = c->d_node_nl;
-    b.str_slot = c->d_str_slot;
-    b.le = c->d_le;
-    b.le_bring = c->d_le_bring;
-    b.le_bfar = c->d_le_bfar;
-    b.src_global = c->d_src_global;
-    b.src_amp = c->d_bsrc_amp;
-    b.src_phase = c->d_bsrc_phase;
-    b.src_omega = c->d_src_omega;
-    b.keep_lc = c->d_keep_lc;
-    b.keep_sb = c->d_keep_sb;
-    b.keep_le = c->d_keep_le;
-    b.h = c->d_bh;
-    b.ring = c->d_bring;
-    b.rec = c->rec_channels.empty() ? nullptr : c->d_rec;
-    b.rec_pos = c->d_rec_pos;
-    b.rec_rows = c->rec_rows;
-    b.rec_decim = c->rec_decim;
-    b.n_rec = (int32_t)c->rec_channels.size();
-    b.n0 = c->step + 1;
-    b.n_steps = n_steps;
-    b.dt = c->dt;
-    cudaError_t e = launch_batch(b, st);
+    cudaError_t e = batch_launch(c, c->step + 1, n_steps, st, !c->rec_channels.empty());
     if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n multi-scenario launch");
     c->step += n_steps;
     c->launches += 1;
@@ -1208,12 +1392,85 @@ extern "C" emt_status emt_reset(emt_ctx* c) {
   return EMT_OK;
 }
 
+extern "C" emt_status emt_autotune(emt_ctx* c, int64_t trial_steps, void* stream) {
+  if (!c) return EMT_EINVAL;
+  if (trial_steps < 1) return c->fail(EMT_EINVAL, "emt_autotune: trial_steps must be >= 1");
+  if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
+  if (!c->batched) {   // the single-network kernel's shape is fixed by the partition
+    c->tuned = true;
+    return EMT_OK;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  // scenarios per CTA: about k CTAs per SM for k = 1..6, and powers of two
+  std::set<int> cand;
+  for (int k = 1; k <= 6; ++k)
+    cand.insert((int)std::min<int64_t>(32, std::max<int64_t>(1, (c->S + (int64_t)n_sm * k - 1) / ((int64_t)n_sm * k))));
+  for (int p2 = 1; p2 <= 32; p2 *= 2)
+    if (p2 <= c->S) cand.insert(p2);
+  const int threads[3] = {256, 512, 1024};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  int best_st = c->S_t, best_th = c->batch_threads;
+  for (int St : cand) {
+    if (!batch_configure(c, St, true)) continue;
+    for (int th : threads) {
+      c->batch_threads = th;
+      emt_status rs = emt_reset(c);
+      if (rs != EMT_OK) return rs;
+      cudaEventRecord(e0, st);
+      cudaError_t e = batch_launch(c, 1, trial_steps, st, false);
+      cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      c->launches += 1;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_st = St;
+        best_th = th;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!batch_configure(c, best_st, true)) return c->fail(EMT_ERESOURCE, "emt_autotune: no launch shape fits");
+  c->batch_threads = best_th;
+  c->tuned = true;
+  return emt_reset(c);
+}
+
 extern "C" emt_status emt_set_option(emt_ctx* c, const char* key, int64_t value) {
   if (!c || !key) return EMT_EINVAL;
   const std::string k(key);
   if (k == "wait_budget_ns") {
     if (value < 0) return c->fail(EMT_EINVAL, "wait_budget_ns must be >= 0");
     c->wait_budget_ns = (unsigned long long)value;
+    return EMT_OK;
+  }
+  if (k == "batch_graph") {   // 0: multi-scenario launches go straight to the stream, not through a graph
+    c->use_graph = value != 0;
+    return EMT_OK;
+  }
+  if (k == "scenarios_per_cta" || k == "batch_threads") {
+    if (!c->batched) return c->fail(EMT_EINVAL, k + " applies to a context built with a scenario set");
+    if (k == "batch_threads") {
+      if (value < 32 || value > batch_max_threads() || value % 32)
+        return c->fail(EMT_EINVAL, "batch_threads must be a multiple of 32 in [32, " +
+                                       std::to_string(batch_max_threads()) + "]");
+      c->batch_threads = (int)value;
+      return EMT_OK;
+    }
+    if (value < 1 || value > 1024 || !batch_configure(c, (int)value, true))
+      return c->fail(EMT_EINVAL, "scenarios_per_cta " + std::to_string(value) + " does not fit in shared memory");
     return EMT_OK;
   }
   if (k == "adjoint_overlap") {   // 0: the adjoint re-runs segments on the caller's stream only
@@ -1237,6 +1494,10 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "n_scenarios") *value = c->S;
   else if (k == "n_matrix_variants") *value = c->batched ? (int64_t)c->var_sub.size() : (int64_t)c->epochs.size();
   else if (k == "scenarios_per_cta") *value = c->batched ? c->S_t : 1;
+  else if (k == "batch_threads") *value = c->batched ? c->batch_threads : 0;
+  else if (k == "batch_groups") *value = c->batched ? (int64_t)c->groups.size() : 0;
+  else if (k == "graph_launches") *value = c->graph.launches;
+  else if (k == "autotuned") *value = c->tuned ? 1 : 0;
   else if (k == "n_epochs_total") *value = (int64_t)c->epochs.size();
   else if (k == "sum_n2") {
     int64_t s2 = 0;
@@ -1265,6 +1526,7 @@ extern "C" const char* emt_last_error(const emt_ctx* c) { return c ? c->err.c_st
 extern "C" void emt_destroy(emt_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
+  batch_graph_destroy(&c->graph);
   for (void* p : c->allocations) cudaFree(p);
   c->allocations.clear();
   delete c;

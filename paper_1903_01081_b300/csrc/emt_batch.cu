@@ -5,13 +5,18 @@
 // SIMT operation over all scenarios.  Here one CTA runs the whole network
 // for a tile of S_t scenarios; a warp's lanes are (item, scenario) with the
 // scenario fastest, so each solve-matrix entry a warp loads serves all its
-// scenarios (for a shared G^-1 the solve over the tile is a dense GEMM
-// G^-1 [i^(1) ... i^(S_t)], done with DFMA: on B300 FP64 DMMA is slower).
-// A scenario that changes a subsystem's G (an element removed, a switch
-// closed) selects its own prefactored matrix for that subsystem and
-// switch epoch.  Scenarios are independent, so CTAs never wait on each
-// other.  Per step and subsystem: injections, solve, updates, three
-// barriers; the work is FP64-throughput-bound, not latency-bound.
+// scenarios (for a shared G^-1 the solve over the tile is a dense product
+// G^-1 [i^(1) ... i^(S_t)], done with DFMA: on B300 the FP64 MMA path shares
+// the DFMA pipe and adds no throughput).  A scenario that changes a
+// subsystem's G (an element removed, a switch closed) selects its own
+// prefactored matrix for that subsystem from the step the change applies.
+// Scenarios are independent, so CTAs never wait on each other.
+//
+// Subsystems exchange values only through lines of delay >= 1, so within
+// one step all subsystems of a group run each process together: all
+// injections, then all solves, then all updates -- three barriers per
+// group and step, and thousands of independent items per phase to hide
+// the FP64 and memory latencies.
 //
 // Formulas as in emt_kernels.cu (trapezoidal companions, Bergeron lines;
 // the paper's Sec. III-A processes with the textbook forms of its ref. [2]).
@@ -27,138 +32,193 @@ namespace emt {
 
 namespace {
 
-constexpr int kBatchThreads = 512;
+constexpr int kBatchMaxThreads = 1024;
 
-__device__ __forceinline__ int mat_for(const BatchParams& P, int sigma, int s, long long step) {
-  const int64_t p0 = P.msel_ptr[(int64_t)sigma * P.n_sub + s], p1 = P.msel_ptr[(int64_t)sigma * P.n_sub + s + 1];
-  int m = P.msel_mat[p0];
-  for (int64_t x = p0 + 1; x < p1 && P.msel_start[x] <= step; ++x) m = P.msel_mat[x];
-  return m;
+// Ring slot of step `step` in a ring of depth d1 (steps stay below 2^31).
+__device__ __forceinline__ int64_t ring_slot(long long step, int d1) { return (int64_t)((unsigned)step % (unsigned)d1); }
+
+// Signed value of one batched injection entry for scenario sg (tile lane sl).
+__device__ __forceinline__ double entry_value(const BatchParams& P, uint32_t raw, int sg, int sl, long long step,
+                                              const double* vs) {
+  const uint32_t kind = (raw >> kBentKindShift) & 3u;
+  if (kind == 3u) return 0.0;
+  const int idx = (int)(raw & kBentIndexMask);
+  double val;
+  if (kind == 0u) {
+    val = P.h[(int64_t)idx * P.S + sg];
+  } else if (kind == 1u) {
+    val = __ldg(P.sb_g + idx) * vs[__ldg(P.sb_src + idx) * P.S_t + sl];
+    if (P.keep_sb && !P.keep_sb[(int64_t)idx * P.S + sg]) val = 0.0;
+  } else {
+    val = P.ring[(__ldg(P.le_bring + idx) + ring_slot(step, __ldg(P.le_d1 + idx))) * P.S + sg];
+  }
+  return (raw & kEntryNeg) ? -val : val;
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchParams P) {
+__global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int St = P.S_t;
   const int sigma0 = blockIdx.x * St;
   const int n_here = min(St, P.S - sigma0);   // scenarios of this tile
-  double* vs = reinterpret_cast<double*>(smem_raw);                  // [n_sources][St]
-  double* iv = vs + (size_t)P.n_sources * St;                        // [max_nc][St]
-  double* vv = iv + (size_t)P.max_nc * St;                           // [max_nc][St]
-  float* ivf = reinterpret_cast<float*>(vv + (size_t)P.max_nc * St); // [max_nc][St]
   const int T = blockDim.x, tid = threadIdx.x;
-  const int S = P.S;
+  const int S = P.S, n_sub = P.n_sub;
+  // item x = tid + i T of a phase is (x / St, x % St); both advance by
+  // (T / St, T % St) per iteration, so no phase loop divides
+  const int q0 = tid / St, r0 = tid - q0 * St, dq = T / St, dr = T - dq * St;
+  double* vs = reinterpret_cast<double*>(smem_raw);                      // [n_sources][St]
+  long long* cur = reinterpret_cast<long long*>(vs + (size_t)P.n_sources * St);   // [St][n_sub] matrix offsets
+  long long* evn = cur + (size_t)St * n_sub;                             // [St] next selection event
+  double* iv = reinterpret_cast<double*>(evn + St);                      // [max_cols][St]
+  double* vv = iv + (size_t)P.max_cols * St;                             // [max_nodes][St]
+  float* ivf = reinterpret_cast<float*>(vv + (size_t)P.max_nodes * St);  // [max_cols][St]
+  double* wsc = reinterpret_cast<double*>(ivf + (((size_t)P.max_cols * St + 1) & ~(size_t)1));   // [n_sources][2]
+
+  // solve matrices in force at the first step
+  for (int sl = tid; sl < n_here; sl += T) {
+    const int sg = sigma0 + sl;
+    int64_t x = P.ev_ptr[sg];
+    const int64_t x1 = P.ev_ptr[sg + 1];
+    for (; x < x1 && P.ev_step[x] <= P.n0; ++x) cur[(size_t)sl * n_sub + P.ev_sub[x]] = P.ev_off[x];
+    evn[sl] = x;
+  }
 
   const int decim = P.rec_decim > 0 ? P.rec_decim : 1;
   const long long n_end = P.n0 + P.n_steps;
   for (long long step = P.n0; step < n_end; ++step) {
     const double t = (double)step * P.dt;
-    // process 1 for sources: v_src(t_n) per scenario, argument (omega t) + phase
-    for (int x = tid; x < P.n_sources * St; x += T) {
-      const int src = x / St, sl = x - src * St;
+    // switch events of this step
+    for (int sl = tid; sl < n_here; sl += T) {
+      const int sg = sigma0 + sl;
+      int64_t x = evn[sl];
+      const int64_t x1 = P.ev_ptr[sg + 1];
+      if (x < x1 && P.ev_step[x] <= step) {
+        for (; x < x1 && P.ev_step[x] <= step; ++x) cur[(size_t)sl * n_sub + P.ev_sub[x]] = P.ev_off[x];
+        evn[sl] = x;
+      }
+    }
+    // process 1 for sources: v_src(t_n) = A sin(omega t + phase)
+    //   = (A cos phase) sin(omega t) + (A sin phase) cos(omega t),
+    // one sin/cos pair per source and step, two FP64 operations per scenario
+    for (int x = tid; x < P.n_sources; x += T) {
+      double sn, cs;
+      sincos(__dmul_rn(P.src_omega[x], t), &sn, &cs);
+      wsc[2 * x] = sn;
+      wsc[2 * x + 1] = cs;
+    }
+    __syncthreads();
+    for (int x = tid, src = q0, sl = r0; x < P.n_sources * St; x += T, src += dq, sl += dr) {
+      if (sl >= St) {
+        sl -= St;
+        ++src;
+      }
       if (sl < n_here) {
-        const int sg = sigma0 + sl;
-        vs[x] = P.src_amp[(int64_t)sg * P.n_sources + src] *
-                sin(__dadd_rn(__dmul_rn(P.src_omega[src], t), P.src_phase[(int64_t)sg * P.n_sources + src]));
+        const int64_t q = (int64_t)(sigma0 + sl) * P.n_sources + src;
+        vs[x] = fma(__ldg(P.src_ac + q), wsc[2 * src], __ldg(P.src_as + q) * wsc[2 * src + 1]);
       }
     }
     __syncthreads();
     const bool rec_now = P.rec != nullptr && step % decim == 0 && step / decim - 1 < P.rec_rows;
     const long long rec_row = step / decim - 1;
 
-    for (int s = 0; s < P.n_sub; ++s) {
-      const SubDev Sd = P.sub[s];
-      const int n = Sd.n, nc = n + Sd.n_str;
-      const int ie_base = Sd.n_lc + Sd.n_sb, zero_slot = ie_base + 2 * Sd.n_le;
+    for (int g = 0; g < P.n_groups; ++g) {
+      const BatchGroupDev G = P.grp[g];
 
       // process 2: nodal injections (and the strong-branch inputs -h)
-      for (int x = tid; x < nc * St; x += T) {
-        const int k = x / St, sl = x - k * St;
+      const int n_cols = G.col1 - G.col0;
+      for (int x = tid, c = q0, sl = r0; x < n_cols * St; x += T, c += dq, sl += dr) {
+        if (sl >= St) {
+          sl -= St;
+          ++c;
+        }
         if (sl >= n_here) continue;
         const int sg = sigma0 + sl;
+        const int code = __ldg(P.col_code + G.col0 + c);
         double acc = 0.0;
-        if (k < n) {
-          const int gk = Sd.node_off + k;
-          const int l0 = P.node_l0[gk], l1 = l0 + P.node_nl[gk];
-          for (int l = l0; l < l1; ++l)
-            for (int u = 0; u < 4; ++u) {
-              const unsigned raw = (unsigned)P.ent[4 * (int64_t)(Sd.il_off + l) + u];
-              const int idx = (int)(raw & ~kEntryNeg);
-              if (idx >= zero_slot) continue;
-              double val;
-              if (idx < Sd.n_lc) {
-                const int64_t gl = Sd.lc_off + idx;
-                val = P.h[gl * S + sg];
-              } else if (idx < ie_base) {
-                const int x2 = idx - Sd.n_lc;
-                const int64_t gs = Sd.sb_off + x2;
-                const BranchDev b = P.br[P.sb_idx[gs]];
-                const int j = b.k <= -2 ? -2 - b.k : -2 - b.m;
-                val = b.g * vs[P.src_global[Sd.src_off + j] * St + sl];
-                if (P.keep_sb && !P.keep_sb[gs * S + sg]) val = 0.0;
-              } else {
-                const int e = idx - ie_base;
-                const int64_t ge = Sd.le_off + e;
-                const LineEndDev L = P.le[ge];
-                val = P.ring[(P.le_bring[ge] + step % (L.d + 1)) * S + sg];
-              }
-              acc += (raw & kEntryNeg) ? -val : val;
-            }
+        if (code >= 0) {
+          const int e0 = __ldg(P.ent_ptr + code), e1 = __ldg(P.ent_ptr + code + 1);
+          if (e0 < e1) acc = entry_value(P, (uint32_t)__ldg(P.bent + e0), sg, sl, step, vs);
+          for (int e = e0 + 1; e < e1; ++e) acc += entry_value(P, (uint32_t)__ldg(P.bent + e), sg, sl, step, vs);
         } else {
-          const int64_t gl = Sd.lc_off + P.str_slot[Sd.str_off + (k - n)];
-          acc = -P.h[gl * S + sg];
+          acc = -P.h[(int64_t)(-1 - code) * S + sg];
         }
-        iv[k * St + sl] = acc;
-        ivf[k * St + sl] = (float)acc;
+        iv[x] = acc;
+        ivf[x] = (float)acc;
       }
       __syncthreads();
 
-      // process 4: v = (X_hi + X_lo) [i; -h_strong] with each scenario's matrix
-      for (int x = tid; x < n * St; x += T) {
-        const int r = x / St, sl = x - r * St;
+      // process 4: v = (X_hi + X_lo) [i; -h_strong], each scenario with its
+      // own solve matrix for the row's subsystem
+      const int n_nodes = G.node1 - G.node0;
+      for (int x = tid, k = q0, sl = r0; x < n_nodes * St; x += T, k += dq, sl += dr) {
+        if (sl >= St) {
+          sl -= St;
+          ++k;
+        }
         if (sl >= n_here) continue;
-        const int sg = sigma0 + sl;
-        const EpochDev E = P.ep[mat_for(P, sg, s, step)];
-        const double* row = P.ginv + E.ginv_off + (int64_t)r * nc;
-        const float* rowl = P.ginv_lo + E.ginv_off + (int64_t)r * nc;
+        const int node = G.node0 + k;
+        const int s = __ldg(P.node_sub + node), r = __ldg(P.node_r + node);
+        const int nc = __ldg(P.sub_nc + s);
+        const int cb = __ldg(P.sub_col_off + s) - G.col0;
+        const int64_t off = cur[(size_t)sl * n_sub + s] + (int64_t)r * nc;
+        const double* row = P.ginv + off;
+        const float* rowl = P.ginv_lo + off;
+        const double* ivc = iv + (size_t)cb * St + sl;
+        const float* ivfc = ivf + (size_t)cb * St + sl;
         double a = 0.0;
         float b = 0.f;
-        for (int j = 0; j < nc; ++j) {
-          a = fma(__ldg(row + j), iv[j * St + sl], a);
-          b = fmaf(__ldg(rowl + j), ivf[j * St + sl], b);
+        int j = 0;
+        // four row entries loaded ahead of their FMAs (same summation order)
+        for (; j + 4 <= nc; j += 4) {
+          const double x0 = __ldg(row + j), x1 = __ldg(row + j + 1), x2 = __ldg(row + j + 2), x3 = __ldg(row + j + 3);
+          const float y0 = __ldg(rowl + j), y1 = __ldg(rowl + j + 1), y2 = __ldg(rowl + j + 2), y3 = __ldg(rowl + j + 3);
+          a = fma(x0, ivc[(size_t)j * St], a);
+          b = fmaf(y0, ivfc[(size_t)j * St], b);
+          a = fma(x1, ivc[(size_t)(j + 1) * St], a);
+          b = fmaf(y1, ivfc[(size_t)(j + 1) * St], b);
+          a = fma(x2, ivc[(size_t)(j + 2) * St], a);
+          b = fmaf(y2, ivfc[(size_t)(j + 2) * St], b);
+          a = fma(x3, ivc[(size_t)(j + 3) * St], a);
+          b = fmaf(y3, ivfc[(size_t)(j + 3) * St], b);
+        }
+        for (; j < nc; ++j) {
+          a = fma(__ldg(row + j), ivc[(size_t)j * St], a);
+          b = fmaf(__ldg(rowl + j), ivfc[(size_t)j * St], b);
         }
         const double v = a + (double)b;
-        vv[r * St + sl] = v;
+        vv[x] = v;
         if (rec_now) {
-          const int pos = P.rec_pos[Sd.node_off + r];
-          if (pos >= 0) P.rec[(rec_row * S + sg) * P.n_rec + pos] = v;
+          const int pos = P.rec_pos[node];
+          if (pos >= 0) P.rec[(rec_row * S + sigma0 + sl) * P.n_rec + pos] = v;
         }
       }
       __syncthreads();
 
-      // process 1: history currents and line outputs of this subsystem
-      const int n_items = Sd.n_lc + Sd.n_le;
-      for (int x = tid; x < n_items * St; x += T) {
-        const int it = x / St, sl = x - it * St;
+      // process 1: history currents and line outputs of the group
+      const int n_lc = G.lc1 - G.lc0, n_items = n_lc + (G.le1 - G.le0);
+      for (int x = tid, it = q0, sl = r0; x < n_items * St; x += T, it += dq, sl += dr) {
+        if (sl >= St) {
+          sl -= St;
+          ++it;
+        }
         if (sl >= n_here) continue;
         const int sg = sigma0 + sl;
-        if (it < Sd.n_lc) {
-          const int64_t gl = Sd.lc_off + it;
-          if (P.keep_lc && !P.keep_lc[gl * S + sg]) continue;   // removed: h stays 0
-          const BranchDev b = P.br[P.lc_idx[gl]];
-          const double vk = b.k >= 0 ? vv[b.k * St + sl]
-                                     : (b.k == -1 ? 0.0 : vs[P.src_global[Sd.src_off + (-2 - b.k)] * St + sl]);
-          const double vm = b.m >= 0 ? vv[b.m * St + sl]
-                                     : (b.m == -1 ? 0.0 : vs[P.src_global[Sd.src_off + (-2 - b.m)] * St + sl]);
-          const double hv = P.h[gl * S + sg];
-          P.h[gl * S + sg] = b.kind == 1 ? fma(b.e, vk - vm, hv) : fma(b.e, vk - vm, -hv);
+        if (it < n_lc) {
+          const int gl = G.lc0 + it;
+          if (P.keep_lc && !P.keep_lc[(int64_t)gl * S + sg]) continue;   // removed: h stays 0
+          const int nk = __ldg(P.lc_nk + gl), nm = __ldg(P.lc_nm + gl);
+          const double vk = nk >= 0 ? vv[(size_t)(nk - G.node0) * St + sl] : (nk == -1 ? 0.0 : vs[(-2 - nk) * St + sl]);
+          const double vm = nm >= 0 ? vv[(size_t)(nm - G.node0) * St + sl] : (nm == -1 ? 0.0 : vs[(-2 - nm) * St + sl]);
+          const double e = __ldg(P.lc_e + gl);
+          double* hp = P.h + (int64_t)gl * S + sg;
+          const double hv = *hp;
+          *hp = __ldg(P.lc_isl + gl) ? fma(e, vk - vm, hv) : fma(e, vk - vm, -hv);
         } else {
-          const int e = it - Sd.n_lc;
-          const int64_t ge = Sd.le_off + e;
-          const LineEndDev L = P.le[ge];
-          const double ie = P.ring[(P.le_bring[ge] + step % (L.d + 1)) * S + sg];
-          double out = fma(-L.y2, vv[L.node * St + sl], -ie);
-          if (P.keep_le && !P.keep_le[ge * S + sg]) out = 0.0;   // removed line
-          P.ring[(P.le_bfar[ge] + (step + L.d) % (L.d + 1)) * S + sg] = out;
+          const int ge = G.le0 + (it - n_lc);
+          const int d1 = __ldg(P.le_d1 + ge);
+          const double ie = P.ring[(__ldg(P.le_bring + ge) + ring_slot(step, d1)) * S + sg];
+          double out = fma(-__ldg(P.le_y2 + ge), vv[(size_t)(__ldg(P.le_nd + ge) - G.node0) * St + sl], -ie);
+          if (P.keep_le && !P.keep_le[(int64_t)ge * S + sg]) out = 0.0;   // removed line
+          P.ring[(__ldg(P.le_bfar + ge) + ring_slot(step + d1 - 1, d1)) * S + sg] = out;
         }
       }
       __syncthreads();
@@ -166,23 +226,104 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batch_kernel(BatchParams P) 
   }
 }
 
-}  // namespace
-
-int batch_threads() { return kBatchThreads; }
-
-size_t batch_smem_bytes(const BatchParams& p) {
-  return (size_t)p.n_sources * p.S_t * sizeof(double) + 2 * (size_t)p.max_nc * p.S_t * sizeof(double) +
-         (size_t)p.max_nc * p.S_t * sizeof(float);
+// Per-slot constants of the multi-scenario kernel, gathered from the
+// companion conductances: e of each L/C slot, g of each source-branch slot.
+__global__ void slot_constants_kernel(const BranchDev* br, const int32_t* lc_idx, int64_t n_lc, const int32_t* sb_idx,
+                                      int64_t n_sb, double* lc_e, double* sb_g) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_lc + n_sb;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n_lc) lc_e[i] = br[lc_idx[i]].e;
+    else sb_g[i - n_lc] = br[sb_idx[i - n_lc]].g;
+  }
 }
 
-cudaError_t launch_batch(const BatchParams& p, cudaStream_t st) {
-  const size_t smem = batch_smem_bytes(p);
-  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+// A cos(phase), A sin(phase) per scenario and source (set-up, once).
+__global__ void source_coefficients_kernel(const double* amp, const double* phase, int64_t count, double* ac,
+                                           double* as) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    double sn, cs;
+    sincos(phase[i], &sn, &cs);
+    ac[i] = amp[i] * cs;
+    as[i] = amp[i] * sn;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_source_coefficients(const double* amp, const double* phase, int64_t count, double* ac, double* as,
+                                       cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((count + 255) / 256, 148 * 8);
+  source_coefficients_kernel<<<blocks, 256, 0, st>>>(amp, phase, count, ac, as);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slot_constants(const BranchDev* br, const int32_t* lc_idx, int64_t n_lc, const int32_t* sb_idx,
+                                  int64_t n_sb, double* lc_e, double* sb_g, cudaStream_t st) {
+  const int64_t total = n_lc + n_sb;
+  if (total <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 4);
+  slot_constants_kernel<<<blocks, 256, 0, st>>>(br, lc_idx, n_lc, sb_idx, n_sb, lc_e, sb_g);
+  return cudaGetLastError();
+}
+
+int batch_max_threads() { return kBatchMaxThreads; }
+
+size_t batch_smem_bytes(int S_t, int n_sources, int n_sub, int max_cols, int max_nodes) {
+  return (size_t)n_sources * S_t * 8 + (size_t)S_t * n_sub * 8 + (size_t)S_t * 8 + (size_t)max_nodes * S_t * 8 +
+         (((size_t)max_cols * S_t + 1) & ~(size_t)1) * 12 + (size_t)n_sources * 16;
+}
+
+void batch_graph_destroy(BatchGraph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  g->exec = nullptr;
+  g->graph = nullptr;
+  g->node = nullptr;
+}
+
+// One launch of batch_kernel over ceil(S / S_t) CTAs.  With `graph`, the
+// launch goes through a CUDA graph that is built once per launch shape and
+// whose kernel node gets this call's arguments.
+cudaError_t launch_batch(const BatchParams& p, int threads, cudaStream_t st, BatchGraph* graph) {
+  const size_t smem = batch_smem_bytes(p.S_t, p.n_sources, p.n_sub, p.max_cols, p.max_nodes);
+  if (smem > 227 * 1024 || threads < 32 || threads > kBatchMaxThreads || threads % 32) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = (p.S + p.S_t - 1) / p.S_t;
-  batch_kernel<<<grid, kBatchThreads, smem, st>>>(p);
-  return cudaGetLastError();
+  if (!graph) {
+    batch_kernel<<<grid, threads, smem, st>>>(p);
+    return cudaGetLastError();
+  }
+  BatchParams arg = p;
+  void* args[] = {&arg};
+  cudaKernelNodeParams kp{};
+  kp.func = (void*)batch_kernel;
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(threads);
+  kp.sharedMemBytes = (unsigned)smem;
+  kp.kernelParams = args;
+  if (graph->exec && (graph->grid != grid || graph->threads != threads || graph->smem != smem))
+    batch_graph_destroy(graph);
+  if (!graph->exec) {
+    e = cudaGraphCreate(&graph->graph, 0);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&graph->node, graph->graph, nullptr, 0, &kp);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&graph->exec, graph->graph, 0);
+    if (e != cudaSuccess) {
+      batch_graph_destroy(graph);
+      return e;
+    }
+    graph->grid = grid;
+    graph->threads = threads;
+    graph->smem = smem;
+  } else {
+    e = cudaGraphExecKernelNodeSetParams(graph->exec, graph->node, &kp);
+    if (e != cudaSuccess) return e;
+  }
+  e = cudaGraphLaunch(graph->exec, st);
+  if (e == cudaSuccess) graph->launches += 1;
+  return e;
 }
 
 }  // namespace emt

@@ -162,33 +162,60 @@ struct PrefParams {
 // Multi-scenario run (the paper's multi-scenario strategy, Sec. III-B):
 // one CTA per tile of S_t scenarios runs the whole network for them; a
 // warp's lanes are (item, scenario) with the scenario fastest, so every
-// solve-matrix load is shared by the scenarios of a warp.  Per-scenario
-// state is scenario-contiguous in global memory: h[lc][S], ring[slot][S]
-// (ring depth d+1: one CTA runs a scenario's subsystems in step order).
+// solve-matrix load is shared by the scenarios of a warp.  Subsystems meet
+// only through lines of delay >= 1, so within a step the subsystems of a
+// group are processed together: all injections, then all solves, then all
+// updates (three barriers per group and step).  Groups are consecutive
+// subsystems whose solve columns fit in shared memory.  Per-scenario state
+// is scenario-contiguous in global memory: h[lc][S], ring[slot][S] (ring
+// depth d+1: one CTA runs a scenario's subsystems in step order).
+//
+// Solve columns are numbered globally, subsystem by subsystem: column
+// sub_col_off[s] + k is node k of s for k < n, else its strong branch
+// k - n.  Batched injection entries name global slots: bits 29-30 the
+// kind (0 L/C slot, 1 source-branch slot, 2 line end, 3 none), bits 0-28
+// the index, bit 31 subtract.
+constexpr uint32_t kBentKindShift = 29;
+constexpr uint32_t kBentIndexMask = (1u << 29) - 1;
+
+struct BatchGroupDev {
+  int32_t node0, node1;        // internal nodes [node0, node1)
+  int32_t col0, col1;          // global solve columns
+  int32_t lc0, lc1;            // L/C slots
+  int32_t le0, le1;            // line ends
+};
+
 struct BatchParams {
   int32_t n_sub, S, S_t;       // subsystems, scenarios, scenarios per CTA
   int32_t n_sources;
-  int32_t max_nc;              // largest n + strong columns
-  const SubDev* sub;
-  const EpochDev* ep;          // solve matrices (variants) by index
+  int32_t n_groups, max_cols, max_nodes;
+  const BatchGroupDev* grp;
   const double* ginv;
   const float* ginv_lo;
-  const int64_t* msel_ptr;     // [S * n_sub + 1]: selections of (scenario, subsystem)
-  const int64_t* msel_start;   // first step of each selection
-  const int32_t* msel_mat;     // solve matrix (index into ep) of each selection
-  const BranchDev* br;
-  const int32_t* lc_idx;
-  const int32_t* sb_idx;
-  const int32_t* ent;          // injection entries (4 per injection lane)
-  const int32_t* node_l0;      // per internal node: first injection lane
-  const int32_t* node_nl;      // per internal node: number of injection lanes
-  const int32_t* str_slot;
-  const LineEndDev* le;
+  const int32_t* col_code;     // per global column: internal node, or -1 - L/C slot of a strong branch
+  const int32_t* node_sub;     // per internal node: subsystem
+  const int32_t* node_r;       // per internal node: row within its subsystem
+  const int32_t* sub_nc;       // per subsystem: solve columns n + n_str
+  const int32_t* sub_col_off;  // per subsystem: first global column
+  const int32_t* ent_ptr;      // [n_nodes + 1]: batched injection entries of each internal node
+  const int32_t* bent;         // batched injection entries (no padding)
+  const int32_t* lc_nk;        // per L/C slot: end k as internal node, -1 ground, -2-g source g
+  const int32_t* lc_nm;
+  const double* lc_e;          // history gain +2g (L) / -2g (C)
+  const int8_t* lc_isl;        // 1 for L, 0 for C
+  const double* sb_g;          // per source-branch slot: conductance
+  const int32_t* sb_src;       // per source-branch slot: global source
+  const int32_t* le_nd;        // per line end: internal node
+  const int32_t* le_d1;        // per line end: d + 1
+  const double* le_y2;         // per line end: 2 / Z_c
   const int64_t* le_bring;     // per line end: first slot of its own ring (depth d+1)
   const int64_t* le_bfar;      // per line end: first slot of the far end's ring
-  const int32_t* src_global;
-  const double* src_amp;       // [S][n_sources]
-  const double* src_phase;     // [S][n_sources]
+  const int64_t* ev_ptr;       // [S + 1]: solve-matrix selections per scenario, by step
+  const int64_t* ev_step;      // first step of the selection (0 for the initial one)
+  const int32_t* ev_sub;       // subsystem it applies to
+  const int64_t* ev_off;       // offset of its solve matrix in ginv / ginv_lo
+  const double* src_ac;        // [S][n_sources]: A cos(phase)
+  const double* src_as;        // [S][n_sources]: A sin(phase)
   const double* src_omega;     // [n_sources]
   const uint8_t* keep_lc;      // [n_lc][S] 1 = present (nullptr: all present)
   const uint8_t* keep_sb;      // [n_sb][S]
@@ -201,6 +228,17 @@ struct BatchParams {
   int32_t rec_decim, n_rec;
   int64_t n0, n_steps;
   double dt;
+};
+
+// A CUDA graph holding the one multi-scenario launch; its kernel node's
+// arguments are updated per call.
+struct BatchGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphNode_t node = nullptr;
+  int grid = 0, threads = 0;
+  size_t smem = 0;
+  int64_t launches = 0;
 };
 
 // Per-launch upper bounds that size the adjoint kernel's shared memory.
@@ -273,9 +311,14 @@ cudaError_t launch_sources(const SourceParams& p, cudaStream_t st);
 cudaError_t launch_forward(const FwdParams& p, cudaStream_t st);
 size_t forward_smem_bytes(const FwdLimits& lim);
 int forward_blocks_per_sm(const FwdLimits& lim);   // resident CTAs per SM (0 on error)
-cudaError_t launch_batch(const BatchParams& p, cudaStream_t st);
-size_t batch_smem_bytes(const BatchParams& p);
-int batch_threads();
+cudaError_t launch_batch(const BatchParams& p, int threads, cudaStream_t st, BatchGraph* graph);
+size_t batch_smem_bytes(int S_t, int n_sources, int n_sub, int max_cols, int max_nodes);
+int batch_max_threads();
+void batch_graph_destroy(BatchGraph* graph);
+cudaError_t launch_source_coefficients(const double* amp, const double* phase, int64_t count, double* ac, double* as,
+                                       cudaStream_t st);
+cudaError_t launch_slot_constants(const BranchDev* br, const int32_t* lc_idx, int64_t n_lc, const int32_t* sb_idx,
+                                  int64_t n_sb, double* lc_e, double* sb_g, cudaStream_t st);
 cudaError_t launch_adjoint(const AdjParams& p, cudaStream_t st);
 size_t adjoint_smem_bytes(const AdjLimits& lim);
 int adjoint_blocks_per_sm(const AdjLimits& lim);

@@ -22,7 +22,7 @@ _STATUS = {0: "EMT_OK", 1: "EMT_EINVAL", 2: "EMT_ESINGULAR", 3: "EMT_ENOMEM", 4:
 # every function include/emt.h declares
 EXPORTS = ("emt_build_network", "emt_prefactor", "emt_set_recording", "emt_step_n", "emt_read_waveforms",
            "emt_reset", "emt_sync", "emt_set_option", "emt_get_info", "emt_get_node_order", "emt_last_error",
-           "emt_destroy", "emt_prefactor_noalloc", "emt_adjoint")
+           "emt_destroy", "emt_prefactor_noalloc", "emt_adjoint", "emt_autotune")
 
 
 class EmtError(RuntimeError):
@@ -87,6 +87,7 @@ def load_library(build_if_needed: bool = True):
         "emt_get_info": [P, ctypes.c_char_p, P],
         "emt_get_node_order": [P, P],
         "emt_adjoint": [P, P, I64, I32, P, P, I32, P],
+        "emt_autotune": [P, I64, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -279,6 +280,11 @@ def emt_adjoint(ctx: Ctx, v_target, n_steps: int, ckpt_every: int = 256, stream=
 
 def _n_params(ctx: Ctx) -> int:
     return emt_get_info(ctx, "n_branches") + emt_get_info(ctx, "n_sources")
+
+
+def emt_autotune(ctx: Ctx, trial_steps: int = 50, stream=None) -> None:
+    """Measure the multi-scenario launch shapes and keep the fastest (include/emt.h)."""
+    _check(ctx, load_library().emt_autotune(ctx.handle, int(trial_steps), _stream_handle(stream)))
 
 
 def emt_reset(ctx: Ctx) -> None:
