@@ -133,7 +133,7 @@ def cpu_baseline(net, n_steps: int):
             "seconds": round(dt, 3), "host_cores_available": os.cpu_count()}
 
 
-def scenario_leg(name, net, sc, n_steps, n_check, rec_channels, decim, warm_steps=500):
+def scenario_leg(name, net, sc, n_steps, n_check, rec_channels, decim, tune_steps, warm_steps=500):
     """Throughput of one multi-scenario study: one emt_step_n launch over all
     scenarios, CUDA events on the launching stream, after a short warm-up
     run; parity of `n_check` sampled scenarios against the oracle on the
@@ -145,6 +145,9 @@ def scenario_leg(name, net, sc, n_steps, n_check, rec_channels, decim, warm_step
     sim = emt.Simulator(net, sc, n_steps=n_steps, channels=rec_channels, decim=decim)
     build_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    emt.emt_autotune(sim.ctx, tune_steps, stream)
+    tune_s = time.perf_counter() - t0
     sim.run(warm_steps, stream)
     sim.sync()
     sim.reset()
@@ -172,7 +175,9 @@ def scenario_leg(name, net, sc, n_steps, n_check, rec_channels, decim, warm_step
            "solve_gflops": flops_per_scen_step * S * n_steps / (ms / 1e3) / 1e9,
            "solve_frac_of_fp64_peak": flops_per_scen_step * S * n_steps / (ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
            "n_matrix_variants": sim.info("n_matrix_variants"), "scenarios_per_cta": sim.info("scenarios_per_cta"),
-           "build_prefactor_s": round(build_s, 3), "kernel_launches": 1,
+           "threads_per_cta": sim.info("batch_threads"), "subsystem_groups": sim.info("batch_groups"),
+           "build_prefactor_s": round(build_s, 3), "autotune_s": round(tune_s, 3),
+           "autotune_trial_steps": tune_steps, "kernel_launches": 1, "launch": "one CUDA-graph launch",
            "parity_rel_err_sampled": worst, "parity_scenarios": check,
            "recorded": f"{len(ch)} nodes every {decim} steps"}
     sim.close()
@@ -182,9 +187,9 @@ def scenario_leg(name, net, sc, n_steps, n_check, rec_channels, decim, warm_step
 def scenario_legs():
     from paper_1903_01081_b300 import netgen as g
     net, sc = g.n1_contingency()
-    n1 = scenario_leg("n1", net, sc, 10000, 4, None, 100)
+    n1 = scenario_leg("n1", net, sc, 10000, 4, None, 100, 100)
     net, sc = g.shared_g()
-    sg = scenario_leg("shared_g", net, sc, 3000, 2, list(range(0, net.n_nodes, 50)), 10)
+    sg = scenario_leg("shared_g", net, sc, 3000, 2, list(range(0, net.n_nodes, 50)), 10, 20)
     return {"n1_contingency": dict(workload="N-1: 600-node three-phase network, 40 subsystems, one connection "
                                             "removed + three-phase fault at step 2,500 per scenario", **n1),
             "shared_g": dict(workload="large-scale network, per-scenario source amplitude/phase and fault "

@@ -83,3 +83,71 @@ def test_n1_full_size_sampled_scenarios():
     for s in check:
         ref = oracle.simulate(sc.expand(net, s), N)[9::10]
         assert rel_err(got[s], ref) <= TOL, s
+
+
+def run_shape(net, sc, N, shape=None, graph=True, autotune=0):
+    ctx = emt.emt_build_network(net, sc)
+    emt.emt_prefactor(ctx)
+    if not graph:
+        emt.emt_set_option(ctx, "batch_graph", 0)
+    if shape:
+        emt.emt_set_option(ctx, "scenarios_per_cta", shape[0])
+        emt.emt_set_option(ctx, "batch_threads", shape[1])
+    if autotune:
+        emt.emt_autotune(ctx, autotune)
+        assert emt.emt_get_info(ctx, "autotuned") == 1
+        assert emt.emt_get_info(ctx, "step") == 0
+    emt.emt_set_recording(ctx, None, 1, N)
+    emt.emt_step_n(ctx, N // 2)
+    emt.emt_step_n(ctx, N - N // 2)
+    emt.emt_sync(ctx)
+    w = emt.emt_read_waveforms(ctx, np.arange(net.n_nodes, dtype=np.int32), 1, N, 0, sc.n_scenarios)
+    info = {k: emt.emt_get_info(ctx, k) for k in ("scenarios_per_cta", "batch_threads", "batch_groups",
+                                                  "graph_launches")}
+    emt.emt_destroy(ctx)
+    return w, info
+
+
+def test_launch_shapes_graph_and_autotune_give_identical_results():
+    """Every (node, scenario) item runs the same arithmetic whatever the
+    tile, block size or launch route, so the results are bit-identical."""
+    net, sc = g.n1_contingency(seed=80, n_scenarios=45, n_buses=40, n_sub=8, n_lines=12, n_sources=3,
+                               n_steps=700, fault_step=300, target_branches=240)
+    N = 700
+    ref, info = run_shape(net, sc, N)
+    assert info["graph_launches"] == 2
+    for shape in ((1, 256), (3, 1024), (7, 512), (16, 256), (32, 1024)):
+        w, info = run_shape(net, sc, N, shape)
+        assert info["scenarios_per_cta"] == shape[0] and info["batch_threads"] == shape[1]
+        assert np.array_equal(w, ref), shape
+    w, info = run_shape(net, sc, N, graph=False)
+    assert info["graph_launches"] == 0 and np.array_equal(w, ref)
+    w, info = run_shape(net, sc, N, autotune=20)
+    assert np.array_equal(w, ref)
+    for s in (0, 22, 44):
+        assert rel_err(ref[:, s, :], oracle.simulate(sc.expand(net, s), N)) <= TOL, s
+
+
+def test_small_shared_memory_budget_splits_subsystems_into_groups():
+    # 32 scenarios per CTA of a 3,000-node network cannot hold one group
+    net, sc = g.shared_g(seed=94, n_scenarios=64, n_steps=300, fault_step=100)
+    N = 300
+    w, info = run_shape(net, sc, N, (32, 1024))
+    assert info["batch_groups"] > 1
+    for s in (0, 63):
+        assert rel_err(w[:, s, :], oracle.simulate(sc.expand(net, s), N)) <= TOL, s
+
+
+def test_launch_shape_options_are_checked():
+    net, sc = g.n1_contingency(seed=81, n_scenarios=4, n_buses=20, n_sub=4, n_lines=5, n_sources=2,
+                               n_steps=100, fault_step=50, target_branches=120)
+    ctx = emt.emt_build_network(net, sc)
+    for key, val in (("batch_threads", 100), ("batch_threads", 2048), ("scenarios_per_cta", 0)):
+        with pytest.raises(emt.EmtError) as ei:
+            emt.emt_set_option(ctx, key, val)
+        assert ei.value.status == emt.EMT_EINVAL
+    emt.emt_destroy(ctx)
+    ctx = emt.emt_build_network(g.single_rlc(n_steps=10))
+    with pytest.raises(emt.EmtError):
+        emt.emt_set_option(ctx, "scenarios_per_cta", 4)
+    emt.emt_destroy(ctx)
