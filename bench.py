@@ -8,7 +8,8 @@ benchmark "step" is one full run of those 50,000 time steps from the
 de-energised state (emt_step_n), i.e. one pass of the whole hot path.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--time-steps T] [--skip-extras]
+                  [--time-steps T] [--skip-extras] [--leg all|single|n1|shared_g|adjoint]
+                  [--leg-steps N] [--leg-warm N] [--shape S_t,threads]
 
 --time-steps shortens each run (for profiling small cases); --skip-extras
 leaves out the end-to-end leg, the CPU baseline, the parity check and the
@@ -46,7 +47,8 @@ METRIC = "node-steps/s and scenario-steps/s at 1 B300 (FP64, rel err ≤1e-10); 
 UNIT = "node-steps/s"
 N_STEPS = 50000
 FP64_PEAK_GFLOPS = 148 * 4 * 2.032          # 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (max SM clock)
-KERNEL_SOURCES = ["paper_1903_01081_b300/csrc/emt_kernels.cu", "paper_1903_01081_b300/csrc/emt_internal.h"]
+KERNEL_SOURCES = ["paper_1903_01081_b300/csrc/emt_kernels.cu", "paper_1903_01081_b300/csrc/emt_device.cuh",
+                  "paper_1903_01081_b300/csrc/emt_internal.h"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fwd_kernel_large_scale.json")
 
 
@@ -133,7 +135,7 @@ def cpu_baseline(net, n_steps: int):
             "seconds": round(dt, 3), "host_cores_available": os.cpu_count()}
 
 
-def scenario_leg(name, net, sc, n_steps, n_check, rec_channels, decim, tune_steps, warm_steps=500):
+def scenario_leg(name, net, sc, n_steps, n_check, rec_channels, decim, tune_steps, warm_steps=500, shape=None):
     """Throughput of one multi-scenario study: one emt_step_n launch over all
     scenarios, CUDA events on the launching stream, after a short warm-up
     run; parity of `n_check` sampled scenarios against the oracle on the
@@ -146,11 +148,16 @@ def scenario_leg(name, net, sc, n_steps, n_check, rec_channels, decim, tune_step
     build_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    emt.emt_autotune(sim.ctx, tune_steps, stream)
+    if shape:
+        emt.emt_set_option(sim.ctx, "scenarios_per_cta", shape[0])
+        emt.emt_set_option(sim.ctx, "batch_threads", shape[1])
+    else:
+        emt.emt_autotune(sim.ctx, tune_steps, stream)
     tune_s = time.perf_counter() - t0
-    sim.run(warm_steps, stream)
-    sim.sync()
-    sim.reset()
+    if warm_steps > 0:
+        sim.run(warm_steps, stream)
+        sim.sync()
+        sim.reset()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     flush.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -184,26 +191,31 @@ def scenario_leg(name, net, sc, n_steps, n_check, rec_channels, decim, tune_step
     return out
 
 
-def scenario_legs():
+def scenario_legs(which=("n1", "shared_g"), steps=None, shape=None, warm=500):
     from paper_1903_01081_b300 import netgen as g
-    net, sc = g.n1_contingency()
-    n1 = scenario_leg("n1", net, sc, 10000, 4, None, 100, 100)
-    net, sc = g.shared_g()
-    sg = scenario_leg("shared_g", net, sc, 3000, 2, list(range(0, net.n_nodes, 50)), 10, 20)
-    return {"n1_contingency": dict(workload="N-1: 600-node three-phase network, 40 subsystems, one connection "
-                                            "removed + three-phase fault at step 2,500 per scenario", **n1),
-            "shared_g": dict(workload="large-scale network, per-scenario source amplitude/phase and fault "
-                                      "resistance at step 2,500; 3,000 of 10,000 steps timed", **sg)}
+    out = {}
+    if "n1" in which:
+        net, sc = g.n1_contingency()
+        n1 = scenario_leg("n1", net, sc, steps or 10000, 4, None, 100, 100, warm, shape)
+        out["n1_contingency"] = dict(workload="N-1: 600-node three-phase network, 40 subsystems, one connection "
+                                              "removed + three-phase fault at step 2,500 per scenario", **n1)
+    if "shared_g" in which:
+        net, sc = g.shared_g()
+        sg = scenario_leg("shared_g", net, sc, steps or 3000, 2, list(range(0, net.n_nodes, 50)), 10, 20, warm,
+                          shape)
+        out["shared_g"] = dict(workload="large-scale network, per-scenario source amplitude/phase and fault "
+                                        "resistance at step 2,500; 3,000 of 10,000 steps timed", **sg)
+    return out
 
 
-def adjoint_leg():
+def adjoint_leg(steps=None, reps=3):
     """emt_adjoint (loss + gradient for all branch values and source
     amplitudes) over the forward run, 20,000 steps of the large-scale
     network; wall time of the call (it allocates and synchronises)."""
     import torch
     from paper_1903_01081_b300 import emt, netgen as g
     net = g.large_scale()
-    N = 20000
+    N = steps or 20000
     br, amp = g.adjoint_target(net, seed=1005)
     pert = net.copy()
     pert.br_value, pert.src_amp = br, amp
@@ -218,7 +230,7 @@ def adjoint_leg():
     emt.emt_prefactor(ctx)
     stream = torch.cuda.current_stream()
     fwd = []
-    for _ in range(3):
+    for _ in range(reps):
         emt.emt_reset(ctx)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -230,7 +242,7 @@ def adjoint_leg():
     res = {}
     for K in (256, 0):
         ts = []
-        for _ in range(3):
+        for _ in range(reps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             J, _ = emt.emt_adjoint(ctx, tgt, N, K, stream)
@@ -239,7 +251,7 @@ def adjoint_leg():
         res[K] = float(np.median(ts))
     emt.emt_destroy(ctx)
     return {"workload": "gradient of sum_n ||v_n - v*_n||^2 over all 3,000 nodes of the large-scale network, "
-                        "20,000 steps, w.r.t. all branch values and source amplitudes",
+                        f"{N:,} steps, w.r.t. all branch values and source amplitudes",
             "n_params": int(net.n_branches + net.n_sources), "forward_ms": t_fwd,
             "adjoint_ms_ckpt256": res[256], "ratio_ckpt256": res[256] / t_fwd,
             "adjoint_ms_full_tape": res[0], "ratio_full_tape": res[0] / t_fwd,
@@ -395,8 +407,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
             "parity_rel_err_first_2000_steps": parity,
-            "scenarios": scenario_legs(),
-            "adjoint": adjoint_leg(),
+            **({"scenarios": scenario_legs(), "adjoint": adjoint_leg()} if args.leg == "all" else {}),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -413,10 +424,31 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--time-steps", type=int, default=N_STEPS)
     ap.add_argument("--skip-extras", action="store_true")
+    ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint"], default="all",
+                    help="all: the JSON line with every leg; single: the single-network leg only; "
+                         "n1 / shared_g / adjoint: that leg alone (profiling)")
+    ap.add_argument("--leg-steps", type=int, default=None, help="time steps of a lone n1 / shared_g / adjoint leg")
+    ap.add_argument("--leg-warm", type=int, default=500, help="warm-up steps of a lone scenario leg")
+    ap.add_argument("--shape", default=None, help="S_t,threads for a lone scenario leg (no autotuning)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg in ("n1", "shared_g", "adjoint"):
+        return run_leg(args)
     return run_ours(args)
+
+
+def run_leg(args):
+    """One leg alone, one JSON line (for profiling small cases)."""
+    import torch
+    torch.cuda.set_device(dist_env()[2])
+    if args.leg == "adjoint":
+        out = adjoint_leg(args.leg_steps, reps=1)
+    else:
+        shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
+        out = scenario_legs((args.leg,), args.leg_steps, shape, args.leg_warm)
+    print(json.dumps({"leg": args.leg, **out}), flush=True)
+    return 0
 
 
 if __name__ == "__main__":
