@@ -427,30 +427,40 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
 
 // Chain rule to the element values and per-source sums, in a fixed order:
 //   dJ/dR = -dJ/dg / R^2,  dJ/dL = -dJ/dg dt / (2 L^2),  dJ/dC = dJ/dg 2 / dt
-//   dJ/dA_s = sum over branches b of source s (internal order) of dsrc[b]
-//   J = sum of the per-thread partial sums (CTA order, then thread order)
-__global__ void adj_finalize_kernel(const BranchDev* br, const int32_t* br_orig, const int32_t* br_src, int64_t n_br,
-                                    const double* dg, const double* dsrc, int64_t n_sources, double dt,
-                                    const double* loss_part, int64_t n_loss, double* grad, double* loss) {
-  const int64_t total = n_br + n_sources + 1;
+//   dJ/dA_s = sum over the branches of source s (internal order) of dsrc[b]
+__global__ void adj_finalize_kernel(const BranchDev* br, const int32_t* br_orig, int64_t n_br, const double* dg,
+                                    const double* dsrc, const int32_t* src_br_ptr, const int32_t* src_br,
+                                    int64_t n_sources, double dt, double* grad) {
+  const int64_t total = n_br + n_sources;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     if (i < n_br) {
       const BranchDev b = br[i];
       const double x = b.value;
       const double dgdp = b.kind == 0 ? -1.0 / (x * x) : (b.kind == 1 ? -dt / (2.0 * x * x) : 2.0 / dt);
       grad[br_orig[i]] = dg[i] * dgdp;
-    } else if (i < n_br + n_sources) {
-      const int32_t s = (int32_t)(i - n_br);
+    } else {
+      const int64_t s = i - n_br;
       double acc = 0.0;
-      for (int64_t b = 0; b < n_br; ++b)
-        if (br_src[b] == s) acc += dsrc[b];
+      for (int32_t j = src_br_ptr[s]; j < src_br_ptr[s + 1]; ++j) acc += dsrc[src_br[j]];
       grad[i] = acc;
-    } else if (loss) {
-      double acc = 0.0;
-      for (int64_t j = 0; j < n_loss; ++j) acc += loss_part[j];
-      *loss = acc;
     }
   }
+}
+
+// J = sum of the per-thread partial sums: strided partial sums per thread,
+// then a fixed pairwise tree (one block of kLossThreads threads).
+constexpr int kLossThreads = 512;
+__global__ void __launch_bounds__(kLossThreads) adj_loss_kernel(const double* part, int64_t n, double* loss) {
+  __shared__ double red[kLossThreads];
+  double acc = 0.0;
+  for (int64_t j = threadIdx.x; j < n; j += kLossThreads) acc += part[j];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = kLossThreads / 2; w > 0; w /= 2) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *loss = red[0];
 }
 
 }  // namespace
@@ -485,13 +495,18 @@ cudaError_t launch_adjoint(const AdjParams& p, cudaStream_t st) {
   return cudaLaunchCooperativeKernel((const void*)adj_kernel, dim3(p.n_sub), dim3(kAdjThreads), args, smem, st);
 }
 
-cudaError_t launch_adj_finalize(const BranchDev* br, const int32_t* br_orig, const int32_t* br_src, int64_t n_br,
-                                const double* dg, const double* dsrc, int64_t n_sources, double dt,
-                                const double* loss_part, int64_t n_loss, double* grad, double* loss, cudaStream_t st) {
-  const int64_t total = n_br + n_sources + 1;
-  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 4);
-  adj_finalize_kernel<<<blocks, 256, 0, st>>>(br, br_orig, br_src, n_br, dg, dsrc, n_sources, dt, loss_part, n_loss,
-                                              grad, loss);
+cudaError_t launch_adj_finalize(const BranchDev* br, const int32_t* br_orig, int64_t n_br, const double* dg,
+                                const double* dsrc, const int32_t* src_br_ptr, const int32_t* src_br, int64_t n_sources,
+                                double dt, const double* loss_part, int64_t n_loss, double* grad, double* loss,
+                                cudaStream_t st) {
+  const int64_t total = n_br + n_sources;
+  if (total > 0) {
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 148 * 4);
+    adj_finalize_kernel<<<blocks, 256, 0, st>>>(br, br_orig, n_br, dg, dsrc, src_br_ptr, src_br, n_sources, dt, grad);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  adj_loss_kernel<<<1, kLossThreads, 0, st>>>(loss_part, n_loss, loss);
   return cudaGetLastError();
 }
 

@@ -56,6 +56,7 @@ struct emt_ctx {
   std::vector<int32_t> br_orig;                        // internal branch -> caller's branch index
   std::vector<int32_t> br_lc;                          // internal branch -> subsystem-local L/C slot or -1
   std::vector<int32_t> br_src;                         // internal branch -> global source at one end or -1
+  std::vector<int32_t> src_br_ptr, src_br;             // per global source: its branches (CSR, internal order)
   std::vector<int32_t> src_global;                     // global source id per local source slot
   std::vector<double> src_amp, src_phase, src_omega;   // per global source
   std::vector<int32_t> nb_sub, nb_dmin;
@@ -80,6 +81,8 @@ struct emt_ctx {
   int32_t* d_br_orig = nullptr;
   int32_t* d_br_lc = nullptr;
   int32_t* d_br_src = nullptr;
+  int32_t* d_src_br_ptr = nullptr;
+  int32_t* d_src_br = nullptr;
   int32_t* d_original_of = nullptr;
   double* d_src_amp = nullptr;
   double* d_src_phase = nullptr;
@@ -730,6 +733,16 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     c->lim.src = std::max(c->lim.src, sd.n_src);
   }
   c->n_lc_total = (int64_t)c->lc_idx.size();
+  c->src_br_ptr.assign(d->n_sources + 1, 0);
+  for (int32_t s : c->br_src)
+    if (s >= 0) ++c->src_br_ptr[s + 1];
+  for (int64_t g = 0; g < d->n_sources; ++g) c->src_br_ptr[g + 1] += c->src_br_ptr[g];
+  c->src_br.assign(c->src_br_ptr[d->n_sources], 0);
+  {
+    std::vector<int32_t> fill(c->src_br_ptr.begin(), c->src_br_ptr.end() - 1);
+    for (size_t b = 0; b < c->br_src.size(); ++b)
+      if (c->br_src[b] >= 0) c->src_br[fill[c->br_src[b]]++] = (int32_t)b;
+  }
   if (c->branches.size() > (1u << 29)) return bail("too many branches");
   for (int64_t g = 0; g < d->n_sources; ++g) {
     c->src_amp.push_back(d->src_amp[g]);
@@ -971,6 +984,8 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   UP(d_br_orig, br_orig)
   UP(d_br_lc, br_lc)
   UP(d_br_src, br_src)
+  UP(d_src_br_ptr, src_br_ptr)
+  UP(d_src_br, src_br)
   UP(d_original_of, original_of)
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_h, (size_t)c->n_lc_total);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ring, 2 * (size_t)std::max<int64_t>(c->ring_len, 1));
@@ -1785,9 +1800,9 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
     if (ev_rev[q]) cudaEventDestroy(ev_rev[q]);
   }
   if (e == cudaSuccess && stt == EMT_OK) {
-    e = launch_adj_finalize(c->d_br, c->d_br_orig, c->d_br_src, nbr, d_dg, d_dsrc, ns, c->dt, d_lp,
+    e = launch_adj_finalize(c->d_br, c->d_br_orig, nbr, d_dg, d_dsrc, c->d_src_br_ptr, c->d_src_br, ns, c->dt, d_lp,
                             (int64_t)c->n_sub * T, d_grad, d_loss, st);
-    c->launches += 1;
+    c->launches += 2;
   }
   double h_loss = 0.0;
   if (e == cudaSuccess && stt == EMT_OK) {

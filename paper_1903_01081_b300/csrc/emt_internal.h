@@ -323,9 +323,10 @@ cudaError_t launch_adjoint(const AdjParams& p, cudaStream_t st);
 size_t adjoint_smem_bytes(const AdjLimits& lim);
 int adjoint_blocks_per_sm(const AdjLimits& lim);
 int adjoint_threads();
-cudaError_t launch_adj_finalize(const BranchDev* br, const int32_t* br_orig, const int32_t* br_src, int64_t n_br,
-                                const double* dg, const double* dsrc, int64_t n_sources, double dt,
-                                const double* loss_part, int64_t n_loss, double* grad, double* loss, cudaStream_t st);
+cudaError_t launch_adj_finalize(const BranchDev* br, const int32_t* br_orig, int64_t n_br, const double* dg,
+                                const double* dsrc, const int32_t* src_br_ptr, const int32_t* src_br, int64_t n_sources,
+                                double dt, const double* loss_part, int64_t n_loss, double* grad, double* loss,
+                                cudaStream_t st);
 cudaError_t launch_gather(const double* rec, int32_t n_rec, int64_t n_scen_rec, const int32_t* col, int64_t n_ch,
                           int64_t row0, int64_t n_rows, int64_t scen0, int64_t n_scen, double* out, cudaStream_t st);
 

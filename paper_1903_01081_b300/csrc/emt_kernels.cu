@@ -281,7 +281,7 @@ constexpr int kItemThreads = kFwdThreads - 32;
 struct FwdSmem {
   size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar;   // 8-byte
   size_t gilo, ivf;                                                 // float
-  size_t lck, lcm, lckind, lcstr, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg;   // int
+  size_t lck, lcm, lckind, lcstr, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, recp;   // int
   size_t bytes;
 };
 
@@ -318,6 +318,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.ilnode = w(L.il);
   s.ilcnt = w(L.il);
   s.srcg = w(L.src);
+  s.recp = w(L.n);
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
 }
@@ -387,6 +388,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   int* ilnode = reinterpret_cast<int*>(smem_raw + L.ilnode);
   int* ilcnt = reinterpret_cast<int*>(smem_raw + L.ilcnt);
   int* srcg = reinterpret_cast<int*>(smem_raw + L.srcg);
+  int* recp = reinterpret_cast<int*>(smem_raw + L.recp);    // per node: record column or -1
 
   const int sidx = blockIdx.x;
   const SubDev S = P.sub[sidx];
@@ -431,6 +433,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     rslot[x] = (int)(P.n0 % e.depth);
     wslot[x] = (int)((P.n0 + e.d) % e.depth);
   }
+  for (int r = tid; r < n; r += T) recp[r] = P.rec != nullptr ? P.rec_pos[S.node_off + r] : -1;
   for (int x = tid; x < 4 * n_il; x += T) ent[x] = P.ent[4 * (size_t)S.il_off + x];
   for (int x = tid; x < n_il; x += T) {
     ilnode[x] = P.il_node[S.il_off + x];
@@ -548,10 +551,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       double v = part[r * Q];
       for (int q = 1; q < Q; ++q) v += part[r * Q + q];
       vv[r] = v;
-      if (rec_now) {
-        const int pos = P.rec_pos[S.node_off + r];
-        if (pos >= 0) P.rec[(rec_row - P.rec_row0) * P.n_rec + pos] = v;
-      }
+      if (rec_now && recp[r] >= 0) P.rec[(rec_row - P.rec_row0) * P.n_rec + recp[r]] = v;
     }
     if (dec == 0) ++rec_row;
     if (++dec == decim) dec = 0;
