@@ -63,6 +63,41 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x: float) -> float:
+    """The largest value of x over the ranks (x itself without a process
+    group); NCCL reduces a CUDA tensor, gloo a CPU one."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, t_max: float) -> float:
+    """Units all ranks processed over the slowest rank's time (weak scaling:
+    every rank processes the same units)."""
+    return world * units_per_rank / t_max
+
+
+def run_rank_selftest():
+    """CPU check of the multi-rank aggregation (gloo): each rank reports a
+    rank-dependent time; rank 0 prints the aggregate as the bench would."""
+    import torch.distributed as dist
+    rank, world, _ = dist_env()
+    dist.init_process_group("gloo")
+    t_local = 1.0 + 0.5 * rank
+    t_max = max_over_ranks(t_local)
+    value = whole_job_rate(1000.0, world, t_max)
+    dist.barrier()
+    if rank == 0:
+        print(json.dumps({"selftest": "ranks", "world": world, "t_max": t_max, "value": value}), flush=True)
+    dist.destroy_process_group()
+    return 0
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -330,12 +365,8 @@ def run_ours(args):
     launches = sim.info("kernel_launches") - launches0
     ms = [a.elapsed_time(b) for a, b in ev]
     t_local = sum(ms) / 1e3
-    t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
-    value = world * n * N_STEPS * args.steps / t_max
+    t_max = max_over_ranks(t_local)
+    value = whole_job_rate(n * N_STEPS * args.steps, world, t_max)
 
     # parity of the timed configuration against the oracle on sampled steps
     w = sim.waveforms(n_rows=min(2000, N_STEPS))[:, 0, :]
@@ -370,11 +401,7 @@ def run_ours(args):
         emt.emt_destroy(ctx)
         if i >= args.warmup:
             e2e_times.append(dt)
-    te = torch.tensor([sum(e2e_times)], device="cuda", dtype=torch.float64)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * n * N_STEPS * args.steps / float(te.item())
+    e2e_value = whole_job_rate(n * N_STEPS * args.steps, world, max_over_ranks(sum(e2e_times)))
 
     if rank == 0:
         import oracle
@@ -430,7 +457,10 @@ def main():
     ap.add_argument("--leg-steps", type=int, default=None, help="time steps of a lone n1 / shared_g / adjoint leg")
     ap.add_argument("--leg-warm", type=int, default=500, help="warm-up steps of a lone scenario leg")
     ap.add_argument("--shape", default=None, help="S_t,threads for a lone scenario leg (no autotuning)")
+    ap.add_argument("--selftest-ranks", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.selftest_ranks:
+        return run_rank_selftest()
     if args.impl == "reference":
         return run_reference(args)
     if args.leg in ("n1", "shared_g", "adjoint"):
