@@ -50,6 +50,9 @@ class _Net(ctypes.Structure):
         ("ln_zc", ctypes.c_void_p), ("ln_d", ctypes.c_void_p),
         ("n_sw", ctypes.c_int64), ("sw_k", ctypes.c_void_p), ("sw_m", ctypes.c_void_p),
         ("sw_r", ctypes.c_void_p), ("sw_on", ctypes.c_void_p), ("sw_off", ctypes.c_void_p),
+        ("n_rs", ctypes.c_int64), ("rs_k", ctypes.c_void_p), ("rs_m", ctypes.c_void_p),
+        ("rs_kind", ctypes.c_void_p), ("rs_ron", ctypes.c_void_p), ("rs_roff", ctypes.c_void_p),
+        ("rs_on0", ctypes.c_void_p), ("rs_trip", ctypes.c_void_p),
     ]
 
 
@@ -64,7 +67,9 @@ def _load():
         lib.orc_adjoint.argtypes = [P, ctypes.c_int64, P, P, P]
         lib.orc_partition.argtypes = [P, P, P]
         lib.orc_lu_solve.argtypes = [ctypes.c_int64, P, P, P]
-        for f in (lib.orc_run, lib.orc_loss_cs, lib.orc_adjoint, lib.orc_partition, lib.orc_lu_solve):
+        lib.orc_rs_states.argtypes = [P, ctypes.c_int64, P]
+        for f in (lib.orc_run, lib.orc_loss_cs, lib.orc_adjoint, lib.orc_partition, lib.orc_lu_solve,
+                  lib.orc_rs_states):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -101,6 +106,12 @@ class _Pinned:
         n.sw_k, n.sw_m = p(net.sw_k, np.int32), p(net.sw_m, np.int32)
         n.sw_r = p(net.sw_r, np.float64)
         n.sw_on, n.sw_off = p(net.sw_close_step, np.int64), p(net.sw_open_step, np.int64)
+        rs = lambda name, dt: getattr(net, name, np.zeros(0, dt))
+        n.n_rs = int(len(rs("rs_k", np.int32)))
+        n.rs_k, n.rs_m = p(rs("rs_k", np.int32), np.int32), p(rs("rs_m", np.int32), np.int32)
+        n.rs_kind = p(rs("rs_kind", np.uint8), np.uint8)
+        n.rs_ron, n.rs_roff = p(rs("rs_ron", np.float64), np.float64), p(rs("rs_roff", np.float64), np.float64)
+        n.rs_on0, n.rs_trip = p(rs("rs_on0", np.uint8), np.uint8), p(rs("rs_trip", np.int64), np.int64)
         self.net = n
 
     @property
@@ -167,6 +178,15 @@ def adjoint(net, n_steps: int, v_target):
     _check(lib.orc_adjoint(pin.ref, int(n_steps), tg.ctypes.data, grad.ctypes.data, ctypes.addressof(J)),
            "orc_adjoint")
     return grad, J.value
+
+
+def runtime_switch_states(net, n_steps: int):
+    """States of the runtime switches in force at steps 1..n_steps: [n_steps, n_rs] uint8."""
+    lib = _load()
+    pin = _Pinned(net)
+    out = np.zeros((int(n_steps), pin.net.n_rs), dtype=np.uint8)
+    _check(lib.orc_rs_states(pin.ref, int(n_steps), out.ctypes.data if out.size else None), "orc_rs_states")
+    return out
 
 
 def partition(net):

@@ -125,6 +125,12 @@ bool valid(const orc_net* net) {
     if (k < -1 || m < -1 || k >= net->n_nodes || m >= net->n_nodes || k == m || (k < 0 && m < 0)) return false;
     if (!(net->sw_r[s] > 0.0)) return false;
   }
+  if (net->n_rs < 0) return false;
+  for (int64_t w = 0; w < net->n_rs; ++w) {
+    int32_t k = net->rs_k[w], m = net->rs_m[w];
+    if (k < -1 || m < -1 || k >= net->n_nodes || m >= net->n_nodes || k == m || (k < 0 && m < 0)) return false;
+    if (net->rs_kind[w] > 1 || !(net->rs_ron[w] > 0.0) || !(net->rs_roff[w] > 0.0)) return false;
+  }
   return true;
 }
 
@@ -146,6 +152,7 @@ void components(const orc_net* net, std::vector<int>& sub, int& n_sub) {
   };
   for (int64_t b = 0; b < net->n_br; ++b) join(net->br_k[b], net->br_m[b]);
   for (int64_t s = 0; s < net->n_sw; ++s) join(net->sw_k[s], net->sw_m[s]);
+  for (int64_t w = 0; w < net->n_rs; ++w) join(net->rs_k[w], net->rs_m[w]);
   sub.assign(n, -1);
   n_sub = 0;
   std::vector<int> label(n, -1);
@@ -188,6 +195,8 @@ struct Sim {
   std::vector<std::vector<T>> ring_k, ring_m;
   std::vector<T> vsrc;   // source voltages at the current step
   std::vector<T> v;      // node voltages at the current step
+  std::vector<char> rs_on;     // runtime-switch state in force at the current step
+  std::vector<double> rs_i;    // breaker current of the previous step
 
   bool init(const T* br_value, const T* src_amp, bool monolithic) {
     n_nodes = (int)net->n_nodes;
@@ -218,17 +227,38 @@ struct Sim {
     }
     vsrc.assign(net->n_src, T(0.0));
     v.assign(n_nodes, T(0.0));
+    rs_on.assign(net->n_rs, 0);
+    for (int64_t w = 0; w < net->n_rs; ++w) rs_on[w] = net->rs_on0[w] ? 1 : 0;
+    rs_i.assign(net->n_rs, 0.0);
     return true;
+  }
+
+  // Runtime switches: the states in force at step n+1 from step n's solution.
+  void decide_runtime_switches(int64_t n) {
+    for (int64_t w = 0; w < net->n_rs; ++w) {
+      const double vb = re(node_voltage(net->rs_k[w])) - re(node_voltage(net->rs_m[w]));
+      if (net->rs_kind[w] == 0) {
+        rs_on[w] = vb > 0.0 ? 1 : 0;
+      } else if (rs_on[w]) {
+        const double i = vb / net->rs_ron[w];
+        if (n >= net->rs_trip[w] && rs_i[w] * i <= 0.0) rs_on[w] = 0;
+        rs_i[w] = i;
+      }
+    }
   }
 
   // Process 3: assemble the subsystem's conductance matrix for the switch
   // state of step n and factorise it, if that state differs from the one
   // the current factors belong to.
   bool refactor_if_needed(int s, int64_t n) {
-    std::vector<char> st(net->n_sw, 0);
+    std::vector<char> st(net->n_sw + net->n_rs, 0);
     for (int64_t w = 0; w < net->n_sw; ++w) {
       int a = net->sw_k[w] >= 0 ? net->sw_k[w] : net->sw_m[w];
       if (sub[a] == s) st[w] = switch_closed(net, w, n) ? 1 : 0;
+    }
+    for (int64_t w = 0; w < net->n_rs; ++w) {
+      int a = net->rs_k[w] >= 0 ? net->rs_k[w] : net->rs_m[w];
+      if (sub[a] == s) st[net->n_sw + w] = rs_on[w];
     }
     if (!lu[s].empty() && st == state[s]) return true;
     state[s] = st;
@@ -257,6 +287,10 @@ struct Sim {
     }
     for (int64_t w = 0; w < net->n_sw; ++w)
       if (st[w]) stamp(net->sw_k[w], net->sw_m[w], T(1.0) / T(net->sw_r[w]));
+    for (int64_t w = 0; w < net->n_rs; ++w) {
+      int a = net->rs_k[w] >= 0 ? net->rs_k[w] : net->rs_m[w];
+      if (sub[a] == s) stamp(net->rs_k[w], net->rs_m[w], T(1.0) / T(rs_on[w] ? net->rs_ron[w] : net->rs_roff[w]));
+    }
     lu[s] = G;
     return lu_factor(ns, lu[s], piv[s]);
   }
@@ -312,6 +346,7 @@ struct Sim {
       ring_m[l][(n + d) % d1] = -y2 * v[net->ln_k[l]] - ik;
       ring_k[l][(n + d) % d1] = -y2 * v[net->ln_m[l]] - im;
     }
+    decide_runtime_switches(n);
     return true;
   }
 };
@@ -385,7 +420,7 @@ extern "C" int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_
 // and finally dg/dR = -1/R^2, dg/dL = -dt/(2L^2), dg/dC = 2/dt.
 extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad,
                            double* loss) {
-  if (!valid(net) || !v_target || !grad || n_steps < 0) return -1;
+  if (!valid(net) || !v_target || !grad || n_steps < 0 || net->n_rs > 0) return -1;
   const int64_t nn = net->n_nodes, nb = net->n_br, ns = net->n_src, nl = net->n_ln;
   Sim<double> sim;
   sim.net = net;
@@ -477,6 +512,18 @@ extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_
     grad[b] = dg[b] * dgdp;
   }
   for (int64_t s = 0; s < ns; ++s) grad[nb + s] = dA[s];
+  return 0;
+}
+
+extern "C" int orc_rs_states(const orc_net* net, int64_t n_steps, uint8_t* states) {
+  if (!valid(net) || n_steps < 0 || (n_steps > 0 && net->n_rs > 0 && !states)) return -1;
+  Sim<double> sim;
+  sim.net = net;
+  sim.init(net->br_val, net->src_amp, false);
+  for (int64_t n = 1; n <= n_steps; ++n) {
+    for (int64_t w = 0; w < net->n_rs; ++w) states[(size_t)(n - 1) * net->n_rs + w] = (uint8_t)sim.rs_on[w];
+    if (!sim.step(n)) return -2;
+  }
   return 0;
 }
 

@@ -45,6 +45,21 @@ typedef struct {
   const double* sw_r;
   const int64_t* sw_on;     /* closed for sw_on <= n < sw_off */
   const int64_t* sw_off;    /* -1 = never opens */
+  /* Runtime switches: two-state resistors whose state in force at step n
+   * is decided from step n-1's solution (state at step 1: rs_on0).
+   *   kind 0, diode (anode k, cathode m): conducting iff v_k - v_m > 0;
+   *   kind 1, breaker: closed until, at a step n >= rs_trip, its current
+   *     g_on (v_k - v_m) changes sign from step n-1 (product <= 0); open
+   *     from step n+1 on, for good.
+   * Ends are unknown nodes or ground. */
+  int64_t n_rs;
+  const int32_t* rs_k;
+  const int32_t* rs_m;
+  const uint8_t* rs_kind;
+  const double* rs_ron;
+  const double* rs_roff;
+  const uint8_t* rs_on0;
+  const int64_t* rs_trip;
 } orc_net;
 
 /* Run n_steps steps from the de-energised state.
@@ -59,6 +74,10 @@ typedef struct {
 int orc_run(const orc_net* net, int monolithic, int64_t n_steps, const int32_t* rec, int64_t n_rec,
             double* v_out, const double* v_target, double* loss);
 
+/* Runtime-switch states in force at steps 1..n_steps: states[(n-1) n_rs + w]
+ * (a run of orc_run's loop, partitioned mode). */
+int orc_rs_states(const orc_net* net, int64_t n_steps, uint8_t* states);
+
 /* Complex-step derivative of the loss with respect to parameter `param`
  * (0..n_br-1: branch value; n_br..n_br+n_src-1: source amplitude):
  * runs the same loop in complex arithmetic with p -> p + i*h.
@@ -67,7 +86,8 @@ int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_target, int
                 double* loss, double* dloss);
 
 /* Discrete adjoint of the loss over the full stored trajectory.
- * grad: [n_br + n_src] = dJ/d(branch value) then dJ/d(source amplitude). */
+ * grad: [n_br + n_src] = dJ/d(branch value) then dJ/d(source amplitude).
+ * Networks with runtime switches are rejected (-1). */
 int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad, double* loss);
 
 /* Subsystem of each unknown node (components over branches and switches). */

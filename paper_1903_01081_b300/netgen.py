@@ -64,6 +64,15 @@ class Network:
     sw_r: np.ndarray            # float64 [n_sw] ohm (closed resistance)
     sw_close_step: np.ndarray   # int64 [n_sw]; closed for close <= n < open
     sw_open_step: np.ndarray    # int64 [n_sw]; -1 = never opens
+    # runtime switches: two-state resistors whose state is decided from the
+    # previous step's solution (kind 0 diode k->m, kind 1 current-zero breaker)
+    rs_k: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    rs_m: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    rs_kind: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint8))
+    rs_ron: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    rs_roff: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    rs_on0: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint8))
+    rs_trip: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
     n_steps: int = 0            # suggested run length
     meta: dict = field(default_factory=dict)
 
@@ -82,6 +91,10 @@ class Network:
     @property
     def n_switches(self) -> int:
         return int(self.sw_k.shape[0])
+
+    @property
+    def n_runtime_switches(self) -> int:
+        return int(self.rs_k.shape[0])
 
     def copy(self) -> "Network":
         kw = {}
@@ -201,6 +214,7 @@ class NetworkBuilder:
         self.src = []    # (amp, phase, freq)
         self.ln = []     # (k, m, zc, d)
         self.sw = []     # (k, m, r, close, open)
+        self.rs = []     # (k, m, kind, r_on, r_off, on0, trip)
 
     def branch(self, k, m, kind, value):
         self.br.append((int(k), int(m), int(kind), float(value)))
@@ -217,6 +231,12 @@ class NetworkBuilder:
     def switch(self, k, m, r, close, open_=-1):
         self.sw.append((int(k), int(m), float(r), int(close), int(open_)))
 
+    def diode(self, anode, cathode, r_on, r_off, on0=False):
+        self.rs.append((int(anode), int(cathode), 0, float(r_on), float(r_off), int(bool(on0)), -1))
+
+    def breaker(self, k, m, r_on, r_off, trip_step):
+        self.rs.append((int(k), int(m), 1, float(r_on), float(r_off), 1, int(trip_step)))
+
     def build(self, dt, n_nodes, n_steps=0, meta=None) -> Network:
         def col(lst, i, dt_):
             return np.ascontiguousarray(np.array([x[i] for x in lst], dtype=dt_))
@@ -230,7 +250,11 @@ class NetworkBuilder:
             ln_zc=col(self.ln, 2, np.float64), ln_delay=col(self.ln, 3, np.int32),
             sw_k=col(self.sw, 0, np.int32), sw_m=col(self.sw, 1, np.int32),
             sw_r=col(self.sw, 2, np.float64), sw_close_step=col(self.sw, 3, np.int64),
-            sw_open_step=col(self.sw, 4, np.int64), n_steps=int(n_steps), meta=dict(meta or {}))
+            sw_open_step=col(self.sw, 4, np.int64),
+            rs_k=col(self.rs, 0, np.int32), rs_m=col(self.rs, 1, np.int32), rs_kind=col(self.rs, 2, np.uint8),
+            rs_ron=col(self.rs, 3, np.float64), rs_roff=col(self.rs, 4, np.float64),
+            rs_on0=col(self.rs, 5, np.uint8), rs_trip=col(self.rs, 6, np.int64),
+            n_steps=int(n_steps), meta=dict(meta or {}))
 
 
 # ----------------------------------------------------------------------------
