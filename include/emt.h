@@ -55,7 +55,20 @@ typedef struct emt_ctx emt_ctx;  /* opaque; owns all device memory it allocates 
  *   ln_delay >= 1 (travel time in whole steps).
  * Switches (ideal resistors while closed): sw_k, sw_m (unknown node or
  *   ground), sw_r > 0 (ohm); closed for sw_close_step <= n < sw_open_step,
- *   sw_open_step = -1 never opens, sw_close_step = -1 never closes. */
+ *   sw_open_step = -1 never opens, sw_close_step = -1 never closes.
+ * Runtime switches (n_rswitches may be 0): two-state resistors, rs_ron
+ *   while on and rs_roff while off (both > 0), between rs_k and rs_m
+ *   (unknown node or ground), whose state in force at step n is decided
+ *   from step n-1's solution (the state at step 1 is rs_on0):
+ *     rs_kind 0, diode (anode rs_k, cathode rs_m): on iff v_k - v_m > 0;
+ *     rs_kind 1, breaker: on until, at a step n >= rs_trip_step, its
+ *       current (v_k - v_m) / rs_ron changes sign from step n-1 (product
+ *       <= 0); off from step n+1 on, for good (rs_on0 is ignored: on).
+ *   The paper's process 3 at run time (Sec. III-A): each subsystem with k
+ *   runtime switches gets a prefactored G^-1 for every one of its 2^k
+ *   states (k <= 8 per subsystem), and the time loop switches matrices
+ *   when a state changes.  Not supported with a scenario set or by
+ *   emt_adjoint. */
 typedef struct {
   double dt;
   int64_t n_nodes;
@@ -79,6 +92,14 @@ typedef struct {
   const double* sw_r;
   const int64_t* sw_close_step;
   const int64_t* sw_open_step;
+  int64_t n_rswitches;
+  const int32_t* rs_k;
+  const int32_t* rs_m;
+  const uint8_t* rs_kind;
+  const double* rs_ron;
+  const double* rs_roff;
+  const uint8_t* rs_on0;
+  const int64_t* rs_trip_step;
 } emt_network_desc;
 
 /* Optional per-scenario overrides of one base network (the paper's

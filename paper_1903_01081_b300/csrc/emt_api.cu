@@ -61,6 +61,8 @@ struct emt_ctx {
   std::vector<double> src_amp, src_phase, src_omega;   // per global source
   std::vector<int32_t> nb_sub, nb_dmin;
   std::vector<SwitchDev> switches;
+  std::vector<RuntimeSwitchDev> rswitches;             // runtime switches, grouped by subsystem
+  std::vector<int32_t> rs_word0;                       // per subsystem: state word at step 1
   int64_t ring_len = 0, ginv_len = 0, n_lc_total = 0;
   FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0};
 
@@ -90,6 +92,9 @@ struct emt_ctx {
   double* d_src_table = nullptr;
   int64_t src_table_steps = 0;
   SwitchDev* d_sw = nullptr;
+  RuntimeSwitchDev* d_rs = nullptr;
+  int32_t* d_rs_word = nullptr;
+  double* d_rs_prev_i = nullptr;
   double* d_ginv = nullptr;
   float* d_ginv_lo = nullptr;
   int32_t* d_err = nullptr;
@@ -232,6 +237,18 @@ std::string validate(const emt_network_desc* d) {
     if (d->ln_delay[l] < 1) return "line " + std::to_string(l) + ": delay must be >= 1 step";
     if (d->ln_delay[l] > (1 << 20)) return "line " + std::to_string(l) + ": delay too large";
     if (!finite_pos(d->ln_zc[l])) return "line " + std::to_string(l) + ": Z_c must be finite and > 0";
+  }
+  if (d->n_rswitches < 0) return "negative count";
+  if (d->n_rswitches && (!d->rs_k || !d->rs_m || !d->rs_kind || !d->rs_ron || !d->rs_roff || !d->rs_on0 ||
+                         !d->rs_trip_step))
+    return "runtime switch array is NULL";
+  for (int64_t w = 0; w < d->n_rswitches; ++w) {
+    const int32_t k = d->rs_k[w], m = d->rs_m[w];
+    if (k < -1 || m < -1 || k >= d->n_nodes || m >= d->n_nodes || k == m || (k < 0 && m < 0))
+      return "runtime switch " + std::to_string(w) + ": ends must be unknown nodes or ground";
+    if (d->rs_kind[w] > 1) return "runtime switch " + std::to_string(w) + ": kind must be 0 (diode) or 1 (breaker)";
+    if (!finite_pos(d->rs_ron[w]) || !finite_pos(d->rs_roff[w]))
+      return "runtime switch " + std::to_string(w) + ": resistances must be finite and > 0";
   }
   if (d->n_switches && (!d->sw_k || !d->sw_m || !d->sw_r || !d->sw_close_step || !d->sw_open_step))
     return "switch array is NULL";
@@ -632,6 +649,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   };
   for (int64_t b = 0; b < d->n_branches; ++b) join(d->br_k[b], d->br_m[b]);
   for (int64_t w = 0; w < d->n_switches; ++w) join(d->sw_k[w], d->sw_m[w]);
+  for (int64_t w = 0; w < d->n_rswitches; ++w) join(d->rs_k[w], d->rs_m[w]);
   if (scen && scen->sw_ptr)   // scenario switches may join nodes too
     for (int64_t w = 0; w < scen->sw_ptr[scen->n_scenarios]; ++w) join(scen->sw_k[w], scen->sw_m[w]);
   c->sub_of_node.assign(N, -1);
@@ -896,9 +914,33 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       const int a = d->sw_k[w] >= 0 ? d->sw_k[w] : d->sw_m[w];
       sw_of[c->sub_of_node[a]].push_back(w);
     }
+    std::vector<std::vector<int64_t>> rs_of(S);
+    for (int64_t w = 0; w < d->n_rswitches; ++w) {
+      const int a = d->rs_k[w] >= 0 ? d->rs_k[w] : d->rs_m[w];
+      rs_of[c->sub_of_node[a]].push_back(w);
+    }
     int64_t goff = 0;
     for (int s = 0; s < S; ++s) {
       SubDev& sd = c->subs[s];
+      if ((int)rs_of[s].size() > kMaxRuntimeSwitches)
+        return bail("subsystem " + std::to_string(s) + " has more than " + std::to_string(kMaxRuntimeSwitches) +
+                    " runtime switches");
+      sd.n_rs = (int)rs_of[s].size();
+      sd.n_states = 1 << sd.n_rs;
+      sd.rs_off = (int)c->rswitches.size();
+      int32_t word0 = 0;
+      for (int j = 0; j < sd.n_rs; ++j) {
+        const int64_t w = rs_of[s][j];
+        RuntimeSwitchDev r{};
+        r.k = d->rs_k[w] >= 0 ? local[d->rs_k[w]] : -1;
+        r.m = d->rs_m[w] >= 0 ? local[d->rs_m[w]] : -1;
+        r.kind = d->rs_kind[w];
+        r.r_on = d->rs_ron[w];
+        r.trip = d->rs_trip_step[w];
+        c->rswitches.push_back(r);
+        if (r.kind == 1 || d->rs_on0[w]) word0 |= 1 << j;
+      }
+      c->rs_word0.push_back(word0);
       std::vector<int64_t> events;
       for (int64_t w : sw_of[s]) {
         if (d->sw_close_step[w] >= 0) events.push_back(d->sw_close_step[w]);
@@ -910,23 +952,32 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       eps.push_back({LLONG_MIN, events.empty() ? 1 : events[0] - 1});
       for (int64_t e : events) eps.push_back({e, e});
       sd.ep_off = (int)c->epochs.size();
-      for (auto& ep : eps) {
-        EpochDev E{};
-        E.start = ep.first;
-        E.ginv_off = goff;
-        goff += (int64_t)sd.n * (sd.n + sd.n_str);
-        E.sw_off = (int)c->switches.size();
-        for (int64_t w : sw_of[s]) {
-          if (!switch_closed(d->sw_close_step[w], d->sw_open_step[w], ep.second)) continue;
-          SwitchDev sw{};
-          sw.k = d->sw_k[w] >= 0 ? local[d->sw_k[w]] : -1;
-          sw.m = d->sw_m[w] >= 0 ? local[d->sw_m[w]] : -1;
-          sw.g = 1.0 / d->sw_r[w];
-          c->switches.push_back(sw);
+      for (auto& ep : eps)
+        for (int word = 0; word < sd.n_states; ++word) {
+          EpochDev E{};
+          E.start = ep.first;
+          E.ginv_off = goff;
+          goff += (int64_t)sd.n * (sd.n + sd.n_str);
+          E.sw_off = (int)c->switches.size();
+          for (int64_t w : sw_of[s]) {
+            if (!switch_closed(d->sw_close_step[w], d->sw_open_step[w], ep.second)) continue;
+            SwitchDev sw{};
+            sw.k = d->sw_k[w] >= 0 ? local[d->sw_k[w]] : -1;
+            sw.m = d->sw_m[w] >= 0 ? local[d->sw_m[w]] : -1;
+            sw.g = 1.0 / d->sw_r[w];
+            c->switches.push_back(sw);
+          }
+          for (int j = 0; j < sd.n_rs; ++j) {   // runtime switches: r_on or r_off by the state word
+            const int64_t w = rs_of[s][j];
+            SwitchDev sw{};
+            sw.k = d->rs_k[w] >= 0 ? local[d->rs_k[w]] : -1;
+            sw.m = d->rs_m[w] >= 0 ? local[d->rs_m[w]] : -1;
+            sw.g = 1.0 / (((word >> j) & 1) ? d->rs_ron[w] : d->rs_roff[w]);
+            c->switches.push_back(sw);
+          }
+          E.n_sw = (int)c->switches.size() - E.sw_off;
+          c->epochs.push_back(E);
         }
-        E.n_sw = (int)c->switches.size() - E.sw_off;
-        c->epochs.push_back(E);
-      }
       sd.n_ep = (int)c->epochs.size() - sd.ep_off;
     }
     c->ginv_len = goff;
@@ -957,6 +1008,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   }
 
   // -------- multi-scenario set
+  if (scen && !c->rswitches.empty()) return bail("runtime switches are not supported with a scenario set");
   if (scen) {
     const std::string bm = build_scenarios(c, d, scen, local, new_of_orig, le_of_end, lc_slot_of, sb_slot_of);
     if (!bm.empty()) return bail(bm);
@@ -981,6 +1033,8 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   UP(d_src_phase, src_phase)
   UP(d_src_omega, src_omega)
   UP(d_sw, switches)
+  UP(d_rs, rswitches)
+  UP(d_rs_word, rs_word0)
   UP(d_br_orig, br_orig)
   UP(d_br_lc, br_lc)
   UP(d_br_src, br_src)
@@ -992,6 +1046,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ginv, (size_t)c->ginv_len);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ginv_lo, (size_t)c->ginv_len);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_err, 4);
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_rs_prev_i, c->rswitches.size());
   if (e == cudaSuccess) e = c->upload(&c->d_node_l0, c->node_l0);
   if (e == cudaSuccess) e = c->upload(&c->d_node_nl, c->node_nl);
   if (c->batched) {
@@ -1274,6 +1329,9 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
   p.n_rec = rs.n_rec;
   p.wait_budget_ns = c->wait_budget_ns;
   p.hold_sub = c->hold_sub;
+  p.rs = c->d_rs;
+  p.rs_word = c->d_rs_word;
+  p.rs_prev_i = c->d_rs_prev_i;
   for (int64_t done = 0; done < n_steps; done += chunk) {
     const int64_t len = std::min(chunk, n_steps - done);
     SourceParams sp{};
@@ -1396,6 +1454,10 @@ extern "C" emt_status emt_reset(emt_ctx* c) {
     e = cudaMemset(c->d_ring, 0, 2 * std::max<int64_t>(c->ring_len, 1) * sizeof(unsigned long long));
   if (e == cudaSuccess) e = launch_ring_init(RingInitParams{c->d_le, (int64_t)c->line_ends.size(), c->d_ring}, nullptr);
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 4 * sizeof(int32_t));
+  if (e == cudaSuccess && !c->rs_word0.empty())
+    e = cudaMemcpy(c->d_rs_word, c->rs_word0.data(), c->rs_word0.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !c->rswitches.empty())
+    e = cudaMemset(c->d_rs_prev_i, 0, c->rswitches.size() * sizeof(double));
   if (c->batched) {
     if (e == cudaSuccess) e = cudaMemset(c->d_bh, 0, std::max<size_t>((size_t)c->n_lc_total * c->S, 1) * sizeof(double));
     if (e == cudaSuccess)
@@ -1525,6 +1587,7 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "n_nodes") *value = c->n_nodes;
   else if (k == "n_line_ends") *value = (int64_t)c->line_ends.size();
   else if (k == "n_strong_branches") *value = (int64_t)c->str_slot.size();
+  else if (k == "n_runtime_switches") *value = (int64_t)c->rswitches.size();
   else if (k == "smem_bytes") *value = (int64_t)forward_smem_bytes(c->lim);
   else return EMT_EINVAL;
   return EMT_OK;
@@ -1558,6 +1621,7 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
                                   double* grad, double* loss, int32_t on_device, void* stream) {
   if (!c) return EMT_EINVAL;
   if (c->batched) return c->fail(EMT_EINVAL, "emt_adjoint: a context built with a scenario set has no adjoint");
+  if (!c->rswitches.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: networks with runtime switches have no adjoint");
   if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
   if (n_steps < 1) return c->fail(EMT_EINVAL, "emt_adjoint: n_steps must be >= 1");
   if (n_steps > (int64_t)INT32_MAX - (int64_t)(1 << 21))

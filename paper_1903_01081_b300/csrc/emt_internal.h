@@ -77,7 +77,23 @@ struct SubDev {
   int32_t il_off, n_il;        // injection lanes (4 entries each; il_node / il_cnt per lane)
   int32_t str_off, n_str;      // strong L/C branches (L/C slots in str_slot)
   int32_t q;                   // column blocks per row in the matvec
+  int32_t n_states;            // 2^(runtime switches): solve matrices per switch epoch
+  int32_t rs_off, n_rs;        // runtime switches (RuntimeSwitchDev list)
+};
+
+// Maximum runtime switches per subsystem (2^k solve matrices each epoch).
+constexpr int kMaxRuntimeSwitches = 8;
+
+// A runtime switch in device form: a two-state resistor whose state in
+// force at step n is decided from step n-1's solution.  Bit `j` (its index
+// within the subsystem) of the subsystem's state word is its state; the
+// solve matrix of epoch e and state word w is entry e n_states + w.
+struct RuntimeSwitchDev {
+  int32_t k, m;        // subsystem-local ends, -1 = ground
+  int32_t kind;        // 0 diode (anode k), 1 breaker
   int32_t pad;
+  double r_on;         // breaker current = (v_k - v_m) / r_on while on
+  int64_t trip;        // breaker: first step at which it may open
 };
 
 // Strong L/C branches.  When a branch's conductance dwarfs the rest of
@@ -91,6 +107,8 @@ constexpr double kStrongRatio = 3.0;
 
 // Switch epoch of a subsystem: state holding from step `start` on.  Its
 // solve matrix is n x nc, nc = n + n_str: [G^-1 | strong-branch columns].
+// With runtime switches each epoch has n_states consecutive entries, one
+// per state word (same start).
 struct EpochDev {
   int64_t start;
   int64_t ginv_off;      // offset of this epoch's n x nc solve matrix
@@ -133,6 +151,9 @@ struct FwdParams {
   int64_t n_steps;
   unsigned long long wait_budget_ns;
   int32_t hold_sub;            // debug: this subsystem never writes its line outputs (-1: none)
+  const RuntimeSwitchDev* rs;  // runtime switches (SubDev rs_off / n_rs)
+  int32_t* rs_word;            // per subsystem: state word in force at step n0 (carried across launches)
+  double* rs_prev_i;           // per runtime switch: breaker current of the previous step
 };
 
 struct PrefParams {

@@ -360,6 +360,9 @@ __device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int la
 __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_abort;
+  __shared__ RuntimeSwitchDev s_rs[kMaxRuntimeSwitches];
+  __shared__ double s_rsi[kMaxRuntimeSwitches];   // breaker currents of the previous step
+  __shared__ int s_rsbit[kMaxRuntimeSwitches];    // states decided for the next step
   const FwdSmem L = fwd_smem(P.lim);
   double* gi = reinterpret_cast<double*>(smem_raw + L.gi);
   double* part = reinterpret_cast<double*>(smem_raw + L.part);
@@ -447,11 +450,19 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     inp[zero_slot] = 0.0;
     s_abort = 0;
   }
-  int ep = 0;
-  while (ep + 1 < S.n_ep && P.ep[S.ep_off + ep + 1].start <= P.n0) ++ep;
-  long long next_ep_start = (ep + 1 < S.n_ep) ? P.ep[S.ep_off + ep + 1].start : LLONG_MAX;
+  // solve matrix: switch epoch te (by step) and runtime-switch state word
+  const int n_rs = S.n_rs, n_states = S.n_states, n_te = S.n_ep / n_states;
+  int word = n_rs > 0 ? P.rs_word[sidx] : 0;
+  for (int x = tid; x < n_rs; x += T) {
+    s_rs[x] = P.rs[S.rs_off + x];
+    s_rsi[x] = P.rs_prev_i[S.rs_off + x];
+    s_rsbit[x] = (word >> x) & 1;
+  }
+  int te = 0;
+  while (te + 1 < n_te && P.ep[S.ep_off + (te + 1) * n_states].start <= P.n0) ++te;
+  long long next_ep_start = (te + 1 < n_te) ? P.ep[S.ep_off + (te + 1) * n_states].start : LLONG_MAX;
   {
-    const int64_t off = P.ep[S.ep_off + ep].ginv_off;
+    const int64_t off = P.ep[S.ep_off + te * n_states + word].ginv_off;
     for (int i = tid; i < n * nc; i += T) {
       const int r = i / nc, c = i - r * nc;
       gi[r * ldg + c] = P.ginv[off + i];
@@ -482,10 +493,14 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     const int par = (int)(step & 1);
     const double* vsc = vs + par * src_vs;
     const int parshift = par * n_le;
-    if (step >= next_ep_start) {
-      while (ep + 1 < S.n_ep && P.ep[S.ep_off + ep + 1].start <= step) ++ep;
-      next_ep_start = (ep + 1 < S.n_ep) ? P.ep[S.ep_off + ep + 1].start : LLONG_MAX;
-      const int64_t off = P.ep[S.ep_off + ep].ginv_off;
+    // runtime-switch states decided from the previous step's solution
+    int new_word = 0;
+    for (int j = 0; j < n_rs; ++j) new_word |= s_rsbit[j] << j;
+    if (step >= next_ep_start || new_word != word) {
+      while (te + 1 < n_te && P.ep[S.ep_off + (te + 1) * n_states].start <= step) ++te;
+      next_ep_start = (te + 1 < n_te) ? P.ep[S.ep_off + (te + 1) * n_states].start : LLONG_MAX;
+      word = new_word;
+      const int64_t off = P.ep[S.ep_off + te * n_states + word].ginv_off;
       for (int i = tid; i < n * nc; i += T) {
         const int r = i / nc, c = i - r * nc;
         gi[r * ldg + c] = P.ginv[off + i];
@@ -566,6 +581,20 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
         if (!ok && lane == 0) s_abort = 1;
       }
     } else {
+      // runtime switches: the states in force at the next step (oracle rules)
+      if (tid < n_rs) {
+        const RuntimeSwitchDev r = s_rs[tid];
+        const double vb = (r.k >= 0 ? vv[r.k] : 0.0) - (r.m >= 0 ? vv[r.m] : 0.0);
+        int bit = (word >> tid) & 1;
+        if (r.kind == 0) {
+          bit = vb > 0.0 ? 1 : 0;
+        } else if (bit) {
+          const double i = vb / r.r_on;
+          if (step >= r.trip && s_rsi[tid] * i <= 0.0) bit = 0;
+          s_rsi[tid] = i;
+        }
+        s_rsbit[tid] = bit;
+      }
       const double* ie_cur = inp + ie_base + parshift;
       const double* vs_next = vs + (par ^ 1) * src_vs;
       for (int it = tid; it < it_end; it += kItemThreads) {
@@ -596,8 +625,15 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     }
     __syncthreads();
   }
-  if (!s_abort)
+  if (!s_abort) {
     for (int b = tid; b < n_lc; b += T) P.h[S.lc_off + b] = inp[b];
+    for (int x = tid; x < n_rs; x += T) P.rs_prev_i[S.rs_off + x] = s_rsi[x];
+    if (n_rs > 0 && tid == 0) {
+      int w = 0;
+      for (int j = 0; j < n_rs; ++j) w |= s_rsbit[j] << j;
+      P.rs_word[sidx] = w;
+    }
+  }
 }
 
 // ------------------------------------------------------------ gather

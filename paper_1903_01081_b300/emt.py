@@ -42,6 +42,9 @@ class _NetworkDesc(ctypes.Structure):
         ("ln_zc", ctypes.c_void_p), ("ln_delay", ctypes.c_void_p),
         ("n_switches", ctypes.c_int64), ("sw_k", ctypes.c_void_p), ("sw_m", ctypes.c_void_p),
         ("sw_r", ctypes.c_void_p), ("sw_close_step", ctypes.c_void_p), ("sw_open_step", ctypes.c_void_p),
+        ("n_rswitches", ctypes.c_int64), ("rs_k", ctypes.c_void_p), ("rs_m", ctypes.c_void_p),
+        ("rs_kind", ctypes.c_void_p), ("rs_ron", ctypes.c_void_p), ("rs_roff", ctypes.c_void_p),
+        ("rs_on0", ctypes.c_void_p), ("rs_trip_step", ctypes.c_void_p),
     ]
 
 
@@ -150,6 +153,12 @@ def network_desc(net, keep: list) -> _NetworkDesc:
     d.sw_k, d.sw_m = p(net.sw_k, np.int32), p(net.sw_m, np.int32)
     d.sw_r = p(net.sw_r, np.float64)
     d.sw_close_step, d.sw_open_step = p(net.sw_close_step, np.int64), p(net.sw_open_step, np.int64)
+    rs = lambda name, dt: getattr(net, name, np.zeros(0, dt))
+    d.n_rswitches = int(len(rs("rs_k", np.int32)))
+    d.rs_k, d.rs_m = p(rs("rs_k", np.int32), np.int32), p(rs("rs_m", np.int32), np.int32)
+    d.rs_kind = p(rs("rs_kind", np.uint8), np.uint8)
+    d.rs_ron, d.rs_roff = p(rs("rs_ron", np.float64), np.float64), p(rs("rs_roff", np.float64), np.float64)
+    d.rs_on0, d.rs_trip_step = p(rs("rs_on0", np.uint8), np.uint8), p(rs("rs_trip", np.int64), np.int64)
     return d
 
 

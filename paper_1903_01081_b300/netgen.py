@@ -567,3 +567,51 @@ def adjoint_target(net: Network, seed: int = 1005, rel: float = 0.05):
     br = net.br_value * (1.0 + rng.uniform(-rel, rel, size=net.n_branches))
     amp = net.src_amp * (1.0 + rng.uniform(-rel, rel, size=net.n_sources))
     return br, amp
+
+
+# ----------------------------------------------------------------------------
+# runtime switches: rectifier loads and breakers on an existing network
+
+def with_rectifier_loads(base: Network, seed: int = 1006, n_rectifiers: int = 30, n_breakers: int = 10,
+                         trip_range=(1000, 4000)) -> Network:
+    """``base`` plus diode-rectifier loads and series breakers.
+
+    Rectifier at a random unknown node a: diode a -> x (r_on 0.01 ohm,
+    r_off 1 Mohm), then R ~ U[50, 500] ohm and C ~ U[10, 100] uF from the new
+    node x to ground.  Breaker at a random node b: breaker b -> y (r_on 1
+    mohm, r_off 1 Mohm, trip step ~ U[trip_range)), then R ~ U[5, 50] ohm to
+    ground from the new node y.  New nodes join the subsystem of the node
+    they hang from."""
+    rng = np.random.default_rng(seed)
+    net = base.copy()
+    n = net.n_nodes
+    br = [list(net.br_k), list(net.br_m), list(net.br_kind), list(net.br_value)]
+    rs = {k: [] for k in ("k", "m", "kind", "ron", "roff", "on0", "trip")}
+    picks = rng.choice(net.n_nodes, size=n_rectifiers + n_breakers, replace=False)
+    for i, a in enumerate(picks):
+        x = n
+        n += 1
+        if i < n_rectifiers:
+            rs["k"].append(int(a)); rs["m"].append(x); rs["kind"].append(0)
+            rs["ron"].append(0.01); rs["roff"].append(1e6); rs["on0"].append(0); rs["trip"].append(-1)
+            for kind, val in ((KIND_R, rng.uniform(50.0, 500.0)), (KIND_C, rng.uniform(10e-6, 100e-6))):
+                br[0].append(x); br[1].append(GROUND); br[2].append(kind); br[3].append(val)
+        else:
+            rs["k"].append(int(a)); rs["m"].append(x); rs["kind"].append(1)
+            rs["ron"].append(1e-3); rs["roff"].append(1e6); rs["on0"].append(1)
+            rs["trip"].append(int(rng.integers(*trip_range)))
+            br[0].append(x); br[1].append(GROUND); br[2].append(KIND_R); br[3].append(rng.uniform(5.0, 50.0))
+    net.n_nodes = n
+    net.br_k = np.asarray(br[0], np.int32)
+    net.br_m = np.asarray(br[1], np.int32)
+    net.br_kind = np.asarray(br[2], np.uint8)
+    net.br_value = np.asarray(br[3], np.float64)
+    net.rs_k = np.asarray(rs["k"], np.int32)
+    net.rs_m = np.asarray(rs["m"], np.int32)
+    net.rs_kind = np.asarray(rs["kind"], np.uint8)
+    net.rs_ron = np.asarray(rs["ron"], np.float64)
+    net.rs_roff = np.asarray(rs["roff"], np.float64)
+    net.rs_on0 = np.asarray(rs["on0"], np.uint8)
+    net.rs_trip = np.asarray(rs["trip"], np.int64)
+    net.meta = dict(net.meta, runtime_switches={"seed": seed, "rectifiers": n_rectifiers, "breakers": n_breakers})
+    return net

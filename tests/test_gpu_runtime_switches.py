@@ -1,0 +1,133 @@
+"""GPU parity of runtime switches (diodes, current-zero breakers) against
+the oracle.  Every case first checks on the oracle's waveforms that no
+switching decision sits within rounding of its threshold, so that both
+sides must take the same decisions."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_01081_b300 import emt, netgen as g
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+def gpu_run(net, N, chunks=(None,)):
+    sim = emt.Simulator(net, n_steps=N)
+    done = 0
+    for c in chunks:
+        k = N - done if c is None else c
+        sim.run(k)
+        done += k
+    sim.sync()
+    w = sim.waveforms()[:, 0, :]
+    sim.close()
+    return w
+
+
+def decision_margin(net, v):
+    """Smallest |v_k - v_m| / max(|v_k|, |v_m|) of the diodes over the run:
+    how close a decision comes to cancellation, where the two sides'
+    rounding (about 1e-12 of the values) could flip its sign.  Values that
+    are exactly zero on both ends (a subsystem not yet energised) carry no
+    rounding and are left out."""
+    node = lambda x: v[:, x] if x >= 0 else np.zeros(len(v))
+    m = np.inf
+    for w in range(net.n_runtime_switches):
+        if net.rs_kind[w] == 0:
+            a, b = node(int(net.rs_k[w])), node(int(net.rs_m[w]))
+            sc = np.maximum(np.abs(a), np.abs(b))
+            ok = sc > 0
+            if ok.any():
+                m = min(m, np.min(np.abs(a - b)[ok] / sc[ok]))
+    return m
+
+
+def rectifier(cap):
+    b = g.NetworkBuilder()
+    b.source(1000.0, 0.3, 60.0)
+    b.branch(g.source_node(0), 0, 0, 1.0)
+    b.diode(0, 1, 0.01, 1e6)
+    b.branch(1, g.GROUND, 0, 10.0)
+    if cap:
+        b.branch(1, g.GROUND, 2, cap)
+    return b.build(50e-6, 2, 2000)
+
+
+@pytest.mark.parametrize("cap", [None, 200e-6])
+def test_rectifier(cap):
+    net = rectifier(cap)
+    N = 2000
+    ref = oracle.simulate(net, N)
+    assert decision_margin(net, ref) > 1e-9
+    assert rel(gpu_run(net, N), ref) <= TOL
+
+
+def test_breaker_interrupts_at_current_zero():
+    b = g.NetworkBuilder()
+    b.source(1000.0, 0.3, 60.0)
+    b.branch(g.source_node(0), 0, 0, 1.0)
+    b.branch(0, 1, 1, 10e-3)
+    b.breaker(1, g.GROUND, 1e-3, 1e5, 777)
+    b.branch(1, g.GROUND, 2, 1e-6)
+    net = b.build(20e-6, 2, 3000)
+    N = 3000
+    ref = oracle.simulate(net, N)
+    st = oracle.runtime_switch_states(net, N)[:, 0]
+    assert st[0] == 1 and st[-1] == 0
+    assert rel(gpu_run(net, N), ref) <= TOL
+
+
+def switched_multi():
+    base = g.multi_subsystem(151, [3, 4, 2, 3], n_lines=5, n_sources=2, dt=20e-6)
+    return g.with_rectifier_loads(base, seed=12, n_rectifiers=6, n_breakers=3, trip_range=(300, 900))
+
+
+def test_multi_subsystem_with_rectifiers_and_breakers_resumable():
+    net = switched_multi()
+    N = 2000
+    ref = oracle.simulate(net, N)
+    assert decision_margin(net, ref) > 1e-9
+    st = oracle.runtime_switch_states(net, N)
+    assert (st[:, :6].min(axis=0) != st[:, :6].max(axis=0)).any()    # diodes switch
+    assert (st[:, 6:].min(axis=0) != st[:, 6:].max(axis=0)).all()    # every breaker opens
+    one = gpu_run(net, N)
+    assert rel(one, ref) <= TOL
+    split = gpu_run(net, N, chunks=(333, 667, None))                   # states carried across launches
+    assert np.array_equal(split, one)
+
+
+def test_large_network_with_runtime_switches():
+    net = g.with_rectifier_loads(g.large_scale(), seed=1006)
+    N = 5000
+    ref = oracle.simulate(net, N)
+    assert decision_margin(net, ref) > 1e-9
+    assert rel(gpu_run(net, N), ref) <= TOL
+
+
+def test_runtime_switch_limits():
+    b = g.NetworkBuilder()
+    b.source(1000.0, 0.0)
+    b.branch(g.source_node(0), 0, 0, 1.0)
+    for i in range(9):
+        b.diode(0, i + 1, 0.01, 1e6)
+        b.branch(i + 1, g.GROUND, 0, 10.0)
+    net = b.build(50e-6, 10, 10)
+    with pytest.raises(emt.EmtError) as ei:
+        emt.emt_build_network(net)
+    assert ei.value.status == emt.EMT_EINVAL and "runtime switches" in str(ei.value)
+    net = switched_multi()
+    ctx = emt.emt_build_network(net)
+    emt.emt_prefactor(ctx)
+    assert emt.emt_get_info(ctx, "n_runtime_switches") == 9
+    with pytest.raises(emt.EmtError) as ei:
+        emt.emt_adjoint(ctx, np.zeros((10, net.n_nodes)), 10, 4)
+    assert ei.value.status == emt.EMT_EINVAL
+    emt.emt_destroy(ctx)
+    with pytest.raises(emt.EmtError) as ei:
+        emt.emt_build_network(net, g.Scenarios(n_scenarios=2))
+    assert ei.value.status == emt.EMT_EINVAL
