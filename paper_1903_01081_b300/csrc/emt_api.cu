@@ -64,7 +64,7 @@ struct emt_ctx {
   std::vector<RuntimeSwitchDev> rswitches;             // runtime switches, grouped by subsystem
   std::vector<int32_t> rs_word0;                       // per subsystem: state word at step 1
   int64_t ring_len = 0, ginv_len = 0, n_lc_total = 0;
-  FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0};
+  FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1};
 
   // device arrays
   SubDev* d_sub = nullptr;
@@ -991,6 +991,17 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     const int q = (int)std::lround(std::sqrt((double)(n + sd.n_str)));
     sd.q = std::max(1, std::min(q, kFwdThreads / n));
     c->lim.q = std::max(c->lim.q, sd.q);
+  }
+
+  // -------- two solve-matrix buffers per CTA when runtime switches change
+  // matrices at run time and both fit
+  c->lim.nbuf = 1;
+  if (!c->rswitches.empty()) {
+    FwdLimits two = c->lim;
+    two.nbuf = 2;
+    two.n = std::max(two.n, 1);
+    two.nc = std::max(two.nc, 1);
+    if (forward_smem_bytes(two) <= 200 * 1024) c->lim.nbuf = 2;
   }
 
   // -------- injection-lane range of every internal node

@@ -118,6 +118,7 @@ struct EpochDev {
 // Per-launch upper bounds that size the forward kernel's shared memory.
 struct FwdLimits {
   int32_t n, nc, q, lc, sb, le, src, il, str;
+  int32_t nbuf;                // solve-matrix buffers in shared memory: 1, or 2 (the last two states kept)
 };
 
 struct FwdParams {

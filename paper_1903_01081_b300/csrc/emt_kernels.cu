@@ -291,7 +291,8 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   auto d = [&](size_t count) { size_t r = o; o += count * 8; return r; };
   auto w = [&](size_t count) { size_t r = o; o += count * 4; return r; };
   const size_t ldg = (size_t)(L.nc | 1);
-  s.gi = d((size_t)L.n * ldg);
+  const size_t nbuf = L.nbuf > 1 ? 2 : 1;
+  s.gi = d(nbuf * (size_t)L.n * ldg);
   s.part = d((size_t)L.n * L.q);
   s.iv = d(L.nc);
   s.vv = d(L.n);
@@ -302,7 +303,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.ley2 = d(L.le);
   s.leown = d(L.le);
   s.lefar = d(L.le);
-  s.gilo = w((size_t)L.n * ldg);
+  s.gilo = w(nbuf * (size_t)L.n * ldg);
   s.ivf = w(L.nc);
   s.lcstr = w(L.lc);
   s.lck = w(L.lc);
@@ -364,7 +365,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   __shared__ double s_rsi[kMaxRuntimeSwitches];   // breaker currents of the previous step
   __shared__ int s_rsbit[kMaxRuntimeSwitches];    // states decided for the next step
   const FwdSmem L = fwd_smem(P.lim);
-  double* gi = reinterpret_cast<double*>(smem_raw + L.gi);
+  double* gi_buf = reinterpret_cast<double*>(smem_raw + L.gi);
   double* part = reinterpret_cast<double*>(smem_raw + L.part);
   double* iv = reinterpret_cast<double*>(smem_raw + L.iv);
   double* vv = reinterpret_cast<double*>(smem_raw + L.vv);
@@ -375,7 +376,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   double* ley2 = reinterpret_cast<double*>(smem_raw + L.ley2);
   long long* leown = reinterpret_cast<long long*>(smem_raw + L.leown);
   long long* lefar = reinterpret_cast<long long*>(smem_raw + L.lefar);
-  float* gilo = reinterpret_cast<float*>(smem_raw + L.gilo);
+  float* gilo_buf = reinterpret_cast<float*>(smem_raw + L.gilo);
   float* ivf = reinterpret_cast<float*>(smem_raw + L.ivf);
   int* lck = reinterpret_cast<int*>(smem_raw + L.lck);
   int* lcm = reinterpret_cast<int*>(smem_raw + L.lcm);
@@ -461,8 +462,15 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   int te = 0;
   while (te + 1 < n_te && P.ep[S.ep_off + (te + 1) * n_states].start <= P.n0) ++te;
   long long next_ep_start = (te + 1 < n_te) ? P.ep[S.ep_off + (te + 1) * n_states].start : LLONG_MAX;
+  // Solve-matrix buffers: with two, the previous state's matrix stays
+  // resident, so a switch that goes back and forth reloads nothing.
+  const size_t buf_len = (size_t)P.lim.n * (size_t)(P.lim.nc | 1);
+  int cur_buf = 0;
+  int tag_cur = te * n_states + word, tag_other = -1;   // solve-matrix entries held by the two buffers
+  double* gi = gi_buf;
+  float* gilo = gilo_buf;
   {
-    const int64_t off = P.ep[S.ep_off + te * n_states + word].ginv_off;
+    const int64_t off = P.ep[S.ep_off + tag_cur].ginv_off;
     for (int i = tid; i < n * nc; i += T) {
       const int r = i / nc, c = i - r * nc;
       gi[r * ldg + c] = P.ginv[off + i];
@@ -500,11 +508,25 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       while (te + 1 < n_te && P.ep[S.ep_off + (te + 1) * n_states].start <= step) ++te;
       next_ep_start = (te + 1 < n_te) ? P.ep[S.ep_off + (te + 1) * n_states].start : LLONG_MAX;
       word = new_word;
-      const int64_t off = P.ep[S.ep_off + te * n_states + word].ginv_off;
-      for (int i = tid; i < n * nc; i += T) {
-        const int r = i / nc, c = i - r * nc;
-        gi[r * ldg + c] = P.ginv[off + i];
-        gilo[r * ldg + c] = P.ginv_lo[off + i];
+      const int entry = te * n_states + word;
+      if (entry != tag_cur) {
+        if (P.lim.nbuf > 1) {   // the other buffer: a hit, or overwritten below
+          cur_buf ^= 1;
+          const int t = tag_cur;
+          tag_cur = tag_other;
+          tag_other = t;
+        }
+        gi = gi_buf + cur_buf * buf_len;
+        gilo = gilo_buf + cur_buf * buf_len;
+        if (entry != tag_cur) {
+          tag_cur = entry;
+          const int64_t off = P.ep[S.ep_off + entry].ginv_off;
+          for (int i = tid; i < n * nc; i += T) {
+            const int r = i / nc, c = i - r * nc;
+            gi[r * ldg + c] = P.ginv[off + i];
+            gilo[r * ldg + c] = P.ginv_lo[off + i];
+          }
+        }
       }
     }
     // next step's source voltages: load issued now, stored after process 4
