@@ -53,6 +53,8 @@ class _Net(ctypes.Structure):
         ("n_rs", ctypes.c_int64), ("rs_k", ctypes.c_void_p), ("rs_m", ctypes.c_void_p),
         ("rs_kind", ctypes.c_void_p), ("rs_ron", ctypes.c_void_p), ("rs_roff", ctypes.c_void_p),
         ("rs_on0", ctypes.c_void_p), ("rs_trip", ctypes.c_void_p),
+        ("n_cl", ctypes.c_int64), ("cl_k", ctypes.c_void_p), ("cl_m", ctypes.c_void_p),
+        ("cl_tv", ctypes.c_void_p), ("cl_z", ctypes.c_void_p), ("cl_tau", ctypes.c_void_p),
     ]
 
 
@@ -112,6 +114,10 @@ class _Pinned:
         n.rs_kind = p(rs("rs_kind", np.uint8), np.uint8)
         n.rs_ron, n.rs_roff = p(rs("rs_ron", np.float64), np.float64), p(rs("rs_roff", np.float64), np.float64)
         n.rs_on0, n.rs_trip = p(rs("rs_on0", np.uint8), np.uint8), p(rs("rs_trip", np.int64), np.int64)
+        n.n_cl = int(len(rs("cl_z", np.float64))) // 3
+        n.cl_k, n.cl_m = p(rs("cl_k", np.int32), np.int32), p(rs("cl_m", np.int32), np.int32)
+        n.cl_tv, n.cl_z = p(rs("cl_tv", np.float64), np.float64), p(rs("cl_z", np.float64), np.float64)
+        n.cl_tau = p(rs("cl_tau", np.float64), np.float64)
         self.net = n
 
     @property

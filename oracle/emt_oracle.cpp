@@ -107,6 +107,23 @@ void lu_solve_transposed(int n, const std::vector<T>& lu, const std::vector<int>
 
 // ---------------------------------------------------------------- network
 
+// Inverse of a 3 x 3 row-major matrix by cofactors; false if singular.
+bool invert3(const double* a, double* inv) {
+  const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+  const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+  if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return false;
+  inv[0] = c00 / det;
+  inv[3] = c01 / det;
+  inv[6] = c02 / det;
+  inv[1] = (a[2] * a[7] - a[1] * a[8]) / det;
+  inv[4] = (a[0] * a[8] - a[2] * a[6]) / det;
+  inv[7] = (a[1] * a[6] - a[0] * a[7]) / det;
+  inv[2] = (a[1] * a[5] - a[2] * a[4]) / det;
+  inv[5] = (a[2] * a[3] - a[0] * a[5]) / det;
+  inv[8] = (a[0] * a[4] - a[1] * a[3]) / det;
+  return true;
+}
+
 bool valid(const orc_net* net) {
   if (!net || !(net->dt > 0.0) || net->n_nodes < 0) return false;
   auto node_ok = [&](int32_t x) { return x >= -1 - net->n_src && x < net->n_nodes; };
@@ -124,6 +141,18 @@ bool valid(const orc_net* net) {
     int32_t k = net->sw_k[s], m = net->sw_m[s];
     if (k < -1 || m < -1 || k >= net->n_nodes || m >= net->n_nodes || k == m || (k < 0 && m < 0)) return false;
     if (!(net->sw_r[s] > 0.0)) return false;
+  }
+  if (net->n_cl < 0) return false;
+  for (int64_t l = 0; l < net->n_cl; ++l) {
+    for (int p = 0; p < 6; ++p) {
+      const int32_t x = p < 3 ? net->cl_k[3 * l + p] : net->cl_m[3 * l + p - 3];
+      if (x < 0 || x >= net->n_nodes) return false;
+    }
+    for (int j = 0; j < 3; ++j)
+      if (!(net->cl_z[3 * l + j] > 0.0) || !(net->cl_tau[3 * l + j] >= net->dt) || !std::isfinite(net->cl_tau[3 * l + j]))
+        return false;
+    double inv[9];
+    if (!invert3(net->cl_tv + 9 * l, inv)) return false;
   }
   if (net->n_rs < 0) return false;
   for (int64_t w = 0; w < net->n_rs; ++w) {
@@ -153,6 +182,11 @@ void components(const orc_net* net, std::vector<int>& sub, int& n_sub) {
   for (int64_t b = 0; b < net->n_br; ++b) join(net->br_k[b], net->br_m[b]);
   for (int64_t s = 0; s < net->n_sw; ++s) join(net->sw_k[s], net->sw_m[s]);
   for (int64_t w = 0; w < net->n_rs; ++w) join(net->rs_k[w], net->rs_m[w]);
+  for (int64_t l = 0; l < net->n_cl; ++l)
+    for (int p = 1; p < 3; ++p) {
+      join(net->cl_k[3 * l], net->cl_k[3 * l + p]);
+      join(net->cl_m[3 * l], net->cl_m[3 * l + p]);
+    }
   sub.assign(n, -1);
   n_sub = 0;
   std::vector<int> label(n, -1);
@@ -197,6 +231,15 @@ struct Sim {
   std::vector<T> v;      // node voltages at the current step
   std::vector<char> rs_on;     // runtime-switch state in force at the current step
   std::vector<double> rs_i;    // breaker current of the previous step
+  // coupled lines: per line T_v^-1, T_i, Y_p (3 x 3), per mode d, f, 2/Z;
+  // c values each end sent, by step modulo d + 2: cl_c[line][end][mode]
+  struct CLine {
+    double tinv[9], ti[9], yp[9], y2[3], f[3];
+    int64_t d[3];
+    std::vector<T> c[2][3];
+    T im[2][3];   // modal history currents of the current step per end
+  };
+  std::vector<CLine> cl;
 
   bool init(const T* br_value, const T* src_amp, bool monolithic) {
     n_nodes = (int)net->n_nodes;
@@ -230,7 +273,33 @@ struct Sim {
     rs_on.assign(net->n_rs, 0);
     for (int64_t w = 0; w < net->n_rs; ++w) rs_on[w] = net->rs_on0[w] ? 1 : 0;
     rs_i.assign(net->n_rs, 0.0);
+    cl.assign(net->n_cl, CLine{});
+    for (int64_t l = 0; l < net->n_cl; ++l) {
+      CLine& L = cl[l];
+      invert3(net->cl_tv + 9 * l, L.tinv);
+      for (int p = 0; p < 3; ++p)
+        for (int j = 0; j < 3; ++j) L.ti[3 * p + j] = L.tinv[3 * j + p];   // T_i = (T_v^-1)^T
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) {
+          double acc = 0.0;
+          for (int j = 0; j < 3; ++j) acc += L.ti[3 * p + j] * (1.0 / net->cl_z[3 * l + j]) * L.tinv[3 * j + q];
+          L.yp[3 * p + q] = acc;
+        }
+      for (int j = 0; j < 3; ++j) {
+        const double steps = net->cl_tau[3 * l + j] / net->dt;
+        L.d[j] = (int64_t)std::floor(steps);
+        L.f[j] = steps - (double)L.d[j];
+        L.y2[j] = 2.0 / net->cl_z[3 * l + j];
+        for (int e = 0; e < 2; ++e) L.c[e][j].assign(L.d[j] + 2, T(0.0));
+      }
+    }
     return true;
+  }
+
+  // c value end e of coupled line L sent at step m (0 before the start)
+  T cl_sent(const CLine& L, int e, int j, int64_t m) const {
+    if (m < 1) return T(0.0);
+    return L.c[e][j][m % (L.d[j] + 2)];
   }
 
   // Runtime switches: the states in force at step n+1 from step n's solution.
@@ -291,6 +360,13 @@ struct Sim {
       int a = net->rs_k[w] >= 0 ? net->rs_k[w] : net->rs_m[w];
       if (sub[a] == s) stamp(net->rs_k[w], net->rs_m[w], T(1.0) / T(rs_on[w] ? net->rs_ron[w] : net->rs_roff[w]));
     }
+    for (int64_t l = 0; l < net->n_cl; ++l)
+      for (int e = 0; e < 2; ++e) {
+        const int32_t* nd = (e == 0 ? net->cl_k : net->cl_m) + 3 * l;
+        if (sub[nd[0]] != s) continue;
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) G[(size_t)local[nd[p]] * ns + local[nd[q]]] += T(cl[l].yp[3 * p + q]);
+      }
     lu[s] = G;
     return lu_factor(ns, lu[s], piv[s]);
   }
@@ -322,6 +398,22 @@ struct Sim {
       rhs[net->ln_k[l]] -= ring_k[l][n % d1];
       rhs[net->ln_m[l]] -= ring_m[l][n % d1];
     }
+    // coupled lines: modal histories from the far end's sent values, then
+    // phase-domain history currents T_i I_mode leaving each end's nodes
+    for (int64_t l = 0; l < net->n_cl; ++l) {
+      CLine& L = cl[l];
+      for (int e = 0; e < 2; ++e) {
+        for (int j = 0; j < 3; ++j)
+          L.im[e][j] = T(1.0 - L.f[j]) * cl_sent(L, 1 - e, j, n - L.d[j]) +
+                       T(L.f[j]) * cl_sent(L, 1 - e, j, n - L.d[j] - 1);
+        const int32_t* nd = (e == 0 ? net->cl_k : net->cl_m) + 3 * l;
+        for (int p = 0; p < 3; ++p) {
+          T ip = T(0.0);
+          for (int j = 0; j < 3; ++j) ip += T(L.ti[3 * p + j]) * L.im[e][j];
+          rhs[nd[p]] -= ip;
+        }
+      }
+    }
     // processes 3 and 4 per subsystem
     for (int s = 0; s < n_sub; ++s) {
       if (!refactor_if_needed(s, n)) return false;
@@ -345,6 +437,18 @@ struct Sim {
       T ik = ring_k[l][n % d1], im = ring_m[l][n % d1];
       ring_m[l][(n + d) % d1] = -y2 * v[net->ln_k[l]] - ik;
       ring_k[l][(n + d) % d1] = -y2 * v[net->ln_m[l]] - im;
+    }
+    // coupled lines: each end sends c_j(n) = -(2/Z_j) v_mode_j(n) - I_mode_j(n)
+    for (int64_t l = 0; l < net->n_cl; ++l) {
+      CLine& L = cl[l];
+      for (int e = 0; e < 2; ++e) {
+        const int32_t* nd = (e == 0 ? net->cl_k : net->cl_m) + 3 * l;
+        for (int j = 0; j < 3; ++j) {
+          T vm = T(0.0);
+          for (int p = 0; p < 3; ++p) vm += T(L.tinv[3 * j + p]) * v[nd[p]];
+          L.c[e][j][n % (L.d[j] + 2)] = -T(L.y2[j]) * vm - L.im[e][j];
+        }
+      }
     }
     decide_runtime_switches(n);
     return true;
@@ -420,7 +524,7 @@ extern "C" int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_
 // and finally dg/dR = -1/R^2, dg/dL = -dt/(2L^2), dg/dC = 2/dt.
 extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad,
                            double* loss) {
-  if (!valid(net) || !v_target || !grad || n_steps < 0 || net->n_rs > 0) return -1;
+  if (!valid(net) || !v_target || !grad || n_steps < 0 || net->n_rs > 0 || net->n_cl > 0) return -1;
   const int64_t nn = net->n_nodes, nb = net->n_br, ns = net->n_src, nl = net->n_ln;
   Sim<double> sim;
   sim.net = net;

@@ -60,6 +60,22 @@ typedef struct {
   const double* rs_roff;
   const uint8_t* rs_on0;
   const int64_t* rs_trip;
+  /* Coupled three-phase lossless lines, modal form (Bergeron per mode):
+   *   cl_k[3 l + p], cl_m[3 l + p]: phase p's node at end k / end m;
+   *   cl_tv[9 l + 3 p + j]: T_v, phase voltages = T_v modal voltages
+   *     (modal currents: T_i = T_v^-T);
+   *   cl_z[3 l + j], cl_tau[3 l + j]: mode j's Z_c (ohm) and travel time
+   *     (s, at least dt).
+   * Each end draws i_p = Y_p v_p + T_i I_mode with Y_p = T_i diag(1/Z) T_v^-1;
+   * mode j sends c_j(n) = -(2/Z_j) v_mode_j(n) - I_mode_j(n) to the far end,
+   * whose history at step n is (1 - f_j) c_j(n - d_j) + f_j c_j(n - d_j - 1),
+   * tau_j = (d_j + f_j) dt, d_j = floor(tau_j / dt). */
+  int64_t n_cl;
+  const int32_t* cl_k;
+  const int32_t* cl_m;
+  const double* cl_tv;
+  const double* cl_z;
+  const double* cl_tau;
 } orc_net;
 
 /* Run n_steps steps from the de-energised state.
@@ -87,7 +103,7 @@ int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_target, int
 
 /* Discrete adjoint of the loss over the full stored trajectory.
  * grad: [n_br + n_src] = dJ/d(branch value) then dJ/d(source amplitude).
- * Networks with runtime switches are rejected (-1). */
+ * Networks with runtime switches or coupled lines are rejected (-1). */
 int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad, double* loss);
 
 /* Subsystem of each unknown node (components over branches and switches). */

@@ -73,6 +73,14 @@ class Network:
     rs_roff: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
     rs_on0: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint8))
     rs_trip: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
+    # coupled three-phase lossless lines in modal form: phase nodes per end
+    # [3 L], T_v [9 L] (phase voltages = T_v modal voltages), modal Z_c and
+    # travel times in seconds [3 L]
+    cl_k: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    cl_m: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    cl_tv: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    cl_z: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    cl_tau: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
     n_steps: int = 0            # suggested run length
     meta: dict = field(default_factory=dict)
 
@@ -95,6 +103,10 @@ class Network:
     @property
     def n_runtime_switches(self) -> int:
         return int(self.rs_k.shape[0])
+
+    @property
+    def n_coupled_lines(self) -> int:
+        return int(self.cl_z.shape[0]) // 3
 
     def copy(self) -> "Network":
         kw = {}
@@ -215,6 +227,7 @@ class NetworkBuilder:
         self.ln = []     # (k, m, zc, d)
         self.sw = []     # (k, m, r, close, open)
         self.rs = []     # (k, m, kind, r_on, r_off, on0, trip)
+        self.cl = []     # (k3, m3, tv9, z3, tau3)
 
     def branch(self, k, m, kind, value):
         self.br.append((int(k), int(m), int(kind), float(value)))
@@ -237,6 +250,11 @@ class NetworkBuilder:
     def breaker(self, k, m, r_on, r_off, trip_step):
         self.rs.append((int(k), int(m), 1, float(r_on), float(r_off), 1, int(trip_step)))
 
+    def coupled_line(self, k3, m3, tv, z3, tau3):
+        """Three-phase lossless line in modal form (see ``Network.cl_*``)."""
+        self.cl.append(([int(x) for x in k3], [int(x) for x in m3], np.asarray(tv, np.float64).reshape(9),
+                        np.asarray(z3, np.float64).reshape(3), np.asarray(tau3, np.float64).reshape(3)))
+
     def build(self, dt, n_nodes, n_steps=0, meta=None) -> Network:
         def col(lst, i, dt_):
             return np.ascontiguousarray(np.array([x[i] for x in lst], dtype=dt_))
@@ -254,6 +272,11 @@ class NetworkBuilder:
             rs_k=col(self.rs, 0, np.int32), rs_m=col(self.rs, 1, np.int32), rs_kind=col(self.rs, 2, np.uint8),
             rs_ron=col(self.rs, 3, np.float64), rs_roff=col(self.rs, 4, np.float64),
             rs_on0=col(self.rs, 5, np.uint8), rs_trip=col(self.rs, 6, np.int64),
+            cl_k=np.ascontiguousarray(np.array([x for c in self.cl for x in c[0]], np.int32)),
+            cl_m=np.ascontiguousarray(np.array([x for c in self.cl for x in c[1]], np.int32)),
+            cl_tv=np.ascontiguousarray(np.concatenate([c[2] for c in self.cl]) if self.cl else np.zeros(0)),
+            cl_z=np.ascontiguousarray(np.concatenate([c[3] for c in self.cl]) if self.cl else np.zeros(0)),
+            cl_tau=np.ascontiguousarray(np.concatenate([c[4] for c in self.cl]) if self.cl else np.zeros(0)),
             n_steps=int(n_steps), meta=dict(meta or {}))
 
 
@@ -615,3 +638,10 @@ def with_rectifier_loads(base: Network, seed: int = 1006, n_rectifiers: int = 30
     net.rs_trip = np.asarray(rs["trip"], np.int64)
     net.meta = dict(net.meta, runtime_switches={"seed": seed, "rectifiers": n_rectifiers, "breakers": n_breakers})
     return net
+
+
+# Power-invariant Clarke transformation (rows: phases a, b, c; columns:
+# modes 0, alpha, beta); orthonormal, so T_i = T_v for a transposed line.
+CLARKE = np.array([[1 / np.sqrt(3), 2 / np.sqrt(6), 0.0],
+                   [1 / np.sqrt(3), -1 / np.sqrt(6), 1 / np.sqrt(2)],
+                   [1 / np.sqrt(3), -1 / np.sqrt(6), -1 / np.sqrt(2)]])
