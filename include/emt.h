@@ -68,7 +68,17 @@ typedef struct emt_ctx emt_ctx;  /* opaque; owns all device memory it allocates 
  *   runtime switches gets a prefactored G^-1 for every one of its 2^k
  *   states (k <= 8 per subsystem), and the time loop switches matrices
  *   when a state changes.  Not supported with a scenario set or by
- *   emt_adjoint. */
+ *   emt_adjoint.
+ * Coupled three-phase lossless lines in modal form (n_clines may be 0):
+ *   cl_k[3 l + p] / cl_m[3 l + p]: phase p's node (unknown) at each end;
+ *   cl_tv[9 l + 3 p + j]: T_v, phase voltages = T_v modal voltages (modal
+ *   currents use T_i = T_v^-T); cl_z[3 l + j], cl_tau[3 l + j]: mode j's
+ *   Z_c (ohm) and travel time (s, >= dt, any real value).  Each end draws
+ *   i_p = Y_p v_p + T_i I_mode with Y_p = T_i diag(1/Z) T_v^-1; mode j sends
+ *   c_j(n) = -(2/Z_j) v_mode_j(n) - I_mode_j(n), and the far end's history
+ *   is (1 - f) c(n - d) + f c(n - d - 1), tau = (d + f) dt, d = floor(tau/dt)
+ *   (linear interpolation of the travel time).  An end's three phase nodes
+ *   are one subsystem.  Not supported with a scenario set or by emt_adjoint. */
 typedef struct {
   double dt;
   int64_t n_nodes;
@@ -100,6 +110,12 @@ typedef struct {
   const double* rs_roff;
   const uint8_t* rs_on0;
   const int64_t* rs_trip_step;
+  int64_t n_clines;
+  const int32_t* cl_k;
+  const int32_t* cl_m;
+  const double* cl_tv;
+  const double* cl_z;
+  const double* cl_tau;
 } emt_network_desc;
 
 /* Optional per-scenario overrides of one base network (the paper's
@@ -255,6 +271,7 @@ emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
  * "threads_per_cta", "kernel_launches", "n_nodes", "n_branches", "n_sources", "n_line_ends",
  * "smem_bytes" (dynamic shared memory per CTA of the persistent kernel),
  * "n_strong_branches" (L/C branches applied through extra solve columns),
+ * "n_runtime_switches", "n_coupled_lines",
  * "n_matrix_variants", "scenarios_per_cta", "batch_threads", "batch_groups"
  * (subsystem groups per step of the multi-scenario kernel),
  * "graph_launches", "autotuned". */

@@ -62,9 +62,10 @@ struct emt_ctx {
   std::vector<int32_t> nb_sub, nb_dmin;
   std::vector<SwitchDev> switches;
   std::vector<RuntimeSwitchDev> rswitches;             // runtime switches, grouped by subsystem
+  std::vector<CoupledEndDev> cends;                    // coupled line ends, grouped by subsystem
   std::vector<int32_t> rs_word0;                       // per subsystem: state word at step 1
   int64_t ring_len = 0, ginv_len = 0, n_lc_total = 0;
-  FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1};
+  FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0};
 
   // device arrays
   SubDev* d_sub = nullptr;
@@ -93,6 +94,8 @@ struct emt_ctx {
   int64_t src_table_steps = 0;
   SwitchDev* d_sw = nullptr;
   RuntimeSwitchDev* d_rs = nullptr;
+  CoupledEndDev* d_ce = nullptr;
+  double* d_le_prev = nullptr;
   int32_t* d_rs_word = nullptr;
   double* d_rs_prev_i = nullptr;
   double* d_ginv = nullptr;
@@ -209,6 +212,24 @@ namespace {
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
+// Inverse of a 3 x 3 row-major matrix (cofactors); false if singular.
+bool invert3_host(const double* a, double* inv) {
+  const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+  const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+  if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return false;
+  inv[0] = c00 / det;
+  inv[3] = c01 / det;
+  inv[6] = c02 / det;
+  inv[1] = (a[2] * a[7] - a[1] * a[8]) / det;
+  inv[4] = (a[0] * a[8] - a[2] * a[6]) / det;
+  inv[7] = (a[1] * a[6] - a[0] * a[7]) / det;
+  inv[2] = (a[1] * a[5] - a[2] * a[4]) / det;
+  inv[5] = (a[2] * a[3] - a[0] * a[5]) / det;
+  inv[8] = (a[0] * a[4] - a[1] * a[3]) / det;
+  return true;
+}
+
+
 std::string validate(const emt_network_desc* d) {
   if (!d) return "desc is NULL";
   if (!finite_pos(d->dt)) return "dt must be finite and > 0";
@@ -237,6 +258,23 @@ std::string validate(const emt_network_desc* d) {
     if (d->ln_delay[l] < 1) return "line " + std::to_string(l) + ": delay must be >= 1 step";
     if (d->ln_delay[l] > (1 << 20)) return "line " + std::to_string(l) + ": delay too large";
     if (!finite_pos(d->ln_zc[l])) return "line " + std::to_string(l) + ": Z_c must be finite and > 0";
+  }
+  if (d->n_clines < 0) return "negative count";
+  if (d->n_clines && (!d->cl_k || !d->cl_m || !d->cl_tv || !d->cl_z || !d->cl_tau)) return "coupled line array is NULL";
+  for (int64_t l = 0; l < d->n_clines; ++l) {
+    const std::string nm = "coupled line " + std::to_string(l);
+    for (int p = 0; p < 3; ++p)
+      if (d->cl_k[3 * l + p] < 0 || d->cl_k[3 * l + p] >= d->n_nodes || d->cl_m[3 * l + p] < 0 ||
+          d->cl_m[3 * l + p] >= d->n_nodes)
+        return nm + ": ends must be unknown nodes";
+    for (int j = 0; j < 3; ++j) {
+      if (!finite_pos(d->cl_z[3 * l + j])) return nm + ": Z_c must be finite and > 0";
+      if (!std::isfinite(d->cl_tau[3 * l + j]) || !(d->cl_tau[3 * l + j] >= d->dt))
+        return nm + ": travel times must be finite and at least dt";
+      if (d->cl_tau[3 * l + j] / d->dt > (double)(1 << 20)) return nm + ": travel time too large";
+    }
+    double inv[9];
+    if (!invert3_host(d->cl_tv + 9 * l, inv)) return nm + ": T_v is singular";
   }
   if (d->n_rswitches < 0) return "negative count";
   if (d->n_rswitches && (!d->rs_k || !d->rs_m || !d->rs_kind || !d->rs_ron || !d->rs_roff || !d->rs_on0 ||
@@ -650,6 +688,11 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   for (int64_t b = 0; b < d->n_branches; ++b) join(d->br_k[b], d->br_m[b]);
   for (int64_t w = 0; w < d->n_switches; ++w) join(d->sw_k[w], d->sw_m[w]);
   for (int64_t w = 0; w < d->n_rswitches; ++w) join(d->rs_k[w], d->rs_m[w]);
+  for (int64_t l = 0; l < d->n_clines; ++l)   // an end's phases are coupled by Y_p
+    for (int p = 1; p < 3; ++p) {
+      join(d->cl_k[3 * l], d->cl_k[3 * l + p]);
+      join(d->cl_m[3 * l], d->cl_m[3 * l + p]);
+    }
   if (scen && scen->sw_ptr)   // scenario switches may join nodes too
     for (int64_t w = 0; w < scen->sw_ptr[scen->n_scenarios]; ++w) join(scen->sw_k[w], scen->sw_m[w]);
   c->sub_of_node.assign(N, -1);
@@ -770,6 +813,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
 
   // -------- line ends: end 2l at ln_k, end 2l+1 at ln_m; ring depth 2d
   std::vector<int64_t> ring_off(2 * d->n_lines);
+  std::vector<int64_t> cl_ring, cl_d;
   {
     int64_t off = 0;
     for (int64_t l = 0; l < d->n_lines; ++l) {
@@ -779,8 +823,23 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       ring_off[2 * l + 1] = off;
       off += depth;
     }
+    // coupled lines: one ring per (end, mode), depth 2 floor(tau / dt)
+    cl_ring.assign(6 * d->n_clines, 0);
+    cl_d.assign(3 * d->n_clines, 0);
+    for (int64_t l = 0; l < d->n_clines; ++l)
+      for (int j = 0; j < 3; ++j) {
+        const int64_t dd = (int64_t)std::floor(d->cl_tau[3 * l + j] / d->dt);
+        cl_d[3 * l + j] = dd;
+        for (int e = 0; e < 2; ++e) {
+          cl_ring[6 * l + 3 * e + j] = off;
+          off += 2 * dd;
+        }
+      }
     c->ring_len = off;
   }
+  std::vector<std::vector<int64_t>> cends_of(S);   // coupled ends (2 l + e) per subsystem
+  for (int64_t x = 0; x < 2 * d->n_clines; ++x)
+    cends_of[c->sub_of_node[(x & 1) ? d->cl_m[3 * (x >> 1)] : d->cl_k[3 * (x >> 1)]]].push_back(x);
   std::vector<std::vector<int64_t>> ends_of(S);
   std::vector<int64_t> le_of_end(2 * d->n_lines, -1);
   for (int64_t e = 0; e < 2 * d->n_lines; ++e) {
@@ -797,6 +856,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       const int far_node = (e & 1) ? d->ln_k[l] : d->ln_m[l];
       LineEndDev le{};
       le.node = local[node];
+      le.ce = -1;
       le.d = d->ln_delay[l];
       le.depth = 2 * d->ln_delay[l];
       le.y = 1.0 / d->ln_zc[l];
@@ -811,6 +871,41 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
         if (it == dmin.end() || it->second > le.d) dmin[fs] = le.d;
       }
     }
+    // coupled line ends: a record each, then its three modes as line ends
+    sd.ce_off = (int)c->cends.size();
+    for (int64_t x : cends_of[s]) {
+      const int64_t l = x >> 1;
+      const int e = (int)(x & 1);
+      const int32_t* nd = (e ? d->cl_m : d->cl_k) + 3 * l;
+      CoupledEndDev ce{};
+      for (int p = 0; p < 3; ++p) ce.node[p] = local[nd[p]];
+      ce.le0 = (int)c->line_ends.size() - sd.le_off;
+      for (int k = 0; k < 9; ++k) ce.tv[k] = d->cl_tv[9 * l + k];
+      for (int j = 0; j < 3; ++j) ce.z[j] = d->cl_z[3 * l + j];
+      const int ce_local = (int)c->cends.size() - sd.ce_off;
+      c->cends.push_back(ce);
+      const int fs = c->sub_of_node[(e ? d->cl_k : d->cl_m)[3 * l]];
+      for (int j = 0; j < 3; ++j) {
+        LineEndDev le{};
+        le.node = -1;
+        le.d = (int32_t)cl_d[3 * l + j];
+        le.depth = 2 * le.d;
+        le.ce = ce_local;
+        le.mode = j;
+        le.f = d->cl_tau[3 * l + j] / d->dt - (double)cl_d[3 * l + j];
+        le.y2 = 2.0 / d->cl_z[3 * l + j];
+        le.y = 0.0;
+        le.own_ring = cl_ring[6 * l + 3 * e + j];
+        le.far_ring = cl_ring[6 * l + 3 * (1 - e) + j];
+        c->line_ends.push_back(le);
+        if (fs != s) {
+          auto it = dmin.find(fs);
+          if (it == dmin.end() || it->second > le.d) dmin[fs] = le.d;
+        }
+      }
+    }
+    sd.n_ce = (int)c->cends.size() - sd.ce_off;
+    c->lim.ce = std::max(c->lim.ce, sd.n_ce);
     sd.n_le = (int)c->line_ends.size() - sd.le_off;
     c->lim.le = std::max(c->lim.le, sd.n_le);
     sd.nb_off = (int)c->nb_sub.size();
@@ -836,7 +931,15 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       if (x.k >= 0) diag[x.k] += g;
       if (x.m >= 0) diag[x.m] += g;
     }
-    for (int e = sd.le_off; e < sd.le_off + sd.n_le; ++e) diag[c->line_ends[e].node] += c->line_ends[e].y;
+    for (int e = sd.le_off; e < sd.le_off + sd.n_le; ++e)
+      if (c->line_ends[e].node >= 0) diag[c->line_ends[e].node] += c->line_ends[e].y;
+    for (int x = sd.ce_off; x < sd.ce_off + sd.n_ce; ++x) {   // Y_p diagonal of coupled ends
+      const CoupledEndDev& ce = c->cends[x];
+      double inv[9];
+      invert3_host(ce.tv, inv);
+      for (int p = 0; p < 3; ++p)
+        for (int j = 0; j < 3; ++j) diag[ce.node[p]] += inv[3 * j + p] * inv[3 * j + p] / ce.z[j];
+    }
     sd.str_off = (int)c->str_slot.size();
     std::vector<std::pair<double, int>> cand;   // (ratio, branch), strongest first
     for (int b = sd.br_off; b < sd.br_off + sd.n_br; ++b) {
@@ -869,7 +972,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   for (int s = 0; s < S; ++s) {
     SubDev& sd = c->subs[s];
     std::vector<std::vector<int32_t>> el(sd.n);
-    const int ie_base = sd.n_lc + sd.n_sb, zero = ie_base + 2 * sd.n_le;
+    const int ie_base = sd.n_lc + sd.n_sb, zero = ie_base + 2 * (sd.n_le + 3 * sd.n_ce);
     for (int b = sd.br_off; b < sd.br_off + sd.n_br; ++b) {
       const BranchDev& x = c->branches[b];
       if (x.kind != 0 && !strong[b]) {
@@ -880,7 +983,12 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       if (sb_slot_of[b] >= 0) el[x.k >= 0 ? x.k : x.m].push_back(sd.n_lc + sb_slot_of[b]);
     }
     for (int e = 0; e < sd.n_le; ++e)
-      el[c->line_ends[sd.le_off + e].node].push_back((int32_t)(kEntryNeg | (uint32_t)(ie_base + e)));
+      if (c->line_ends[sd.le_off + e].node >= 0)
+        el[c->line_ends[sd.le_off + e].node].push_back((int32_t)(kEntryNeg | (uint32_t)(ie_base + e)));
+    for (int x = 0; x < sd.n_ce; ++x)   // coupled ends: phase-domain history currents leave the phase nodes
+      for (int p = 0; p < 3; ++p)
+        el[c->cends[sd.ce_off + x].node[p]].push_back(
+            (int32_t)(kEntryNeg | (uint32_t)(ie_base + sd.n_le + 3 * x + p)));
     sd.il_off = (int)c->il_node.size();
     int lanes = 0;
     for (int k = 0; k < sd.n; ++k) {
@@ -1020,6 +1128,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
 
   // -------- multi-scenario set
   if (scen && !c->rswitches.empty()) return bail("runtime switches are not supported with a scenario set");
+  if (scen && !c->cends.empty()) return bail("coupled lines are not supported with a scenario set");
   if (scen) {
     const std::string bm = build_scenarios(c, d, scen, local, new_of_orig, le_of_end, lc_slot_of, sb_slot_of);
     if (!bm.empty()) return bail(bm);
@@ -1045,6 +1154,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   UP(d_src_omega, src_omega)
   UP(d_sw, switches)
   UP(d_rs, rswitches)
+  UP(d_ce, cends)
   UP(d_rs_word, rs_word0)
   UP(d_br_orig, br_orig)
   UP(d_br_lc, br_lc)
@@ -1058,6 +1168,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ginv_lo, (size_t)c->ginv_len);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_err, 4);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_rs_prev_i, c->rswitches.size());
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_le_prev, c->line_ends.size());
   if (e == cudaSuccess) e = c->upload(&c->d_node_l0, c->node_l0);
   if (e == cudaSuccess) e = c->upload(&c->d_node_nl, c->node_nl);
   if (c->batched) {
@@ -1102,6 +1213,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
 #undef UP
   if (e == cudaSuccess && c->batched && !batch_configure(c, c->S_t, true)) e = cudaErrorMemoryAllocation;
   if (e == cudaSuccess) e = launch_companion(c->d_br, (int64_t)c->branches.size(), c->dt, nullptr);
+  if (e == cudaSuccess) e = launch_coupled_constants(c->d_ce, (int64_t)c->cends.size(), nullptr);
   if (e == cudaSuccess && c->batched)
     e = launch_source_coefficients(c->d_bsrc_amp, c->d_bsrc_phase, c->S * c->n_sources, c->d_src_ac, c->d_src_as,
                                    nullptr);
@@ -1151,6 +1263,7 @@ extern "C" emt_status emt_prefactor(emt_ctx* c) {
   p.br = c->d_br;
   p.le = c->d_le;
   p.sw = c->d_sw;
+  p.ce = c->d_ce;
   p.lc_idx = c->d_lc_idx;
   p.str_slot = c->d_str_slot;
   p.ginv = c->d_ginv;
@@ -1340,6 +1453,8 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
   p.n_rec = rs.n_rec;
   p.wait_budget_ns = c->wait_budget_ns;
   p.hold_sub = c->hold_sub;
+  p.ce = c->d_ce;
+  p.le_prev = c->d_le_prev;
   p.rs = c->d_rs;
   p.rs_word = c->d_rs_word;
   p.rs_prev_i = c->d_rs_prev_i;
@@ -1469,6 +1584,8 @@ extern "C" emt_status emt_reset(emt_ctx* c) {
     e = cudaMemcpy(c->d_rs_word, c->rs_word0.data(), c->rs_word0.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !c->rswitches.empty())
     e = cudaMemset(c->d_rs_prev_i, 0, c->rswitches.size() * sizeof(double));
+  if (e == cudaSuccess && !c->line_ends.empty())
+    e = cudaMemset(c->d_le_prev, 0, c->line_ends.size() * sizeof(double));
   if (c->batched) {
     if (e == cudaSuccess) e = cudaMemset(c->d_bh, 0, std::max<size_t>((size_t)c->n_lc_total * c->S, 1) * sizeof(double));
     if (e == cudaSuccess)
@@ -1599,6 +1716,7 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "n_line_ends") *value = (int64_t)c->line_ends.size();
   else if (k == "n_strong_branches") *value = (int64_t)c->str_slot.size();
   else if (k == "n_runtime_switches") *value = (int64_t)c->rswitches.size();
+  else if (k == "n_coupled_lines") *value = (int64_t)c->cends.size() / 2;
   else if (k == "smem_bytes") *value = (int64_t)forward_smem_bytes(c->lim);
   else return EMT_EINVAL;
   return EMT_OK;
@@ -1633,6 +1751,7 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
   if (!c) return EMT_EINVAL;
   if (c->batched) return c->fail(EMT_EINVAL, "emt_adjoint: a context built with a scenario set has no adjoint");
   if (!c->rswitches.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: networks with runtime switches have no adjoint");
+  if (!c->cends.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: networks with coupled lines have no adjoint");
   if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
   if (n_steps < 1) return c->fail(EMT_EINVAL, "emt_adjoint: n_steps must be >= 1");
   if (n_steps > (int64_t)INT32_MAX - (int64_t)(1 << 21))
@@ -1986,6 +2105,7 @@ extern "C" emt_status emt_prefactor_noalloc(emt_ctx* c, void* stream) {
   p.br = c->d_br;
   p.le = c->d_le;
   p.sw = c->d_sw;
+  p.ce = c->d_ce;
   p.lc_idx = c->d_lc_idx;
   p.str_slot = c->d_str_slot;
   p.ginv = c->d_ginv;

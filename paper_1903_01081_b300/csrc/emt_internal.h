@@ -47,14 +47,32 @@ struct BranchDev {
 // end's write at step m carries a value computed from this end's output of
 // step m - d, which this end produced after reading the slot.
 struct LineEndDev {
-  int32_t node;        // local node of this end
-  int32_t d;           // travel time in steps
+  int32_t node;        // local node of this end (-1: a mode of a coupled line end)
+  int32_t d;           // travel time in steps (whole part)
   int32_t depth;       // ring depth D = 2d
-  int32_t pad;
+  int32_t ce;          // coupled line end (subsystem-local) this mode belongs to, or -1
   double y2;           // 2 / Z_c
-  double y;            // 1 / Z_c
+  double y;            // 1 / Z_c (shunt stamped at node; 0 for modes, whose ends stamp Y_p)
   int64_t own_ring;    // first slot of this end's ring (values consumed here)
   int64_t far_ring;    // first slot of the far end's ring (values produced here)
+  int32_t mode;        // mode index within its coupled end (0..2)
+  int32_t pad;
+  double f;            // fractional travel time: history = (1 - f) c(n - d) + f c(n - d - 1)
+};
+
+// One end of a coupled three-phase lossless line in modal form.  Its three
+// modes are consecutive line ends starting at le0; the phase-domain history
+// currents T_i I_mode leave its three phase nodes, and the end stamps
+// Y_p = T_i diag(1/Z) T_v^-1 into G (T_i = T_v^-T).  tinv, ti and yp are
+// computed on the device from tv and z.
+struct CoupledEndDev {
+  int32_t node[3];     // phase nodes (subsystem-local)
+  int32_t le0;         // subsystem-local index of the mode-0 line end
+  double tv[9];        // T_v (phase voltages = T_v modal voltages), row-major
+  double z[3];         // modal Z_c
+  double tinv[9];      // T_v^-1
+  double ti[9];        // T_i
+  double yp[9];        // Y_p
 };
 
 // A switch in device form (subsystem-local ends, -1 = ground).
@@ -79,6 +97,7 @@ struct SubDev {
   int32_t q;                   // column blocks per row in the matvec
   int32_t n_states;            // 2^(runtime switches): solve matrices per switch epoch
   int32_t rs_off, n_rs;        // runtime switches (RuntimeSwitchDev list)
+  int32_t ce_off, n_ce;        // coupled line ends (CoupledEndDev list)
 };
 
 // Maximum runtime switches per subsystem (2^k solve matrices each epoch).
@@ -119,6 +138,7 @@ struct EpochDev {
 struct FwdLimits {
   int32_t n, nc, q, lc, sb, le, src, il, str;
   int32_t nbuf;                // solve-matrix buffers in shared memory: 1, or 2 (the last two states kept)
+  int32_t ce;                  // coupled line ends per subsystem
 };
 
 struct FwdParams {
@@ -152,6 +172,8 @@ struct FwdParams {
   int64_t n_steps;
   unsigned long long wait_budget_ns;
   int32_t hold_sub;            // debug: this subsystem never writes its line outputs (-1: none)
+  const CoupledEndDev* ce;     // coupled line ends (SubDev ce_off / n_ce)
+  double* le_prev;             // per line end: value consumed at step n0 - 1 (modes' interpolation)
   const RuntimeSwitchDev* rs;  // runtime switches (SubDev rs_off / n_rs)
   int32_t* rs_word;            // per subsystem: state word in force at step n0 (carried across launches)
   double* rs_prev_i;           // per runtime switch: breaker current of the previous step
@@ -166,6 +188,7 @@ struct PrefParams {
   const BranchDev* br;
   const LineEndDev* le;
   const SwitchDev* sw;
+  const CoupledEndDev* ce;     // coupled line ends: Y_p blocks
   const int32_t* lc_idx;       // branch index per L/C slot
   const int32_t* str_slot;     // L/C slot of each strong branch
   double* ginv;                // X_hi: G^-1 rounded to double
@@ -328,6 +351,7 @@ struct RingInitParams {
 // kernels / launchers (emt_kernels.cu)
 cudaError_t launch_ring_init(const RingInitParams& p, cudaStream_t st);
 cudaError_t launch_companion(BranchDev* br, int64_t n_br, double dt, cudaStream_t st);
+cudaError_t launch_coupled_constants(CoupledEndDev* ce, int64_t n_ce, cudaStream_t st);
 cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st);
 cudaError_t launch_sources(const SourceParams& p, cudaStream_t st);
 cudaError_t launch_forward(const FwdParams& p, cudaStream_t st);

@@ -68,6 +68,38 @@ __global__ void companion_kernel(BranchDev* br, int64_t n_br, double dt) {
   br[b].e = x.kind == 1 ? 2.0 * g : (x.kind == 2 ? -2.0 * g : 0.0);
 }
 
+// ------------------------------------------------------------ coupled lines
+
+// Per coupled line end: T_v^-1 (cofactors), T_i = T_v^-T and
+// Y_p = T_i diag(1/Z) T_v^-1.
+__global__ void coupled_constants_kernel(CoupledEndDev* ce, int64_t n_ce) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_ce) return;
+  CoupledEndDev& c = ce[i];
+  const double* a = c.tv;
+  const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+  const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+  double inv[9];
+  inv[0] = c00 / det;
+  inv[3] = c01 / det;
+  inv[6] = c02 / det;
+  inv[1] = (a[2] * a[7] - a[1] * a[8]) / det;
+  inv[4] = (a[0] * a[8] - a[2] * a[6]) / det;
+  inv[7] = (a[1] * a[6] - a[0] * a[7]) / det;
+  inv[2] = (a[1] * a[5] - a[2] * a[4]) / det;
+  inv[5] = (a[2] * a[3] - a[0] * a[5]) / det;
+  inv[8] = (a[0] * a[4] - a[1] * a[3]) / det;
+  for (int k = 0; k < 9; ++k) c.tinv[k] = inv[k];
+  for (int p = 0; p < 3; ++p)
+    for (int j = 0; j < 3; ++j) c.ti[3 * p + j] = inv[3 * j + p];
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) {
+      double acc = 0.0;
+      for (int j = 0; j < 3; ++j) acc += c.ti[3 * p + j] * (1.0 / c.z[j]) * inv[3 * j + q];
+      c.yp[3 * p + q] = acc;
+    }
+}
+
 // ------------------------------------------------------------ prefactor
 
 __device__ __forceinline__ void stamp(double* A, int n, int k, int m, double g) {
@@ -107,7 +139,12 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
       for (int x = rl0; x < rl1; ++x) removed |= (P.rm_le[x] == S.le_off + e);
       if (removed) continue;
       const LineEndDev le = P.le[S.le_off + e];
-      A[le.node * n + le.node] += le.y;
+      if (le.node >= 0) A[le.node * n + le.node] += le.y;
+    }
+    for (int x = 0; x < S.n_ce; ++x) {   // coupled line ends: the 3 x 3 block Y_p
+      const CoupledEndDev& c = P.ce[S.ce_off + x];
+      for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) A[c.node[p] * n + c.node[q]] += c.yp[3 * p + q];
     }
     for (int w = 0; w < E.n_sw; ++w) {
       const SwitchDev sw = P.sw[E.sw_off + w];
@@ -279,9 +316,10 @@ constexpr int kItemThreads = kFwdThreads - 32;
 // rows are stored with an odd stride (n | 1) so that the rows a warp reads
 // together fall in different banks.
 struct FwdSmem {
-  size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar;   // 8-byte
-  size_t gilo, ivf;                                                 // float
-  size_t lck, lcm, lckind, lcstr, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, recp;   // int
+  size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar, lef, imode, ceti, cetinv;   // 8-byte
+  size_t gilo, ivf;                                                                        // float
+  size_t lck, lcm, lckind, lcstr, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, recp,
+      lece, lemode, cele0, cenode;                                                         // int
   size_t bytes;
 };
 
@@ -296,13 +334,17 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.part = d((size_t)L.n * L.q);
   s.iv = d(L.nc);
   s.vv = d(L.n);
-  s.inp = d((size_t)L.lc + L.sb + 2 * (size_t)L.le + 1);
+  s.inp = d((size_t)L.lc + L.sb + 2 * ((size_t)L.le + 3 * (size_t)L.ce) + 1);
   s.vs = d(2 * (size_t)L.src);
   s.lce = d(L.lc);
   s.sbg = d(L.sb);
   s.ley2 = d(L.le);
   s.leown = d(L.le);
   s.lefar = d(L.le);
+  s.lef = d(L.le);
+  s.imode = d(2 * (size_t)L.le);
+  s.ceti = d(9 * (size_t)L.ce);
+  s.cetinv = d(9 * (size_t)L.ce);
   s.gilo = w(nbuf * (size_t)L.n * ldg);
   s.ivf = w(L.nc);
   s.lcstr = w(L.lc);
@@ -320,8 +362,31 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.ilcnt = w(L.il);
   s.srcg = w(L.src);
   s.recp = w(L.n);
+  s.lece = w(L.le);
+  s.lemode = w(L.le);
+  s.cele0 = w(L.ce);
+  s.cenode = w(3 * (size_t)L.ce);
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
+}
+
+// Coupled line modes (poll warp, after collecting step m's values into
+// blk_new): each mode's interpolated history I_mode(m) = (1 - f) c(m - d)
+// + f c(m - d - 1) from the values consumed at steps m (blk_new) and m - 1
+// (blk_old), then the phase-domain history currents T_i I_mode of each
+// coupled end into the phase slots that follow the n_le line-end slots.
+__device__ void fold_modes(int lane, int n_le, int n_ce, const int* lece, const double* lef, const double* blk_old,
+                           double* blk_new, double* imode_new, const int* cele0, const double* ceti) {
+  for (int e = lane; e < n_le; e += 32)
+    if (lece[e] >= 0) imode_new[e] = fma(lef[e], blk_old[e], (1.0 - lef[e]) * blk_new[e]);
+  __syncwarp();
+  for (int x = lane; x < 3 * n_ce; x += 32) {
+    const int c = x / 3, p = x - 3 * c;
+    const double* ti = ceti + 9 * c + 3 * p;
+    const double* im = imode_new + cele0[c];
+    blk_new[n_le + x] = fma(ti[0], im[0], fma(ti[1], im[1], ti[2] * im[2]));
+  }
+  __syncwarp();
 }
 
 // One warp collects one step's line-end histories I_e(n) from the tagged
@@ -393,15 +458,25 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   int* ilcnt = reinterpret_cast<int*>(smem_raw + L.ilcnt);
   int* srcg = reinterpret_cast<int*>(smem_raw + L.srcg);
   int* recp = reinterpret_cast<int*>(smem_raw + L.recp);    // per node: record column or -1
+  double* lef = reinterpret_cast<double*>(smem_raw + L.lef);        // per line end: fractional delay
+  double* imode = reinterpret_cast<double*>(smem_raw + L.imode);    // [2][le]: modal histories by parity
+  double* ceti = reinterpret_cast<double*>(smem_raw + L.ceti);      // per coupled end: T_i
+  double* cetinv = reinterpret_cast<double*>(smem_raw + L.cetinv);  // per coupled end: T_v^-1
+  int* lece = reinterpret_cast<int*>(smem_raw + L.lece);            // per line end: coupled end or -1
+  int* lemode = reinterpret_cast<int*>(smem_raw + L.lemode);
+  int* cele0 = reinterpret_cast<int*>(smem_raw + L.cele0);
+  int* cenode = reinterpret_cast<int*>(smem_raw + L.cenode);
 
   const int sidx = blockIdx.x;
   const SubDev S = P.sub[sidx];
   const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = S.n, Q = S.q, n_str = S.n_str, nc = n + n_str, ldg = nc | 1;
   const int blk = (nc + Q - 1) / Q;   // columns per matvec task
-  const int n_lc = S.n_lc, n_sb = S.n_sb, n_le = S.n_le, n_il = S.n_il;
+  const int n_lc = S.n_lc, n_sb = S.n_sb, n_le = S.n_le, n_il = S.n_il, n_ce = S.n_ce;
   const int ie_base = n_lc + n_sb;
-  const int zero_slot = ie_base + 2 * n_le;
+  const int blk_len = n_le + 3 * n_ce;   // per parity: line-end values, then coupled ends' phase currents
+  const int zero_slot = ie_base + 2 * blk_len;
+  const int lv = P.lim.le;
   const int src_vs = P.lim.src;
   const bool writes_lines = sidx != P.hold_sub;
   const int src_thread = T - 1 - tid;
@@ -436,6 +511,20 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     led[x] = e.d;
     rslot[x] = (int)(P.n0 % e.depth);
     wslot[x] = (int)((P.n0 + e.d) % e.depth);
+    lef[x] = e.f;
+    lece[x] = e.ce;
+    lemode[x] = e.mode;
+    // the value consumed at step n0 - 1 (for interpolated modal histories)
+    inp[ie_base + (int)((P.n0 - 1) & 1) * blk_len + x] = P.le_prev[S.le_off + x];
+  }
+  for (int c = tid; c < n_ce; c += T) {
+    const CoupledEndDev& ce = P.ce[S.ce_off + c];
+    cele0[c] = ce.le0;
+    for (int k = 0; k < 3; ++k) cenode[3 * c + k] = ce.node[k];
+    for (int k = 0; k < 9; ++k) {
+      ceti[9 * c + k] = ce.ti[k];
+      cetinv[9 * c + k] = ce.tinv[k];
+    }
   }
   for (int r = tid; r < n; r += T) recp[r] = P.rec != nullptr ? P.rec_pos[S.node_off + r] : -1;
   for (int x = tid; x < 4 * n_il; x += T) ent[x] = P.ent[4 * (size_t)S.il_off + x];
@@ -486,9 +575,12 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     ivf[n + t] = (float)(-inp[x]);
   }
   if (warp == kPollWarp && n_le > 0) {
+    const int p0 = (int)(P.n0 & 1);
     const bool ok = collect_lines(P, n_le, (unsigned)P.n0, lane, sidx, leown, ledepth, rslot,
-                                  inp + ie_base + (int)(P.n0 & 1) * n_le);
+                                  inp + ie_base + p0 * blk_len);
     if (!ok && lane == 0) s_abort = 1;
+    fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + (p0 ^ 1) * blk_len, inp + ie_base + p0 * blk_len,
+               imode + p0 * lv, cele0, ceti);
   }
   // recording counters: steps decim, 2 decim, ... go to rows 0, 1, ...
   const int decim = P.rec_decim > 0 ? P.rec_decim : 1;
@@ -500,7 +592,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   for (long long step = P.n0; step < n_end && !s_abort; ++step) {
     const int par = (int)(step & 1);
     const double* vsc = vs + par * src_vs;
-    const int parshift = par * n_le;
+    const int parshift = par * blk_len;
     // runtime-switch states decided from the previous step's solution
     int new_word = 0;
     for (int j = 0; j < n_rs; ++j) new_word |= s_rsbit[j] << j;
@@ -544,10 +636,10 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
         node = ilnode[l];
         cnt = ilcnt[l];
         const int* e4 = ent + 4 * l;
-        s = (signed_entry(inp, (unsigned)e4[0], ie_base, n_le, parshift) +
-             signed_entry(inp, (unsigned)e4[1], ie_base, n_le, parshift)) +
-            (signed_entry(inp, (unsigned)e4[2], ie_base, n_le, parshift) +
-             signed_entry(inp, (unsigned)e4[3], ie_base, n_le, parshift));
+        s = (signed_entry(inp, (unsigned)e4[0], ie_base, blk_len, parshift) +
+             signed_entry(inp, (unsigned)e4[1], ie_base, blk_len, parshift)) +
+            (signed_entry(inp, (unsigned)e4[2], ie_base, blk_len, parshift) +
+             signed_entry(inp, (unsigned)e4[3], ie_base, blk_len, parshift));
       }
       const int wmax = __reduce_max_sync(0xffffffffu, cnt);
       double acc = s;
@@ -599,8 +691,10 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     if (warp == kPollWarp) {
       if (n_le > 0 && step + 1 < n_end) {
         const bool ok = collect_lines(P, n_le, (unsigned)(step + 1), lane, sidx, leown, ledepth, rslot,
-                                      inp + ie_base + (par ^ 1) * n_le);
+                                      inp + ie_base + (par ^ 1) * blk_len);
         if (!ok && lane == 0) s_abort = 1;
+        fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + par * blk_len, inp + ie_base + (par ^ 1) * blk_len,
+                   imode + (par ^ 1) * lv, cele0, ceti);
       }
     } else {
       // runtime switches: the states in force at the next step (oracle rules)
@@ -634,9 +728,17 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
           }
         } else if (it >= it_le && it < it_le + n_le) {
           const int e = it - it_le;
-          if (writes_lines)
-            st_tagged(P.ring + 2 * (lefar[e] + wslot[e]), (unsigned)(step + led[e]),
-                      fma(-ley2[e], vv[lenode[e]], -ie_cur[e]));
+          double out;
+          const int c = lece[e];
+          if (c < 0) {
+            out = fma(-ley2[e], vv[lenode[e]], -ie_cur[e]);
+          } else {   // a mode: c_j = -(2/Z_j) (T_v^-1 v_p)_j - I_mode_j(n)
+            const double* tr = cetinv + 9 * c + 3 * lemode[e];
+            const int* nd = cenode + 3 * c;
+            const double vm = fma(tr[0], vv[nd[0]], fma(tr[1], vv[nd[1]], tr[2] * vv[nd[2]]));
+            out = fma(-ley2[e], vm, -imode[par * lv + e]);
+          }
+          if (writes_lines) st_tagged(P.ring + 2 * (lefar[e] + wslot[e]), (unsigned)(step + led[e]), out);
           const int nx = wslot[e] + 1;
           wslot[e] = nx == ledepth[e] ? 0 : nx;
         } else if (it >= it_sb) {
@@ -649,6 +751,9 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   }
   if (!s_abort) {
     for (int b = tid; b < n_lc; b += T) P.h[S.lc_off + b] = inp[b];
+    if (P.n_steps > 0)   // the values consumed at the last step, for the next launch's interpolation
+      for (int x = tid; x < n_le; x += T)
+        P.le_prev[S.le_off + x] = inp[ie_base + (int)((n_end - 1) & 1) * blk_len + x];
     for (int x = tid; x < n_rs; x += T) P.rs_prev_i[S.rs_off + x] = s_rsi[x];
     if (n_rs > 0 && tid == 0) {
       int w = 0;
@@ -682,6 +787,12 @@ cudaError_t launch_companion(BranchDev* br, int64_t n_br, double dt, cudaStream_
   if (n_br <= 0) return cudaSuccess;
   const int th = 256;
   companion_kernel<<<(unsigned)((n_br + th - 1) / th), th, 0, st>>>(br, n_br, dt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coupled_constants(CoupledEndDev* ce, int64_t n_ce, cudaStream_t st) {
+  if (n_ce <= 0) return cudaSuccess;
+  coupled_constants_kernel<<<(unsigned)((n_ce + 127) / 128), 128, 0, st>>>(ce, n_ce);
   return cudaGetLastError();
 }
 

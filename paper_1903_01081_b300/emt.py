@@ -45,6 +45,8 @@ class _NetworkDesc(ctypes.Structure):
         ("n_rswitches", ctypes.c_int64), ("rs_k", ctypes.c_void_p), ("rs_m", ctypes.c_void_p),
         ("rs_kind", ctypes.c_void_p), ("rs_ron", ctypes.c_void_p), ("rs_roff", ctypes.c_void_p),
         ("rs_on0", ctypes.c_void_p), ("rs_trip_step", ctypes.c_void_p),
+        ("n_clines", ctypes.c_int64), ("cl_k", ctypes.c_void_p), ("cl_m", ctypes.c_void_p),
+        ("cl_tv", ctypes.c_void_p), ("cl_z", ctypes.c_void_p), ("cl_tau", ctypes.c_void_p),
     ]
 
 
@@ -159,6 +161,10 @@ def network_desc(net, keep: list) -> _NetworkDesc:
     d.rs_kind = p(rs("rs_kind", np.uint8), np.uint8)
     d.rs_ron, d.rs_roff = p(rs("rs_ron", np.float64), np.float64), p(rs("rs_roff", np.float64), np.float64)
     d.rs_on0, d.rs_trip_step = p(rs("rs_on0", np.uint8), np.uint8), p(rs("rs_trip", np.int64), np.int64)
+    d.n_clines = int(len(rs("cl_z", np.float64))) // 3
+    d.cl_k, d.cl_m = p(rs("cl_k", np.int32), np.int32), p(rs("cl_m", np.int32), np.int32)
+    d.cl_tv, d.cl_z = p(rs("cl_tv", np.float64), np.float64), p(rs("cl_z", np.float64), np.float64)
+    d.cl_tau = p(rs("cl_tau", np.float64), np.float64)
     return d
 
 

@@ -645,3 +645,38 @@ def with_rectifier_loads(base: Network, seed: int = 1006, n_rectifiers: int = 30
 CLARKE = np.array([[1 / np.sqrt(3), 2 / np.sqrt(6), 0.0],
                    [1 / np.sqrt(3), -1 / np.sqrt(6), 1 / np.sqrt(2)],
                    [1 / np.sqrt(3), -1 / np.sqrt(6), -1 / np.sqrt(2)]])
+
+
+def with_coupled_lines(base: Network, seed: int = 1007) -> Network:
+    """``base`` with every three-phase line (a triplet of single-phase lines,
+    phases 0, 1, 2) replaced by one transposed coupled line in Clarke modes:
+    aerial modes Z_1 = Z_2 = the triplet's Z_c with travel time (d + U[0, 1))
+    dt, zero-sequence mode Z_0 = Z_c U[1.4, 1.9] with travel time
+    U[1.05, 1.25] times the aerial one (non-integer numbers of steps)."""
+    if base.n_lines % 3:
+        raise ValueError("lines must come in three-phase triplets")
+    rng = np.random.default_rng(seed)
+    net = base.copy()
+    L = base.n_lines // 3
+    cl_k, cl_m, cl_tv, cl_z, cl_tau = [], [], [], [], []
+    for l in range(L):
+        idx = slice(3 * l, 3 * l + 3)
+        zc, d = float(base.ln_zc[3 * l]), int(base.ln_delay[3 * l])
+        tau1 = (d + rng.uniform(0.0, 1.0)) * base.dt
+        tau0 = tau1 * rng.uniform(1.05, 1.25)
+        cl_k.extend(base.ln_k[idx].tolist())
+        cl_m.extend(base.ln_m[idx].tolist())
+        cl_tv.extend(CLARKE.reshape(9).tolist())
+        cl_z.extend([zc * rng.uniform(1.4, 1.9), zc, zc])
+        cl_tau.extend([tau0, tau1, tau1])
+    net.ln_k = np.zeros(0, np.int32)
+    net.ln_m = np.zeros(0, np.int32)
+    net.ln_zc = np.zeros(0, np.float64)
+    net.ln_delay = np.zeros(0, np.int32)
+    net.cl_k = np.asarray(cl_k, np.int32)
+    net.cl_m = np.asarray(cl_m, np.int32)
+    net.cl_tv = np.asarray(cl_tv, np.float64)
+    net.cl_z = np.asarray(cl_z, np.float64)
+    net.cl_tau = np.asarray(cl_tau, np.float64)
+    net.meta = dict(net.meta, coupled_lines={"seed": seed, "lines": L})
+    return net
