@@ -22,7 +22,9 @@ two further legs the metric names, reported as extra keys of the line:
       sum_n ||v_n - v*_n||^2 over 20,000 steps of the large-scale network
       with checkpoints every 256 steps (and with the whole tape kept);
   "runtime_switches": the large-scale network with 30 diode-rectifier loads
-      and 10 current-zero breakers, against the same network without them.
+      and 10 current-zero breakers, against the same network without them;
+  "coupled_lines": the large-scale network with its three-phase lines as
+      coupled modal lines with interpolated travel times, against the plain one.
 
 N > 1 runs N independent replicas (the single-network path does not shard;
 see the design doc), launched by torch.distributed.run.  `--impl reference`
@@ -297,18 +299,16 @@ def adjoint_leg(steps=None, reps=3):
             "loss": J}
 
 
-def runtime_switch_leg(steps=None, reps=3):
-    """The large-scale network with 30 diode-rectifier loads and 10
-    current-zero breakers (runtime switches, 40 extra nodes): node-steps/s of
-    a run from the de-energised state, beside the same network without them,
-    and sampled parity against the oracle."""
+def variant_leg(variant, workload, steps=None, reps=3, extra=None):
+    """node-steps/s of a run from the de-energised state of ``variant`` (a
+    variant of the large-scale network), beside the plain network, and
+    sampled parity of the variant against the oracle."""
     import torch
     import oracle
     from paper_1903_01081_b300 import emt, netgen as g
     N = steps or N_STEPS
     out = {}
-    for tag, net in (("with_switches", g.with_rectifier_loads(g.large_scale(), seed=1006)),
-                     ("without", g.large_scale())):
+    for tag, net in (("variant", variant), ("plain", g.large_scale())):
         sim = emt.Simulator(net, n_steps=N)
         stream = torch.cuda.current_stream()
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -325,20 +325,43 @@ def runtime_switch_leg(steps=None, reps=3):
         t = float(np.median(ms))
         d = {"nodes": int(net.n_nodes), "time_steps": N, "ms": t, "us_per_step": 1e3 * t / N,
              "node_steps_per_s": net.n_nodes * N / (t / 1e3)}
-        if tag == "with_switches":
+        if tag == "variant":
             n_chk = min(2000, N)
             w = sim.waveforms(n_rows=n_chk)[:, 0, :]
             ref = oracle.simulate(net, n_chk)
             d["parity_rel_err_first_steps"] = float(np.max(np.abs(w - ref)) / np.max(np.abs(ref)))
-            d["runtime_switches"] = int(net.n_runtime_switches)
-            st = oracle.runtime_switch_states(net, n_chk)
-            d["state_changes_in_checked_steps"] = int(np.sum(st[1:] != st[:-1]))
+            if extra:
+                d.update(extra(net, n_chk))
         sim.close()
         out[tag] = d
-    out["workload"] = ("large-scale network plus 30 diode-rectifier loads (diode, R, C) and 10 breakers that open "
-                       "at the first current zero after a trip step; all nodes recorded")
-    out["overhead"] = out["with_switches"]["us_per_step"] / out["without"]["us_per_step"]
+    out["workload"] = workload
+    out["slowdown_vs_plain"] = out["variant"]["us_per_step"] / out["plain"]["us_per_step"]
     return out
+
+
+def runtime_switch_leg(steps=None, reps=3):
+    """The large-scale network with 30 diode-rectifier loads and 10
+    current-zero breakers (runtime switches, 40 extra nodes)."""
+    import oracle
+    from paper_1903_01081_b300 import netgen as g
+
+    def changes(net, n):
+        st = oracle.runtime_switch_states(net, n)
+        return {"runtime_switches": int(net.n_runtime_switches),
+                "state_changes_in_checked_steps": int(np.sum(st[1:] != st[:-1]))}
+    return variant_leg(g.with_rectifier_loads(g.large_scale(), seed=1006),
+                       "large-scale network plus 30 diode-rectifier loads (diode, R, C) and 10 breakers that open "
+                       "at the first current zero after a trip step; all nodes recorded", steps, reps, changes)
+
+
+def coupled_line_leg(steps=None, reps=3):
+    """The large-scale network with its 700 three-phase lines as coupled
+    Clarke-mode lines with non-integer travel times."""
+    from paper_1903_01081_b300 import netgen as g
+    return variant_leg(g.with_coupled_lines(g.large_scale()),
+                       "large-scale network with its 700 three-phase lines as transposed coupled lines in Clarke "
+                       "modes (zero-sequence Z_c and travel time larger), travel times (d + U[0,1)) dt interpolated; "
+                       "all nodes recorded", steps, reps)
 
 
 def run_reference(args):
@@ -480,8 +503,8 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
             "parity_rel_err_first_2000_steps": parity,
-            **({"scenarios": scenario_legs(), "adjoint": adjoint_leg(), "runtime_switches": runtime_switch_leg()}
-               if args.leg == "all" else {}),
+            **({"scenarios": scenario_legs(), "adjoint": adjoint_leg(), "runtime_switches": runtime_switch_leg(),
+                "coupled_lines": coupled_line_leg()} if args.leg == "all" else {}),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -498,7 +521,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--time-steps", type=int, default=N_STEPS)
     ap.add_argument("--skip-extras", action="store_true")
-    ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches"], default="all",
+    ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines"],
+                    default="all",
                     help="all: the JSON line with every leg; single: the single-network leg only; "
                          "n1 / shared_g / adjoint: that leg alone (profiling)")
     ap.add_argument("--leg-steps", type=int, default=None, help="time steps of a lone n1 / shared_g / adjoint leg")
@@ -510,7 +534,7 @@ def main():
         return run_rank_selftest()
     if args.impl == "reference":
         return run_reference(args)
-    if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches"):
+    if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines"):
         return run_leg(args)
     return run_ours(args)
 
@@ -523,6 +547,8 @@ def run_leg(args):
         out = adjoint_leg(args.leg_steps, reps=1)
     elif args.leg == "runtime_switches":
         out = runtime_switch_leg(args.leg_steps, reps=1)
+    elif args.leg == "coupled_lines":
+        out = coupled_line_leg(args.leg_steps, reps=1)
     else:
         shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
         out = scenario_legs((args.leg,), args.leg_steps, shape, args.leg_warm)
