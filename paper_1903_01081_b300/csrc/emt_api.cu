@@ -122,7 +122,6 @@ struct emt_ctx {
   bool batched = false;
   int64_t S = 1;
   int S_t = 1;
-  int max_nc = 1;
   int64_t n_base_epochs = 0;
   std::vector<int32_t> node_l0, node_nl;
   std::vector<int64_t> le_bring, le_bfar;
@@ -153,8 +152,6 @@ struct emt_ctx {
   BatchGraph graph;
   bool use_graph = true;
   bool tuned = false;
-  int32_t* d_node_l0 = nullptr;
-  int32_t* d_node_nl = nullptr;
   int64_t* d_le_bring = nullptr;
   int64_t* d_le_bfar = nullptr;
   double* d_bsrc_amp = nullptr;
@@ -557,8 +554,6 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
   }
   for (size_t e = 0; e < c->line_ends.size(); ++e) c->le_bfar[e] = c->le_bring[le_of_end[end_of_le[e] ^ 1]];
   c->bring_len = off;
-  c->max_nc = 1;
-  for (const SubDev& sd : c->subs) c->max_nc = std::max(c->max_nc, sd.n + sd.n_str);
 
   // flat per-slot arrays (global numbering of columns, lanes and slots)
   if (c->lc_idx.size() >= kBentIndexMask || c->sb_idx.size() >= kBentIndexMask ||
@@ -1169,8 +1164,6 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_err, 4);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_rs_prev_i, c->rswitches.size());
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_le_prev, c->line_ends.size());
-  if (e == cudaSuccess) e = c->upload(&c->d_node_l0, c->node_l0);
-  if (e == cudaSuccess) e = c->upload(&c->d_node_nl, c->node_nl);
   if (c->batched) {
     UP(d_col_code, b_col_code)
     UP(d_node_sub, b_node_sub)
