@@ -579,8 +579,9 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     const bool ok = collect_lines(P, n_le, (unsigned)P.n0, lane, sidx, leown, ledepth, rslot,
                                   inp + ie_base + p0 * blk_len);
     if (!ok && lane == 0) s_abort = 1;
-    fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + (p0 ^ 1) * blk_len, inp + ie_base + p0 * blk_len,
-               imode + p0 * lv, cele0, ceti);
+    if (n_ce > 0)
+      fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + (p0 ^ 1) * blk_len, inp + ie_base + p0 * blk_len,
+                 imode + p0 * lv, cele0, ceti);
   }
   // recording counters: steps decim, 2 decim, ... go to rows 0, 1, ...
   const int decim = P.rec_decim > 0 ? P.rec_decim : 1;
@@ -693,8 +694,9 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
         const bool ok = collect_lines(P, n_le, (unsigned)(step + 1), lane, sidx, leown, ledepth, rslot,
                                       inp + ie_base + (par ^ 1) * blk_len);
         if (!ok && lane == 0) s_abort = 1;
-        fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + par * blk_len, inp + ie_base + (par ^ 1) * blk_len,
-                   imode + (par ^ 1) * lv, cele0, ceti);
+        if (n_ce > 0)
+          fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + par * blk_len,
+                     inp + ie_base + (par ^ 1) * blk_len, imode + (par ^ 1) * lv, cele0, ceti);
       }
     } else {
       // runtime switches: the states in force at the next step (oracle rules)
