@@ -43,7 +43,7 @@ constexpr int kAdjItemThreads = kAdjThreads - 32;
 
 struct AdjSmem {
   size_t gi, part, iv, ww, vn, ev, inp, xr, hb, lce, brg, bre, dga, dsa, ley2, leown, lefar, amp, sn, vsrc;   // 8-byte
-  size_t gilo, ivf;                                                                                      // float
+  size_t gilo, ivf, partf;                                                                               // float
   size_t brk, brm, brlc, brkind, lcstr, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, orig;   // int
   size_t bytes;
 };
@@ -76,6 +76,7 @@ __host__ __device__ inline AdjSmem adj_smem(const AdjLimits& L) {
   s.vsrc = d(2 * (size_t)L.src);
   s.gilo = w((size_t)L.n * ldg);
   s.ivf = w(L.nc);
+  s.partf = w((size_t)L.n * L.q);
   s.brk = w(L.br);
   s.brm = w(L.br);
   s.brlc = w(L.br);
@@ -157,6 +158,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
   double* vsrc = reinterpret_cast<double*>(smem_raw + L.vsrc); // [2][src]
   float* gilo = reinterpret_cast<float*>(smem_raw + L.gilo);
   float* ivf = reinterpret_cast<float*>(smem_raw + L.ivf);
+  float* partf = reinterpret_cast<float*>(smem_raw + L.partf);
   int* brk = reinterpret_cast<int*>(smem_raw + L.brk);
   int* brm = reinterpret_cast<int*>(smem_raw + L.brm);
   int* brlc = reinterpret_cast<int*>(smem_raw + L.brlc);
@@ -338,7 +340,8 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
         a = fma(row[j], iv[j], a);
         b = fmaf(rowl[j], ivf[j], b);
       }
-      part[task] = a + (double)b;
+      part[task] = a;
+      partf[task] = b;
     }
     if (more) {
       if (tid < n) {
@@ -354,7 +357,12 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
 
     for (int r = tid; r < n; r += T) {
       double w = part[r * Q];
-      for (int q = 1; q < Q; ++q) w += part[r * Q + q];
+      float wl = partf[r * Q];
+      for (int q = 1; q < Q; ++q) {
+        w += part[r * Q + q];
+        wl += partf[r * Q + q];
+      }
+      w += (double)wl;
       ww[r] = w;
       const double e = ev[par * nv + r];
       jacc = fma(e, e, jacc);

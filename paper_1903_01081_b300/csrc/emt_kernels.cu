@@ -317,7 +317,7 @@ constexpr int kItemThreads = kFwdThreads - 32;
 // together fall in different banks.
 struct FwdSmem {
   size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar, lef, imode, ceti, cetinv;   // 8-byte
-  size_t gilo, ivf;                                                                        // float
+  size_t gilo, ivf, partf;                                                                 // float
   size_t lck, lcm, lckind, lcstr, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, recp,
       lece, lemode, cele0, cenode;                                                         // int
   size_t bytes;
@@ -347,6 +347,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.cetinv = d(9 * (size_t)L.ce);
   s.gilo = w(nbuf * (size_t)L.n * ldg);
   s.ivf = w(L.nc);
+  s.partf = w((size_t)L.n * L.q);
   s.lcstr = w(L.lc);
   s.lck = w(L.lc);
   s.lcm = w(L.lc);
@@ -443,6 +444,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   long long* lefar = reinterpret_cast<long long*>(smem_raw + L.lefar);
   float* gilo_buf = reinterpret_cast<float*>(smem_raw + L.gilo);
   float* ivf = reinterpret_cast<float*>(smem_raw + L.ivf);
+  float* partf = reinterpret_cast<float*>(smem_raw + L.partf);   // X_lo partial sums per task
   int* lck = reinterpret_cast<int*>(smem_raw + L.lck);
   int* lcm = reinterpret_cast<int*>(smem_raw + L.lcm);
   int* lckind = reinterpret_cast<int*>(smem_raw + L.lckind);
@@ -670,7 +672,8 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
         a = fma(row[j], iv[j], a);
         b = fmaf(rowl[j], ivf[j], b);
       }
-      part[task] = a + (double)b;
+      part[task] = a;
+      partf[task] = b;
     }
     if (src_thread < S.n_src) vs[(par ^ 1) * src_vs + src_thread] = vnext;
     __syncthreads();
@@ -678,8 +681,14 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     // node voltages
     const bool rec_now = P.rec != nullptr && dec == 0 && rec_row < P.rec_rows;
     for (int r = tid; r < n; r += T) {
+      // the X_hi partial sums in double, the X_lo ones in single precision
       double v = part[r * Q];
-      for (int q = 1; q < Q; ++q) v += part[r * Q + q];
+      float vl = partf[r * Q];
+      for (int q = 1; q < Q; ++q) {
+        v += part[r * Q + q];
+        vl += partf[r * Q + q];
+      }
+      v += (double)vl;
       vv[r] = v;
       if (rec_now && recp[r] >= 0) P.rec[(rec_row - P.rec_row0) * P.n_rec + recp[r]] = v;
     }
