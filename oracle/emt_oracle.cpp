@@ -524,14 +524,18 @@ extern "C" int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_
 // and finally dg/dR = -1/R^2, dg/dL = -dt/(2L^2), dg/dC = 2/dt.
 extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad,
                            double* loss) {
-  if (!valid(net) || !v_target || !grad || n_steps < 0 || net->n_rs > 0 || net->n_cl > 0) return -1;
-  const int64_t nn = net->n_nodes, nb = net->n_br, ns = net->n_src, nl = net->n_ln;
+  if (!valid(net) || !v_target || !grad || n_steps < 0 || net->n_cl > 0) return -1;
+  const int64_t nn = net->n_nodes, nb = net->n_br, ns = net->n_src, nl = net->n_ln, nr = net->n_rs;
   Sim<double> sim;
   sim.net = net;
   sim.init(net->br_val, net->src_amp, false);
   std::vector<double> tape((size_t)n_steps * nn);
+  // runtime-switch states in force at each step: the reverse sweep uses
+  // the matrices the forward run used (decisions held fixed)
+  std::vector<char> rs_tape((size_t)n_steps * nr);
   double J = 0.0;
   for (int64_t n = 1; n <= n_steps; ++n) {
+    for (int64_t w = 0; w < nr; ++w) rs_tape[(size_t)(n - 1) * nr + w] = sim.rs_on[w];
     if (!sim.step(n)) return -2;
     double* row = tape.data() + (size_t)(n - 1) * nn;
     const double* tg = v_target + (size_t)(n - 1) * nn;
@@ -570,6 +574,7 @@ extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_
       vbar[net->ln_m[l]] += -y2 * ibar_k[l][(n + d) % d1];
     }
     // w_n = G_n^{-T} vbar_n, per subsystem with the factors of step n
+    for (int64_t w = 0; w < nr; ++w) sim.rs_on[w] = rs_tape[(size_t)(n - 1) * nr + w];
     for (int s = 0; s < sim.n_sub; ++s) {
       if (!sim.refactor_if_needed(s, n)) return -2;
       int m = (int)sim.nodes[s].size();

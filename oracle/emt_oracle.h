@@ -103,7 +103,9 @@ int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_target, int
 
 /* Discrete adjoint of the loss over the full stored trajectory.
  * grad: [n_br + n_src] = dJ/d(branch value) then dJ/d(source amplitude).
- * Networks with runtime switches or coupled lines are rejected (-1). */
+ * With runtime switches the reverse sweep uses the states the forward run
+ * decided (the gradient of the smooth piece the run lies on).  Networks
+ * with coupled lines are rejected (-1). */
 int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad, double* loss);
 
 /* Subsystem of each unknown node (components over branches and switches). */

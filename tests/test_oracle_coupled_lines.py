@@ -121,3 +121,9 @@ def test_coupled_line_validation():
     net = three_line_net(True, tv=np.ones((3, 3)))               # singular transformation
     with pytest.raises(oracle.OracleError):
         oracle.simulate(net, 10)
+
+
+def test_adjoint_rejects_coupled_lines():
+    net = three_line_net(True)
+    with pytest.raises(oracle.OracleError):
+        oracle.adjoint(net, 10, np.zeros((10, net.n_nodes)))

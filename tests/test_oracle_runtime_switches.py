@@ -151,9 +151,3 @@ def test_monolithic_equals_partitioned_with_runtime_switches():
     assert rel(a, b) <= 1e-12
     st = oracle.runtime_switch_states(net, N)
     assert st[:, 0].min() != st[:, 0].max() or st[:, 2].min() != st[:, 2].max()
-
-
-def test_adjoint_rejects_runtime_switches():
-    net = rectifier()
-    with pytest.raises(oracle.OracleError):
-        oracle.adjoint(net, 10, np.zeros((10, net.n_nodes)))
