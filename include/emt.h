@@ -67,8 +67,8 @@ typedef struct emt_ctx emt_ctx;  /* opaque; owns all device memory it allocates 
  *   The paper's process 3 at run time (Sec. III-A): each subsystem with k
  *   runtime switches gets a prefactored G^-1 for every one of its 2^k
  *   states (k <= 8 per subsystem), and the time loop switches matrices
- *   when a state changes.  Not supported with a scenario set or by
- *   emt_adjoint.
+ *   when a state changes.  Not supported with a scenario set; emt_adjoint
+ *   differentiates with the decisions the forward run took held fixed.
  * Coupled three-phase lossless lines in modal form (n_clines may be 0):
  *   cl_k[3 l + p] / cl_m[3 l + p]: phase p's node (unknown) at each end;
  *   cl_tv[9 l + 3 p + j]: T_v, phase voltages = T_v modal voltages (modal
@@ -240,8 +240,10 @@ emt_status emt_autotune(emt_ctx* ctx, int64_t trial_steps, void* cuda_stream);
  *   loss:       host double, or NULL (not both NULL).
  *   on_device:  non-zero: v_target and grad are device memory; else host.
  *   cuda_stream: stream for the launches (NULL: legacy default stream).
- * Requires emt_prefactor; a context built with a scenario set returns
- * EINVAL.  Resets the context to step 0 before and after (the recording
+ * With runtime switches the reverse sweep uses the states the forward run
+ * decided (the forward re-runs record them per step), i.e. the gradient of
+ * the smooth piece of J the run lies on.  Requires emt_prefactor; a context
+ * built with a scenario set or with coupled lines returns EINVAL.  Resets the context to step 0 before and after (the recording
  * buffer is not written).  Allocates its work buffers (about 8 N n_nodes
  * bytes for a host v_target, N/K checkpoints, the tape) and frees them
  * before returning.  Synchronous.  ETIMEOUT as for emt_step_n. */

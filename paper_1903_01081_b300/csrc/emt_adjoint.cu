@@ -247,11 +247,16 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
     inp[zero_slot] = 0.0;
     s_abort = 0;
   }
-  int ep = 0;
-  while (ep + 1 < S.n_ep && P.ep[S.ep_off + ep + 1].start <= P.n_hi) ++ep;
-  long long ep_start = P.ep[S.ep_off + ep].start;
+  // solve matrix of step n: switch epoch te (by step) and, with runtime
+  // switches, the state word the forward run had at step n (word tape)
+  const int n_states = S.n_states, n_te = S.n_ep / n_states;
+  const bool words = P.word_tape != nullptr && S.n_rs > 0;
+  int te = 0;
+  while (te + 1 < n_te && P.ep[S.ep_off + (te + 1) * n_states].start <= P.n_hi) ++te;
+  long long ep_start = P.ep[S.ep_off + te * n_states].start;
+  int word = words ? P.word_tape[(P.n_hi - 1 - P.tape_row0) * P.n_sub + sidx] : 0;
   {
-    const int64_t off = P.ep[S.ep_off + ep].ginv_off;
+    const int64_t off = P.ep[S.ep_off + te * n_states + word].ginv_off;
     for (int i = tid; i < n * nc; i += T) {
       const int r = i / nc, c = i - r * nc;
       gi[r * ldg + c] = P.ginv[off + i];
@@ -280,10 +285,12 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
     const int par = (int)(tau & 1);
     const int parshift = par * n_le;
     const bool more = i + 1 < P.n_steps;
-    if (nstep < ep_start) {   // switch state of the earlier epoch
-      while (ep > 0 && P.ep[S.ep_off + ep].start > nstep) --ep;
-      ep_start = P.ep[S.ep_off + ep].start;
-      const int64_t off = P.ep[S.ep_off + ep].ginv_off;
+    const int w_now = words ? P.word_tape[(nstep - 1 - P.tape_row0) * P.n_sub + sidx] : 0;
+    if (nstep < ep_start || w_now != word) {   // an earlier epoch, or another runtime-switch state
+      while (te > 0 && P.ep[S.ep_off + te * n_states].start > nstep) --te;
+      ep_start = P.ep[S.ep_off + te * n_states].start;
+      word = w_now;
+      const int64_t off = P.ep[S.ep_off + te * n_states + word].ginv_off;
       for (int x = tid; x < n * nc; x += T) {
         const int r = x / nc, c = x - r * nc;
         gi[r * ldg + c] = P.ginv[off + x];

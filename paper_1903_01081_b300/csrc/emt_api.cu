@@ -1343,6 +1343,7 @@ struct RecSpec {
   int32_t decim = 1;
   int64_t rows = 0;
   int64_t row0 = 0;
+  int32_t* word_tape = nullptr;   // optional per-step runtime-switch state words, rows from row0
 };
 
 // The one multi-scenario launch for steps n0 .. n0 + n_steps - 1.
@@ -1442,6 +1443,8 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
   p.rec_pos = rs.pos;
   p.rec_rows = rs.rows;
   p.rec_row0 = rs.row0;
+  p.word_tape = rs.word_tape;
+  p.word_row0 = rs.row0;
   p.rec_decim = rs.decim;
   p.n_rec = rs.n_rec;
   p.wait_budget_ns = c->wait_budget_ns;
@@ -1743,7 +1746,6 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
                                   double* grad, double* loss, int32_t on_device, void* stream) {
   if (!c) return EMT_EINVAL;
   if (c->batched) return c->fail(EMT_EINVAL, "emt_adjoint: a context built with a scenario set has no adjoint");
-  if (!c->rswitches.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: networks with runtime switches have no adjoint");
   if (!c->cends.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: networks with coupled lines have no adjoint");
   if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
   if (n_steps < 1) return c->fail(EMT_EINVAL, "emt_adjoint: n_steps must be >= 1");
@@ -1803,6 +1805,8 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
   double *d_hbar = nullptr, *d_dg = nullptr, *d_dsrc = nullptr, *d_lp = nullptr, *d_grad = grad, *d_loss = nullptr;
   unsigned long long *d_ck_ring = nullptr, *d_aring = nullptr;
   int32_t* d_pos = nullptr;
+  int32_t *d_wtape = nullptr, *d_ck_word = nullptr;   // runtime switches: per-step state words, checkpoints
+  double* d_ck_rsi = nullptr;
   cudaError_t e = cudaSuccess;
   if (!on_device) {
     e = c->alloc_zero(&d_tgt_copy, (size_t)(N * nn));
@@ -1822,6 +1826,13 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
   ADJ_ALLOC(d_ck_h, std::max<int64_t>((n_seg - 1) * n_lc, 1))
   ADJ_ALLOC(d_ck_ring, std::max<int64_t>((n_seg - 1) * ring_words, 1))
   ADJ_ALLOC(d_tape, (overlap ? 2 : 1) * K * nn)
+  const bool rsw = !c->rswitches.empty();
+  const int64_t n_rsw = (int64_t)c->rswitches.size();
+  if (rsw) {
+    ADJ_ALLOC(d_wtape, (overlap ? 2 : 1) * K * c->n_sub)
+    ADJ_ALLOC(d_ck_word, std::max<int64_t>((n_seg - 1) * c->n_sub, 1))
+    ADJ_ALLOC(d_ck_rsi, std::max<int64_t>((n_seg - 1) * n_rsw, 1))
+  }
   ADJ_ALLOC(d_aring, ring_words)
   ADJ_ALLOC(d_hbar, n_lc)
   ADJ_ALLOC(d_dg, std::max<int64_t>(nbr, 1))
@@ -1866,8 +1877,10 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
     return c->cuda_fail(e, "emt_adjoint sin table");
   }
   auto tape_of = [&](int64_t j) { return d_tape + (overlap ? (j & 1) : 0) * K * nn; };
+  auto wtape_of = [&](int64_t j) { return rsw ? d_wtape + (overlap ? (j & 1) : 0) * K * c->n_sub : nullptr; };
   auto tape_spec = [&](int64_t j, int64_t seg0, int64_t len) {
     RecSpec r;
+    r.word_tape = wtape_of(j);
     r.rec = tape_of(j);
     r.pos = d_pos;
     r.n_rec = (int32_t)nn;
@@ -1885,6 +1898,12 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_ck_ring + j * ring_words, c->d_ring, ring_words * sizeof(unsigned long long),
                             cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess && rsw)
+        e = cudaMemcpyAsync(d_ck_word + j * c->n_sub, c->d_rs_word, c->n_sub * sizeof(int32_t),
+                            cudaMemcpyDeviceToDevice, st);
+      if (e == cudaSuccess && rsw)
+        e = cudaMemcpyAsync(d_ck_rsi + j * n_rsw, c->d_rs_prev_i, n_rsw * sizeof(double), cudaMemcpyDeviceToDevice,
+                            st);
       if (e != cudaSuccess) break;
     }
     stt = forward_steps(c, len, st, j == n_seg - 1 ? tape_spec(j, s0, len) : RecSpec());
@@ -1929,6 +1948,11 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(c->d_ring, d_ck_ring + j * ring_words, ring_words * sizeof(unsigned long long),
                           cudaMemcpyDeviceToDevice, rs);
+    if (e == cudaSuccess && rsw)
+      e = cudaMemcpyAsync(c->d_rs_word, d_ck_word + j * c->n_sub, c->n_sub * sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                          rs);
+    if (e == cudaSuccess && rsw)
+      e = cudaMemcpyAsync(c->d_rs_prev_i, d_ck_rsi + j * n_rsw, n_rsw * sizeof(double), cudaMemcpyDeviceToDevice, rs);
     if (e != cudaSuccess) return c->cuda_fail(e, "emt_adjoint checkpoint restore");
     c->step = s0;
     return forward_steps(c, len, rs, tape_spec(j, s0, len));
@@ -1960,6 +1984,7 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
       if (e != cudaSuccess || stt != EMT_OK) break;
     }
     a.tape = tape_of(j);
+    a.word_tape = wtape_of(j);
     a.tape_row0 = s0;
     a.n_hi = s0 + len;
     a.n_steps = len;

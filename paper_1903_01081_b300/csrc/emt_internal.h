@@ -177,6 +177,8 @@ struct FwdParams {
   const RuntimeSwitchDev* rs;  // runtime switches (SubDev rs_off / n_rs)
   int32_t* rs_word;            // per subsystem: state word in force at step n0 (carried across launches)
   double* rs_prev_i;           // per runtime switch: breaker current of the previous step
+  int32_t* word_tape;          // optional [rows][n_sub]: state word in force at step n (row n - 1 - word_row0)
+  int64_t word_row0;
 };
 
 struct PrefParams {
@@ -320,6 +322,7 @@ struct AdjParams {
   const double* tape;          // [rows][n_nodes] internal order: v_n in row n - 1 - tape_row0
   int64_t tape_row0;
   const double* target;        // [n_total][n_nodes] caller's node order: v*_n in row n - 1
+  const int32_t* word_tape;    // [rows][n_sub]: runtime-switch state word of step n (row n - 1 - tape_row0), or null
   const int32_t* orig_of;      // internal node -> caller's node
   int64_t n_nodes;
   double* hbar;                // per L/C slot: adjoint of h (carried across launches)

@@ -599,6 +599,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     // runtime-switch states decided from the previous step's solution
     int new_word = 0;
     for (int j = 0; j < n_rs; ++j) new_word |= s_rsbit[j] << j;
+    if (P.word_tape != nullptr && tid == 0) P.word_tape[(step - 1 - P.word_row0) * P.n_sub + sidx] = new_word;
     if (step >= next_ep_start || new_word != word) {
       while (te + 1 < n_te && P.ep[S.ep_off + (te + 1) * n_states].start <= step) ++te;
       next_ep_start = (te + 1 < n_te) ? P.ep[S.ep_off + (te + 1) * n_states].start : LLONG_MAX;

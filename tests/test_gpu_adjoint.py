@@ -91,6 +91,26 @@ def test_device_tensors_and_stream():
     assert np.array_equal(g_d.cpu().numpy(), g_h)
 
 
+def test_adjoint_with_runtime_switches():
+    """Rectifier loads and breakers: the reverse sweep uses the switch states
+    the forward run decided (word tape), across checkpoint segments."""
+    base = g.multi_subsystem(43, [2, 3, 2], n_lines=4, n_sources=2, dt=20e-6, n_series_extra=2,
+                             delay_range=(1, 6))
+    net = g.with_rectifier_loads(base, seed=7, n_rectifiers=3, n_breakers=2, trip_range=(100, 300))
+    N = 900
+    tgt = target_of(net, N)
+    g_ref, J_ref = oracle.adjoint(net, N, tgt)
+    st = oracle.runtime_switch_states(net, N)
+    assert (st.min(axis=0) != st.max(axis=0)).any()
+    ref = gpu_adjoint(net, tgt, N, 0)
+    assert abs(ref[0] - J_ref) <= 1e-12 * J_ref
+    assert close(ref[1], g_ref)
+    for K in (1, 64, 300):
+        for overlap in (True, False):
+            J, grad = gpu_adjoint(net, tgt, N, K, overlap)
+            assert J == ref[0] and np.array_equal(grad, ref[1]), (K, overlap)
+
+
 def test_single_subsystem_and_one_step():
     net = g.single_rlc(n_steps=400)
     for N, K in ((1, 1), (400, 32)):

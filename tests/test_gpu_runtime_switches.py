@@ -124,9 +124,6 @@ def test_runtime_switch_limits():
     ctx = emt.emt_build_network(net)
     emt.emt_prefactor(ctx)
     assert emt.emt_get_info(ctx, "n_runtime_switches") == 9
-    with pytest.raises(emt.EmtError) as ei:
-        emt.emt_adjoint(ctx, np.zeros((10, net.n_nodes)), 10, 4)
-    assert ei.value.status == emt.EMT_EINVAL
     emt.emt_destroy(ctx)
     with pytest.raises(emt.EmtError) as ei:
         emt.emt_build_network(net, g.Scenarios(n_scenarios=2))
