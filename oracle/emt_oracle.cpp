@@ -524,7 +524,7 @@ extern "C" int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_
 // and finally dg/dR = -1/R^2, dg/dL = -dt/(2L^2), dg/dC = 2/dt.
 extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad,
                            double* loss) {
-  if (!valid(net) || !v_target || !grad || n_steps < 0 || net->n_cl > 0) return -1;
+  if (!valid(net) || !v_target || !grad || n_steps < 0) return -1;
   const int64_t nn = net->n_nodes, nb = net->n_br, ns = net->n_src, nl = net->n_ln, nr = net->n_rs;
   Sim<double> sim;
   sim.net = net;
@@ -553,6 +553,19 @@ extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_
     ibar_k[l].assign(net->ln_d[l] + 1, 0.0);
     ibar_m[l].assign(net->ln_d[l] + 1, 0.0);
   }
+  // coupled lines: adjoints Ibar of the modal histories per end and mode,
+  // by step modulo d + 2 (zero beyond the last step); the adjoint of the
+  // value c_e,j(n) an end sent is X = (1 - f) Ibar_far(n + d) + f Ibar_far(n + d + 1)
+  const int64_t ncl = net->n_cl;
+  std::vector<std::vector<double>> cl_ibar((size_t)ncl * 6);
+  std::vector<double> cl_x((size_t)ncl * 6, 0.0);
+  for (int64_t l = 0; l < ncl; ++l)
+    for (int e = 0; e < 2; ++e)
+      for (int j = 0; j < 3; ++j) cl_ibar[6 * l + 3 * e + j].assign(sim.cl[l].d[j] + 2, 0.0);
+  auto cl_ibar_at = [&](int64_t l, int e, int j, int64_t m) -> double {
+    if (m > n_steps) return 0.0;
+    return cl_ibar[6 * l + 3 * e + j][m % (sim.cl[l].d[j] + 2)];
+  };
   auto V = [&](const double* vn, int32_t x) { return x >= 0 ? vn[x] : (x == -1 ? 0.0 : vs[-2 - x]); };
   for (int64_t n = n_steps; n >= 1; --n) {
     const double* vn = tape.data() + (size_t)(n - 1) * nn;
@@ -572,6 +585,20 @@ extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_
       double y2 = 2.0 / net->ln_zc[l];
       vbar[net->ln_k[l]] += -y2 * ibar_m[l][(n + d) % d1];
       vbar[net->ln_m[l]] += -y2 * ibar_k[l][(n + d) % d1];
+    }
+    // coupled lines: c_e,j(n) = -(2/Z_j) (T_v^-1 v_e)_j - I_e,j(n) feeds the far
+    // end's histories at n + d and n + d + 1
+    for (int64_t l = 0; l < ncl; ++l) {
+      const auto& L = sim.cl[l];
+      for (int e = 0; e < 2; ++e) {
+        const int32_t* nd = (e == 0 ? net->cl_k : net->cl_m) + 3 * l;
+        for (int j = 0; j < 3; ++j) {
+          const double x = (1.0 - L.f[j]) * cl_ibar_at(l, 1 - e, j, n + L.d[j]) +
+                           L.f[j] * cl_ibar_at(l, 1 - e, j, n + L.d[j] + 1);
+          cl_x[6 * l + 3 * e + j] = x;
+          for (int p = 0; p < 3; ++p) vbar[nd[p]] += -L.y2[j] * L.tinv[3 * j + p] * x;
+        }
+      }
     }
     // w_n = G_n^{-T} vbar_n, per subsystem with the factors of step n
     for (int64_t w = 0; w < nr; ++w) sim.rs_on[w] = rs_tape[(size_t)(n - 1) * nr + w];
@@ -613,6 +640,18 @@ extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_
       double far_m = ibar_m[l][(n + d) % d1], far_k = ibar_k[l][(n + d) % d1];
       ibar_k[l][n % d1] = -w[net->ln_k[l]] - far_m;
       ibar_m[l][n % d1] = -w[net->ln_m[l]] - far_k;
+    }
+    // coupled lines: I_e,j(n) leaves the phase nodes through T_i and enters c_e,j(n)
+    for (int64_t l = 0; l < ncl; ++l) {
+      const auto& L = sim.cl[l];
+      for (int e = 0; e < 2; ++e) {
+        const int32_t* nd = (e == 0 ? net->cl_k : net->cl_m) + 3 * l;
+        for (int j = 0; j < 3; ++j) {
+          double tw = 0.0;
+          for (int p = 0; p < 3; ++p) tw += L.ti[3 * p + j] * w[nd[p]];
+          cl_ibar[6 * l + 3 * e + j][n % (L.d[j] + 2)] = -tw - cl_x[6 * l + 3 * e + j];
+        }
+      }
     }
   }
   for (int64_t b = 0; b < nb; ++b) {

@@ -104,8 +104,9 @@ int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_target, int
 /* Discrete adjoint of the loss over the full stored trajectory.
  * grad: [n_br + n_src] = dJ/d(branch value) then dJ/d(source amplitude).
  * With runtime switches the reverse sweep uses the states the forward run
- * decided (the gradient of the smooth piece the run lies on).  Networks
- * with coupled lines are rejected (-1). */
+ * decided (the gradient of the smooth piece the run lies on).  The
+ * parameters of coupled lines themselves (Z, T_v, travel times) are not
+ * differentiated. */
 int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad, double* loss);
 
 /* Subsystem of each unknown node (components over branches and switches). */

@@ -123,7 +123,15 @@ def test_coupled_line_validation():
         oracle.simulate(net, 10)
 
 
-def test_adjoint_rejects_coupled_lines():
-    net = three_line_net(True)
-    with pytest.raises(oracle.OracleError):
-        oracle.adjoint(net, 10, np.zeros((10, net.n_nodes)))
+def test_adjoint_with_coupled_lines_vs_complex_step():
+    """The reverse of the modal line (interpolated delays, T_v, Y_p) against
+    complex-step derivatives of every parameter."""
+    net = three_line_net(True, tau=[3.4 * DT, 5.1 * DT, 7.9 * DT], tv=g.CLARKE, z=(550.0, 280.0, 280.0))
+    N = 600
+    br_t, amp_t = g.adjoint_target(net, seed=77)
+    tgt = oracle.simulate(net.with_params(br_t, amp_t), N)
+    grad, J = oracle.adjoint(net, N, tgt)
+    n_par = net.n_branches + net.n_sources
+    cs = np.array([oracle.loss_complex_step(net, N, tgt, p)[1] for p in range(n_par)])
+    p = np.concatenate([net.br_value, net.src_amp])
+    assert np.max(np.abs(p * (grad - cs)) / J) < 1e-9
