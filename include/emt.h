@@ -78,7 +78,9 @@ typedef struct emt_ctx emt_ctx;  /* opaque; owns all device memory it allocates 
  *   c_j(n) = -(2/Z_j) v_mode_j(n) - I_mode_j(n), and the far end's history
  *   is (1 - f) c(n - d) + f c(n - d - 1), tau = (d + f) dt, d = floor(tau/dt)
  *   (linear interpolation of the travel time).  An end's three phase nodes
- *   are one subsystem.  Not supported with a scenario set or by emt_adjoint. */
+ *   are one subsystem.  Not supported with a scenario set; emt_adjoint
+ *   differentiates through them (their own Z, T_v and travel times are not
+ *   parameters). */
 typedef struct {
   double dt;
   int64_t n_nodes;
@@ -242,8 +244,9 @@ emt_status emt_autotune(emt_ctx* ctx, int64_t trial_steps, void* cuda_stream);
  *   cuda_stream: stream for the launches (NULL: legacy default stream).
  * With runtime switches the reverse sweep uses the states the forward run
  * decided (the forward re-runs record them per step), i.e. the gradient of
- * the smooth piece of J the run lies on.  Requires emt_prefactor; a context
- * built with a scenario set or with coupled lines returns EINVAL.  Resets the context to step 0 before and after (the recording
+ * the smooth piece of J the run lies on.  Coupled lines' own Z, T_v and
+ * travel times are not parameters.  Requires emt_prefactor; a context built
+ * with a scenario set returns EINVAL.  Resets the context to step 0 before and after (the recording
  * buffer is not written).  Allocates its work buffers (about 8 N n_nodes
  * bytes for a host v_target, N/K checkpoints, the tape) and frees them
  * before returning.  Synchronous.  ETIMEOUT as for emt_step_n. */

@@ -42,9 +42,11 @@ constexpr int kAdjPollWarp = kAdjThreads / 32 - 1;
 constexpr int kAdjItemThreads = kAdjThreads - 32;
 
 struct AdjSmem {
-  size_t gi, part, iv, ww, vn, ev, inp, xr, hb, lce, brg, bre, dga, dsa, ley2, leown, lefar, amp, sn, vsrc;   // 8-byte
+  size_t gi, part, iv, ww, vn, ev, inp, xr, hb, lce, brg, bre, dga, dsa, ley2, leown, lefar, amp, sn, vsrc, lef,
+      xmode, ceti, cetinv;                                                                               // 8-byte
   size_t gilo, ivf, partf;                                                                               // float
-  size_t brk, brm, brlc, brkind, lcstr, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, orig;   // int
+  size_t brk, brm, brlc, brkind, lcstr, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, orig, lece,
+      lemode, cele0, cenode;                                                                             // int
   size_t bytes;
 };
 
@@ -60,7 +62,7 @@ __host__ __device__ inline AdjSmem adj_smem(const AdjLimits& L) {
   s.ww = d(L.n);
   s.vn = d(2 * (size_t)L.n);
   s.ev = d(2 * (size_t)L.n);
-  s.inp = d((size_t)L.lc + L.sb + 2 * (size_t)L.le + 1);
+  s.inp = d((size_t)L.lc + L.sb + 2 * ((size_t)L.le + 3 * (size_t)L.ce) + 1);
   s.xr = d(2 * (size_t)L.le);
   s.hb = d(L.lc);
   s.lce = d(L.lc);
@@ -74,6 +76,10 @@ __host__ __device__ inline AdjSmem adj_smem(const AdjLimits& L) {
   s.amp = d(L.src);
   s.sn = d(2 * (size_t)L.src);
   s.vsrc = d(2 * (size_t)L.src);
+  s.lef = d(L.le);
+  s.xmode = d(2 * (size_t)L.le);
+  s.ceti = d(9 * (size_t)L.ce);
+  s.cetinv = d(9 * (size_t)L.ce);
   s.gilo = w((size_t)L.n * ldg);
   s.ivf = w(L.nc);
   s.partf = w((size_t)L.n * L.q);
@@ -92,6 +98,10 @@ __host__ __device__ inline AdjSmem adj_smem(const AdjLimits& L) {
   s.ilcnt = w(L.il);
   s.srcg = w(L.src);
   s.orig = w(L.n);
+  s.lece = w(L.le);
+  s.lemode = w(L.le);
+  s.cele0 = w(L.ce);
+  s.cenode = w(3 * (size_t)L.ce);
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
 }
@@ -130,6 +140,27 @@ __device__ bool collect_adj(const AdjParams& P, int n_le, unsigned tag, int lane
     rslot[e] = nx == ledepth[e] ? 0 : nx;
   }
   return __all_sync(0xffffffffu, ok);
+}
+
+// Coupled line modes in reverse (poll warp, after collecting): the adjoint
+// of the value each mode sent, X = (1 - f) Ibar_far(n + d) + f Ibar_far(n + d
+// + 1), from the values consumed at this reverse step (xr_new) and the
+// previous one (xr_old); then the phase slots sum_j T_i[p][j] (2/Z_j) X_j
+// that the injection entries subtract at the phase nodes.
+__device__ void fold_modes_adj(int lane, int n_le, int n_ce, const int* lece, const double* lef, const double* ley2,
+                               const double* xr_old, const double* xr_new, double* xmode_new, double* blk_new,
+                               const int* cele0, const double* ceti) {
+  for (int e = lane; e < n_le; e += 32)
+    if (lece[e] >= 0) xmode_new[e] = fma(lef[e], xr_old[e], (1.0 - lef[e]) * xr_new[e]);
+  __syncwarp();
+  for (int x = lane; x < 3 * n_ce; x += 32) {
+    const int c = x / 3, p = x - 3 * c;
+    const double* ti = ceti + 9 * c + 3 * p;
+    const int e0 = cele0[c];
+    blk_new[n_le + x] = fma(ti[0], ley2[e0] * xmode_new[e0],
+                            fma(ti[1], ley2[e0 + 1] * xmode_new[e0 + 1], ti[2] * (ley2[e0 + 2] * xmode_new[e0 + 2])));
+  }
+  __syncwarp();
 }
 
 __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
@@ -174,6 +205,14 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
   int* ilcnt = reinterpret_cast<int*>(smem_raw + L.ilcnt);
   int* srcg = reinterpret_cast<int*>(smem_raw + L.srcg);
   int* orig = reinterpret_cast<int*>(smem_raw + L.orig);
+  double* lef = reinterpret_cast<double*>(smem_raw + L.lef);
+  double* xmode = reinterpret_cast<double*>(smem_raw + L.xmode);    // [2][le]: modes' X by parity
+  double* ceti = reinterpret_cast<double*>(smem_raw + L.ceti);
+  double* cetinv = reinterpret_cast<double*>(smem_raw + L.cetinv);
+  int* lece = reinterpret_cast<int*>(smem_raw + L.lece);
+  int* lemode = reinterpret_cast<int*>(smem_raw + L.lemode);
+  int* cele0 = reinterpret_cast<int*>(smem_raw + L.cele0);
+  int* cenode = reinterpret_cast<int*>(smem_raw + L.cenode);
 
   const int sidx = blockIdx.x;
   const SubDev S = P.sub[sidx];
@@ -181,8 +220,10 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
   const int n = S.n, Q = S.q, n_str = S.n_str, nc = n + n_str, ldg = nc | 1;
   const int blk = (nc + Q - 1) / Q;
   const int n_br = S.n_br, n_lc = S.n_lc, n_sb = S.n_sb, n_le = S.n_le, n_il = S.n_il, n_src = S.n_src;
+  const int n_ce = S.n_ce;
   const int ie_base = n_lc + n_sb;
-  const int zero_slot = ie_base + 2 * n_le;
+  const int blk_len = n_le + 3 * n_ce;   // per parity: line-end values, then coupled ends' phase slots
+  const int zero_slot = ie_base + 2 * blk_len;
   const int nv = P.lim.n, sv = P.lim.src, lv = P.lim.le;   // strides of the parity-doubled arrays
   const int src_thread = T - 1 - tid;
   const int it_le = (n_br + 31) & ~31;   // branch items, then line ends on their own warps
@@ -221,6 +262,19 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
     led[x] = e.d;
     rslot[x] = (int)(tau0 % e.depth);
     wslot[x] = (int)((tau0 + e.d) % e.depth);
+    lef[x] = e.f;
+    lece[x] = e.ce;
+    lemode[x] = e.mode;
+    xr[(int)((tau0 - 1) & 1) * lv + x] = P.le_prev[S.le_off + x];   // consumed at the previous reverse step
+  }
+  for (int c = tid; c < n_ce; c += T) {
+    const CoupledEndDev& ce = P.ce[S.ce_off + c];
+    cele0[c] = ce.le0;
+    for (int k = 0; k < 3; ++k) cenode[3 * c + k] = ce.node[k];
+    for (int k = 0; k < 9; ++k) {
+      ceti[9 * c + k] = ce.ti[k];
+      cetinv[9 * c + k] = ce.tinv[k];
+    }
   }
   for (int x = tid; x < 4 * n_il; x += T) ent[x] = P.ent[4 * (size_t)S.il_off + x];
   for (int x = tid; x < n_il; x += T) {
@@ -273,8 +327,11 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
   }
   if (warp == kAdjPollWarp && n_le > 0) {
     const bool ok = collect_adj(P, n_le, (unsigned)tau0, lane, sidx, leown, ledepth, rslot, ley2, xr + par0 * lv,
-                                inp + ie_base + par0 * n_le);
+                                inp + ie_base + par0 * blk_len);
     if (!ok && lane == 0) s_abort = 1;
+    if (n_ce > 0)
+      fold_modes_adj(lane, n_le, n_ce, lece, lef, ley2, xr + (par0 ^ 1) * lv, xr + par0 * lv, xmode + par0 * lv,
+                     inp + ie_base + par0 * blk_len, cele0, ceti);
   }
   double jacc = P.loss_part[(int64_t)sidx * T + tid];
   __syncthreads();
@@ -283,7 +340,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
     const long long nstep = P.n_hi - i;
     const long long tau = tau0 + i;
     const int par = (int)(tau & 1);
-    const int parshift = par * n_le;
+    const int parshift = par * blk_len;
     const bool more = i + 1 < P.n_steps;
     const int w_now = words ? P.word_tape[(nstep - 1 - P.tape_row0) * P.n_sub + sidx] : 0;
     if (nstep < ep_start || w_now != word) {   // an earlier epoch, or another runtime-switch state
@@ -316,10 +373,10 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
         node = ilnode[l];
         cnt = ilcnt[l];
         const int* e4 = ent + 4 * l;
-        s = (signed_entry(inp, (unsigned)e4[0], ie_base, n_le, parshift) +
-             signed_entry(inp, (unsigned)e4[1], ie_base, n_le, parshift)) +
-            (signed_entry(inp, (unsigned)e4[2], ie_base, n_le, parshift) +
-             signed_entry(inp, (unsigned)e4[3], ie_base, n_le, parshift));
+        s = (signed_entry(inp, (unsigned)e4[0], ie_base, blk_len, parshift) +
+             signed_entry(inp, (unsigned)e4[1], ie_base, blk_len, parshift)) +
+            (signed_entry(inp, (unsigned)e4[2], ie_base, blk_len, parshift) +
+             signed_entry(inp, (unsigned)e4[3], ie_base, blk_len, parshift));
       }
       const int wmax = __reduce_max_sync(0xffffffffu, cnt);
       double acc = s;
@@ -380,8 +437,11 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
     if (warp == kAdjPollWarp) {
       if (n_le > 0 && more) {
         const bool ok = collect_adj(P, n_le, (unsigned)(tau + 1), lane, sidx, leown, ledepth, rslot, ley2,
-                                    xr + (par ^ 1) * lv, inp + ie_base + (par ^ 1) * n_le);
+                                    xr + (par ^ 1) * lv, inp + ie_base + (par ^ 1) * blk_len);
         if (!ok && lane == 0) s_abort = 1;
+        if (n_ce > 0)
+          fold_modes_adj(lane, n_le, n_ce, lece, lef, ley2, xr + par * lv, xr + (par ^ 1) * lv, xmode + (par ^ 1) * lv,
+                         inp + ie_base + (par ^ 1) * blk_len, cele0, ceti);
       }
     } else {
       const double* vnc = vn + par * nv;
@@ -421,8 +481,16 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
           }
         } else if (it >= it_le) {
           const int e = it - it_le;
-          st_tagged(P.ring + 2 * (lefar[e] + wslot[e]), (unsigned)(tau + led[e]),
-                    -ww[lenode[e]] - xr[par * lv + e]);
+          const int c = lece[e];
+          double out;
+          if (c < 0) {
+            out = -ww[lenode[e]] - xr[par * lv + e];
+          } else {   // a mode: Ibar_j(n) = -(T_i^T w)_j - X_j, T_i^T = T_v^-1
+            const double* tr = cetinv + 9 * c + 3 * lemode[e];
+            const int* nd = cenode + 3 * c;
+            out = -fma(tr[0], ww[nd[0]], fma(tr[1], ww[nd[1]], tr[2] * ww[nd[2]])) - xmode[par * lv + e];
+          }
+          st_tagged(P.ring + 2 * (lefar[e] + wslot[e]), (unsigned)(tau + led[e]), out);
           const int nx = wslot[e] + 1;
           wslot[e] = nx == ledepth[e] ? 0 : nx;
         }
@@ -432,6 +500,9 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
   }
   if (!s_abort) {
     for (int x = tid; x < n_lc; x += T) P.hbar[S.lc_off + x] = hb[x];
+    if (P.n_steps > 0)
+      for (int x = tid; x < n_le; x += T)
+        P.le_prev[S.le_off + x] = xr[(int)((tau0 + P.n_steps - 1) & 1) * lv + x];
     for (int x = tid; x < n_br; x += T) {
       P.dg[S.br_off + x] = dga[x];
       P.dsrc[S.br_off + x] = dsa[x];

@@ -1746,7 +1746,6 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
                                   double* grad, double* loss, int32_t on_device, void* stream) {
   if (!c) return EMT_EINVAL;
   if (c->batched) return c->fail(EMT_EINVAL, "emt_adjoint: a context built with a scenario set has no adjoint");
-  if (!c->cends.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: networks with coupled lines have no adjoint");
   if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
   if (n_steps < 1) return c->fail(EMT_EINVAL, "emt_adjoint: n_steps must be >= 1");
   if (n_steps > (int64_t)INT32_MAX - (int64_t)(1 << 21))
@@ -1764,6 +1763,7 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
   al.le = c->lim.le;
   al.src = c->lim.src;
   al.il = c->lim.il;
+  al.ce = c->lim.ce;
   if (adjoint_smem_bytes(al) > 227 * 1024)
     return c->fail(EMT_ERESOURCE, "emt_adjoint: a subsystem needs more shared memory than one CTA has");
   emt_status rs0 = emt_reset(c);
@@ -1807,6 +1807,7 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
   int32_t* d_pos = nullptr;
   int32_t *d_wtape = nullptr, *d_ck_word = nullptr;   // runtime switches: per-step state words, checkpoints
   double* d_ck_rsi = nullptr;
+  double *d_adj_lep = nullptr, *d_ck_lep = nullptr;    // line ends: adjoint carry; forward carry checkpoints
   cudaError_t e = cudaSuccess;
   if (!on_device) {
     e = c->alloc_zero(&d_tgt_copy, (size_t)(N * nn));
@@ -1828,6 +1829,10 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
   ADJ_ALLOC(d_tape, (overlap ? 2 : 1) * K * nn)
   const bool rsw = !c->rswitches.empty();
   const int64_t n_rsw = (int64_t)c->rswitches.size();
+  const bool cpl = !c->cends.empty();
+  const int64_t n_lend = std::max<int64_t>((int64_t)c->line_ends.size(), 1);
+  ADJ_ALLOC(d_adj_lep, n_lend)
+  if (cpl) ADJ_ALLOC(d_ck_lep, std::max<int64_t>((n_seg - 1) * n_lend, 1))
   if (rsw) {
     ADJ_ALLOC(d_wtape, (overlap ? 2 : 1) * K * c->n_sub)
     ADJ_ALLOC(d_ck_word, std::max<int64_t>((n_seg - 1) * c->n_sub, 1))
@@ -1904,6 +1909,9 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
       if (e == cudaSuccess && rsw)
         e = cudaMemcpyAsync(d_ck_rsi + j * n_rsw, c->d_rs_prev_i, n_rsw * sizeof(double), cudaMemcpyDeviceToDevice,
                             st);
+      if (e == cudaSuccess && cpl)
+        e = cudaMemcpyAsync(d_ck_lep + j * n_lend, c->d_le_prev, c->line_ends.size() * sizeof(double),
+                            cudaMemcpyDeviceToDevice, st);
       if (e != cudaSuccess) break;
     }
     stt = forward_steps(c, len, st, j == n_seg - 1 ? tape_spec(j, s0, len) : RecSpec());
@@ -1932,6 +1940,8 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
   a.sin_table = d_sin;
   a.n_sources = (int32_t)ns;
   a.target = d_tgt;
+  a.ce = c->d_ce;
+  a.le_prev = d_adj_lep;
   a.orig_of = c->d_original_of;
   a.n_nodes = nn;
   a.hbar = d_hbar;
@@ -1953,6 +1963,9 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
                           rs);
     if (e == cudaSuccess && rsw)
       e = cudaMemcpyAsync(c->d_rs_prev_i, d_ck_rsi + j * n_rsw, n_rsw * sizeof(double), cudaMemcpyDeviceToDevice, rs);
+    if (e == cudaSuccess && cpl)
+      e = cudaMemcpyAsync(c->d_le_prev, d_ck_lep + j * n_lend, c->line_ends.size() * sizeof(double),
+                          cudaMemcpyDeviceToDevice, rs);
     if (e != cudaSuccess) return c->cuda_fail(e, "emt_adjoint checkpoint restore");
     c->step = s0;
     return forward_steps(c, len, rs, tape_spec(j, s0, len));

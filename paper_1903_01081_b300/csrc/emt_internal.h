@@ -290,7 +290,7 @@ struct BatchGraph {
 
 // Per-launch upper bounds that size the adjoint kernel's shared memory.
 struct AdjLimits {
-  int32_t n, nc, q, br, lc, sb, le, src, il;
+  int32_t n, nc, q, br, lc, sb, le, src, il, ce;
 };
 
 // Reverse sweep of the discrete adjoint over steps n = n_hi, n_hi - 1, ...,
@@ -323,6 +323,8 @@ struct AdjParams {
   int64_t tape_row0;
   const double* target;        // [n_total][n_nodes] caller's node order: v*_n in row n - 1
   const int32_t* word_tape;    // [rows][n_sub]: runtime-switch state word of step n (row n - 1 - tape_row0), or null
+  const CoupledEndDev* ce;     // coupled line ends
+  double* le_prev;             // per line end: adjoint value consumed at the previous reverse step (carried)
   const int32_t* orig_of;      // internal node -> caller's node
   int64_t n_nodes;
   double* hbar;                // per L/C slot: adjoint of h (carried across launches)

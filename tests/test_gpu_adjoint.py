@@ -111,6 +111,24 @@ def test_adjoint_with_runtime_switches():
             assert J == ref[0] and np.array_equal(grad, ref[1]), (K, overlap)
 
 
+def test_adjoint_with_coupled_lines():
+    """Clarke-mode coupled lines with interpolated travel times: the reverse of
+    the modal exchange, across checkpoint segments."""
+    base = g.multi_subsystem(44, [2, 3, 2, 2], n_lines=5, n_sources=2, dt=20e-6, n_series_extra=2,
+                             delay_range=(1, 6))
+    net = g.with_coupled_lines(base, seed=8)
+    N = 900
+    tgt = target_of(net, N)
+    g_ref, J_ref = oracle.adjoint(net, N, tgt)
+    ref = gpu_adjoint(net, tgt, N, 0)
+    assert abs(ref[0] - J_ref) <= 1e-12 * J_ref
+    assert close(ref[1], g_ref)
+    for K in (1, 64, 300):
+        for overlap in (True, False):
+            J, grad = gpu_adjoint(net, tgt, N, K, overlap)
+            assert J == ref[0] and np.array_equal(grad, ref[1]), (K, overlap)
+
+
 def test_single_subsystem_and_one_step():
     net = g.single_rlc(n_steps=400)
     for N, K in ((1, 1), (400, 32)):

@@ -78,9 +78,6 @@ def test_coupled_lines_rejected_where_unsupported():
     ctx = emt.emt_build_network(net)
     emt.emt_prefactor(ctx)
     assert emt.emt_get_info(ctx, "n_coupled_lines") == 3   # three three-phase lines
-    with pytest.raises(emt.EmtError) as ei:
-        emt.emt_adjoint(ctx, np.zeros((10, net.n_nodes)), 10, 4)
-    assert ei.value.status == emt.EMT_EINVAL
     emt.emt_destroy(ctx)
     with pytest.raises(emt.EmtError) as ei:
         emt.emt_build_network(net, g.Scenarios(n_scenarios=2))
