@@ -209,11 +209,15 @@ namespace {
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
-// Inverse of a 3 x 3 row-major matrix (cofactors); false if singular.
+// Inverse of a 3 x 3 row-major matrix (cofactors); false if singular to working
+// precision: |det| at most 1e-12 of Hadamard's bound, the product of the row norms.
 bool invert3_host(const double* a, double* inv) {
   const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
   const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
-  if (!(std::fabs(det) > 0.0) || !std::isfinite(det)) return false;
+  double bound = 1.0;
+  for (int r = 0; r < 3; ++r)
+    bound *= std::sqrt(a[3 * r] * a[3 * r] + a[3 * r + 1] * a[3 * r + 1] + a[3 * r + 2] * a[3 * r + 2]);
+  if (!std::isfinite(det) || !std::isfinite(bound) || !(std::fabs(det) > 1e-12 * bound)) return false;
   inv[0] = c00 / det;
   inv[3] = c01 / det;
   inv[6] = c02 / det;

@@ -73,3 +73,48 @@ def test_rejects_oversized_subsystem():
     for i in range(n - 1):
         b.branch(i, i + 1, 0, 1.0)
     assert "at most 128" in bad(b.build(1e-5, n))
+
+
+def test_rejects_bad_runtime_switches():
+    net = g.with_rectifier_loads(g.multi_subsystem(5, [6, 6], n_lines=2, n_sources=2, dt=20e-6),
+                                 n_rectifiers=3, n_breakers=1)
+    assert net.n_runtime_switches == 4
+    kind = net.rs_kind.copy(); kind[0] = 2
+    assert "diode" in bad(net, rs_kind=kind)
+    assert "resistances" in bad(net, rs_ron=np.zeros_like(net.rs_ron))
+    assert "resistances" in bad(net, rs_roff=np.full_like(net.rs_roff, np.inf))
+    k = net.rs_k.copy(); m = net.rs_m.copy(); k[1] = -1; m[1] = -1
+    assert "ground" in bad(net, rs_k=k, rs_m=m)
+    # more two-state switches in one subsystem than the state word holds
+    b = g.NetworkBuilder()
+    b.source(1.0, 0.0)
+    b.branch(g.source_node(0), 0, 0, 1.0)
+    for i in range(9):
+        b.branch(0, i + 1, 0, 2.0)
+        b.diode(i + 1, g.GROUND, 0.01, 1e6)
+    assert "more than 8 runtime switches" in str(pytest.raises(
+        emt.EmtError, emt.emt_build_network, b.build(20e-6, 10)).value)
+
+
+def test_rejects_bad_coupled_lines():
+    net = g.with_coupled_lines(g.multi_subsystem(7, [6, 6], n_lines=1, n_sources=2, dt=20e-6))
+    assert net.n_coupled_lines >= 1
+    tau = net.cl_tau.copy(); tau.flat[0] = 0.5 * net.dt
+    assert "at least dt" in bad(net, cl_tau=tau)
+    z = net.cl_z.copy(); z.flat[1] = 0.0
+    assert "Z_c" in bad(net, cl_z=z)
+    tv = net.cl_tv.copy().reshape(-1, 3, 3); tv[0, 2] = tv[0, 0]
+    assert "singular" in bad(net, cl_tv=tv.reshape(net.cl_tv.shape))
+    k = net.cl_k.copy(); k.flat[0] = -1
+    assert "unknown nodes" in bad(net, cl_k=k)
+
+
+def test_rejects_scenario_set_with_runtime_switches_or_coupled_lines():
+    net, sc = g.n1_contingency(n_scenarios=4, n_buses=24, n_sub=4, n_steps=10)
+    rs = g.with_rectifier_loads(net, n_rectifiers=2, n_breakers=0)
+    with pytest.raises(emt.EmtError, match="runtime switches are not supported"):
+        emt.emt_build_network(rs, sc)
+    cl = g.with_coupled_lines(net)
+    assert cl.n_coupled_lines > 0
+    with pytest.raises(emt.EmtError, match="coupled lines are not supported"):
+        emt.emt_build_network(cl, sc)
