@@ -55,6 +55,10 @@ class _Net(ctypes.Structure):
         ("rs_on0", ctypes.c_void_p), ("rs_trip", ctypes.c_void_p),
         ("n_cl", ctypes.c_int64), ("cl_k", ctypes.c_void_p), ("cl_m", ctypes.c_void_p),
         ("cl_tv", ctypes.c_void_p), ("cl_z", ctypes.c_void_p), ("cl_tau", ctypes.c_void_p),
+        ("n_cb", ctypes.c_int64), ("cb_type", ctypes.c_void_p), ("cb_in0", ctypes.c_void_p),
+        ("cb_in1", ctypes.c_void_p), ("cb_node", ctypes.c_void_p), ("cb_p0", ctypes.c_void_p),
+        ("cb_p1", ctypes.c_void_p),
+        ("n_ci", ctypes.c_int64), ("ci_block", ctypes.c_void_p), ("ci_node", ctypes.c_void_p),
     ]
 
 
@@ -70,8 +74,9 @@ def _load():
         lib.orc_partition.argtypes = [P, P, P]
         lib.orc_lu_solve.argtypes = [ctypes.c_int64, P, P, P]
         lib.orc_rs_states.argtypes = [P, ctypes.c_int64, P]
+        lib.orc_controls.argtypes = [P, ctypes.c_int64, P]
         for f in (lib.orc_run, lib.orc_loss_cs, lib.orc_adjoint, lib.orc_partition, lib.orc_lu_solve,
-                  lib.orc_rs_states):
+                  lib.orc_rs_states, lib.orc_controls):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -118,6 +123,13 @@ class _Pinned:
         n.cl_k, n.cl_m = p(rs("cl_k", np.int32), np.int32), p(rs("cl_m", np.int32), np.int32)
         n.cl_tv, n.cl_z = p(rs("cl_tv", np.float64), np.float64), p(rs("cl_z", np.float64), np.float64)
         n.cl_tau = p(rs("cl_tau", np.float64), np.float64)
+        n.n_cb = int(len(rs("cb_type", np.uint8)))
+        n.cb_type = p(rs("cb_type", np.uint8), np.uint8)
+        n.cb_in0, n.cb_in1 = p(rs("cb_in0", np.int32), np.int32), p(rs("cb_in1", np.int32), np.int32)
+        n.cb_node = p(rs("cb_node", np.int32), np.int32)
+        n.cb_p0, n.cb_p1 = p(rs("cb_p0", np.float64), np.float64), p(rs("cb_p1", np.float64), np.float64)
+        n.n_ci = int(len(rs("ci_block", np.int32)))
+        n.ci_block, n.ci_node = p(rs("ci_block", np.int32), np.int32), p(rs("ci_node", np.int32), np.int32)
         self.net = n
 
     @property
@@ -192,6 +204,15 @@ def runtime_switch_states(net, n_steps: int):
     pin = _Pinned(net)
     out = np.zeros((int(n_steps), pin.net.n_rs), dtype=np.uint8)
     _check(lib.orc_rs_states(pin.ref, int(n_steps), out.ctypes.data if out.size else None), "orc_rs_states")
+    return out
+
+
+def controls(net, n_steps: int):
+    """Control block outputs of steps 1..n_steps: [n_steps, n_cb]."""
+    lib = _load()
+    pin = _Pinned(net)
+    out = np.zeros((int(n_steps), pin.net.n_cb), dtype=np.float64)
+    _check(lib.orc_controls(pin.ref, int(n_steps), out.ctypes.data if out.size else None), "orc_controls")
     return out
 
 

@@ -160,6 +160,22 @@ bool valid(const orc_net* net) {
     if (k < -1 || m < -1 || k >= net->n_nodes || m >= net->n_nodes || k == m || (k < 0 && m < 0)) return false;
     if (net->rs_kind[w] > 1 || !(net->rs_ron[w] > 0.0) || !(net->rs_roff[w] > 0.0)) return false;
   }
+  if (net->n_cb < 0 || net->n_ci < 0) return false;
+  for (int64_t b = 0; b < net->n_cb; ++b) {
+    const int t = net->cb_type[b];
+    if (t > 8 || !std::isfinite(net->cb_p0[b]) || !std::isfinite(net->cb_p1[b])) return false;
+    const int n_in = (t <= 1) ? 0 : (t == 3 || t == 4) ? 2 : 1;
+    const int32_t in[2] = {net->cb_in0[b], net->cb_in1[b]};
+    for (int i = 0; i < n_in; ++i)
+      if (in[i] < 0 || in[i] >= net->n_cb) return false;
+    if (t == 1 && (net->cb_node[b] < 0 || net->cb_node[b] >= net->n_nodes)) return false;
+    if (t == 5 && !(net->cb_p0[b] <= net->cb_p1[b])) return false;
+    if (t == 7 && !(net->cb_p1[b] > 0.0)) return false;
+  }
+  for (int64_t c = 0; c < net->n_ci; ++c)
+    if (net->ci_block[c] < 0 || net->ci_block[c] >= net->n_cb || net->ci_node[c] < 0 ||
+        net->ci_node[c] >= net->n_nodes)
+      return false;
   return true;
 }
 
@@ -240,6 +256,9 @@ struct Sim {
     T im[2][3];   // modal history currents of the current step per end
   };
   std::vector<CLine> cl;
+  // control blocks: output of the latest evaluation, and the two states
+  // (integral or previous output; previous input)
+  std::vector<T> cy, cs0, cs1;
 
   bool init(const T* br_value, const T* src_amp, bool monolithic) {
     n_nodes = (int)net->n_nodes;
@@ -273,6 +292,9 @@ struct Sim {
     rs_on.assign(net->n_rs, 0);
     for (int64_t w = 0; w < net->n_rs; ++w) rs_on[w] = net->rs_on0[w] ? 1 : 0;
     rs_i.assign(net->n_rs, 0.0);
+    cy.assign(net->n_cb, T(0.0));
+    cs0.assign(net->n_cb, T(0.0));
+    cs1.assign(net->n_cb, T(0.0));
     cl.assign(net->n_cl, CLine{});
     for (int64_t l = 0; l < net->n_cl; ++l) {
       CLine& L = cl[l];
@@ -313,6 +335,47 @@ struct Sim {
         if (n >= net->rs_trip[w] && rs_i[w] * i <= 0.0) rs_on[w] = 0;
         rs_i[w] = i;
       }
+    }
+  }
+
+  // Control blocks at step n, in index order over one array: an input of
+  // lower index has already been overwritten with its step-n output, one of
+  // equal or higher index still holds step n-1's.
+  void evaluate_controls() {
+    const double dt = net->dt;
+    for (int64_t b = 0; b < net->n_cb; ++b) {
+      const double p0 = net->cb_p0[b], p1 = net->cb_p1[b];
+      const T u0 = net->cb_in0[b] >= 0 ? cy[net->cb_in0[b]] : T(0.0);
+      const T u1 = net->cb_in1[b] >= 0 ? cy[net->cb_in1[b]] : T(0.0);
+      T y;
+      switch (net->cb_type[b]) {
+        case 0: y = T(p0); break;
+        case 1: y = v[net->cb_node[b]]; break;
+        case 2: y = T(p0) * u0; break;
+        case 3: y = T(p0) * u0 + T(p1) * u1; break;
+        case 4: y = T(p0) * u0 * u1; break;
+        case 5: y = re(u0) < p0 ? T(p0) : (re(u0) > p1 ? T(p1) : u0); break;
+        case 6:
+          y = cs0[b] + T(p0 * (dt / 2.0)) * (u0 + cs1[b]);
+          cs0[b] = y;
+          cs1[b] = u0;
+          break;
+        case 7: {
+          const double a = (2.0 * p1 - dt) / (2.0 * p1 + dt), bb = p0 * dt / (2.0 * p1 + dt);
+          y = T(a) * cs0[b] + T(bb) * (u0 + cs1[b]);
+          cs0[b] = y;
+          cs1[b] = u0;
+          break;
+        }
+        default: {   // 8: PI
+          const T integral = cs0[b] + T(dt / 2.0) * (u0 + cs1[b]);
+          y = T(p0) * u0 + T(p1) * integral;
+          cs0[b] = integral;
+          cs1[b] = u0;
+          break;
+        }
+      }
+      cy[b] = y;
     }
   }
 
@@ -393,6 +456,7 @@ struct Sim {
         if (m >= 0) rhs[m] += h[b];
       }
     }
+    for (int64_t c = 0; c < net->n_ci; ++c) rhs[net->ci_node[c]] += cy[net->ci_block[c]];   // y(n-1)
     for (int64_t l = 0; l < net->n_ln; ++l) {
       int64_t d1 = net->ln_d[l] + 1;
       rhs[net->ln_k[l]] -= ring_k[l][n % d1];
@@ -450,6 +514,7 @@ struct Sim {
         }
       }
     }
+    evaluate_controls();
     decide_runtime_switches(n);
     return true;
   }
@@ -524,7 +589,7 @@ extern "C" int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_
 // and finally dg/dR = -1/R^2, dg/dL = -dt/(2L^2), dg/dC = 2/dt.
 extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad,
                            double* loss) {
-  if (!valid(net) || !v_target || !grad || n_steps < 0) return -1;
+  if (!valid(net) || !v_target || !grad || n_steps < 0 || net->n_cb > 0) return -1;
   const int64_t nn = net->n_nodes, nb = net->n_br, ns = net->n_src, nl = net->n_ln, nr = net->n_rs;
   Sim<double> sim;
   sim.net = net;
@@ -660,6 +725,18 @@ extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_
     grad[b] = dg[b] * dgdp;
   }
   for (int64_t s = 0; s < ns; ++s) grad[nb + s] = dA[s];
+  return 0;
+}
+
+extern "C" int orc_controls(const orc_net* net, int64_t n_steps, double* y_out) {
+  if (!valid(net) || n_steps < 0 || (n_steps > 0 && net->n_cb > 0 && !y_out)) return -1;
+  Sim<double> sim;
+  sim.net = net;
+  sim.init(net->br_val, net->src_amp, false);
+  for (int64_t n = 1; n <= n_steps; ++n) {
+    if (!sim.step(n)) return -2;
+    for (int64_t b = 0; b < net->n_cb; ++b) y_out[(size_t)(n - 1) * net->n_cb + b] = sim.cy[b];
+  }
   return 0;
 }
 

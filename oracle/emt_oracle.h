@@ -76,6 +76,32 @@ typedef struct {
   const double* cl_tv;
   const double* cl_z;
   const double* cl_tau;
+  /* Control system (Sec. III-A: each control component is one basic process
+   * of the computation graph).  Block b has one output y_b, inputs
+   * cb_in0[b], cb_in1[b] (block indices, -1 = unused) and parameters p0, p1:
+   *   0 CONST  y = p0                 5 LIMIT  y = min(max(u0, p0), p1)
+   *   1 MEAS   y = v(cb_node[b])      6 INTEG  y = y(n-1) + p0 (dt/2)(u0 + u0(n-1))
+   *   2 GAIN   y = p0 u0              7 LAG    p0 / (1 + s p1), trapezoidal:
+   *   3 SUM    y = p0 u0 + p1 u1               y = a y(n-1) + b (u0 + u0(n-1)),
+   *   4 MUL    y = p0 u0 u1                    a = (2 p1 - dt) / (2 p1 + dt),
+   *   8 PI     y = p0 u0 + p1 I,               b = p0 dt / (2 p1 + dt)
+   *            I = I(n-1) + (dt/2)(u0 + u0(n-1))
+   * (states start at 0).  At step n, after the node voltages v(n) are
+   * solved, the blocks are evaluated in index order: an input from a block
+   * of lower index reads that block's step-n output, an input from a block
+   * of equal or higher index its step-(n-1) output (0 at n = 1) -- this is
+   * how algebraic loops are broken.  Controlled current injection c:
+   * y_{ci_block[c]}(n) enters node ci_node[c] at step n + 1. */
+  int64_t n_cb;
+  const uint8_t* cb_type;
+  const int32_t* cb_in0;
+  const int32_t* cb_in1;
+  const int32_t* cb_node;
+  const double* cb_p0;
+  const double* cb_p1;
+  int64_t n_ci;
+  const int32_t* ci_block;
+  const int32_t* ci_node;
 } orc_net;
 
 /* Run n_steps steps from the de-energised state.
@@ -106,8 +132,12 @@ int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_target, int
  * With runtime switches the reverse sweep uses the states the forward run
  * decided (the gradient of the smooth piece the run lies on).  The
  * parameters of coupled lines themselves (Z, T_v, travel times) are not
- * differentiated. */
+ * differentiated.  Networks with control blocks are rejected (-1). */
 int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad, double* loss);
+
+/* Control block outputs of steps 1..n_steps: y_out[(n-1) n_cb + b]
+ * (partitioned mode; node voltages as orc_run). */
+int orc_controls(const orc_net* net, int64_t n_steps, double* y_out);
 
 /* Subsystem of each unknown node (components over branches and switches). */
 int orc_partition(const orc_net* net, int32_t* sub_of_node, int64_t* n_sub);

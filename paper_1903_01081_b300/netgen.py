@@ -81,6 +81,18 @@ class Network:
     cl_tv: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
     cl_z: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
     cl_tau: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    # control blocks (CB_* types), evaluated after each step's solve; an input
+    # of lower index reads its step-n output, of equal or higher index its
+    # step-(n-1) output.  Controlled current injections: block output y(n)
+    # enters node ci_node at step n + 1.
+    cb_type: np.ndarray = field(default_factory=lambda: np.zeros(0, np.uint8))
+    cb_in0: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    cb_in1: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    cb_node: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    cb_p0: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    cb_p1: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    ci_block: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    ci_node: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
     n_steps: int = 0            # suggested run length
     meta: dict = field(default_factory=dict)
 
@@ -107,6 +119,14 @@ class Network:
     @property
     def n_coupled_lines(self) -> int:
         return int(self.cl_z.shape[0]) // 3
+
+    @property
+    def n_control_blocks(self) -> int:
+        return int(self.cb_type.shape[0])
+
+    @property
+    def n_control_injections(self) -> int:
+        return int(self.ci_block.shape[0])
 
     def copy(self) -> "Network":
         kw = {}
@@ -228,6 +248,8 @@ class NetworkBuilder:
         self.sw = []     # (k, m, r, close, open)
         self.rs = []     # (k, m, kind, r_on, r_off, on0, trip)
         self.cl = []     # (k3, m3, tv9, z3, tau3)
+        self.cb = []     # (type, in0, in1, node, p0, p1)
+        self.ci = []     # (block, node)
 
     def branch(self, k, m, kind, value):
         self.br.append((int(k), int(m), int(kind), float(value)))
@@ -255,6 +277,15 @@ class NetworkBuilder:
         self.cl.append(([int(x) for x in k3], [int(x) for x in m3], np.asarray(tv, np.float64).reshape(9),
                         np.asarray(z3, np.float64).reshape(3), np.asarray(tau3, np.float64).reshape(3)))
 
+    def block(self, kind, in0=-1, in1=-1, node=-1, p0=0.0, p1=0.0):
+        """Control block of type ``kind`` (CB_*); returns its index."""
+        self.cb.append((int(kind), int(in0), int(in1), int(node), float(p0), float(p1)))
+        return len(self.cb) - 1
+
+    def injection(self, block, node):
+        """Controlled current: block output y(n) enters ``node`` at step n + 1."""
+        self.ci.append((int(block), int(node)))
+
     def build(self, dt, n_nodes, n_steps=0, meta=None) -> Network:
         def col(lst, i, dt_):
             return np.ascontiguousarray(np.array([x[i] for x in lst], dtype=dt_))
@@ -277,6 +308,9 @@ class NetworkBuilder:
             cl_tv=np.ascontiguousarray(np.concatenate([c[2] for c in self.cl]) if self.cl else np.zeros(0)),
             cl_z=np.ascontiguousarray(np.concatenate([c[3] for c in self.cl]) if self.cl else np.zeros(0)),
             cl_tau=np.ascontiguousarray(np.concatenate([c[4] for c in self.cl]) if self.cl else np.zeros(0)),
+            cb_type=col(self.cb, 0, np.uint8), cb_in0=col(self.cb, 1, np.int32), cb_in1=col(self.cb, 2, np.int32),
+            cb_node=col(self.cb, 3, np.int32), cb_p0=col(self.cb, 4, np.float64), cb_p1=col(self.cb, 5, np.float64),
+            ci_block=col(self.ci, 0, np.int32), ci_node=col(self.ci, 1, np.int32),
             n_steps=int(n_steps), meta=dict(meta or {}))
 
 
@@ -637,6 +671,73 @@ def with_rectifier_loads(base: Network, seed: int = 1006, n_rectifiers: int = 30
     net.rs_on0 = np.asarray(rs["on0"], np.uint8)
     net.rs_trip = np.asarray(rs["trip"], np.int64)
     net.meta = dict(net.meta, runtime_switches={"seed": seed, "rectifiers": n_rectifiers, "breakers": n_breakers})
+    return net
+
+
+# control block types (see Network.cb_*)
+CB_CONST, CB_MEAS, CB_GAIN, CB_SUM, CB_MUL, CB_LIMIT, CB_INTEG, CB_LAG, CB_PI = range(9)
+
+
+def add_converter_control(b: NetworkBuilder, phase_nodes, i_ref: float, t_filter: float,
+                          kp: float = 0.05, ki: float = 5.0, m_max: float = 100.0, i_max: float = 40.0) -> int:
+    """A three-phase converter drawing a regulated power, as 24 control
+    blocks and three controlled current injections; returns its first block.
+    Per phase p: u_p = v_p / V_PEAK; drawn power P = sum u_p c_p with the
+    converter's own currents c_p of the previous step (the loop closes
+    through blocks of higher index); m = limit(PI(1.5 i_ref - P), 0, m_max);
+    c_p = lag(limit(m u_p, -i_max, i_max), t_filter), and -c_p is injected
+    into the phase node, so the injected currents stay within i_max."""
+    c0 = len(b.cb)
+    meas = [b.block(CB_MEAS, node=x) for x in phase_nodes]
+    u = [b.block(CB_GAIN, m, p0=1.0 / V_PEAK) for m in meas]
+    out0 = c0 + 21                                  # first output block (lags, below)
+    pw = [b.block(CB_MUL, u[p], out0 + p, p0=-1.0) for p in range(3)]
+    s01 = b.block(CB_SUM, pw[0], pw[1], p0=1.0, p1=1.0)
+    ptot = b.block(CB_SUM, s01, pw[2], p0=1.0, p1=1.0)
+    ref = b.block(CB_CONST, p0=1.5 * i_ref)
+    err = b.block(CB_SUM, ref, ptot, p0=1.0, p1=-1.0)
+    m = b.block(CB_PI, err, p0=kp, p1=ki)
+    mlim = b.block(CB_LIMIT, m, p0=0.0, p1=m_max)
+    iraw = [b.block(CB_MUL, mlim, u[p], p0=1.0) for p in range(3)]
+    iref = [b.block(CB_LIMIT, iraw[p], p0=-i_max, p1=i_max) for p in range(3)]
+    outs = [b.block(CB_LAG, iref[p], p0=-1.0, p1=t_filter) for p in range(3)]
+    assert outs[0] == out0
+    for p in range(3):
+        b.injection(outs[p], phase_nodes[p])
+    return c0
+
+
+def with_converter_controls(base: Network, seed: int = 1008, n_converters: int = 180,
+                            r_damp: float = 20.0) -> Network:
+    """``base`` (a three-phase network with ``meta['bus_nodes']``) plus
+    ``n_converters`` power-regulated loads (``add_converter_control``) at distinct
+    buses (the source buses, then random ones), i_ref ~ U[5, 20] A, current filter ~ U[0.5, 2] ms, and a damping
+    resistor ``r_damp`` from each of their phase nodes to ground.  The block
+    count per node is about that of the paper's largest PV case (990 PV
+    units with their controls on 16,653 nodes); the PV models themselves are
+    not available, so this synthetic control stands in for them."""
+    rng = np.random.default_rng(seed)
+    buses = base.meta["bus_nodes"]
+    # the source buses first (stiff, near 1 p.u.: the power loop regulates),
+    # then random others (weak: the loop mostly runs into its limits)
+    first = list(dict.fromkeys(int(x) for x in base.meta.get("source_bus", [])))[:n_converters]
+    rest = [x for x in rng.permutation(len(buses)).tolist() if x not in set(first)]
+    picks = first + rest[:max(0, min(n_converters, len(buses)) - len(first))]
+    b = NetworkBuilder()
+    damp = []
+    for bus in picks:
+        add_converter_control(b, buses[int(bus)], float(rng.uniform(5.0, 20.0)), float(rng.uniform(0.5e-3, 2e-3)))
+        damp += list(buses[int(bus)])
+    net = base.copy()
+    ctl = b.build(base.dt, 0)
+    for f in ("cb_type", "cb_in0", "cb_in1", "cb_node", "cb_p0", "cb_p1", "ci_block", "ci_node"):
+        setattr(net, f, getattr(ctl, f))
+    # the converter's output filter: a damping resistor per phase to ground
+    net.br_k = np.concatenate([net.br_k, np.asarray(damp, np.int32)])
+    net.br_m = np.concatenate([net.br_m, np.full(len(damp), GROUND, np.int32)])
+    net.br_kind = np.concatenate([net.br_kind, np.full(len(damp), KIND_R, np.uint8)])
+    net.br_value = np.concatenate([net.br_value, np.full(len(damp), r_damp, np.float64)])
+    net.meta = dict(net.meta, controls={"seed": seed, "converters": len(picks), "blocks": ctl.n_control_blocks})
     return net
 
 
