@@ -364,6 +364,23 @@ def coupled_line_leg(steps=None, reps=3):
                        "all nodes recorded", steps, reps)
 
 
+def control_leg(steps=None, reps=3):
+    """The large-scale network with 180 power-regulated converter loads, each
+    24 layered control blocks driving three controlled current injections."""
+    import oracle
+    from paper_1903_01081_b300 import netgen as g
+
+    def blocks(net, n):
+        y = oracle.controls(net, n)
+        return {"control_blocks": int(net.n_control_blocks), "control_injections": int(net.n_control_injections),
+                "max_abs_injected_current_in_checked_steps": float(np.max(np.abs(y[:, 21::24])))}
+    return variant_leg(g.with_converter_controls(g.large_scale()),
+                       "large-scale network plus 180 converter loads (the 50 source buses, then random buses): "
+                       "24 control blocks each in 11 layers (measure, per-unit, power, PI, limits, lag), drawing "
+                       "a regulated power through controlled current injections, a 20 ohm damping resistor per "
+                       "phase; all nodes recorded", steps, reps, blocks)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -504,7 +521,7 @@ def run_ours(args):
             "clocks": clocks.summary(),
             "parity_rel_err_first_2000_steps": parity,
             **({"scenarios": scenario_legs(), "adjoint": adjoint_leg(), "runtime_switches": runtime_switch_leg(),
-                "coupled_lines": coupled_line_leg()} if args.leg == "all" else {}),
+                "coupled_lines": coupled_line_leg(), "controls": control_leg()} if args.leg == "all" else {}),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -521,7 +538,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--time-steps", type=int, default=N_STEPS)
     ap.add_argument("--skip-extras", action="store_true")
-    ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines"],
+    ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines",
+                                      "controls"],
                     default="all",
                     help="all: the JSON line with every leg; single: the single-network leg only; "
                          "n1 / shared_g / adjoint: that leg alone (profiling)")
@@ -534,7 +552,7 @@ def main():
         return run_rank_selftest()
     if args.impl == "reference":
         return run_reference(args)
-    if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines"):
+    if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "controls"):
         return run_leg(args)
     return run_ours(args)
 
@@ -549,6 +567,8 @@ def run_leg(args):
         out = runtime_switch_leg(args.leg_steps, reps=1)
     elif args.leg == "coupled_lines":
         out = coupled_line_leg(args.leg_steps, reps=1)
+    elif args.leg == "controls":
+        out = control_leg(args.leg_steps, reps=1)
     else:
         shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
         out = scenario_legs((args.leg,), args.leg_steps, shape, args.leg_warm)

@@ -80,7 +80,30 @@ typedef struct emt_ctx emt_ctx;  /* opaque; owns all device memory it allocates 
  *   (linear interpolation of the travel time).  An end's three phase nodes
  *   are one subsystem.  Not supported with a scenario set; emt_adjoint
  *   differentiates through them (their own Z, T_v and travel times are not
- *   parameters). */
+ *   parameters).
+ * Control system (n_cblocks may be 0): the paper's control components as
+ *   basic processes of its computation graph (Sec. III-A), layered into a
+ *   directed acyclic graph whose layers run one after another (Sec. III-B).
+ *   Block b: type cb_type[b], inputs cb_in0[b], cb_in1[b] (block indices;
+ *   -1 where the type has no such input), parameters cb_p0[b], cb_p1[b]
+ *   (finite), u0 / u1 its input values:
+ *     0 CONST  y = p0                 5 LIMIT  y = min(max(u0, p0), p1), p0 <= p1
+ *     1 MEAS   y = v(cb_node[b])      6 INTEG  y = y(n-1) + p0 (dt/2)(u0 + u0(n-1))
+ *     2 GAIN   y = p0 u0              7 LAG    p0 / (1 + s p1), p1 > 0, trapezoidal:
+ *     3 SUM    y = p0 u0 + p1 u1               y = a y(n-1) + b (u0 + u0(n-1)),
+ *     4 MUL    y = p0 u0 u1                    a = (2 p1 - dt)/(2 p1 + dt),
+ *     8 PI     y = p0 u0 + p1 I,               b = p0 dt / (2 p1 + dt)
+ *              I = I(n-1) + (dt/2)(u0 + u0(n-1))
+ *   (MEAS: cb_node an unknown node; states start at 0).  At step n, after
+ *   v(n) is solved, the blocks act in index order: an input from a block of
+ *   lower index sees its step-n output, one from a block of equal or higher
+ *   index its step-(n-1) output (0 at step 1); that is how algebraic loops
+ *   are broken.  Controlled current injections (n_cinj may be 0): the
+ *   output of block ci_block[c] at step n enters unknown node ci_node[c]
+ *   at step n + 1 (0 at step 1).  Every connected group of blocks, with the
+ *   nodes it measures and drives, lies in one subsystem (a block group that
+ *   touches no node runs in subsystem 0).  Not supported with a scenario
+ *   set or by emt_adjoint. */
 typedef struct {
   double dt;
   int64_t n_nodes;
@@ -118,6 +141,16 @@ typedef struct {
   const double* cl_tv;
   const double* cl_z;
   const double* cl_tau;
+  int64_t n_cblocks;
+  const uint8_t* cb_type;
+  const int32_t* cb_in0;
+  const int32_t* cb_in1;
+  const int32_t* cb_node;
+  const double* cb_p0;
+  const double* cb_p1;
+  int64_t n_cinj;
+  const int32_t* ci_block;
+  const int32_t* ci_node;
 } emt_network_desc;
 
 /* Optional per-scenario overrides of one base network (the paper's
@@ -210,6 +243,12 @@ emt_status emt_step_n(emt_ctx* ctx, int64_t n_steps, void* cuda_stream);
 emt_status emt_read_waveforms(emt_ctx* ctx, const int32_t* channels, int64_t n_ch, int64_t step0, int64_t n_rows,
                               int64_t scen0, int64_t n_scen, double* out, int32_t out_on_device);
 
+/* Control block outputs of the last completed step (all 0 at step 0):
+ * y[b] for b = 0 .. n_cblocks-1 in the caller's block order; n must equal
+ * n_cblocks.  y is device memory if on_device != 0 else host memory.
+ * Synchronous. */
+emt_status emt_read_controls(emt_ctx* ctx, double* y, int64_t n, int32_t on_device);
+
 /* Pick the launch shape of the multi-scenario kernel by measurement: for
  * scenarios per CTA S_t (about k CTAs per SM for k = 1..6, and the powers
  * of two up to 32, where the subsystem groups fit in shared memory) and
@@ -246,7 +285,7 @@ emt_status emt_autotune(emt_ctx* ctx, int64_t trial_steps, void* cuda_stream);
  * decided (the forward re-runs record them per step), i.e. the gradient of
  * the smooth piece of J the run lies on.  Coupled lines' own Z, T_v and
  * travel times are not parameters.  Requires emt_prefactor; a context built
- * with a scenario set returns EINVAL.  Resets the context to step 0 before and after (the recording
+ * with a scenario set, or with control blocks, returns EINVAL.  Resets the context to step 0 before and after (the recording
  * buffer is not written).  Allocates its work buffers (about 8 N n_nodes
  * bytes for a host v_target, N/K checkpoints, the tape) and frees them
  * before returning.  Synchronous.  ETIMEOUT as for emt_step_n. */
@@ -276,7 +315,9 @@ emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
  * "threads_per_cta", "kernel_launches", "n_nodes", "n_branches", "n_sources", "n_line_ends",
  * "smem_bytes" (dynamic shared memory per CTA of the persistent kernel),
  * "n_strong_branches" (L/C branches applied through extra solve columns),
- * "n_runtime_switches", "n_coupled_lines",
+ * "n_runtime_switches", "n_coupled_lines", "n_control_blocks",
+ * "n_control_injections", "max_control_layers" (largest layer count of one
+ * subsystem's control graph),
  * "n_matrix_variants", "scenarios_per_cta", "batch_threads", "batch_groups"
  * (subsystem groups per step of the multi-scenario kernel),
  * "graph_launches", "autotuned". */

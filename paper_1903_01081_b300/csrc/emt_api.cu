@@ -64,8 +64,13 @@ struct emt_ctx {
   std::vector<RuntimeSwitchDev> rswitches;             // runtime switches, grouped by subsystem
   std::vector<CoupledEndDev> cends;                    // coupled line ends, grouped by subsystem
   std::vector<int32_t> rs_word0;                       // per subsystem: state word at step 1
+  std::vector<CtrlDev> cblocks;                        // control blocks, grouped by subsystem, by layer
+  std::vector<int32_t> clay, cinj;                     // layer starts; block slot per control injection
+  std::vector<int32_t> cb_slot_of;                     // caller's block index -> subsystem-local slot
+  std::vector<int32_t> cb_sub_of;                      // caller's block index -> subsystem
+  int max_clayers = 0;
   int64_t ring_len = 0, ginv_len = 0, n_lc_total = 0;
-  FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0};
+  FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0};
 
   // device arrays
   SubDev* d_sub = nullptr;
@@ -98,6 +103,11 @@ struct emt_ctx {
   double* d_le_prev = nullptr;
   int32_t* d_rs_word = nullptr;
   double* d_rs_prev_i = nullptr;
+  CtrlDev* d_cb = nullptr;
+  int32_t* d_clay = nullptr;
+  int32_t* d_cinj = nullptr;
+  double* d_cstate = nullptr;
+  double* d_cy = nullptr;
   double* d_ginv = nullptr;
   float* d_ginv_lo = nullptr;
   int32_t* d_err = nullptr;
@@ -289,6 +299,27 @@ std::string validate(const emt_network_desc* d) {
     if (!finite_pos(d->rs_ron[w]) || !finite_pos(d->rs_roff[w]))
       return "runtime switch " + std::to_string(w) + ": resistances must be finite and > 0";
   }
+  if (d->n_cblocks < 0 || d->n_cinj < 0) return "negative count";
+  if (d->n_cblocks && (!d->cb_type || !d->cb_in0 || !d->cb_in1 || !d->cb_node || !d->cb_p0 || !d->cb_p1))
+    return "control block array is NULL";
+  if (d->n_cinj && (!d->ci_block || !d->ci_node)) return "control injection array is NULL";
+  if (d->n_cblocks > (1 << 24)) return "too many control blocks";
+  for (int64_t b = 0; b < d->n_cblocks; ++b) {
+    const std::string nm = "control block " + std::to_string(b);
+    const int t = d->cb_type[b];
+    if (t > 8) return nm + ": type must be 0..8";
+    if (!std::isfinite(d->cb_p0[b]) || !std::isfinite(d->cb_p1[b])) return nm + ": non-finite parameter";
+    const int n_in = t <= 1 ? 0 : (t == 3 || t == 4) ? 2 : 1;
+    const int32_t in[2] = {d->cb_in0[b], d->cb_in1[b]};
+    for (int i = 0; i < n_in; ++i)
+      if (in[i] < 0 || in[i] >= d->n_cblocks) return nm + ": input " + std::to_string(i) + " is not a block";
+    if (t == 1 && (d->cb_node[b] < 0 || d->cb_node[b] >= d->n_nodes)) return nm + ": measured node must be unknown";
+    if (t == 5 && !(d->cb_p0[b] <= d->cb_p1[b])) return nm + ": limits need p0 <= p1";
+    if (t == 7 && !(d->cb_p1[b] > 0.0)) return nm + ": lag time constant must be > 0";
+  }
+  for (int64_t x = 0; x < d->n_cinj; ++x)
+    if (d->ci_block[x] < 0 || d->ci_block[x] >= d->n_cblocks || d->ci_node[x] < 0 || d->ci_node[x] >= d->n_nodes)
+      return "control injection " + std::to_string(x) + ": needs a block and an unknown node";
   if (d->n_switches && (!d->sw_k || !d->sw_m || !d->sw_r || !d->sw_close_step || !d->sw_open_step))
     return "switch array is NULL";
   for (int64_t w = 0; w < d->n_switches; ++w) {
@@ -966,12 +997,110 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     c->lim.nc = std::max(c->lim.nc, sd.n + sd.n_str);
   }
 
+  // -------- control blocks (Sec. III-A/B: control components as basic
+  // processes, layered).  Each connected group of blocks runs in the
+  // subsystem of the nodes it measures and drives; within a subsystem a
+  // block's layer is one more than the deepest block it reads at the same
+  // step (inputs of lower index), and the CTA evaluates layer after layer.
+  std::vector<std::vector<int32_t>> ci_nodes_of(S);   // local node per control injection, by subsystem
+  {
+    const int64_t NB = d->n_cblocks;
+    auto n_inputs = [&](int64_t b) { const int t = d->cb_type[b]; return t <= 1 ? 0 : (t == 3 || t == 4) ? 2 : 1; };
+    auto input = [&](int64_t b, int i) { return i == 0 ? d->cb_in0[b] : d->cb_in1[b]; };
+    std::vector<int> grp(NB);
+    std::iota(grp.begin(), grp.end(), 0);
+    for (int64_t b = 0; b < NB; ++b)
+      for (int i = 0; i < n_inputs(b); ++i) {
+        const int x = uf_find(grp, (int)b), y = uf_find(grp, input(b, i));
+        if (x != y) grp[std::max(x, y)] = std::min(x, y);
+      }
+    std::vector<int> gsub(NB, -1);
+    auto claim = [&](int64_t b, int32_t node) -> bool {
+      const int r = uf_find(grp, (int)b), sn = c->sub_of_node[node];
+      if (gsub[r] >= 0 && gsub[r] != sn) return false;
+      gsub[r] = sn;
+      return true;
+    };
+    for (int64_t b = 0; b < NB; ++b)
+      if (d->cb_type[b] == 1 && !claim(b, d->cb_node[b]))
+        return bail("control block " + std::to_string(b) + " belongs to a block group spanning two subsystems");
+    for (int64_t x = 0; x < d->n_cinj; ++x)
+      if (!claim(d->ci_block[x], d->ci_node[x]))
+        return bail("control injection " + std::to_string(x) + " drives a node outside its block group's subsystem");
+    c->cb_sub_of.assign(NB, 0);
+    c->cb_slot_of.assign(NB, -1);
+    std::vector<std::vector<int64_t>> cb_of(S);
+    for (int64_t b = 0; b < NB; ++b) {
+      const int r = uf_find(grp, (int)b);
+      c->cb_sub_of[b] = gsub[r] >= 0 ? gsub[r] : 0;
+      if (S > 0) cb_of[c->cb_sub_of[b]].push_back(b);   // increasing caller index
+    }
+    std::vector<int> layer(NB, 0);
+    for (int s = 0; s < S; ++s) {
+      SubDev& sd = c->subs[s];
+      int n_layers = 0;
+      for (int64_t b : cb_of[s]) {
+        for (int i = 0; i < n_inputs(b); ++i)
+          if (input(b, i) < b) layer[b] = std::max(layer[b], layer[input(b, i)] + 1);
+        n_layers = std::max(n_layers, layer[b] + 1);
+      }
+      std::vector<int64_t> order = cb_of[s];
+      std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return layer[a] < layer[b]; });
+      for (size_t j = 0; j < order.size(); ++j) c->cb_slot_of[order[j]] = (int32_t)j;
+      sd.cb_off = (int)c->cblocks.size();
+      sd.n_cb = (int)order.size();
+      sd.clay_off = (int)c->clay.size();
+      sd.n_clay = sd.n_cb > 0 ? n_layers : 0;
+      const double dt = d->dt;
+      for (size_t j = 0; j < order.size(); ++j) {
+        const int64_t b = order[j];
+        if (j == 0 || layer[b] != layer[order[j - 1]]) c->clay.push_back((int32_t)j);
+        CtrlDev r{};
+        r.type = d->cb_type[b];
+        r.in0 = r.in1 = -1;
+        for (int i = 0; i < n_inputs(b); ++i) {
+          (i == 0 ? r.in0 : r.in1) = c->cb_slot_of[input(b, i)];
+          if (input(b, i) >= b) r.late |= 1 << i;
+        }
+        r.node = r.type == 1 ? local[d->cb_node[b]] : -1;
+        const double p0 = d->cb_p0[b], p1 = d->cb_p1[b];
+        r.p0 = p0;
+        r.p1 = p1;
+        if (r.type == 6) r.p0 = p0 * (dt / 2.0);
+        if (r.type == 7) {
+          r.p0 = (2.0 * p1 - dt) / (2.0 * p1 + dt);
+          r.p1 = p0 * dt / (2.0 * p1 + dt);
+        }
+        if (r.type == 8) r.p2 = dt / 2.0;
+        c->cblocks.push_back(r);
+      }
+      if (sd.n_cb > 0) c->clay.push_back(sd.n_cb);
+      c->lim.cb = std::max(c->lim.cb, sd.n_cb);
+      c->lim.clay = std::max(c->lim.clay, sd.n_clay + 1);
+      c->max_clayers = std::max(c->max_clayers, sd.n_clay);
+    }
+    std::vector<std::vector<int32_t>> ci_of(S);
+    for (int64_t x = 0; x < d->n_cinj; ++x) ci_of[c->sub_of_node[d->ci_node[x]]].push_back((int32_t)x);
+    for (int s = 0; s < S; ++s) {
+      SubDev& sd = c->subs[s];
+      sd.ci_off = (int)c->cinj.size();
+      sd.n_ci = (int)ci_of[s].size();
+      for (int32_t x : ci_of[s]) {
+        c->cinj.push_back(c->cb_slot_of[d->ci_block[x]]);
+        ci_nodes_of[s].push_back(local[d->ci_node[x]]);
+      }
+      c->lim.ci = std::max(c->lim.ci, sd.n_ci);
+    }
+  }
+
   // -------- injection lanes (see kEntryNeg): 4 entries each, a node's
   // lanes consecutive and inside one warp; strong branches stay out
   for (int s = 0; s < S; ++s) {
     SubDev& sd = c->subs[s];
     std::vector<std::vector<int32_t>> el(sd.n);
     const int ie_base = sd.n_lc + sd.n_sb, zero = ie_base + 2 * (sd.n_le + 3 * sd.n_ce);
+    for (int x = 0; x < sd.n_ci; ++x)   // controlled currents enter their nodes
+      el[ci_nodes_of[s][x]].push_back((int32_t)(zero + 1 + x));
     for (int b = sd.br_off; b < sd.br_off + sd.n_br; ++b) {
       const BranchDev& x = c->branches[b];
       if (x.kind != 0 && !strong[b]) {
@@ -1128,6 +1257,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   // -------- multi-scenario set
   if (scen && !c->rswitches.empty()) return bail("runtime switches are not supported with a scenario set");
   if (scen && !c->cends.empty()) return bail("coupled lines are not supported with a scenario set");
+  if (scen && (d->n_cblocks > 0 || d->n_cinj > 0)) return bail("control blocks are not supported with a scenario set");
   if (scen) {
     const std::string bm = build_scenarios(c, d, scen, local, new_of_orig, le_of_end, lc_slot_of, sb_slot_of);
     if (!bm.empty()) return bail(bm);
@@ -1155,6 +1285,9 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   UP(d_rs, rswitches)
   UP(d_ce, cends)
   UP(d_rs_word, rs_word0)
+  UP(d_cb, cblocks)
+  UP(d_clay, clay)
+  UP(d_cinj, cinj)
   UP(d_br_orig, br_orig)
   UP(d_br_lc, br_lc)
   UP(d_br_src, br_src)
@@ -1167,6 +1300,8 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ginv_lo, (size_t)c->ginv_len);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_err, 4);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_rs_prev_i, c->rswitches.size());
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_cstate, 2 * c->cblocks.size());
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_cy, c->cblocks.size());
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_le_prev, c->line_ends.size());
   if (c->batched) {
     UP(d_col_code, b_col_code)
@@ -1458,6 +1593,11 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
   p.rs = c->d_rs;
   p.rs_word = c->d_rs_word;
   p.rs_prev_i = c->d_rs_prev_i;
+  p.cb = c->d_cb;
+  p.clay = c->d_clay;
+  p.cinj = c->d_cinj;
+  p.cstate = c->d_cstate;
+  p.cy = c->d_cy;
   for (int64_t done = 0; done < n_steps; done += chunk) {
     const int64_t len = std::min(chunk, n_steps - done);
     SourceParams sp{};
@@ -1572,6 +1712,27 @@ extern "C" emt_status emt_read_waveforms(emt_ctx* c, const int32_t* channels, in
   return EMT_OK;
 }
 
+extern "C" emt_status emt_read_controls(emt_ctx* c, double* y, int64_t n, int32_t on_device) {
+  if (!c) return EMT_EINVAL;
+  if (n != (int64_t)c->cb_slot_of.size())
+    return c->fail(EMT_EINVAL, "emt_read_controls: n must equal the number of control blocks");
+  if (n == 0) return EMT_OK;
+  if (!y) return c->fail(EMT_EINVAL, "NULL buffer");
+  const emt_status st = emt_sync(c, nullptr);
+  if (st != EMT_OK) return st;
+  std::vector<double> dev(c->cblocks.size()), out(n);
+  cudaError_t e = cudaMemcpy(dev.data(), c->d_cy, dev.size() * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_read_controls");
+  for (int64_t b = 0; b < n; ++b) out[b] = dev[c->subs[c->cb_sub_of[b]].cb_off + c->cb_slot_of[b]];
+  if (on_device) {
+    e = cudaMemcpy(y, out.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return c->cuda_fail(e, "emt_read_controls");
+  } else {
+    std::copy(out.begin(), out.end(), y);
+  }
+  return EMT_OK;
+}
+
 extern "C" emt_status emt_reset(emt_ctx* c) {
   if (!c) return EMT_EINVAL;
   cudaError_t e = cudaDeviceSynchronize();
@@ -1586,6 +1747,8 @@ extern "C" emt_status emt_reset(emt_ctx* c) {
     e = cudaMemset(c->d_rs_prev_i, 0, c->rswitches.size() * sizeof(double));
   if (e == cudaSuccess && !c->line_ends.empty())
     e = cudaMemset(c->d_le_prev, 0, c->line_ends.size() * sizeof(double));
+  if (e == cudaSuccess && !c->cblocks.empty()) e = cudaMemset(c->d_cstate, 0, 2 * c->cblocks.size() * sizeof(double));
+  if (e == cudaSuccess && !c->cblocks.empty()) e = cudaMemset(c->d_cy, 0, c->cblocks.size() * sizeof(double));
   if (c->batched) {
     if (e == cudaSuccess) e = cudaMemset(c->d_bh, 0, std::max<size_t>((size_t)c->n_lc_total * c->S, 1) * sizeof(double));
     if (e == cudaSuccess)
@@ -1717,6 +1880,9 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "n_strong_branches") *value = (int64_t)c->str_slot.size();
   else if (k == "n_runtime_switches") *value = (int64_t)c->rswitches.size();
   else if (k == "n_coupled_lines") *value = (int64_t)c->cends.size() / 2;
+  else if (k == "n_control_blocks") *value = (int64_t)c->cblocks.size();
+  else if (k == "n_control_injections") *value = (int64_t)c->cinj.size();
+  else if (k == "max_control_layers") *value = c->max_clayers;
   else if (k == "smem_bytes") *value = (int64_t)forward_smem_bytes(c->lim);
   else return EMT_EINVAL;
   return EMT_OK;
@@ -1750,6 +1916,7 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
                                   double* grad, double* loss, int32_t on_device, void* stream) {
   if (!c) return EMT_EINVAL;
   if (c->batched) return c->fail(EMT_EINVAL, "emt_adjoint: a context built with a scenario set has no adjoint");
+  if (!c->cblocks.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: control blocks have no adjoint");
   if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
   if (n_steps < 1) return c->fail(EMT_EINVAL, "emt_adjoint: n_steps must be >= 1");
   if (n_steps > (int64_t)INT32_MAX - (int64_t)(1 << 21))

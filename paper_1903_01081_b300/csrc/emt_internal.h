@@ -17,7 +17,8 @@ constexpr int kFwdThreads = 256;
 // Injection entries (process 2).  Every node's injection is a signed sum of
 // entries of one shared-memory input vector
 //     inp = [ h (L/C slots) | g_b v_src (source-branch slots) |
-//             I_e parity 0 (line ends) | I_e parity 1 | 0 ]
+//             I_e parity 0 (line ends) | I_e parity 1 | 0 |
+//             controlled currents (one slot per control injection) ]
 // An entry is an int32: bit 31 = subtract, bits 0..30 = index into inp with
 // line ends addressed in their parity-0 block.  A node's entries are split
 // into "injection lanes" of 4 entries (padded with the trailing zero); the
@@ -98,6 +99,23 @@ struct SubDev {
   int32_t n_states;            // 2^(runtime switches): solve matrices per switch epoch
   int32_t rs_off, n_rs;        // runtime switches (RuntimeSwitchDev list)
   int32_t ce_off, n_ce;        // coupled line ends (CoupledEndDev list)
+  int32_t cb_off, n_cb;        // control blocks (CtrlDev list, by layer)
+  int32_t clay_off, n_clay;    // control layers: n_clay + 1 starts in clay (local block slots)
+  int32_t ci_off, n_ci;        // control injections: local block slot per injection in cinj
+};
+
+// A control block in device form (subsystem-local, ordered by layer).  Its
+// inputs are local block slots (-1: none); bit 0 / 1 of `late` marks input
+// 0 / 1 as read from the previous step's outputs (the loop-breaking rule).
+// Coefficients: GAIN p0; SUM p0, p1; MUL p0; LIMIT lo p0, hi p1; INTEG
+// p0 = k dt / 2; LAG p0 = a, p1 = b; PI kp p0, ki p1, p2 = dt / 2.
+struct CtrlDev {
+  int32_t type;        // 0 CONST .. 8 PI, as in the public header
+  int32_t in0, in1;    // local block slots, -1 unused
+  int32_t node;        // MEAS: local node
+  int32_t late;        // delayed-input bits
+  int32_t pad;
+  double p0, p1, p2;
 };
 
 // Maximum runtime switches per subsystem (2^k solve matrices each epoch).
@@ -139,6 +157,7 @@ struct FwdLimits {
   int32_t n, nc, q, lc, sb, le, src, il, str;
   int32_t nbuf;                // solve-matrix buffers in shared memory: 1, or 2 (the last two states kept)
   int32_t ce;                  // coupled line ends per subsystem
+  int32_t cb, clay, ci;        // control blocks, layers + 1 and injections per subsystem
 };
 
 struct FwdParams {
@@ -179,6 +198,11 @@ struct FwdParams {
   double* rs_prev_i;           // per runtime switch: breaker current of the previous step
   int32_t* word_tape;          // optional [rows][n_sub]: state word in force at step n (row n - 1 - word_row0)
   int64_t word_row0;
+  const CtrlDev* cb;           // control blocks (SubDev cb_off / n_cb)
+  const int32_t* clay;         // control layer starts (SubDev clay_off)
+  const int32_t* cinj;         // local block slot per control injection (SubDev ci_off / n_ci)
+  double* cstate;              // per control block: two states (s0, s1)
+  double* cy;                  // per control block: output of the last step (carried across launches)
 };
 
 struct PrefParams {

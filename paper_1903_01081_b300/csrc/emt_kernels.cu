@@ -316,10 +316,10 @@ constexpr int kItemThreads = kFwdThreads - 32;
 // rows are stored with an odd stride (n | 1) so that the rows a warp reads
 // together fall in different banks.
 struct FwdSmem {
-  size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar, lef, imode, ceti, cetinv;   // 8-byte
+  size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar, lef, imode, ceti, cetinv, cbr, cy, cs;   // 8-byte
   size_t gilo, ivf, partf;                                                                 // float
   size_t lck, lcm, lckind, lcstr, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, recp,
-      lece, lemode, cele0, cenode;                                                         // int
+      lece, lemode, cele0, cenode, clay, cinj;                                             // int
   size_t bytes;
 };
 
@@ -334,7 +334,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.part = d((size_t)L.n * L.q);
   s.iv = d(L.nc);
   s.vv = d(L.n);
-  s.inp = d((size_t)L.lc + L.sb + 2 * ((size_t)L.le + 3 * (size_t)L.ce) + 1);
+  s.inp = d((size_t)L.lc + L.sb + 2 * ((size_t)L.le + 3 * (size_t)L.ce) + 1 + (size_t)L.ci);
   s.vs = d(2 * (size_t)L.src);
   s.lce = d(L.lc);
   s.sbg = d(L.sb);
@@ -345,6 +345,9 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.imode = d(2 * (size_t)L.le);
   s.ceti = d(9 * (size_t)L.ce);
   s.cetinv = d(9 * (size_t)L.ce);
+  s.cbr = d(sizeof(CtrlDev) / 8 * (size_t)L.cb);
+  s.cy = d(2 * (size_t)L.cb);
+  s.cs = d(2 * (size_t)L.cb);
   s.gilo = w(nbuf * (size_t)L.n * ldg);
   s.ivf = w(L.nc);
   s.partf = w((size_t)L.n * L.q);
@@ -367,6 +370,8 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.lemode = w(L.le);
   s.cele0 = w(L.ce);
   s.cenode = w(3 * (size_t)L.ce);
+  s.clay = w(L.clay);
+  s.cinj = w(L.ci);
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
 }
@@ -388,6 +393,42 @@ __device__ void fold_modes(int lane, int n_le, int n_ce, const int* lece, const 
     blk_new[n_le + x] = fma(ti[0], im[0], fma(ti[1], im[1], ti[2] * im[2]));
   }
   __syncwarp();
+}
+
+// One control block at the current step (its layer's inputs are final):
+// an input marked late reads the previous step's outputs.  s = the block's
+// two states.
+__device__ __forceinline__ double control_block(const CtrlDev& r, const double* yprev, const double* ycur,
+                                                const double* vv, double* s) {
+  const double u0 = r.in0 >= 0 ? ((r.late & 1) ? yprev : ycur)[r.in0] : 0.0;
+  const double u1 = r.in1 >= 0 ? ((r.late & 2) ? yprev : ycur)[r.in1] : 0.0;
+  double y;
+  switch (r.type) {
+    case 0: y = r.p0; break;
+    case 1: y = vv[r.node]; break;
+    case 2: y = r.p0 * u0; break;
+    case 3: y = fma(r.p0, u0, r.p1 * u1); break;
+    case 4: y = r.p0 * u0 * u1; break;
+    case 5: y = u0 < r.p0 ? r.p0 : (u0 > r.p1 ? r.p1 : u0); break;
+    case 6:   // trapezoidal integral
+      y = fma(r.p0, u0 + s[1], s[0]);
+      s[0] = y;
+      s[1] = u0;
+      break;
+    case 7:   // first-order lag, Tustin
+      y = fma(r.p0, s[0], r.p1 * (u0 + s[1]));
+      s[0] = y;
+      s[1] = u0;
+      break;
+    default: {   // PI: proportional + trapezoidal integral
+      const double integral = fma(r.p2, u0 + s[1], s[0]);
+      y = fma(r.p0, u0, r.p1 * integral);
+      s[0] = integral;
+      s[1] = u0;
+      break;
+    }
+  }
+  return y;
 }
 
 // One warp collects one step's line-end histories I_e(n) from the tagged
@@ -468,6 +509,11 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   int* lemode = reinterpret_cast<int*>(smem_raw + L.lemode);
   int* cele0 = reinterpret_cast<int*>(smem_raw + L.cele0);
   int* cenode = reinterpret_cast<int*>(smem_raw + L.cenode);
+  CtrlDev* cbr = reinterpret_cast<CtrlDev*>(smem_raw + L.cbr);      // control blocks, by layer
+  double* cy = reinterpret_cast<double*>(smem_raw + L.cy);          // [2][cb]: block outputs by step parity
+  double* cs = reinterpret_cast<double*>(smem_raw + L.cs);          // [cb][2]: block states
+  int* clay = reinterpret_cast<int*>(smem_raw + L.clay);            // layer starts
+  int* cinj = reinterpret_cast<int*>(smem_raw + L.cinj);            // block slot per control injection
 
   const int sidx = blockIdx.x;
   const SubDev S = P.sub[sidx];
@@ -478,6 +524,11 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   const int ie_base = n_lc + n_sb;
   const int blk_len = n_le + 3 * n_ce;   // per parity: line-end values, then coupled ends' phase currents
   const int zero_slot = ie_base + 2 * blk_len;
+  const int ci_base = zero_slot + 1;   // controlled currents
+  const int n_cb = S.n_cb, n_clay = S.n_clay, n_ci = S.n_ci, lcb = P.lim.cb;
+  // with control blocks the warp before the poll warp evaluates them in the
+  // update phase, layer by layer; the update items take the other warps
+  const int item_threads = n_cb > 0 ? kItemThreads - 32 : kItemThreads;
   const int lv = P.lim.le;
   const int src_vs = P.lim.src;
   const bool writes_lines = sidx != P.hold_sub;
@@ -527,6 +578,18 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       ceti[9 * c + k] = ce.ti[k];
       cetinv[9 * c + k] = ce.tinv[k];
     }
+  }
+  for (int x = tid; x < n_cb; x += T) {
+    cbr[x] = P.cb[S.cb_off + x];
+    cs[2 * x] = P.cstate[2 * (size_t)(S.cb_off + x)];
+    cs[2 * x + 1] = P.cstate[2 * (size_t)(S.cb_off + x) + 1];
+    cy[(int)((P.n0 - 1) & 1) * lcb + x] = P.cy[S.cb_off + x];
+  }
+  for (int x = tid; x < (n_cb > 0 ? n_clay + 1 : 0); x += T) clay[x] = P.clay[S.clay_off + x];
+  for (int x = tid; x < n_ci; x += T) {
+    const int b = P.cinj[S.ci_off + x];
+    cinj[x] = b;
+    inp[ci_base + x] = P.cy[S.cb_off + b];   // the last step's output drives this step
   }
   for (int r = tid; r < n; r += T) recp[r] = P.rec != nullptr ? P.rec_pos[S.node_off + r] : -1;
   for (int x = tid; x < 4 * n_il; x += T) ent[x] = P.ent[4 * (size_t)S.il_off + x];
@@ -708,6 +771,16 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
           fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + par * blk_len,
                      inp + ie_base + (par ^ 1) * blk_len, imode + (par ^ 1) * lv, cele0, ceti);
       }
+    } else if (n_cb > 0 && warp == kPollWarp - 1) {
+      // control blocks at this step, one layer after another; then the
+      // controlled currents of the next step
+      const double* yprev = cy + (par ^ 1) * lcb;
+      double* ycur = cy + par * lcb;
+      for (int l = 0; l < n_clay; ++l) {
+        for (int b = clay[l] + lane; b < clay[l + 1]; b += 32) ycur[b] = control_block(cbr[b], yprev, ycur, vv, cs + 2 * b);
+        __syncwarp();
+      }
+      for (int c = lane; c < n_ci; c += 32) inp[ci_base + c] = ycur[cinj[c]];
     } else {
       // runtime switches: the states in force at the next step (oracle rules)
       if (tid < n_rs) {
@@ -725,7 +798,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       }
       const double* ie_cur = inp + ie_base + parshift;
       const double* vs_next = vs + (par ^ 1) * src_vs;
-      for (int it = tid; it < it_end; it += kItemThreads) {
+      for (int it = tid; it < it_end; it += item_threads) {
         if (it < n_lc) {
           const int k = lck[it], m = lcm[it];
           const double vk = k >= 0 ? vv[k] : (k == -1 ? 0.0 : vsc[-2 - k]);
@@ -767,6 +840,11 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       for (int x = tid; x < n_le; x += T)
         P.le_prev[S.le_off + x] = inp[ie_base + (int)((n_end - 1) & 1) * blk_len + x];
     for (int x = tid; x < n_rs; x += T) P.rs_prev_i[S.rs_off + x] = s_rsi[x];
+    for (int x = tid; x < n_cb; x += T) {
+      P.cstate[2 * (size_t)(S.cb_off + x)] = cs[2 * x];
+      P.cstate[2 * (size_t)(S.cb_off + x) + 1] = cs[2 * x + 1];
+      P.cy[S.cb_off + x] = cy[(int)((n_end - 1) & 1) * lcb + x];
+    }
     if (n_rs > 0 && tid == 0) {
       int w = 0;
       for (int j = 0; j < n_rs; ++j) w |= s_rsbit[j] << j;

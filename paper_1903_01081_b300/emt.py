@@ -22,7 +22,7 @@ _STATUS = {0: "EMT_OK", 1: "EMT_EINVAL", 2: "EMT_ESINGULAR", 3: "EMT_ENOMEM", 4:
 # every function include/emt.h declares
 EXPORTS = ("emt_build_network", "emt_prefactor", "emt_set_recording", "emt_step_n", "emt_read_waveforms",
            "emt_reset", "emt_sync", "emt_set_option", "emt_get_info", "emt_get_node_order", "emt_last_error",
-           "emt_destroy", "emt_prefactor_noalloc", "emt_adjoint", "emt_autotune")
+           "emt_destroy", "emt_prefactor_noalloc", "emt_adjoint", "emt_autotune", "emt_read_controls")
 
 
 class EmtError(RuntimeError):
@@ -47,6 +47,10 @@ class _NetworkDesc(ctypes.Structure):
         ("rs_on0", ctypes.c_void_p), ("rs_trip_step", ctypes.c_void_p),
         ("n_clines", ctypes.c_int64), ("cl_k", ctypes.c_void_p), ("cl_m", ctypes.c_void_p),
         ("cl_tv", ctypes.c_void_p), ("cl_z", ctypes.c_void_p), ("cl_tau", ctypes.c_void_p),
+        ("n_cblocks", ctypes.c_int64), ("cb_type", ctypes.c_void_p), ("cb_in0", ctypes.c_void_p),
+        ("cb_in1", ctypes.c_void_p), ("cb_node", ctypes.c_void_p), ("cb_p0", ctypes.c_void_p),
+        ("cb_p1", ctypes.c_void_p),
+        ("n_cinj", ctypes.c_int64), ("ci_block", ctypes.c_void_p), ("ci_node", ctypes.c_void_p),
     ]
 
 
@@ -93,6 +97,7 @@ def load_library(build_if_needed: bool = True):
         "emt_get_node_order": [P, P],
         "emt_adjoint": [P, P, I64, I32, P, P, I32, P],
         "emt_autotune": [P, I64, P],
+        "emt_read_controls": [P, P, I64, I32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -165,6 +170,13 @@ def network_desc(net, keep: list) -> _NetworkDesc:
     d.cl_k, d.cl_m = p(rs("cl_k", np.int32), np.int32), p(rs("cl_m", np.int32), np.int32)
     d.cl_tv, d.cl_z = p(rs("cl_tv", np.float64), np.float64), p(rs("cl_z", np.float64), np.float64)
     d.cl_tau = p(rs("cl_tau", np.float64), np.float64)
+    d.n_cblocks = int(len(rs("cb_type", np.uint8)))
+    d.cb_type = p(rs("cb_type", np.uint8), np.uint8)
+    d.cb_in0, d.cb_in1 = p(rs("cb_in0", np.int32), np.int32), p(rs("cb_in1", np.int32), np.int32)
+    d.cb_node = p(rs("cb_node", np.int32), np.int32)
+    d.cb_p0, d.cb_p1 = p(rs("cb_p0", np.float64), np.float64), p(rs("cb_p1", np.float64), np.float64)
+    d.n_cinj = int(len(rs("ci_block", np.int32)))
+    d.ci_block, d.ci_node = p(rs("ci_block", np.int32), np.int32), p(rs("ci_node", np.int32), np.int32)
     return d
 
 
@@ -255,6 +267,29 @@ def emt_read_waveforms(ctx: Ctx, channels, step0: int, n_rows: int, scen0: int =
         return out
     _check(ctx, lib.emt_read_waveforms(ctx.handle, ch.ctypes.data, int(ch.size), int(step0), int(n_rows),
                                        int(scen0), int(n_scen), ptr, on_device))
+    return out
+
+
+def emt_read_controls(ctx: Ctx, out=None):
+    """Control block outputs of the last completed step, caller's block
+    order: a new numpy array, or written into ``out`` (numpy array or CUDA
+    float64 tensor of n_control_blocks entries)."""
+    lib = load_library()
+    n = emt_get_info(ctx, "n_control_blocks")
+    on_device = 0
+    if out is None:
+        out = np.zeros(n, dtype=np.float64)
+        ptr = out.ctypes.data if n else None
+    elif isinstance(out, np.ndarray):
+        if out.dtype != np.float64 or not out.flags.c_contiguous or out.size != n:
+            raise ValueError(f"out must be a C-contiguous float64 array of {n} entries")
+        ptr = out.ctypes.data if n else None
+    else:   # torch tensor
+        if not out.is_contiguous() or out.numel() != n or str(out.dtype) != "torch.float64":
+            raise ValueError(f"out must be a contiguous float64 tensor of {n} entries")
+        ptr = out.data_ptr() if n else None
+        on_device = 1 if out.is_cuda else 0
+    _check(ctx, lib.emt_read_controls(ctx.handle, ptr, int(n), on_device))
     return out
 
 
@@ -367,6 +402,10 @@ class Simulator:
             n_rows = emt_get_info(self.ctx, "step") // self.decim - (step0 // self.decim - 1)
         n_scen = self.ctx.n_scenarios if n_scen is None else n_scen
         return emt_read_waveforms(self.ctx, self.channels, step0, n_rows, scen0, n_scen, out)
+
+    def controls(self, out=None):
+        """Control block outputs of the last completed step."""
+        return emt_read_controls(self.ctx, out)
 
     def sync(self):
         return emt_sync(self.ctx)

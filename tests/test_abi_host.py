@@ -118,3 +118,34 @@ def test_rejects_scenario_set_with_runtime_switches_or_coupled_lines():
     assert cl.n_coupled_lines > 0
     with pytest.raises(emt.EmtError, match="coupled lines are not supported"):
         emt.emt_build_network(cl, sc)
+
+
+def test_rejects_bad_controls():
+    net = g.with_converter_controls(g.multi_subsystem(11, [4, 5, 3, 6], n_lines=5, n_sources=3, dt=20e-6),
+                                    n_converters=4)
+    t = net.cb_type.copy(); t[3] = 9
+    assert "type" in bad(net, cb_type=t)
+    i0 = net.cb_in0.copy(); i0[4] = net.n_control_blocks
+    assert "not a block" in bad(net, cb_in0=i0)
+    p1 = net.cb_p1.copy(); p1[21] = 0.0
+    assert "time constant" in bad(net, cb_p1=p1)
+    p0 = net.cb_p0.copy(); p0[14] = 1e9
+    assert "p0 <= p1" in bad(net, cb_p0=p0)
+    p0 = net.cb_p0.copy(); p0[3] = np.nan
+    assert "non-finite" in bad(net, cb_p0=p0)
+    nd = net.cb_node.copy(); nd[0] = net.n_nodes
+    assert "unknown" in bad(net, cb_node=nd)
+    cb = net.ci_block.copy(); cb[0] = -1
+    assert "needs a block" in bad(net, ci_block=cb)
+    # one converter measuring a node of another subsystem
+    from oracle import partition
+    sub, _ = partition(net)
+    other = int(np.nonzero(sub != sub[net.cb_node[0]])[0][0])
+    nd = net.cb_node.copy(); nd[0] = other
+    assert "spanning two subsystems" in bad(net, cb_node=nd)
+    cn = net.ci_node.copy(); cn[0] = other
+    assert "outside its block group" in bad(net, ci_node=cn)
+    sc_net, sc = g.n1_contingency(n_scenarios=4, n_buses=24, n_sub=4, n_steps=10)
+    ctl = g.with_converter_controls(sc_net, n_converters=2)
+    with pytest.raises(emt.EmtError, match="control blocks are not supported"):
+        emt.emt_build_network(ctl, sc)
