@@ -303,7 +303,7 @@ std::string validate(const emt_network_desc* d) {
   if (d->n_cblocks && (!d->cb_type || !d->cb_in0 || !d->cb_in1 || !d->cb_node || !d->cb_p0 || !d->cb_p1))
     return "control block array is NULL";
   if (d->n_cinj && (!d->ci_block || !d->ci_node)) return "control injection array is NULL";
-  if (d->n_cblocks > (1 << 24)) return "too many control blocks";
+  if (d->n_cblocks >= (1 << 24)) return "too many control blocks";
   for (int64_t b = 0; b < d->n_cblocks; ++b) {
     const std::string nm = "control block " + std::to_string(b);
     const int t = d->cb_type[b];
@@ -1052,16 +1052,20 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       sd.clay_off = (int)c->clay.size();
       sd.n_clay = sd.n_cb > 0 ? n_layers : 0;
       const double dt = d->dt;
+      const int zero_pair = 2 * sd.n_cb;
       for (size_t j = 0; j < order.size(); ++j) {
         const int64_t b = order[j];
-        if (j == 0 || layer[b] != layer[order[j - 1]]) c->clay.push_back((int32_t)j);
+        if (j == 0 || layer[b] != layer[order[j - 1]]) {   // a layer starts: its type if uniform
+          int lt = d->cb_type[b];
+          for (size_t q = j; q < order.size() && layer[order[q]] == layer[b]; ++q)
+            if (d->cb_type[order[q]] != lt) lt = kMixedLayer;
+          c->clay.push_back((int32_t)j | (lt << kLayerTypeShift));
+        }
         CtrlDev r{};
         r.type = d->cb_type[b];
-        r.in0 = r.in1 = -1;
-        for (int i = 0; i < n_inputs(b); ++i) {
-          (i == 0 ? r.in0 : r.in1) = c->cb_slot_of[input(b, i)];
-          if (input(b, i) >= b) r.late |= 1 << i;
-        }
+        r.i0 = r.i1 = zero_pair;
+        for (int i = 0; i < n_inputs(b); ++i)
+          (i == 0 ? r.i0 : r.i1) = 2 * c->cb_slot_of[input(b, i)] + (input(b, i) >= b ? 1 : 0);
         r.node = r.type == 1 ? local[d->cb_node[b]] : -1;
         const double p0 = d->cb_p0[b], p1 = d->cb_p1[b];
         r.p0 = p0;

@@ -100,23 +100,30 @@ struct SubDev {
   int32_t rs_off, n_rs;        // runtime switches (RuntimeSwitchDev list)
   int32_t ce_off, n_ce;        // coupled line ends (CoupledEndDev list)
   int32_t cb_off, n_cb;        // control blocks (CtrlDev list, by layer)
-  int32_t clay_off, n_clay;    // control layers: n_clay + 1 starts in clay (local block slots)
+  int32_t clay_off, n_clay;    // control layers: n_clay + 1 starts in clay (with the layer's type, see kLayerTypeShift)
   int32_t ci_off, n_ci;        // control injections: local block slot per injection in cinj
 };
 
-// A control block in device form (subsystem-local, ordered by layer).  Its
-// inputs are local block slots (-1: none); bit 0 / 1 of `late` marks input
-// 0 / 1 as read from the previous step's outputs (the loop-breaking rule).
-// Coefficients: GAIN p0; SUM p0, p1; MUL p0; LIMIT lo p0, hi p1; INTEG
-// p0 = k dt / 2; LAG p0 = a, p1 = b; PI kp p0, ki p1, p2 = dt / 2.
-struct CtrlDev {
+// A control block in device form (subsystem-local, ordered by layer).  The
+// CTA keeps block outputs as pairs y[2 slot + parity of the step]; an input
+// is stored as i = 2 slot + late, where late = 1 marks a read of the
+// previous step's output (the loop-breaking rule), so that the value read
+// at a step of parity par is y[i ^ par].  An unused input points at the
+// zero pair after the last block (i = 2 n_cb).  Coefficients: GAIN p0; SUM
+// p0, p1; MUL p0; LIMIT lo p0, hi p1; INTEG p0 = k dt / 2; LAG p0 = a,
+// p1 = b; PI kp p0, ki p1, p2 = dt / 2.
+struct __align__(16) CtrlDev {
   int32_t type;        // 0 CONST .. 8 PI, as in the public header
-  int32_t in0, in1;    // local block slots, -1 unused
+  int32_t i0, i1;      // inputs, encoded as above
   int32_t node;        // MEAS: local node
-  int32_t late;        // delayed-input bits
-  int32_t pad;
   double p0, p1, p2;
+  double pad;
 };
+
+// Control layer starts (local block slots) carry the layer's block type in
+// bits 24..27 when all its blocks share one type, else kMixedLayer.
+constexpr int kLayerTypeShift = 24;
+constexpr int kMixedLayer = 15;
 
 // Maximum runtime switches per subsystem (2^k solve matrices each epoch).
 constexpr int kMaxRuntimeSwitches = 8;

@@ -328,6 +328,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   size_t o = 0;
   auto d = [&](size_t count) { size_t r = o; o += count * 8; return r; };
   auto w = [&](size_t count) { size_t r = o; o += count * 4; return r; };
+  auto d16 = [&](size_t count) { o = (o + 15) & ~(size_t)15; return d(count); };
   const size_t ldg = (size_t)(L.nc | 1);
   const size_t nbuf = L.nbuf > 1 ? 2 : 1;
   s.gi = d(nbuf * (size_t)L.n * ldg);
@@ -345,9 +346,9 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.imode = d(2 * (size_t)L.le);
   s.ceti = d(9 * (size_t)L.ce);
   s.cetinv = d(9 * (size_t)L.ce);
-  s.cbr = d(sizeof(CtrlDev) / 8 * (size_t)L.cb);
-  s.cy = d(2 * (size_t)L.cb);
-  s.cs = d(2 * (size_t)L.cb);
+  s.cbr = d16(sizeof(CtrlDev) / 8 * (size_t)L.cb);
+  s.cy = d16(2 * (size_t)L.cb + 2);
+  s.cs = d16(2 * (size_t)L.cb);
   s.gilo = w(nbuf * (size_t)L.n * ldg);
   s.ivf = w(L.nc);
   s.partf = w((size_t)L.n * L.q);
@@ -395,40 +396,76 @@ __device__ void fold_modes(int lane, int n_le, int n_ce, const int* lece, const 
   __syncwarp();
 }
 
-// One control block at the current step (its layer's inputs are final):
-// an input marked late reads the previous step's outputs.  s = the block's
-// two states.
-__device__ __forceinline__ double control_block(const CtrlDev& r, const double* yprev, const double* ycur,
-                                                const double* vv, double* s) {
-  const double u0 = r.in0 >= 0 ? ((r.late & 1) ? yprev : ycur)[r.in0] : 0.0;
-  const double u1 = r.in1 >= 0 ? ((r.late & 2) ? yprev : ycur)[r.in1] : 0.0;
-  double y;
-  switch (r.type) {
-    case 0: y = r.p0; break;
-    case 1: y = vv[r.node]; break;
-    case 2: y = r.p0 * u0; break;
-    case 3: y = fma(r.p0, u0, r.p1 * u1); break;
-    case 4: y = r.p0 * u0 * u1; break;
-    case 5: y = u0 < r.p0 ? r.p0 : (u0 > r.p1 ? r.p1 : u0); break;
-    case 6:   // trapezoidal integral
-      y = fma(r.p0, u0 + s[1], s[0]);
-      s[0] = y;
-      s[1] = u0;
+// Total order of finite doubles as signed 64-bit integers (the magnitude
+// bits of negative values flipped), so that a limiter compares on the
+// integer pipe instead of spending FP64 latency.
+__device__ __forceinline__ long long ordered_bits(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
+// One control block of type `type` at a step of parity par (its layer's
+// current inputs are final): inputs are y[i ^ par] (see CtrlDev), st = the
+// block's two states, updated into *ns (and *has_state set) for the types
+// that keep state; the caller stores only for its own block.  FP64
+// instructions cost ~64 cycles of the warp each, so each type uses as few
+// as it can; a limiter compares on the integer pipe.
+__device__ __forceinline__ double control_block(int type, const CtrlDev& r, const double* y, int par,
+                                                const double* vv, const double* st, double2* ns, bool* has_state) {
+  const double u0 = y[r.i0 ^ par];
+  const double u1 = y[r.i1 ^ par];
+  double out;
+  switch (type) {
+    case 0: out = r.p0; break;
+    case 1: out = vv[r.node]; break;
+    case 2: out = r.p0 * u0; break;
+    case 3: out = fma(r.p0, u0, r.p1 * u1); break;
+    case 4: out = r.p0 * u0 * u1; break;
+    case 5: {   // lo if u0 < lo, hi if u0 > hi, else u0 (finite values)
+      const long long k = ordered_bits(u0);
+      out = k < ordered_bits(r.p0) ? r.p0 : (k > ordered_bits(r.p1) ? r.p1 : u0);
       break;
-    case 7:   // first-order lag, Tustin
-      y = fma(r.p0, s[0], r.p1 * (u0 + s[1]));
-      s[0] = y;
-      s[1] = u0;
+    }
+    case 6: {   // trapezoidal integral
+      const double2 s = *reinterpret_cast<const double2*>(st);
+      out = fma(r.p0, u0 + s.y, s.x);
+      *ns = make_double2(out, u0);
+      *has_state = true;
       break;
+    }
+    case 7: {   // first-order lag, Tustin: a y(n-1) + b (u0 + u0(n-1))
+      const double2 s = *reinterpret_cast<const double2*>(st);
+      out = fma(r.p1, u0 + s.y, r.p0 * s.x);
+      *ns = make_double2(out, u0);
+      *has_state = true;
+      break;
+    }
     default: {   // PI: proportional + trapezoidal integral
-      const double integral = fma(r.p2, u0 + s[1], s[0]);
-      y = fma(r.p0, u0, r.p1 * integral);
-      s[0] = integral;
-      s[1] = u0;
+      const double2 s = *reinterpret_cast<const double2*>(st);
+      const double integral = fma(r.p2, u0 + s.y, s.x);
+      out = fma(r.p1, integral, r.p0 * u0);
+      *ns = make_double2(integral, u0);
+      *has_state = true;
       break;
     }
   }
-  return y;
+  return out;
+}
+
+// Block b of a layer (type lt, or each block's own for a mixed layer);
+// lanes past the layer's end evaluate the layer's first block and store
+// nothing (a straight path without a per-lane loop is much shorter here).
+__device__ __forceinline__ void control_slot(int b, int first, bool act, int lt, const CtrlDev* cbr, double* cy,
+                                             double* cs, int par, const double* vv) {
+  const int bb = act ? b : first;
+  const CtrlDev& r = cbr[bb];
+  double2 ns = make_double2(0.0, 0.0);
+  bool has_state = false;
+  const double y = control_block(lt == kMixedLayer ? r.type : lt, r, cy, par, vv, cs + 2 * bb, &ns, &has_state);
+  if (act) {
+    cy[2 * b + par] = y;
+    if (has_state) *reinterpret_cast<double2*>(cs + 2 * b) = ns;
+  }
 }
 
 // One warp collects one step's line-end histories I_e(n) from the tagged
@@ -510,9 +547,9 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   int* cele0 = reinterpret_cast<int*>(smem_raw + L.cele0);
   int* cenode = reinterpret_cast<int*>(smem_raw + L.cenode);
   CtrlDev* cbr = reinterpret_cast<CtrlDev*>(smem_raw + L.cbr);      // control blocks, by layer
-  double* cy = reinterpret_cast<double*>(smem_raw + L.cy);          // [2][cb]: block outputs by step parity
+  double* cy = reinterpret_cast<double*>(smem_raw + L.cy);          // [cb + 1][2]: outputs by step parity, zero pair
   double* cs = reinterpret_cast<double*>(smem_raw + L.cs);          // [cb][2]: block states
-  int* clay = reinterpret_cast<int*>(smem_raw + L.clay);            // layer starts
+  int* clay = reinterpret_cast<int*>(smem_raw + L.clay);            // layer starts and types
   int* cinj = reinterpret_cast<int*>(smem_raw + L.cinj);            // block slot per control injection
 
   const int sidx = blockIdx.x;
@@ -525,7 +562,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   const int blk_len = n_le + 3 * n_ce;   // per parity: line-end values, then coupled ends' phase currents
   const int zero_slot = ie_base + 2 * blk_len;
   const int ci_base = zero_slot + 1;   // controlled currents
-  const int n_cb = S.n_cb, n_clay = S.n_clay, n_ci = S.n_ci, lcb = P.lim.cb;
+  const int n_cb = S.n_cb, n_clay = S.n_clay, n_ci = S.n_ci;
   // with control blocks the warp before the poll warp evaluates them in the
   // update phase, layer by layer; the update items take the other warps
   const int item_threads = n_cb > 0 ? kItemThreads - 32 : kItemThreads;
@@ -583,8 +620,9 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     cbr[x] = P.cb[S.cb_off + x];
     cs[2 * x] = P.cstate[2 * (size_t)(S.cb_off + x)];
     cs[2 * x + 1] = P.cstate[2 * (size_t)(S.cb_off + x) + 1];
-    cy[(int)((P.n0 - 1) & 1) * lcb + x] = P.cy[S.cb_off + x];
+    cy[2 * x + (int)((P.n0 - 1) & 1)] = P.cy[S.cb_off + x];
   }
+  if (tid < 2 && n_cb > 0) cy[2 * n_cb + tid] = 0.0;   // the zero pair read by unused inputs
   for (int x = tid; x < (n_cb > 0 ? n_clay + 1 : 0); x += T) clay[x] = P.clay[S.clay_off + x];
   for (int x = tid; x < n_ci; x += T) {
     const int b = P.cinj[S.ci_off + x];
@@ -648,6 +686,9 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + (p0 ^ 1) * blk_len, inp + ie_base + p0 * blk_len,
                  imode + p0 * lv, cele0, ceti);
   }
+  // control layer starts 0..31 in the control warp's registers (lane l)
+  int lay_reg = 0;
+  if (n_cb > 0 && lane <= n_clay) lay_reg = clay[lane];
   // recording counters: steps decim, 2 decim, ... go to rows 0, 1, ...
   const int decim = P.rec_decim > 0 ? P.rec_decim : 1;
   int dec = (int)(P.n0 % decim);
@@ -774,13 +815,18 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     } else if (n_cb > 0 && warp == kPollWarp - 1) {
       // control blocks at this step, one layer after another; then the
       // controlled currents of the next step
-      const double* yprev = cy + (par ^ 1) * lcb;
-      double* ycur = cy + par * lcb;
+      constexpr int kSlotMask = (1 << kLayerTypeShift) - 1;
+      int cur = __shfl_sync(0xffffffffu, lay_reg, 0);
       for (int l = 0; l < n_clay; ++l) {
-        for (int b = clay[l] + lane; b < clay[l + 1]; b += 32) ycur[b] = control_block(cbr[b], yprev, ycur, vv, cs + 2 * b);
+        const int nxt = l + 1 < 32 ? __shfl_sync(0xffffffffu, lay_reg, l + 1) : clay[l + 1];
+        const int lt = cur >> kLayerTypeShift, first = cur & kSlotMask, b1 = nxt & kSlotMask;
+        control_slot(first + lane, first, first + lane < b1, lt, cbr, cy, cs, par, vv);
+        for (int b = first + 32 + lane; b - lane < b1; b += 32)   // layers wider than a warp
+          control_slot(b, first, b < b1, lt, cbr, cy, cs, par, vv);
+        cur = nxt;
         __syncwarp();
       }
-      for (int c = lane; c < n_ci; c += 32) inp[ci_base + c] = ycur[cinj[c]];
+      for (int c = lane; c < n_ci; c += 32) inp[ci_base + c] = cy[2 * cinj[c] + par];
     } else {
       // runtime switches: the states in force at the next step (oracle rules)
       if (tid < n_rs) {
@@ -843,7 +889,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     for (int x = tid; x < n_cb; x += T) {
       P.cstate[2 * (size_t)(S.cb_off + x)] = cs[2 * x];
       P.cstate[2 * (size_t)(S.cb_off + x) + 1] = cs[2 * x + 1];
-      P.cy[S.cb_off + x] = cy[(int)((n_end - 1) & 1) * lcb + x];
+      P.cy[S.cb_off + x] = cy[2 * x + (int)((n_end - 1) & 1)];
     }
     if (n_rs > 0 && tid == 0) {
       int w = 0;
