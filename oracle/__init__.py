@@ -55,6 +55,10 @@ class _Net(ctypes.Structure):
         ("rs_on0", ctypes.c_void_p), ("rs_trip", ctypes.c_void_p),
         ("n_cl", ctypes.c_int64), ("cl_k", ctypes.c_void_p), ("cl_m", ctypes.c_void_p),
         ("cl_tv", ctypes.c_void_p), ("cl_z", ctypes.c_void_p), ("cl_tau", ctypes.c_void_p),
+        ("n_fl", ctypes.c_int64), ("fl_k", ctypes.c_void_p), ("fl_m", ctypes.c_void_p),
+        ("fl_tau", ctypes.c_void_p), ("fl_y0", ctypes.c_void_p), ("fl_ny", ctypes.c_void_p),
+        ("fl_yq", ctypes.c_void_p), ("fl_yc", ctypes.c_void_p), ("fl_a0", ctypes.c_void_p),
+        ("fl_na", ctypes.c_void_p), ("fl_ap", ctypes.c_void_p), ("fl_ar", ctypes.c_void_p),
         ("n_cb", ctypes.c_int64), ("cb_type", ctypes.c_void_p), ("cb_in0", ctypes.c_void_p),
         ("cb_in1", ctypes.c_void_p), ("cb_node", ctypes.c_void_p), ("cb_p0", ctypes.c_void_p),
         ("cb_p1", ctypes.c_void_p),
@@ -123,6 +127,13 @@ class _Pinned:
         n.cl_k, n.cl_m = p(rs("cl_k", np.int32), np.int32), p(rs("cl_m", np.int32), np.int32)
         n.cl_tv, n.cl_z = p(rs("cl_tv", np.float64), np.float64), p(rs("cl_z", np.float64), np.float64)
         n.cl_tau = p(rs("cl_tau", np.float64), np.float64)
+        n.n_fl = int(len(rs("fl_k", np.int32)))
+        n.fl_k, n.fl_m = p(rs("fl_k", np.int32), np.int32), p(rs("fl_m", np.int32), np.int32)
+        n.fl_tau, n.fl_y0 = p(rs("fl_tau", np.float64), np.float64), p(rs("fl_y0", np.float64), np.float64)
+        n.fl_ny, n.fl_na = p(rs("fl_ny", np.int32), np.int32), p(rs("fl_na", np.int32), np.int32)
+        n.fl_yq, n.fl_yc = p(rs("fl_yq", np.float64), np.float64), p(rs("fl_yc", np.float64), np.float64)
+        n.fl_a0 = p(rs("fl_a0", np.float64), np.float64)
+        n.fl_ap, n.fl_ar = p(rs("fl_ap", np.float64), np.float64), p(rs("fl_ar", np.float64), np.float64)
         n.n_cb = int(len(rs("cb_type", np.uint8)))
         n.cb_type = p(rs("cb_type", np.uint8), np.uint8)
         n.cb_in0, n.cb_in1 = p(rs("cb_in0", np.int32), np.int32), p(rs("cb_in1", np.int32), np.int32)

@@ -160,6 +160,25 @@ bool valid(const orc_net* net) {
     if (k < -1 || m < -1 || k >= net->n_nodes || m >= net->n_nodes || k == m || (k < 0 && m < 0)) return false;
     if (net->rs_kind[w] > 1 || !(net->rs_ron[w] > 0.0) || !(net->rs_roff[w] > 0.0)) return false;
   }
+  if (net->n_fl < 0) return false;
+  for (int64_t l = 0; l < net->n_fl; ++l) {
+    const int32_t k = net->fl_k[l], m = net->fl_m[l];
+    if (k < 0 || m < 0 || k >= net->n_nodes || m >= net->n_nodes || k == m) return false;
+    if (!(net->fl_tau[l] >= net->dt) || !std::isfinite(net->fl_tau[l])) return false;
+    if (!(net->fl_y0[l] >= 0.0) || !std::isfinite(net->fl_y0[l]) || !std::isfinite(net->fl_a0[l])) return false;
+    if (net->fl_ny[l] < 0 || net->fl_ny[l] > 4 || net->fl_na[l] < 0 || net->fl_na[l] > 4) return false;
+    double geq = net->fl_y0[l];
+    for (int i = 0; i < net->fl_ny[l]; ++i) {
+      const double q = net->fl_yq[4 * l + i], c = net->fl_yc[4 * l + i];
+      if (!(q < 0.0) || !std::isfinite(q) || !std::isfinite(c)) return false;
+      geq += c * (net->dt / 2.0) / (1.0 - q * net->dt / 2.0);
+    }
+    if (!(geq > 0.0)) return false;
+    for (int i = 0; i < net->fl_na[l]; ++i)
+      if (!(net->fl_ap[4 * l + i] < 0.0) || !std::isfinite(net->fl_ap[4 * l + i]) ||
+          !std::isfinite(net->fl_ar[4 * l + i]))
+        return false;
+  }
   if (net->n_cb < 0 || net->n_ci < 0) return false;
   for (int64_t b = 0; b < net->n_cb; ++b) {
     const int t = net->cb_type[b];
@@ -256,6 +275,18 @@ struct Sim {
     T im[2][3];   // modal history currents of the current step per end
   };
   std::vector<CLine> cl;
+  // frequency-dependent lines: per line the discretised terms, per end the
+  // states, the values w each end sent (by step modulo d + 3) and W of the
+  // previous step
+  struct FLine {
+    int64_t d;
+    double phi, geq, y0, a0;
+    int ny, na;
+    double lam_y[4], mu_y[4], lam_a[4], mu_a[4];
+    T s[2][4], z[2][4], vprev[2], wprev[2], b[2];
+    std::vector<T> w[2];
+  };
+  std::vector<FLine> fl;
   // control blocks: output of the latest evaluation, and the two states
   // (integral or previous output; previous input)
   std::vector<T> cy, cs0, cs1;
@@ -292,6 +323,34 @@ struct Sim {
     rs_on.assign(net->n_rs, 0);
     for (int64_t w = 0; w < net->n_rs; ++w) rs_on[w] = net->rs_on0[w] ? 1 : 0;
     rs_i.assign(net->n_rs, 0.0);
+    fl.assign(net->n_fl, FLine{});
+    for (int64_t l = 0; l < net->n_fl; ++l) {
+      FLine& L = fl[l];
+      const double dt = net->dt, steps = net->fl_tau[l] / dt;
+      L.d = (int64_t)std::floor(steps);
+      L.phi = steps - (double)L.d;
+      L.y0 = net->fl_y0[l];
+      L.a0 = net->fl_a0[l];
+      L.ny = net->fl_ny[l];
+      L.na = net->fl_na[l];
+      L.geq = L.y0;
+      for (int i = 0; i < L.ny; ++i) {
+        const double q = net->fl_yq[4 * l + i], den = 1.0 - q * dt / 2.0;
+        L.lam_y[i] = (1.0 + q * dt / 2.0) / den;
+        L.mu_y[i] = net->fl_yc[4 * l + i] * (dt / 2.0) / den;
+        L.geq += L.mu_y[i];
+      }
+      for (int i = 0; i < L.na; ++i) {
+        const double p = net->fl_ap[4 * l + i], den = 1.0 - p * dt / 2.0;
+        L.lam_a[i] = (1.0 + p * dt / 2.0) / den;
+        L.mu_a[i] = net->fl_ar[4 * l + i] * (dt / 2.0) / den;
+      }
+      for (int e = 0; e < 2; ++e) {
+        for (int i = 0; i < 4; ++i) L.s[e][i] = L.z[e][i] = T(0.0);
+        L.vprev[e] = L.wprev[e] = L.b[e] = T(0.0);
+        L.w[e].assign(L.d + 3, T(0.0));
+      }
+    }
     cy.assign(net->n_cb, T(0.0));
     cs0.assign(net->n_cb, T(0.0));
     cs1.assign(net->n_cb, T(0.0));
@@ -336,6 +395,12 @@ struct Sim {
         rs_i[w] = i;
       }
     }
+  }
+
+  // w value end e of frequency-dependent line L sent at step m (0 before the start)
+  T fl_sent(const FLine& L, int e, int64_t m) const {
+    if (m < 1) return T(0.0);
+    return L.w[e][m % (L.d + 3)];
   }
 
   // Control blocks at step n, in index order over one array: an input of
@@ -417,6 +482,9 @@ struct Sim {
       if (sub[net->ln_k[l]] == s) G[(size_t)local[net->ln_k[l]] * ns + local[net->ln_k[l]]] += y;
       if (sub[net->ln_m[l]] == s) G[(size_t)local[net->ln_m[l]] * ns + local[net->ln_m[l]]] += y;
     }
+    for (int64_t l = 0; l < net->n_fl; ++l)
+      for (int32_t x : {net->fl_k[l], net->fl_m[l]})
+        if (sub[x] == s) G[(size_t)local[x] * ns + local[x]] += T(fl[l].geq);
     for (int64_t w = 0; w < net->n_sw; ++w)
       if (st[w]) stamp(net->sw_k[w], net->sw_m[w], T(1.0) / T(net->sw_r[w]));
     for (int64_t w = 0; w < net->n_rs; ++w) {
@@ -457,6 +525,24 @@ struct Sim {
       }
     }
     for (int64_t c = 0; c < net->n_ci; ++c) rhs[net->ci_node[c]] += cy[net->ci_block[c]];   // y(n-1)
+    // frequency-dependent lines: the far end's interpolated w, A's terms,
+    // and the history current each end draws
+    for (int64_t l = 0; l < net->n_fl; ++l) {
+      FLine& L = fl[l];
+      for (int e = 0; e < 2; ++e) {
+        const T W = T(1.0 - L.phi) * fl_sent(L, 1 - e, n - L.d) + T(L.phi) * fl_sent(L, 1 - e, n - L.d - 1);
+        T b = T(L.a0) * W;
+        for (int i = 0; i < L.na; ++i) {
+          L.z[e][i] = T(L.lam_a[i]) * L.z[e][i] + T(L.mu_a[i]) * (W + L.wprev[e]);
+          b += L.z[e][i];
+        }
+        L.wprev[e] = W;
+        L.b[e] = b;
+        T hist = -b;
+        for (int i = 0; i < L.ny; ++i) hist += T(L.lam_y[i]) * L.s[e][i] + T(L.mu_y[i]) * L.vprev[e];
+        rhs[e == 0 ? net->fl_k[l] : net->fl_m[l]] -= hist;
+      }
+    }
     for (int64_t l = 0; l < net->n_ln; ++l) {
       int64_t d1 = net->ln_d[l] + 1;
       rhs[net->ln_k[l]] -= ring_k[l][n % d1];
@@ -512,6 +598,19 @@ struct Sim {
           for (int p = 0; p < 3; ++p) vm += T(L.tinv[3 * j + p]) * v[nd[p]];
           L.c[e][j][n % (L.d[j] + 2)] = -T(L.y2[j]) * vm - L.im[e][j];
         }
+      }
+    }
+    for (int64_t l = 0; l < net->n_fl; ++l) {
+      FLine& L = fl[l];
+      for (int e = 0; e < 2; ++e) {
+        const T ve = v[e == 0 ? net->fl_k[l] : net->fl_m[l]];
+        T yc = T(L.y0) * ve;
+        for (int i = 0; i < L.ny; ++i) {
+          L.s[e][i] = T(L.lam_y[i]) * L.s[e][i] + T(L.mu_y[i]) * (ve + L.vprev[e]);
+          yc += L.s[e][i];
+        }
+        L.w[e][n % (L.d + 3)] = T(2.0) * yc - L.b[e];
+        L.vprev[e] = ve;
       }
     }
     evaluate_controls();
@@ -589,7 +688,7 @@ extern "C" int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_
 // and finally dg/dR = -1/R^2, dg/dL = -dt/(2L^2), dg/dC = 2/dt.
 extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad,
                            double* loss) {
-  if (!valid(net) || !v_target || !grad || n_steps < 0 || net->n_cb > 0) return -1;
+  if (!valid(net) || !v_target || !grad || n_steps < 0 || net->n_cb > 0 || net->n_fl > 0) return -1;
   const int64_t nn = net->n_nodes, nb = net->n_br, ns = net->n_src, nl = net->n_ln, nr = net->n_rs;
   Sim<double> sim;
   sim.net = net;

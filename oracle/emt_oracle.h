@@ -92,6 +92,35 @@ typedef struct {
    * of equal or higher index its step-(n-1) output (0 at n = 1) -- this is
    * how algebraic loops are broken.  Controlled current injection c:
    * y_{ci_block[c]}(n) enters node ci_node[c] at step n + 1. */
+  /* Frequency-dependent lines (one conductor each, ends fl_k / fl_m, both
+   * unknown nodes): characteristic admittance and propagation function as
+   * pole-residue sums,
+   *   Y_c(s) = y0 + sum_i c_i / (s - q_i),  A(s) = e^{-s tau} (a0 + sum_i r_i / (s - p_i)),
+   * up to 4 real poles each ([4 l + i] layout), poles < 0, tau >= dt.
+   * Each first-order term is discretised by the trapezoidal rule,
+   *   x(n) = lam x(n-1) + mu (u(n) + u(n-1)),  lam = (1 + p dt/2)/(1 - p dt/2),
+   *   mu = r (dt/2)/(1 - p dt/2).
+   * At an end e with far end f:
+   *   yc_e(n) = y0 v_e(n) + sum_i s_ei(n)              (s_ei: Y_c's terms of v_e)
+   *   i_e(n)  = yc_e(n) - b_e(n)                       (current into the line)
+   *   b_e(n)  = a0 W_f(n) + sum_i z_ei(n)              (z_ei: A's terms of W_f)
+   *   W_f(n)  = (1 - phi) w_f(n - d) + phi w_f(n - d - 1),  tau = (d + phi) dt
+   *   w_f(m)  = yc_f(m) + i_f(m) = 2 yc_f(m) - b_f(m)  (0 for m <= 0).
+   * So each end stamps G_eq = y0 + sum mu_i and draws the history current
+   * sum_i (lam_i s_ei(n-1) + mu_i v_e(n-1)) - b_e(n).  With y0 = 1/Z, a0 = 1,
+   * no poles and tau = d dt this is the lossless Bergeron line. */
+  int64_t n_fl;
+  const int32_t* fl_k;
+  const int32_t* fl_m;
+  const double* fl_tau;
+  const double* fl_y0;
+  const int32_t* fl_ny;
+  const double* fl_yq;
+  const double* fl_yc;
+  const double* fl_a0;
+  const int32_t* fl_na;
+  const double* fl_ap;
+  const double* fl_ar;
   int64_t n_cb;
   const uint8_t* cb_type;
   const int32_t* cb_in0;
@@ -132,7 +161,8 @@ int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_target, int
  * With runtime switches the reverse sweep uses the states the forward run
  * decided (the gradient of the smooth piece the run lies on).  The
  * parameters of coupled lines themselves (Z, T_v, travel times) are not
- * differentiated.  Networks with control blocks are rejected (-1). */
+ * differentiated.  Networks with control blocks or frequency-dependent
+ * lines are rejected (-1). */
 int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad, double* loss);
 
 /* Control block outputs of steps 1..n_steps: y_out[(n-1) n_cb + b]

@@ -81,6 +81,20 @@ class Network:
     cl_tv: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
     cl_z: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
     cl_tau: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    # frequency-dependent lines (one conductor each): ends, travel time (s),
+    # Y_c = y0 + sum c_i/(s - q_i) and A = e^{-s tau}(a0 + sum r_i/(s - p_i)),
+    # up to 4 poles each in [4 l + i] slots (unused slots 0)
+    fl_k: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    fl_m: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    fl_tau: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    fl_y0: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    fl_ny: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    fl_yq: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    fl_yc: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    fl_a0: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    fl_na: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    fl_ap: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    fl_ar: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
     # control blocks (CB_* types), evaluated after each step's solve; an input
     # of lower index reads its step-n output, of equal or higher index its
     # step-(n-1) output.  Controlled current injections: block output y(n)
@@ -119,6 +133,10 @@ class Network:
     @property
     def n_coupled_lines(self) -> int:
         return int(self.cl_z.shape[0]) // 3
+
+    @property
+    def n_fd_lines(self) -> int:
+        return int(self.fl_k.shape[0])
 
     @property
     def n_control_blocks(self) -> int:
@@ -248,6 +266,7 @@ class NetworkBuilder:
         self.sw = []     # (k, m, r, close, open)
         self.rs = []     # (k, m, kind, r_on, r_off, on0, trip)
         self.cl = []     # (k3, m3, tv9, z3, tau3)
+        self.fl = []     # (k, m, tau, y0, yq4, yc4, ny, a0, ap4, ar4, na)
         self.cb = []     # (type, in0, in1, node, p0, p1)
         self.ci = []     # (block, node)
 
@@ -276,6 +295,16 @@ class NetworkBuilder:
         """Three-phase lossless line in modal form (see ``Network.cl_*``)."""
         self.cl.append(([int(x) for x in k3], [int(x) for x in m3], np.asarray(tv, np.float64).reshape(9),
                         np.asarray(z3, np.float64).reshape(3), np.asarray(tau3, np.float64).reshape(3)))
+
+    def fd_line(self, k, m, tau, y0, yq=(), yc=(), a0=0.0, ap=(), ar=()):
+        """Frequency-dependent line (see ``Network.fl_*``): travel time ``tau``
+        in seconds, Y_c's direct term and poles/residues, A's direct term and
+        poles/residues (at most 4 each)."""
+        pad = lambda x: list(map(float, x)) + [0.0] * (4 - len(x))
+        assert len(yq) == len(yc) <= 4 and len(ap) == len(ar) <= 4
+        self.fl.append((int(k), int(m), float(tau), float(y0), pad(yq), pad(yc), len(yq), float(a0), pad(ap), pad(ar),
+                        len(ap)))
+        return len(self.fl) - 1
 
     def block(self, kind, in0=-1, in1=-1, node=-1, p0=0.0, p1=0.0):
         """Control block of type ``kind`` (CB_*); returns its index."""
@@ -308,6 +337,13 @@ class NetworkBuilder:
             cl_tv=np.ascontiguousarray(np.concatenate([c[2] for c in self.cl]) if self.cl else np.zeros(0)),
             cl_z=np.ascontiguousarray(np.concatenate([c[3] for c in self.cl]) if self.cl else np.zeros(0)),
             cl_tau=np.ascontiguousarray(np.concatenate([c[4] for c in self.cl]) if self.cl else np.zeros(0)),
+            fl_k=col(self.fl, 0, np.int32), fl_m=col(self.fl, 1, np.int32), fl_tau=col(self.fl, 2, np.float64),
+            fl_y0=col(self.fl, 3, np.float64), fl_ny=col(self.fl, 6, np.int32), fl_a0=col(self.fl, 7, np.float64),
+            fl_na=col(self.fl, 10, np.int32),
+            fl_yq=np.ascontiguousarray(np.array([x for f in self.fl for x in f[4]], np.float64)),
+            fl_yc=np.ascontiguousarray(np.array([x for f in self.fl for x in f[5]], np.float64)),
+            fl_ap=np.ascontiguousarray(np.array([x for f in self.fl for x in f[8]], np.float64)),
+            fl_ar=np.ascontiguousarray(np.array([x for f in self.fl for x in f[9]], np.float64)),
             cb_type=col(self.cb, 0, np.uint8), cb_in0=col(self.cb, 1, np.int32), cb_in1=col(self.cb, 2, np.int32),
             cb_node=col(self.cb, 3, np.int32), cb_p0=col(self.cb, 4, np.float64), cb_p1=col(self.cb, 5, np.float64),
             ci_block=col(self.ci, 0, np.int32), ci_node=col(self.ci, 1, np.int32),
@@ -671,6 +707,44 @@ def with_rectifier_loads(base: Network, seed: int = 1006, n_rectifiers: int = 30
     net.rs_on0 = np.asarray(rs["on0"], np.uint8)
     net.rs_trip = np.asarray(rs["trip"], np.int64)
     net.meta = dict(net.meta, runtime_switches={"seed": seed, "rectifiers": n_rectifiers, "breakers": n_breakers})
+    return net
+
+
+def with_fd_lines(base: Network, seed: int = 1009, fractional: bool = True) -> Network:
+    """``base`` with every Bergeron line replaced by a lossy frequency-dependent
+    line of the same surge impedance Z_c and travel time (plus U[0, 1) dt when
+    ``fractional``): Y_c = 1/Z_c + c/(s - q), q ~ -U[1e3, 1e5] 1/s, c = -q
+    delta / Z_c with delta ~ U[0.05, 0.3] (so Y_c(0) = (1 + delta) / Z_c,
+    positive real); A = e^{-s tau} sum_{i=1,2} r_i / (s - p_i), p_1 ~ -U[2e3,
+    2e4], p_2 ~ -U[2e4, 2e5] 1/s, r_i = -p_i w_i A_0 with weights w ~ U(0, 1),
+    w_1 + w_2 = 1 and DC transmission A_0 = exp(-U[0.02, 0.2]), so |A(jw)| <=
+    A_0 < 1: a passive line whose losses grow with frequency.  The fitted
+    models of real lines are not available; these stand in for them."""
+    rng = np.random.default_rng(seed)
+    net = base.copy()
+    L = base.n_lines
+    yq = np.zeros((L, 4)); yc = np.zeros((L, 4)); ap = np.zeros((L, 4)); ar = np.zeros((L, 4))
+    tau = (base.ln_delay.astype(np.float64) + (rng.uniform(0.0, 1.0, L) if fractional else 0.0)) * base.dt
+    for l in range(L):
+        z = float(base.ln_zc[l])
+        q = -rng.uniform(1e3, 1e5)
+        yq[l, 0], yc[l, 0] = q, -q * rng.uniform(0.05, 0.3) / z
+        a0 = np.exp(-rng.uniform(0.02, 0.2))
+        w1 = rng.uniform(0.0, 1.0)
+        p1, p2 = -rng.uniform(2e3, 2e4), -rng.uniform(2e4, 2e5)
+        ap[l, :2] = p1, p2
+        ar[l, :2] = -p1 * w1 * a0, -p2 * (1.0 - w1) * a0
+    net.fl_k, net.fl_m = base.ln_k.copy(), base.ln_m.copy()
+    net.fl_tau = tau
+    net.fl_y0 = 1.0 / base.ln_zc
+    net.fl_ny = np.ones(L, np.int32)
+    net.fl_yq, net.fl_yc = yq.reshape(-1), yc.reshape(-1)
+    net.fl_a0 = np.zeros(L)
+    net.fl_na = np.full(L, 2, np.int32)
+    net.fl_ap, net.fl_ar = ap.reshape(-1), ar.reshape(-1)
+    for f in ("ln_k", "ln_m", "ln_zc", "ln_delay"):
+        setattr(net, f, getattr(base, f)[:0].copy())
+    net.meta = dict(net.meta, fd_lines={"seed": seed, "lines": L, "fractional": fractional})
     return net
 
 
