@@ -364,6 +364,17 @@ def coupled_line_leg(steps=None, reps=3):
                        "all nodes recorded", steps, reps)
 
 
+def fd_line_leg(steps=None, reps=3):
+    """The large-scale network with its 2,100 line conductors as lossy
+    frequency-dependent lines (one Y_c pole, two propagation poles, travel
+    times with a fractional part)."""
+    from paper_1903_01081_b300 import netgen as g
+    return variant_leg(g.with_fd_lines(g.large_scale()),
+                       "large-scale network with its 2,100 line conductors as frequency-dependent lines: Y_c = 1/Z_c "
+                       "+ one pole, A = e^{-s tau} x two poles (DC transmission 0.82-0.98), travel times (d + U[0,1)) "
+                       "dt; all nodes recorded", steps, reps)
+
+
 def control_leg(steps=None, reps=3):
     """The large-scale network with 180 power-regulated converter loads, each
     24 layered control blocks driving three controlled current injections."""
@@ -521,7 +532,8 @@ def run_ours(args):
             "clocks": clocks.summary(),
             "parity_rel_err_first_2000_steps": parity,
             **({"scenarios": scenario_legs(), "adjoint": adjoint_leg(), "runtime_switches": runtime_switch_leg(),
-                "coupled_lines": coupled_line_leg(), "controls": control_leg()} if args.leg == "all" else {}),
+                "coupled_lines": coupled_line_leg(), "fd_lines": fd_line_leg(), "controls": control_leg()}
+               if args.leg == "all" else {}),
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -539,7 +551,7 @@ def main():
     ap.add_argument("--time-steps", type=int, default=N_STEPS)
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines",
-                                      "controls"],
+                                      "fd_lines", "controls"],
                     default="all",
                     help="all: the JSON line with every leg; single: the single-network leg only; "
                          "n1 / shared_g / adjoint: that leg alone (profiling)")
@@ -552,7 +564,7 @@ def main():
         return run_rank_selftest()
     if args.impl == "reference":
         return run_reference(args)
-    if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "controls"):
+    if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "fd_lines", "controls"):
         return run_leg(args)
     return run_ours(args)
 
@@ -569,6 +581,8 @@ def run_leg(args):
         out = coupled_line_leg(args.leg_steps, reps=1)
     elif args.leg == "controls":
         out = control_leg(args.leg_steps, reps=1)
+    elif args.leg == "fd_lines":
+        out = fd_line_leg(args.leg_steps, reps=1)
     else:
         shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
         out = scenario_legs((args.leg,), args.leg_steps, shape, args.leg_warm)

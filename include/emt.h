@@ -103,7 +103,24 @@ typedef struct emt_ctx emt_ctx;  /* opaque; owns all device memory it allocates 
  *   at step n + 1 (0 at step 1).  Every connected group of blocks, with the
  *   nodes it measures and drives, lies in one subsystem (a block group that
  *   touches no node runs in subsystem 0).  Not supported with a scenario
- *   set or by emt_adjoint. */
+ *   set or by emt_adjoint.
+ * Frequency-dependent lines (n_fdlines may be 0), one conductor each, ends
+ *   fl_k / fl_m (unknown nodes, cut into different subsystems like any
+ *   line): characteristic admittance and propagation function as
+ *   pole-residue sums, up to 4 real poles each in slots [4 l + i] (unused
+ *   slots ignored):
+ *     Y_c(s) = fl_y0 + sum_{i < fl_ny} fl_yc_i / (s - fl_yq_i),
+ *     A(s)   = e^{-s tau} (fl_a0 + sum_{i < fl_na} fl_ar_i / (s - fl_ap_i)),
+ *   poles < 0, fl_y0 >= 0, tau = fl_tau >= dt (s, any real value).  Each
+ *   pole term is discretised by the trapezoidal rule, x(n) = lam x(n-1) +
+ *   mu (u(n) + u(n-1)), lam = (1 + p dt/2)/(1 - p dt/2), mu = r (dt/2)/
+ *   (1 - p dt/2).  An end e (far end f) draws i_e(n) = yc_e(n) - b_e(n)
+ *   with yc = Y_c applied to its voltage and b_e(n) = A applied to W_f,
+ *   W_f(n) = (1 - phi) w_f(n - d) + phi w_f(n - d - 1), tau = (d + phi) dt,
+ *   w_f(m) = 2 yc_f(m) - b_f(m): it stamps G_eq = fl_y0 + sum mu (> 0
+ *   required) and draws a history current from the previous step.  With
+ *   fl_y0 = 1/Z, fl_a0 = 1, no poles and tau = d dt this is the Bergeron
+ *   line above.  Not supported with a scenario set or by emt_adjoint. */
 typedef struct {
   double dt;
   int64_t n_nodes;
@@ -151,6 +168,18 @@ typedef struct {
   int64_t n_cinj;
   const int32_t* ci_block;
   const int32_t* ci_node;
+  int64_t n_fdlines;
+  const int32_t* fl_k;
+  const int32_t* fl_m;
+  const double* fl_tau;
+  const double* fl_y0;
+  const int32_t* fl_ny;
+  const double* fl_yq;
+  const double* fl_yc;
+  const double* fl_a0;
+  const int32_t* fl_na;
+  const double* fl_ap;
+  const double* fl_ar;
 } emt_network_desc;
 
 /* Optional per-scenario overrides of one base network (the paper's
@@ -285,7 +314,8 @@ emt_status emt_autotune(emt_ctx* ctx, int64_t trial_steps, void* cuda_stream);
  * decided (the forward re-runs record them per step), i.e. the gradient of
  * the smooth piece of J the run lies on.  Coupled lines' own Z, T_v and
  * travel times are not parameters.  Requires emt_prefactor; a context built
- * with a scenario set, or with control blocks, returns EINVAL.  Resets the context to step 0 before and after (the recording
+ * with a scenario set, control blocks or frequency-dependent lines returns
+ * EINVAL.  Resets the context to step 0 before and after (the recording
  * buffer is not written).  Allocates its work buffers (about 8 N n_nodes
  * bytes for a host v_target, N/K checkpoints, the tape) and frees them
  * before returning.  Synchronous.  ETIMEOUT as for emt_step_n. */
@@ -315,7 +345,7 @@ emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
  * "threads_per_cta", "kernel_launches", "n_nodes", "n_branches", "n_sources", "n_line_ends",
  * "smem_bytes" (dynamic shared memory per CTA of the persistent kernel),
  * "n_strong_branches" (L/C branches applied through extra solve columns),
- * "n_runtime_switches", "n_coupled_lines", "n_control_blocks",
+ * "n_runtime_switches", "n_coupled_lines", "n_fd_lines", "n_control_blocks",
  * "n_control_injections", "max_control_layers" (largest layer count of one
  * subsystem's control graph),
  * "n_matrix_variants", "scenarios_per_cta", "batch_threads", "batch_groups"

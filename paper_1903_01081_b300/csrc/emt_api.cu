@@ -64,13 +64,14 @@ struct emt_ctx {
   std::vector<RuntimeSwitchDev> rswitches;             // runtime switches, grouped by subsystem
   std::vector<CoupledEndDev> cends;                    // coupled line ends, grouped by subsystem
   std::vector<int32_t> rs_word0;                       // per subsystem: state word at step 1
+  std::vector<FdEndDev> fdends;                        // frequency-dependent line ends, grouped by subsystem
   std::vector<CtrlDev> cblocks;                        // control blocks, grouped by subsystem, by layer
   std::vector<int32_t> clay, cinj;                     // layer starts; block slot per control injection
   std::vector<int32_t> cb_slot_of;                     // caller's block index -> subsystem-local slot
   std::vector<int32_t> cb_sub_of;                      // caller's block index -> subsystem
   int max_clayers = 0;
   int64_t ring_len = 0, ginv_len = 0, n_lc_total = 0;
-  FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0};
+  FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0};
 
   // device arrays
   SubDev* d_sub = nullptr;
@@ -103,6 +104,8 @@ struct emt_ctx {
   double* d_le_prev = nullptr;
   int32_t* d_rs_word = nullptr;
   double* d_rs_prev_i = nullptr;
+  FdEndDev* d_fd = nullptr;
+  double* d_fd_state = nullptr;
   CtrlDev* d_cb = nullptr;
   int32_t* d_clay = nullptr;
   int32_t* d_cinj = nullptr;
@@ -298,6 +301,32 @@ std::string validate(const emt_network_desc* d) {
     if (d->rs_kind[w] > 1) return "runtime switch " + std::to_string(w) + ": kind must be 0 (diode) or 1 (breaker)";
     if (!finite_pos(d->rs_ron[w]) || !finite_pos(d->rs_roff[w]))
       return "runtime switch " + std::to_string(w) + ": resistances must be finite and > 0";
+  }
+  if (d->n_fdlines < 0) return "negative count";
+  if (d->n_fdlines && (!d->fl_k || !d->fl_m || !d->fl_tau || !d->fl_y0 || !d->fl_ny || !d->fl_yq || !d->fl_yc ||
+                       !d->fl_a0 || !d->fl_na || !d->fl_ap || !d->fl_ar))
+    return "frequency-dependent line array is NULL";
+  for (int64_t l = 0; l < d->n_fdlines; ++l) {
+    const std::string nm = "frequency-dependent line " + std::to_string(l);
+    const int32_t k = d->fl_k[l], m = d->fl_m[l];
+    if (k < 0 || m < 0 || k >= d->n_nodes || m >= d->n_nodes) return nm + ": ends must be unknown nodes";
+    if (k == m) return nm + ": both ends on one node";
+    if (!std::isfinite(d->fl_tau[l]) || !(d->fl_tau[l] >= d->dt)) return nm + ": travel time must be finite and at least dt";
+    if (d->fl_tau[l] / d->dt > (double)(1 << 20)) return nm + ": travel time too large";
+    if (!std::isfinite(d->fl_y0[l]) || !(d->fl_y0[l] >= 0.0) || !std::isfinite(d->fl_a0[l]))
+      return nm + ": y0 must be finite and >= 0, a0 finite";
+    if (d->fl_ny[l] < 0 || d->fl_ny[l] > 4 || d->fl_na[l] < 0 || d->fl_na[l] > 4)
+      return nm + ": at most 4 poles each";
+    double geq = d->fl_y0[l];
+    for (int i = 0; i < d->fl_ny[l]; ++i) {
+      const double q = d->fl_yq[4 * l + i], r = d->fl_yc[4 * l + i];
+      if (!std::isfinite(q) || !(q < 0.0) || !std::isfinite(r)) return nm + ": poles must be finite and < 0";
+      geq += r * (d->dt / 2.0) / (1.0 - q * d->dt / 2.0);
+    }
+    for (int i = 0; i < d->fl_na[l]; ++i)
+      if (!std::isfinite(d->fl_ap[4 * l + i]) || !(d->fl_ap[4 * l + i] < 0.0) || !std::isfinite(d->fl_ar[4 * l + i]))
+        return nm + ": poles must be finite and < 0";
+    if (!(geq > 0.0)) return nm + ": its end conductance y0 + sum mu must be > 0";
   }
   if (d->n_cblocks < 0 || d->n_cinj < 0) return "negative count";
   if (d->n_cblocks && (!d->cb_type || !d->cb_in0 || !d->cb_in1 || !d->cb_node || !d->cb_p0 || !d->cb_p1))
@@ -843,7 +872,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
 
   // -------- line ends: end 2l at ln_k, end 2l+1 at ln_m; ring depth 2d
   std::vector<int64_t> ring_off(2 * d->n_lines);
-  std::vector<int64_t> cl_ring, cl_d;
+  std::vector<int64_t> cl_ring, cl_d, fl_ring;
   {
     int64_t off = 0;
     for (int64_t l = 0; l < d->n_lines; ++l) {
@@ -865,11 +894,23 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
           off += 2 * dd;
         }
       }
+    // frequency-dependent lines: one ring per end, depth 2 floor(tau / dt)
+    fl_ring.assign(2 * d->n_fdlines, 0);
+    for (int64_t l = 0; l < d->n_fdlines; ++l) {
+      const int64_t dd = (int64_t)std::floor(d->fl_tau[l] / d->dt);
+      for (int e = 0; e < 2; ++e) {
+        fl_ring[2 * l + e] = off;
+        off += 2 * dd;
+      }
+    }
     c->ring_len = off;
   }
   std::vector<std::vector<int64_t>> cends_of(S);   // coupled ends (2 l + e) per subsystem
   for (int64_t x = 0; x < 2 * d->n_clines; ++x)
     cends_of[c->sub_of_node[(x & 1) ? d->cl_m[3 * (x >> 1)] : d->cl_k[3 * (x >> 1)]]].push_back(x);
+  std::vector<std::vector<int64_t>> fends_of(S);   // frequency-dependent ends (2 l + e) per subsystem
+  for (int64_t x = 0; x < 2 * d->n_fdlines; ++x)
+    fends_of[c->sub_of_node[(x & 1) ? d->fl_m[x >> 1] : d->fl_k[x >> 1]]].push_back(x);
   std::vector<std::vector<int64_t>> ends_of(S);
   std::vector<int64_t> le_of_end(2 * d->n_lines, -1);
   for (int64_t e = 0; e < 2 * d->n_lines; ++e) {
@@ -887,6 +928,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       LineEndDev le{};
       le.node = local[node];
       le.ce = -1;
+      le.fd = -1;
       le.d = d->ln_delay[l];
       le.depth = 2 * d->ln_delay[l];
       le.y = 1.0 / d->ln_zc[l];
@@ -918,6 +960,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       for (int j = 0; j < 3; ++j) {
         LineEndDev le{};
         le.node = -1;
+        le.fd = -1;
         le.d = (int32_t)cl_d[3 * l + j];
         le.depth = 2 * le.d;
         le.ce = ce_local;
@@ -936,6 +979,53 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     }
     sd.n_ce = (int)c->cends.size() - sd.ce_off;
     c->lim.ce = std::max(c->lim.ce, sd.n_ce);
+    // frequency-dependent line ends: a line end each (the ring carries w)
+    // and a record with the discretised pole terms
+    sd.fd_off = (int)c->fdends.size();
+    for (int64_t x : fends_of[s]) {
+      const int64_t l = x >> 1;
+      const int e = (int)(x & 1);
+      const double dt = d->dt, steps = d->fl_tau[l] / dt;
+      FdEndDev r{};
+      r.ny = d->fl_ny[l];
+      r.na = d->fl_na[l];
+      r.y0 = d->fl_y0[l];
+      r.a0 = d->fl_a0[l];
+      double geq = r.y0;
+      for (int i = 0; i < r.ny; ++i) {
+        const double q = d->fl_yq[4 * l + i], den = 1.0 - q * dt / 2.0;
+        r.lam_y[i] = (1.0 + q * dt / 2.0) / den;
+        r.mu_y[i] = d->fl_yc[4 * l + i] * (dt / 2.0) / den;
+        r.mu_sum += r.mu_y[i];
+        geq += r.mu_y[i];
+      }
+      for (int i = 0; i < r.na; ++i) {
+        const double p = d->fl_ap[4 * l + i], den = 1.0 - p * dt / 2.0;
+        r.lam_a[i] = (1.0 + p * dt / 2.0) / den;
+        r.mu_a[i] = d->fl_ar[4 * l + i] * (dt / 2.0) / den;
+      }
+      r.le = (int)c->line_ends.size() - sd.le_off;
+      LineEndDev le{};
+      le.node = local[e ? d->fl_m[l] : d->fl_k[l]];
+      le.ce = -1;
+      le.fd = (int)c->fdends.size() - sd.fd_off;
+      le.d = (int32_t)std::floor(steps);
+      le.depth = 2 * le.d;
+      le.f = steps - (double)le.d;
+      le.y = geq;
+      le.y2 = 0.0;
+      le.own_ring = fl_ring[2 * l + e];
+      le.far_ring = fl_ring[2 * l + 1 - e];
+      c->fdends.push_back(r);
+      c->line_ends.push_back(le);
+      const int fs = c->sub_of_node[e ? d->fl_k[l] : d->fl_m[l]];
+      if (fs != s) {
+        auto it = dmin.find(fs);
+        if (it == dmin.end() || it->second > le.d) dmin[fs] = le.d;
+      }
+    }
+    sd.n_fd = (int)c->fdends.size() - sd.fd_off;
+    c->lim.fd = std::max(c->lim.fd, sd.n_fd);
     sd.n_le = (int)c->line_ends.size() - sd.le_off;
     c->lim.le = std::max(c->lim.le, sd.n_le);
     sd.nb_off = (int)c->nb_sub.size();
@@ -1102,9 +1192,14 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   for (int s = 0; s < S; ++s) {
     SubDev& sd = c->subs[s];
     std::vector<std::vector<int32_t>> el(sd.n);
-    const int ie_base = sd.n_lc + sd.n_sb, zero = ie_base + 2 * (sd.n_le + 3 * sd.n_ce);
+    const int ie_base = sd.n_lc + sd.n_sb, zero = ie_base + 2 * (sd.n_le + 3 * sd.n_ce + sd.n_fd);
     for (int x = 0; x < sd.n_ci; ++x)   // controlled currents enter their nodes
       el[ci_nodes_of[s][x]].push_back((int32_t)(zero + 1 + x));
+    for (int x = 0; x < sd.n_fd; ++x) {   // FD ends draw Hy - b
+      const int node = c->line_ends[sd.le_off + c->fdends[sd.fd_off + x].le].node;
+      el[node].push_back((int32_t)(ie_base + sd.n_le + 3 * sd.n_ce + x));
+      el[node].push_back((int32_t)(kEntryNeg | (uint32_t)(zero + 1 + sd.n_ci + x)));
+    }
     for (int b = sd.br_off; b < sd.br_off + sd.n_br; ++b) {
       const BranchDev& x = c->branches[b];
       if (x.kind != 0 && !strong[b]) {
@@ -1115,7 +1210,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       if (sb_slot_of[b] >= 0) el[x.k >= 0 ? x.k : x.m].push_back(sd.n_lc + sb_slot_of[b]);
     }
     for (int e = 0; e < sd.n_le; ++e)
-      if (c->line_ends[sd.le_off + e].node >= 0)
+      if (c->line_ends[sd.le_off + e].node >= 0 && c->line_ends[sd.le_off + e].fd < 0)
         el[c->line_ends[sd.le_off + e].node].push_back((int32_t)(kEntryNeg | (uint32_t)(ie_base + e)));
     for (int x = 0; x < sd.n_ce; ++x)   // coupled ends: phase-domain history currents leave the phase nodes
       for (int p = 0; p < 3; ++p)
@@ -1262,6 +1357,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   if (scen && !c->rswitches.empty()) return bail("runtime switches are not supported with a scenario set");
   if (scen && !c->cends.empty()) return bail("coupled lines are not supported with a scenario set");
   if (scen && (d->n_cblocks > 0 || d->n_cinj > 0)) return bail("control blocks are not supported with a scenario set");
+  if (scen && d->n_fdlines > 0) return bail("frequency-dependent lines are not supported with a scenario set");
   if (scen) {
     const std::string bm = build_scenarios(c, d, scen, local, new_of_orig, le_of_end, lc_slot_of, sb_slot_of);
     if (!bm.empty()) return bail(bm);
@@ -1289,6 +1385,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   UP(d_rs, rswitches)
   UP(d_ce, cends)
   UP(d_rs_word, rs_word0)
+  UP(d_fd, fdends)
   UP(d_cb, cblocks)
   UP(d_clay, clay)
   UP(d_cinj, cinj)
@@ -1304,6 +1401,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ginv_lo, (size_t)c->ginv_len);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_err, 4);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_rs_prev_i, c->rswitches.size());
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_fd_state, kFdState * c->fdends.size());
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_cstate, 2 * c->cblocks.size());
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_cy, c->cblocks.size());
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_le_prev, c->line_ends.size());
@@ -1597,6 +1695,8 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
   p.rs = c->d_rs;
   p.rs_word = c->d_rs_word;
   p.rs_prev_i = c->d_rs_prev_i;
+  p.fd = c->d_fd;
+  p.fd_state = c->d_fd_state;
   p.cb = c->d_cb;
   p.clay = c->d_clay;
   p.cinj = c->d_cinj;
@@ -1751,6 +1851,8 @@ extern "C" emt_status emt_reset(emt_ctx* c) {
     e = cudaMemset(c->d_rs_prev_i, 0, c->rswitches.size() * sizeof(double));
   if (e == cudaSuccess && !c->line_ends.empty())
     e = cudaMemset(c->d_le_prev, 0, c->line_ends.size() * sizeof(double));
+  if (e == cudaSuccess && !c->fdends.empty())
+    e = cudaMemset(c->d_fd_state, 0, kFdState * c->fdends.size() * sizeof(double));
   if (e == cudaSuccess && !c->cblocks.empty()) e = cudaMemset(c->d_cstate, 0, 2 * c->cblocks.size() * sizeof(double));
   if (e == cudaSuccess && !c->cblocks.empty()) e = cudaMemset(c->d_cy, 0, c->cblocks.size() * sizeof(double));
   if (c->batched) {
@@ -1884,6 +1986,7 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "n_strong_branches") *value = (int64_t)c->str_slot.size();
   else if (k == "n_runtime_switches") *value = (int64_t)c->rswitches.size();
   else if (k == "n_coupled_lines") *value = (int64_t)c->cends.size() / 2;
+  else if (k == "n_fd_lines") *value = (int64_t)c->fdends.size() / 2;
   else if (k == "n_control_blocks") *value = (int64_t)c->cblocks.size();
   else if (k == "n_control_injections") *value = (int64_t)c->cinj.size();
   else if (k == "max_control_layers") *value = c->max_clayers;
@@ -1921,6 +2024,7 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
   if (!c) return EMT_EINVAL;
   if (c->batched) return c->fail(EMT_EINVAL, "emt_adjoint: a context built with a scenario set has no adjoint");
   if (!c->cblocks.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: control blocks have no adjoint");
+  if (!c->fdends.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: frequency-dependent lines have no adjoint");
   if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
   if (n_steps < 1) return c->fail(EMT_EINVAL, "emt_adjoint: n_steps must be >= 1");
   if (n_steps > (int64_t)INT32_MAX - (int64_t)(1 << 21))

@@ -18,7 +18,10 @@ constexpr int kFwdThreads = 256;
 // entries of one shared-memory input vector
 //     inp = [ h (L/C slots) | g_b v_src (source-branch slots) |
 //             I_e parity 0 (line ends) | I_e parity 1 | 0 |
-//             controlled currents (one slot per control injection) ]
+//             controlled currents (one slot per control injection) |
+//             Hy of the frequency-dependent line ends ]
+// A parity block holds the line-end values, then the coupled ends' phase
+// currents, then the frequency-dependent ends' b values.
 // An entry is an int32: bit 31 = subtract, bits 0..30 = index into inp with
 // line ends addressed in their parity-0 block.  A node's entries are split
 // into "injection lanes" of 4 entries (padded with the trailing zero); the
@@ -57,8 +60,26 @@ struct LineEndDev {
   int64_t own_ring;    // first slot of this end's ring (values consumed here)
   int64_t far_ring;    // first slot of the far end's ring (values produced here)
   int32_t mode;        // mode index within its coupled end (0..2)
-  int32_t pad;
+  int32_t fd;          // frequency-dependent end (subsystem-local FdEndDev) or -1
   double f;            // fractional travel time: history = (1 - f) c(n - d) + f c(n - d - 1)
+};
+
+// One end of a frequency-dependent line (one conductor): Y_c = y0 +
+// sum c_i / (s - q_i) and A = e^{-s tau} (a0 + sum r_i / (s - p_i)), each
+// pole term discretised by the trapezoidal rule, x(n) = lam x(n-1) +
+// mu (u(n) + u(n-1)).  The end is a line end (node, rings, d, f) that
+// stamps G_eq = y0 + sum mu_y and whose ring carries the far end's
+//   w(m) = 2 yc(m) - b(m),  yc = y0 v + sum s_i  (s_i: Y_c's terms of v),
+// while its own history is b(n) = a0 W(n) + sum z_i(n) (z_i: A's terms of
+// W), W(n) = (1 - f) w(n - d) + f w(n - d - 1).  It draws the current
+// G_eq v(n) + Hy(n) - b(n), Hy(n) = sum (lam_y s_i(n-1) + mu_y v(n-1)).
+struct FdEndDev {
+  int32_t le;          // subsystem-local line end
+  int32_t ny, na;      // pole counts (<= 4)
+  int32_t pad;
+  double y0, a0;
+  double mu_sum;       // sum of mu_y: G_eq - y0
+  double lam_y[4], mu_y[4], lam_a[4], mu_a[4];
 };
 
 // One end of a coupled three-phase lossless line in modal form.  Its three
@@ -102,6 +123,7 @@ struct SubDev {
   int32_t cb_off, n_cb;        // control blocks (CtrlDev list, by layer)
   int32_t clay_off, n_clay;    // control layers: n_clay + 1 starts in clay (with the layer's type, see kLayerTypeShift)
   int32_t ci_off, n_ci;        // control injections: local block slot per injection in cinj
+  int32_t fd_off, n_fd;        // frequency-dependent line ends (FdEndDev list)
 };
 
 // A control block in device form (subsystem-local, ordered by layer).  The
@@ -165,6 +187,7 @@ struct FwdLimits {
   int32_t nbuf;                // solve-matrix buffers in shared memory: 1, or 2 (the last two states kept)
   int32_t ce;                  // coupled line ends per subsystem
   int32_t cb, clay, ci;        // control blocks, layers + 1 and injections per subsystem
+  int32_t fd;                  // frequency-dependent line ends per subsystem
 };
 
 struct FwdParams {
@@ -210,7 +233,11 @@ struct FwdParams {
   const int32_t* cinj;         // local block slot per control injection (SubDev ci_off / n_ci)
   double* cstate;              // per control block: two states (s0, s1)
   double* cy;                  // per control block: output of the last step (carried across launches)
+  const FdEndDev* fd;          // frequency-dependent line ends (SubDev fd_off / n_fd)
+  double* fd_state;            // per FD end: s[4], z[4], v(n-1), W(n-1), Hy(n) (11 doubles, carried)
 };
+
+constexpr int kFdState = 11;
 
 struct PrefParams {
   int32_t n_mats;

@@ -316,10 +316,11 @@ constexpr int kItemThreads = kFwdThreads - 32;
 // rows are stored with an odd stride (n | 1) so that the rows a warp reads
 // together fall in different banks.
 struct FwdSmem {
-  size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar, lef, imode, ceti, cetinv, cbr, cy, cs;   // 8-byte
+  size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar, lef, imode, ceti, cetinv, cbr, cy, cs, fdr,
+      fdst;                                                                                // 8-byte
   size_t gilo, ivf, partf;                                                                 // float
   size_t lck, lcm, lckind, lcstr, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, recp,
-      lece, lemode, cele0, cenode, clay, cinj;                                             // int
+      lece, lemode, cele0, cenode, clay, cinj, lefd;                                       // int
   size_t bytes;
 };
 
@@ -335,7 +336,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.part = d((size_t)L.n * L.q);
   s.iv = d(L.nc);
   s.vv = d(L.n);
-  s.inp = d((size_t)L.lc + L.sb + 2 * ((size_t)L.le + 3 * (size_t)L.ce) + 1 + (size_t)L.ci);
+  s.inp = d((size_t)L.lc + L.sb + 2 * ((size_t)L.le + 3 * (size_t)L.ce + L.fd) + 1 + (size_t)L.ci + L.fd);
   s.vs = d(2 * (size_t)L.src);
   s.lce = d(L.lc);
   s.sbg = d(L.sb);
@@ -349,6 +350,8 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.cbr = d16(sizeof(CtrlDev) / 8 * (size_t)L.cb);
   s.cy = d16(2 * (size_t)L.cb + 2);
   s.cs = d16(2 * (size_t)L.cb);
+  s.fdr = d(sizeof(FdEndDev) / 8 * (size_t)L.fd);
+  s.fdst = d(kFdState * (size_t)L.fd);
   s.gilo = w(nbuf * (size_t)L.n * ldg);
   s.ivf = w(L.nc);
   s.partf = w((size_t)L.n * L.q);
@@ -373,6 +376,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.cenode = w(3 * (size_t)L.ce);
   s.clay = w(L.clay);
   s.cinj = w(L.ci);
+  s.lefd = w(L.le);
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
 }
@@ -468,6 +472,31 @@ __device__ __forceinline__ void control_slot(int b, int first, bool act, int lt,
   }
 }
 
+// Frequency-dependent line ends (poll warp, after collecting step m's
+// values into blk_new): W(m) interpolated like a mode, A's pole terms
+// z_i(m) = lam z_i(m-1) + mu (W(m) + W(m-1)), and b(m) = a0 W(m) + sum z_i
+// into the b slots that follow the coupled ends' phase slots.  st = the
+// ends' states (z at 4..7, W(m-1) at 9).
+__device__ void fold_fd(int lane, int n_fd, int b_base, const FdEndDev* fdr, double* st, const double* lef,
+                        const double* blk_old, double* blk_new) {
+  for (int x = lane; x < n_fd; x += 32) {
+    const FdEndDev& r = fdr[x];
+    const int e = r.le;
+    double* sx = st + kFdState * x;
+    const double W = fma(lef[e], blk_old[e], (1.0 - lef[e]) * blk_new[e]);
+    const double ws = W + sx[9];
+    double b = r.a0 * W;
+    for (int i = 0; i < r.na; ++i) {
+      const double z = fma(r.lam_a[i], sx[4 + i], r.mu_a[i] * ws);
+      sx[4 + i] = z;
+      b += z;
+    }
+    sx[9] = W;
+    blk_new[b_base + x] = b;
+  }
+  __syncwarp();
+}
+
 // One warp collects one step's line-end histories I_e(n) from the tagged
 // rings.  Bounded: on exceeding the time budget (or seeing another CTA's
 // error) it latches an error and returns false.
@@ -551,6 +580,9 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   double* cs = reinterpret_cast<double*>(smem_raw + L.cs);          // [cb][2]: block states
   int* clay = reinterpret_cast<int*>(smem_raw + L.clay);            // layer starts and types
   int* cinj = reinterpret_cast<int*>(smem_raw + L.cinj);            // block slot per control injection
+  FdEndDev* fdr = reinterpret_cast<FdEndDev*>(smem_raw + L.fdr);   // frequency-dependent line ends
+  double* fdst = reinterpret_cast<double*>(smem_raw + L.fdst);      // their states (kFdState each)
+  int* lefd = reinterpret_cast<int*>(smem_raw + L.lefd);            // per line end: FD end or -1
 
   const int sidx = blockIdx.x;
   const SubDev S = P.sub[sidx];
@@ -559,10 +591,13 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   const int blk = (nc + Q - 1) / Q;   // columns per matvec task
   const int n_lc = S.n_lc, n_sb = S.n_sb, n_le = S.n_le, n_il = S.n_il, n_ce = S.n_ce;
   const int ie_base = n_lc + n_sb;
-  const int blk_len = n_le + 3 * n_ce;   // per parity: line-end values, then coupled ends' phase currents
+  const int n_fd = S.n_fd;
+  const int fd_base = n_le + 3 * n_ce;   // b values of the FD ends within a parity block
+  const int blk_len = n_le + 3 * n_ce + n_fd;   // per parity: line-end values, coupled phase currents, FD b
   const int zero_slot = ie_base + 2 * blk_len;
   const int ci_base = zero_slot + 1;   // controlled currents
   const int n_cb = S.n_cb, n_clay = S.n_clay, n_ci = S.n_ci;
+  const int hy_base = ci_base + n_ci;   // Hy of the FD ends
   // with control blocks the warp before the poll warp evaluates them in the
   // update phase, layer by layer; the update items take the other warps
   const int item_threads = n_cb > 0 ? kItemThreads - 32 : kItemThreads;
@@ -604,6 +639,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     lef[x] = e.f;
     lece[x] = e.ce;
     lemode[x] = e.mode;
+    lefd[x] = e.fd;
     // the value consumed at step n0 - 1 (for interpolated modal histories)
     inp[ie_base + (int)((P.n0 - 1) & 1) * blk_len + x] = P.le_prev[S.le_off + x];
   }
@@ -628,6 +664,11 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     const int b = P.cinj[S.ci_off + x];
     cinj[x] = b;
     inp[ci_base + x] = P.cy[S.cb_off + b];   // the last step's output drives this step
+  }
+  for (int x = tid; x < n_fd; x += T) {
+    fdr[x] = P.fd[S.fd_off + x];
+    for (int k = 0; k < kFdState; ++k) fdst[kFdState * x + k] = P.fd_state[kFdState * (size_t)(S.fd_off + x) + k];
+    inp[hy_base + x] = P.fd_state[kFdState * (size_t)(S.fd_off + x) + 10];
   }
   for (int r = tid; r < n; r += T) recp[r] = P.rec != nullptr ? P.rec_pos[S.node_off + r] : -1;
   for (int x = tid; x < 4 * n_il; x += T) ent[x] = P.ent[4 * (size_t)S.il_off + x];
@@ -685,6 +726,8 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     if (n_ce > 0)
       fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + (p0 ^ 1) * blk_len, inp + ie_base + p0 * blk_len,
                  imode + p0 * lv, cele0, ceti);
+    if (n_fd > 0)
+      fold_fd(lane, n_fd, fd_base, fdr, fdst, lef, inp + ie_base + (p0 ^ 1) * blk_len, inp + ie_base + p0 * blk_len);
   }
   // control layer starts 0..31 in the control warp's registers (lane l)
   int lay_reg = 0;
@@ -811,6 +854,9 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
         if (n_ce > 0)
           fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + par * blk_len,
                      inp + ie_base + (par ^ 1) * blk_len, imode + (par ^ 1) * lv, cele0, ceti);
+        if (n_fd > 0)
+          fold_fd(lane, n_fd, fd_base, fdr, fdst, lef, inp + ie_base + par * blk_len,
+                  inp + ie_base + (par ^ 1) * blk_len);
       }
     } else if (n_cb > 0 && warp == kPollWarp - 1) {
       // control blocks at this step, one layer after another; then the
@@ -860,8 +906,24 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
         } else if (it >= it_le && it < it_le + n_le) {
           const int e = it - it_le;
           double out;
-          const int c = lece[e];
-          if (c < 0) {
+          const int c = lece[e], fx = lefd[e];
+          if (fx >= 0) {   // frequency-dependent end: Y_c's terms of v, then w = 2 yc - b
+            const FdEndDev& r = fdr[fx];
+            double* sx = fdst + kFdState * fx;
+            const double v = vv[lenode[e]], vsum = v + sx[8];
+            double yc = r.y0 * v, lam_s = 0.0;
+            for (int i = 0; i < r.ny; ++i) {
+              const double si = fma(r.lam_y[i], sx[i], r.mu_y[i] * vsum);
+              sx[i] = si;
+              yc += si;
+              lam_s = fma(r.lam_y[i], si, lam_s);
+            }
+            out = fma(2.0, yc, -ie_cur[fd_base + fx]);
+            sx[8] = v;
+            const double hy = fma(r.mu_sum, v, lam_s);   // Hy(n+1)
+            sx[10] = hy;
+            inp[hy_base + fx] = hy;
+          } else if (c < 0) {
             out = fma(-ley2[e], vv[lenode[e]], -ie_cur[e]);
           } else {   // a mode: c_j = -(2/Z_j) (T_v^-1 v_p)_j - I_mode_j(n)
             const double* tr = cetinv + 9 * c + 3 * lemode[e];
@@ -886,6 +948,9 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       for (int x = tid; x < n_le; x += T)
         P.le_prev[S.le_off + x] = inp[ie_base + (int)((n_end - 1) & 1) * blk_len + x];
     for (int x = tid; x < n_rs; x += T) P.rs_prev_i[S.rs_off + x] = s_rsi[x];
+    if (P.n_steps > 0)   // (the prologue advanced A's terms to step n0, which a launch of 0 steps never ran)
+      for (int x = tid; x < n_fd; x += T)
+        for (int k = 0; k < kFdState; ++k) P.fd_state[kFdState * (size_t)(S.fd_off + x) + k] = fdst[kFdState * x + k];
     for (int x = tid; x < n_cb; x += T) {
       P.cstate[2 * (size_t)(S.cb_off + x)] = cs[2 * x];
       P.cstate[2 * (size_t)(S.cb_off + x) + 1] = cs[2 * x + 1];

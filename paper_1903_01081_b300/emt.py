@@ -51,6 +51,10 @@ class _NetworkDesc(ctypes.Structure):
         ("cb_in1", ctypes.c_void_p), ("cb_node", ctypes.c_void_p), ("cb_p0", ctypes.c_void_p),
         ("cb_p1", ctypes.c_void_p),
         ("n_cinj", ctypes.c_int64), ("ci_block", ctypes.c_void_p), ("ci_node", ctypes.c_void_p),
+        ("n_fdlines", ctypes.c_int64), ("fl_k", ctypes.c_void_p), ("fl_m", ctypes.c_void_p),
+        ("fl_tau", ctypes.c_void_p), ("fl_y0", ctypes.c_void_p), ("fl_ny", ctypes.c_void_p),
+        ("fl_yq", ctypes.c_void_p), ("fl_yc", ctypes.c_void_p), ("fl_a0", ctypes.c_void_p),
+        ("fl_na", ctypes.c_void_p), ("fl_ap", ctypes.c_void_p), ("fl_ar", ctypes.c_void_p),
     ]
 
 
@@ -177,6 +181,13 @@ def network_desc(net, keep: list) -> _NetworkDesc:
     d.cb_p0, d.cb_p1 = p(rs("cb_p0", np.float64), np.float64), p(rs("cb_p1", np.float64), np.float64)
     d.n_cinj = int(len(rs("ci_block", np.int32)))
     d.ci_block, d.ci_node = p(rs("ci_block", np.int32), np.int32), p(rs("ci_node", np.int32), np.int32)
+    d.n_fdlines = int(len(rs("fl_k", np.int32)))
+    d.fl_k, d.fl_m = p(rs("fl_k", np.int32), np.int32), p(rs("fl_m", np.int32), np.int32)
+    d.fl_tau, d.fl_y0 = p(rs("fl_tau", np.float64), np.float64), p(rs("fl_y0", np.float64), np.float64)
+    d.fl_ny, d.fl_na = p(rs("fl_ny", np.int32), np.int32), p(rs("fl_na", np.int32), np.int32)
+    d.fl_yq, d.fl_yc = p(rs("fl_yq", np.float64), np.float64), p(rs("fl_yc", np.float64), np.float64)
+    d.fl_a0 = p(rs("fl_a0", np.float64), np.float64)
+    d.fl_ap, d.fl_ar = p(rs("fl_ap", np.float64), np.float64), p(rs("fl_ar", np.float64), np.float64)
     return d
 
 

@@ -149,3 +149,24 @@ def test_rejects_bad_controls():
     ctl = g.with_converter_controls(sc_net, n_converters=2)
     with pytest.raises(emt.EmtError, match="control blocks are not supported"):
         emt.emt_build_network(ctl, sc)
+
+
+def test_rejects_bad_fd_lines():
+    net = g.with_fd_lines(g.multi_subsystem(21, [4, 5, 3, 6], n_lines=6, n_sources=3, dt=20e-6))
+    assert "at least dt" in bad(net, fl_tau=np.full_like(net.fl_tau, 0.5 * net.dt))
+    ny = net.fl_ny.copy(); ny[0] = 5
+    assert "at most 4" in bad(net, fl_ny=ny)
+    q = net.fl_yq.copy(); q[0] = 1.0
+    assert "< 0" in bad(net, fl_yq=q)
+    ap = net.fl_ap.copy(); ap[1] = np.nan
+    assert "< 0" in bad(net, fl_ap=ap)
+    assert "y0" in bad(net, fl_y0=-net.fl_y0)
+    m = net.fl_m.copy(); m[0] = net.fl_k[0]
+    assert "one node" in bad(net, fl_m=m)
+    k = net.fl_k.copy(); k[0] = -1
+    assert "unknown nodes" in bad(net, fl_k=k)
+    y0 = np.zeros_like(net.fl_y0); ny0 = np.zeros_like(net.fl_ny)
+    assert "end conductance" in bad(net, fl_y0=y0, fl_ny=ny0)
+    sc_net, sc = g.n1_contingency(n_scenarios=4, n_buses=24, n_sub=4, n_steps=10)
+    with pytest.raises(emt.EmtError, match="frequency-dependent lines are not supported"):
+        emt.emt_build_network(g.with_fd_lines(sc_net), sc)
