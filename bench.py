@@ -24,10 +24,15 @@ two further legs the metric names, reported as extra keys of the line:
   "runtime_switches": the large-scale network with 30 diode-rectifier loads
       and 10 current-zero breakers, against the same network without them;
   "coupled_lines": the large-scale network with its three-phase lines as
-      coupled modal lines with interpolated travel times, against the plain one.
+      coupled modal lines with interpolated travel times, against the plain one;
+  "fd_lines": the same with its line conductors as lossy frequency-dependent
+      lines, against the plain one;
+  "controls": the same with 180 converter loads (4,320 layered control
+      blocks driving controlled current injections), against the plain one.
 
-N > 1 runs N independent replicas (the single-network path does not shard;
-see the design doc), launched by torch.distributed.run.  `--impl reference`
+N > 1 runs N independent replicas (the single-network path does not shard:
+its subsystems exchange line values every few steps), launched by
+torch.distributed.run.  `--impl reference`
 times the plain CPU oracle (test infrastructure) on a bounded sample of the
 same workload.
 """
@@ -150,7 +155,7 @@ class ClockSampler:
 
 
 def algorithmic_flops_per_step(net, sim) -> float:
-    """FP64 operations the method needs per time step (see DESIGN.md):
+    """FP64 operations the method needs per time step:
     dense solve 2 n_s^2 per subsystem, plus 1 add per injection term (two
     per L/C branch, one per source branch and line end), 3 per L/C branch
     history update, 2 per line-end output, 1 per source-branch injection."""
@@ -469,6 +474,7 @@ def run_ours(args):
     w = sim.waveforms(n_rows=min(2000, N_STEPS))[:, 0, :]
     flops = algorithmic_flops_per_step(net, sim) * N_STEPS
     n_sub = sim.info("n_subsystems")
+    n_max = sim.info("max_subsystem_nodes")
     sim.close()
 
     if args.skip_extras:
@@ -524,7 +530,12 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                          "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
                          "kernel": "fwd_kernel (+ source_kernel, <0.5% of the time)",
-                         "peak_source": "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz"},
+                         "peak_source": "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz",
+                         # the step cannot end before the largest subsystem's dense solve (2 n^2 flop) has run
+                         # on its one SM: that SM's share of the FP64 peak against the measured step time
+                         "critical_path_sm_frac": (2.0 * n_max * n_max) / (per_launch_s / N_STEPS)
+                                                  / (FP64_PEAK_GFLOPS / 148 * 1e9),
+                         "critical_path": f"2 n^2 flop of the largest subsystem (n = {n_max}) per step on one SM"},
             "cpu_baseline": cpu_baseline(net, N_STEPS),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(N_STEPS * n * 8)},
