@@ -235,7 +235,33 @@ def scenario_leg(name, net, sc, n_steps, n_check, rec_channels, decim, tune_step
     return out
 
 
-def scenario_legs(which=("n1", "shared_g"), steps=None, shape=None, warm=500):
+def _oracle_scenario(args):
+    """One scenario on the CPU oracle (a spawn-pool worker): seconds taken."""
+    net, sc, s_, n = args
+    import oracle
+    t0 = time.perf_counter()
+    oracle.simulate(sc.expand(net, s_), n, rec=np.zeros(1, np.int32))
+    return time.perf_counter() - t0
+
+
+def oracle_scenario_baseline(net, sc, n_scen, n_steps):
+    """The CPU oracle as it stands on the first `n_scen` scenarios of a study,
+    `n_steps` steps each, one scenario per process over the host's cores (a
+    spawn pool: the parent already holds a CUDA context).  The rate divides
+    the scenario-steps by the busy time per core (pool start-up excluded)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    workers = max(1, min(os.cpu_count() or 1, n_scen))
+    # an executor, not a Pool: a worker that dies raises here instead of hanging
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        secs = list(ex.map(_oracle_scenario, [(net, sc, s_, n_steps) for s_ in range(n_scen)], timeout=600))
+    total = float(sum(secs))
+    return {"value": n_scen * n_steps / (total / workers), "unit": "scenario-steps/s", "cores": workers,
+            "kind": "oracle", "single_thread_value": n_scen * n_steps / total,
+            "sample": f"scenarios 0..{n_scen - 1}, {n_steps} steps each, one process per core"}
+
+
+def scenario_legs(which=("n1", "shared_g"), steps=None, shape=None, warm=500, cpu=False):
     from paper_1903_01081_b300 import netgen as g
     out = {}
     if "n1" in which:
@@ -243,12 +269,16 @@ def scenario_legs(which=("n1", "shared_g"), steps=None, shape=None, warm=500):
         n1 = scenario_leg("n1", net, sc, steps or 10000, 4, None, 100, 100, warm, shape)
         out["n1_contingency"] = dict(workload="N-1: 600-node three-phase network, 40 subsystems, one connection "
                                               "removed + three-phase fault at step 2,500 per scenario", **n1)
+        if cpu:
+            out["n1_contingency"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 32, 3000)
     if "shared_g" in which:
         net, sc = g.shared_g()
         sg = scenario_leg("shared_g", net, sc, steps or 3000, 2, list(range(0, net.n_nodes, 50)), 10, 20, warm,
                           shape)
         out["shared_g"] = dict(workload="large-scale network, per-scenario source amplitude/phase and fault "
                                         "resistance at step 2,500; 3,000 of 10,000 steps timed", **sg)
+        if cpu:
+            out["shared_g"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 16, 3000)
     return out
 
 
@@ -542,7 +572,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
             "parity_rel_err_first_2000_steps": parity,
-            **({"scenarios": scenario_legs(), "adjoint": adjoint_leg(), "runtime_switches": runtime_switch_leg(),
+            **({"scenarios": scenario_legs(cpu=True), "adjoint": adjoint_leg(), "runtime_switches": runtime_switch_leg(),
                 "coupled_lines": coupled_line_leg(), "fd_lines": fd_line_leg(), "controls": control_leg()}
                if args.leg == "all" else {}),
         }
