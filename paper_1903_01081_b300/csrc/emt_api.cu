@@ -1012,6 +1012,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
       le.d = (int32_t)std::floor(steps);
       le.depth = 2 * le.d;
       le.f = steps - (double)le.d;
+      r.omf = 1.0 - le.f;
       le.y = geq;
       le.y2 = 0.0;
       le.own_ring = fl_ring[2 * l + e];

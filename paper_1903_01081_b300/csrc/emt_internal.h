@@ -79,6 +79,7 @@ struct FdEndDev {
   int32_t pad;
   double y0, a0;
   double mu_sum;       // sum of mu_y: G_eq - y0
+  double omf;          // 1 - f of its line end (interpolation weight of w(n - d))
   double lam_y[4], mu_y[4], lam_a[4], mu_a[4];
 };
 

@@ -306,8 +306,9 @@ __global__ void ring_init_kernel(RingInitParams P) {
 // count of the busiest warp small: four-entry injection lanes joined by
 // shuffles, one FMA chain per matvec task over a contiguous block of
 // columns (plus a single-precision chain for X_lo), node sums in their own
-// phase, and update items of one kind per warp.  The last warp only
-// collects the next step's line values.
+// phase, and update items of one kind per warp.  The next step's line
+// values are collected by the update threads once their items are done, one
+// thread per line end (per coupled end), so that all waits run at once.
 
 constexpr int kPollWarp = kFwdThreads / 32 - 1;
 constexpr int kItemThreads = kFwdThreads - 32;
@@ -320,7 +321,7 @@ struct FwdSmem {
       fdst;                                                                                // 8-byte
   size_t gilo, ivf, partf;                                                                 // float
   size_t lck, lcm, lckind, lcstr, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, recp,
-      lece, lemode, cele0, cenode, clay, cinj, lefd;                                       // int
+      lece, lemode, cele0, cenode, clay, cinj, lefd, cecnt;                                // int
   size_t bytes;
 };
 
@@ -377,6 +378,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.clay = w(L.clay);
   s.cinj = w(L.ci);
   s.lefd = w(L.le);
+  s.cecnt = w(L.ce);
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
 }
@@ -472,59 +474,76 @@ __device__ __forceinline__ void control_slot(int b, int first, bool act, int lt,
   }
 }
 
-// Frequency-dependent line ends (poll warp, after collecting step m's
-// values into blk_new): W(m) interpolated like a mode, A's pole terms
-// z_i(m) = lam z_i(m-1) + mu (W(m) + W(m-1)), and b(m) = a0 W(m) + sum z_i
-// into the b slots that follow the coupled ends' phase slots.  st = the
-// ends' states (z at 4..7, W(m-1) at 9).
-__device__ void fold_fd(int lane, int n_fd, int b_base, const FdEndDev* fdr, double* st, const double* lef,
-                        const double* blk_old, double* blk_new) {
-  for (int x = lane; x < n_fd; x += 32) {
-    const FdEndDev& r = fdr[x];
-    const int e = r.le;
-    double* sx = st + kFdState * x;
-    const double W = fma(lef[e], blk_old[e], (1.0 - lef[e]) * blk_new[e]);
-    const double ws = W + sx[9];
-    double b = r.a0 * W;
-    for (int i = 0; i < r.na; ++i) {
-      const double z = fma(r.lam_a[i], sx[4 + i], r.mu_a[i] * ws);
-      sx[4 + i] = z;
-      b += z;
-    }
-    sx[9] = W;
-    blk_new[b_base + x] = b;
+// A frequency-dependent line end's history at step m, folded by the poll
+// lane that just collected its ring value w_far(m - d) (so the fold of an
+// early value hides behind the wait for a late one): W(m) interpolated like
+// a mode, A's pole terms z_i(m) = lam z_i(m-1) + mu (W(m) + W(m-1)), and
+// b(m) = a0 W(m) + sum z_i into its b slot.  sx = the end's states (z at
+// 4..7, W(m-1) at 9).
+struct FdFold {
+  const int* lefd;          // per line end: FD end or -1 (nullptr: none in this subsystem)
+  const FdEndDev* fdr;
+  double* fdst;
+  const double* lef;
+  const double* blk_old;    // the previous step's collected values
+  int b_base;               // first b slot in the parity block
+};
+
+__device__ __forceinline__ void fold_fd_end(const FdFold& F, int e, double w_new, double* blk_new) {
+  const int x = F.lefd[e];
+  if (x < 0) return;
+  const FdEndDev& r = F.fdr[x];
+  double* sx = F.fdst + kFdState * x;
+  const double W = fma(F.lef[e], F.blk_old[e], r.omf * w_new);
+  const double ws = W + sx[9];
+  double zsum = 0.0;
+  for (int i = 0; i < r.na; ++i) {
+    const double z = fma(r.lam_a[i], sx[4 + i], r.mu_a[i] * ws);
+    sx[4 + i] = z;
+    zsum = i == 0 ? z : zsum + z;
   }
-  __syncwarp();
+  sx[9] = W;
+  blk_new[F.b_base + x] = fma(r.a0, W, zsum);
 }
 
 // One warp collects one step's line-end histories I_e(n) from the tagged
 // rings.  Bounded: on exceeding the time budget (or seeing another CTA's
 // error) it latches an error and returns false.
-__device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int lane, int sidx, const long long* leown,
-                              const int* ledepth, int* rslot, double* ie) {
-  bool ok = true;
-  for (int e = lane; e < n_le && ok; e += 32) {
-    const unsigned long long* slot = P.ring + 2 * (leown[e] + rslot[e]);
-    double v = 0.0;
-    if (!ld_tagged(slot, tag, v)) {
-      const unsigned long long t0 = global_ns();
-      unsigned spins = 0;
-      while (!ld_tagged(slot, tag, v)) {
-        if ((++spins & 31u) == 0) {
-          if (ld_volatile(P.err) != 0) { ok = false; break; }
-          if (global_ns() - t0 > P.wait_budget_ns || spins > (1u << 30)) {
-            if (atomicCAS(P.err, 0, 5) == 0) {
-              P.err[1] = sidx;
-              P.err[2] = e;
-              P.err[3] = (int)tag;
-            }
-            ok = false;
-            break;
-          }
+// Wait for a ring slot to carry `tag` and return its value.  Bounded: on
+// exceeding the time budget (or seeing another CTA's error) it latches an
+// error {5, subsystem, line end, tag} and returns false.
+__device__ __forceinline__ bool poll_slot(const FwdParams& P, const unsigned long long* slot, unsigned tag, int sidx,
+                                          int e, double& v) {
+  if (ld_tagged(slot, tag, v)) return true;
+  const unsigned long long t0 = global_ns();
+  unsigned spins = 0;
+  while (!ld_tagged(slot, tag, v)) {
+    if ((++spins & 31u) == 0) {
+      if (ld_volatile(P.err) != 0) return false;
+      if (global_ns() - t0 > P.wait_budget_ns || spins > (1u << 30)) {
+        if (atomicCAS(P.err, 0, 5) == 0) {
+          P.err[1] = sidx;
+          P.err[2] = e;
+          P.err[3] = (int)tag;
         }
+        return false;
       }
     }
+  }
+  return true;
+}
+
+// One warp collects the values of step `tag` of every line end (the first
+// step of a launch; frequency-dependent ends folded on arrival).
+__device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int lane, int sidx, const long long* leown,
+                              const int* ledepth, int* rslot, double* ie, const FdFold& F) {
+  bool ok = true;
+  for (int e = lane; e < n_le && ok; e += 32) {
+    const bool fd = F.lefd != nullptr && F.lefd[e] >= 0;
+    double v = 0.0;
+    ok = poll_slot(P, P.ring + 2 * (leown[e] + rslot[e]), tag, sidx, e, v);
     ie[e] = v;
+    if (ok && fd) fold_fd_end(F, e, v, ie);
     const int nx = rslot[e] + 1;
     rslot[e] = nx == ledepth[e] ? 0 : nx;
   }
@@ -583,6 +602,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   FdEndDev* fdr = reinterpret_cast<FdEndDev*>(smem_raw + L.fdr);   // frequency-dependent line ends
   double* fdst = reinterpret_cast<double*>(smem_raw + L.fdst);      // their states (kFdState each)
   int* lefd = reinterpret_cast<int*>(smem_raw + L.lefd);            // per line end: FD end or -1
+  int* cecnt = reinterpret_cast<int*>(smem_raw + L.cecnt);          // per coupled end: modes collected this step
 
   const int sidx = blockIdx.x;
   const SubDev S = P.sub[sidx];
@@ -645,6 +665,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   }
   for (int c = tid; c < n_ce; c += T) {
     const CoupledEndDev& ce = P.ce[S.ce_off + c];
+    cecnt[c] = 0;
     cele0[c] = ce.le0;
     for (int k = 0; k < 3; ++k) cenode[3 * c + k] = ce.node[k];
     for (int k = 0; k < 9; ++k) {
@@ -720,14 +741,13 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   }
   if (warp == kPollWarp && n_le > 0) {
     const int p0 = (int)(P.n0 & 1);
+    const FdFold F{n_fd > 0 ? lefd : nullptr, fdr, fdst, lef, inp + ie_base + (p0 ^ 1) * blk_len, fd_base};
     const bool ok = collect_lines(P, n_le, (unsigned)P.n0, lane, sidx, leown, ledepth, rslot,
-                                  inp + ie_base + p0 * blk_len);
+                                  inp + ie_base + p0 * blk_len, F);
     if (!ok && lane == 0) s_abort = 1;
     if (n_ce > 0)
       fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + (p0 ^ 1) * blk_len, inp + ie_base + p0 * blk_len,
                  imode + p0 * lv, cele0, ceti);
-    if (n_fd > 0)
-      fold_fd(lane, n_fd, fd_base, fdr, fdst, lef, inp + ie_base + (p0 ^ 1) * blk_len, inp + ie_base + p0 * blk_len);
   }
   // control layer starts 0..31 in the control warp's registers (lane l)
   int lay_reg = 0;
@@ -847,17 +867,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     // process 1: history currents, line outputs, next step's source
     // injections; the poll warp meanwhile collects next step's line values
     if (warp == kPollWarp) {
-      if (n_le > 0 && step + 1 < n_end) {
-        const bool ok = collect_lines(P, n_le, (unsigned)(step + 1), lane, sidx, leown, ledepth, rslot,
-                                      inp + ie_base + (par ^ 1) * blk_len);
-        if (!ok && lane == 0) s_abort = 1;
-        if (n_ce > 0)
-          fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + par * blk_len,
-                     inp + ie_base + (par ^ 1) * blk_len, imode + (par ^ 1) * lv, cele0, ceti);
-        if (n_fd > 0)
-          fold_fd(lane, n_fd, fd_base, fdr, fdst, lef, inp + ie_base + par * blk_len,
-                  inp + ie_base + (par ^ 1) * blk_len);
-      }
+      // (the update threads collect the next step's line values below)
     } else if (n_cb > 0 && warp == kPollWarp - 1) {
       // control blocks at this step, one layer after another; then the
       // controlled currents of the next step
@@ -911,13 +921,14 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
             const FdEndDev& r = fdr[fx];
             double* sx = fdst + kFdState * fx;
             const double v = vv[lenode[e]], vsum = v + sx[8];
-            double yc = r.y0 * v, lam_s = 0.0;
+            double ssum = 0.0, lam_s = 0.0;
             for (int i = 0; i < r.ny; ++i) {
               const double si = fma(r.lam_y[i], sx[i], r.mu_y[i] * vsum);
               sx[i] = si;
-              yc += si;
-              lam_s = fma(r.lam_y[i], si, lam_s);
+              ssum = i == 0 ? si : ssum + si;
+              lam_s = i == 0 ? r.lam_y[i] * si : fma(r.lam_y[i], si, lam_s);
             }
+            const double yc = fma(r.y0, v, ssum);
             out = fma(2.0, yc, -ie_cur[fd_base + fx]);
             sx[8] = v;
             const double hy = fma(r.mu_sum, v, lam_s);   // Hy(n+1)
@@ -938,6 +949,45 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
           const int x = it - it_sb;
           inp[n_lc + x] = sbg[x] * vs_next[sbsrc[x]];
         }
+      }
+      // next step's ring values: one update thread per line end, counted
+      // from the last thread (the first threads hold the update items), so
+      // that all waits run at once and the folds spread over several warps.
+      // A coupled end's phase currents are formed by whichever thread
+      // collects the last of its three modes.
+      if (n_le > 0 && step + 1 < n_end) {
+        const unsigned tag = (unsigned)(step + 1);
+        double* ie_old = inp + ie_base + par * blk_len;
+        double* ie_next = inp + ie_base + (par ^ 1) * blk_len;
+        double* imode_next = imode + (par ^ 1) * lv;
+        const FdFold F{n_fd > 0 ? lefd : nullptr, fdr, fdst, lef, ie_old, fd_base};
+        bool ok = true;
+        for (int e = item_threads - 1 - tid; e < n_le && ok; e += item_threads) {
+          double v = 0.0;
+          ok = poll_slot(P, P.ring + 2 * (leown[e] + rslot[e]), tag, sidx, e, v);
+          ie_next[e] = v;
+          const int nx = rslot[e] + 1;
+          rslot[e] = nx == ledepth[e] ? 0 : nx;
+          if (!ok) break;
+          const int c = lece[e];
+          if (c >= 0) {   // a mode: its interpolated history; the third of its end's modes forms T_i I_mode
+            imode_next[e] = fma(lef[e], ie_old[e], (1.0 - lef[e]) * v);
+            __threadfence_block();
+            if (atomicAdd(&cecnt[c], 1) == 2) {
+              __threadfence_block();
+              cecnt[c] = 0;
+              const volatile double* im = imode_next + cele0[c];
+              const double m0 = im[0], m1 = im[1], m2 = im[2];
+              for (int p = 0; p < 3; ++p) {
+                const double* ti = ceti + 9 * c + 3 * p;
+                ie_next[n_le + 3 * c + p] = fma(ti[0], m0, fma(ti[1], m1, ti[2] * m2));
+              }
+            }
+          } else if (F.lefd != nullptr) {
+            fold_fd_end(F, e, v, ie_next);
+          }
+        }
+        if (!ok) s_abort = 1;
       }
     }
     __syncthreads();
