@@ -46,7 +46,7 @@ struct AdjSmem {
       xmode, ceti, cetinv;                                                                               // 8-byte
   size_t gilo, ivf, partf;                                                                               // float
   size_t brk, brm, brlc, brkind, lcstr, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, orig, lece,
-      lemode, cele0, cenode;                                                                             // int
+      lemode, cele0, cenode, cecnt;                                                                      // int
   size_t bytes;
 };
 
@@ -101,6 +101,7 @@ __host__ __device__ inline AdjSmem adj_smem(const AdjLimits& L) {
   s.lece = w(L.le);
   s.lemode = w(L.le);
   s.cele0 = w(L.ce);
+  s.cecnt = w(L.ce);
   s.cenode = w(3 * (size_t)L.ce);
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
@@ -212,6 +213,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
   int* lece = reinterpret_cast<int*>(smem_raw + L.lece);
   int* lemode = reinterpret_cast<int*>(smem_raw + L.lemode);
   int* cele0 = reinterpret_cast<int*>(smem_raw + L.cele0);
+  int* cecnt = reinterpret_cast<int*>(smem_raw + L.cecnt);   // per coupled end: modes collected this step
   int* cenode = reinterpret_cast<int*>(smem_raw + L.cenode);
 
   const int sidx = blockIdx.x;
@@ -270,6 +272,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
   for (int c = tid; c < n_ce; c += T) {
     const CoupledEndDev& ce = P.ce[S.ce_off + c];
     cele0[c] = ce.le0;
+    cecnt[c] = 0;
     for (int k = 0; k < 3; ++k) cenode[3 * c + k] = ce.node[k];
     for (int k = 0; k < 9; ++k) {
       ceti[9 * c + k] = ce.ti[k];
@@ -433,17 +436,9 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
     }
     __syncthreads();
 
-    // parameter terms, hbar_{n-1}, Ibar_e(n); the poll warp collects step n-1's line values
-    if (warp == kAdjPollWarp) {
-      if (n_le > 0 && more) {
-        const bool ok = collect_adj(P, n_le, (unsigned)(tau + 1), lane, sidx, leown, ledepth, rslot, ley2,
-                                    xr + (par ^ 1) * lv, inp + ie_base + (par ^ 1) * blk_len);
-        if (!ok && lane == 0) s_abort = 1;
-        if (n_ce > 0)
-          fold_modes_adj(lane, n_le, n_ce, lece, lef, ley2, xr + par * lv, xr + (par ^ 1) * lv, xmode + (par ^ 1) * lv,
-                         inp + ie_base + (par ^ 1) * blk_len, cele0, ceti);
-      }
-    } else {
+    // parameter terms, hbar_{n-1}, Ibar_e(n); then the update threads
+    // collect step n-1's line values (the last warp idles)
+    if (warp != kAdjPollWarp) {
       const double* vnc = vn + par * nv;
       const double* vsc = vsrc + par * sv;
       for (int it = tid; it < it_end; it += kAdjItemThreads) {
@@ -494,6 +489,43 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
           const int nx = wslot[e] + 1;
           wslot[e] = nx == ledepth[e] ? 0 : nx;
         }
+      }
+      // one update thread per line end, counted from the last thread, as in
+      // the forward kernel; a coupled end's phase slots are formed by the
+      // thread that collects the last of its three modes
+      if (n_le > 0 && more) {
+        const unsigned tag = (unsigned)(tau + 1);
+        const double* xr_old = xr + par * lv;
+        double* xr_new = xr + (par ^ 1) * lv;
+        double* blk_new = inp + ie_base + (par ^ 1) * blk_len;
+        double* xmode_new = xmode + (par ^ 1) * lv;
+        bool ok = true;
+        for (int e = kAdjItemThreads - 1 - tid; e < n_le && ok; e += kAdjItemThreads) {
+          double v = 0.0;
+          ok = poll_slot(P, P.ring + 2 * (leown[e] + rslot[e]), tag, sidx, e, v);
+          xr_new[e] = v;
+          blk_new[e] = ley2[e] * v;
+          const int nx = rslot[e] + 1;
+          rslot[e] = nx == ledepth[e] ? 0 : nx;
+          if (!ok) break;
+          const int c = lece[e];
+          if (c >= 0) {
+            xmode_new[e] = fma(lef[e], xr_old[e], (1.0 - lef[e]) * v);
+            __threadfence_block();
+            if (atomicAdd(&cecnt[c], 1) == 2) {
+              __threadfence_block();
+              cecnt[c] = 0;
+              const int e0 = cele0[c];
+              const volatile double* xm = xmode_new + e0;
+              const double x0 = ley2[e0] * xm[0], x1 = ley2[e0 + 1] * xm[1], x2 = ley2[e0 + 2] * xm[2];
+              for (int p = 0; p < 3; ++p) {
+                const double* ti = ceti + 9 * c + 3 * p;
+                blk_new[n_le + 3 * c + p] = fma(ti[0], x0, fma(ti[1], x1, ti[2] * x2));
+              }
+            }
+          }
+        }
+        if (!ok) s_abort = 1;
       }
     }
     __syncthreads();

@@ -33,6 +33,33 @@ __device__ __forceinline__ bool ld_tagged(const unsigned long long* p, unsigned 
   return true;
 }
 
+// Wait for a ring slot to carry `tag` and return its value.  Bounded: on
+// exceeding the time budget (or seeing another CTA's error) it latches an
+// error {5, subsystem, line end, tag} and returns false.  Params: the
+// forward or adjoint kernel's parameters (ring-independent fields err,
+// wait_budget_ns).
+template <class Params>
+__device__ __forceinline__ bool poll_slot(const Params& P, const unsigned long long* slot, unsigned tag, int sidx,
+                                          int e, double& v) {
+  if (ld_tagged(slot, tag, v)) return true;
+  const unsigned long long t0 = global_ns();
+  unsigned spins = 0;
+  while (!ld_tagged(slot, tag, v)) {
+    if ((++spins & 31u) == 0) {
+      if (ld_volatile(P.err) != 0) return false;
+      if (global_ns() - t0 > P.wait_budget_ns || spins > (1u << 30)) {
+        if (atomicCAS(P.err, 0, 5) == 0) {
+          P.err[1] = sidx;
+          P.err[2] = e;
+          P.err[3] = (int)tag;
+        }
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
 // Signed injection entry (see kEntryNeg): the input value with the entry's
 // sign bit applied; line-end entries are shifted to the current parity block.
 __device__ __forceinline__ double signed_entry(const double* inp, unsigned raw, int ie_base, int n_le, int parshift) {

@@ -509,30 +509,6 @@ __device__ __forceinline__ void fold_fd_end(const FdFold& F, int e, double w_new
 // One warp collects one step's line-end histories I_e(n) from the tagged
 // rings.  Bounded: on exceeding the time budget (or seeing another CTA's
 // error) it latches an error and returns false.
-// Wait for a ring slot to carry `tag` and return its value.  Bounded: on
-// exceeding the time budget (or seeing another CTA's error) it latches an
-// error {5, subsystem, line end, tag} and returns false.
-__device__ __forceinline__ bool poll_slot(const FwdParams& P, const unsigned long long* slot, unsigned tag, int sidx,
-                                          int e, double& v) {
-  if (ld_tagged(slot, tag, v)) return true;
-  const unsigned long long t0 = global_ns();
-  unsigned spins = 0;
-  while (!ld_tagged(slot, tag, v)) {
-    if ((++spins & 31u) == 0) {
-      if (ld_volatile(P.err) != 0) return false;
-      if (global_ns() - t0 > P.wait_budget_ns || spins > (1u << 30)) {
-        if (atomicCAS(P.err, 0, 5) == 0) {
-          P.err[1] = sidx;
-          P.err[2] = e;
-          P.err[3] = (int)tag;
-        }
-        return false;
-      }
-    }
-  }
-  return true;
-}
-
 // One warp collects the values of step `tag` of every line end (the first
 // step of a launch; frequency-dependent ends folded on arrival).
 __device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int lane, int sidx, const long long* leown,
