@@ -59,6 +59,8 @@ class _Net(ctypes.Structure):
         ("fl_tau", ctypes.c_void_p), ("fl_y0", ctypes.c_void_p), ("fl_ny", ctypes.c_void_p),
         ("fl_yq", ctypes.c_void_p), ("fl_yc", ctypes.c_void_p), ("fl_a0", ctypes.c_void_p),
         ("fl_na", ctypes.c_void_p), ("fl_ap", ctypes.c_void_p), ("fl_ar", ctypes.c_void_p),
+        ("n_nl", ctypes.c_int64), ("nl_k", ctypes.c_void_p), ("nl_m", ctypes.c_void_p),
+        ("nl_np", ctypes.c_void_p), ("nl_v", ctypes.c_void_p), ("nl_i", ctypes.c_void_p),
         ("n_cb", ctypes.c_int64), ("cb_type", ctypes.c_void_p), ("cb_in0", ctypes.c_void_p),
         ("cb_in1", ctypes.c_void_p), ("cb_node", ctypes.c_void_p), ("cb_p0", ctypes.c_void_p),
         ("cb_p1", ctypes.c_void_p),
@@ -134,6 +136,10 @@ class _Pinned:
         n.fl_yq, n.fl_yc = p(rs("fl_yq", np.float64), np.float64), p(rs("fl_yc", np.float64), np.float64)
         n.fl_a0 = p(rs("fl_a0", np.float64), np.float64)
         n.fl_ap, n.fl_ar = p(rs("fl_ap", np.float64), np.float64), p(rs("fl_ar", np.float64), np.float64)
+        n.n_nl = int(len(rs("nl_k", np.int32)))
+        n.nl_k, n.nl_m = p(rs("nl_k", np.int32), np.int32), p(rs("nl_m", np.int32), np.int32)
+        n.nl_np = p(rs("nl_np", np.int32), np.int32)
+        n.nl_v, n.nl_i = p(rs("nl_v", np.float64), np.float64), p(rs("nl_i", np.float64), np.float64)
         n.n_cb = int(len(rs("cb_type", np.uint8)))
         n.cb_type = p(rs("cb_type", np.uint8), np.uint8)
         n.cb_in0, n.cb_in1 = p(rs("cb_in0", np.int32), np.int32), p(rs("cb_in1", np.int32), np.int32)

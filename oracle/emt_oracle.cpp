@@ -179,6 +179,20 @@ bool valid(const orc_net* net) {
           !std::isfinite(net->fl_ar[4 * l + i]))
         return false;
   }
+  if (net->n_nl < 0) return false;
+  for (int64_t e = 0; e < net->n_nl; ++e) {
+    const int32_t k = net->nl_k[e], m = net->nl_m[e];
+    if (k < -1 || m < -1 || k >= net->n_nodes || m >= net->n_nodes || k == m || (k < 0 && m < 0)) return false;
+    const int np = net->nl_np[e];
+    if (np < 1 || np > 8) return false;
+    double pv = 0.0, pi = 0.0;
+    for (int j = 0; j < np; ++j) {
+      const double vj = net->nl_v[8 * e + j], ij = net->nl_i[8 * e + j];
+      if (!std::isfinite(vj) || !std::isfinite(ij) || !(vj > pv) || !(ij >= pi)) return false;
+      pv = vj;
+      pi = ij;
+    }
+  }
   if (net->n_cb < 0 || net->n_ci < 0) return false;
   for (int64_t b = 0; b < net->n_cb; ++b) {
     const int t = net->cb_type[b];
@@ -217,6 +231,7 @@ void components(const orc_net* net, std::vector<int>& sub, int& n_sub) {
   for (int64_t b = 0; b < net->n_br; ++b) join(net->br_k[b], net->br_m[b]);
   for (int64_t s = 0; s < net->n_sw; ++s) join(net->sw_k[s], net->sw_m[s]);
   for (int64_t w = 0; w < net->n_rs; ++w) join(net->rs_k[w], net->rs_m[w]);
+  for (int64_t e = 0; e < net->n_nl; ++e) join(net->nl_k[e], net->nl_m[e]);
   for (int64_t l = 0; l < net->n_cl; ++l)
     for (int p = 1; p < 3; ++p) {
       join(net->cl_k[3 * l], net->cl_k[3 * l + p]);
@@ -287,6 +302,10 @@ struct Sim {
     std::vector<T> w[2];
   };
   std::vector<FLine> fl;
+  // nonlinear resistors: the one of each subsystem (or -1) and its column
+  // z = G^-1 (e_k - e_m) over the subsystem's nodes, for the current factors
+  std::vector<int> nl_of_sub;
+  std::vector<std::vector<T>> nl_z;
   // control blocks: output of the latest evaluation, and the two states
   // (integral or previous output; previous input)
   std::vector<T> cy, cs0, cs1;
@@ -323,6 +342,13 @@ struct Sim {
     rs_on.assign(net->n_rs, 0);
     for (int64_t w = 0; w < net->n_rs; ++w) rs_on[w] = net->rs_on0[w] ? 1 : 0;
     rs_i.assign(net->n_rs, 0.0);
+    nl_of_sub.assign(n_sub, -1);
+    nl_z.assign(n_sub, {});
+    for (int64_t e = 0; e < net->n_nl; ++e) {
+      const int a = net->nl_k[e] >= 0 ? net->nl_k[e] : net->nl_m[e];
+      if (nl_of_sub[sub[a]] >= 0) return false;   // at most one per subsystem
+      nl_of_sub[sub[a]] = (int)e;
+    }
     fl.assign(net->n_fl, FLine{});
     for (int64_t l = 0; l < net->n_fl; ++l) {
       FLine& L = fl[l];
@@ -499,7 +525,39 @@ struct Sim {
           for (int q = 0; q < 3; ++q) G[(size_t)local[nd[p]] * ns + local[nd[q]]] += T(cl[l].yp[3 * p + q]);
       }
     lu[s] = G;
-    return lu_factor(ns, lu[s], piv[s]);
+    if (!lu_factor(ns, lu[s], piv[s])) return false;
+    if (nl_of_sub[s] >= 0) {   // the nonlinear resistor's column G^-1 (e_k - e_m)
+      const int64_t e = nl_of_sub[s];
+      std::vector<T> z(ns, T(0.0));
+      if (net->nl_k[e] >= 0) z[local[net->nl_k[e]]] += T(1.0);
+      if (net->nl_m[e] >= 0) z[local[net->nl_m[e]]] -= T(1.0);
+      lu_solve(ns, lu[s], piv[s], z.data());
+      nl_z[s] = z;
+    }
+    return true;
+  }
+
+  // The current of nonlinear resistor e from its Thevenin source v_th behind
+  // r_th: the unique i with i = f(v_th - r_th i), f odd and piecewise linear
+  // (the segment whose image under u -> u + r_th f(u) holds |v_th|).
+  T nl_current(int64_t e, const T& v_th, const T& r_th) const {
+    const double* pv = net->nl_v + 8 * e;
+    const double* pi = net->nl_i + 8 * e;
+    const int np = net->nl_np[e];
+    const double sgn = re(v_th) < 0.0 ? -1.0 : 1.0;
+    const T x = T(sgn) * v_th;   // |v_th|
+    double v0 = 0.0, i0 = 0.0, slope = 0.0;
+    int j = 0;
+    for (; j < np; ++j) {
+      slope = (pi[j] - i0) / (pv[j] - v0);
+      if (re(x) < pv[j] + re(r_th) * pi[j]) break;   // the image of breakpoint j
+      v0 = pv[j];
+      i0 = pi[j];
+    }
+    // on the segment from (v0, i0) with this slope (past the last point the
+    // last segment's slope): u + r_th (i0 + slope (u - v0)) = |v_th|
+    const T u = (x - r_th * T(i0 - slope * v0)) / (T(1.0) + r_th * T(slope));
+    return T(sgn) * (T(i0) + T(slope) * (u - T(v0)));
   }
 
   T node_voltage(int32_t x) const {
@@ -571,6 +629,15 @@ struct Sim {
       std::vector<T> x(ns);
       for (int i = 0; i < ns; ++i) x[i] = rhs[nodes[s][i]];
       lu_solve(ns, lu[s], piv[s], x.data());
+      if (nl_of_sub[s] >= 0) {   // compensation: the nonlinear resistor against the linear solution
+        const int64_t e = nl_of_sub[s];
+        const int32_t k = net->nl_k[e], m = net->nl_m[e];
+        const std::vector<T>& z = nl_z[s];
+        const T vth = (k >= 0 ? x[local[k]] : T(0.0)) - (m >= 0 ? x[local[m]] : T(0.0));
+        const T rth = (k >= 0 ? z[local[k]] : T(0.0)) - (m >= 0 ? z[local[m]] : T(0.0));
+        const T inl = nl_current(e, vth, rth);
+        for (int i = 0; i < ns; ++i) x[i] -= z[i] * inl;
+      }
       for (int i = 0; i < ns; ++i) v[nodes[s][i]] = x[i];
     }
     // process 1: history currents of L and C branches
@@ -624,7 +691,7 @@ int run_loss(const orc_net* net, bool monolithic, int64_t n_steps, const T* br_v
              const int32_t* rec, int64_t n_rec, double* v_out, const double* v_target, T* loss) {
   Sim<T> sim;
   sim.net = net;
-  sim.init(br_value, src_amp, monolithic);
+  if (!sim.init(br_value, src_amp, monolithic)) return -1;
   T J = T(0.0);
   for (int64_t n = 1; n <= n_steps; ++n) {
     if (!sim.step(n)) return -2;
@@ -688,11 +755,11 @@ extern "C" int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_
 // and finally dg/dR = -1/R^2, dg/dL = -dt/(2L^2), dg/dC = 2/dt.
 extern "C" int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad,
                            double* loss) {
-  if (!valid(net) || !v_target || !grad || n_steps < 0 || net->n_cb > 0 || net->n_fl > 0) return -1;
+  if (!valid(net) || !v_target || !grad || n_steps < 0 || net->n_cb > 0 || net->n_fl > 0 || net->n_nl > 0) return -1;
   const int64_t nn = net->n_nodes, nb = net->n_br, ns = net->n_src, nl = net->n_ln, nr = net->n_rs;
   Sim<double> sim;
   sim.net = net;
-  sim.init(net->br_val, net->src_amp, false);
+  if (!sim.init(net->br_val, net->src_amp, false)) return -1;
   std::vector<double> tape((size_t)n_steps * nn);
   // runtime-switch states in force at each step: the reverse sweep uses
   // the matrices the forward run used (decisions held fixed)
@@ -831,7 +898,7 @@ extern "C" int orc_controls(const orc_net* net, int64_t n_steps, double* y_out) 
   if (!valid(net) || n_steps < 0 || (n_steps > 0 && net->n_cb > 0 && !y_out)) return -1;
   Sim<double> sim;
   sim.net = net;
-  sim.init(net->br_val, net->src_amp, false);
+  if (!sim.init(net->br_val, net->src_amp, false)) return -1;
   for (int64_t n = 1; n <= n_steps; ++n) {
     if (!sim.step(n)) return -2;
     for (int64_t b = 0; b < net->n_cb; ++b) y_out[(size_t)(n - 1) * net->n_cb + b] = sim.cy[b];
@@ -843,7 +910,7 @@ extern "C" int orc_rs_states(const orc_net* net, int64_t n_steps, uint8_t* state
   if (!valid(net) || n_steps < 0 || (n_steps > 0 && net->n_rs > 0 && !states)) return -1;
   Sim<double> sim;
   sim.net = net;
-  sim.init(net->br_val, net->src_amp, false);
+  if (!sim.init(net->br_val, net->src_amp, false)) return -1;
   for (int64_t n = 1; n <= n_steps; ++n) {
     for (int64_t w = 0; w < net->n_rs; ++w) states[(size_t)(n - 1) * net->n_rs + w] = (uint8_t)sim.rs_on[w];
     if (!sim.step(n)) return -2;

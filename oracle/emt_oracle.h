@@ -121,6 +121,23 @@ typedef struct {
   const int32_t* fl_na;
   const double* fl_ap;
   const double* fl_ar;
+  /* Nonlinear resistors, solved by the compensation method: element e
+   * between nl_k and nl_m (unknown node or ground, not both ground) carries
+   * i = f(v_k - v_m), f odd and piecewise linear through (0, 0) and
+   * (nl_v[8 e + j], nl_i[8 e + j]), j < nl_np[e] <= 8, with 0 < v_1 < v_2 <
+   * ... and 0 <= i_1 <= i_2 <= ... (monotone), continued past the last
+   * point with the last segment's slope.  At each step the subsystem is
+   * solved without the element (v0), the element sees the Thevenin source
+   * v_th = v0_k - v0_m behind R_th = z_k - z_m, z = G^-1 (e_k - e_m); its
+   * current solves i = f(v_th - R_th i) (unique: f monotone, R_th > 0);
+   * then v = v0 - z i.  At most one nonlinear resistor per subsystem.  The
+   * element joins k and m into one subsystem. */
+  int64_t n_nl;
+  const int32_t* nl_k;
+  const int32_t* nl_m;
+  const int32_t* nl_np;
+  const double* nl_v;
+  const double* nl_i;
   int64_t n_cb;
   const uint8_t* cb_type;
   const int32_t* cb_in0;
@@ -161,8 +178,8 @@ int orc_loss_cs(const orc_net* net, int64_t n_steps, const double* v_target, int
  * With runtime switches the reverse sweep uses the states the forward run
  * decided (the gradient of the smooth piece the run lies on).  The
  * parameters of coupled lines themselves (Z, T_v, travel times) are not
- * differentiated.  Networks with control blocks or frequency-dependent
- * lines are rejected (-1). */
+ * differentiated.  Networks with control blocks, frequency-dependent
+ * lines or nonlinear resistors are rejected (-1). */
 int orc_adjoint(const orc_net* net, int64_t n_steps, const double* v_target, double* grad, double* loss);
 
 /* Control block outputs of steps 1..n_steps: y_out[(n-1) n_cb + b]

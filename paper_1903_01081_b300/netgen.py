@@ -95,6 +95,14 @@ class Network:
     fl_na: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
     fl_ap: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
     fl_ar: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    # nonlinear resistors (compensation method): ends, and an odd piecewise-
+    # linear i(v) through (0, 0) and up to 8 points (v > 0 increasing, i
+    # nondecreasing) in [8 e + j] slots; at most one per subsystem
+    nl_k: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    nl_m: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    nl_np: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    nl_v: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
+    nl_i: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
     # control blocks (CB_* types), evaluated after each step's solve; an input
     # of lower index reads its step-n output, of equal or higher index its
     # step-(n-1) output.  Controlled current injections: block output y(n)
@@ -133,6 +141,10 @@ class Network:
     @property
     def n_coupled_lines(self) -> int:
         return int(self.cl_z.shape[0]) // 3
+
+    @property
+    def n_nonlinear(self) -> int:
+        return int(self.nl_k.shape[0])
 
     @property
     def n_fd_lines(self) -> int:
@@ -267,6 +279,7 @@ class NetworkBuilder:
         self.rs = []     # (k, m, kind, r_on, r_off, on0, trip)
         self.cl = []     # (k3, m3, tv9, z3, tau3)
         self.fl = []     # (k, m, tau, y0, yq4, yc4, ny, a0, ap4, ar4, na)
+        self.nl = []     # (k, m, np, v8, i8)
         self.cb = []     # (type, in0, in1, node, p0, p1)
         self.ci = []     # (block, node)
 
@@ -306,6 +319,14 @@ class NetworkBuilder:
                         len(ap)))
         return len(self.fl) - 1
 
+    def nonlinear_resistor(self, k, m, v_points, i_points):
+        """Odd piecewise-linear resistor i = f(v_k - v_m) through (0, 0) and the
+        given points (see ``Network.nl_*``)."""
+        assert 1 <= len(v_points) == len(i_points) <= 8
+        pad = lambda x: list(map(float, x)) + [0.0] * (8 - len(x))
+        self.nl.append((int(k), int(m), len(v_points), pad(v_points), pad(i_points)))
+        return len(self.nl) - 1
+
     def block(self, kind, in0=-1, in1=-1, node=-1, p0=0.0, p1=0.0):
         """Control block of type ``kind`` (CB_*); returns its index."""
         self.cb.append((int(kind), int(in0), int(in1), int(node), float(p0), float(p1)))
@@ -344,6 +365,9 @@ class NetworkBuilder:
             fl_yc=np.ascontiguousarray(np.array([x for f in self.fl for x in f[5]], np.float64)),
             fl_ap=np.ascontiguousarray(np.array([x for f in self.fl for x in f[8]], np.float64)),
             fl_ar=np.ascontiguousarray(np.array([x for f in self.fl for x in f[9]], np.float64)),
+            nl_k=col(self.nl, 0, np.int32), nl_m=col(self.nl, 1, np.int32), nl_np=col(self.nl, 2, np.int32),
+            nl_v=np.ascontiguousarray(np.array([x for e in self.nl for x in e[3]], np.float64)),
+            nl_i=np.ascontiguousarray(np.array([x for e in self.nl for x in e[4]], np.float64)),
             cb_type=col(self.cb, 0, np.uint8), cb_in0=col(self.cb, 1, np.int32), cb_in1=col(self.cb, 2, np.int32),
             cb_node=col(self.cb, 3, np.int32), cb_p0=col(self.cb, 4, np.float64), cb_p1=col(self.cb, 5, np.float64),
             ci_block=col(self.ci, 0, np.int32), ci_node=col(self.ci, 1, np.int32),
@@ -745,6 +769,61 @@ def with_fd_lines(base: Network, seed: int = 1009, fractional: bool = True) -> N
     for f in ("ln_k", "ln_m", "ln_zc", "ln_delay"):
         setattr(net, f, getattr(base, f)[:0].copy())
     net.meta = dict(net.meta, fd_lines={"seed": seed, "lines": L, "fractional": fractional})
+    return net
+
+
+# a surge arrester's characteristic as an odd piecewise-linear resistor
+# (volts, amperes): nearly open below ~0.8 kV (the 1 kV-peak system clips
+# at its source buses), a few kA near 1.5 kV
+ARRESTER_V = (800.0, 950.0, 1050.0, 1150.0, 1300.0, 1500.0)
+ARRESTER_I = (1e-3, 1.0, 50.0, 300.0, 1500.0, 4000.0)
+
+
+def with_arresters(base: Network, seed: int = 1010, n_arresters: int = 40, scale=(0.9, 1.1)) -> Network:
+    """``base`` plus ``n_arresters`` phase-to-ground surge arresters (odd
+    piecewise-linear resistors, characteristic ``ARRESTER_V/I`` with its
+    voltages scaled by U[scale]): first at a phase node of each source bus
+    (where the 1 kV peaks make them conduct), then at random nodes, at most
+    one per subsystem (the compensation method solves one nonlinear element
+    per subsystem)."""
+    rng = np.random.default_rng(seed)
+    net = base.copy()
+    # subsystems: components over branches and switches (lines cut them)
+    parent = list(range(net.n_nodes))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+    for k, m in list(zip(net.br_k, net.br_m)) + list(zip(net.rs_k, net.rs_m)) + list(zip(net.sw_k, net.sw_m)):
+        if k >= 0 and m >= 0:
+            a, b = find(int(k)), find(int(m))
+            if a != b:
+                parent[max(a, b)] = min(a, b)
+    for x in range(0, len(net.cl_k), 3):
+        for y in (net.cl_k, net.cl_m):
+            for p in (1, 2):
+                a, b = find(int(y[x])), find(int(y[x + p]))
+                if a != b:
+                    parent[max(a, b)] = min(a, b)
+    taken, nodes = set(), []
+    first = [int(net.meta["bus_nodes"][b_][0]) for b_ in net.meta.get("source_bus", [])]
+    for x in first + rng.permutation(net.n_nodes).tolist():
+        r = find(int(x))
+        if r not in taken:
+            taken.add(r)
+            nodes.append(int(x))
+        if len(nodes) == n_arresters:
+            break
+    b = NetworkBuilder()
+    for x in nodes:
+        s = rng.uniform(*scale)
+        b.nonlinear_resistor(x, GROUND, [v * s for v in ARRESTER_V], ARRESTER_I)
+    nl = b.build(base.dt, 0)
+    for f in ("nl_k", "nl_m", "nl_np", "nl_v", "nl_i"):
+        setattr(net, f, getattr(nl, f))
+    net.meta = dict(net.meta, arresters={"seed": seed, "count": len(nodes)})
     return net
 
 
