@@ -27,6 +27,8 @@ two further legs the metric names, reported as extra keys of the line:
       coupled modal lines with interpolated travel times, against the plain one;
   "fd_lines": the same with its line conductors as lossy frequency-dependent
       lines, against the plain one;
+  "nonlinear": the same with 40 surge arresters solved by the compensation
+      method, against the plain one;
   "controls": the same with 180 converter loads (4,320 layered control
       blocks driving controlled current injections), against the plain one.
 
@@ -410,6 +412,22 @@ def fd_line_leg(steps=None, reps=3):
                        "dt; all nodes recorded", steps, reps)
 
 
+def nonlinear_leg(steps=None, reps=3):
+    """The large-scale network with 40 surge arresters (odd piecewise-linear
+    resistors solved by the compensation method, one per subsystem)."""
+    import oracle
+    from paper_1903_01081_b300 import netgen as g
+
+    def active(net, n):
+        v = oracle.simulate(net, n, rec=net.nl_k)
+        return {"nonlinear_resistors": int(net.n_nonlinear),
+                "conducting_in_checked_steps": int(np.sum(np.max(np.abs(v), axis=0) > g.ARRESTER_V[0]))}
+    return variant_leg(g.with_arresters(g.large_scale()),
+                       "large-scale network plus 40 phase-to-ground surge arresters (odd piecewise-linear, knee "
+                       "~0.8-1.5 kV, one per subsystem, at the source buses first) solved by the compensation "
+                       "method; all nodes recorded", steps, reps, active)
+
+
 def control_leg(steps=None, reps=3):
     """The large-scale network with 180 power-regulated converter loads, each
     24 layered control blocks driving three controlled current injections."""
@@ -573,7 +591,8 @@ def run_ours(args):
             "clocks": clocks.summary(),
             "parity_rel_err_first_2000_steps": parity,
             **({"scenarios": scenario_legs(cpu=True), "adjoint": adjoint_leg(), "runtime_switches": runtime_switch_leg(),
-                "coupled_lines": coupled_line_leg(), "fd_lines": fd_line_leg(), "controls": control_leg()}
+                "coupled_lines": coupled_line_leg(), "fd_lines": fd_line_leg(), "nonlinear": nonlinear_leg(),
+                "controls": control_leg()}
                if args.leg == "all" else {}),
         }
         print(json.dumps(line), flush=True)
@@ -592,7 +611,7 @@ def main():
     ap.add_argument("--time-steps", type=int, default=N_STEPS)
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines",
-                                      "fd_lines", "controls"],
+                                      "fd_lines", "nonlinear", "controls"],
                     default="all",
                     help="all: the JSON line with every leg; single: the single-network leg only; "
                          "n1 / shared_g / adjoint: that leg alone (profiling)")
@@ -605,7 +624,8 @@ def main():
         return run_rank_selftest()
     if args.impl == "reference":
         return run_reference(args)
-    if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "fd_lines", "controls"):
+    if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "fd_lines", "nonlinear",
+                    "controls"):
         return run_leg(args)
     return run_ours(args)
 
@@ -624,6 +644,8 @@ def run_leg(args):
         out = control_leg(args.leg_steps, reps=1)
     elif args.leg == "fd_lines":
         out = fd_line_leg(args.leg_steps, reps=1)
+    elif args.leg == "nonlinear":
+        out = nonlinear_leg(args.leg_steps, reps=1)
     else:
         shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
         out = scenario_legs((args.leg,), args.leg_steps, shape, args.leg_warm)

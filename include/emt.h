@@ -120,7 +120,19 @@ typedef struct emt_ctx emt_ctx;  /* opaque; owns all device memory it allocates 
  *   w_f(m) = 2 yc_f(m) - b_f(m): it stamps G_eq = fl_y0 + sum mu (> 0
  *   required) and draws a history current from the previous step.  With
  *   fl_y0 = 1/Z, fl_a0 = 1, no poles and tau = d dt this is the Bergeron
- *   line above.  Not supported with a scenario set or by emt_adjoint. */
+ *   line above.  Not supported with a scenario set or by emt_adjoint.
+ * Nonlinear resistors (n_nonlin may be 0), solved by the compensation
+ *   method (the paper's process 3 at run time, Sec. III-A): element x between
+ *   nl_k and nl_m (unknown node or ground, not both ground) carries
+ *   i = f(v_k - v_m), f odd and piecewise linear through (0, 0) and
+ *   (nl_v[8 x + j], nl_i[8 x + j]), j < nl_np[x] <= 8, 0 < v_1 < v_2 < ...,
+ *   0 <= i_1 <= i_2 <= ..., continued past the last point with the last
+ *   slope.  Each step solves the subsystem without the element (v0), takes
+ *   the element's Thevenin source v_th = v0_k - v0_m behind R_th = z_k - z_m,
+ *   z = G^-1 (e_k - e_m) (prefactored with G^-1 for every switch state), solves
+ *   i = f(v_th - R_th i) exactly on the right segment and sets v = v0 - z i.
+ *   At most one per subsystem (the element joins its two ends into one
+ *   subsystem).  Not supported with a scenario set or by emt_adjoint. */
 typedef struct {
   double dt;
   int64_t n_nodes;
@@ -180,6 +192,12 @@ typedef struct {
   const int32_t* fl_na;
   const double* fl_ap;
   const double* fl_ar;
+  int64_t n_nonlin;
+  const int32_t* nl_k;
+  const int32_t* nl_m;
+  const int32_t* nl_np;
+  const double* nl_v;
+  const double* nl_i;
 } emt_network_desc;
 
 /* Optional per-scenario overrides of one base network (the paper's
@@ -314,8 +332,8 @@ emt_status emt_autotune(emt_ctx* ctx, int64_t trial_steps, void* cuda_stream);
  * decided (the forward re-runs record them per step), i.e. the gradient of
  * the smooth piece of J the run lies on.  Coupled lines' own Z, T_v and
  * travel times are not parameters.  Requires emt_prefactor; a context built
- * with a scenario set, control blocks or frequency-dependent lines returns
- * EINVAL.  Resets the context to step 0 before and after (the recording
+ * with a scenario set, control blocks, frequency-dependent lines or nonlinear
+ * resistors returns EINVAL.  Resets the context to step 0 before and after (the recording
  * buffer is not written).  Allocates its work buffers (about 8 N n_nodes
  * bytes for a host v_target, N/K checkpoints, the tape) and frees them
  * before returning.  Synchronous.  ETIMEOUT as for emt_step_n. */
@@ -345,7 +363,7 @@ emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
  * "threads_per_cta", "kernel_launches", "n_nodes", "n_branches", "n_sources", "n_line_ends",
  * "smem_bytes" (dynamic shared memory per CTA of the persistent kernel),
  * "n_strong_branches" (L/C branches applied through extra solve columns),
- * "n_runtime_switches", "n_coupled_lines", "n_fd_lines", "n_control_blocks",
+ * "n_runtime_switches", "n_coupled_lines", "n_fd_lines", "n_nonlinear", "n_control_blocks",
  * "n_control_injections", "max_control_layers" (largest layer count of one
  * subsystem's control graph),
  * "n_matrix_variants", "scenarios_per_cta", "batch_threads", "batch_groups"

@@ -65,13 +65,15 @@ struct emt_ctx {
   std::vector<CoupledEndDev> cends;                    // coupled line ends, grouped by subsystem
   std::vector<int32_t> rs_word0;                       // per subsystem: state word at step 1
   std::vector<FdEndDev> fdends;                        // frequency-dependent line ends, grouped by subsystem
+  std::vector<NlDev> nls;                              // nonlinear resistors, one per subsystem at most
+  int64_t nlz_len = 0;                                 // doubles of their columns over all matrix entries
   std::vector<CtrlDev> cblocks;                        // control blocks, grouped by subsystem, by layer
   std::vector<int32_t> clay, cinj;                     // layer starts; block slot per control injection
   std::vector<int32_t> cb_slot_of;                     // caller's block index -> subsystem-local slot
   std::vector<int32_t> cb_sub_of;                      // caller's block index -> subsystem
   int max_clayers = 0;
   int64_t ring_len = 0, ginv_len = 0, n_lc_total = 0;
-  FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0};
+  FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0};
 
   // device arrays
   SubDev* d_sub = nullptr;
@@ -105,6 +107,9 @@ struct emt_ctx {
   int32_t* d_rs_word = nullptr;
   double* d_rs_prev_i = nullptr;
   FdEndDev* d_fd = nullptr;
+  NlDev* d_nl = nullptr;
+  double* d_nlz = nullptr;
+  float* d_nlz_lo = nullptr;
   double* d_fd_state = nullptr;
   CtrlDev* d_cb = nullptr;
   int32_t* d_clay = nullptr;
@@ -301,6 +306,24 @@ std::string validate(const emt_network_desc* d) {
     if (d->rs_kind[w] > 1) return "runtime switch " + std::to_string(w) + ": kind must be 0 (diode) or 1 (breaker)";
     if (!finite_pos(d->rs_ron[w]) || !finite_pos(d->rs_roff[w]))
       return "runtime switch " + std::to_string(w) + ": resistances must be finite and > 0";
+  }
+  if (d->n_nonlin < 0) return "negative count";
+  if (d->n_nonlin && (!d->nl_k || !d->nl_m || !d->nl_np || !d->nl_v || !d->nl_i))
+    return "nonlinear resistor array is NULL";
+  for (int64_t x = 0; x < d->n_nonlin; ++x) {
+    const std::string nm = "nonlinear resistor " + std::to_string(x);
+    const int32_t k = d->nl_k[x], m = d->nl_m[x];
+    if (k < -1 || m < -1 || k >= d->n_nodes || m >= d->n_nodes || k == m || (k < 0 && m < 0))
+      return nm + ": ends must be unknown nodes or ground";
+    if (d->nl_np[x] < 1 || d->nl_np[x] > kNlMaxPoints) return nm + ": 1 to 8 breakpoints";
+    double pv = 0.0, pi = 0.0;
+    for (int j = 0; j < d->nl_np[x]; ++j) {
+      const double v = d->nl_v[kNlMaxPoints * x + j], i = d->nl_i[kNlMaxPoints * x + j];
+      if (!std::isfinite(v) || !std::isfinite(i) || !(v > pv) || !(i >= pi))
+        return nm + ": breakpoints need increasing v > 0 and nondecreasing i >= 0";
+      pv = v;
+      pi = i;
+    }
   }
   if (d->n_fdlines < 0) return "negative count";
   if (d->n_fdlines && (!d->fl_k || !d->fl_m || !d->fl_tau || !d->fl_y0 || !d->fl_ny || !d->fl_yq || !d->fl_yc ||
@@ -582,6 +605,7 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
           E.start = 0;
           E.ginv_off = goff;
           goff += (int64_t)sd.n * (sd.n + sd.n_str);
+          E.nlz_off = -1;
           E.sw_off = (int)c->switches.size();
           for (auto& cl : closed) {
             SwitchDev sw{};
@@ -747,6 +771,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   for (int64_t b = 0; b < d->n_branches; ++b) join(d->br_k[b], d->br_m[b]);
   for (int64_t w = 0; w < d->n_switches; ++w) join(d->sw_k[w], d->sw_m[w]);
   for (int64_t w = 0; w < d->n_rswitches; ++w) join(d->rs_k[w], d->rs_m[w]);
+  for (int64_t x = 0; x < d->n_nonlin; ++x) join(d->nl_k[x], d->nl_m[x]);
   for (int64_t l = 0; l < d->n_clines; ++l)   // an end's phases are coupled by Y_p
     for (int p = 1; p < 3; ++p) {
       join(d->cl_k[3 * l], d->cl_k[3 * l + p]);
@@ -1088,6 +1113,40 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     c->lim.nc = std::max(c->lim.nc, sd.n + sd.n_str);
   }
 
+  // -------- nonlinear resistors (compensation method): at most one per
+  // subsystem, the odd characteristic as segments from (0, 0)
+  {
+    std::vector<int64_t> nl_of(S, -1);
+    for (int64_t x = 0; x < d->n_nonlin; ++x) {
+      const int a = d->nl_k[x] >= 0 ? d->nl_k[x] : d->nl_m[x];
+      const int sb = c->sub_of_node[a];
+      if (nl_of[sb] >= 0)
+        return bail("subsystem " + std::to_string(sb) + " has more than one nonlinear resistor (nonlinear resistors " +
+                    std::to_string(nl_of[sb]) + " and " + std::to_string(x) + ")");
+      nl_of[sb] = x;
+    }
+    for (int s = 0; s < S; ++s) {
+      SubDev& sd = c->subs[s];
+      sd.nl_off = (int)c->nls.size();
+      sd.n_nl = 0;
+      const int64_t x = nl_of[s];
+      if (x < 0) continue;
+      NlDev q{};
+      q.k = d->nl_k[x] >= 0 ? local[d->nl_k[x]] : -1;
+      q.m = d->nl_m[x] >= 0 ? local[d->nl_m[x]] : -1;
+      q.np = d->nl_np[x];
+      for (int j = 0; j < q.np; ++j) {
+        q.bv[j + 1] = d->nl_v[kNlMaxPoints * x + j];
+        q.bi[j + 1] = d->nl_i[kNlMaxPoints * x + j];
+      }
+      for (int j = 0; j < q.np; ++j) q.sl[j] = (q.bi[j + 1] - q.bi[j]) / (q.bv[j + 1] - q.bv[j]);
+      q.sl[q.np] = q.sl[q.np - 1];   // past the last point, the last slope
+      c->nls.push_back(q);
+      sd.n_nl = 1;
+      c->lim.nl = 1;
+    }
+  }
+
   // -------- control blocks (Sec. III-A/B: control components as basic
   // processes, layered).  Each connected group of blocks runs in the
   // subsystem of the nodes it measures and drives; within a subsystem a
@@ -1294,6 +1353,11 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
           E.start = ep.first;
           E.ginv_off = goff;
           goff += (int64_t)sd.n * (sd.n + sd.n_str);
+          E.nlz_off = -1;
+          if (sd.n_nl > 0) {
+            E.nlz_off = c->nlz_len;
+            c->nlz_len += sd.n;
+          }
           E.sw_off = (int)c->switches.size();
           for (int64_t w : sw_of[s]) {
             if (!switch_closed(d->sw_close_step[w], d->sw_open_step[w], ep.second)) continue;
@@ -1359,6 +1423,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   if (scen && !c->cends.empty()) return bail("coupled lines are not supported with a scenario set");
   if (scen && (d->n_cblocks > 0 || d->n_cinj > 0)) return bail("control blocks are not supported with a scenario set");
   if (scen && d->n_fdlines > 0) return bail("frequency-dependent lines are not supported with a scenario set");
+  if (scen && d->n_nonlin > 0) return bail("nonlinear resistors are not supported with a scenario set");
   if (scen) {
     const std::string bm = build_scenarios(c, d, scen, local, new_of_orig, le_of_end, lc_slot_of, sb_slot_of);
     if (!bm.empty()) return bail(bm);
@@ -1387,6 +1452,7 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   UP(d_ce, cends)
   UP(d_rs_word, rs_word0)
   UP(d_fd, fdends)
+  UP(d_nl, nls)
   UP(d_cb, cblocks)
   UP(d_clay, clay)
   UP(d_cinj, cinj)
@@ -1403,6 +1469,8 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_err, 4);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_rs_prev_i, c->rswitches.size());
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_fd_state, kFdState * c->fdends.size());
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_nlz, (size_t)c->nlz_len);
+  if (e == cudaSuccess) e = c->alloc_zero(&c->d_nlz_lo, (size_t)c->nlz_len);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_cstate, 2 * c->cblocks.size());
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_cy, c->cblocks.size());
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_le_prev, c->line_ends.size());
@@ -1503,6 +1571,9 @@ extern "C" emt_status emt_prefactor(emt_ctx* c) {
   p.str_slot = c->d_str_slot;
   p.ginv = c->d_ginv;
   p.ginv_lo = c->d_ginv_lo;
+  p.nl = c->d_nl;
+  p.nlz = c->d_nlz;
+  p.nlz_lo = c->d_nlz_lo;
   p.work_g = d_wg;
   p.work_r = d_wr;
   p.status = d_status;
@@ -1698,6 +1769,9 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
   p.rs_prev_i = c->d_rs_prev_i;
   p.fd = c->d_fd;
   p.fd_state = c->d_fd_state;
+  p.nl = c->d_nl;
+  p.nlz = c->d_nlz;
+  p.nlz_lo = c->d_nlz_lo;
   p.cb = c->d_cb;
   p.clay = c->d_clay;
   p.cinj = c->d_cinj;
@@ -1988,6 +2062,7 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "n_runtime_switches") *value = (int64_t)c->rswitches.size();
   else if (k == "n_coupled_lines") *value = (int64_t)c->cends.size() / 2;
   else if (k == "n_fd_lines") *value = (int64_t)c->fdends.size() / 2;
+  else if (k == "n_nonlinear") *value = (int64_t)c->nls.size();
   else if (k == "n_control_blocks") *value = (int64_t)c->cblocks.size();
   else if (k == "n_control_injections") *value = (int64_t)c->cinj.size();
   else if (k == "max_control_layers") *value = c->max_clayers;
@@ -2026,6 +2101,7 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
   if (c->batched) return c->fail(EMT_EINVAL, "emt_adjoint: a context built with a scenario set has no adjoint");
   if (!c->cblocks.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: control blocks have no adjoint");
   if (!c->fdends.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: frequency-dependent lines have no adjoint");
+  if (!c->nls.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: nonlinear resistors have no adjoint");
   if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
   if (n_steps < 1) return c->fail(EMT_EINVAL, "emt_adjoint: n_steps must be >= 1");
   if (n_steps > (int64_t)INT32_MAX - (int64_t)(1 << 21))
@@ -2421,6 +2497,9 @@ extern "C" emt_status emt_prefactor_noalloc(emt_ctx* c, void* stream) {
   p.str_slot = c->d_str_slot;
   p.ginv = c->d_ginv;
   p.ginv_lo = c->d_ginv_lo;
+  p.nl = c->d_nl;
+  p.nlz = c->d_nlz;
+  p.nlz_lo = c->d_nlz_lo;
   p.work_g = work_g;
   p.work_r = work_r;
   p.status = status;

@@ -125,6 +125,21 @@ struct SubDev {
   int32_t clay_off, n_clay;    // control layers: n_clay + 1 starts in clay (with the layer's type, see kLayerTypeShift)
   int32_t ci_off, n_ci;        // control injections: local block slot per injection in cinj
   int32_t fd_off, n_fd;        // frequency-dependent line ends (FdEndDev list)
+  int32_t nl_off, n_nl;        // nonlinear resistor (NlDev list; at most one)
+};
+
+// A nonlinear resistor solved by the compensation method: odd, piecewise
+// linear, segment j (0 <= j <= np) starting at (bv[j], bi[j]) with slope
+// sl[j], (bv[0], bi[0]) = (0, 0), the last segment unbounded.  Each solve
+// matrix entry of its subsystem carries the column z = G^-1 (e_k - e_m)
+// (EpochDev::nlz_off); the step solves i = f(v_th - R_th i) against the
+// linear solution, R_th = z_k - z_m, and corrects v by -z i.
+constexpr int kNlMaxPoints = 8;
+struct NlDev {
+  int32_t k, m;        // subsystem-local ends, -1 = ground
+  int32_t np;          // breakpoints after (0, 0)
+  int32_t pad;
+  double bv[kNlMaxPoints + 1], bi[kNlMaxPoints + 1], sl[kNlMaxPoints + 1];
 };
 
 // A control block in device form (subsystem-local, ordered by layer).  The
@@ -180,6 +195,7 @@ struct EpochDev {
   int64_t start;
   int64_t ginv_off;      // offset of this epoch's n x nc solve matrix
   int32_t sw_off, n_sw;  // closed switches (SwitchDev list)
+  int64_t nlz_off;       // offset of its nonlinear resistor's column z (n doubles), or -1
 };
 
 // Per-launch upper bounds that size the forward kernel's shared memory.
@@ -189,6 +205,7 @@ struct FwdLimits {
   int32_t ce;                  // coupled line ends per subsystem
   int32_t cb, clay, ci;        // control blocks, layers + 1 and injections per subsystem
   int32_t fd;                  // frequency-dependent line ends per subsystem
+  int32_t nl;                  // 1 if some subsystem has a nonlinear resistor
 };
 
 struct FwdParams {
@@ -236,6 +253,9 @@ struct FwdParams {
   double* cy;                  // per control block: output of the last step (carried across launches)
   const FdEndDev* fd;          // frequency-dependent line ends (SubDev fd_off / n_fd)
   double* fd_state;            // per FD end: s[4], z[4], v(n-1), W(n-1), Hy(n) (11 doubles, carried)
+  const NlDev* nl;             // nonlinear resistors (SubDev nl_off / n_nl)
+  const double* nlz;           // their columns z per solve matrix entry (EpochDev::nlz_off)
+  const float* nlz_lo;         // z minus that rounding, in single precision
 };
 
 constexpr int kFdState = 11;
@@ -254,6 +274,9 @@ struct PrefParams {
   const int32_t* str_slot;     // L/C slot of each strong branch
   double* ginv;                // X_hi: G^-1 rounded to double
   float* ginv_lo;              // X_lo: G^-1 - X_hi in single precision
+  const NlDev* nl;             // nonlinear resistors: their columns z are written to nlz / nlz_lo
+  double* nlz;
+  float* nlz_lo;
   double* work_g;              // copy of G per matrix, at ep.ginv_off
   double* work_r;              // residual I - G X per matrix, at ep.ginv_off
   int32_t* status;             // per matrix: 0 ok, 1 singular

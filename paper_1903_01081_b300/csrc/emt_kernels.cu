@@ -266,6 +266,21 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
     out[i * nc + n + t] = s;
     out_lo[i * nc + n + t] = (float)e;
   }
+  // the nonlinear resistor's column G^-1 (e_k - e_m), formed the same way
+  if (S.n_nl > 0 && E.nlz_off >= 0) {
+    const NlDev& q = P.nl[S.nl_off];
+    for (int i = tid; i < n; i += T) {
+      const double a = q.k >= 0 ? out[i * nc + q.k] : 0.0, b = q.m >= 0 ? out[i * nc + q.m] : 0.0;
+      const double al = q.k >= 0 ? (double)out_lo[i * nc + q.k] : 0.0;
+      const double bl = q.m >= 0 ? (double)out_lo[i * nc + q.m] : 0.0;
+      double d1, e1;
+      two_sum(a, -b, d1, e1);
+      double s, e;
+      two_sum(d1, e1 + (al - bl), s, e);
+      P.nlz[E.nlz_off + i] = s;
+      P.nlz_lo[E.nlz_off + i] = (float)e;
+    }
+  }
   if (tid == 0) P.status[mi] = 0;
 }
 
@@ -318,10 +333,10 @@ constexpr int kItemThreads = kFwdThreads - 32;
 // together fall in different banks.
 struct FwdSmem {
   size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar, lef, imode, ceti, cetinv, cbr, cy, cs, fdr,
-      fdst;                                                                                // 8-byte
+      fdst, nlz;                                                                           // 8-byte
   size_t gilo, ivf, partf;                                                                 // float
   size_t lck, lcm, lckind, lcstr, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, recp,
-      lece, lemode, cele0, cenode, clay, cinj, lefd, cecnt;                                // int
+      lece, lemode, cele0, cenode, clay, cinj, lefd, cecnt, nlzl;                          // int / float
   size_t bytes;
 };
 
@@ -351,6 +366,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.cbr = d16(sizeof(CtrlDev) / 8 * (size_t)L.cb);
   s.cy = d16(2 * (size_t)L.cb + 2);
   s.cs = d16(2 * (size_t)L.cb);
+  s.nlz = d(L.nl ? (size_t)L.n : 0);
   s.fdr = d(sizeof(FdEndDev) / 8 * (size_t)L.fd);
   s.fdst = d(kFdState * (size_t)L.fd);
   s.gilo = w(nbuf * (size_t)L.n * ldg);
@@ -378,6 +394,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.clay = w(L.clay);
   s.cinj = w(L.ci);
   s.lefd = w(L.le);
+  s.nlzl = w(L.nl ? (size_t)L.n : 0);
   s.cecnt = w(L.ce);
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
@@ -472,6 +489,35 @@ __device__ __forceinline__ void control_slot(int b, int first, bool act, int lt,
     cy[2 * b + par] = y;
     if (has_state) *reinterpret_cast<double2*>(cs + 2 * b) = ns;
   }
+}
+
+// Nonlinear resistor (compensation method), per solve-matrix entry: the
+// Thevenin resistance R = z_k - z_m of its column and, per segment j, the
+// image H_j = v_j + R i_j of the segment's start, 1 / (1 + R s_j) and
+// R (i_j - s_j v_j).  c = [R, H[9], a[9], b[9]].
+__device__ void nl_setup(const NlDev& q, const double* zh, const float* zl, double* c) {
+  const double zk = q.k >= 0 ? zh[q.k] + (double)zl[q.k] : 0.0;
+  const double zm = q.m >= 0 ? zh[q.m] + (double)zl[q.m] : 0.0;
+  const double R = zk - zm;
+  c[0] = R;
+  for (int j = 0; j <= q.np; ++j) {
+    c[1 + j] = fma(R, q.bi[j], q.bv[j]);
+    c[1 + (kNlMaxPoints + 1) + j] = 1.0 / fma(R, q.sl[j], 1.0);
+    c[1 + 2 * (kNlMaxPoints + 1) + j] = R * fma(-q.sl[j], q.bv[j], q.bi[j]);
+  }
+}
+
+// Its current from the Thevenin voltage: the segment whose image holds
+// |v_th| (integer compares of finite doubles), then u on that segment and
+// i = f(u) with the sign of v_th.
+__device__ double nl_current(const NlDev& q, const double* c, double vth) {
+  const double x = fabs(vth);
+  const long long kx = ordered_bits(x);
+  int j = 0;
+  while (j < q.np && kx >= ordered_bits(c[1 + j + 1])) ++j;
+  const double u = (x - c[1 + 2 * (kNlMaxPoints + 1) + j]) * c[1 + (kNlMaxPoints + 1) + j];
+  const double i = fma(q.sl[j], u - q.bv[j], q.bi[j]);
+  return vth < 0.0 ? -i : i;
 }
 
 // A frequency-dependent line end's history at step m, folded by the poll
@@ -579,6 +625,11 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   double* fdst = reinterpret_cast<double*>(smem_raw + L.fdst);      // their states (kFdState each)
   int* lefd = reinterpret_cast<int*>(smem_raw + L.lefd);            // per line end: FD end or -1
   int* cecnt = reinterpret_cast<int*>(smem_raw + L.cecnt);          // per coupled end: modes collected this step
+  double* nlz = reinterpret_cast<double*>(smem_raw + L.nlz);        // nonlinear resistor's column z (current matrix)
+  float* nlzl = reinterpret_cast<float*>(smem_raw + L.nlzl);
+  __shared__ NlDev s_nl;
+  __shared__ double s_nlc[1 + 3 * (kNlMaxPoints + 1)];
+  __shared__ double s_inl;
 
   const int sidx = blockIdx.x;
   const SubDev S = P.sub[sidx];
@@ -707,6 +758,18 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       gilo[r * ldg + c] = P.ginv_lo[off + i];
     }
   }
+  // nonlinear resistor: its record and the column of the current matrix;
+  // its constants are (re)computed before the first compensation after a load
+  const int n_nl = S.n_nl;
+  bool nl_dirty = n_nl > 0;
+  if (n_nl > 0) {
+    if (tid == 0) s_nl = P.nl[S.nl_off];
+    const int64_t zoff = P.ep[S.ep_off + tag_cur].nlz_off;
+    for (int i = tid; i < n; i += T) {
+      nlz[i] = P.nlz[zoff + i];
+      nlzl[i] = P.nlz_lo[zoff + i];
+    }
+  }
   __syncthreads();
   for (int x = tid; x < n_sb; x += T) inp[n_lc + x] = sbg[x] * vs[(P.n0 & 1) * src_vs + sbsrc[x]];
   for (int t = tid; t < n_str; t += T) {
@@ -749,6 +812,14 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       word = new_word;
       const int entry = te * n_states + word;
       if (entry != tag_cur) {
+        if (n_nl > 0) {   // the nonlinear resistor's column follows the matrix
+          const int64_t zoff = P.ep[S.ep_off + entry].nlz_off;
+          for (int i = tid; i < n; i += T) {
+            nlz[i] = P.nlz[zoff + i];
+            nlzl[i] = P.nlz_lo[zoff + i];
+          }
+          nl_dirty = true;
+        }
         if (P.lim.nbuf > 1) {   // the other buffer: a hit, or overwritten below
           cur_buf ^= 1;
           const int t = tag_cur;
@@ -824,6 +895,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
 
     // node voltages
     const bool rec_now = P.rec != nullptr && dec == 0 && rec_row < P.rec_rows;
+    const long long row_now = rec_row;
     for (int r = tid; r < n; r += T) {
       // the X_hi partial sums in double, the X_lo ones in single precision
       double v = part[r * Q];
@@ -834,11 +906,30 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       }
       v += (double)vl;
       vv[r] = v;
-      if (rec_now && recp[r] >= 0) P.rec[(rec_row - P.rec_row0) * P.n_rec + recp[r]] = v;
+      if (rec_now && n_nl == 0 && recp[r] >= 0) P.rec[(row_now - P.rec_row0) * P.n_rec + recp[r]] = v;
     }
     if (dec == 0) ++rec_row;
     if (++dec == decim) dec = 0;
     __syncthreads();
+
+    // compensation method: the nonlinear resistor against the linear
+    // solution, its current from the Thevenin source, then v -= z i
+    if (n_nl > 0) {
+      if (tid == 0) {
+        if (nl_dirty) nl_setup(s_nl, nlz, nlzl, s_nlc);
+        const double vth = (s_nl.k >= 0 ? vv[s_nl.k] : 0.0) - (s_nl.m >= 0 ? vv[s_nl.m] : 0.0);
+        s_inl = nl_current(s_nl, s_nlc, vth);
+      }
+      nl_dirty = false;
+      __syncthreads();
+      const double inl = s_inl;
+      for (int r = tid; r < n; r += T) {
+        const double v = fma(-(double)nlzl[r], inl, fma(-nlz[r], inl, vv[r]));
+        vv[r] = v;
+        if (rec_now && recp[r] >= 0) P.rec[(row_now - P.rec_row0) * P.n_rec + recp[r]] = v;
+      }
+      __syncthreads();
+    }
 
     // process 1: history currents, line outputs, next step's source
     // injections; the poll warp meanwhile collects next step's line values

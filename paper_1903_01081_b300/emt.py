@@ -55,6 +55,8 @@ class _NetworkDesc(ctypes.Structure):
         ("fl_tau", ctypes.c_void_p), ("fl_y0", ctypes.c_void_p), ("fl_ny", ctypes.c_void_p),
         ("fl_yq", ctypes.c_void_p), ("fl_yc", ctypes.c_void_p), ("fl_a0", ctypes.c_void_p),
         ("fl_na", ctypes.c_void_p), ("fl_ap", ctypes.c_void_p), ("fl_ar", ctypes.c_void_p),
+        ("n_nonlin", ctypes.c_int64), ("nl_k", ctypes.c_void_p), ("nl_m", ctypes.c_void_p),
+        ("nl_np", ctypes.c_void_p), ("nl_v", ctypes.c_void_p), ("nl_i", ctypes.c_void_p),
     ]
 
 
@@ -188,6 +190,10 @@ def network_desc(net, keep: list) -> _NetworkDesc:
     d.fl_yq, d.fl_yc = p(rs("fl_yq", np.float64), np.float64), p(rs("fl_yc", np.float64), np.float64)
     d.fl_a0 = p(rs("fl_a0", np.float64), np.float64)
     d.fl_ap, d.fl_ar = p(rs("fl_ap", np.float64), np.float64), p(rs("fl_ar", np.float64), np.float64)
+    d.n_nonlin = int(len(rs("nl_k", np.int32)))
+    d.nl_k, d.nl_m = p(rs("nl_k", np.int32), np.int32), p(rs("nl_m", np.int32), np.int32)
+    d.nl_np = p(rs("nl_np", np.int32), np.int32)
+    d.nl_v, d.nl_i = p(rs("nl_v", np.float64), np.float64), p(rs("nl_i", np.float64), np.float64)
     return d
 
 

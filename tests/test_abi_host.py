@@ -170,3 +170,20 @@ def test_rejects_bad_fd_lines():
     sc_net, sc = g.n1_contingency(n_scenarios=4, n_buses=24, n_sub=4, n_steps=10)
     with pytest.raises(emt.EmtError, match="frequency-dependent lines are not supported"):
         emt.emt_build_network(g.with_fd_lines(sc_net), sc)
+
+
+def test_rejects_bad_nonlinear():
+    base = g.multi_subsystem(41, [4, 5, 3], n_lines=4, n_sources=2, dt=20e-6)
+    net = g.with_arresters(base, n_arresters=2)
+    v = net.nl_v.copy(); v[1] = v[0]
+    assert "breakpoints" in bad(net, nl_v=v)
+    assert "1 to 8" in bad(net, nl_np=np.array([9, 6], np.int32))
+    assert "ground" in bad(net, nl_k=np.array([-1, net.nl_k[1]], np.int32))
+    from oracle import partition
+    sub, _ = partition(net)
+    same = [x for x in range(net.n_nodes) if sub[x] == sub[net.nl_k[0]] and x != net.nl_k[0]][0]
+    k = net.nl_k.copy(); k[1] = same
+    assert "more than one nonlinear resistor" in bad(net, nl_k=k)
+    sc_net, sc = g.n1_contingency(n_scenarios=4, n_buses=24, n_sub=4, n_steps=10)
+    with pytest.raises(emt.EmtError, match="nonlinear resistors are not supported"):
+        emt.emt_build_network(g.with_arresters(sc_net, n_arresters=1), sc)

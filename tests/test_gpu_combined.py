@@ -1,7 +1,7 @@
 """All network features in one run: Bergeron lines, coupled three-phase lines,
 frequency-dependent lines, runtime switches (diodes, a breaker), scheduled
-switches and control blocks with controlled injections, against the oracle
-over several launches."""
+switches, nonlinear resistors and control blocks with controlled
+injections, against the oracle over several launches."""
 import numpy as np
 import pytest
 
@@ -16,6 +16,7 @@ def combined_network():
     coupled = g.with_coupled_lines(base)                 # every three-phase line becomes a coupled line
     net = g.with_converter_controls(coupled, n_converters=4)
     net = g.with_rectifier_loads(net, n_rectifiers=3, n_breakers=1, trip_range=(300, 600))
+    net = g.with_arresters(net, n_arresters=3)
     sub, n_sub = oracle.partition(net)
     rng = np.random.default_rng(5)
     # three frequency-dependent lines and one plain Bergeron line between subsystems
@@ -48,6 +49,7 @@ def test_all_features_together():
     net = combined_network()
     assert net.n_coupled_lines > 0 and net.n_fd_lines == 3 and net.n_lines == 1
     assert net.n_runtime_switches == 4 and net.n_control_blocks == 96 and net.n_switches == 1
+    assert net.n_nonlinear == 3
     N = 2400
     ref = oracle.simulate(net, N)
     # no diode decision within rounding of its threshold on the oracle's run

@@ -1,0 +1,84 @@
+"""GPU parity of nonlinear resistors solved by the compensation method
+(odd piecewise-linear surge-arrester characteristics) against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_01081_b300 import emt, netgen as g
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+def gpu_run(net, N, chunks=None):
+    sim = emt.Simulator(net, n_steps=N)
+    for c in (chunks or [N]):
+        sim.run(c)
+    sim.sync()
+    w = sim.waveforms()[:, 0, :]
+    sim.close()
+    return w
+
+
+def test_arresters_large_scale():
+    net = g.with_arresters(g.large_scale(n_steps=3000))
+    sim = emt.Simulator(net, n_steps=1)
+    assert sim.info("n_nonlinear") == 40
+    sim.close()
+    ref = oracle.simulate(net, 3000)
+    assert rel(gpu_run(net, 3000), ref) <= TOL
+    assert np.max(np.abs(ref[:, net.nl_k])) > g.ARRESTER_V[0]        # some arresters conduct
+
+
+def test_arresters_large_scale_full_length():
+    net = g.with_arresters(g.large_scale())
+    assert rel(gpu_run(net, net.n_steps), oracle.simulate(net, net.n_steps)) <= TOL
+
+
+def test_resistive_circuit_past_the_last_point():
+    b = g.NetworkBuilder()
+    b.source(20000.0, 0.2, 60.0)
+    b.branch(g.source_node(0), 0, g.KIND_R, 2.0)
+    b.branch(0, g.GROUND, g.KIND_R, 50.0)
+    b.nonlinear_resistor(0, g.GROUND, g.ARRESTER_V, g.ARRESTER_I)
+    b.branch(0, 1, g.KIND_L, 0.01)                       # a second node and a dynamic element
+    b.branch(1, g.GROUND, g.KIND_C, 30e-6)
+    net = b.build(20e-6, 2)
+    ref = oracle.simulate(net, 2500)
+    assert np.max(np.abs(ref[:, 0])) > g.ARRESTER_V[-1]
+    assert rel(gpu_run(net, 2500), ref) <= TOL
+
+
+def test_node_to_node_element_with_switching():
+    """An element between two unknown nodes, in a subsystem whose matrix
+    changes with a scheduled switch and a diode (its column follows)."""
+    b = g.NetworkBuilder()
+    b.source(1500.0, 0.3, 60.0)
+    b.branch(g.source_node(0), 0, g.KIND_R, 1.0)
+    b.branch(0, 1, g.KIND_L, 0.02)
+    b.branch(1, g.GROUND, g.KIND_R, 40.0)
+    b.branch(0, g.GROUND, g.KIND_C, 20e-6)
+    b.nonlinear_resistor(0, 1, [300.0, 600.0, 900.0], [0.1, 50.0, 400.0])
+    b.switch(1, g.GROUND, 2.0, 700, 1600)
+    b.diode(1, 2, 0.01, 1e6)
+    b.branch(2, g.GROUND, g.KIND_R, 30.0)
+    b.branch(2, g.GROUND, g.KIND_C, 50e-6)
+    net = b.build(20e-6, 3)
+    ref = oracle.simulate(net, 3000)
+    a = gpu_run(net, 3000)
+    bb = gpu_run(net, 3000, chunks=[650, 1, 1000, 1349])
+    assert np.array_equal(a, bb)
+    assert rel(a, ref) <= TOL
+
+
+def test_adjoint_rejects_nonlinear():
+    net = g.with_arresters(g.multi_subsystem(41, [4, 5, 3], n_lines=4, n_sources=2, dt=20e-6), n_arresters=1)
+    ctx = emt.emt_build_network(net)
+    emt.emt_prefactor(ctx)
+    with pytest.raises(emt.EmtError, match="nonlinear resistors have no adjoint"):
+        emt.emt_adjoint(ctx, np.zeros((10, net.n_nodes)), 10)
+    emt.emt_destroy(ctx)
