@@ -328,15 +328,33 @@ __global__ void ring_init_kernel(RingInitParams P) {
 constexpr int kPollWarp = kFwdThreads / 32 - 1;
 constexpr int kItemThreads = kFwdThreads - 32;
 
+// A CTA's nonlinear resistor in shared memory: its record, the constants
+// of the current matrix (see nl_setup), the current of the step, the record
+// row of the step being compensated (or -1) and whether the constants need
+// recomputing after a matrix load; then the current matrix's column z
+// (n doubles, then n floats of remainder).  Its address is recomputed where
+// it is used (only CTAs with a nonlinear resistor), so that the step loop of
+// the others keeps no extra pointer live.
+struct NlState {
+  NlDev q;
+  double c[1 + 3 * (kNlMaxPoints + 1)];
+  double inl;
+  long long row;
+  int dirty;
+  int pad;
+  __device__ double* z() { return reinterpret_cast<double*>(this + 1); }
+  __device__ float* zl(int n) { return reinterpret_cast<float*>(z() + n); }
+};
+
 // Shared-memory layout of fwd_kernel, from the per-launch limits.  G^-1
 // rows are stored with an odd stride (n | 1) so that the rows a warp reads
 // together fall in different banks.
 struct FwdSmem {
   size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar, lef, imode, ceti, cetinv, cbr, cy, cs, fdr,
-      fdst, nlz;                                                                           // 8-byte
+      fdst, nls;                                                                           // 8-byte
   size_t gilo, ivf, partf;                                                                 // float
   size_t lck, lcm, lckind, lcstr, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, recp,
-      lece, lemode, cele0, cenode, clay, cinj, lefd, cecnt, nlzl;                          // int / float
+      lece, lemode, cele0, cenode, clay, cinj, lefd, cecnt;                                // int
   size_t bytes;
 };
 
@@ -366,7 +384,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.cbr = d16(sizeof(CtrlDev) / 8 * (size_t)L.cb);
   s.cy = d16(2 * (size_t)L.cb + 2);
   s.cs = d16(2 * (size_t)L.cb);
-  s.nlz = d(L.nl ? (size_t)L.n : 0);
+  s.nls = d(L.nl ? sizeof(NlState) / 8 + (size_t)L.n + ((size_t)L.n + 1) / 2 : 0);
   s.fdr = d(sizeof(FdEndDev) / 8 * (size_t)L.fd);
   s.fdst = d(kFdState * (size_t)L.fd);
   s.gilo = w(nbuf * (size_t)L.n * ldg);
@@ -394,7 +412,6 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.clay = w(L.clay);
   s.cinj = w(L.ci);
   s.lefd = w(L.le);
-  s.nlzl = w(L.nl ? (size_t)L.n : 0);
   s.cecnt = w(L.ce);
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
@@ -520,6 +537,32 @@ __device__ double nl_current(const NlDev& q, const double* c, double vth) {
   return vth < 0.0 ? -i : i;
 }
 
+// The compensation step of a CTA with a nonlinear resistor (after the node
+// sums, two barriers inside; every thread of the CTA calls it): the current
+// from the Thevenin source on thread 0, then v -= z i and the record.
+__device__ __forceinline__ void compensate(const FwdParams& P, int n, NlState* s, double* vv, const int* recp) {
+  const int tid = threadIdx.x, T = blockDim.x;
+  const double* z = s->z();
+  const float* zl = s->zl(n);
+  if (tid == 0) {
+    if (s->dirty) {
+      nl_setup(s->q, z, zl, s->c);
+      s->dirty = 0;
+    }
+    const double vth = (s->q.k >= 0 ? vv[s->q.k] : 0.0) - (s->q.m >= 0 ? vv[s->q.m] : 0.0);
+    s->inl = nl_current(s->q, s->c, vth);
+  }
+  __syncthreads();
+  const double inl = s->inl;
+  const long long row = s->row;
+  for (int r = tid; r < n; r += T) {
+    const double v = fma(-(double)zl[r], inl, fma(-z[r], inl, vv[r]));
+    vv[r] = v;
+    if (row >= 0 && recp[r] >= 0) P.rec[(row - P.rec_row0) * P.n_rec + recp[r]] = v;
+  }
+  __syncthreads();
+}
+
 // A frequency-dependent line end's history at step m, folded by the poll
 // lane that just collected its ring value w_far(m - d) (so the fold of an
 // early value hides behind the wait for a late one): W(m) interpolated like
@@ -625,11 +668,6 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   double* fdst = reinterpret_cast<double*>(smem_raw + L.fdst);      // their states (kFdState each)
   int* lefd = reinterpret_cast<int*>(smem_raw + L.lefd);            // per line end: FD end or -1
   int* cecnt = reinterpret_cast<int*>(smem_raw + L.cecnt);          // per coupled end: modes collected this step
-  double* nlz = reinterpret_cast<double*>(smem_raw + L.nlz);        // nonlinear resistor's column z (current matrix)
-  float* nlzl = reinterpret_cast<float*>(smem_raw + L.nlzl);
-  __shared__ NlDev s_nl;
-  __shared__ double s_nlc[1 + 3 * (kNlMaxPoints + 1)];
-  __shared__ double s_inl;
 
   const int sidx = blockIdx.x;
   const SubDev S = P.sub[sidx];
@@ -761,13 +799,16 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
   // nonlinear resistor: its record and the column of the current matrix;
   // its constants are (re)computed before the first compensation after a load
   const int n_nl = S.n_nl;
-  bool nl_dirty = n_nl > 0;
   if (n_nl > 0) {
-    if (tid == 0) s_nl = P.nl[S.nl_off];
+    NlState* nls = reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls);
+    if (tid == 0) {
+      nls->q = P.nl[S.nl_off];
+      nls->dirty = 1;
+    }
     const int64_t zoff = P.ep[S.ep_off + tag_cur].nlz_off;
     for (int i = tid; i < n; i += T) {
-      nlz[i] = P.nlz[zoff + i];
-      nlzl[i] = P.nlz_lo[zoff + i];
+      nls->z()[i] = P.nlz[zoff + i];
+      nls->zl(n)[i] = P.nlz_lo[zoff + i];
     }
   }
   __syncthreads();
@@ -813,12 +854,13 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       const int entry = te * n_states + word;
       if (entry != tag_cur) {
         if (n_nl > 0) {   // the nonlinear resistor's column follows the matrix
+          NlState* nls = reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls);
           const int64_t zoff = P.ep[S.ep_off + entry].nlz_off;
           for (int i = tid; i < n; i += T) {
-            nlz[i] = P.nlz[zoff + i];
-            nlzl[i] = P.nlz_lo[zoff + i];
+            nls->z()[i] = P.nlz[zoff + i];
+            nls->zl(n)[i] = P.nlz_lo[zoff + i];
           }
-          nl_dirty = true;
+          if (tid == 0) nls->dirty = 1;
         }
         if (P.lim.nbuf > 1) {   // the other buffer: a hit, or overwritten below
           cur_buf ^= 1;
@@ -895,7 +937,6 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
 
     // node voltages
     const bool rec_now = P.rec != nullptr && dec == 0 && rec_row < P.rec_rows;
-    const long long row_now = rec_row;
     for (int r = tid; r < n; r += T) {
       // the X_hi partial sums in double, the X_lo ones in single precision
       double v = part[r * Q];
@@ -906,30 +947,17 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       }
       v += (double)vl;
       vv[r] = v;
-      if (rec_now && n_nl == 0 && recp[r] >= 0) P.rec[(row_now - P.rec_row0) * P.n_rec + recp[r]] = v;
+      if (rec_now && recp[r] >= 0) P.rec[(rec_row - P.rec_row0) * P.n_rec + recp[r]] = v;
     }
+    if (n_nl > 0 && tid == 0)   // rewritten after the compensation
+      reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls)->row = rec_now ? rec_row : -1;
     if (dec == 0) ++rec_row;
     if (++dec == decim) dec = 0;
     __syncthreads();
 
     // compensation method: the nonlinear resistor against the linear
     // solution, its current from the Thevenin source, then v -= z i
-    if (n_nl > 0) {
-      if (tid == 0) {
-        if (nl_dirty) nl_setup(s_nl, nlz, nlzl, s_nlc);
-        const double vth = (s_nl.k >= 0 ? vv[s_nl.k] : 0.0) - (s_nl.m >= 0 ? vv[s_nl.m] : 0.0);
-        s_inl = nl_current(s_nl, s_nlc, vth);
-      }
-      nl_dirty = false;
-      __syncthreads();
-      const double inl = s_inl;
-      for (int r = tid; r < n; r += T) {
-        const double v = fma(-(double)nlzl[r], inl, fma(-nlz[r], inl, vv[r]));
-        vv[r] = v;
-        if (rec_now && recp[r] >= 0) P.rec[(row_now - P.rec_row0) * P.n_rec + recp[r]] = v;
-      }
-      __syncthreads();
-    }
+    if (n_nl > 0) compensate(P, n, reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls), vv, recp);
 
     // process 1: history currents, line outputs, next step's source
     // injections; the poll warp meanwhile collects next step's line values
