@@ -27,6 +27,7 @@
 #include <cuda_runtime.h>
 
 #include "emt_internal.h"
+#include "emt_device.cuh"
 
 namespace emt {
 
@@ -52,7 +53,8 @@ __device__ __forceinline__ double entry_value(const BatchParams& P, uint32_t raw
   } else {
     val = P.ring[(__ldg(P.le_bring + idx) + ring_slot(step, __ldg(P.le_d1 + idx))) * P.S + sg];
   }
-  return (raw & kEntryNeg) ? -val : val;
+  // the sign by flipping the sign bit (integer pipe)
+  return __longlong_as_double(__double_as_longlong(val) ^ ((long long)(raw & kEntryNeg) << 32));
 }
 
 __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams P) {
@@ -142,7 +144,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
           acc = -P.h[(int64_t)(-1 - code) * S + sg];
         }
         iv[x] = acc;
-        ivf[x] = (float)acc;
+        ivf[x] = f32_trunc(acc);
       }
       __syncthreads();
 
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
           a = fma(__ldg(row + j), ivc[(size_t)j * St], a);
           b = fmaf(__ldg(rowl + j), ivfc[(size_t)j * St], b);
         }
-        const double v = a + (double)b;
+        const double v = a + f64_of(b);
         vv[x] = v;
         if (rec_now) {
           const int pos = P.rec_pos[node];

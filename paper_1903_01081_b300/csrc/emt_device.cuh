@@ -33,6 +33,31 @@ __device__ __forceinline__ bool ld_tagged(const unsigned long long* p, unsigned 
   return true;
 }
 
+// double -> float by truncation, on the integer pipe (a conversion
+// instruction would take the slow FP64 pipe on B300).  Only for the
+// single-precision correction chains, where the truncation error (< 1 ulp
+// of a float) is far below what they correct; values below 2^-126 become 0
+// and finite values stay finite (|x| < 2^128 on these paths).
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32);
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const unsigned sign = hi & 0x80000000u;
+  if (e <= 0) return __uint_as_float(sign);
+  return __uint_as_float(sign | ((unsigned)e << 23) | (unsigned)((b >> 29) & 0x7fffffull));
+}
+
+// float -> double, exact for normal floats, on the integer pipe (subnormal
+// floats become 0: they only occur as corrections below 2^-126).
+__device__ __forceinline__ double f64_of(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0) return __longlong_as_double((long long)sign);
+  return __longlong_as_double((long long)(sign | ((unsigned long long)(e - 127 + 1023) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
 // Wait for a ring slot to carry `tag` and return its value.  Bounded: on
 // exceeding the time budget (or seeing another CTA's error) it latches an
 // error {5, subsystem, line end, tag} and returns false.  Params: the
