@@ -143,7 +143,7 @@ __device__ bool collect_adj(const AdjParams& P, int n_le, unsigned tag, int lane
   return __all_sync(0xffffffffu, ok);
 }
 
-// Coupled line modes in reverse (poll warp, after collecting): the adjoint
+// Coupled line modes in reverse (first reverse step of a launch, after collecting): the adjoint
 // of the value each mode sent, X = (1 - f) Ibar_far(n + d) + f Ibar_far(n + d
 // + 1), from the values consumed at this reverse step (xr_new) and the
 // previous one (xr_old); then the phase slots sum_j T_i[p][j] (2/Z_j) X_j

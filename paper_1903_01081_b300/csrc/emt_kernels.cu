@@ -325,6 +325,9 @@ __global__ void ring_init_kernel(RingInitParams P) {
 // values are collected by the update threads once their items are done, one
 // thread per line end (per coupled end), so that all waits run at once.
 
+// the last warp: collects the first step's line values of a launch, and
+// serves the source-value prefetch; the warp before it evaluates control
+// blocks when the subsystem has some
 constexpr int kPollWarp = kFwdThreads / 32 - 1;
 constexpr int kItemThreads = kFwdThreads - 32;
 
@@ -417,8 +420,9 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   return s;
 }
 
-// Coupled line modes (poll warp, after collecting step m's values into
-// blk_new): each mode's interpolated history I_mode(m) = (1 - f) c(m - d)
+// Coupled line modes at the first step of a launch (the last warp, after
+// collecting step m's values into blk_new; later steps fold them as they
+// arrive): each mode's interpolated history I_mode(m) = (1 - f) c(m - d)
 // + f c(m - d - 1) from the values consumed at steps m (blk_new) and m - 1
 // (blk_old), then the phase-domain history currents T_i I_mode of each
 // coupled end into the phase slots that follow the n_le line-end slots.
@@ -960,7 +964,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
     if (n_nl > 0) compensate(P, n, reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls), vv, recp);
 
     // process 1: history currents, line outputs, next step's source
-    // injections; the poll warp meanwhile collects next step's line values
+    // injections; then the update threads collect next step's line values
     if (warp == kPollWarp) {
       // (the update threads collect the next step's line values below)
     } else if (n_cb > 0 && warp == kPollWarp - 1) {
