@@ -21,6 +21,8 @@ two further legs the metric names, reported as extra keys of the line:
   "adjoint": emt_adjoint time over the forward time for the gradient of
       sum_n ||v_n - v*_n||^2 over 20,000 steps of the large-scale network
       with checkpoints every 256 steps (and with the whole tape kept);
+  "small_network": the 12-node single-subsystem network (latency of one
+      CTA's dependent chain), with parity over every step;
   "runtime_switches": the large-scale network with 30 diode-rectifier loads
       and 10 current-zero breakers, against the same network without them;
   "coupled_lines": the large-scale network with its three-phase lines as
@@ -246,21 +248,23 @@ def _oracle_scenario(args):
     return time.perf_counter() - t0
 
 
-def oracle_scenario_baseline(net, sc, n_scen, n_steps):
-    """The CPU oracle as it stands on the first `n_scen` scenarios of a study,
-    `n_steps` steps each, one scenario per process over the host's cores (a
-    spawn pool: the parent already holds a CUDA context).  The rate divides
-    the scenario-steps by the busy time per core (pool start-up excluded)."""
+def oracle_scenario_baseline(net, sc, n_scen, n_steps, seed=64):
+    """The CPU oracle as it stands on a seeded subset of `n_scen` scenarios
+    of a study, `n_steps` steps each, one scenario per process over the
+    host's cores (a spawn pool: the parent already holds a CUDA context).
+    The rate divides the scenario-steps by the busy time per core (pool
+    start-up excluded), and extrapolates per scenario-step."""
     import multiprocessing as mp
     from concurrent.futures import ProcessPoolExecutor
+    picks = sorted(np.random.default_rng(seed).choice(sc.n_scenarios, size=n_scen, replace=False).tolist())
     workers = max(1, min(os.cpu_count() or 1, n_scen))
     # an executor, not a Pool: a worker that dies raises here instead of hanging
     with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
-        secs = list(ex.map(_oracle_scenario, [(net, sc, s_, n_steps) for s_ in range(n_scen)], timeout=600))
+        secs = list(ex.map(_oracle_scenario, [(net, sc, s_, n_steps) for s_ in picks], timeout=600))
     total = float(sum(secs))
     return {"value": n_scen * n_steps / (total / workers), "unit": "scenario-steps/s", "cores": workers,
             "kind": "oracle", "single_thread_value": n_scen * n_steps / total,
-            "sample": f"scenarios 0..{n_scen - 1}, {n_steps} steps each, one process per core"}
+            "sample": f"{n_scen} seeded scenarios, {n_steps} steps each, one process per core"}
 
 
 def scenario_legs(which=("n1", "shared_g"), steps=None, shape=None, warm=500, cpu=False):
@@ -272,7 +276,7 @@ def scenario_legs(which=("n1", "shared_g"), steps=None, shape=None, warm=500, cp
         out["n1_contingency"] = dict(workload="N-1: 600-node three-phase network, 40 subsystems, one connection "
                                               "removed + three-phase fault at step 2,500 per scenario", **n1)
         if cpu:
-            out["n1_contingency"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 32, 3000)
+            out["n1_contingency"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 64, 3000)
     if "shared_g" in which:
         net, sc = g.shared_g()
         sg = scenario_leg("shared_g", net, sc, steps or 3000, 2, list(range(0, net.n_nodes, 50)), 10, 20, warm,
@@ -280,7 +284,7 @@ def scenario_legs(which=("n1", "shared_g"), steps=None, shape=None, warm=500, cp
         out["shared_g"] = dict(workload="large-scale network, per-scenario source amplitude/phase and fault "
                                         "resistance at step 2,500; 3,000 of 10,000 steps timed", **sg)
         if cpu:
-            out["shared_g"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 16, 3000)
+            out["shared_g"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 64, 1000)
     return out
 
 
@@ -333,7 +337,54 @@ def adjoint_leg(steps=None, reps=3):
             "adjoint_ms_full_tape": res[0], "ratio_full_tape": res[0] / t_fwd,
             "timing": "wall time of the emt_adjoint call (allocations, forward with checkpoints, re-runs, reverse "
                       "sweep, gradient copy) over the CUDA-event time of emt_step_n for the same 20,000 steps",
-            "loss": J}
+            "loss": J, "cpu_baseline": oracle_adjoint_baseline(net, tgt, min(2000, N), N)}
+
+
+def oracle_adjoint_baseline(net, tgt, n_sample, n_full):
+    """The CPU oracle's full-tape adjoint (one thread) on the first n_sample
+    steps of the same target, scaled to the leg's step count."""
+    import oracle
+    tg = tgt[:n_sample].cpu().numpy()
+    t0 = time.perf_counter()
+    oracle.adjoint(net, n_sample, tg)
+    sec = time.perf_counter() - t0
+    return {"seconds_for_sample": round(sec, 3), "sample_steps": n_sample, "cores": 1, "kind": "oracle",
+            "estimated_ms_full": 1e3 * sec * n_full / n_sample,
+            "sample": f"oracle adjoint (whole tape, 1 thread) over steps 1..{n_sample}, scaled to {n_full:,} steps"}
+
+
+def small_network_leg(reps=3):
+    """The 12-node single-subsystem RLC network with its fault at step 2,000:
+    20,000 steps, one CTA (latency of the dependent chain), parity over all
+    steps, and the CPU oracle on the same run."""
+    import torch
+    import oracle
+    from paper_1903_01081_b300 import emt, netgen as g
+    net = g.single_rlc()
+    N = net.n_steps
+    sim = emt.Simulator(net, n_steps=N)
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(reps):
+        sim.reset()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.run(N, stream)
+        e1.record(stream)
+        sim.sync()
+        ms.append(e0.elapsed_time(e1))
+    w = sim.waveforms()[:, 0, :]
+    sim.close()
+    t0 = time.perf_counter()
+    ref = oracle.simulate(net, N)
+    cpu = time.perf_counter() - t0
+    t = float(np.median(ms))
+    return {"workload": "12-node single-phase RLC network, 20 branches, 1 kV source, 0.01 ohm fault at step 2,000; "
+                        "dt 50 us, 20,000 steps, all nodes recorded",
+            "ms": t, "us_per_step": 1e3 * t / N, "node_steps_per_s": net.n_nodes * N / (t / 1e3),
+            "parity_rel_err_all_steps": float(np.max(np.abs(w - ref)) / np.max(np.abs(ref))),
+            "cpu_baseline": {"value": net.n_nodes * N / cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "the whole run, 1 thread"}}
 
 
 def variant_leg(variant, workload, steps=None, reps=3, extra=None):
@@ -590,7 +641,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
             "parity_rel_err_first_2000_steps": parity,
-            **({"scenarios": scenario_legs(cpu=True), "adjoint": adjoint_leg(), "runtime_switches": runtime_switch_leg(),
+            **({"scenarios": scenario_legs(cpu=True), "adjoint": adjoint_leg(), "small_network": small_network_leg(), "runtime_switches": runtime_switch_leg(),
                 "coupled_lines": coupled_line_leg(), "fd_lines": fd_line_leg(), "nonlinear": nonlinear_leg(),
                 "controls": control_leg()}
                if args.leg == "all" else {}),
