@@ -219,8 +219,9 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
   const int sidx = blockIdx.x;
   const SubDev S = P.sub[sidx];
   const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int n = S.n, Q = S.q, n_str = S.n_str, nc = n + n_str, ldg = nc | 1;
+  const int n = S.n, Q = S.q, n_str = S.n_str, nc = n + n_str;
   const int blk = (nc + Q - 1) / Q;
+  const int ldg = (Q * blk) | 1;   // columns nc .. Q blk - 1 are zero
   const int n_br = S.n_br, n_lc = S.n_lc, n_sb = S.n_sb, n_le = S.n_le, n_il = S.n_il, n_src = S.n_src;
   const int n_ce = S.n_ce;
   const int ie_base = n_lc + n_sb;
@@ -319,6 +320,16 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
       gi[r * ldg + c] = P.ginv[off + i];
       gilo[r * ldg + c] = P.ginv_lo[off + i];
     }
+    const int pad = Q * blk - nc;   // the padding columns (reloads leave them zero)
+    for (int i = tid; i < n * pad; i += T) {
+      const int r = i / pad, c = nc + i - r * pad;
+      gi[r * ldg + c] = 0.0;
+      gilo[r * ldg + c] = 0.f;
+    }
+    for (int c = nc + tid; c < Q * blk; c += T) {
+      iv[c] = 0.0;
+      ivf[c] = 0.f;
+    }
   }
   __syncthreads();
   for (int t = tid; t < n_str; t += T) {
@@ -400,10 +411,9 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
       const int r = task / Q, q = task - r * Q;
       const double* row = gi + r * ldg;
       const float* rowl = gilo + r * ldg;
-      const int j1 = min(nc, (q + 1) * blk);
       double a = 0.0;
       float b = 0.f;
-      for (int j = q * blk; j < j1; ++j) {
+      for (int j = q * blk; j < (q + 1) * blk; ++j) {
         a = fma(row[j], iv[j], a);
         b = fmaf(rowl[j], ivf[j], b);
       }

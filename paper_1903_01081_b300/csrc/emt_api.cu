@@ -1391,6 +1391,10 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     const int q = (int)std::lround(std::sqrt((double)(n + sd.n_str)));
     sd.q = std::max(1, std::min(q, kFwdThreads / n));
     c->lim.q = std::max(c->lim.q, sd.q);
+    // every task runs the same number of columns (zero columns pad the
+    // last block), so that no warp diverges inside the FMA loop
+    const int nc = sd.n + sd.n_str;
+    c->lim.nc = std::max(c->lim.nc, sd.q * ((nc + sd.q - 1) / sd.q));
   }
 
   // -------- two solve-matrix buffers per CTA when runtime switches change

@@ -929,6 +929,7 @@ __global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
       const int j1 = min(nc, (q + 1) * blk);
       double a = 0.0;
       float b = 0.f;
+#pragma unroll 2   // measured: 2 beats 1, 3 and 4 (the loop is not unrolled by default)
       for (int j = q * blk; j < j1; ++j) {
         a = fma(row[j], iv[j], a);
         b = fmaf(rowl[j], ivf[j], b);
