@@ -32,7 +32,10 @@ two further legs the metric names, reported as extra keys of the line:
   "nonlinear": the same with 40 surge arresters solved by the compensation
       method, against the plain one;
   "controls": the same with 180 converter loads (4,320 layered control
-      blocks driving controlled current injections), against the plain one.
+      blocks driving controlled current injections), against the plain one;
+  "sizes": the same family as 500 subsystems of 6 nodes, and as the most
+      subsystems of 6..60 nodes that stay co-resident (up to 440, 14,520
+      nodes).
 
 N > 1 runs N independent replicas (the single-network path does not shard:
 its subsystems exchange line values every few steps), launched by
@@ -170,6 +173,49 @@ def algorithmic_flops_per_step(net, sim) -> float:
     n_sb = int(np.sum((np.asarray(net.br_k) <= -2) | (np.asarray(net.br_m) <= -2)))
     n_le = 2 * net.n_lines
     return 2.0 * sum_n2 + (2 * n_lc + n_sb + n_le) + 3 * n_lc + 2 * n_le + n_sb
+
+
+def sparse_solve_flops_per_step(net) -> dict:
+    """The solve as the paper's own processes 3-4 do it (sparse LU once,
+    forward and back substitution every step; Sec. III-A), counted for the
+    same subsystems at the first step's switch state: 2 (nnz(L) + nnz(U))
+    - 3 n flop per subsystem with SuperLU's COLAMD ordering, against the
+    explicit inverse's 2 n^2.  Reported beside the roofline, not used as its
+    work (the method here is the dense prefactored inverse)."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    from scipy.sparse.linalg import splu
+    n = int(net.n_nodes)
+    gk, gm, gv = [], [], []
+    dt = float(net.dt)
+    for k, m, kind, val in zip(net.br_k, net.br_m, net.br_kind, net.br_value):
+        g = 1.0 / val if kind == 0 else (dt / (2.0 * val) if kind == 1 else 2.0 * val / dt)
+        gk.append(int(k)); gm.append(int(m)); gv.append(g)
+    for k, m, r, c0, c1 in zip(net.sw_k, net.sw_m, net.sw_r, net.sw_close_step, net.sw_open_step):
+        if c0 <= 1 and (c1 < 0 or 1 < c1):
+            gk.append(int(k)); gm.append(int(m)); gv.append(1.0 / r)
+    rows, cols, vals = [], [], []
+    for k, m, g in zip(gk, gm, gv):
+        for a in (k, m):
+            if a >= 0:
+                rows.append(a); cols.append(a); vals.append(g)
+        if k >= 0 and m >= 0:
+            rows += [k, m]; cols += [m, k]; vals += [-g, -g]
+    for k, m, z in zip(net.ln_k, net.ln_m, net.ln_zc):
+        for a in (int(k), int(m)):
+            rows.append(a); cols.append(a); vals.append(1.0 / z)
+    G = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    adj = sp.csr_matrix((np.ones(len(rows)), (rows, cols)), shape=(n, n))
+    n_comp, lab = connected_components(adj, directed=False)
+    sparse = dense = 0
+    for c in range(n_comp):
+        idx = np.flatnonzero(lab == c)
+        lu = splu(G[idx][:, idx].tocsc(), permc_spec="COLAMD")
+        sparse += 2 * (lu.L.nnz + lu.U.nnz) - 3 * len(idx)
+        dense += 2 * len(idx) ** 2
+    return {"sparse_lu_substitution_flop_per_step": int(sparse), "dense_inverse_flop_per_step": int(dense),
+            "note": "the paper's sparse LU solve would need this many flop per step for the same subsystems "
+                    "(SuperLU, COLAMD); the explicit inverse does the dense count"}
 
 
 def cpu_baseline(net, n_steps: int):
@@ -496,6 +542,74 @@ def control_leg(steps=None, reps=3):
                        "phase; all nodes recorded", steps, reps, blocks)
 
 
+def size_leg(net, workload, steps, reps=3, n_check=1000, cpu_steps=1000):
+    """node-steps/s of one network from the de-energised state (L2 flushed
+    between runs), its whole-chip and critical-path FP64 fractions, parity
+    on the first steps and the single-thread oracle on a sample."""
+    import torch
+    import oracle
+    from paper_1903_01081_b300 import emt
+    N = steps
+    sim = emt.Simulator(net, n_steps=N)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ms = []
+    for _ in range(reps):
+        sim.reset()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.run(N, stream)
+        e1.record(stream)
+        sim.sync()
+        ms.append(e0.elapsed_time(e1))
+    t = float(np.median(ms)) / 1e3
+    flops = algorithmic_flops_per_step(net, sim)
+    n_max = sim.info("max_subsystem_nodes")
+    out = {"workload": workload, "nodes": int(net.n_nodes), "subsystems": sim.info("n_subsystems"),
+           "largest_subsystem": n_max, "time_steps": N, "ms": 1e3 * t, "us_per_step": 1e6 * t / N,
+           "node_steps_per_s": net.n_nodes * N / t,
+           "fp64_frac_of_derived_peak": flops * N / t / 1e9 / FP64_PEAK_GFLOPS,
+           "critical_path_sm_frac": (2.0 * n_max * n_max) / (t / N) / (FP64_PEAK_GFLOPS / 148 * 1e9),
+           "smem_bytes_per_cta": sim.info("smem_bytes")}
+    n_chk = min(n_check, N)
+    w = sim.waveforms(n_rows=n_chk)[:, 0, :]
+    sim.close()
+    t0 = time.perf_counter()
+    ref = oracle.simulate(net, n_chk)
+    cpu = time.perf_counter() - t0
+    out["parity_rel_err_first_steps"] = float(np.max(np.abs(w - ref)) / np.max(np.abs(ref)))
+    out["parity_steps"] = n_chk
+    out["cpu_baseline"] = {"value": net.n_nodes * n_chk / cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                           "sample": f"the first {n_chk} steps, all nodes recorded, 1 thread"}
+    return out
+
+
+def scale_legs(steps=None, reps=3):
+    """The large-scale family at two other sizes: the strict reading of
+    500 subsystems of 6 nodes (3,000 nodes), and the most subsystems of
+    6..60 nodes (33 on average) that one launch holds co-resident (towards
+    the paper's 16,653-node case)."""
+    import torch
+    from paper_1903_01081_b300 import emt, netgen as g
+    N = steps or 20000
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    for n_sub in (440, 400, 360, 320, 296, 280):   # the largest that stays co-resident
+        net = g.paper_scale(n_sub, n_steps=N)
+        ctx = emt.emt_build_network(net)
+        per_sm = emt.emt_get_info(ctx, "ctas_per_sm")
+        emt.emt_destroy(ctx)
+        if n_sub <= per_sm * n_sm:
+            break
+    return {"strict_500x6": size_leg(g.large_scale(strict_500=True), "strict reading: 500 subsystems of 2 "
+                                     "three-phase buses (3,000 nodes), 700 three-phase lines, 50 sources; dt 20 us",
+                                     N, reps),
+            "paper_scale": size_leg(net, f"{n_sub} subsystems of 2..20 three-phase buses ({net.n_nodes:,} nodes, "
+                                    f"{net.n_branches:,} R/L/C branches, {net.n_lines // 3:,} three-phase lines, "
+                                    f"{net.n_sources // 3} three-phase sources; lines, sources and branches scaled "
+                                    "from the 1,000-bus network); dt 20 us", N, reps)}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -634,7 +748,8 @@ def run_ours(args):
                          # on its one SM: that SM's share of the FP64 peak against the measured step time
                          "critical_path_sm_frac": (2.0 * n_max * n_max) / (per_launch_s / N_STEPS)
                                                   / (FP64_PEAK_GFLOPS / 148 * 1e9),
-                         "critical_path": f"2 n^2 flop of the largest subsystem (n = {n_max}) per step on one SM"},
+                         "critical_path": f"2 n^2 flop of the largest subsystem (n = {n_max}) per step on one SM",
+                       "paper_sparse_solve": sparse_solve_flops_per_step(net)},
             "cpu_baseline": cpu_baseline(net, N_STEPS),
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(N_STEPS * n * 8)},
@@ -643,7 +758,7 @@ def run_ours(args):
             "parity_rel_err_first_2000_steps": parity,
             **({"scenarios": scenario_legs(cpu=True), "adjoint": adjoint_leg(), "small_network": small_network_leg(), "runtime_switches": runtime_switch_leg(),
                 "coupled_lines": coupled_line_leg(), "fd_lines": fd_line_leg(), "nonlinear": nonlinear_leg(),
-                "controls": control_leg()}
+                "controls": control_leg(), "sizes": scale_legs()}
                if args.leg == "all" else {}),
         }
         print(json.dumps(line), flush=True)
@@ -662,7 +777,7 @@ def main():
     ap.add_argument("--time-steps", type=int, default=N_STEPS)
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines",
-                                      "fd_lines", "nonlinear", "controls"],
+                                      "fd_lines", "nonlinear", "controls", "sizes"],
                     default="all",
                     help="all: the JSON line with every leg; single: the single-network leg only; "
                          "n1 / shared_g / adjoint: that leg alone (profiling)")
@@ -676,7 +791,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "fd_lines", "nonlinear",
-                    "controls"):
+                    "controls", "sizes"):
         return run_leg(args)
     return run_ours(args)
 
@@ -697,6 +812,8 @@ def run_leg(args):
         out = fd_line_leg(args.leg_steps, reps=1)
     elif args.leg == "nonlinear":
         out = nonlinear_leg(args.leg_steps, reps=1)
+    elif args.leg == "sizes":
+        out = scale_legs(args.leg_steps, reps=1)
     else:
         shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
         out = scenario_legs((args.leg,), args.leg_steps, shape, args.leg_warm)

@@ -2071,6 +2071,12 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "n_control_injections") *value = (int64_t)c->cinj.size();
   else if (k == "max_control_layers") *value = c->max_clayers;
   else if (k == "smem_bytes") *value = (int64_t)forward_smem_bytes(c->lim);
+  else if (k == "ctas_per_sm") {   // co-resident persistent CTAs per SM (occupancy of the single-network kernel)
+    FwdLimits fl = c->lim;
+    fl.n = std::max(fl.n, 1);
+    fl.nc = std::max(fl.nc, 1);
+    *value = forward_blocks_per_sm(fl);
+  }
   else return EMT_EINVAL;
   return EMT_OK;
 }

@@ -565,17 +565,20 @@ def _sizes_fixed_count(rng, total, count, lo, hi):
 
 def large_scale(seed: int = 1002, n_buses: int = 1000, n_lines: int = 700, n_sources: int = 50,
                 dt: float = 20e-6, n_steps: int = 50000, target_branches: int = 6000,
-                strict_500: bool = False) -> Network:
+                strict_500: bool = False, n_sub: Optional[int] = None) -> Network:
     """Large-scale three-phase network: 1,000 buses (3,000 nodes), ~6,000
     branches, 700 three-phase Bergeron lines, 50 three-phase sources.
 
     Subsystem sizes are 3*U{2..20} nodes drawn until the 1,000 buses are used
     (the subsystem count falls out, about a hundred).  ``strict_500`` instead
-    makes 500 subsystems of 2 buses (6 nodes) each.
+    makes 500 subsystems of 2 buses (6 nodes) each; ``n_sub`` makes exactly
+    that many subsystems of 2..20 buses.
     """
     rng = np.random.default_rng(seed)
     if strict_500:
         bus_counts = [2] * (n_buses // 2)
+    elif n_sub is not None:
+        bus_counts = _sizes_fixed_count(rng, n_buses, n_sub, 2, 20)
     else:
         bus_counts = _sizes_uniform_to_total(rng, n_buses, 2, 20)
     tree = n_buses - len(bus_counts)
@@ -585,6 +588,21 @@ def large_scale(seed: int = 1002, n_buses: int = 1000, n_lines: int = 700, n_sou
     net = multi_subsystem(sub_seed, bus_counts, n_lines, n_sources, dt, n_steps=n_steps,
                           n_series_extra=extra)
     net.meta.update({"config": "large_scale_strict500" if strict_500 else "large_scale", "seed": seed})
+    return net
+
+
+def paper_scale(n_sub: int = 440, seed: int = 1011, dt: float = 20e-6, n_steps: int = 20000) -> Network:
+    """The large-scale family grown towards the size of the paper's largest
+    case (16,653 nodes): ``n_sub`` subsystems of 2..20 three-phase buses
+    (11 on average), and lines, sources and branches scaled from the
+    1,000-bus network by the bus count (440 subsystems: 14,520 nodes).  One
+    persistent launch needs every subsystem's CTA co-resident, so the count
+    that fits depends on the shared memory the largest subsystem needs."""
+    n_buses = 11 * n_sub
+    f = n_buses / 1000.0
+    net = large_scale(seed=seed, n_buses=n_buses, n_lines=int(round(700 * f)), n_sources=int(round(50 * f)),
+                      dt=dt, n_steps=n_steps, target_branches=int(round(6000 * f)), n_sub=n_sub)
+    net.meta.update({"config": "paper_scale", "seed": seed})
     return net
 
 
