@@ -182,3 +182,28 @@ def test_singular_network_is_reported():
         emt.emt_prefactor(ctx)
     assert ei.value.status == emt.EMT_ESINGULAR
     emt.emt_destroy(ctx)
+
+
+def test_largest_coresident_network_and_the_limit():
+    """A network of 360 subsystems (11,880 nodes) runs in one persistent
+    launch with parity; one of 440 such subsystems needs more CTAs than the
+    device holds at once and is refused before any launch (ERESOURCE), the
+    context staying usable for reads."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    big = g.paper_scale(440, n_steps=10)
+    ctx = emt.emt_build_network(big)
+    try:
+        emt.emt_prefactor(ctx)
+        per_sm = emt.emt_get_info(ctx, "ctas_per_sm")
+        if 440 <= per_sm * n_sm:
+            pytest.skip("this device holds 440 CTAs at once")
+        with pytest.raises(emt.EmtError, match="co-resident"):
+            emt.emt_step_n(ctx, 10)
+        assert emt.emt_get_info(ctx, "step") == 0
+    finally:
+        emt.emt_destroy(ctx)
+    net = g.paper_scale(360, n_steps=600)
+    N = 600
+    got = gpu_run(net, N)
+    assert rel_err(got, oracle.simulate(net, N)) <= TOL
