@@ -33,9 +33,8 @@ two further legs the metric names, reported as extra keys of the line:
       method, against the plain one;
   "controls": the same with 180 converter loads (4,320 layered control
       blocks driving controlled current injections), against the plain one;
-  "sizes": the same family as 500 subsystems of 6 nodes, and as the most
-      subsystems of 6..60 nodes that stay co-resident (up to 440, 14,520
-      nodes).
+  "sizes": the same family as 500 subsystems of 6 nodes, and as 500
+      subsystems of 6..60 nodes (16,500 nodes, packed several to a CTA).
 
 N > 1 runs N independent replicas (the single-network path does not shard:
 its subsystems exchange line values every few steps), launched by
@@ -167,7 +166,7 @@ def algorithmic_flops_per_step(net, sim) -> float:
     per L/C branch, one per source branch and line end), 3 per L/C branch
     history update, 2 per line-end output, 1 per source-branch injection."""
     from paper_1903_01081_b300 import emt
-    sum_n2 = emt.emt_get_info(sim.ctx, "sum_n2")
+    sum_n2 = emt.emt_get_info(sim.ctx, "sum_n2_components")   # the subsystems' own blocks, not a packed CTA's zeros
     kinds = np.asarray(net.br_kind)
     n_lc = int(np.sum(kinds != 0))
     n_sb = int(np.sum((np.asarray(net.br_k) <= -2) | (np.asarray(net.br_m) <= -2)))
@@ -566,10 +565,12 @@ def size_leg(net, workload, steps, reps=3, n_check=1000, cpu_steps=1000):
     t = float(np.median(ms)) / 1e3
     flops = algorithmic_flops_per_step(net, sim)
     n_max = sim.info("max_subsystem_nodes")
-    out = {"workload": workload, "nodes": int(net.n_nodes), "subsystems": sim.info("n_subsystems"),
-           "largest_subsystem": n_max, "time_steps": N, "ms": 1e3 * t, "us_per_step": 1e6 * t / N,
+    out = {"workload": workload, "nodes": int(net.n_nodes), "subsystems": sim.info("n_components"),
+           "ctas": sim.info("n_subsystems"), "largest_component": sim.info("max_component_nodes"),
+           "largest_cta_nodes": n_max, "time_steps": N, "ms": 1e3 * t, "us_per_step": 1e6 * t / N,
            "node_steps_per_s": net.n_nodes * N / t,
            "fp64_frac_of_derived_peak": flops * N / t / 1e9 / FP64_PEAK_GFLOPS,
+           # the largest CTA's dense solve (a packed CTA's zero blocks included: its SM runs them)
            "critical_path_sm_frac": (2.0 * n_max * n_max) / (t / N) / (FP64_PEAK_GFLOPS / 148 * 1e9),
            "smem_bytes_per_cta": sim.info("smem_bytes")}
     n_chk = min(n_check, N)
@@ -587,20 +588,13 @@ def size_leg(net, workload, steps, reps=3, n_check=1000, cpu_steps=1000):
 
 def scale_legs(steps=None, reps=3):
     """The large-scale family at two other sizes: the strict reading of
-    500 subsystems of 6 nodes (3,000 nodes), and the most subsystems of
-    6..60 nodes (33 on average) that one launch holds co-resident (towards
-    the paper's 16,653-node case)."""
-    import torch
-    from paper_1903_01081_b300 import emt, netgen as g
+    500 subsystems of 6 nodes (3,000 nodes), and 500 subsystems of 6..60
+    nodes (33 on average, 16,500 nodes, near the paper's 16,653-node case),
+    more than one launch holds co-resident, so packed several to a CTA."""
+    from paper_1903_01081_b300 import netgen as g
     N = steps or 20000
-    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-    for n_sub in (440, 400, 360, 320, 296, 280):   # the largest that stays co-resident
-        net = g.paper_scale(n_sub, n_steps=N)
-        ctx = emt.emt_build_network(net)
-        per_sm = emt.emt_get_info(ctx, "ctas_per_sm")
-        emt.emt_destroy(ctx)
-        if n_sub <= per_sm * n_sm:
-            break
+    n_sub = 500
+    net = g.paper_scale(n_sub, n_steps=N)
     return {"strict_500x6": size_leg(g.large_scale(strict_500=True), "strict reading: 500 subsystems of 2 "
                                      "three-phase buses (3,000 nodes), 700 three-phase lines, 50 sources; dt 20 us",
                                      N, reps),

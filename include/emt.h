@@ -358,7 +358,12 @@ emt_status emt_sync(emt_ctx* ctx, int32_t* dev_err_info);
  * for failure-path tests).  EINVAL for an unknown key. */
 emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
 
-/* Read-only facts: "n_subsystems", "n_ctas", "step", "max_subsystem_nodes",
+/* Read-only facts: "n_subsystems", "n_ctas" (the CTAs of the persistent
+ * kernel: one per subsystem, or several subsystems to a CTA when a single
+ * network has more subsystems than the device holds CTAs at once),
+ * "n_components" (the subsystems proper: components over branches and
+ * switches), "sum_n2_components", "max_component_nodes", "step",
+ * "max_subsystem_nodes" (nodes of the largest CTA),
  * "n_scenarios", "n_epochs_total", "sum_n2" (sum over subsystems of n_s^2),
  * "threads_per_cta", "kernel_launches", "n_nodes", "n_branches", "n_sources", "n_line_ends",
  * "smem_bytes" (dynamic shared memory per CTA of the persistent kernel),

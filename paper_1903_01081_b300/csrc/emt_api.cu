@@ -73,6 +73,8 @@ struct emt_ctx {
   std::vector<int32_t> cb_sub_of;                      // caller's block index -> subsystem
   int max_clayers = 0;
   int64_t ring_len = 0, ginv_len = 0, n_lc_total = 0;
+  int64_t n_components = 0;   // electrical subsystems (components); n_sub counts CTAs, several components each when packed
+  int64_t comp_sum_n2 = 0, comp_max_n = 0;   // over the components
   FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0};
 
   // device arrays
@@ -727,7 +729,79 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
 
 // ------------------------------------------------------------------ build
 
+// Components packed into at most `target` groups (one CTA each) by
+// first-fit decreasing under a node cap: the largest component's size at
+// first, raised until the groups fit.  A component with runtime switches
+// or a nonlinear resistor keeps a group of its own (its switch states and
+// compensation are per CTA).  A group's G is block-diagonal, so its inverse
+// is the blocks' inverses: the same solve with zero blocks.
+std::vector<std::vector<int>> pack_components(const std::vector<std::vector<int>>& comps,
+                                              const std::vector<char>& alone, int target) {
+  const int n_comp = (int)comps.size();
+  std::vector<int> order(n_comp);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return comps[a].size() > comps[b].size(); });
+  size_t cap = comps[order[0]].size();
+  for (;;) {
+    std::vector<std::vector<int>> groups;
+    std::vector<size_t> fill;
+    for (int x : order) {
+      int g = -1;
+      if (!alone[x])
+        for (size_t j = 0; j < groups.size() && g < 0; ++j)
+          if (fill[j] + comps[x].size() <= cap) g = (int)j;
+      if (g < 0) {
+        groups.emplace_back();
+        fill.push_back(alone[x] ? cap + 1 : 0);   // a group of its own stays closed
+        g = (int)groups.size() - 1;
+      }
+      groups[g].insert(groups[g].end(), comps[x].begin(), comps[x].end());
+      if (!alone[x]) fill[g] += comps[x].size();
+    }
+    if ((int)groups.size() <= target || cap >= (size_t)kMaxSubsystemNodes) return groups;
+    cap = std::min(cap + 6, (size_t)kMaxSubsystemNodes);
+  }
+}
+
+static emt_status build_network(const emt_network_desc* d, const emt_scenario_desc* scen, emt_ctx** out,
+                                 int pack_to);
+
+// Co-resident CTAs of the single-network kernel for this context's limits.
+static int64_t forward_capacity(const emt_ctx* c) {
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  FwdLimits fl = c->lim;
+  fl.n = std::max(fl.n, 1);
+  fl.nc = std::max(fl.nc, 1);
+  return (int64_t)n_sm * forward_blocks_per_sm(fl);
+}
+
+// A single network whose subsystems would not all be co-resident is built
+// again with its subsystems packed several to a CTA (fewer CTAs, each with
+// a block-diagonal solve), with a smaller target while the packed limits
+// still do not fit.  Scenario sets are not packed.
 extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_scenario_desc* scen, emt_ctx** out) {
+  emt_status st = build_network(d, scen, out, 0);
+  if (st != EMT_OK || scen) return st;
+  int64_t cap = forward_capacity(*out);
+  if (cap <= 0 || (*out)->n_sub <= cap) return st;
+  int64_t target = cap, prev = (*out)->n_sub;
+  for (int attempt = 0; attempt < 6 && target > 0; ++attempt) {
+    emt_destroy(*out);
+    *out = nullptr;
+    st = build_network(d, scen, out, (int)target);
+    if (st != EMT_OK) return st;
+    const int64_t cap2 = forward_capacity(*out);
+    if ((*out)->n_sub <= cap2 || (*out)->n_sub >= prev) return st;   // fits, or packing gains nothing more
+    prev = (*out)->n_sub;
+    target = std::min(cap2, target - std::max<int64_t>(1, target / 10));
+  }
+  return st;   // still too many CTAs: emt_step_n reports EMT_ERESOURCE
+}
+
+static emt_status build_network(const emt_network_desc* d, const emt_scenario_desc* scen, emt_ctx** out,
+                                 int pack_to) {
   if (!out) {
     g_build_error = "out is NULL";
     return EMT_EINVAL;
@@ -790,6 +864,22 @@ extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_sce
     }
     c->sub_of_node[i] = label[r];
     nodes_of[label[r]].push_back(i);
+  }
+  c->n_components = (int64_t)nodes_of.size();
+  for (const auto& v : nodes_of) {
+    c->comp_sum_n2 += (int64_t)v.size() * (int64_t)v.size();
+    c->comp_max_n = std::max<int64_t>(c->comp_max_n, (int64_t)v.size());
+  }
+  if (pack_to > 0 && (int)nodes_of.size() > pack_to) {
+    std::vector<char> alone(nodes_of.size(), 0);
+    auto mark = [&](int32_t a) {
+      if (a >= 0) alone[c->sub_of_node[a]] = 1;
+    };
+    for (int64_t w = 0; w < d->n_rswitches; ++w) mark(d->rs_k[w] >= 0 ? d->rs_k[w] : d->rs_m[w]);
+    for (int64_t x = 0; x < d->n_nonlin; ++x) mark(d->nl_k[x] >= 0 ? d->nl_k[x] : d->nl_m[x]);
+    nodes_of = pack_components(nodes_of, alone, pack_to);
+    for (size_t g = 0; g < nodes_of.size(); ++g)
+      for (int v : nodes_of[g]) c->sub_of_node[v] = (int)g;
   }
   c->n_sub = (int)nodes_of.size();
   const int S = c->n_sub;
@@ -2052,6 +2142,9 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "graph_launches") *value = c->graph.launches;
   else if (k == "autotuned") *value = c->tuned ? 1 : 0;
   else if (k == "n_epochs_total") *value = (int64_t)c->epochs.size();
+  else if (k == "n_components") *value = c->n_components;
+  else if (k == "sum_n2_components") *value = c->comp_sum_n2;
+  else if (k == "max_component_nodes") *value = c->comp_max_n;
   else if (k == "sum_n2") {
     int64_t s2 = 0;
     for (const SubDev& s : c->subs) s2 += (int64_t)s.n * s.n;

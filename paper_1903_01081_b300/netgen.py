@@ -591,13 +591,11 @@ def large_scale(seed: int = 1002, n_buses: int = 1000, n_lines: int = 700, n_sou
     return net
 
 
-def paper_scale(n_sub: int = 440, seed: int = 1011, dt: float = 20e-6, n_steps: int = 20000) -> Network:
+def paper_scale(n_sub: int = 500, seed: int = 1011, dt: float = 20e-6, n_steps: int = 20000) -> Network:
     """The large-scale family grown towards the size of the paper's largest
     case (16,653 nodes): ``n_sub`` subsystems of 2..20 three-phase buses
     (11 on average), and lines, sources and branches scaled from the
-    1,000-bus network by the bus count (440 subsystems: 14,520 nodes).  One
-    persistent launch needs every subsystem's CTA co-resident, so the count
-    that fits depends on the shared memory the largest subsystem needs."""
+    1,000-bus network by the bus count (500 subsystems: 16,500 nodes)."""
     n_buses = 11 * n_sub
     f = n_buses / 1000.0
     net = large_scale(seed=seed, n_buses=n_buses, n_lines=int(round(700 * f)), n_sources=int(round(50 * f)),

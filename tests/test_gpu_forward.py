@@ -184,26 +184,36 @@ def test_singular_network_is_reported():
     emt.emt_destroy(ctx)
 
 
-def test_largest_coresident_network_and_the_limit():
-    """A network of 360 subsystems (11,880 nodes) runs in one persistent
-    launch with parity; one of 440 such subsystems needs more CTAs than the
-    device holds at once and is refused before any launch (ERESOURCE), the
-    context staying usable for reads."""
+def test_packed_network_beyond_coresidency():
+    """A network of 500 subsystems (16,500 nodes) has more subsystems than
+    CTAs the device holds at once: the build packs them several to a CTA
+    (block-diagonal solves) and the run matches the oracle, which solves
+    each subsystem on its own.  With a surge arrester in every subsystem
+    (each keeps a CTA of its own) nothing can be packed, and the step is
+    refused before any launch (ERESOURCE), the context staying readable."""
     import torch
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    big = g.paper_scale(440, n_steps=10)
-    ctx = emt.emt_build_network(big)
+    N = 400
+    net = g.paper_scale(500, n_steps=N)
+    sim = emt.Simulator(net, n_steps=N)
+    n_cta, n_comp = sim.info("n_subsystems"), sim.info("n_components")
+    assert n_comp == 500
+    assert n_cta < 500 and n_cta <= sim.info("ctas_per_sm") * n_sm
+    sim.run(N)
+    sim.sync()
+    got = sim.waveforms()[:, 0, :]
+    sim.close()
+    assert rel_err(got, oracle.simulate(net, N)) <= TOL
+
+    locked = g.with_arresters(g.paper_scale(500, n_steps=10), n_arresters=500)
+    ctx = emt.emt_build_network(locked)
     try:
+        assert emt.emt_get_info(ctx, "n_subsystems") == 500
+        if 500 <= emt.emt_get_info(ctx, "ctas_per_sm") * n_sm:
+            pytest.skip("this device holds 500 CTAs at once")
         emt.emt_prefactor(ctx)
-        per_sm = emt.emt_get_info(ctx, "ctas_per_sm")
-        if 440 <= per_sm * n_sm:
-            pytest.skip("this device holds 440 CTAs at once")
         with pytest.raises(emt.EmtError, match="co-resident"):
             emt.emt_step_n(ctx, 10)
         assert emt.emt_get_info(ctx, "step") == 0
     finally:
         emt.emt_destroy(ctx)
-    net = g.paper_scale(360, n_steps=600)
-    N = 600
-    got = gpu_run(net, N)
-    assert rel_err(got, oracle.simulate(net, N)) <= TOL
