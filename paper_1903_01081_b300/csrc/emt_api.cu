@@ -7,6 +7,7 @@
 #include <cstring>
 #include <map>
 #include <numeric>
+#include <queue>
 #include <set>
 #include <array>
 #include <string>
@@ -729,42 +730,63 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
 
 // ------------------------------------------------------------------ build
 
-// Components packed into at most `target` groups (one CTA each) by
-// first-fit decreasing under a node cap: the largest component's size at
-// first, raised until the groups fit.  A component with runtime switches
-// or a nonlinear resistor keeps a group of its own (its switch states and
-// compensation are per CTA).  A group's G is block-diagonal, so its inverse
-// is the blocks' inverses: the same solve with zero blocks.
+// Components packed into at most `target` groups (one CTA each).  The
+// smallest group merges with the smallest partner that keeps the merged
+// group within `relax` times the largest component's nodes, line ends and
+// L/C branches, while there are too many groups: the large components keep
+// CTAs of their own, a merged group stays small (its solve runs the zero
+// blocks too) and the per-CTA shared memory, sized by those maxima, hardly
+// grows.  A component with runtime switches or a nonlinear resistor keeps a
+// group of its own (switch states and compensation are per CTA).  A group's
+// G is block-diagonal, so its inverse is the blocks' inverses.
 std::vector<std::vector<int>> pack_components(const std::vector<std::vector<int>>& comps,
-                                              const std::vector<char>& alone, int target) {
-  const int n_comp = (int)comps.size();
-  std::vector<int> order(n_comp);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return comps[a].size() > comps[b].size(); });
-  size_t cap = comps[order[0]].size();
-  for (;;) {
-    std::vector<std::vector<int>> groups;
-    std::vector<size_t> fill;
-    for (int x : order) {
-      int g = -1;
-      if (!alone[x])
-        for (size_t j = 0; j < groups.size() && g < 0; ++j)
-          if (fill[j] + comps[x].size() <= cap) g = (int)j;
-      if (g < 0) {
-        groups.emplace_back();
-        fill.push_back(alone[x] ? cap + 1 : 0);   // a group of its own stays closed
-        g = (int)groups.size() - 1;
-      }
-      groups[g].insert(groups[g].end(), comps[x].begin(), comps[x].end());
-      if (!alone[x]) fill[g] += comps[x].size();
-    }
-    if ((int)groups.size() <= target || cap >= (size_t)kMaxSubsystemNodes) return groups;
-    cap = std::min(cap + 6, (size_t)kMaxSubsystemNodes);
+                                              const std::vector<char>& alone, const std::vector<int>& w_le,
+                                              const std::vector<int>& w_lc, int target, double relax) {
+  const size_t K = comps.size();
+  size_t max_n = 0;
+  int max_le = 0, max_lc = 0;
+  for (size_t x = 0; x < K; ++x) {
+    max_n = std::max(max_n, comps[x].size());
+    max_le = std::max(max_le, w_le[x]);
+    max_lc = std::max(max_lc, w_lc[x]);
   }
+  const double cap_n = relax * (double)max_n, cap_le = relax * max_le, cap_lc = relax * max_lc;
+  std::vector<std::vector<int>> groups(comps.begin(), comps.end());
+  std::vector<int> le(w_le), lc(w_lc);
+  std::vector<int> open;   // mergeable groups
+  for (size_t x = 0; x < K; ++x)
+    if (!alone[x]) open.push_back((int)x);
+  int n_groups = (int)K;
+  while (n_groups > target && open.size() >= 2) {
+    std::sort(open.begin(), open.end(), [&](int a, int b) { return groups[a].size() < groups[b].size(); });
+    const int a = open[0];
+    int pick = -1;
+    for (size_t j = 1; j < open.size() && pick < 0; ++j) {
+      const int b = open[j];
+      if ((double)(groups[a].size() + groups[b].size()) <= cap_n && le[a] + le[b] <= cap_le &&
+          lc[a] + lc[b] <= cap_lc)
+        pick = (int)j;
+    }
+    if (pick < 0) {   // the smallest fits with nothing: it stays as it is
+      open.erase(open.begin());
+      continue;
+    }
+    const int b = open[pick];
+    groups[a].insert(groups[a].end(), groups[b].begin(), groups[b].end());
+    groups[b].clear();
+    le[a] += le[b];
+    lc[a] += lc[b];
+    open.erase(open.begin() + pick);
+    --n_groups;
+  }
+  std::vector<std::vector<int>> out;
+  for (auto& g : groups)
+    if (!g.empty()) out.push_back(std::move(g));
+  return out;
 }
 
 static emt_status build_network(const emt_network_desc* d, const emt_scenario_desc* scen, emt_ctx** out,
-                                 int pack_to);
+                                 int pack_to, double relax);
 
 // Co-resident CTAs of the single-network kernel for this context's limits.
 static int64_t forward_capacity(const emt_ctx* c) {
@@ -779,29 +801,25 @@ static int64_t forward_capacity(const emt_ctx* c) {
 
 // A single network whose subsystems would not all be co-resident is built
 // again with its subsystems packed several to a CTA (fewer CTAs, each with
-// a block-diagonal solve), with a smaller target while the packed limits
-// still do not fit.  Scenario sets are not packed.
+// a block-diagonal solve), the merged groups allowed to grow past the
+// largest component step by step until the packed network fits.  Scenario
+// sets are not packed.
 extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_scenario_desc* scen, emt_ctx** out) {
-  emt_status st = build_network(d, scen, out, 0);
+  emt_status st = build_network(d, scen, out, 0, 1.0);
   if (st != EMT_OK || scen) return st;
-  int64_t cap = forward_capacity(*out);
+  const int64_t cap = forward_capacity(*out);
   if (cap <= 0 || (*out)->n_sub <= cap) return st;
-  int64_t target = cap, prev = (*out)->n_sub;
-  for (int attempt = 0; attempt < 6 && target > 0; ++attempt) {
+  for (double relax : {1.0, 1.2, 1.5, 2.0}) {
     emt_destroy(*out);
     *out = nullptr;
-    st = build_network(d, scen, out, (int)target);
-    if (st != EMT_OK) return st;
-    const int64_t cap2 = forward_capacity(*out);
-    if ((*out)->n_sub <= cap2 || (*out)->n_sub >= prev) return st;   // fits, or packing gains nothing more
-    prev = (*out)->n_sub;
-    target = std::min(cap2, target - std::max<int64_t>(1, target / 10));
+    st = build_network(d, scen, out, (int)cap, relax);
+    if (st != EMT_OK || (*out)->n_sub <= forward_capacity(*out)) return st;
   }
   return st;   // still too many CTAs: emt_step_n reports EMT_ERESOURCE
 }
 
 static emt_status build_network(const emt_network_desc* d, const emt_scenario_desc* scen, emt_ctx** out,
-                                 int pack_to) {
+                                 int pack_to, double relax) {
   if (!out) {
     g_build_error = "out is NULL";
     return EMT_EINVAL;
@@ -877,7 +895,22 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
     };
     for (int64_t w = 0; w < d->n_rswitches; ++w) mark(d->rs_k[w] >= 0 ? d->rs_k[w] : d->rs_m[w]);
     for (int64_t x = 0; x < d->n_nonlin; ++x) mark(d->nl_k[x] >= 0 ? d->nl_k[x] : d->nl_m[x]);
-    nodes_of = pack_components(nodes_of, alone, pack_to);
+    std::vector<int> w_le(nodes_of.size(), 0), w_lc(nodes_of.size(), 0);
+    for (int64_t l = 0; l < d->n_lines; ++l) {
+      ++w_le[c->sub_of_node[d->ln_k[l]]];
+      ++w_le[c->sub_of_node[d->ln_m[l]]];
+    }
+    for (int64_t l = 0; l < 3 * d->n_clines; ++l) {   // a mode per phase at each end
+      ++w_le[c->sub_of_node[d->cl_k[l]]];
+      ++w_le[c->sub_of_node[d->cl_m[l]]];
+    }
+    for (int64_t l = 0; l < d->n_fdlines; ++l) {
+      ++w_le[c->sub_of_node[d->fl_k[l]]];
+      ++w_le[c->sub_of_node[d->fl_m[l]]];
+    }
+    for (int64_t b = 0; b < d->n_branches; ++b)
+      if (d->br_kind[b] != 0) ++w_lc[c->sub_of_node[d->br_k[b] >= 0 ? d->br_k[b] : d->br_m[b]]];
+    nodes_of = pack_components(nodes_of, alone, w_le, w_lc, pack_to, relax);
     for (size_t g = 0; g < nodes_of.size(); ++g)
       for (int v : nodes_of[g]) c->sub_of_node[v] = (int)g;
   }
