@@ -286,9 +286,26 @@ emt_status emt_step_n(emt_ctx* ctx, int64_t n_steps, void* cuda_stream);
  * rows for steps step0, step0+decim, ... (n_rows of them; step0 a positive
  * multiple of decim); scenarios scen0 .. scen0+n_scen-1.
  * out: [n_rows][n_scen][n_ch] doubles, caller-owned, device memory if
- * out_on_device != 0 else host memory.  Synchronous. */
+ * out_on_device != 0 else host memory.  Every recorded channel in recording
+ * order, over all scenarios (or one row), is one plain copy of the record
+ * buffer; other requests gather on the device first.  Synchronous. */
 emt_status emt_read_waveforms(emt_ctx* ctx, const int32_t* channels, int64_t n_ch, int64_t step0, int64_t n_rows,
                               int64_t scen0, int64_t n_scen, double* out, int32_t out_on_device);
+
+/* emt_read_waveforms, stream-ordered: enqueues the gather (and, for a host
+ * `out`, the device-to-host copy) on `cuda_stream` (NULL: the legacy
+ * default stream) and returns without waiting, so that reading the rows of
+ * one chunk of steps overlaps the run of the next.  The rows must be
+ * recorded by steps enqueued before it on `cuda_stream`, or ordered before
+ * it by the caller (an event the stream waits on); emt_step_n counts steps
+ * as enqueued, so the bounds checks are those of emt_read_waveforms.  A
+ * host `out` must be page-locked for the copy to run asynchronously, and
+ * stays in use until the stream reaches this point; the temporary device
+ * buffers are stream-ordered allocations.  Device errors of the steps
+ * (wait timeouts) surface on emt_sync. */
+emt_status emt_read_waveforms_async(emt_ctx* ctx, const int32_t* channels, int64_t n_ch, int64_t step0,
+                                    int64_t n_rows, int64_t scen0, int64_t n_scen, double* out,
+                                    int32_t out_on_device, void* cuda_stream);
 
 /* Control block outputs of the last completed step (all 0 at step 0):
  * y[b] for b = 0 .. n_cblocks-1 in the caller's block order; n must equal

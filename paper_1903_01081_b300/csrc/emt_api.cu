@@ -1974,6 +1974,19 @@ extern "C" emt_status emt_sync(emt_ctx* c, int32_t* info) {
   return EMT_OK;
 }
 
+// The recorded block itself when the request is every recorded channel in
+// recording order over rows whose scenarios lie contiguously in the record
+// buffer ([row][scenario][column]); else NULL (a gather is needed).
+static const double* contiguous_rows(const emt_ctx* c, const std::vector<int32_t>& col, int64_t row0, int64_t n_rows,
+                                     int64_t scen0, int64_t n_scen) {
+  const int64_t n_rec = (int64_t)c->rec_channels.size();
+  if ((int64_t)col.size() != n_rec) return nullptr;
+  for (int64_t i = 0; i < n_rec; ++i)
+    if (col[i] != i) return nullptr;
+  if (!(scen0 == 0 && n_scen == c->S) && n_rows != 1) return nullptr;
+  return c->d_rec + (row0 * c->S + scen0) * n_rec;
+}
+
 extern "C" emt_status emt_read_waveforms(emt_ctx* c, const int32_t* channels, int64_t n_ch, int64_t step0,
                                          int64_t n_rows, int64_t scen0, int64_t n_scen, double* out,
                                          int32_t out_on_device) {
@@ -1997,10 +2010,15 @@ extern "C" emt_status emt_read_waveforms(emt_ctx* c, const int32_t* channels, in
   }
   const emt_status st = emt_sync(c, nullptr);
   if (st != EMT_OK) return st;
+  const size_t bytes = (size_t)n_rows * n_scen * n_ch * sizeof(double);
+  if (const double* src = contiguous_rows(c, col, row0, n_rows, scen0, n_scen)) {   // one plain copy
+    const cudaError_t e = cudaMemcpy(out, src, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return c->cuda_fail(e, "emt_read_waveforms");
+    return EMT_OK;
+  }
   int32_t* d_col = nullptr;
   double* d_out = out;
   cudaError_t e = c->upload(&d_col, col);
-  const size_t bytes = (size_t)n_rows * n_scen * n_ch * sizeof(double);
   if (e == cudaSuccess && !out_on_device) {
     void* p = nullptr;
     e = cudaMalloc(&p, bytes);
@@ -2015,6 +2033,55 @@ extern "C" emt_status emt_read_waveforms(emt_ctx* c, const int32_t* channels, in
   c->release(d_col);
   if (!out_on_device) c->release(d_out);
   if (e != cudaSuccess) return c->cuda_fail(e, "emt_read_waveforms");
+  return EMT_OK;
+}
+
+extern "C" emt_status emt_read_waveforms_async(emt_ctx* c, const int32_t* channels, int64_t n_ch, int64_t step0,
+                                               int64_t n_rows, int64_t scen0, int64_t n_scen, double* out,
+                                               int32_t out_on_device, void* cuda_stream) {
+  if (!c) return EMT_EINVAL;
+  if (n_ch < 0 || n_rows < 0 || n_scen < 0) return c->fail(EMT_EINVAL, "negative count");
+  if (n_ch == 0 || n_rows == 0 || n_scen == 0) return EMT_OK;
+  if (!out || !channels) return c->fail(EMT_EINVAL, "NULL buffer");
+  if (c->rec_channels.empty()) return c->fail(EMT_ESTATE, "nothing is being recorded");
+  if (scen0 < 0 || scen0 + n_scen > c->S) return c->fail(EMT_EINVAL, "scenario range out of bounds");
+  if (step0 < c->rec_decim || step0 % c->rec_decim != 0)
+    return c->fail(EMT_EINVAL, "step0 must be a positive multiple of the recording decimation");
+  const int64_t row0 = step0 / c->rec_decim - 1;
+  if (row0 + n_rows > c->rec_rows || (row0 + n_rows) * c->rec_decim > c->step)
+    return c->fail(EMT_EINVAL, "requested steps have not been recorded");
+  std::vector<int32_t> col(n_ch);
+  for (int64_t i = 0; i < n_ch; ++i) {
+    const int32_t x = channels[i];
+    if (x < 0 || x >= c->n_nodes || c->rec_col_of[x] < 0)
+      return c->fail(EMT_EINVAL, "channel " + std::to_string(x) + " is not recorded");
+    col[i] = c->rec_col_of[x];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const size_t bytes = (size_t)n_rows * n_scen * n_ch * sizeof(double);
+  if (const double* src = contiguous_rows(c, col, row0, n_rows, scen0, n_scen)) {   // the copy engine alone
+    const cudaError_t e =
+        cudaMemcpyAsync(out, src, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return c->cuda_fail(e, "emt_read_waveforms_async");
+    return EMT_OK;
+  }
+  void* d_col = nullptr;
+  void* d_tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(&d_col, col.size() * sizeof(int32_t), st);
+  // from pageable memory the copy is staged before the call returns, so `col` may go
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_col, col.data(), col.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  double* d_out = out;
+  if (e == cudaSuccess && !out_on_device) {
+    e = cudaMallocAsync(&d_tmp, bytes, st);
+    d_out = static_cast<double*>(d_tmp);
+  }
+  if (e == cudaSuccess)
+    e = launch_gather(c->d_rec, (int32_t)c->rec_channels.size(), c->S, static_cast<const int32_t*>(d_col), n_ch,
+                      row0, n_rows, scen0, n_scen, d_out, st);
+  if (e == cudaSuccess && !out_on_device) e = cudaMemcpyAsync(out, d_out, bytes, cudaMemcpyDeviceToHost, st);
+  if (d_tmp) cudaFreeAsync(d_tmp, st);
+  if (d_col) cudaFreeAsync(d_col, st);
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_read_waveforms_async");
   return EMT_OK;
 }
 

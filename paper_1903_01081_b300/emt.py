@@ -22,7 +22,8 @@ _STATUS = {0: "EMT_OK", 1: "EMT_EINVAL", 2: "EMT_ESINGULAR", 3: "EMT_ENOMEM", 4:
 # every function include/emt.h declares
 EXPORTS = ("emt_build_network", "emt_prefactor", "emt_set_recording", "emt_step_n", "emt_read_waveforms",
            "emt_reset", "emt_sync", "emt_set_option", "emt_get_info", "emt_get_node_order", "emt_last_error",
-           "emt_destroy", "emt_prefactor_noalloc", "emt_adjoint", "emt_autotune", "emt_read_controls")
+           "emt_destroy", "emt_prefactor_noalloc", "emt_adjoint", "emt_autotune", "emt_read_controls",
+           "emt_read_waveforms_async")
 
 
 class EmtError(RuntimeError):
@@ -96,6 +97,7 @@ def load_library(build_if_needed: bool = True):
         "emt_set_recording": [P, P, I64, I32, I64],
         "emt_step_n": [P, I64, P],
         "emt_read_waveforms": [P, P, I64, I64, I64, I64, I64, P, I32],
+        "emt_read_waveforms_async": [P, P, I64, I64, I64, I64, I64, P, I32, P],
         "emt_reset": [P],
         "emt_sync": [P, P],
         "emt_set_option": [P, ctypes.c_char_p, I64],
@@ -287,6 +289,56 @@ def emt_read_waveforms(ctx: Ctx, channels, step0: int, n_rows: int, scen0: int =
     return out
 
 
+def emt_read_waveforms_async(ctx: Ctx, channels, step0: int, n_rows: int, scen0: int, n_scen: int, out, stream=None):
+    """Stream-ordered read of recorded waveforms into ``out`` ([n_rows][n_scen][n_ch]
+    float64: a CUDA tensor, or a pinned host tensor for an asynchronous
+    copy), enqueued on ``stream``; returns at once (include/emt.h)."""
+    lib = load_library()
+    ch = _arr(channels, np.int32)
+    shape = (int(n_rows), int(n_scen), int(ch.size))
+    if not out.is_contiguous() or out.numel() != int(np.prod(shape)) or str(out.dtype) != "torch.float64":
+        raise ValueError("out must be a contiguous float64 tensor of shape " + str(shape))
+    if int(np.prod(shape)) == 0:
+        return out
+    _check(ctx, lib.emt_read_waveforms_async(ctx.handle, ch.ctypes.data, int(ch.size), int(step0), int(n_rows),
+                                             int(scen0), int(n_scen), out.data_ptr(), 1 if out.is_cuda else 0,
+                                             _stream_handle(stream)))
+    return out
+
+
+def step_and_read(ctx: Ctx, channels, decim: int, n_steps: int, out, chunk: int = 5000, stream=None):
+    """Run ``n_steps`` steps and copy their recorded rows (channels
+    ``channels``, every scenario) into ``out``, a pinned host tensor
+    [rows][scenarios][channels] whose row 0 is the first row recorded after
+    the current step.  The steps go to ``stream`` (default: torch's current
+    stream) in chunks; each chunk's rows are read on a second stream, which
+    waits for the chunk, while the next chunk runs (emt_step_n and
+    emt_read_waveforms_async).  Returns ``out`` once both streams are done."""
+    import torch
+    compute = stream if stream is not None else torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
+    decim = int(decim)
+    n_scen = ctx.n_scenarios
+    base = emt_get_info(ctx, "step")
+    row_base = base // decim + 1
+    done = 0
+    while done < n_steps:
+        n = min(int(chunk), n_steps - done)
+        emt_step_n(ctx, n, compute)
+        first, last = (base + done) // decim + 1, (base + done + n) // decim   # rows completed by this chunk
+        if last >= first:
+            ev = torch.cuda.Event()
+            ev.record(compute)
+            copy.wait_event(ev)
+            r0 = first - row_base
+            emt_read_waveforms_async(ctx, channels, first * decim, last - first + 1, 0, n_scen,
+                                     out[r0:r0 + last - first + 1], copy)
+        done += n
+    copy.synchronize()
+    compute.synchronize()
+    return out
+
+
 def emt_read_controls(ctx: Ctx, out=None):
     """Control block outputs of the last completed step, caller's block
     order: a new numpy array, or written into ``out`` (numpy array or CUDA
@@ -419,6 +471,11 @@ class Simulator:
             n_rows = emt_get_info(self.ctx, "step") // self.decim - (step0 // self.decim - 1)
         n_scen = self.ctx.n_scenarios if n_scen is None else n_scen
         return emt_read_waveforms(self.ctx, self.channels, step0, n_rows, scen0, n_scen, out)
+
+    def run_to_host(self, n_steps: int, out, chunk: int = 5000, stream=None):
+        """Run ``n_steps`` steps and copy their recorded rows into ``out``
+        (see step_and_read)."""
+        return step_and_read(self.ctx, self.channels, self.decim, n_steps, out, chunk, stream)
 
     def controls(self, out=None):
         """Control block outputs of the last completed step."""

@@ -217,3 +217,25 @@ def test_packed_network_beyond_coresidency():
         assert emt.emt_get_info(ctx, "step") == 0
     finally:
         emt.emt_destroy(ctx)
+
+
+@pytest.mark.parametrize("decim,chunk", [(1, 700), (3, 1000)])
+def test_pipelined_read_to_pinned_host_is_bitwise(decim, chunk):
+    """Steps in chunks with each chunk's rows copied to pinned host memory on
+    a second stream (emt_read_waveforms_async) give the same rows as one
+    run followed by a synchronous read."""
+    import torch
+    net = g.multi_subsystem(11, [4, 5, 3, 6], n_lines=6, n_sources=2, dt=20e-6)
+    N = 4000
+    a = emt.Simulator(net, n_steps=N, decim=decim)
+    a.run(N)
+    a.sync()
+    want = a.waveforms()
+    a.close()
+    b = emt.Simulator(net, n_steps=N, decim=decim)
+    out = torch.empty((N // decim, 1, net.n_nodes), dtype=torch.float64, pin_memory=True)
+    b.run_to_host(N, out, chunk=chunk)
+    b.sync()
+    b.close()
+    assert np.array_equal(out.numpy(), want)
+    assert rel_err(want[:, 0, :], oracle.simulate(net, N)[decim - 1::decim]) <= TOL
