@@ -207,7 +207,13 @@ typedef struct {
  *   rm_branch_ptr[n_scenarios+1], rm_branch[]: branches removed per scenario
  *   rm_line_ptr[n_scenarios+1], rm_line[]:     lines removed per scenario
  *   sw_ptr[n_scenarios+1], sw_k[], sw_m[], sw_r[], sw_close_step[],
- *     sw_open_step[]: switches added per scenario (same rules as above). */
+ *     sw_open_step[]: switches added per scenario (same rules as above).
+ *   cbo_ptr[n_scenarios+1], cbo_block[], cbo_p0[]: control blocks whose
+ *     parameter p0 a scenario sets (block index, finite value; a block at
+ *     most once per scenario; for a LIMIT the new lower bound must not
+ *     exceed p1), e.g. a set point per scenario.  NULL: none.
+ * Scenario sets take control blocks; they do not take runtime switches,
+ * coupled or frequency-dependent lines or nonlinear resistors. */
 typedef struct {
   int64_t n_scenarios;
   const double* src_amp;
@@ -222,6 +228,9 @@ typedef struct {
   const double* sw_r;
   const int64_t* sw_close_step;
   const int64_t* sw_open_step;
+  const int64_t* cbo_ptr;
+  const int32_t* cbo_block;
+  const double* cbo_p0;
 } emt_scenario_desc;
 
 /* Validate the description, split the network into subsystems (connected
@@ -310,7 +319,7 @@ emt_status emt_read_waveforms_async(emt_ctx* ctx, const int32_t* channels, int64
 /* Control block outputs of the last completed step (all 0 at step 0):
  * y[b] for b = 0 .. n_cblocks-1 in the caller's block order; n must equal
  * n_cblocks.  y is device memory if on_device != 0 else host memory.
- * Synchronous. */
+ * Synchronous.  EINVAL for a context built with a scenario set. */
 emt_status emt_read_controls(emt_ctx* ctx, double* y, int64_t n, int32_t on_device);
 
 /* Pick the launch shape of the multi-scenario kernel by measurement: for

@@ -186,6 +186,13 @@ struct emt_ctx {
   int32_t* d_rm_br = nullptr;
   int32_t* d_rm_ptr_le = nullptr;
   int32_t* d_rm_le = nullptr;
+  // control blocks of the multi-scenario kernel (see BatchParams)
+  std::vector<CtrlDev> b_cb;
+  std::vector<int32_t> b_cinj, b_cb_lay, b_cb_list;
+  std::vector<double> b_cbo;
+  CtrlDev* d_bcb = nullptr;
+  int32_t *d_bcinj = nullptr, *d_bcb_lay = nullptr, *d_bcb_list = nullptr;
+  double *d_bcbo = nullptr, *d_bcy = nullptr, *d_bcs = nullptr;
 
   std::vector<void*> allocations;
 
@@ -396,6 +403,20 @@ int uf_find(std::vector<int>& p, int x) {
 
 bool switch_closed(int64_t on, int64_t off, int64_t n) { return on >= 0 && n >= on && (off < 0 || n < off); }
 
+// A control block's coefficients in device form (see CtrlDev) from its
+// parameters p0, p1 and the step.
+void ctrl_coefficients(CtrlDev& r, double p0, double p1, double dt) {
+  r.p0 = p0;
+  r.p1 = p1;
+  r.p2 = 0.0;
+  if (r.type == 6) r.p0 = p0 * (dt / 2.0);
+  if (r.type == 7) {
+    r.p0 = (2.0 * p1 - dt) / (2.0 * p1 + dt);
+    r.p1 = p0 * dt / (2.0 * p1 + dt);
+  }
+  if (r.type == 8) r.p2 = dt / 2.0;
+}
+
 std::string validate_scenarios(const emt_network_desc* d, const emt_scenario_desc* sc) {
   if (sc->n_scenarios < 1 || sc->n_scenarios > (1 << 24)) return "n_scenarios must be in 1 .. 2^24";
   const int64_t S = sc->n_scenarios;
@@ -430,6 +451,21 @@ std::string validate_scenarios(const emt_network_desc* d, const emt_scenario_des
       if (!finite_pos(sc->sw_r[w])) return "scenario switch " + std::to_string(w) + ": resistance must be > 0";
     }
   }
+  if (sc->cbo_ptr) {
+    m = csr(sc->cbo_ptr, sc->cbo_block, "control-parameter");
+    if (!m.empty()) return m;
+    if (sc->cbo_ptr[S] > 0 && !sc->cbo_p0) return "control-parameter value list is NULL";
+    for (int64_t q = 0; q < S; ++q) {
+      std::set<int32_t> seen;
+      for (int64_t i = sc->cbo_ptr[q]; i < sc->cbo_ptr[q + 1]; ++i) {
+        const int32_t b = sc->cbo_block[i];
+        if (b < 0 || b >= d->n_cblocks) return "control-parameter block out of range";
+        if (!seen.insert(b).second) return "a scenario sets the parameter of a control block twice";
+        if (!std::isfinite(sc->cbo_p0[i])) return "control-parameter value is not finite";
+        if (d->cb_type[b] == 5 && sc->cbo_p0[i] > d->cb_p1[b]) return "a LIMIT's lower bound exceeds its upper bound";
+      }
+    }
+  }
   return "";
 }
 
@@ -450,6 +486,7 @@ bool batch_configure(emt_ctx* c, int S_t, bool upload) {
   if (fixed >= 227 * 1024) return false;
   const size_t budget = 227 * 1024 - fixed - 16;
   std::vector<BatchGroupDev> groups;
+  std::vector<int32_t> lay, list;   // control layers per group (see BatchGroupDev)
   int max_cols = 0, max_nodes = 0;
   int s0 = 0;
   while (s0 < c->n_sub) {
@@ -466,6 +503,20 @@ bool batch_configure(emt_ctx* c, int S_t, bool upload) {
     const SubDev& a = c->subs[s0];
     const SubDev& b = c->subs[s1 - 1];
     BatchGroupDev G{};
+    // control layers: layer l of the group = layer l of each of its subsystems
+    G.lay0 = (int)lay.size();
+    for (int s = s0; s < s1; ++s) G.n_lay = std::max(G.n_lay, c->subs[s].n_clay);
+    for (int l = 0; l < G.n_lay; ++l) {
+      lay.push_back((int32_t)list.size());
+      for (int s = s0; s < s1; ++s) {
+        const SubDev& sd = c->subs[s];
+        if (l >= sd.n_clay) continue;
+        constexpr int kSlotMask = (1 << kLayerTypeShift) - 1;
+        const int j0 = c->clay[sd.clay_off + l] & kSlotMask, j1 = c->clay[sd.clay_off + l + 1] & kSlotMask;
+        for (int j = j0; j < j1; ++j) list.push_back(sd.cb_off + j);
+      }
+    }
+    lay.push_back((int32_t)list.size());
     G.node0 = a.node_off;
     G.node1 = b.node_off + b.n;
     G.col0 = c->b_sub_col_off[s0];
@@ -486,6 +537,15 @@ bool batch_configure(emt_ctx* c, int S_t, bool upload) {
     c->d_grp = nullptr;
   }
   if (c->upload(&c->d_grp, groups) != cudaSuccess) return false;
+  if (!list.empty()) {
+    c->release(c->d_bcb_lay);
+    c->release(c->d_bcb_list);
+    c->d_bcb_lay = nullptr;
+    c->d_bcb_list = nullptr;
+    if (c->upload(&c->d_bcb_lay, lay) != cudaSuccess || c->upload(&c->d_bcb_list, list) != cudaSuccess) return false;
+  }
+  c->b_cb_lay = lay;
+  c->b_cb_list = list;
   c->groups = groups;
   c->max_cols = std::max(max_cols, 1);
   c->max_nodes = std::max(max_nodes, 1);
@@ -673,9 +733,11 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
           const uint32_t raw = (uint32_t)c->ent[4 * (size_t)(sd.il_off + l) + u];
           const int idx = (int)(raw & ~kEntryNeg);
           uint32_t code;
+          const int zero = ie_base + 2 * sd.n_le;   // (no coupled or frequency-dependent ends here)
           if (idx < sd.n_lc) code = (0u << kBentKindShift) | (uint32_t)(sd.lc_off + idx);
           else if (idx < ie_base) code = (1u << kBentKindShift) | (uint32_t)(sd.sb_off + idx - sd.n_lc);
           else if (idx < ie_base + sd.n_le) code = (2u << kBentKindShift) | (uint32_t)(sd.le_off + idx - ie_base);
+          else if (idx > zero && idx <= zero + sd.n_ci) code = (3u << kBentKindShift) | (uint32_t)(sd.ci_off + idx - zero - 1);
           else continue;
           c->b_bent.push_back((int32_t)(code | (raw & kEntryNeg)));
         }
@@ -721,6 +783,51 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
     }
     c->b_ev_ptr.push_back((int64_t)c->b_ev_step.size());
   }
+  // control blocks in global slots: inputs over all blocks (the zero pair
+  // after the last one), MEAS nodes as internal nodes; the block of each
+  // control injection; per-scenario coefficients of the blocks a scenario
+  // sets a parameter of (the base ones in the other scenarios)
+  const int NCB = (int)c->cblocks.size();
+  c->b_cb = c->cblocks;
+  for (int q = 0; q < nsub; ++q) {
+    const SubDev& sd = c->subs[q];
+    auto remap = [&](int32_t i) { return i >= 2 * sd.n_cb ? 2 * NCB : 2 * (sd.cb_off + (i >> 1)) + (i & 1); };
+    for (int j = 0; j < sd.n_cb; ++j) {
+      CtrlDev& r = c->b_cb[sd.cb_off + j];
+      r.i0 = remap(r.i0);
+      r.i1 = remap(r.i1);
+      if (r.type == 1) r.node = sd.node_off + r.node;
+    }
+    for (int x = 0; x < sd.n_ci; ++x) c->b_cinj.push_back(sd.cb_off + c->cinj[sd.ci_off + x]);
+  }
+  if (sc->cbo_ptr && sc->cbo_ptr[S] > 0) {
+    std::map<int32_t, int> row_of;
+    for (int64_t i = 0; i < sc->cbo_ptr[S]; ++i) row_of.emplace(sc->cbo_block[i], (int)row_of.size());
+    c->b_cbo.assign(row_of.size() * (size_t)S * 3, 0.0);
+    auto slot = [&](int32_t b) { return c->subs[c->cb_sub_of[b]].cb_off + c->cb_slot_of[b]; };
+    for (const auto& kv : row_of) {
+      CtrlDev& r = c->b_cb[slot(kv.first)];
+      r.ov = (double)kv.second;
+      for (int64_t q = 0; q < S; ++q) {
+        double* o = &c->b_cbo[((size_t)kv.second * S + q) * 3];
+        o[0] = r.p0;
+        o[1] = r.p1;
+        o[2] = r.p2;
+      }
+    }
+    for (int64_t q = 0; q < S; ++q)
+      for (int64_t i = sc->cbo_ptr[q]; i < sc->cbo_ptr[q + 1]; ++i) {
+        const int32_t b = sc->cbo_block[i];
+        CtrlDev t{};
+        t.type = d->cb_type[b];
+        ctrl_coefficients(t, sc->cbo_p0[i], d->cb_p1[b], d->dt);
+        double* o = &c->b_cbo[((size_t)row_of[b] * S + q) * 3];
+        o[0] = t.p0;
+        o[1] = t.p1;
+        o[2] = t.p2;
+      }
+  }
+
   // default launch shape: about one CTA per SM
   c->S_t = (int)std::min<int64_t>(32, std::max<int64_t>(1, (S + 147) / 148));
   while (c->S_t > 1 && !batch_configure(c, c->S_t, false)) c->S_t = std::max(1, c->S_t / 2);
@@ -1341,14 +1448,8 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
           (i == 0 ? r.i0 : r.i1) = 2 * c->cb_slot_of[input(b, i)] + (input(b, i) >= b ? 1 : 0);
         r.node = r.type == 1 ? local[d->cb_node[b]] : -1;
         const double p0 = d->cb_p0[b], p1 = d->cb_p1[b];
-        r.p0 = p0;
-        r.p1 = p1;
-        if (r.type == 6) r.p0 = p0 * (dt / 2.0);
-        if (r.type == 7) {
-          r.p0 = (2.0 * p1 - dt) / (2.0 * p1 + dt);
-          r.p1 = p0 * dt / (2.0 * p1 + dt);
-        }
-        if (r.type == 8) r.p2 = dt / 2.0;
+        ctrl_coefficients(r, p0, p1, dt);
+        r.ov = -1.0;
         c->cblocks.push_back(r);
       }
       if (sd.n_cb > 0) c->clay.push_back(sd.n_cb);
@@ -1548,7 +1649,6 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   // -------- multi-scenario set
   if (scen && !c->rswitches.empty()) return bail("runtime switches are not supported with a scenario set");
   if (scen && !c->cends.empty()) return bail("coupled lines are not supported with a scenario set");
-  if (scen && (d->n_cblocks > 0 || d->n_cinj > 0)) return bail("control blocks are not supported with a scenario set");
   if (scen && d->n_fdlines > 0) return bail("frequency-dependent lines are not supported with a scenario set");
   if (scen && d->n_nonlin > 0) return bail("nonlinear resistors are not supported with a scenario set");
   if (scen) {
@@ -1632,6 +1732,13 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
       if (e == cudaSuccess) e = c->upload(&c->d_keep_lc, c->keep_lc);
       if (e == cudaSuccess) e = c->upload(&c->d_keep_sb, c->keep_sb);
       if (e == cudaSuccess) e = c->upload(&c->d_keep_le, c->keep_le);
+    }
+    if (!c->b_cb.empty()) {
+      if (e == cudaSuccess) e = c->upload(&c->d_bcb, c->b_cb);
+      if (e == cudaSuccess && !c->b_cinj.empty()) e = c->upload(&c->d_bcinj, c->b_cinj);
+      if (e == cudaSuccess && !c->b_cbo.empty()) e = c->upload(&c->d_bcbo, c->b_cbo);
+      if (e == cudaSuccess) e = c->alloc_zero(&c->d_bcy, (2 * c->b_cb.size() + 2) * (size_t)c->S);
+      if (e == cudaSuccess) e = c->alloc_zero(&c->d_bcs, 2 * c->b_cb.size() * (size_t)c->S);
     }
     if (e == cudaSuccess) e = c->alloc_zero(&c->d_bh, (size_t)c->n_lc_total * c->S);
     if (e == cudaSuccess) e = c->alloc_zero(&c->d_bring, (size_t)std::max<int64_t>(c->bring_len, 1) * c->S);
@@ -1829,6 +1936,13 @@ static cudaError_t batch_launch(emt_ctx* c, int64_t n0, int64_t n_steps, cudaStr
   b.keep_le = c->d_keep_le;
   b.h = c->d_bh;
   b.ring = c->d_bring;
+  b.cb = c->d_bcb;
+  b.cb_lay = c->d_bcb_lay;
+  b.cb_list = c->d_bcb_list;
+  b.cinj = c->d_bcinj;
+  b.cbo = c->d_bcbo;
+  b.cy = c->d_bcy;
+  b.cs = c->d_bcs;
   b.rec = record ? c->d_rec : nullptr;
   b.rec_pos = c->d_rec_pos;
   b.rec_rows = c->rec_rows;
@@ -2087,6 +2201,7 @@ extern "C" emt_status emt_read_waveforms_async(emt_ctx* c, const int32_t* channe
 
 extern "C" emt_status emt_read_controls(emt_ctx* c, double* y, int64_t n, int32_t on_device) {
   if (!c) return EMT_EINVAL;
+  if (c->batched) return c->fail(EMT_EINVAL, "emt_read_controls: a scenario set's block outputs are per scenario");
   if (n != (int64_t)c->cb_slot_of.size())
     return c->fail(EMT_EINVAL, "emt_read_controls: n must equal the number of control blocks");
   if (n == 0) return EMT_OK;
@@ -2128,6 +2243,8 @@ extern "C" emt_status emt_reset(emt_ctx* c) {
     if (e == cudaSuccess) e = cudaMemset(c->d_bh, 0, std::max<size_t>((size_t)c->n_lc_total * c->S, 1) * sizeof(double));
     if (e == cudaSuccess)
       e = cudaMemset(c->d_bring, 0, std::max<size_t>((size_t)std::max<int64_t>(c->bring_len, 1) * c->S, 1) * sizeof(double));
+    if (e == cudaSuccess && c->d_bcy) e = cudaMemset(c->d_bcy, 0, (2 * c->b_cb.size() + 2) * (size_t)c->S * sizeof(double));
+    if (e == cudaSuccess && c->d_bcs) e = cudaMemset(c->d_bcs, 0, 2 * c->b_cb.size() * (size_t)c->S * sizeof(double));
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return c->cuda_fail(e, "emt_reset");

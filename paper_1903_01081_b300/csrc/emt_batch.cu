@@ -42,10 +42,11 @@ __device__ __forceinline__ int64_t ring_slot(long long step, int d1) { return (i
 __device__ __forceinline__ double entry_value(const BatchParams& P, uint32_t raw, int sg, int sl, long long step,
                                               const double* vs) {
   const uint32_t kind = (raw >> kBentKindShift) & 3u;
-  if (kind == 3u) return 0.0;
   const int idx = (int)(raw & kBentIndexMask);
   double val;
-  if (kind == 0u) {
+  if (kind == 3u) {   // a controlled current: its block's output of the previous step
+    val = P.cy[(int64_t)(2 * __ldg(P.cinj + idx) + (int)((step - 1) & 1)) * P.S + sg];
+  } else if (kind == 0u) {
     val = P.h[(int64_t)idx * P.S + sg];
   } else if (kind == 1u) {
     val = __ldg(P.sb_g + idx) * vs[__ldg(P.sb_src + idx) * P.S_t + sl];
@@ -55,6 +56,54 @@ __device__ __forceinline__ double entry_value(const BatchParams& P, uint32_t raw
   }
   // the sign by flipping the sign bit (integer pipe)
   return __longlong_as_double(__double_as_longlong(val) ^ ((long long)(raw & kEntryNeg) << 32));
+}
+
+// Control block g (global slot) for scenario sg at a step of parity par:
+// the same formulas as the single-network kernel, with inputs, outputs and
+// states per scenario in global memory and, for a block with scenario
+// parameters, this scenario's coefficients; MEAS reads the group's node
+// voltages (vv, tile lane sl, nodes from node0).
+__device__ __forceinline__ void batch_control(const BatchParams& P, int g, int sg, int sl, int par, const double* vv,
+                                              int node0, int St) {
+  const CtrlDev& r = P.cb[g];
+  const int64_t S = P.S;
+  double p0 = r.p0, p1 = r.p1, p2 = r.p2;
+  if (r.ov >= 0.0) {
+    const double* o = P.cbo + ((int64_t)r.ov * S + sg) * 3;
+    p0 = o[0];
+    p1 = o[1];
+    p2 = o[2];
+  }
+  const double u0 = P.cy[(int64_t)(r.i0 ^ par) * S + sg];
+  const double u1 = P.cy[(int64_t)(r.i1 ^ par) * S + sg];
+  double* sx = P.cs + (int64_t)(2 * g) * S + sg;   // (y or integral of the last step, u0 of the last step)
+  double out;
+  switch (r.type) {
+    case 0: out = p0; break;
+    case 1: out = vv[(size_t)(r.node - node0) * St + sl]; break;
+    case 2: out = p0 * u0; break;
+    case 3: out = fma(p0, u0, p1 * u1); break;
+    case 4: out = p0 * u0 * u1; break;
+    case 5: out = u0 < p0 ? p0 : (u0 > p1 ? p1 : u0); break;
+    case 6:
+      out = fma(p0, u0 + sx[S], sx[0]);
+      sx[0] = out;
+      sx[S] = u0;
+      break;
+    case 7:
+      out = fma(p1, u0 + sx[S], p0 * sx[0]);
+      sx[0] = out;
+      sx[S] = u0;
+      break;
+    default: {
+      const double integral = fma(p2, u0 + sx[S], sx[0]);
+      out = fma(p1, integral, p0 * u0);
+      sx[0] = integral;
+      sx[S] = u0;
+      break;
+    }
+  }
+  P.cy[(int64_t)(2 * g + par) * S + sg] = out;
 }
 
 __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams P) {
@@ -194,6 +243,21 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
         }
       }
       __syncthreads();
+
+      // control blocks of the group's subsystems at this step, layer by
+      // layer (their controlled currents enter the next step's injections)
+      for (int l = 0; l < G.n_lay; ++l) {
+        const int b0 = __ldg(P.cb_lay + G.lay0 + l), nb = __ldg(P.cb_lay + G.lay0 + l + 1) - b0;
+        for (int x = tid, k = q0, sl = r0; x < nb * St; x += T, k += dq, sl += dr) {
+          if (sl >= St) {
+            sl -= St;
+            ++k;
+          }
+          if (sl >= n_here) continue;
+          batch_control(P, __ldg(P.cb_list + b0 + k), sigma0 + sl, sl, (int)(step & 1), vv, G.node0, St);
+        }
+        __syncthreads();
+      }
 
       // process 1: history currents and line outputs of the group
       const int n_lc = G.lc1 - G.lc0, n_items = n_lc + (G.le1 - G.le0);

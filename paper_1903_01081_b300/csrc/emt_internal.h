@@ -155,7 +155,7 @@ struct __align__(16) CtrlDev {
   int32_t i0, i1;      // inputs, encoded as above
   int32_t node;        // MEAS: local node
   double p0, p1, p2;
-  double pad;
+  double ov;           // multi-scenario kernel: row of its per-scenario coefficients (BatchParams::cbo), or -1
 };
 
 // Control layer starts (local block slots) carry the layer's block type in
@@ -302,8 +302,9 @@ struct PrefParams {
 // Solve columns are numbered globally, subsystem by subsystem: column
 // sub_col_off[s] + k is node k of s for k < n, else its strong branch
 // k - n.  Batched injection entries name global slots: bits 29-30 the
-// kind (0 L/C slot, 1 source-branch slot, 2 line end, 3 none), bits 0-28
-// the index, bit 31 subtract.
+// kind (0 L/C slot, 1 source-branch slot, 2 line end, 3 control injection:
+// its block's output of the previous step), bits 0-28 the index, bit 31
+// subtract.
 constexpr uint32_t kBentKindShift = 29;
 constexpr uint32_t kBentIndexMask = (1u << 29) - 1;
 
@@ -312,6 +313,7 @@ struct BatchGroupDev {
   int32_t col0, col1;          // global solve columns
   int32_t lc0, lc1;            // L/C slots
   int32_t le0, le1;            // line ends
+  int32_t lay0, n_lay;         // control layers: block lists cb_lay[lay0 .. lay0 + n_lay] into cb_list
 };
 
 struct BatchParams {
@@ -351,6 +353,16 @@ struct BatchParams {
   const uint8_t* keep_le;      // [n_le][S]
   double* h;                   // [n_lc][S]
   double* ring;                // [slots][S]
+  // control blocks (global slots: subsystem by subsystem, by layer), their
+  // inputs as 2 slot + late over all blocks (zero pair 2 n_cb); outputs
+  // cy[(2 slot + parity) S + scenario], states cs[(2 slot + k) S + scenario]
+  const CtrlDev* cb;
+  const int32_t* cb_lay;       // per group and layer: first entry of cb_list (n_lay + 1 per group)
+  const int32_t* cb_list;      // global block slots, layer by layer
+  const int32_t* cinj;         // per control injection: global block slot
+  const double* cbo;           // [rows][S][3]: per-scenario p0, p1, p2 of blocks with scenario parameters
+  double* cy;
+  double* cs;
   double* rec;                 // [rows][S][n_rec]
   const int32_t* rec_pos;
   int64_t rec_rows;

@@ -69,6 +69,7 @@ class _ScenarioDesc(ctypes.Structure):
         ("rm_line_ptr", ctypes.c_void_p), ("rm_line", ctypes.c_void_p),
         ("sw_ptr", ctypes.c_void_p), ("sw_k", ctypes.c_void_p), ("sw_m", ctypes.c_void_p),
         ("sw_r", ctypes.c_void_p), ("sw_close_step", ctypes.c_void_p), ("sw_open_step", ctypes.c_void_p),
+        ("cbo_ptr", ctypes.c_void_p), ("cbo_block", ctypes.c_void_p), ("cbo_p0", ctypes.c_void_p),
     ]
 
 
@@ -215,6 +216,8 @@ def scenario_desc(sc, keep: list) -> _ScenarioDesc:
     d.sw_ptr, d.sw_k, d.sw_m = p(sc.sw_ptr, np.int64), p(sc.sw_k, np.int32), p(sc.sw_m, np.int32)
     d.sw_r = p(sc.sw_r, np.float64)
     d.sw_close_step, d.sw_open_step = p(sc.sw_close_step, np.int64), p(sc.sw_open_step, np.int64)
+    d.cbo_ptr, d.cbo_block = p(sc.cbo_ptr, np.int64), p(sc.cbo_block, np.int32)
+    d.cbo_p0 = p(sc.cbo_p0, np.float64)
     return d
 
 

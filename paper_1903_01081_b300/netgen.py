@@ -181,6 +181,7 @@ class Scenarios:
     * ``src_amp`` / ``src_phase``: [S, n_src] or None (base values).
     * removed branches / lines: CSR lists (``*_ptr`` has S+1 entries).
     * extra switches (faults): CSR over scenarios of (k, m, r, close, open).
+    * control-block parameters: CSR over scenarios of (block, new p0).
     """
     n_scenarios: int
     src_amp: Optional[np.ndarray] = None
@@ -195,6 +196,9 @@ class Scenarios:
     sw_r: Optional[np.ndarray] = None
     sw_close_step: Optional[np.ndarray] = None
     sw_open_step: Optional[np.ndarray] = None
+    cbo_ptr: Optional[np.ndarray] = None
+    cbo_block: Optional[np.ndarray] = None
+    cbo_p0: Optional[np.ndarray] = None
     meta: dict = field(default_factory=dict)
 
     def subset(self, idx) -> "Scenarios":
@@ -226,6 +230,8 @@ class Scenarios:
         if self.sw_ptr is not None:
             (out.sw_ptr, out.sw_k, out.sw_m, out.sw_r, out.sw_close_step, out.sw_open_step) = sub_csr(
                 self.sw_ptr, self.sw_k, self.sw_m, self.sw_r, self.sw_close_step, self.sw_open_step)
+        if self.cbo_ptr is not None:
+            out.cbo_ptr, out.cbo_block, out.cbo_p0 = sub_csr(self.cbo_ptr, self.cbo_block, self.cbo_p0)
         return out
 
     def expand(self, base: Network, s: int) -> Network:
@@ -259,6 +265,10 @@ class Scenarios:
                 np.concatenate([net.sw_close_step, self.sw_close_step[a:b]]).astype(np.int64))
             net.sw_open_step = np.ascontiguousarray(
                 np.concatenate([net.sw_open_step, self.sw_open_step[a:b]]).astype(np.int64))
+        if self.cbo_ptr is not None:
+            a, b = int(self.cbo_ptr[s]), int(self.cbo_ptr[s + 1])
+            net.cb_p0 = np.array(net.cb_p0, dtype=np.float64)
+            net.cb_p0[self.cbo_block[a:b]] = self.cbo_p0[a:b]
         return net
 
 
@@ -690,6 +700,44 @@ def shared_g(seed: int = 1004, n_scenarios: int = 4096, dt: float = 20e-6, n_ste
                    sw_m=np.asarray(swm, np.int32), sw_r=np.asarray(swr, np.float64),
                    sw_close_step=np.asarray(swc, np.int64), sw_open_step=np.asarray(swo, np.int64),
                    meta={"fault_bus": fault_bus, "fault_step": fault_step})
+    return net, sc
+
+
+def converter_study(seed: int = 1012, n_scenarios: int = 1024, n_converters: int = 40, dt: float = 20e-6,
+                    n_steps: int = 10000, fault_step: int = 2500):
+    """Multi-scenario study with control blocks, after the paper's PV case
+    (scenarios that differ in the PV units' irradiance): the 600-node
+    network of the N-1 study with ``n_converters`` power-regulated converter
+    loads (``with_converter_controls``, 24 blocks each).  Scenario s scales
+    every converter's power set point (its CONST block) by U[0.2, 1.0], and a
+    three-phase fault of R_f ~ U[0.01, 10] ohm at one seeded bus closes at
+    ``fault_step``.  Scenario s draws from ``default_rng([seed, s])``."""
+    base, _ = n1_contingency(n_scenarios=1, dt=dt, n_steps=n_steps)
+    net = with_converter_controls(base, seed=seed, n_converters=n_converters)
+    net.n_steps = n_steps
+    rng = np.random.default_rng(seed)
+    fault_bus = int(rng.integers(0, len(net.meta["bus_nodes"])))
+    refs = np.arange(n_converters, dtype=np.int32) * 24 + 11     # each converter's set-point block
+    assert np.all(np.asarray(net.cb_type)[refs] == CB_CONST)
+    cbo_ptr, cbo_block, cbo_p0 = [0], [], []
+    sw_ptr, swk, swm, swr, swc, swo = [0], [], [], [], [], []
+    for s in range(n_scenarios):
+        srng = np.random.default_rng([seed, s])
+        f = srng.uniform(0.2, 1.0, size=n_converters)
+        cbo_block += refs.tolist()
+        cbo_p0 += (np.asarray(net.cb_p0)[refs] * f).tolist()
+        cbo_ptr.append(len(cbo_block))
+        rf = float(srng.uniform(0.01, 10.0))
+        for nd in net.meta["bus_nodes"][fault_bus]:
+            swk.append(nd); swm.append(GROUND); swr.append(rf); swc.append(fault_step); swo.append(-1)
+        sw_ptr.append(len(swk))
+    sc = Scenarios(n_scenarios=n_scenarios,
+                   sw_ptr=np.asarray(sw_ptr, np.int64), sw_k=np.asarray(swk, np.int32),
+                   sw_m=np.asarray(swm, np.int32), sw_r=np.asarray(swr, np.float64),
+                   sw_close_step=np.asarray(swc, np.int64), sw_open_step=np.asarray(swo, np.int64),
+                   cbo_ptr=np.asarray(cbo_ptr, np.int64), cbo_block=np.asarray(cbo_block, np.int32),
+                   cbo_p0=np.asarray(cbo_p0, np.float64),
+                   meta={"fault_bus": fault_bus, "fault_step": fault_step, "set_point_blocks": refs})
     return net, sc
 
 

@@ -1,6 +1,7 @@
 """Host-side checks of the C ABI that need no GPU: the library builds and
 loads, exports every function include/emt.h declares, and rejects invalid
 network descriptions before touching the device."""
+import dataclasses
 import os
 import re
 
@@ -145,10 +146,20 @@ def test_rejects_bad_controls():
     assert "spanning two subsystems" in bad(net, cb_node=nd)
     cn = net.ci_node.copy(); cn[0] = other
     assert "outside its block group" in bad(net, ci_node=cn)
-    sc_net, sc = g.n1_contingency(n_scenarios=4, n_buses=24, n_sub=4, n_steps=10)
+    # per-scenario control parameters are validated before any device work
+    sc_net, sc = g.n1_contingency(n_scenarios=2, n_buses=24, n_sub=4, n_steps=10)
     ctl = g.with_converter_controls(sc_net, n_converters=2)
-    with pytest.raises(emt.EmtError, match="control blocks are not supported"):
-        emt.emt_build_network(ctl, sc)
+    lim = int(np.flatnonzero(np.asarray(ctl.cb_type) == g.CB_LIMIT)[0])
+
+    def bad_sc(blocks, values, match):
+        x = dataclasses.replace(sc, cbo_ptr=np.array([0, len(blocks), len(blocks)], np.int64),
+                                cbo_block=np.asarray(blocks, np.int32), cbo_p0=np.asarray(values, np.float64))
+        with pytest.raises(emt.EmtError, match=match):
+            emt.emt_build_network(ctl, x)
+    bad_sc([ctl.n_control_blocks], [1.0], "out of range")
+    bad_sc([3, 3], [1.0, 2.0], "twice")
+    bad_sc([3], [np.nan], "not finite")
+    bad_sc([lim], [float(ctl.cb_p1[lim]) + 1.0], "lower bound exceeds")
 
 
 def test_rejects_bad_fd_lines():

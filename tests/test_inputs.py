@@ -42,3 +42,22 @@ def test_condition_numbers_below_bound(make):
     net = make()
     conds = [np.linalg.cond(M) for M in subsystem_matrices(net)]
     assert max(conds) < 1e6, max(conds)
+
+
+def test_converter_study_scenarios_set_only_the_set_points():
+    """Scenario s of the control study, written out: the converters' CONST
+    set points scaled by its factors in [0.2, 1], every other block as in
+    the base network; a subset writes out the same scenarios."""
+    net, sc = g.converter_study(n_scenarios=6, n_converters=5, n_steps=10)
+    refs = sc.meta["set_point_blocks"]
+    base = np.asarray(net.cb_p0)
+    for s in range(6):
+        x = np.asarray(sc.expand(net, s).cb_p0)
+        f = x[refs] / base[refs]
+        assert np.all((f >= 0.2) & (f <= 1.0))
+        other = np.setdiff1d(np.arange(net.n_control_blocks), refs)
+        assert np.array_equal(x[other], base[other])
+    sub = sc.subset([4, 1])
+    assert np.array_equal(sub.expand(net, 0).cb_p0, sc.expand(net, 4).cb_p0)
+    assert np.array_equal(sub.expand(net, 1).cb_p0, sc.expand(net, 1).cb_p0)
+    assert np.array_equal(np.asarray(net.cb_p0), base)   # the base network is untouched
