@@ -15,9 +15,11 @@ de-energised state (emt_step_n), i.e. one pass of the whole hot path.
 leaves out the end-to-end leg, the CPU baseline, the parity check and the
 two further legs the metric names, reported as extra keys of the line:
   "scenarios": multi-scenario throughput (scenario-steps/s) of the N-1 study
-      (1,024 scenarios of a 600-node network, 10,000 steps, one launch) and
-      of the shared-G study (4,096 scenarios of the large-scale network;
-      3,000 of its 10,000 steps timed, across the fault at step 2,500);
+      (1,024 scenarios of a 600-node network, 10,000 steps, one launch), of
+      the shared-G study (4,096 scenarios of the large-scale network; 3,000
+      of its 10,000 steps timed, across the fault at step 2,500) and of a
+      control study (1,024 scenarios of the 600-node network with 40
+      converter loads, set points per scenario, 10,000 steps);
   "adjoint": emt_adjoint time over the forward time for the gradient of
       sum_n ||v_n - v*_n||^2 over 20,000 steps of the large-scale network
       with checkpoints every 256 steps (and with the whole tape kept);
@@ -313,7 +315,7 @@ def oracle_scenario_baseline(net, sc, n_scen, n_steps, seed=64):
             "sample": f"{n_scen} seeded scenarios, {n_steps} steps each, one process per core"}
 
 
-def scenario_legs(which=("n1", "shared_g"), steps=None, shape=None, warm=500, cpu=False):
+def scenario_legs(which=("n1", "shared_g", "controls"), steps=None, shape=None, warm=500, cpu=False):
     from paper_1903_01081_b300 import netgen as g
     out = {}
     if "n1" in which:
@@ -331,6 +333,15 @@ def scenario_legs(which=("n1", "shared_g"), steps=None, shape=None, warm=500, cp
                                         "resistance at step 2,500; 3,000 of 10,000 steps timed", **sg)
         if cpu:
             out["shared_g"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 64, 1000)
+    if "controls" in which:
+        net, sc = g.converter_study()
+        ct = scenario_leg("controls", net, sc, steps or 10000, 4, None, 100, 100, warm, shape)
+        out["control_study"] = dict(workload="600-node network with 40 converter loads (960 control blocks in 11 "
+                                             "layers, 120 controlled injections), per scenario the converters' power "
+                                             "set points x U[0.2, 1] and a fault resistance at step 2,500 (after the "
+                                             "paper's PV study across irradiances)", **ct)
+        if cpu:
+            out["control_study"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 64, 3000)
     return out
 
 
@@ -776,7 +787,7 @@ def main():
     ap.add_argument("--time-steps", type=int, default=N_STEPS)
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines",
-                                      "fd_lines", "nonlinear", "controls", "sizes"],
+                                      "fd_lines", "nonlinear", "controls", "sizes", "control_study"],
                     default="all",
                     help="all: the JSON line with every leg; single: the single-network leg only; "
                          "n1 / shared_g / adjoint: that leg alone (profiling)")
@@ -790,7 +801,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "fd_lines", "nonlinear",
-                    "controls", "sizes"):
+                    "controls", "sizes", "control_study"):
         return run_leg(args)
     return run_ours(args)
 
@@ -813,6 +824,9 @@ def run_leg(args):
         out = nonlinear_leg(args.leg_steps, reps=1)
     elif args.leg == "sizes":
         out = scale_legs(args.leg_steps, reps=1)
+    elif args.leg == "control_study":
+        shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
+        out = scenario_legs(("controls",), args.leg_steps, shape, args.leg_warm)
     else:
         shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
         out = scenario_legs((args.leg,), args.leg_steps, shape, args.leg_warm)
