@@ -193,6 +193,10 @@ struct emt_ctx {
   CtrlDev* d_bcb = nullptr;
   int32_t *d_bcinj = nullptr, *d_bcb_lay = nullptr, *d_bcb_list = nullptr;
   double *d_bcbo = nullptr, *d_bcy = nullptr, *d_bcs = nullptr;
+  // nonlinear resistors of the multi-scenario kernel (see BatchParams)
+  std::vector<int32_t> b_nlinfo, b_nlc;
+  int32_t *d_bnlinfo = nullptr, *d_bnlc = nullptr;
+  double* d_bnli = nullptr;
 
   std::vector<void*> allocations;
 
@@ -517,6 +521,16 @@ bool batch_configure(emt_ctx* c, int S_t, bool upload) {
       }
     }
     lay.push_back((int32_t)list.size());
+    // nonlinear resistors of the group's subsystems and their correction pairs
+    G.nl0 = a.nl_off;
+    G.nl1 = b.nl_off + b.n_nl;
+    G.nlc0 = G.nlc1 = 0;
+    for (int s = 0, pos = 0; s < s1; ++s) {
+      const SubDev& sd = c->subs[s];
+      if (s == s0) G.nlc0 = pos;
+      pos += sd.n_nl * sd.n;
+      G.nlc1 = pos;
+    }
     G.node0 = a.node_off;
     G.node1 = b.node_off + b.n;
     G.col0 = c->b_sub_col_off[s0];
@@ -669,6 +683,10 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
           E.ginv_off = goff;
           goff += (int64_t)sd.n * (sd.n + sd.n_str);
           E.nlz_off = -1;
+          if (sd.n_nl > 0) {   // its nonlinear resistor's column z right after the matrix (and its remainder)
+            E.nlz_off = goff;
+            goff += sd.n;
+          }
           E.sw_off = (int)c->switches.size();
           for (auto& cl : closed) {
             SwitchDev sw{};
@@ -783,6 +801,17 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
     }
     c->b_ev_ptr.push_back((int64_t)c->b_ev_step.size());
   }
+  // nonlinear resistors: per element its subsystem, nodes and first
+  // internal node; the (node, element) pairs its compensation corrects
+  for (int q = 0; q < nsub; ++q) {
+    const SubDev& sd = c->subs[q];
+    for (int x = 0; x < sd.n_nl; ++x) {
+      const int e = sd.nl_off + x;
+      c->b_nlinfo.insert(c->b_nlinfo.end(), {q, sd.n, sd.node_off, 0});
+      for (int r = 0; r < sd.n; ++r) c->b_nlc.insert(c->b_nlc.end(), {sd.node_off + r, e});
+    }
+  }
+
   // control blocks in global slots: inputs over all blocks (the zero pair
   // after the last one), MEAS nodes as internal nodes; the block of each
   // control injection; per-scenario coefficients of the blocks a scenario
@@ -1650,7 +1679,6 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   if (scen && !c->rswitches.empty()) return bail("runtime switches are not supported with a scenario set");
   if (scen && !c->cends.empty()) return bail("coupled lines are not supported with a scenario set");
   if (scen && d->n_fdlines > 0) return bail("frequency-dependent lines are not supported with a scenario set");
-  if (scen && d->n_nonlin > 0) return bail("nonlinear resistors are not supported with a scenario set");
   if (scen) {
     const std::string bm = build_scenarios(c, d, scen, local, new_of_orig, le_of_end, lc_slot_of, sb_slot_of);
     if (!bm.empty()) return bail(bm);
@@ -1740,6 +1768,11 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
       if (e == cudaSuccess) e = c->alloc_zero(&c->d_bcy, (2 * c->b_cb.size() + 2) * (size_t)c->S);
       if (e == cudaSuccess) e = c->alloc_zero(&c->d_bcs, 2 * c->b_cb.size() * (size_t)c->S);
     }
+    if (!c->b_nlinfo.empty()) {
+      if (e == cudaSuccess) e = c->upload(&c->d_bnlinfo, c->b_nlinfo);
+      if (e == cudaSuccess) e = c->upload(&c->d_bnlc, c->b_nlc);
+      if (e == cudaSuccess) e = c->alloc_zero(&c->d_bnli, c->nls.size() * (size_t)c->S);
+    }
     if (e == cudaSuccess) e = c->alloc_zero(&c->d_bh, (size_t)c->n_lc_total * c->S);
     if (e == cudaSuccess) e = c->alloc_zero(&c->d_bring, (size_t)std::max<int64_t>(c->bring_len, 1) * c->S);
     if (e == cudaSuccess) e = c->alloc_zero(&c->d_src_ac, (size_t)c->S * c->n_sources);
@@ -1806,8 +1839,8 @@ extern "C" emt_status emt_prefactor(emt_ctx* c) {
   p.ginv = c->d_ginv;
   p.ginv_lo = c->d_ginv_lo;
   p.nl = c->d_nl;
-  p.nlz = c->d_nlz;
-  p.nlz_lo = c->d_nlz_lo;
+  p.nlz = c->batched ? c->d_ginv : c->d_nlz;   // a scenario variant keeps z after its matrix
+  p.nlz_lo = c->batched ? c->d_ginv_lo : c->d_nlz_lo;
   p.work_g = d_wg;
   p.work_r = d_wr;
   p.status = d_status;
@@ -1943,6 +1976,10 @@ static cudaError_t batch_launch(emt_ctx* c, int64_t n0, int64_t n_steps, cudaStr
   b.cbo = c->d_bcbo;
   b.cy = c->d_bcy;
   b.cs = c->d_bcs;
+  b.nl = c->d_nl;
+  b.nlinfo = c->d_bnlinfo;
+  b.nlc = c->d_bnlc;
+  b.nl_i = c->d_bnli;
   b.rec = record ? c->d_rec : nullptr;
   b.rec_pos = c->d_rec_pos;
   b.rec_rows = c->rec_rows;

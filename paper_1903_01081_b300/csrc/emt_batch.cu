@@ -106,6 +106,30 @@ __device__ __forceinline__ void batch_control(const BatchParams& P, int g, int s
   P.cy[(int64_t)(2 * g + par) * S + sg] = out;
 }
 
+// Nonlinear resistor e for tile lane sl: the Thevenin voltage from the
+// linear solution vv, R_th from the column z of the scenario's current
+// matrix (after the matrix in ginv), then the segment j of the odd
+// piecewise-linear f whose image u + R_th f(u) holds |v_th| (images of the
+// breakpoints compared, no division), u on it and i = f(u) with v_th's sign.
+__device__ __forceinline__ double batch_nl_current(const BatchParams& P, int e, int sl, const long long* cur,
+                                                   const double* vv, int node0, int St) {
+  const NlDev& q = P.nl[e];
+  const int s = __ldg(P.nlinfo + 4 * e), n = __ldg(P.nlinfo + 4 * e + 1), node_off = __ldg(P.nlinfo + 4 * e + 2);
+  const int64_t zoff = cur[(size_t)sl * P.n_sub + s] + (int64_t)n * __ldg(P.sub_nc + s);
+  const double* z = P.ginv + zoff;
+  const float* zl = P.ginv_lo + zoff;
+  const double vk = q.k >= 0 ? vv[(size_t)(node_off + q.k - node0) * St + sl] : 0.0;
+  const double vm = q.m >= 0 ? vv[(size_t)(node_off + q.m - node0) * St + sl] : 0.0;
+  const double zk = q.k >= 0 ? z[q.k] + (double)zl[q.k] : 0.0;
+  const double zm = q.m >= 0 ? z[q.m] + (double)zl[q.m] : 0.0;
+  const double R = zk - zm, vth = vk - vm, x = fabs(vth);
+  int j = 0;
+  while (j < q.np && x >= fma(R, q.bi[j + 1], q.bv[j + 1])) ++j;
+  const double u = (x - R * fma(-q.sl[j], q.bv[j], q.bi[j])) / fma(R, q.sl[j], 1.0);
+  const double i = fma(q.sl[j], u - q.bv[j], q.bi[j]);
+  return vth < 0.0 ? -i : i;
+}
+
 __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int St = P.S_t;
@@ -243,6 +267,44 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
         }
       }
       __syncthreads();
+
+      // compensation method: each nonlinear resistor against its
+      // subsystem's linear solution, per scenario (its current from the
+      // Thevenin source v_th behind R_th = z_k - z_m), then v -= z i
+      if (G.nl1 > G.nl0) {
+        const int n_nlg = G.nl1 - G.nl0;
+        for (int x = tid, j = q0, sl = r0; x < n_nlg * St; x += T, j += dq, sl += dr) {
+          if (sl >= St) {
+            sl -= St;
+            ++j;
+          }
+          if (sl >= n_here) continue;
+          const int e = G.nl0 + j, sg = sigma0 + sl;
+          P.nl_i[(int64_t)e * S + sg] = batch_nl_current(P, e, sl, cur, vv, G.node0, St);
+        }
+        __syncthreads();
+        const int n_c = G.nlc1 - G.nlc0;
+        for (int x = tid, j = q0, sl = r0; x < n_c * St; x += T, j += dq, sl += dr) {
+          if (sl >= St) {
+            sl -= St;
+            ++j;
+          }
+          if (sl >= n_here) continue;
+          const int node = __ldg(P.nlc + 2 * (G.nlc0 + j)), e = __ldg(P.nlc + 2 * (G.nlc0 + j) + 1);
+          const int s = __ldg(P.nlinfo + 4 * e), n = __ldg(P.nlinfo + 4 * e + 1), node_off = __ldg(P.nlinfo + 4 * e + 2);
+          const int64_t zoff = cur[(size_t)sl * n_sub + s] + (int64_t)n * __ldg(P.sub_nc + s);
+          const int r = node - node_off;
+          const double i = P.nl_i[(int64_t)e * S + sigma0 + sl];
+          double* vp = vv + (size_t)(node - G.node0) * St + sl;
+          const double v = fma(-(double)__ldg(P.ginv_lo + zoff + r), i, fma(-__ldg(P.ginv + zoff + r), i, *vp));
+          *vp = v;
+          if (rec_now) {
+            const int pos = P.rec_pos[node];
+            if (pos >= 0) P.rec[(rec_row * S + sigma0 + sl) * P.n_rec + pos] = v;
+          }
+        }
+        __syncthreads();
+      }
 
       // control blocks of the group's subsystems at this step, layer by
       // layer (their controlled currents enter the next step's injections)

@@ -314,6 +314,8 @@ struct BatchGroupDev {
   int32_t lc0, lc1;            // L/C slots
   int32_t le0, le1;            // line ends
   int32_t lay0, n_lay;         // control layers: block lists cb_lay[lay0 .. lay0 + n_lay] into cb_list
+  int32_t nl0, nl1;            // nonlinear resistors of its subsystems
+  int32_t nlc0, nlc1;          // their (node, element) correction pairs in BatchParams::nlc
 };
 
 struct BatchParams {
@@ -363,6 +365,14 @@ struct BatchParams {
   const double* cbo;           // [rows][S][3]: per-scenario p0, p1, p2 of blocks with scenario parameters
   double* cy;
   double* cs;
+  // nonlinear resistors (compensation method per scenario): records, per
+  // element (subsystem, its nodes, its first internal node, 0), the
+  // correction pairs (internal node, element), and the currents [n_nl][S];
+  // a variant's column z (and its remainder) follows its matrix in ginv
+  const NlDev* nl;
+  const int32_t* nlinfo;
+  const int32_t* nlc;
+  double* nl_i;
   double* rec;                 // [rows][S][n_rec]
   const int32_t* rec_pos;
   int64_t rec_rows;

@@ -195,6 +195,8 @@ def test_rejects_bad_nonlinear():
     same = [x for x in range(net.n_nodes) if sub[x] == sub[net.nl_k[0]] and x != net.nl_k[0]][0]
     k = net.nl_k.copy(); k[1] = same
     assert "more than one nonlinear resistor" in bad(net, nl_k=k)
+    # the same checks hold with a scenario set (validated before any device work)
     sc_net, sc = g.n1_contingency(n_scenarios=4, n_buses=24, n_sub=4, n_steps=10)
-    with pytest.raises(emt.EmtError, match="nonlinear resistors are not supported"):
-        emt.emt_build_network(g.with_arresters(sc_net, n_arresters=1), sc)
+    arr = g.with_arresters(sc_net, n_arresters=1)
+    with pytest.raises(emt.EmtError, match="1 to 8"):
+        emt.emt_build_network(dataclasses.replace(arr, nl_np=np.array([9], np.int32)), sc)

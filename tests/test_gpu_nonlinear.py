@@ -82,3 +82,28 @@ def test_adjoint_rejects_nonlinear():
     with pytest.raises(emt.EmtError, match="nonlinear resistors have no adjoint"):
         emt.emt_adjoint(ctx, np.zeros((10, net.n_nodes)), 10)
     emt.emt_destroy(ctx)
+
+
+def test_scenario_set_with_arresters():
+    """Surge arresters in an N-1 study (compensation per scenario against the
+    scenario's own solve matrix): sampled scenarios against the oracle, each
+    written out as a plain network; the arresters conduct; two launches
+    equal one bit for bit."""
+    base, sc = g.n1_contingency(n_scenarios=32, n_steps=3000)
+    net = g.with_arresters(base, n_arresters=20)
+    N = 3000
+    sim = emt.Simulator(net, sc, n_steps=N)
+    sim.run(N)
+    sim.sync()
+    w = sim.waveforms()
+    sim.close()
+    for s in (0, 9, 31):
+        assert rel(w[:, s, :], oracle.simulate(sc.expand(net, s), N)) <= TOL
+    knee = min(g.ARRESTER_V) * 0.9
+    assert np.max(np.abs(w[:, :, np.asarray(net.nl_k)])) > knee
+    two = emt.Simulator(net, sc, n_steps=N)
+    two.run(1100)
+    two.run(N - 1100)
+    two.sync()
+    assert np.array_equal(two.waveforms(), w)
+    two.close()
