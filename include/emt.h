@@ -102,8 +102,9 @@ typedef struct emt_ctx emt_ctx;  /* opaque; owns all device memory it allocates 
  *   output of block ci_block[c] at step n enters unknown node ci_node[c]
  *   at step n + 1 (0 at step 1).  Every connected group of blocks, with the
  *   nodes it measures and drives, lies in one subsystem (a block group that
- *   touches no node runs in subsystem 0).  Not supported with a scenario
- *   set or by emt_adjoint.
+ *   touches no node runs in subsystem 0).  A scenario set may give blocks
+ *   their own p0 per scenario (emt_scenario_desc).  Not supported by
+ *   emt_adjoint.
  * Frequency-dependent lines (n_fdlines may be 0), one conductor each, ends
  *   fl_k / fl_m (unknown nodes, cut into different subsystems like any
  *   line): characteristic admittance and propagation function as
@@ -132,7 +133,8 @@ typedef struct emt_ctx emt_ctx;  /* opaque; owns all device memory it allocates 
  *   z = G^-1 (e_k - e_m) (prefactored with G^-1 for every switch state), solves
  *   i = f(v_th - R_th i) exactly on the right segment and sets v = v0 - z i.
  *   At most one per subsystem (the element joins its two ends into one
- *   subsystem).  Not supported with a scenario set or by emt_adjoint. */
+ *   subsystem).  With a scenario set each scenario solves it against its
+ *   own matrices.  Not supported by emt_adjoint. */
 typedef struct {
   double dt;
   int64_t n_nodes;
@@ -212,8 +214,8 @@ typedef struct {
  *     parameter p0 a scenario sets (block index, finite value; a block at
  *     most once per scenario; for a LIMIT the new lower bound must not
  *     exceed p1), e.g. a set point per scenario.  NULL: none.
- * Scenario sets take control blocks; they do not take runtime switches,
- * coupled or frequency-dependent lines or nonlinear resistors. */
+ * Scenario sets take control blocks and nonlinear resistors; they do not
+ * take runtime switches or coupled or frequency-dependent lines. */
 typedef struct {
   int64_t n_scenarios;
   const double* src_amp;
