@@ -396,7 +396,9 @@ emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
  * "threads_per_cta", "kernel_launches", "n_nodes", "n_branches", "n_sources", "n_line_ends",
  * "smem_bytes" (dynamic shared memory per CTA of the persistent kernel),
  * "ctas_per_sm" (how many of its CTAs one SM holds; a single network needs
- * n_subsystems <= that x the SM count),
+ * n_subsystems <= that x the SM count), "cta_max_line_ends",
+ * "cta_max_lc_branches", "cta_max_control_blocks", "cta_max_lanes",
+ * "cta_max_columns" (the per-CTA maxima that size its shared memory),
  * "n_strong_branches" (L/C branches applied through extra solve columns),
  * "n_runtime_switches", "n_coupled_lines", "n_fd_lines", "n_nonlinear", "n_control_blocks",
  * "n_control_injections", "max_control_layers" (largest layer count of one

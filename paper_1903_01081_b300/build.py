@@ -32,7 +32,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB_PATH
     nvcc = os.environ.get("NVCC", "nvcc")
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    cmd = [nvcc, "-shared", "-Xcompiler", "-fPIC", ARCH, "-lineinfo", "-O3", "-std=c++17",
+    # warnings are errors: one (a host-only constexpr call in __host__ __device__ code) once compiled to
+    # device code that silently did nothing
+    cmd = [nvcc, "-shared", "-Xcompiler", "-fPIC", ARCH, "-lineinfo", "-O3", "-std=c++17", "-Werror", "all-warnings",
            "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-o", tmp] + sources()
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

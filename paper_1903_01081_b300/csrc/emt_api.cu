@@ -868,8 +868,10 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
 
 // Components packed into at most `target` groups (one CTA each).  The
 // smallest group merges with the smallest partner that keeps the merged
-// group within `relax` times the largest component's nodes, line ends and
-// L/C branches, while there are too many groups: the large components keep
+// group within `relax_n` times the largest component's nodes and `relax`
+// times its line ends, L/C branches and control blocks (shared memory grows
+// with the square of the nodes, linearly with the rest), while there are
+// too many groups: the large components keep
 // CTAs of their own, a merged group stays small (its solve runs the zero
 // blocks too) and the per-CTA shared memory, sized by those maxima, hardly
 // grows.  A component with runtime switches or a nonlinear resistor keeps a
@@ -877,18 +879,21 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
 // G is block-diagonal, so its inverse is the blocks' inverses.
 std::vector<std::vector<int>> pack_components(const std::vector<std::vector<int>>& comps,
                                               const std::vector<char>& alone, const std::vector<int>& w_le,
-                                              const std::vector<int>& w_lc, int target, double relax) {
+                                              const std::vector<int>& w_lc, const std::vector<int>& w_cb,
+                                              int target, double relax, double relax_n) {
   const size_t K = comps.size();
   size_t max_n = 0;
-  int max_le = 0, max_lc = 0;
+  int max_le = 0, max_lc = 0, max_cb = 0;
   for (size_t x = 0; x < K; ++x) {
     max_n = std::max(max_n, comps[x].size());
     max_le = std::max(max_le, w_le[x]);
     max_lc = std::max(max_lc, w_lc[x]);
+    max_cb = std::max(max_cb, w_cb[x]);
   }
-  const double cap_n = relax * (double)max_n, cap_le = relax * max_le, cap_lc = relax * max_lc;
+  const double cap_n = relax_n * (double)max_n, cap_le = relax * max_le, cap_lc = relax * max_lc;
+  const double cap_cb = relax * max_cb;
   std::vector<std::vector<int>> groups(comps.begin(), comps.end());
-  std::vector<int> le(w_le), lc(w_lc);
+  std::vector<int> le(w_le), lc(w_lc), cb(w_cb);
   std::vector<int> open;   // mergeable groups
   for (size_t x = 0; x < K; ++x)
     if (!alone[x]) open.push_back((int)x);
@@ -900,7 +905,7 @@ std::vector<std::vector<int>> pack_components(const std::vector<std::vector<int>
     for (size_t j = 1; j < open.size() && pick < 0; ++j) {
       const int b = open[j];
       if ((double)(groups[a].size() + groups[b].size()) <= cap_n && le[a] + le[b] <= cap_le &&
-          lc[a] + lc[b] <= cap_lc)
+          lc[a] + lc[b] <= cap_lc && cb[a] + cb[b] <= cap_cb)
         pick = (int)j;
     }
     if (pick < 0) {   // the smallest fits with nothing: it stays as it is
@@ -912,6 +917,7 @@ std::vector<std::vector<int>> pack_components(const std::vector<std::vector<int>
     groups[b].clear();
     le[a] += le[b];
     lc[a] += lc[b];
+    cb[a] += cb[b];
     open.erase(open.begin() + pick);
     --n_groups;
   }
@@ -922,7 +928,7 @@ std::vector<std::vector<int>> pack_components(const std::vector<std::vector<int>
 }
 
 static emt_status build_network(const emt_network_desc* d, const emt_scenario_desc* scen, emt_ctx** out,
-                                 int pack_to, double relax);
+                                 int pack_to, double relax, double relax_n);
 
 // Co-resident CTAs of the single-network kernel for this context's limits.
 static int64_t forward_capacity(const emt_ctx* c) {
@@ -941,21 +947,33 @@ static int64_t forward_capacity(const emt_ctx* c) {
 // largest component step by step until the packed network fits.  Scenario
 // sets are not packed.
 extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_scenario_desc* scen, emt_ctx** out) {
-  emt_status st = build_network(d, scen, out, 0, 1.0);
+  emt_status st = build_network(d, scen, out, 0, 1.0, 1.0);
   if (st != EMT_OK || scen) return st;
-  const int64_t cap = forward_capacity(*out);
-  if (cap <= 0 || (*out)->n_sub <= cap) return st;
-  for (double relax : {1.0, 1.2, 1.5, 2.0}) {
+  int64_t target = forward_capacity(*out);
+  if (target <= 0 || (*out)->n_sub <= target) return st;
+  // bounds on a merged group, loosest last: the linear counts first, the nodes last
+  static const double kRelax[][2] = {{1.0, 1.0}, {1.5, 1.0}, {2.0, 1.0}, {3.0, 1.0}, {3.0, 1.25}, {3.0, 1.5}, {3.0, 2.0}};
+  int step = 0;
+  for (int attempt = 0; attempt < 16; ++attempt) {
     emt_destroy(*out);
     *out = nullptr;
-    st = build_network(d, scen, out, (int)cap, relax);
-    if (st != EMT_OK || (*out)->n_sub <= forward_capacity(*out)) return st;
+    st = build_network(d, scen, out, (int)target, kRelax[step][0], kRelax[step][1]);
+    if (st != EMT_OK) return st;
+    const int64_t n = (*out)->n_sub, cap = forward_capacity(*out);
+    if (n <= cap) return st;
+    if (n <= target) {
+      target = std::min(target - 1, cap);   // packed as asked, but its CTAs need more memory: aim lower
+    } else if (step + 1 < (int)(sizeof(kRelax) / sizeof(kRelax[0]))) {
+      ++step;                               // the bounds stop the merging short of the target
+    } else {
+      break;
+    }
   }
   return st;   // still too many CTAs: emt_step_n reports EMT_ERESOURCE
 }
 
 static emt_status build_network(const emt_network_desc* d, const emt_scenario_desc* scen, emt_ctx** out,
-                                 int pack_to, double relax) {
+                                 int pack_to, double relax, double relax_n) {
   if (!out) {
     g_build_error = "out is NULL";
     return EMT_EINVAL;
@@ -1046,7 +1064,28 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
     }
     for (int64_t b = 0; b < d->n_branches; ++b)
       if (d->br_kind[b] != 0) ++w_lc[c->sub_of_node[d->br_k[b] >= 0 ? d->br_k[b] : d->br_m[b]]];
-    nodes_of = pack_components(nodes_of, alone, w_le, w_lc, pack_to, relax);
+    // control blocks: a connected group of blocks sits with the nodes it measures or drives
+    std::vector<int> w_cb(nodes_of.size(), 0);
+    if (d->n_cblocks > 0) {
+      const int64_t NB = d->n_cblocks;
+      std::vector<int> bg(NB);
+      std::iota(bg.begin(), bg.end(), 0);
+      for (int64_t b = 0; b < NB; ++b)
+        for (const int32_t in : {d->cb_in0[b], d->cb_in1[b]})
+          if (in >= 0 && in < NB) {
+            const int x = uf_find(bg, (int)b), y = uf_find(bg, in);
+            if (x != y) bg[std::max(x, y)] = std::min(x, y);
+          }
+      std::vector<int> comp_of_group(NB, -1);
+      for (int64_t b = 0; b < NB; ++b)
+        if (d->cb_type[b] == 1) comp_of_group[uf_find(bg, (int)b)] = c->sub_of_node[d->cb_node[b]];
+      for (int64_t x = 0; x < d->n_cinj; ++x) comp_of_group[uf_find(bg, d->ci_block[x])] = c->sub_of_node[d->ci_node[x]];
+      for (int64_t b = 0; b < NB; ++b) {
+        const int cp = comp_of_group[uf_find(bg, (int)b)];
+        ++w_cb[cp >= 0 ? cp : 0];
+      }
+    }
+    nodes_of = pack_components(nodes_of, alone, w_le, w_lc, w_cb, pack_to, relax, relax_n);
     for (size_t g = 0; g < nodes_of.size(); ++g)
       for (int v : nodes_of[g]) c->sub_of_node[v] = (int)g;
   }
@@ -2397,6 +2436,11 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "autotuned") *value = c->tuned ? 1 : 0;
   else if (k == "n_epochs_total") *value = (int64_t)c->epochs.size();
   else if (k == "n_components") *value = c->n_components;
+  else if (k == "cta_max_line_ends") *value = c->lim.le;
+  else if (k == "cta_max_lc_branches") *value = c->lim.lc;
+  else if (k == "cta_max_control_blocks") *value = c->lim.cb;
+  else if (k == "cta_max_lanes") *value = c->lim.il;
+  else if (k == "cta_max_columns") *value = c->lim.nc;
   else if (k == "sum_n2_components") *value = c->comp_sum_n2;
   else if (k == "max_component_nodes") *value = c->comp_max_n;
   else if (k == "sum_n2") {

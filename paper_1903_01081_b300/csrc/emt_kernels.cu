@@ -370,7 +370,9 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   const size_t ldg = (size_t)(L.nc | 1);
   const size_t nbuf = L.nbuf > 1 ? 2 : 1;
   s.gi = d(nbuf * (size_t)L.n * ldg);
-  s.part = d((size_t)L.n * L.q);
+  const size_t nq = (size_t)L.n * L.q;
+  const size_t n_tasks = nq < (size_t)kFwdThreads ? nq : (size_t)kFwdThreads;   // a CTA's n q <= its threads
+  s.part = d(n_tasks);
   s.iv = d(L.nc);
   s.vv = d(L.n);
   s.inp = d((size_t)L.lc + L.sb + 2 * ((size_t)L.le + 3 * (size_t)L.ce + L.fd) + 1 + (size_t)L.ci + L.fd);
@@ -392,7 +394,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.fdst = d(kFdState * (size_t)L.fd);
   s.gilo = w(nbuf * (size_t)L.n * ldg);
   s.ivf = w(L.nc);
-  s.partf = w((size_t)L.n * L.q);
+  s.partf = w(n_tasks);
   s.lcstr = w(L.lc);
   s.lck = w(L.lc);
   s.lcm = w(L.lc);

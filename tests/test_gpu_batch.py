@@ -151,3 +151,22 @@ def test_launch_shape_options_are_checked():
     with pytest.raises(emt.EmtError):
         emt.emt_set_option(ctx, "scenarios_per_cta", 4)
     emt.emt_destroy(ctx)
+
+
+def test_pipelined_read_of_a_scenario_set():
+    """run_to_host on a scenario set (every scenario, decimated rows) equals
+    the synchronous read of the same run."""
+    import torch
+    net, sc = g.n1_contingency(n_scenarios=12, n_buses=40, n_sub=8, n_lines=12, n_sources=3, n_steps=3000,
+                               target_branches=240)
+    N, decim = 3000, 4
+    a = emt.Simulator(net, sc, n_steps=N, decim=decim)
+    a.run(N)
+    a.sync()
+    want = a.waveforms()
+    a.close()
+    b = emt.Simulator(net, sc, n_steps=N, decim=decim)
+    out = torch.empty((N // decim, 12, net.n_nodes), dtype=torch.float64, pin_memory=True)
+    b.run_to_host(N, out, chunk=900)
+    b.close()
+    assert np.array_equal(out.numpy(), want)

@@ -70,3 +70,24 @@ def test_all_features_together():
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= 1e-10
     yr = oracle.controls(net, N)[-1]
     assert np.max(np.abs(y - yr)) <= 1e-9 * np.max(np.abs(yr))
+
+
+def test_packed_network_with_controls_and_arresters():
+    """A 400-subsystem network with converter controls and surge arresters
+    (their subsystems keep CTAs of their own): the controls' shared memory
+    leaves room for two CTAs per SM, fewer than the subsystems, so the build
+    packs the others several to a CTA; against the oracle."""
+    import torch
+    N = 300
+    base = g.paper_scale(400, n_steps=N)
+    net = g.with_arresters(g.with_converter_controls(base, n_converters=100), n_arresters=40)
+    sim = emt.Simulator(net, n_steps=N)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    assert sim.info("n_components") == 400
+    assert sim.info("n_subsystems") < 400 and sim.info("n_subsystems") <= sim.info("ctas_per_sm") * n_sm
+    sim.run(N)
+    sim.sync()
+    got = sim.waveforms()[:, 0, :]
+    sim.close()
+    ref = oracle.simulate(net, N)
+    assert np.max(np.abs(got - ref)) <= 1e-10 * np.max(np.abs(ref))
