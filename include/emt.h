@@ -121,7 +121,7 @@ typedef struct emt_ctx emt_ctx;  /* opaque; owns all device memory it allocates 
  *   w_f(m) = 2 yc_f(m) - b_f(m): it stamps G_eq = fl_y0 + sum mu (> 0
  *   required) and draws a history current from the previous step.  With
  *   fl_y0 = 1/Z, fl_a0 = 1, no poles and tau = d dt this is the Bergeron
- *   line above.  Not supported with a scenario set or by emt_adjoint.
+ *   line above.  Not supported by emt_adjoint.
  * Nonlinear resistors (n_nonlin may be 0), solved by the compensation
  *   method (the paper's process 3 at run time, Sec. III-A): element x between
  *   nl_k and nl_m (unknown node or ground, not both ground) carries
@@ -214,8 +214,9 @@ typedef struct {
  *     parameter p0 a scenario sets (block index, finite value; a block at
  *     most once per scenario; for a LIMIT the new lower bound must not
  *     exceed p1), e.g. a set point per scenario.  NULL: none.
- * Scenario sets take control blocks and nonlinear resistors; they do not
- * take runtime switches or coupled or frequency-dependent lines. */
+ * Scenario sets take control blocks, nonlinear resistors and
+ * frequency-dependent lines (rm_line names lossless lines only); they do
+ * not take runtime switches or coupled lines. */
 typedef struct {
   int64_t n_scenarios;
   const double* src_amp;

@@ -197,6 +197,10 @@ struct emt_ctx {
   std::vector<int32_t> b_nlinfo, b_nlc;
   int32_t *d_bnlinfo = nullptr, *d_bnlc = nullptr;
   double* d_bnli = nullptr;
+  // frequency-dependent ends of the multi-scenario kernel (see BatchParams)
+  std::vector<int32_t> b_fd_le, b_le_fd;
+  int32_t *d_bfd_le = nullptr, *d_ble_fd = nullptr;
+  double* d_bfds = nullptr;
 
   std::vector<void*> allocations;
 
@@ -524,6 +528,8 @@ bool batch_configure(emt_ctx* c, int S_t, bool upload) {
     // nonlinear resistors of the group's subsystems and their correction pairs
     G.nl0 = a.nl_off;
     G.nl1 = b.nl_off + b.n_nl;
+    G.fd0 = a.fd_off;
+    G.fd1 = b.fd_off + b.n_fd;
     G.nlc0 = G.nlc1 = 0;
     for (int s = 0, pos = 0; s < s1; ++s) {
       const SubDev& sd = c->subs[s];
@@ -584,7 +590,7 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
       c->bsrc_phase[q * nsrc + j] = sc->src_phase ? sc->src_phase[q * nsrc + j] : d->src_phase[j];
     }
   std::vector<int> sub_of_br(c->branches.size()), sub_of_le(c->line_ends.size());
-  std::vector<int64_t> end_of_le(c->line_ends.size());
+  std::vector<int64_t> end_of_le(c->line_ends.size(), -1);
   for (int q = 0; q < nsub; ++q) {
     const SubDev& sd = c->subs[q];
     for (int b = sd.br_off; b < sd.br_off + sd.n_br; ++b) sub_of_br[b] = q;
@@ -719,9 +725,15 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
   int64_t off = 0;
   for (size_t e = 0; e < c->line_ends.size(); ++e) {
     c->le_bring[e] = off;
-    off += c->line_ends[e].d + 1;
+    off += c->line_ends[e].d + (c->line_ends[e].fd >= 0 ? 2 : 1);   // FD: w(n - d) and w(n - d - 1) stay readable
   }
-  for (size_t e = 0; e < c->line_ends.size(); ++e) c->le_bfar[e] = c->le_bring[le_of_end[end_of_le[e] ^ 1]];
+  // the far end of a lossless line by its line index, of a frequency-dependent one by its own ring
+  std::map<int64_t, size_t> fd_by_ring;
+  for (size_t e = 0; e < c->line_ends.size(); ++e)
+    if (c->line_ends[e].fd >= 0) fd_by_ring[c->line_ends[e].own_ring] = e;
+  for (size_t e = 0; e < c->line_ends.size(); ++e)
+    c->le_bfar[e] = c->line_ends[e].fd >= 0 ? c->le_bring[fd_by_ring.at(c->line_ends[e].far_ring)]
+                                            : c->le_bring[le_of_end[end_of_le[e] ^ 1]];
   c->bring_len = off;
 
   // flat per-slot arrays (global numbering of columns, lanes and slots)
@@ -751,11 +763,15 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
           const uint32_t raw = (uint32_t)c->ent[4 * (size_t)(sd.il_off + l) + u];
           const int idx = (int)(raw & ~kEntryNeg);
           uint32_t code;
-          const int zero = ie_base + 2 * sd.n_le;   // (no coupled or frequency-dependent ends here)
+          const int blk = sd.n_le + sd.n_fd;             // (no coupled ends here)
+          const int zero = ie_base + 2 * blk;
           if (idx < sd.n_lc) code = (0u << kBentKindShift) | (uint32_t)(sd.lc_off + idx);
           else if (idx < ie_base) code = (1u << kBentKindShift) | (uint32_t)(sd.sb_off + idx - sd.n_lc);
           else if (idx < ie_base + sd.n_le) code = (2u << kBentKindShift) | (uint32_t)(sd.le_off + idx - ie_base);
+          else if (idx < ie_base + blk) code = (4u << kBentKindShift) | (uint32_t)(sd.fd_off + idx - ie_base - sd.n_le);
           else if (idx > zero && idx <= zero + sd.n_ci) code = (3u << kBentKindShift) | (uint32_t)(sd.ci_off + idx - zero - 1);
+          else if (idx > zero + sd.n_ci && idx <= zero + sd.n_ci + sd.n_fd)
+            code = (5u << kBentKindShift) | (uint32_t)(sd.fd_off + idx - zero - 1 - sd.n_ci);
           else continue;
           c->b_bent.push_back((int32_t)(code | (raw & kEntryNeg)));
         }
@@ -801,6 +817,18 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
     }
     c->b_ev_ptr.push_back((int64_t)c->b_ev_step.size());
   }
+  // frequency-dependent ends: each one's global line end, and per line end
+  // its FD end (or -1)
+  c->b_le_fd.assign(c->line_ends.size(), -1);
+  for (int q = 0; q < nsub; ++q) {
+    const SubDev& sd = c->subs[q];
+    for (int x = 0; x < sd.n_fd; ++x) {
+      const int ge = sd.le_off + c->fdends[sd.fd_off + x].le;
+      c->b_fd_le.push_back(ge);
+      c->b_le_fd[ge] = sd.fd_off + x;
+    }
+  }
+
   // nonlinear resistors: per element its subsystem, nodes and first
   // internal node; the (node, element) pairs its compensation corrects
   for (int q = 0; q < nsub; ++q) {
@@ -1717,7 +1745,6 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   // -------- multi-scenario set
   if (scen && !c->rswitches.empty()) return bail("runtime switches are not supported with a scenario set");
   if (scen && !c->cends.empty()) return bail("coupled lines are not supported with a scenario set");
-  if (scen && d->n_fdlines > 0) return bail("frequency-dependent lines are not supported with a scenario set");
   if (scen) {
     const std::string bm = build_scenarios(c, d, scen, local, new_of_orig, le_of_end, lc_slot_of, sb_slot_of);
     if (!bm.empty()) return bail(bm);
@@ -1806,6 +1833,11 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
       if (e == cudaSuccess && !c->b_cbo.empty()) e = c->upload(&c->d_bcbo, c->b_cbo);
       if (e == cudaSuccess) e = c->alloc_zero(&c->d_bcy, (2 * c->b_cb.size() + 2) * (size_t)c->S);
       if (e == cudaSuccess) e = c->alloc_zero(&c->d_bcs, 2 * c->b_cb.size() * (size_t)c->S);
+    }
+    if (!c->b_fd_le.empty()) {
+      if (e == cudaSuccess) e = c->upload(&c->d_bfd_le, c->b_fd_le);
+      if (e == cudaSuccess) e = c->upload(&c->d_ble_fd, c->b_le_fd);
+      if (e == cudaSuccess) e = c->alloc_zero(&c->d_bfds, c->b_fd_le.size() * kBatchFdState * (size_t)c->S);
     }
     if (!c->b_nlinfo.empty()) {
       if (e == cudaSuccess) e = c->upload(&c->d_bnlinfo, c->b_nlinfo);
@@ -2019,6 +2051,10 @@ static cudaError_t batch_launch(emt_ctx* c, int64_t n0, int64_t n_steps, cudaStr
   b.nlinfo = c->d_bnlinfo;
   b.nlc = c->d_bnlc;
   b.nl_i = c->d_bnli;
+  b.fd = c->d_fd;
+  b.fd_le = c->d_bfd_le;
+  b.le_fd = c->d_ble_fd;
+  b.fds = c->d_bfds;
   b.rec = record ? c->d_rec : nullptr;
   b.rec_pos = c->d_rec_pos;
   b.rec_rows = c->rec_rows;
@@ -2321,6 +2357,8 @@ extern "C" emt_status emt_reset(emt_ctx* c) {
       e = cudaMemset(c->d_bring, 0, std::max<size_t>((size_t)std::max<int64_t>(c->bring_len, 1) * c->S, 1) * sizeof(double));
     if (e == cudaSuccess && c->d_bcy) e = cudaMemset(c->d_bcy, 0, (2 * c->b_cb.size() + 2) * (size_t)c->S * sizeof(double));
     if (e == cudaSuccess && c->d_bcs) e = cudaMemset(c->d_bcs, 0, 2 * c->b_cb.size() * (size_t)c->S * sizeof(double));
+    if (e == cudaSuccess && c->d_bfds)
+      e = cudaMemset(c->d_bfds, 0, c->b_fd_le.size() * kBatchFdState * (size_t)c->S * sizeof(double));
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return c->cuda_fail(e, "emt_reset");

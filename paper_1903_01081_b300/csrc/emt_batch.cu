@@ -41,10 +41,12 @@ __device__ __forceinline__ int64_t ring_slot(long long step, int d1) { return (i
 // Signed value of one batched injection entry for scenario sg (tile lane sl).
 __device__ __forceinline__ double entry_value(const BatchParams& P, uint32_t raw, int sg, int sl, long long step,
                                               const double* vs) {
-  const uint32_t kind = (raw >> kBentKindShift) & 3u;
+  const uint32_t kind = (raw >> kBentKindShift) & 7u;
   const int idx = (int)(raw & kBentIndexMask);
   double val;
-  if (kind == 3u) {   // a controlled current: its block's output of the previous step
+  if (kind >= 4u) {   // a frequency-dependent end's b (4) or Hy (5) of this step
+    val = P.fds[((int64_t)idx * kBatchFdState + (kind == 4u ? 11 : 10)) * P.S + sg];
+  } else if (kind == 3u) {   // a controlled current: its block's output of the previous step
     val = P.cy[(int64_t)(2 * __ldg(P.cinj + idx) + (int)((step - 1) & 1)) * P.S + sg];
   } else if (kind == 0u) {
     val = P.h[(int64_t)idx * P.S + sg];
@@ -130,6 +132,55 @@ __device__ __forceinline__ double batch_nl_current(const BatchParams& P, int e, 
   return vth < 0.0 ? -i : i;
 }
 
+// The far end's w of step m from this FD end's ring (depth d + 2); 0 before step 1.
+__device__ __forceinline__ double fd_ring_w(const BatchParams& P, int ge, long long m, int sg) {
+  if (m < 1) return 0.0;
+  const int depth = __ldg(P.le_d1 + ge) + 1;
+  return P.ring[(__ldg(P.le_bring + ge) + (int64_t)((unsigned long long)m % (unsigned)depth)) * P.S + sg];
+}
+
+// FD end x at the start of step n (scenario sg): b(n) and the A terms.
+__device__ __forceinline__ void batch_fd_fold(const BatchParams& P, int x, int sg, long long step) {
+  const FdEndDev& r = P.fd[x];
+  const int ge = __ldg(P.fd_le + x);
+  const int d = __ldg(P.le_d1 + ge) - 1;
+  const int64_t S = P.S;
+  double* st = P.fds + (int64_t)x * kBatchFdState * S + sg;
+  const double w_new = fd_ring_w(P, ge, step - d, sg), w_old = fd_ring_w(P, ge, step - d - 1, sg);
+  const double W = fma(1.0 - r.omf, w_old, r.omf * w_new);
+  const double ws = W + st[9 * S];
+  double zsum = 0.0;
+  for (int i = 0; i < r.na; ++i) {
+    const double z = fma(r.lam_a[i], st[(4 + i) * S], r.mu_a[i] * ws);
+    st[(4 + i) * S] = z;
+    zsum = i == 0 ? z : zsum + z;
+  }
+  st[9 * S] = W;
+  st[11 * S] = fma(r.a0, W, zsum);
+}
+
+// FD end x (line end ge) after the solve of step n: Y_c's terms of v, the
+// line output w = 2 yc - b into the far end's ring, and Hy(n+1).
+__device__ __forceinline__ void batch_fd_update(const BatchParams& P, int ge, int x, int sg, long long step, double v) {
+  const FdEndDev& r = P.fd[x];
+  const int64_t S = P.S;
+  double* st = P.fds + (int64_t)x * kBatchFdState * S + sg;
+  const double vsum = v + st[8 * S];
+  double ssum = 0.0, lam_s = 0.0;
+  for (int i = 0; i < r.ny; ++i) {
+    const double si = fma(r.lam_y[i], st[i * S], r.mu_y[i] * vsum);
+    st[i * S] = si;
+    ssum = i == 0 ? si : ssum + si;
+    lam_s = i == 0 ? r.lam_y[i] * si : fma(r.lam_y[i], si, lam_s);
+  }
+  const double yc = fma(r.y0, v, ssum);
+  const double w = fma(2.0, yc, -st[11 * S]);
+  const int depth = __ldg(P.le_d1 + ge) + 1;
+  P.ring[(__ldg(P.le_bfar + ge) + (int64_t)((unsigned long long)step % (unsigned)depth)) * S + sg] = w;
+  st[8 * S] = v;
+  st[10 * S] = fma(r.mu_sum, v, lam_s);
+}
+
 __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int St = P.S_t;
@@ -197,6 +248,22 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
 
     for (int g = 0; g < P.n_groups; ++g) {
       const BatchGroupDev G = P.grp[g];
+
+      // frequency-dependent ends: W(n) interpolated from the far end's w of
+      // steps n - d and n - d - 1 (its ring, depth d + 2), A's pole terms
+      // z_i(n) = lam z_i(n-1) + mu (W(n) + W(n-1)) and b(n) = a0 W + sum z_i
+      if (G.fd1 > G.fd0) {
+        const int n_fdg = G.fd1 - G.fd0;
+        for (int x = tid, j = q0, sl = r0; x < n_fdg * St; x += T, j += dq, sl += dr) {
+          if (sl >= St) {
+            sl -= St;
+            ++j;
+          }
+          if (sl >= n_here) continue;
+          batch_fd_fold(P, G.fd0 + j, sigma0 + sl, step);
+        }
+        __syncthreads();
+      }
 
       // process 2: nodal injections (and the strong-branch inputs -h)
       const int n_cols = G.col1 - G.col0;
@@ -340,6 +407,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
           double* hp = P.h + (int64_t)gl * S + sg;
           const double hv = *hp;
           *hp = __ldg(P.lc_isl + gl) ? fma(e, vk - vm, hv) : fma(e, vk - vm, -hv);
+        } else if (P.le_fd != nullptr && __ldg(P.le_fd + G.le0 + (it - n_lc)) >= 0) {
+          const int ge = G.le0 + (it - n_lc);
+          batch_fd_update(P, ge, __ldg(P.le_fd + ge), sg, step, vv[(size_t)(__ldg(P.le_nd + ge) - G.node0) * St + sl]);
         } else {
           const int ge = G.le0 + (it - n_lc);
           const int d1 = __ldg(P.le_d1 + ge);

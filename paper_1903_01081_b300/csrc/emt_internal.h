@@ -301,12 +301,15 @@ struct PrefParams {
 //
 // Solve columns are numbered globally, subsystem by subsystem: column
 // sub_col_off[s] + k is node k of s for k < n, else its strong branch
-// k - n.  Batched injection entries name global slots: bits 29-30 the
+// k - n.  Batched injection entries name global slots: bits 28-30 the
 // kind (0 L/C slot, 1 source-branch slot, 2 line end, 3 control injection:
-// its block's output of the previous step), bits 0-28 the index, bit 31
-// subtract.
-constexpr uint32_t kBentKindShift = 29;
-constexpr uint32_t kBentIndexMask = (1u << 29) - 1;
+// its block's output of the previous step, 4 / 5 a frequency-dependent
+// end's b / Hy of the step), bits 0-27 the index, bit 31 subtract.
+constexpr uint32_t kBentKindShift = 28;
+constexpr uint32_t kBentIndexMask = (1u << 28) - 1;
+// Per-scenario state of a frequency-dependent end in the multi-scenario
+// kernel: Y_c terms s 0..3, A terms z 4..7, v(n-1) 8, W(n-1) 9, Hy 10, b 11.
+constexpr int kBatchFdState = 12;
 
 struct BatchGroupDev {
   int32_t node0, node1;        // internal nodes [node0, node1)
@@ -316,6 +319,7 @@ struct BatchGroupDev {
   int32_t lay0, n_lay;         // control layers: block lists cb_lay[lay0 .. lay0 + n_lay] into cb_list
   int32_t nl0, nl1;            // nonlinear resistors of its subsystems
   int32_t nlc0, nlc1;          // their (node, element) correction pairs in BatchParams::nlc
+  int32_t fd0, fd1;            // frequency-dependent line ends of its subsystems
 };
 
 struct BatchParams {
@@ -373,6 +377,13 @@ struct BatchParams {
   const int32_t* nlinfo;
   const int32_t* nlc;
   double* nl_i;
+  // frequency-dependent line ends: records, each one's line end, per line
+  // end its FD end or -1, and the states [x][kBatchFdState][S]; an FD end's
+  // ring (depth d + 2) holds w by the step it was sent
+  const FdEndDev* fd;
+  const int32_t* fd_le;
+  const int32_t* le_fd;
+  double* fds;
   double* rec;                 // [rows][S][n_rec]
   const int32_t* rec_pos;
   int64_t rec_rows;

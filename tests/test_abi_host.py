@@ -178,9 +178,11 @@ def test_rejects_bad_fd_lines():
     assert "unknown nodes" in bad(net, fl_k=k)
     y0 = np.zeros_like(net.fl_y0); ny0 = np.zeros_like(net.fl_ny)
     assert "end conductance" in bad(net, fl_y0=y0, fl_ny=ny0)
+    # scenario sets take frequency-dependent lines, but their removals name lossless lines only
     sc_net, sc = g.n1_contingency(n_scenarios=4, n_buses=24, n_sub=4, n_steps=10)
-    with pytest.raises(emt.EmtError, match="frequency-dependent lines are not supported"):
-        emt.emt_build_network(g.with_fd_lines(sc_net), sc)
+    x = dataclasses.replace(sc, rm_line_ptr=np.array([0, 1, 1, 1, 1], np.int64), rm_line=np.array([0], np.int32))
+    with pytest.raises(emt.EmtError, match="removed line out of range"):
+        emt.emt_build_network(g.with_fd_lines(sc_net), x)
 
 
 def test_rejects_bad_nonlinear():

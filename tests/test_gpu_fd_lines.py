@@ -91,3 +91,28 @@ def test_adjoint_rejects_fd_lines():
     with pytest.raises(emt.EmtError, match="frequency-dependent lines have no adjoint"):
         emt.emt_adjoint(ctx, np.zeros((10, net.n_nodes)), 10)
     emt.emt_destroy(ctx)
+
+
+def test_scenario_set_with_fd_lines():
+    """A study on the 600-node network with its lines frequency-dependent
+    (per scenario the source amplitudes and angles and a fault resistance):
+    sampled scenarios against the oracle, each written out as a plain
+    network; two launches equal one bit for bit."""
+    N = 3000
+    base, _ = g.n1_contingency(n_scenarios=1, n_steps=N)
+    net, sc = g.shared_g(n_scenarios=24, n_steps=N, fault_step=1500, base=g.with_fd_lines(base))
+    assert net.n_fd_lines > 0 and net.n_lines == 0
+    sim = emt.Simulator(net, sc, n_steps=N)
+    sim.run(N)
+    sim.sync()
+    w = sim.waveforms()
+    sim.close()
+    for s in (0, 11, 23):
+        ref = oracle.simulate(sc.expand(net, s), N)
+        assert np.max(np.abs(w[:, s, :] - ref)) <= 1e-10 * np.max(np.abs(ref))
+    two = emt.Simulator(net, sc, n_steps=N)
+    two.run(1234)
+    two.run(N - 1234)
+    two.sync()
+    assert np.array_equal(two.waveforms(), w)
+    two.close()
