@@ -19,8 +19,9 @@ two further legs the metric names, reported as extra keys of the line:
       the shared-G study (4,096 scenarios of the large-scale network; 3,000
       of its 10,000 steps timed, across the fault at step 2,500) and of a
       control study (1,024 scenarios of the 600-node network with 40
-      converter loads, set points per scenario, 10,000 steps) and of the
-      N-1 study with 20 surge arresters;
+      converter loads, set points per scenario, 10,000 steps), of the N-1
+      study with 20 surge arresters and of a study of the 600-node network
+      with frequency-dependent lines;
   "adjoint": emt_adjoint time over the forward time for the gradient of
       sum_n ||v_n - v*_n||^2 over 20,000 steps of the large-scale network
       with checkpoints every 256 steps (and with the whole tape kept);
@@ -316,7 +317,8 @@ def oracle_scenario_baseline(net, sc, n_scen, n_steps, seed=64):
             "sample": f"{n_scen} seeded scenarios, {n_steps} steps each, one process per core"}
 
 
-def scenario_legs(which=("n1", "shared_g", "controls", "arresters"), steps=None, shape=None, warm=500, cpu=False):
+def scenario_legs(which=("n1", "shared_g", "controls", "arresters", "fd"), steps=None, shape=None, warm=500,
+                  cpu=False):
     from paper_1903_01081_b300 import netgen as g
     out = {}
     if "n1" in which:
@@ -352,6 +354,16 @@ def scenario_legs(which=("n1", "shared_g", "controls", "arresters"), steps=None,
                                               "solved by the compensation method per scenario", **ar)
         if cpu:
             out["arrester_study"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 64, 3000)
+    if "fd" in which:
+        base, _ = g.n1_contingency(n_scenarios=1)
+        net, sc = g.shared_g(n_scenarios=1024, base=g.with_fd_lines(base))
+        fd = scenario_leg("fd", net, sc, steps or 10000, 4, None, 100, 100, warm, shape)
+        out["fd_line_study"] = dict(workload="the 600-node network with its 168 line conductors frequency-dependent "
+                                             "(one Y_c pole, two propagation poles, fractional travel times); per "
+                                             "scenario source amplitudes and angles and a fault resistance at step "
+                                             "2,500", **fd)
+        if cpu:
+            out["fd_line_study"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 64, 3000)
     return out
 
 
@@ -798,7 +810,7 @@ def main():
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines",
                                       "fd_lines", "nonlinear", "controls", "sizes", "control_study",
-                                      "arrester_study"],
+                                      "arrester_study", "fd_line_study"],
                     default="all",
                     help="all: the JSON line with every leg; single: the single-network leg only; "
                          "n1 / shared_g / adjoint: that leg alone (profiling)")
@@ -812,7 +824,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "fd_lines", "nonlinear",
-                    "controls", "sizes", "control_study", "arrester_study"):
+                    "controls", "sizes", "control_study", "arrester_study", "fd_line_study"):
         return run_leg(args)
     return run_ours(args)
 
@@ -835,9 +847,9 @@ def run_leg(args):
         out = nonlinear_leg(args.leg_steps, reps=1)
     elif args.leg == "sizes":
         out = scale_legs(args.leg_steps, reps=1)
-    elif args.leg in ("control_study", "arrester_study"):
+    elif args.leg in ("control_study", "arrester_study", "fd_line_study"):
         shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
-        which = {"control_study": "controls", "arrester_study": "arresters"}[args.leg]
+        which = {"control_study": "controls", "arrester_study": "arresters", "fd_line_study": "fd"}[args.leg]
         out = scenario_legs((which,), args.leg_steps, shape, args.leg_warm)
     else:
         shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
