@@ -20,8 +20,8 @@ two further legs the metric names, reported as extra keys of the line:
       of its 10,000 steps timed, across the fault at step 2,500) and of a
       control study (1,024 scenarios of the 600-node network with 40
       converter loads, set points per scenario, 10,000 steps), of the N-1
-      study with 20 surge arresters and of a study of the 600-node network
-      with frequency-dependent lines;
+      study with 20 surge arresters and of studies of the 600-node network
+      with frequency-dependent and with coupled lines;
   "adjoint": emt_adjoint time over the forward time for the gradient of
       sum_n ||v_n - v*_n||^2 over 20,000 steps of the large-scale network
       with checkpoints every 256 steps (and with the whole tape kept);
@@ -317,8 +317,8 @@ def oracle_scenario_baseline(net, sc, n_scen, n_steps, seed=64):
             "sample": f"{n_scen} seeded scenarios, {n_steps} steps each, one process per core"}
 
 
-def scenario_legs(which=("n1", "shared_g", "controls", "arresters", "fd"), steps=None, shape=None, warm=500,
-                  cpu=False):
+def scenario_legs(which=("n1", "shared_g", "controls", "arresters", "fd", "coupled"), steps=None, shape=None,
+                  warm=500, cpu=False):
     from paper_1903_01081_b300 import netgen as g
     out = {}
     if "n1" in which:
@@ -364,6 +364,16 @@ def scenario_legs(which=("n1", "shared_g", "controls", "arresters", "fd"), steps
                                              "2,500", **fd)
         if cpu:
             out["fd_line_study"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 64, 3000)
+    if "coupled" in which:
+        base, _ = g.n1_contingency(n_scenarios=1)
+        net, sc = g.shared_g(n_scenarios=1024, base=g.with_coupled_lines(base))
+        cl = scenario_leg("coupled", net, sc, steps or 10000, 4, None, 100, 100, warm, shape)
+        out["coupled_line_study"] = dict(workload="the 600-node network with its 56 three-phase lines as coupled "
+                                                  "Clarke-mode lines with interpolated travel times; per scenario "
+                                                  "source amplitudes and angles and a fault resistance at step 2,500",
+                                         **cl)
+        if cpu:
+            out["coupled_line_study"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 64, 3000)
     return out
 
 
@@ -810,7 +820,7 @@ def main():
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines",
                                       "fd_lines", "nonlinear", "controls", "sizes", "control_study",
-                                      "arrester_study", "fd_line_study"],
+                                      "arrester_study", "fd_line_study", "coupled_line_study"],
                     default="all",
                     help="all: the JSON line with every leg; single: the single-network leg only; "
                          "n1 / shared_g / adjoint: that leg alone (profiling)")
@@ -824,7 +834,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "fd_lines", "nonlinear",
-                    "controls", "sizes", "control_study", "arrester_study", "fd_line_study"):
+                    "controls", "sizes", "control_study", "arrester_study", "fd_line_study", "coupled_line_study"):
         return run_leg(args)
     return run_ours(args)
 
@@ -847,9 +857,10 @@ def run_leg(args):
         out = nonlinear_leg(args.leg_steps, reps=1)
     elif args.leg == "sizes":
         out = scale_legs(args.leg_steps, reps=1)
-    elif args.leg in ("control_study", "arrester_study", "fd_line_study"):
+    elif args.leg in ("control_study", "arrester_study", "fd_line_study", "coupled_line_study"):
         shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
-        which = {"control_study": "controls", "arrester_study": "arresters", "fd_line_study": "fd"}[args.leg]
+        which = {"control_study": "controls", "arrester_study": "arresters", "fd_line_study": "fd",
+                 "coupled_line_study": "coupled"}[args.leg]
         out = scenario_legs((which,), args.leg_steps, shape, args.leg_warm)
     else:
         shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None

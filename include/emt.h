@@ -78,7 +78,7 @@ typedef struct emt_ctx emt_ctx;  /* opaque; owns all device memory it allocates 
  *   c_j(n) = -(2/Z_j) v_mode_j(n) - I_mode_j(n), and the far end's history
  *   is (1 - f) c(n - d) + f c(n - d - 1), tau = (d + f) dt, d = floor(tau/dt)
  *   (linear interpolation of the travel time).  An end's three phase nodes
- *   are one subsystem.  Not supported with a scenario set; emt_adjoint
+ *   are one subsystem.  Scenario sets take them; emt_adjoint
  *   differentiates through them (their own Z, T_v and travel times are not
  *   parameters).
  * Control system (n_cblocks may be 0): the paper's control components as
@@ -214,9 +214,9 @@ typedef struct {
  *     parameter p0 a scenario sets (block index, finite value; a block at
  *     most once per scenario; for a LIMIT the new lower bound must not
  *     exceed p1), e.g. a set point per scenario.  NULL: none.
- * Scenario sets take control blocks, nonlinear resistors and
+ * Scenario sets take control blocks, nonlinear resistors, coupled and
  * frequency-dependent lines (rm_line names lossless lines only); they do
- * not take runtime switches or coupled lines. */
+ * not take runtime switches. */
 typedef struct {
   int64_t n_scenarios;
   const double* src_amp;

@@ -201,6 +201,11 @@ struct emt_ctx {
   std::vector<int32_t> b_fd_le, b_le_fd;
   int32_t *d_bfd_le = nullptr, *d_ble_fd = nullptr;
   double* d_bfds = nullptr;
+  // coupled ends of the multi-scenario kernel (see BatchParams)
+  std::vector<int32_t> b_ce_le0, b_le_ce, b_ce_node;
+  std::vector<double> b_le_f;
+  int32_t *d_bce_le0 = nullptr, *d_ble_ce = nullptr, *d_bce_node = nullptr;
+  double *d_ble_f = nullptr, *d_bcim = nullptr, *d_bcph = nullptr;
 
   std::vector<void*> allocations;
 
@@ -530,6 +535,8 @@ bool batch_configure(emt_ctx* c, int S_t, bool upload) {
     G.nl1 = b.nl_off + b.n_nl;
     G.fd0 = a.fd_off;
     G.fd1 = b.fd_off + b.n_fd;
+    G.ce0 = a.ce_off;
+    G.ce1 = b.ce_off + b.n_ce;
     G.nlc0 = G.nlc1 = 0;
     for (int s = 0, pos = 0; s < s1; ++s) {
       const SubDev& sd = c->subs[s];
@@ -725,15 +732,16 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
   int64_t off = 0;
   for (size_t e = 0; e < c->line_ends.size(); ++e) {
     c->le_bring[e] = off;
-    off += c->line_ends[e].d + (c->line_ends[e].fd >= 0 ? 2 : 1);   // FD: w(n - d) and w(n - d - 1) stay readable
+    // FD ends and coupled modes interpolate: their values of steps n - d and n - d - 1 stay readable
+    off += c->line_ends[e].d + (c->line_ends[e].fd >= 0 || c->line_ends[e].ce >= 0 ? 2 : 1);
   }
   // the far end of a lossless line by its line index, of a frequency-dependent one by its own ring
-  std::map<int64_t, size_t> fd_by_ring;
+  std::map<int64_t, size_t> by_ring;   // FD ends and coupled modes by their own ring
   for (size_t e = 0; e < c->line_ends.size(); ++e)
-    if (c->line_ends[e].fd >= 0) fd_by_ring[c->line_ends[e].own_ring] = e;
+    if (c->line_ends[e].fd >= 0 || c->line_ends[e].ce >= 0) by_ring[c->line_ends[e].own_ring] = e;
   for (size_t e = 0; e < c->line_ends.size(); ++e)
-    c->le_bfar[e] = c->line_ends[e].fd >= 0 ? c->le_bring[fd_by_ring.at(c->line_ends[e].far_ring)]
-                                            : c->le_bring[le_of_end[end_of_le[e] ^ 1]];
+    c->le_bfar[e] = c->line_ends[e].fd >= 0 || c->line_ends[e].ce >= 0 ? c->le_bring[by_ring.at(c->line_ends[e].far_ring)]
+                                                                        : c->le_bring[le_of_end[end_of_le[e] ^ 1]];
   c->bring_len = off;
 
   // flat per-slot arrays (global numbering of columns, lanes and slots)
@@ -763,12 +771,13 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
           const uint32_t raw = (uint32_t)c->ent[4 * (size_t)(sd.il_off + l) + u];
           const int idx = (int)(raw & ~kEntryNeg);
           uint32_t code;
-          const int blk = sd.n_le + sd.n_fd;             // (no coupled ends here)
-          const int zero = ie_base + 2 * blk;
+          const int blk = sd.n_le + 3 * sd.n_ce + sd.n_fd;
+          const int zero = ie_base + 2 * blk, cph0 = ie_base + sd.n_le, fdb0 = cph0 + 3 * sd.n_ce;
           if (idx < sd.n_lc) code = (0u << kBentKindShift) | (uint32_t)(sd.lc_off + idx);
           else if (idx < ie_base) code = (1u << kBentKindShift) | (uint32_t)(sd.sb_off + idx - sd.n_lc);
-          else if (idx < ie_base + sd.n_le) code = (2u << kBentKindShift) | (uint32_t)(sd.le_off + idx - ie_base);
-          else if (idx < ie_base + blk) code = (4u << kBentKindShift) | (uint32_t)(sd.fd_off + idx - ie_base - sd.n_le);
+          else if (idx < cph0) code = (2u << kBentKindShift) | (uint32_t)(sd.le_off + idx - ie_base);
+          else if (idx < fdb0) code = (6u << kBentKindShift) | (uint32_t)(3 * sd.ce_off + idx - cph0);
+          else if (idx < ie_base + blk) code = (4u << kBentKindShift) | (uint32_t)(sd.fd_off + idx - fdb0);
           else if (idx > zero && idx <= zero + sd.n_ci) code = (3u << kBentKindShift) | (uint32_t)(sd.ci_off + idx - zero - 1);
           else if (idx > zero + sd.n_ci && idx <= zero + sd.n_ci + sd.n_fd)
             code = (5u << kBentKindShift) | (uint32_t)(sd.fd_off + idx - zero - 1 - sd.n_ci);
@@ -817,6 +826,21 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
     }
     c->b_ev_ptr.push_back((int64_t)c->b_ev_step.size());
   }
+  // coupled ends: each one's first mode line end; per line end its coupled
+  // end (or -1) and interpolation fraction
+  c->b_le_ce.assign(c->line_ends.size(), -1);
+  c->b_le_f.assign(c->line_ends.size(), 0.0);
+  for (size_t e = 0; e < c->line_ends.size(); ++e) c->b_le_f[e] = c->line_ends[e].f;
+  for (int q = 0; q < nsub; ++q) {
+    const SubDev& sd = c->subs[q];
+    for (int x = 0; x < sd.n_ce; ++x) {
+      const int ge0 = sd.le_off + c->cends[sd.ce_off + x].le0;
+      c->b_ce_le0.push_back(ge0);
+      for (int p = 0; p < 3; ++p) c->b_ce_node.push_back(sd.node_off + c->cends[sd.ce_off + x].node[p]);
+      for (int j = 0; j < 3; ++j) c->b_le_ce[ge0 + j] = sd.ce_off + x;
+    }
+  }
+
   // frequency-dependent ends: each one's global line end, and per line end
   // its FD end (or -1)
   c->b_le_fd.assign(c->line_ends.size(), -1);
@@ -1744,7 +1768,6 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
 
   // -------- multi-scenario set
   if (scen && !c->rswitches.empty()) return bail("runtime switches are not supported with a scenario set");
-  if (scen && !c->cends.empty()) return bail("coupled lines are not supported with a scenario set");
   if (scen) {
     const std::string bm = build_scenarios(c, d, scen, local, new_of_orig, le_of_end, lc_slot_of, sb_slot_of);
     if (!bm.empty()) return bail(bm);
@@ -1833,6 +1856,14 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
       if (e == cudaSuccess && !c->b_cbo.empty()) e = c->upload(&c->d_bcbo, c->b_cbo);
       if (e == cudaSuccess) e = c->alloc_zero(&c->d_bcy, (2 * c->b_cb.size() + 2) * (size_t)c->S);
       if (e == cudaSuccess) e = c->alloc_zero(&c->d_bcs, 2 * c->b_cb.size() * (size_t)c->S);
+    }
+    if (!c->b_ce_le0.empty()) {
+      if (e == cudaSuccess) e = c->upload(&c->d_bce_le0, c->b_ce_le0);
+      if (e == cudaSuccess) e = c->upload(&c->d_bce_node, c->b_ce_node);
+      if (e == cudaSuccess) e = c->upload(&c->d_ble_ce, c->b_le_ce);
+      if (e == cudaSuccess) e = c->upload(&c->d_ble_f, c->b_le_f);
+      if (e == cudaSuccess) e = c->alloc_zero(&c->d_bcim, 3 * c->b_ce_le0.size() * (size_t)c->S);
+      if (e == cudaSuccess) e = c->alloc_zero(&c->d_bcph, 3 * c->b_ce_le0.size() * (size_t)c->S);
     }
     if (!c->b_fd_le.empty()) {
       if (e == cudaSuccess) e = c->upload(&c->d_bfd_le, c->b_fd_le);
@@ -2055,6 +2086,13 @@ static cudaError_t batch_launch(emt_ctx* c, int64_t n0, int64_t n_steps, cudaStr
   b.fd_le = c->d_bfd_le;
   b.le_fd = c->d_ble_fd;
   b.fds = c->d_bfds;
+  b.ce = c->d_ce;
+  b.ce_le0 = c->d_bce_le0;
+  b.ce_node = c->d_bce_node;
+  b.le_ce = c->d_ble_ce;
+  b.le_f = c->d_ble_f;
+  b.cim = c->d_bcim;
+  b.cph = c->d_bcph;
   b.rec = record ? c->d_rec : nullptr;
   b.rec_pos = c->d_rec_pos;
   b.rec_rows = c->rec_rows;
@@ -2359,6 +2397,8 @@ extern "C" emt_status emt_reset(emt_ctx* c) {
     if (e == cudaSuccess && c->d_bcs) e = cudaMemset(c->d_bcs, 0, 2 * c->b_cb.size() * (size_t)c->S * sizeof(double));
     if (e == cudaSuccess && c->d_bfds)
       e = cudaMemset(c->d_bfds, 0, c->b_fd_le.size() * kBatchFdState * (size_t)c->S * sizeof(double));
+    if (e == cudaSuccess && c->d_bcim) e = cudaMemset(c->d_bcim, 0, 3 * c->b_ce_le0.size() * (size_t)c->S * sizeof(double));
+    if (e == cudaSuccess && c->d_bcph) e = cudaMemset(c->d_bcph, 0, 3 * c->b_ce_le0.size() * (size_t)c->S * sizeof(double));
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return c->cuda_fail(e, "emt_reset");

@@ -44,7 +44,9 @@ __device__ __forceinline__ double entry_value(const BatchParams& P, uint32_t raw
   const uint32_t kind = (raw >> kBentKindShift) & 7u;
   const int idx = (int)(raw & kBentIndexMask);
   double val;
-  if (kind >= 4u) {   // a frequency-dependent end's b (4) or Hy (5) of this step
+  if (kind == 6u) {   // a coupled end's phase history current of this step
+    val = P.cph[(int64_t)idx * P.S + sg];
+  } else if (kind >= 4u) {   // a frequency-dependent end's b (4) or Hy (5) of this step
     val = P.fds[((int64_t)idx * kBatchFdState + (kind == 4u ? 11 : 10)) * P.S + sg];
   } else if (kind == 3u) {   // a controlled current: its block's output of the previous step
     val = P.cy[(int64_t)(2 * __ldg(P.cinj + idx) + (int)((step - 1) & 1)) * P.S + sg];
@@ -181,6 +183,40 @@ __device__ __forceinline__ void batch_fd_update(const BatchParams& P, int ge, in
   st[10 * S] = fma(r.mu_sum, v, lam_s);
 }
 
+// Coupled end x at the start of step n (scenario sg): mode j's history
+// I_j(n) = (1 - f_j) c_j(n - d_j) + f_j c_j(n - d_j - 1) from the far end's
+// values in its ring, then the phase history currents T_i I.
+__device__ __forceinline__ void batch_ce_fold(const BatchParams& P, int x, int sg, long long step) {
+  const CoupledEndDev& r = P.ce[x];
+  const int64_t S = P.S;
+  const int ge0 = __ldg(P.ce_le0 + x);
+  double im[3];
+  for (int j = 0; j < 3; ++j) {
+    const int ge = ge0 + j, d = __ldg(P.le_d1 + ge) - 1;
+    const double f = __ldg(P.le_f + ge);
+    const double c_new = fd_ring_w(P, ge, step - d, sg), c_old = fd_ring_w(P, ge, step - d - 1, sg);
+    im[j] = fma(f, c_old, (1.0 - f) * c_new);
+    P.cim[(int64_t)(3 * x + j) * S + sg] = im[j];
+  }
+  for (int p = 0; p < 3; ++p)
+    P.cph[(int64_t)(3 * x + p) * S + sg] = fma(r.ti[3 * p], im[0], fma(r.ti[3 * p + 1], im[1], r.ti[3 * p + 2] * im[2]));
+}
+
+// A coupled line's mode (line end ge, end x) after the solve of step n:
+// c_j(n) = -(2/Z_j) (T_v^-1 v_p)_j - I_j(n) into the far end's ring.
+__device__ __forceinline__ void batch_ce_update(const BatchParams& P, int ge, int x, int sg, int sl, long long step,
+                                                const double* vv, int node0, int St) {
+  const CoupledEndDev& r = P.ce[x];
+  const int64_t S = P.S;
+  const int j = ge - __ldg(P.ce_le0 + x);
+  double v[3];
+  for (int p = 0; p < 3; ++p) v[p] = vv[(size_t)(__ldg(P.ce_node + 3 * x + p) - node0) * St + sl];
+  const double vm = fma(r.tinv[3 * j], v[0], fma(r.tinv[3 * j + 1], v[1], r.tinv[3 * j + 2] * v[2]));
+  const double out = fma(-__ldg(P.le_y2 + ge), vm, -P.cim[(int64_t)(3 * x + j) * S + sg]);
+  const int depth = __ldg(P.le_d1 + ge) + 1;
+  P.ring[(__ldg(P.le_bfar + ge) + (int64_t)((unsigned long long)step % (unsigned)depth)) * S + sg] = out;
+}
+
 __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int St = P.S_t;
@@ -252,15 +288,17 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
       // frequency-dependent ends: W(n) interpolated from the far end's w of
       // steps n - d and n - d - 1 (its ring, depth d + 2), A's pole terms
       // z_i(n) = lam z_i(n-1) + mu (W(n) + W(n-1)) and b(n) = a0 W + sum z_i
-      if (G.fd1 > G.fd0) {
-        const int n_fdg = G.fd1 - G.fd0;
-        for (int x = tid, j = q0, sl = r0; x < n_fdg * St; x += T, j += dq, sl += dr) {
+      // (and coupled ends: each mode's interpolated history, then T_i I_mode)
+      if (G.fd1 > G.fd0 || G.ce1 > G.ce0) {
+        const int n_fdg = G.fd1 - G.fd0, n_fold = n_fdg + (G.ce1 - G.ce0);
+        for (int x = tid, j = q0, sl = r0; x < n_fold * St; x += T, j += dq, sl += dr) {
           if (sl >= St) {
             sl -= St;
             ++j;
           }
           if (sl >= n_here) continue;
-          batch_fd_fold(P, G.fd0 + j, sigma0 + sl, step);
+          if (j < n_fdg) batch_fd_fold(P, G.fd0 + j, sigma0 + sl, step);
+          else batch_ce_fold(P, G.ce0 + j - n_fdg, sigma0 + sl, step);
         }
         __syncthreads();
       }
@@ -410,6 +448,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
         } else if (P.le_fd != nullptr && __ldg(P.le_fd + G.le0 + (it - n_lc)) >= 0) {
           const int ge = G.le0 + (it - n_lc);
           batch_fd_update(P, ge, __ldg(P.le_fd + ge), sg, step, vv[(size_t)(__ldg(P.le_nd + ge) - G.node0) * St + sl]);
+        } else if (P.le_ce != nullptr && __ldg(P.le_ce + G.le0 + (it - n_lc)) >= 0) {
+          const int ge = G.le0 + (it - n_lc);
+          batch_ce_update(P, ge, __ldg(P.le_ce + ge), sg, sl, step, vv, G.node0, St);
         } else {
           const int ge = G.le0 + (it - n_lc);
           const int d1 = __ldg(P.le_d1 + ge);

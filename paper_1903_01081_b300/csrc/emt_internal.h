@@ -304,7 +304,8 @@ struct PrefParams {
 // k - n.  Batched injection entries name global slots: bits 28-30 the
 // kind (0 L/C slot, 1 source-branch slot, 2 line end, 3 control injection:
 // its block's output of the previous step, 4 / 5 a frequency-dependent
-// end's b / Hy of the step), bits 0-27 the index, bit 31 subtract.
+// end's b / Hy of the step, 6 a coupled end's phase history current of the
+// step), bits 0-27 the index, bit 31 subtract.
 constexpr uint32_t kBentKindShift = 28;
 constexpr uint32_t kBentIndexMask = (1u << 28) - 1;
 // Per-scenario state of a frequency-dependent end in the multi-scenario
@@ -320,6 +321,7 @@ struct BatchGroupDev {
   int32_t nl0, nl1;            // nonlinear resistors of its subsystems
   int32_t nlc0, nlc1;          // their (node, element) correction pairs in BatchParams::nlc
   int32_t fd0, fd1;            // frequency-dependent line ends of its subsystems
+  int32_t ce0, ce1;            // coupled line ends of its subsystems
 };
 
 struct BatchParams {
@@ -384,6 +386,17 @@ struct BatchParams {
   const int32_t* fd_le;
   const int32_t* le_fd;
   double* fds;
+  // coupled line ends: records (T_v^-1, T_i, modal Z), each one's first
+  // mode line end, per line end its coupled end or -1 and its interpolation
+  // fraction f; modal histories [3 x + j][S] and phase currents [3 x + p][S]
+  // of the step; a mode's ring (depth d + 2) holds c by the step it was sent
+  const CoupledEndDev* ce;
+  const int32_t* ce_le0;
+  const int32_t* ce_node;      // [3 x + p]: phase nodes as internal nodes
+  const int32_t* le_ce;
+  const double* le_f;
+  double* cim;
+  double* cph;
   double* rec;                 // [rows][S][n_rec]
   const int32_t* rec_pos;
   int64_t rec_rows;

@@ -110,15 +110,11 @@ def test_rejects_bad_coupled_lines():
     assert "unknown nodes" in bad(net, cl_k=k)
 
 
-def test_rejects_scenario_set_with_runtime_switches_or_coupled_lines():
+def test_rejects_scenario_set_with_runtime_switches():
     net, sc = g.n1_contingency(n_scenarios=4, n_buses=24, n_sub=4, n_steps=10)
     rs = g.with_rectifier_loads(net, n_rectifiers=2, n_breakers=0)
     with pytest.raises(emt.EmtError, match="runtime switches are not supported"):
         emt.emt_build_network(rs, sc)
-    cl = g.with_coupled_lines(net)
-    assert cl.n_coupled_lines > 0
-    with pytest.raises(emt.EmtError, match="coupled lines are not supported"):
-        emt.emt_build_network(cl, sc)
 
 
 def test_rejects_bad_controls():

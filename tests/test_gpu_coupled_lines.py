@@ -72,19 +72,41 @@ def test_large_network_with_coupled_lines():
     assert rel(gpu_run(net, N), oracle.simulate(net, N)) <= TOL
 
 
-def test_coupled_lines_rejected_where_unsupported():
+def test_coupled_lines_count_and_invalid_travel_time():
     base = g.multi_subsystem(161, [3, 4, 2], n_lines=3, n_sources=2, dt=20e-6)
     net = g.with_coupled_lines(base, seed=3)
     ctx = emt.emt_build_network(net)
     emt.emt_prefactor(ctx)
     assert emt.emt_get_info(ctx, "n_coupled_lines") == 3   # three three-phase lines
     emt.emt_destroy(ctx)
-    with pytest.raises(emt.EmtError) as ei:
-        emt.emt_build_network(net, g.Scenarios(n_scenarios=2))
-    assert ei.value.status == emt.EMT_EINVAL
     bad = net.copy()
     bad.cl_tau = bad.cl_tau.copy()
     bad.cl_tau[0] = 0.5 * net.dt
     with pytest.raises(emt.EmtError) as ei:
         emt.emt_build_network(bad)
     assert ei.value.status == emt.EMT_EINVAL
+
+
+def test_scenario_set_with_coupled_lines():
+    """A study on the 600-node network with its three-phase lines as coupled
+    modal lines with interpolated travel times (per scenario the source
+    amplitudes and angles and a fault resistance): sampled scenarios against
+    the oracle; two launches equal one bit for bit."""
+    N = 3000
+    base, _ = g.n1_contingency(n_scenarios=1, n_steps=N)
+    net, sc = g.shared_g(n_scenarios=24, n_steps=N, fault_step=1500, base=g.with_coupled_lines(base))
+    assert net.n_coupled_lines > 0 and net.n_lines == 0
+    sim = emt.Simulator(net, sc, n_steps=N)
+    sim.run(N)
+    sim.sync()
+    w = sim.waveforms()
+    sim.close()
+    for s in (0, 11, 23):
+        ref = oracle.simulate(sc.expand(net, s), N)
+        assert np.max(np.abs(w[:, s, :] - ref)) <= 1e-10 * np.max(np.abs(ref))
+    two = emt.Simulator(net, sc, n_steps=N)
+    two.run(1234)
+    two.run(N - 1234)
+    two.sync()
+    assert np.array_equal(two.waveforms(), w)
+    two.close()
