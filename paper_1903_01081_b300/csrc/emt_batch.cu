@@ -44,12 +44,13 @@ __device__ __forceinline__ double entry_value(const BatchParams& P, uint32_t raw
   const uint32_t kind = (raw >> kBentKindShift) & 7u;
   const int idx = (int)(raw & kBentIndexMask);
   double val;
-  if (kind == 6u) {   // a coupled end's phase history current of this step
-    val = P.cph[(int64_t)idx * P.S + sg];
-  } else if (kind >= 4u) {   // a frequency-dependent end's b (4) or Hy (5) of this step
-    val = P.fds[((int64_t)idx * kBatchFdState + (kind == 4u ? 11 : 10)) * P.S + sg];
-  } else if (kind == 3u) {   // a controlled current: its block's output of the previous step
-    val = P.cy[(int64_t)(2 * __ldg(P.cinj + idx) + (int)((step - 1) & 1)) * P.S + sg];
+  if (kind > 2u) {   // the rarer kinds
+    if (kind == 3u)   // a controlled current: its block's output of the previous step
+      val = P.cy[(int64_t)(2 * __ldg(P.cinj + idx) + (int)((step - 1) & 1)) * P.S + sg];
+    else if (kind == 6u)   // a coupled end's phase history current of this step
+      val = P.cph[(int64_t)idx * P.S + sg];
+    else   // a frequency-dependent end's b (4) or Hy (5) of this step
+      val = P.fds[((int64_t)idx * kBatchFdState + (kind == 4u ? 11 : 10)) * P.S + sg];
   } else if (kind == 0u) {
     val = P.h[(int64_t)idx * P.S + sg];
   } else if (kind == 1u) {
