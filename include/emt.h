@@ -67,7 +67,8 @@ typedef struct emt_ctx emt_ctx;  /* opaque; owns all device memory it allocates 
  *   The paper's process 3 at run time (Sec. III-A): each subsystem with k
  *   runtime switches gets a prefactored G^-1 for every one of its 2^k
  *   states (k <= 8 per subsystem), and the time loop switches matrices
- *   when a state changes.  Not supported with a scenario set; emt_adjoint
+ *   when a state changes (with a scenario set: per scenario, every
+ *   scenario matrix variant having its 2^k states); emt_adjoint
  *   differentiates with the decisions the forward run took held fixed.
  * Coupled three-phase lossless lines in modal form (n_clines may be 0):
  *   cl_k[3 l + p] / cl_m[3 l + p]: phase p's node (unknown) at each end;
@@ -214,9 +215,8 @@ typedef struct {
  *     parameter p0 a scenario sets (block index, finite value; a block at
  *     most once per scenario; for a LIMIT the new lower bound must not
  *     exceed p1), e.g. a set point per scenario.  NULL: none.
- * Scenario sets take control blocks, nonlinear resistors, coupled and
- * frequency-dependent lines (rm_line names lossless lines only); they do
- * not take runtime switches. */
+ * Scenario sets take every element kind (rm_line names lossless lines
+ * only); each scenario keeps its own runtime-switch states. */
 typedef struct {
   int64_t n_scenarios;
   const double* src_amp;

@@ -63,6 +63,7 @@ struct emt_ctx {
   std::vector<int32_t> nb_sub, nb_dmin;
   std::vector<SwitchDev> switches;
   std::vector<RuntimeSwitchDev> rswitches;             // runtime switches, grouped by subsystem
+  std::vector<double> rs_roff;                         // their off resistances
   std::vector<CoupledEndDev> cends;                    // coupled line ends, grouped by subsystem
   std::vector<int32_t> rs_word0;                       // per subsystem: state word at step 1
   std::vector<FdEndDev> fdends;                        // frequency-dependent line ends, grouped by subsystem
@@ -201,6 +202,11 @@ struct emt_ctx {
   std::vector<int32_t> b_fd_le, b_le_fd;
   int32_t *d_bfd_le = nullptr, *d_ble_fd = nullptr;
   double* d_bfds = nullptr;
+  // runtime switches of the multi-scenario kernel (see BatchParams)
+  std::vector<int32_t> b_sub_rs;
+  int32_t *d_bsub_rs = nullptr, *d_bword = nullptr;
+  double* d_brsi = nullptr;
+  long long* d_bvbase = nullptr;
   // coupled ends of the multi-scenario kernel (see BatchParams)
   std::vector<int32_t> b_ce_le0, b_le_ce, b_ce_node;
   std::vector<double> b_le_f;
@@ -494,6 +500,14 @@ std::string validate_scenarios(const emt_network_desc* d, const emt_scenario_des
 // fit in the multi-scenario kernel's shared memory for S_t scenarios per
 // CTA; upload the groups when `upload`.  False if one subsystem alone does
 // not fit.
+// Every scenario's runtime-switch state words back to the initial ones.
+cudaError_t reset_batch_words(emt_ctx* c) {
+  std::vector<int32_t> w((size_t)c->n_sub * c->S);
+  for (int s = 0; s < c->n_sub; ++s)
+    std::fill(w.begin() + (size_t)s * c->S, w.begin() + (size_t)(s + 1) * c->S, c->rs_word0[s]);
+  return cudaMemcpy(c->d_bword, w.data(), w.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+}
+
 bool batch_configure(emt_ctx* c, int S_t, bool upload) {
   const size_t fixed = batch_smem_bytes(S_t, (int)c->n_sources, c->n_sub, 0, 0);
   if (fixed >= 227 * 1024) return false;
@@ -537,6 +551,8 @@ bool batch_configure(emt_ctx* c, int S_t, bool upload) {
     G.fd1 = b.fd_off + b.n_fd;
     G.ce0 = a.ce_off;
     G.ce1 = b.ce_off + b.n_ce;
+    G.sub0 = s0;
+    G.sub1 = s1;
     G.nlc0 = G.nlc1 = 0;
     for (int s = 0, pos = 0; s < s1; ++s) {
       const SubDev& sd = c->subs[s];
@@ -689,32 +705,43 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
         auto it = variants.find(key);
         int vid;
         if (it == variants.end()) {
-          vid = (int)variants.size();
+          // one matrix per runtime-switch state word, consecutive (stride n (n + n_str) [+ n])
+          vid = (int)((int64_t)c->epochs.size() - c->n_base_epochs);
           variants.emplace(key, vid);
-          EpochDev E{};
-          E.start = 0;
-          E.ginv_off = goff;
-          goff += (int64_t)sd.n * (sd.n + sd.n_str);
-          E.nlz_off = -1;
-          if (sd.n_nl > 0) {   // its nonlinear resistor's column z right after the matrix (and its remainder)
-            E.nlz_off = goff;
-            goff += sd.n;
+          for (int word = 0; word < sd.n_states; ++word) {
+            EpochDev E{};
+            E.start = 0;
+            E.ginv_off = goff;
+            goff += (int64_t)sd.n * (sd.n + sd.n_str);
+            E.nlz_off = -1;
+            if (sd.n_nl > 0) {   // its nonlinear resistor's column z right after the matrix (and its remainder)
+              E.nlz_off = goff;
+              goff += sd.n;
+            }
+            E.sw_off = (int)c->switches.size();
+            for (auto& cl : closed) {
+              SwitchDev sw{};
+              sw.k = (int32_t)cl[0];
+              sw.m = (int32_t)cl[1];
+              std::memcpy(&sw.g, &cl[2], sizeof(sw.g));
+              c->switches.push_back(sw);
+            }
+            for (int j = 0; j < sd.n_rs; ++j) {   // runtime switches: r_on or r_off by the state word
+              const RuntimeSwitchDev& r = c->rswitches[sd.rs_off + j];
+              SwitchDev sw{};
+              sw.k = r.k;
+              sw.m = r.m;
+              sw.g = 1.0 / (((word >> j) & 1) ? r.r_on : c->rs_roff[sd.rs_off + j]);
+              c->switches.push_back(sw);
+            }
+            E.n_sw = (int)c->switches.size() - E.sw_off;
+            c->epochs.push_back(E);
+            c->var_sub.push_back(k);
+            c->rm_br.insert(c->rm_br.end(), rb[k].begin(), rb[k].end());
+            c->rm_ptr_br.push_back((int32_t)c->rm_br.size());
+            c->rm_le.insert(c->rm_le.end(), rl[k].begin(), rl[k].end());
+            c->rm_ptr_le.push_back((int32_t)c->rm_le.size());
           }
-          E.sw_off = (int)c->switches.size();
-          for (auto& cl : closed) {
-            SwitchDev sw{};
-            sw.k = (int32_t)cl[0];
-            sw.m = (int32_t)cl[1];
-            std::memcpy(&sw.g, &cl[2], sizeof(sw.g));
-            c->switches.push_back(sw);
-          }
-          E.n_sw = (int)closed.size();
-          c->epochs.push_back(E);
-          c->var_sub.push_back(k);
-          c->rm_br.insert(c->rm_br.end(), rb[k].begin(), rb[k].end());
-          c->rm_ptr_br.push_back((int32_t)c->rm_br.size());
-          c->rm_le.insert(c->rm_le.end(), rl[k].begin(), rl[k].end());
-          c->rm_ptr_le.push_back((int32_t)c->rm_le.size());
         } else {
           vid = it->second;
         }
@@ -826,6 +853,14 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
     }
     c->b_ev_ptr.push_back((int64_t)c->b_ev_step.size());
   }
+  // runtime switches: per subsystem (first switch, count, matrix stride,
+  // first internal node); states are per scenario
+  for (int q = 0; q < nsub; ++q) {
+    const SubDev& sd = c->subs[q];
+    const int64_t stride = (int64_t)sd.n * (sd.n + sd.n_str) + (sd.n_nl > 0 ? sd.n : 0);
+    c->b_sub_rs.insert(c->b_sub_rs.end(), {sd.rs_off, sd.n_rs, (int32_t)stride, sd.node_off});
+  }
+
   // coupled ends: each one's first mode line end; per line end its coupled
   // end (or -1) and interpolation fraction
   c->b_le_ce.assign(c->line_ends.size(), -1);
@@ -1677,6 +1712,7 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
         r.r_on = d->rs_ron[w];
         r.trip = d->rs_trip_step[w];
         c->rswitches.push_back(r);
+        c->rs_roff.push_back(d->rs_roff[w]);
         if (r.kind == 1 || d->rs_on0[w]) word0 |= 1 << j;
       }
       c->rs_word0.push_back(word0);
@@ -1767,7 +1803,6 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   }
 
   // -------- multi-scenario set
-  if (scen && !c->rswitches.empty()) return bail("runtime switches are not supported with a scenario set");
   if (scen) {
     const std::string bm = build_scenarios(c, d, scen, local, new_of_orig, le_of_end, lc_slot_of, sb_slot_of);
     if (!bm.empty()) return bail(bm);
@@ -1856,6 +1891,13 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
       if (e == cudaSuccess && !c->b_cbo.empty()) e = c->upload(&c->d_bcbo, c->b_cbo);
       if (e == cudaSuccess) e = c->alloc_zero(&c->d_bcy, (2 * c->b_cb.size() + 2) * (size_t)c->S);
       if (e == cudaSuccess) e = c->alloc_zero(&c->d_bcs, 2 * c->b_cb.size() * (size_t)c->S);
+    }
+    if (!c->rswitches.empty()) {
+      if (e == cudaSuccess) e = c->upload(&c->d_bsub_rs, c->b_sub_rs);
+      if (e == cudaSuccess) e = c->alloc_zero(&c->d_bword, (size_t)c->n_sub * c->S);
+      if (e == cudaSuccess) e = c->alloc_zero(&c->d_brsi, c->rswitches.size() * (size_t)c->S);
+      if (e == cudaSuccess) e = c->alloc_zero(&c->d_bvbase, (size_t)c->n_sub * c->S);
+      if (e == cudaSuccess) e = reset_batch_words(c);
     }
     if (!c->b_ce_le0.empty()) {
       if (e == cudaSuccess) e = c->upload(&c->d_bce_le0, c->b_ce_le0);
@@ -2086,6 +2128,11 @@ static cudaError_t batch_launch(emt_ctx* c, int64_t n0, int64_t n_steps, cudaStr
   b.fd_le = c->d_bfd_le;
   b.le_fd = c->d_ble_fd;
   b.fds = c->d_bfds;
+  b.rs = c->d_rs;
+  b.sub_rs = c->d_bsub_rs;
+  b.rs_word = c->d_bword;
+  b.rs_prev_i = c->d_brsi;
+  b.vbase = c->d_bvbase;
   b.ce = c->d_ce;
   b.ce_le0 = c->d_bce_le0;
   b.ce_node = c->d_bce_node;
@@ -2398,6 +2445,8 @@ extern "C" emt_status emt_reset(emt_ctx* c) {
     if (e == cudaSuccess && c->d_bfds)
       e = cudaMemset(c->d_bfds, 0, c->b_fd_le.size() * kBatchFdState * (size_t)c->S * sizeof(double));
     if (e == cudaSuccess && c->d_bcim) e = cudaMemset(c->d_bcim, 0, 3 * c->b_ce_le0.size() * (size_t)c->S * sizeof(double));
+    if (e == cudaSuccess && c->d_bword) e = reset_batch_words(c);
+    if (e == cudaSuccess && c->d_brsi) e = cudaMemset(c->d_brsi, 0, c->rswitches.size() * (size_t)c->S * sizeof(double));
     if (e == cudaSuccess && c->d_bcph) e = cudaMemset(c->d_bcph, 0, 3 * c->b_ce_le0.size() * (size_t)c->S * sizeof(double));
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();

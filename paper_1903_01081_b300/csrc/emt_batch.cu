@@ -218,6 +218,53 @@ __device__ __forceinline__ void batch_ce_update(const BatchParams& P, int ge, in
   P.ring[(__ldg(P.le_bfar + ge) + (int64_t)((unsigned long long)step % (unsigned)depth)) * S + sg] = out;
 }
 
+// Scenario sg selects variant base `base` for subsystem s: its matrix is
+// the one of the scenario's current runtime-switch state word.
+__device__ __forceinline__ void select_matrix(const BatchParams& P, long long* cur, int sl, int sg, int s,
+                                              long long base) {
+  long long off = base;
+  if (P.vbase != nullptr) {
+    P.vbase[(int64_t)sg * P.n_sub + s] = base;
+    off += (long long)P.rs_word[(int64_t)s * P.S + sg] * __ldg(P.sub_rs + 4 * s + 2);
+  }
+  cur[(size_t)sl * P.n_sub + s] = off;
+}
+
+// Subsystem s, scenario sg, after the solve of step n: the state in force
+// at step n+1 of each runtime switch (a diode conducts iff v_k - v_m > 0; a
+// breaker, once past its trip step, opens for good at a sign change of its
+// current), and the matrix of the new state word.
+__device__ __forceinline__ void batch_rs_decide(const BatchParams& P, long long* cur, int s, int sl, int sg,
+                                                long long step, const double* vv, int node0, int St) {
+  const int n_rs = __ldg(P.sub_rs + 4 * s + 1);
+  if (n_rs == 0) return;
+  const int rs0 = __ldg(P.sub_rs + 4 * s), node_off = __ldg(P.sub_rs + 4 * s + 3);
+  const int64_t S = P.S;
+  int* wp = P.rs_word + (int64_t)s * S + sg;
+  const int word = *wp;
+  int nw = 0;
+  for (int j = 0; j < n_rs; ++j) {
+    const RuntimeSwitchDev& r = P.rs[rs0 + j];
+    const double vk = r.k >= 0 ? vv[(size_t)(node_off + r.k - node0) * St + sl] : 0.0;
+    const double vm = r.m >= 0 ? vv[(size_t)(node_off + r.m - node0) * St + sl] : 0.0;
+    const double vb = vk - vm;
+    int bit = (word >> j) & 1;
+    if (r.kind == 0) {
+      bit = vb > 0.0 ? 1 : 0;
+    } else if (bit) {
+      double* ip = P.rs_prev_i + (int64_t)(rs0 + j) * S + sg;
+      const double i = vb / r.r_on;
+      if (step >= r.trip && *ip * i <= 0.0) bit = 0;
+      *ip = i;
+    }
+    nw |= bit << j;
+  }
+  if (nw != word) {
+    *wp = nw;
+    cur[(size_t)sl * P.n_sub + s] = P.vbase[(int64_t)sg * P.n_sub + s] + (long long)nw * __ldg(P.sub_rs + 4 * s + 2);
+  }
+}
+
 __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int St = P.S_t;
@@ -241,7 +288,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
     const int sg = sigma0 + sl;
     int64_t x = P.ev_ptr[sg];
     const int64_t x1 = P.ev_ptr[sg + 1];
-    for (; x < x1 && P.ev_step[x] <= P.n0; ++x) cur[(size_t)sl * n_sub + P.ev_sub[x]] = P.ev_off[x];
+    for (; x < x1 && P.ev_step[x] <= P.n0; ++x) select_matrix(P, cur, sl, sg, P.ev_sub[x], P.ev_off[x]);
     evn[sl] = x;
   }
 
@@ -255,7 +302,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
       int64_t x = evn[sl];
       const int64_t x1 = P.ev_ptr[sg + 1];
       if (x < x1 && P.ev_step[x] <= step) {
-        for (; x < x1 && P.ev_step[x] <= step; ++x) cur[(size_t)sl * n_sub + P.ev_sub[x]] = P.ev_off[x];
+        for (; x < x1 && P.ev_step[x] <= step; ++x) select_matrix(P, cur, sl, sg, P.ev_sub[x], P.ev_off[x]);
         evn[sl] = x;
       }
     }
@@ -410,6 +457,20 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
           }
         }
         __syncthreads();
+      }
+
+      // runtime switches: each subsystem's state word for the next step from
+      // this step's solution (its matrix for that word from then on)
+      if (P.vbase != nullptr) {
+        const int n_sg = G.sub1 - G.sub0;
+        for (int x = tid, j = q0, sl = r0; x < n_sg * St; x += T, j += dq, sl += dr) {
+          if (sl >= St) {
+            sl -= St;
+            ++j;
+          }
+          if (sl >= n_here) continue;
+          batch_rs_decide(P, cur, G.sub0 + j, sl, sigma0 + sl, step, vv, G.node0, St);
+        }
       }
 
       // control blocks of the group's subsystems at this step, layer by

@@ -322,6 +322,7 @@ struct BatchGroupDev {
   int32_t nlc0, nlc1;          // their (node, element) correction pairs in BatchParams::nlc
   int32_t fd0, fd1;            // frequency-dependent line ends of its subsystems
   int32_t ce0, ce1;            // coupled line ends of its subsystems
+  int32_t sub0, sub1;          // its subsystems
 };
 
 struct BatchParams {
@@ -390,6 +391,16 @@ struct BatchParams {
   // mode line end, per line end its coupled end or -1 and its interpolation
   // fraction f; modal histories [3 x + j][S] and phase currents [3 x + p][S]
   // of the step; a mode's ring (depth d + 2) holds c by the step it was sent
+  // runtime switches (states per scenario): records, per subsystem (first
+  // switch, count, matrix stride between state words, first internal node),
+  // the state words [n_sub][S], breaker currents of the last step [n_rs][S]
+  // and each scenario's current variant base [S][n_sub] (its matrix for
+  // state word w is at base + w stride)
+  const RuntimeSwitchDev* rs;
+  const int32_t* sub_rs;
+  int32_t* rs_word;
+  double* rs_prev_i;
+  long long* vbase;
   const CoupledEndDev* ce;
   const int32_t* ce_le0;
   const int32_t* ce_node;      // [3 x + p]: phase nodes as internal nodes

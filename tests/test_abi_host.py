@@ -110,13 +110,6 @@ def test_rejects_bad_coupled_lines():
     assert "unknown nodes" in bad(net, cl_k=k)
 
 
-def test_rejects_scenario_set_with_runtime_switches():
-    net, sc = g.n1_contingency(n_scenarios=4, n_buses=24, n_sub=4, n_steps=10)
-    rs = g.with_rectifier_loads(net, n_rectifiers=2, n_breakers=0)
-    with pytest.raises(emt.EmtError, match="runtime switches are not supported"):
-        emt.emt_build_network(rs, sc)
-
-
 def test_rejects_bad_controls():
     net = g.with_converter_controls(g.multi_subsystem(11, [4, 5, 3, 6], n_lines=5, n_sources=3, dt=20e-6),
                                     n_converters=4)

@@ -125,6 +125,30 @@ def test_runtime_switch_limits():
     emt.emt_prefactor(ctx)
     assert emt.emt_get_info(ctx, "n_runtime_switches") == 9
     emt.emt_destroy(ctx)
-    with pytest.raises(emt.EmtError) as ei:
-        emt.emt_build_network(net, g.Scenarios(n_scenarios=2))
-    assert ei.value.status == emt.EMT_EINVAL
+
+
+def test_scenario_set_with_runtime_switches():
+    """An N-1 study of the 600-node network with 10 diode-rectifier loads and
+    4 current-zero breakers: each scenario keeps its own state words and
+    picks the matching prefactored matrices; sampled scenarios against the
+    oracle (each written out as a plain network); the switches change state;
+    two launches equal one bit for bit."""
+    N = 3000
+    base, sc = g.n1_contingency(n_scenarios=32, n_steps=N)
+    net = g.with_rectifier_loads(base, n_rectifiers=10, n_breakers=4)
+    sim = emt.Simulator(net, sc, n_steps=N)
+    sim.run(N)
+    sim.sync()
+    w = sim.waveforms()
+    sim.close()
+    for s in (0, 9, 31):
+        x = sc.expand(net, s)
+        assert rel(w[:, s, :], oracle.simulate(x, N)) <= TOL
+    st = oracle.runtime_switch_states(sc.expand(net, 9), N)
+    assert np.sum(st[1:] != st[:-1]) > 0
+    two = emt.Simulator(net, sc, n_steps=N)
+    two.run(1500)
+    two.run(N - 1500)
+    two.sync()
+    assert np.array_equal(two.waveforms(), w)
+    two.close()
