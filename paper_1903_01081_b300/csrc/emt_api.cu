@@ -75,7 +75,8 @@ struct emt_ctx {
   std::vector<int32_t> cb_sub_of;                      // caller's block index -> subsystem
   int max_clayers = 0;
   int64_t ring_len = 0, ginv_len = 0, n_lc_total = 0;
-  int64_t n_components = 0;   // electrical subsystems (components); n_sub counts CTAs, several components each when packed
+  int64_t n_components = 0;
+  bool forward_narrow = false;   // emt_adjoint: its re-runs share the device with the reverse sweep   // electrical subsystems (components); n_sub counts CTAs, several components each when packed
   int64_t comp_sum_n2 = 0, comp_max_n = 0;   // over the components
   FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0};
 
@@ -2230,7 +2231,7 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
     if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n source table");
     p.n0 = c->step + 1;
     p.n_steps = len;
-    e = launch_forward(p, st);
+    e = launch_forward(p, st, !c->forward_narrow);
     if (e == cudaErrorCooperativeLaunchTooLarge)
       return c->fail(EMT_ERESOURCE, "persistent launch of " + std::to_string(c->n_sub) +
                                         " CTAs cannot be co-resident on this device");
@@ -2623,9 +2624,20 @@ extern "C" void emt_destroy(emt_ctx* c) {
 // v_n directly.  Reverse pass, segments last to first: restore the
 // segment's checkpoint, run it forward again recording the tape, then run
 // the reverse kernel over it.  K = 0 keeps the whole tape (one segment).
+static emt_status adjoint_run(emt_ctx* c, const double* v_target, int64_t n_steps, int32_t ckpt_every,
+                              double* grad, double* loss, int32_t on_device, void* stream);
+
 extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_steps, int32_t ckpt_every,
                                   double* grad, double* loss, int32_t on_device, void* stream) {
   if (!c) return EMT_EINVAL;
+  c->forward_narrow = true;   // the re-runs may share the device with the reverse sweep
+  const emt_status st = adjoint_run(c, v_target, n_steps, ckpt_every, grad, loss, on_device, stream);
+  c->forward_narrow = false;
+  return st;
+}
+
+static emt_status adjoint_run(emt_ctx* c, const double* v_target, int64_t n_steps, int32_t ckpt_every,
+                              double* grad, double* loss, int32_t on_device, void* stream) {
   if (c->batched) return c->fail(EMT_EINVAL, "emt_adjoint: a context built with a scenario set has no adjoint");
   if (!c->cblocks.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: control blocks have no adjoint");
   if (!c->fdends.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: frequency-dependent lines have no adjoint");

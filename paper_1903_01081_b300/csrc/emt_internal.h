@@ -498,7 +498,8 @@ cudaError_t launch_companion(BranchDev* br, int64_t n_br, double dt, cudaStream_
 cudaError_t launch_coupled_constants(CoupledEndDev* ce, int64_t n_ce, cudaStream_t st);
 cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st);
 cudaError_t launch_sources(const SourceParams& p, cudaStream_t st);
-cudaError_t launch_forward(const FwdParams& p, cudaStream_t st);
+// wide = false: the 64-register build only (while another persistent grid shares the device)
+cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide = true);
 size_t forward_smem_bytes(const FwdLimits& lim);
 int forward_blocks_per_sm(const FwdLimits& lim);   // resident CTAs per SM (0 on error)
 cudaError_t launch_batch(const BatchParams& p, int threads, cudaStream_t st, BatchGraph* graph);

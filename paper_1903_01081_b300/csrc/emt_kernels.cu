@@ -621,7 +621,12 @@ __device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int la
   return __all_sync(0xffffffffu, ok);
 }
 
-__global__ void __launch_bounds__(kFwdThreads, 4) fwd_kernel(FwdParams P) {
+// Two builds: at most 64 registers per thread (four CTAs per SM, for
+// networks of many subsystems) and at most 128 (two per SM): the second
+// keeps more of the step loop's state in registers and is used whenever its
+// residency holds every CTA.
+template <int kMinBlocks>
+__global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_abort;
   __shared__ RuntimeSwitchDev s_rs[kMaxRuntimeSwitches];
@@ -1171,27 +1176,33 @@ size_t forward_smem_bytes(const FwdLimits& lim) { return fwd_smem(lim).bytes; }
 int forward_blocks_per_sm(const FwdLimits& lim) {
   const size_t smem = forward_smem_bytes(lim);
   if (smem > 227 * 1024) return 0;
-  if (cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(fwd_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel, kFwdThreads, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<4>, kFwdThreads, smem) != cudaSuccess) return 0;
   return per_sm;
 }
 
-cudaError_t launch_forward(const FwdParams& p, cudaStream_t st) {
+cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide) {
   const size_t smem = forward_smem_bytes(p.lim);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, n_sm = 0, per_sm = 0;
+  int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel, kFwdThreads, smem);
-  if (e != cudaSuccess) return e;
-  if ((long long)per_sm * n_sm < p.n_sub) return cudaErrorCooperativeLaunchTooLarge;
-  FwdParams arg = p;
-  void* args[] = {&arg};
-  // cooperative launch: all CTAs co-resident, so every ring wait can end
-  return cudaLaunchCooperativeKernel((const void*)fwd_kernel, dim3(p.n_sub), dim3(kFwdThreads), args, smem, st);
+  // the 128-register build when allowed and its residency holds every CTA, else the 64-register one
+  const void* fns[2] = {(const void*)fwd_kernel<2>, (const void*)fwd_kernel<4>};
+  for (int v = wide ? 0 : 1; v < 2; ++v) {
+    cudaError_t e = cudaFuncSetAttribute(fns[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[v], kFwdThreads, smem);
+    if (e != cudaSuccess) return e;
+    if ((long long)per_sm * n_sm < p.n_sub) continue;
+    FwdParams arg = p;
+    void* args[] = {&arg};
+    // cooperative launch: all CTAs co-resident, so every ring wait can end
+    return cudaLaunchCooperativeKernel(fns[v], dim3(p.n_sub), dim3(kFwdThreads), args, smem, st);
+  }
+  return cudaErrorCooperativeLaunchTooLarge;
 }
 
 cudaError_t launch_gather(const double* rec, int32_t n_rec, int64_t n_scen_rec, const int32_t* col, int64_t n_ch,
