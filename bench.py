@@ -16,8 +16,9 @@ leaves out the end-to-end leg, the CPU baseline, the parity check and the
 two further legs the metric names, reported as extra keys of the line:
   "scenarios": multi-scenario throughput (scenario-steps/s) of the N-1 study
       (1,024 scenarios of a 600-node network, 10,000 steps, one launch), of
-      the shared-G study (4,096 scenarios of the large-scale network; 3,000
-      of its 10,000 steps timed, across the fault at step 2,500) and of a
+      the shared-G study (4,096 scenarios of the large-scale network, all
+      10,000 steps across the fault at step 2,500, every node recorded
+      every 100th step) and of a
       control study (1,024 scenarios of the 600-node network with 40
       converter loads, set points per scenario, 10,000 steps), of the N-1
       study with 20 surge arresters and of studies of the 600-node network
@@ -330,10 +331,10 @@ def scenario_legs(which=("n1", "shared_g", "controls", "arresters", "fd", "coupl
             out["n1_contingency"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 64, 3000)
     if "shared_g" in which:
         net, sc = g.shared_g()
-        sg = scenario_leg("shared_g", net, sc, steps or 3000, 2, list(range(0, net.n_nodes, 50)), 10, 20, warm,
-                          shape)
+        sg = scenario_leg("shared_g", net, sc, steps or 10000, 2, None, 100, 20, warm, shape)
         out["shared_g"] = dict(workload="large-scale network, per-scenario source amplitude/phase and fault "
-                                        "resistance at step 2,500; 3,000 of 10,000 steps timed", **sg)
+                                        "resistance at step 2,500; all 10,000 steps timed, every node of every "
+                                        "scenario recorded every 100th step", **sg)
         if cpu:
             out["shared_g"]["cpu_baseline"] = oracle_scenario_baseline(net, sc, 64, 1000)
     if "controls" in which:

@@ -85,6 +85,30 @@ def test_n1_full_size_sampled_scenarios():
         assert rel_err(got[s], ref) <= TOL, s
 
 
+def test_shared_g_full_length_sampled_scenarios():
+    """The shared-G study at its stated network and length: the 3,000-node
+    large-scale network, 10,000 steps across the fault at step 2,500, the
+    first 256 of its scenarios (scenario s is the same whatever the count) in
+    one launch of the autotuned shape.  Four seeded scenarios are compared
+    with the oracle on all 3,000 nodes at every 10th step, so a drift over the
+    long recursion shows."""
+    net, sc = g.shared_g(n_scenarios=256)
+    N = net.n_steps
+    assert N == 10000 and net.n_nodes == 3000
+    rng = np.random.default_rng(6)
+    check = sorted({0, 255} | set(rng.choice(np.arange(1, 255), size=2, replace=False).tolist()))
+    sim = emt.Simulator(net, sc, n_steps=N, decim=10)
+    emt.emt_autotune(sim.ctx, 20)
+    sim.run(N)
+    sim.sync()
+    for s in check:
+        got = sim.waveforms(scen0=s, n_scen=1)[:, 0, :]
+        assert got.shape == (N // 10, net.n_nodes)
+        ref = oracle.simulate(sc.expand(net, s), N)[9::10]
+        assert rel_err(got, ref) <= TOL, s
+    sim.close()
+
+
 def run_shape(net, sc, N, shape=None, graph=True, autotune=0):
     ctx = emt.emt_build_network(net, sc)
     emt.emt_prefactor(ctx)
