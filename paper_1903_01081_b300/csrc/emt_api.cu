@@ -17,7 +17,6 @@
 
 #include "../../include/emt.h"
 #include "emt_internal.h"
-#include "emt_digits.cuh"
 
 using namespace emt;
 
@@ -124,9 +123,6 @@ struct emt_ctx {
   double* d_cy = nullptr;
   double* d_ginv = nullptr;
   float* d_ginv_lo = nullptr;
-  uint32_t* d_dig = nullptr;             // the solve matrices in digit form (EpochDev::dig_off)
-  int64_t dig_len = 0;                   // its 32-bit words
-  bool digit_ok = false;                 // every CTA fits the digit form (n <= 64, nc <= 128)
   int32_t* d_err = nullptr;
 
   // recording
@@ -1782,56 +1778,15 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
     c->lim.nc = std::max(c->lim.nc, sd.q * ((nc + sd.q - 1) / sd.q));
   }
 
-  // -------- the solve in digit form on the tensor cores (emt_digits.cuh)
-  // when every CTA's matrix fits it: n <= 64 rows, n + strong <= 128 columns
-  for (EpochDev& E : c->epochs) E.dig_off = -1;
-  c->digit_ok = !scen && S > 0;
-  for (int s = 0; s < S && c->digit_ok; ++s)
-    c->digit_ok = c->subs[s].n <= kDigitMaxRows && c->subs[s].n + c->subs[s].n_str <= kDigitMaxK;
-  if (c->digit_ok) {
-    int64_t off = 0;
-    for (int s = 0; s < S; ++s) {
-      const SubDev& sd = c->subs[s];
-      const int rt = (sd.n + 15) >> 4, ks = (sd.n + sd.n_str + 15) >> 4;
-      c->lim.rt = std::max(c->lim.rt, rt);
-      c->lim.ks = std::max(c->lim.ks, ks);
-      for (int k = 0; k < sd.n_ep; ++k) {
-        c->epochs[sd.ep_off + k].dig_off = off;
-        off += dg_matrix_words(rt, ks);
-      }
-    }
-    c->dig_len = off;
-    c->lim.digit = 1;
-  }
-
   // -------- two solve-matrix buffers per CTA when runtime switches change
-  // matrices at run time and both fit (in either form of the solve)
+  // matrices at run time and both fit
   c->lim.nbuf = 1;
   if (!c->rswitches.empty()) {
     FwdLimits two = c->lim;
     two.nbuf = 2;
     two.n = std::max(two.n, 1);
     two.nc = std::max(two.nc, 1);
-    FwdLimits two_fp64 = two;
-    two_fp64.digit = 0;
-    if (forward_smem_bytes(two) <= 200 * 1024 && forward_smem_bytes(two_fp64) <= 200 * 1024) c->lim.nbuf = 2;
-  }
-  // the digit form needs more shared memory per CTA (16 bytes per matrix
-  // entry against 12): keep it only where it does not cost the co-residency
-  // this network needs
-  if (c->lim.digit) {
-    FwdLimits fd = c->lim;
-    fd.n = std::max(fd.n, 1);
-    fd.nc = std::max(fd.nc, 1);
-    FwdLimits fp = fd;
-    fp.digit = 0;
-    int dev = 0, n_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    const int bd = forward_blocks_per_sm(fd), bp = forward_blocks_per_sm(fp);
-    if (bd == 0 || ((int64_t)bd * n_sm < S && bp > bd)) c->lim.digit = 0;
-    c->digit_ok = c->lim.digit != 0;
-    c->lim.digit = 0;   // measured slower than the FP64 solve on every network tried: opt-in only
+    if (forward_smem_bytes(two) <= 200 * 1024) c->lim.nbuf = 2;
   }
 
   // -------- injection-lane range of every internal node
@@ -1891,7 +1846,6 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ring, 2 * (size_t)std::max<int64_t>(c->ring_len, 1));
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ginv, (size_t)c->ginv_len);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_ginv_lo, (size_t)c->ginv_len);
-  if (e == cudaSuccess && c->digit_ok) e = c->alloc_zero(&c->d_dig, (size_t)c->dig_len);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_err, 4);
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_rs_prev_i, c->rswitches.size());
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_fd_state, kFdState * c->fdends.size());
@@ -2042,7 +1996,6 @@ extern "C" emt_status emt_prefactor(emt_ctx* c) {
     p.rm_le = c->d_rm_le;
   }
   if (e == cudaSuccess) e = launch_prefactor(p, std::max(c->lim.n, 1), nullptr);
-  if (e == cudaSuccess && c->digit_ok) e = launch_digits(p, c->d_dig, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   std::vector<int32_t> status(mat_sub.size(), 0);
   if (e == cudaSuccess && !status.empty())
@@ -2224,7 +2177,6 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
   p.ep = c->d_ep;
   p.ginv = c->d_ginv;
   p.ginv_lo = c->d_ginv_lo;
-  p.dig = c->d_dig;
   p.br = c->d_br;
   p.lc_idx = c->d_lc_idx;
   p.sb_idx = c->d_sb_idx;
@@ -2585,12 +2537,6 @@ extern "C" emt_status emt_set_option(emt_ctx* c, const char* key, int64_t value)
       return c->fail(EMT_EINVAL, "scenarios_per_cta " + std::to_string(value) + " does not fit in shared memory");
     return EMT_OK;
   }
-  if (k == "digit_solve") {   // 0: the forward solve runs in FP64 (X_hi + X_lo) instead of digit form
-    if (value != 0 && !c->digit_ok) return c->fail(EMT_EINVAL, "this network's CTAs do not fit the digit form");
-    cudaDeviceSynchronize();
-    c->lim.digit = value != 0 ? 1 : 0;
-    return EMT_OK;
-  }
   if (k == "adjoint_overlap") {   // 0: the adjoint re-runs segments on the caller's stream only
     c->overlap_adjoint = value != 0;
     return EMT_OK;
@@ -2644,7 +2590,6 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "n_control_injections") *value = (int64_t)c->cinj.size();
   else if (k == "max_control_layers") *value = c->max_clayers;
   else if (k == "smem_bytes") *value = (int64_t)forward_smem_bytes(c->lim);
-  else if (k == "digit_solve") *value = c->lim.digit;
   else if (k == "ctas_per_sm") {   // co-resident persistent CTAs per SM (occupancy of the single-network kernel)
     FwdLimits fl = c->lim;
     fl.n = std::max(fl.n, 1);
@@ -3099,7 +3044,6 @@ extern "C" emt_status emt_prefactor_noalloc(emt_ctx* c, void* stream) {
   p.work_r = work_r;
   p.status = status;
   if (e == cudaSuccess) e = launch_prefactor(p, std::max(c->lim.n, 1), st);
-  if (e == cudaSuccess && c->digit_ok) e = launch_digits(p, c->d_dig, st);
   int32_t* first = status + n_mats;
   if (e == cudaSuccess) e = cudaMemsetAsync(first, 0x7f, sizeof(int32_t), st);
   if (e == cudaSuccess) {

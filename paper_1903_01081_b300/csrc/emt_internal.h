@@ -196,7 +196,6 @@ struct EpochDev {
   int64_t ginv_off;      // offset of this epoch's n x nc solve matrix
   int32_t sw_off, n_sw;  // closed switches (SwitchDev list)
   int64_t nlz_off;       // offset of its nonlinear resistor's column z (n doubles), or -1
-  int64_t dig_off;       // 32-bit word offset of the same matrix in digit form (emt_digits.cuh), or -1
 };
 
 // Per-launch upper bounds that size the forward kernel's shared memory.
@@ -207,8 +206,6 @@ struct FwdLimits {
   int32_t cb, clay, ci;        // control blocks, layers + 1 and injections per subsystem
   int32_t fd;                  // frequency-dependent line ends per subsystem
   int32_t nl;                  // 1 if some subsystem has a nonlinear resistor
-  int32_t digit;               // 1: the solve runs in digit form on the tensor cores (every CTA n <= 64, nc <= 128)
-  int32_t rt, ks;              // digit form: row tiles (16 rows) and column steps (16 columns) of the largest CTA
 };
 
 struct FwdParams {
@@ -218,7 +215,6 @@ struct FwdParams {
   const EpochDev* ep;
   const double* ginv;          // G^-1 rounded to double, per epoch
   const float* ginv_lo;        // G^-1 minus that rounding, in single precision
-  const uint32_t* dig;         // the solve matrices in digit form (lim.digit), at EpochDev::dig_off
   const BranchDev* br;
   const int32_t* lc_idx;       // branch index per L/C slot
   const int32_t* sb_idx;       // branch index per source-branch slot
@@ -501,8 +497,6 @@ cudaError_t launch_ring_init(const RingInitParams& p, cudaStream_t st);
 cudaError_t launch_companion(BranchDev* br, int64_t n_br, double dt, cudaStream_t st);
 cudaError_t launch_coupled_constants(CoupledEndDev* ce, int64_t n_ce, cudaStream_t st);
 cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st);
-// after launch_prefactor: the matrices of p (X_hi + X_lo) in digit form at EpochDev::dig_off of dig
-cudaError_t launch_digits(const PrefParams& p, uint32_t* dig, cudaStream_t st);
 cudaError_t launch_sources(const SourceParams& p, cudaStream_t st);
 // wide = false: the 64-register build only (while another persistent grid shares the device)
 cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide = true);

@@ -32,7 +32,6 @@
 
 #include "emt_internal.h"
 #include "emt_device.cuh"
-#include "emt_digits.cuh"
 
 namespace emt {
 
@@ -285,48 +284,6 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
   if (tid == 0) P.status[mi] = 0;
 }
 
-// ------------------------------------------------------------ digit form
-
-// One CTA per matrix: X = X_hi + X_lo of each row as 62-bit fixed point
-// against the row's own scale, split into balanced base-256 digits, written
-// as bf16 in the A-fragment order of mma.m16n8k16 (row tile R, digit a,
-// column step s; lane l = 4 g + t holds rows g and g + 8 of the tile and
-// columns 2t, 2t + 1 and 2t + 8, 2t + 9 of the step), then the row exponents.
-// Entries outside n x nc are never written and stay zero.
-__global__ void __launch_bounds__(256) digits_kernel(PrefParams P, uint32_t* dig) {
-  __shared__ unsigned s_em[kDigitMaxRows];
-  const int mi = blockIdx.x;
-  const SubDev S = P.sub[P.mat_sub[mi]];
-  const EpochDev E = P.ep[P.mat_ep[mi]];
-  if (E.dig_off < 0) return;
-  const int n = S.n, nc = n + S.n_str, rt = (n + 15) >> 4, ks = (nc + 15) >> 4, T = blockDim.x, tid = threadIdx.x;
-  const double* xh = P.ginv + E.ginv_off;
-  const float* xl = P.ginv_lo + E.ginv_off;
-  uint32_t* out = dig + E.dig_off;
-  int* ex = reinterpret_cast<int*>(out + dg_frag_words(rt, ks));
-  for (int r = tid; r < 16 * rt; r += T) {
-    unsigned em = 1;
-    for (int k = 0; r < n && k < nc; ++k)
-      em = max(em, max(dg_expo(xh[r * nc + k]), dg_expo((double)xl[r * nc + k])));
-    s_em[r] = em;
-    ex[r] = (int)em;
-  }
-  __syncthreads();
-  unsigned short* o16 = reinterpret_cast<unsigned short*>(out);
-  for (int idx = tid; idx < n * nc; idx += T) {
-    const int r = idx / nc, k = idx - r * nc;
-    const unsigned em = s_em[r];
-    const long long np = dg_fixed(xh[idx], em) + dg_fixed((double)xl[idx], em) + kDigitBias;
-    const int R = r >> 4, g = r & 7, rh = (r >> 3) & 1;
-    const int st = k >> 4, kk = k & 15, t = (kk & 7) >> 1, ch = kk >> 3, el = kk & 1;
-    const long long w0 = (long long)(4 * g + t) * 4 + rh + 2 * ch;
-    for (int a = 0; a < kDigits; ++a) {
-      const long long word = ((long long)(R * kDigits + a) * ks + st) * 128 + w0;
-      o16[2 * word + el] = (unsigned short)dg_digit_bf16(np, a);
-    }
-  }
-}
-
 // ------------------------------------------------------------ sources
 
 __global__ void source_kernel(SourceParams P) {
@@ -397,19 +354,12 @@ struct NlState {
 // together fall in different banks.
 struct FwdSmem {
   size_t gi, part, iv, vv, inp, vs, lce, sbg, ley2, leown, lefar, lef, imode, ceti, cetinv, cbr, cy, cs, fdr,
-      fdst, nls, dga, dxch;                                                                // 8-byte (dga: 16)
+      fdst, nls;                                                                           // 8-byte
   size_t gilo, ivf, partf;                                                                 // float
   size_t lck, lcm, lckind, lcstr, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, recp,
-      lece, lemode, cele0, cenode, clay, cinj, lefd, cecnt, dtab;                          // int
+      lece, lemode, cele0, cenode, clay, cinj, lefd, cecnt;                                // int
   size_t bytes;
 };
-
-// Digit form in shared memory: a solve-matrix buffer holds the fragments and
-// row exponents of the largest CTA's matrix; each solve warp has its own
-// table of the injection vector's digits, 8 rows of 16 ks + 8 halfwords
-// (the padding makes the fragment loads conflict-free).
-__host__ __device__ inline size_t dg_buf_words(const FwdLimits& L) { return (size_t)dg_matrix_words(L.rt, L.ks); }
-__host__ __device__ inline int dg_tab_words(int ks) { return kDigits * (8 * ks + 4); }
 
 __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   FwdSmem s{};
@@ -417,17 +367,13 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   auto d = [&](size_t count) { size_t r = o; o += count * 8; return r; };
   auto w = [&](size_t count) { size_t r = o; o += count * 4; return r; };
   auto d16 = [&](size_t count) { o = (o + 15) & ~(size_t)15; return d(count); };
-  const bool dig = L.digit != 0;
   const size_t ldg = (size_t)(L.nc | 1);
   const size_t nbuf = L.nbuf > 1 ? 2 : 1;
-  const size_t mat = dig ? 0 : nbuf * (size_t)L.n * ldg;   // FP64 form: X_hi (and X_lo below)
-  s.gi = d(mat);
+  s.gi = d(nbuf * (size_t)L.n * ldg);
   const size_t nq = (size_t)L.n * L.q;
-  const size_t n_tasks = dig ? 0 : (nq < (size_t)kFwdThreads ? nq : (size_t)kFwdThreads);   // a CTA's n q <= its threads
+  const size_t n_tasks = nq < (size_t)kFwdThreads ? nq : (size_t)kFwdThreads;   // a CTA's n q <= its threads
   s.part = d(n_tasks);
-  s.iv = d16(dig ? ((size_t)L.nc > 16 * (size_t)L.ks ? (size_t)L.nc : 16 * (size_t)L.ks) : (size_t)L.nc);
-  s.dga = d16(dig ? (nbuf * dg_buf_words(L) + 1) / 2 : 0);
-  s.dxch = d(dig ? 4 * 16 * 2 : 0);
+  s.iv = d(L.nc);
   s.vv = d(L.n);
   s.inp = d((size_t)L.lc + L.sb + 2 * ((size_t)L.le + 3 * (size_t)L.ce + L.fd) + 1 + (size_t)L.ci + L.fd);
   s.vs = d(2 * (size_t)L.src);
@@ -446,10 +392,9 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.nls = d(L.nl ? sizeof(NlState) / 8 + (size_t)L.n + ((size_t)L.n + 1) / 2 : 0);
   s.fdr = d(sizeof(FdEndDev) / 8 * (size_t)L.fd);
   s.fdst = d(kFdState * (size_t)L.fd);
-  s.gilo = w(mat);
-  s.ivf = w(dig ? 0 : L.nc);
+  s.gilo = w(nbuf * (size_t)L.n * ldg);
+  s.ivf = w(L.nc);
   s.partf = w(n_tasks);
-  s.dtab = w(dig ? (size_t)(kFwdThreads / 32) * dg_tab_words(L.ks) : 0);
   s.lcstr = w(L.lc);
   s.lck = w(L.lc);
   s.lcm = w(L.lc);
@@ -676,112 +621,6 @@ __device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int la
   return __all_sync(0xffffffffu, ok);
 }
 
-// v = X i in digit form (emt_digits.cuh) on the bf16 tensor cores, for a
-// CTA of n <= 64 rows and nc <= 128 solve columns: warp 2R + h takes row
-// tile R and digits a = 4h .. 4h + 3 of X against all eight digits of i.
-// Each warp scales and splits i itself (its own digit table, no CTA barrier),
-// runs 4 ks mma.m16n8k16, turns its fp32 accumulators (exact integers) into
-// the two 64-bit halves of its part of T, sums them over the quad, and the
-// h = 1 warp hands its rows to the h = 0 warp (named barrier 1 + R); that
-// warp rounds T to double, writes v and the record.  Warps past 2 rt idle.
-__device__ __forceinline__ void mma_16816_bf16(float* d, const uint4& a, unsigned b0, unsigned b1) {
-  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ long long dg_shl(int x, int sh) {
-  return (long long)((unsigned long long)(long long)x << sh);
-}
-
-__device__ __forceinline__ void digit_solve(int n, int nc, int ks_max, const double* iv, const uint32_t* dm,
-                                            unsigned* dtab, long long* dxch, double* vv, double* rec_row,
-                                            const int* recp) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int rt = (n + 15) >> 4, ks = (nc + 15) >> 4, K = 16 * ks;
-  if (warp >= 2 * rt) return;
-  const int R = warp >> 1, hs = warp & 1, g = lane >> 2, t = lane & 3;
-  // scale of the injection vector: its largest exponent
-  unsigned em = 0;
-  for (int k = 2 * lane; k < K; k += 64) {
-    const double2 x = *reinterpret_cast<const double2*>(iv + k);
-    em = max(em, max(dg_expo(x.x), dg_expo(x.y)));
-  }
-  em = max(__reduce_max_sync(0xffffffffu, em), 1u);
-  // this warp's digit table: row j, word k / 2 = digit j of values k, k + 1
-  const int stw = 8 * ks + 4;
-  unsigned* tab = dtab + warp * dg_tab_words(ks_max);
-  for (int k = 2 * lane; k < K; k += 64) {
-    const double2 x = *reinterpret_cast<const double2*>(iv + k);
-    const long long n0 = dg_fixed(x.x, em) + kDigitBias, n1 = dg_fixed(x.y, em) + kDigitBias;
-#pragma unroll
-    for (int j = 0; j < kDigits; ++j) tab[j * stw + (k >> 1)] = dg_digit_bf16(n0, j) | (dg_digit_bf16(n1, j) << 16);
-  }
-  __syncwarp();
-  float acc[4][4];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-  const uint4* A = reinterpret_cast<const uint4*>(dm) + (size_t)(R * kDigits + 4 * hs) * ks * 32 + lane;
-  const unsigned* bt = tab + g * stw + t;   // B fragment: digit g of values 16 s + 2t (+1), (+8, +9)
-#pragma unroll 2
-  for (int s = 0; s < ks; ++s) {
-    const unsigned b0 = bt[8 * s], b1 = bt[8 * s + 4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) mma_16816_bf16(acc[j], A[(j * ks + s) * 32], b0, b1);
-  }
-  // groups a + b = base + u of rows g (c0, c1) and g + 8 (c2, c3): b = 2t + (c & 1)
-  int q0[5] = {0, 0, 0, 0, 0}, q1[5] = {0, 0, 0, 0, 0};
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    q0[j] += dg_acc_int(acc[j][0]);
-    q0[j + 1] += dg_acc_int(acc[j][1]);
-    q1[j] += dg_acc_int(acc[j][2]);
-    q1[j + 1] += dg_acc_int(acc[j][3]);
-  }
-  long long ta0 = 0, tb0 = 0, ta1 = 0, tb1 = 0;
-  const int base = 4 * hs + 2 * t;
-#pragma unroll
-  for (int u = 0; u < 5; ++u) {
-    const int sg = base + u;
-    if (sg >= 11) {
-      ta0 += dg_shl(q0[u], 8 * (sg - 11));
-      ta1 += dg_shl(q1[u], 8 * (sg - 11));
-    } else if (sg >= kDigitGroupLo) {
-      tb0 += dg_shl(q0[u], 8 * (sg - kDigitGroupLo));
-      tb1 += dg_shl(q1[u], 8 * (sg - kDigitGroupLo));
-    }
-  }
-#pragma unroll
-  for (int off = 1; off <= 2; off <<= 1) {
-    ta0 += __shfl_xor_sync(0xffffffffu, ta0, off);
-    tb0 += __shfl_xor_sync(0xffffffffu, tb0, off);
-    ta1 += __shfl_xor_sync(0xffffffffu, ta1, off);
-    tb1 += __shfl_xor_sync(0xffffffffu, tb1, off);
-  }
-  long long* xch = dxch + R * 32;   // [16 rows][2]: the h = 1 warp's sums
-  const int rr = g + 8 * t;
-  if (hs == 1 && t < 2) {
-    xch[2 * rr] = t ? ta1 : ta0;
-    xch[2 * rr + 1] = t ? tb1 : tb0;
-  }
-  switch (R) {   // named barrier 1 + R of the two warps of row tile R (constant ids: ptxas reserves only these)
-    case 0: asm volatile("bar.sync 1, 64;" ::: "memory"); break;
-    case 1: asm volatile("bar.sync 2, 64;" ::: "memory"); break;
-    case 2: asm volatile("bar.sync 3, 64;" ::: "memory"); break;
-    default: asm volatile("bar.sync 4, 64;" ::: "memory"); break;
-  }
-  if (hs == 0 && t < 2) {
-    const int r = 16 * R + rr;
-    if (r < n) {
-      const int* ex = reinterpret_cast<const int*>(dm + dg_frag_words(rt, ks));
-      const long long ta = (t ? ta1 : ta0) + xch[2 * rr], tb = (t ? tb1 : tb0) + xch[2 * rr + 1];
-      const double v = dg_to_double(ta, tb, ex[r] + (int)em - 2120);
-      vv[r] = v;
-      if (rec_row != nullptr && recp[r] >= 0) rec_row[recp[r]] = v;
-    }
-  }
-}
-
 // Two builds: at most 64 registers per thread (four CTAs per SM, for
 // networks of many subsystems) and at most 128 (two per SM): the second
 // keeps more of the step loop's state in registers and is used whenever its
@@ -840,11 +679,6 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   double* fdst = reinterpret_cast<double*>(smem_raw + L.fdst);      // their states (kFdState each)
   int* lefd = reinterpret_cast<int*>(smem_raw + L.lefd);            // per line end: FD end or -1
   int* cecnt = reinterpret_cast<int*>(smem_raw + L.cecnt);          // per coupled end: modes collected this step
-  // digit form (P.lim.digit): solve-matrix buffers, per-warp digit tables, the solve warps' exchange
-  uint32_t* dga_buf = reinterpret_cast<uint32_t*>(smem_raw + L.dga);
-  unsigned* dtab = reinterpret_cast<unsigned*>(smem_raw + L.dtab);
-  long long* dxch = reinterpret_cast<long long*>(smem_raw + L.dxch);
-  const bool digit = P.lim.digit != 0;
 
   const int sidx = blockIdx.x;
   const SubDev S = P.sub[sidx];
@@ -961,18 +795,11 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   // Solve-matrix buffers: with two, the previous state's matrix stays
   // resident, so a switch that goes back and forth reloads nothing.
   const size_t buf_len = (size_t)P.lim.n * (size_t)(P.lim.nc | 1);
-  const size_t dbuf_len = dg_buf_words(P.lim);
-  const int dg_vec = (int)(dg_matrix_words((n + 15) >> 4, (nc + 15) >> 4) / 4);   // this CTA's matrix in 16-byte words
   int cur_buf = 0;
   int tag_cur = te * n_states + word, tag_other = -1;   // solve-matrix entries held by the two buffers
   double* gi = gi_buf;
   float* gilo = gilo_buf;
-  uint32_t* dm = dga_buf;
-  if (digit) {
-    const uint4* src = reinterpret_cast<const uint4*>(P.dig + P.ep[S.ep_off + tag_cur].dig_off);
-    for (int i = tid; i < dg_vec; i += T) reinterpret_cast<uint4*>(dm)[i] = src[i];
-    for (int k = nc + tid; k < 16 * ((nc + 15) >> 4); k += T) iv[k] = 0.0;   // padding columns of the last step
-  } else {
+  {
     const int64_t off = P.ep[S.ep_off + tag_cur].ginv_off;
     for (int i = tid; i < n * nc; i += T) {
       const int r = i / nc, c = i - r * nc;
@@ -1001,7 +828,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
     const int x = P.str_slot[S.str_off + t];
     lcstr[x] = t;
     iv[n + t] = -inp[x];
-    if (!digit) ivf[n + t] = (float)(-inp[x]);
+    ivf[n + t] = (float)(-inp[x]);
   }
   if (warp == kPollWarp && n_le > 0) {
     const int p0 = (int)(P.n0 & 1);
@@ -1054,19 +881,13 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
         }
         gi = gi_buf + cur_buf * buf_len;
         gilo = gilo_buf + cur_buf * buf_len;
-        dm = dga_buf + cur_buf * dbuf_len;
         if (entry != tag_cur) {
           tag_cur = entry;
-          if (digit) {
-            const uint4* src = reinterpret_cast<const uint4*>(P.dig + P.ep[S.ep_off + entry].dig_off);
-            for (int i = tid; i < dg_vec; i += T) reinterpret_cast<uint4*>(dm)[i] = src[i];
-          } else {
-            const int64_t off = P.ep[S.ep_off + entry].ginv_off;
-            for (int i = tid; i < n * nc; i += T) {
-              const int r = i / nc, c = i - r * nc;
-              gi[r * ldg + c] = P.ginv[off + i];
-              gilo[r * ldg + c] = P.ginv_lo[off + i];
-            }
+          const int64_t off = P.ep[S.ep_off + entry].ginv_off;
+          for (int i = tid; i < n * nc; i += T) {
+            const int r = i / nc, c = i - r * nc;
+            gi[r * ldg + c] = P.ginv[off + i];
+            gilo[r * ldg + c] = P.ginv_lo[off + i];
           }
         }
       }
@@ -1099,7 +920,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
       }
       if (cnt > 0) {
         iv[node] = acc;
-        if (!digit) ivf[node] = (float)acc;
+        ivf[node] = (float)acc;
       }
     }
     __syncthreads();
@@ -1108,12 +929,6 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
     // the contiguous column block q (the warp issue rate, not the FMA
     // latency, is the limit; contiguous blocks keep the rounding of the
     // partial sums small, measured over long runs)
-    const bool rec_now = P.rec != nullptr && dec == 0 && rec_row < P.rec_rows;
-    if (digit) {   // the same product in digit form on the tensor cores (node sums included)
-      digit_solve(n, nc, P.lim.ks, iv, dm, dtab, dxch, vv,
-                  rec_now ? P.rec + (rec_row - P.rec_row0) * P.n_rec : nullptr, recp);
-      if (src_thread < S.n_src) vs[(par ^ 1) * src_vs + src_thread] = vnext;
-    } else {
     for (int task = tid; task < n * Q; task += T) {
       const int r = task / Q, q = task - r * Q;
       const double* row = gi + r * ldg;
@@ -1133,6 +948,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
     __syncthreads();
 
     // node voltages
+    const bool rec_now = P.rec != nullptr && dec == 0 && rec_row < P.rec_rows;
     for (int r = tid; r < n; r += T) {
       // the X_hi partial sums in double, the X_lo ones in single precision
       double v = part[r * Q];
@@ -1144,7 +960,6 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
       v += (double)vl;
       vv[r] = v;
       if (rec_now && recp[r] >= 0) P.rec[(rec_row - P.rec_row0) * P.n_rec + recp[r]] = v;
-    }
     }
     if (n_nl > 0 && tid == 0)   // rewritten after the compensation
       reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls)->row = rec_now ? rec_row : -1;
@@ -1203,7 +1018,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
           const int t = lcstr[it];
           if (t >= 0) {   // strong branch: its current drives the extra matvec column
             iv[n + t] = -hn;
-            if (!digit) ivf[n + t] = (float)(-hn);
+            ivf[n + t] = (float)(-hn);
           }
         } else if (it >= it_le && it < it_le + n_le) {
           const int e = it - it_le;
@@ -1345,12 +1160,6 @@ cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(prefactor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   prefactor_kernel<<<p.n_mats, 256, smem, st>>>(p);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_digits(const PrefParams& p, uint32_t* dig, cudaStream_t st) {
-  if (p.n_mats <= 0 || dig == nullptr) return cudaSuccess;
-  digits_kernel<<<p.n_mats, 256, 0, st>>>(p, dig);
   return cudaGetLastError();
 }
 
