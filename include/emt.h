@@ -257,21 +257,29 @@ emt_status emt_prefactor(emt_ctx* ctx);
  * workspace emt_prefactor obtains from cudaMalloc (matrix lists, per-matrix
  * status, a copy of G and the Newton residual for every matrix) lives in a
  * fixed device array built into the library instead.  It is for callers
- * that must not allocate device memory at this point -- while recording a
- * CUDA graph, in a service that reserves all device memory up front, or in
- * a loop that cannot accept cudaMalloc's implicit synchronisation or its
- * failure -- having built the context beforehand.  The paper has no
- * counterpart; it is a deployment convenience.
+ * that must not allocate device memory when they refactorise, having built
+ * the context beforehand: a service that reserves all device memory up
+ * front and hands it out itself, or a loop that cannot take cudaMalloc's
+ * implicit device synchronisation or risk its failure half-way through a
+ * run.  The paper has no counterpart; it is a deployment convenience.
  *   Limit: at most 16383 matrices (subsystems x switch states) and 491,520
  *   solve-matrix entries (the "solve matrix" is n x (n + strong columns) per
  *   matrix); larger networks get EINVAL with a message (use emt_prefactor).
  *   The fixed array (about 7.7 MiB) is held on every device that loads the
  *   library until the process exits.
  *   The first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
- *   The context's device must be current.  Runs on `cuda_stream` and
- *   synchronises it.  All calls share the one array: calls that overlap on
- *   the GPU (other threads, other streams) race and must be serialised. */
+ *   (cudaGetSymbolAddress) and keeps it for the life of the process; make
+ *   that first call before any stream capture.  A cudaDeviceReset frees the
+ *   array with everything else on the device (every emt_ctx included), so
+ *   the library is not usable on that device after a reset.
+ *   The context's device must be current.  Single-scenario contexts only
+ *   (EINVAL otherwise).  ESINGULAR names the subsystem, as emt_prefactor.
+ *   Runs on `cuda_stream` and synchronises it.  It rewrites the context's
+ *   solve matrices on that stream: order it after every earlier emt_step_n
+ *   or emt_adjoint of the context issued on other streams (an event the
+ *   stream waits on, or a synchronisation).  All calls share the one array:
+ *   calls that overlap on the GPU (other threads, other streams, other
+ *   contexts) race and must be serialised. */
 emt_status emt_prefactor_noalloc(emt_ctx* ctx, void* cuda_stream);
 
 /* Choose the recorded node voltages ("waveform channels", Sec. II-A):

@@ -1,6 +1,7 @@
 // Host side of libemt: validation, partitioning into subsystems, device
 // layout, launches and the C ABI of include/emt.h.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -2952,10 +2953,11 @@ static emt_status adjoint_run(emt_ctx* c, const double* v_target, int64_t n_step
 // emt_prefactor allocates temporary device buffers (the matrix lists, a
 // status word per matrix, and two n x nc workspaces per matrix: a copy of G
 // and the Newton residual).  Callers that must not allocate device memory
-// while they run -- code recording a CUDA graph, services that reserve all
-// device memory up front, loops that cannot afford cudaMalloc's implicit
-// synchronisation or its failure -- use emt_prefactor_noalloc instead,
-// which keeps that workspace in the fixed array below.
+// when they refactorise -- services that reserve all device memory up front
+// and hand it out themselves, loops that cannot take cudaMalloc's implicit
+// device synchronisation or risk its failure half-way through a run -- use
+// emt_prefactor_noalloc instead, which keeps that workspace in the fixed
+// array below.
 
 namespace {
 
@@ -2967,9 +2969,11 @@ constexpr size_t kNoAllocScratchBytes =
 // Shared by every call on a device; holds the last call's contents.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch per device, found on first use.
+// Device address of g_noalloc_scratch per device, looked up on the first
+// call on that device.  Every thread that looks it up stores the same
+// value; the atomics make concurrent first calls well defined.
 constexpr int kNoAllocMaxDevices = 64;
-void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+std::atomic<void*> g_noalloc_ptr[kNoAllocMaxDevices];
 
 // Matrix m is epoch m: epochs are stored subsystem by subsystem.
 __global__ void noalloc_mat_lists(const SubDev* sub, int n_sub, int32_t* mat_sub, int32_t* mat_ep) {
@@ -3001,13 +3005,13 @@ extern "C" emt_status emt_prefactor_noalloc(emt_ctx* c, void* stream) {
   if (n_mats + 1 > kNoAllocMaxMats || (size_t)c->ginv_len > kNoAllocMaxWorkDoubles)
     return c->fail(EMT_EINVAL, "network too large for emt_prefactor_noalloc's fixed workspace "
                                "(at most 16383 matrices and 491520 solve-matrix entries); use emt_prefactor");
-  if (!g_noalloc_ptr[dev]) {   // one-time set-up on this device
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  void* sym = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!sym) {   // one-time set-up on this device (the device is current)
+    e = cudaGetSymbolAddress(&sym, g_noalloc_scratch);
     if (e != cudaSuccess) return c->cuda_fail(e, "emt_prefactor_noalloc: cudaGetSymbolAddress");
-    g_noalloc_ptr[dev] = p;
+    g_noalloc_ptr[dev].store(sym, std::memory_order_release);
   }
-  unsigned char* base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  unsigned char* base = static_cast<unsigned char*>(sym);
   int32_t* mat_sub = reinterpret_cast<int32_t*>(base);
   int32_t* mat_ep = mat_sub + kNoAllocMaxMats;
   int32_t* status = mat_ep + kNoAllocMaxMats;      // status[0 .. n_mats), then the "first" word
@@ -3054,7 +3058,15 @@ extern "C" emt_status emt_prefactor_noalloc(emt_ctx* c, void* stream) {
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h_first, first, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return c->cuda_fail(e, "emt_prefactor_noalloc");
-  if (h_first != 0x7f7f7f7f) return c->fail(EMT_ESINGULAR, "a subsystem conductance matrix is singular");
+  if (h_first != 0x7f7f7f7f) {   // matrix h_first - 1 is epoch h_first - 1 (epochs subsystem by subsystem)
+    const int m = h_first - 1;
+    for (int s = 0; s < c->n_sub; ++s)
+      if (m >= c->subs[s].ep_off && m < c->subs[s].ep_off + c->subs[s].n_ep)
+        return c->fail(EMT_ESINGULAR, "conductance matrix of subsystem " + std::to_string(s) + " (first node " +
+                                          std::to_string(c->original_of[c->subs[s].node_off]) + ", switch state " +
+                                          std::to_string(m - c->subs[s].ep_off) + ") is singular");
+    return c->fail(EMT_ESINGULAR, "a subsystem conductance matrix is singular");
+  }
   c->prefactored = true;
   return EMT_OK;
 }
