@@ -67,7 +67,42 @@ METRIC = "node-steps/s and scenario-steps/s at 1 B300 (FP64, rel err ≤1e-10); 
 UNIT = "node-steps/s"
 N_STEPS = 50000
 E2E_CHUNK = 5000      # time steps per launch of the end-to-end leg (its copies overlap the next chunk)
-FP64_PEAK_GFLOPS = 148 * 4 * 2.032          # 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (max SM clock)
+FP64_PEAK_GFLOPS = 148 * 4 * 2.032          # derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (max SM clock)
+PEAKS_SOURCE = os.path.join(ROOT, "bench_peaks.cu")
+_PEAKS = {}
+
+
+def build_peaks() -> str:
+    """Compile bench_peaks.cu for sm_103a into _build/ (once per source
+    version); return the executable's path."""
+    src = open(PEAKS_SOURCE, "rb").read()
+    exe = os.path.join(ROOT, "_build", "bench_peaks_" + hashlib.sha256(src).hexdigest()[:12])
+    if not os.path.exists(exe):
+        os.makedirs(os.path.dirname(exe), exist_ok=True)
+        subprocess.check_call([os.environ.get("NVCC", "nvcc"), "-gencode", "arch=compute_103a,code=sm_103a", "-O3",
+                               "-o", exe + ".tmp", PEAKS_SOURCE])
+        os.replace(exe + ".tmp", exe)
+    return exe
+
+
+def measure_peaks() -> dict:
+    """FP64 (and bf16 mma.sync) peaks measured on this GPU by bench_peaks.cu,
+    built with nvcc into _build/ on first use; {} if it cannot run."""
+    if _PEAKS:
+        return _PEAKS
+    try:
+        exe = build_peaks()
+        out = subprocess.run([exe], capture_output=True, text=True, timeout=120).stdout.strip().splitlines()
+        _PEAKS.update(json.loads(out[-1]))
+    except (OSError, subprocess.SubprocessError, ValueError, IndexError) as e:
+        _PEAKS.update({"error": str(e)})
+    return _PEAKS
+
+
+def fp64_peak_gflops() -> float:
+    """The roofline's FP64 denominator: the DFMA rate measured in this run,
+    else the derived figure."""
+    return float(measure_peaks().get("fp64_dfma_gflops") or FP64_PEAK_GFLOPS)
 KERNEL_SOURCES = ["paper_1903_01081_b300/csrc/emt_kernels.cu", "paper_1903_01081_b300/csrc/emt_device.cuh",
                   "paper_1903_01081_b300/csrc/emt_internal.h"]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "fwd_kernel_large_scale.json")
@@ -279,7 +314,7 @@ def scenario_leg(name, net, sc, n_steps, n_check, rec_channels, decim, tune_step
            "scenario_steps_per_s": S * n_steps / (ms / 1e3),
            "node_steps_per_s": S * net.n_nodes * n_steps / (ms / 1e3),
            "solve_gflops": flops_per_scen_step * S * n_steps / (ms / 1e3) / 1e9,
-           "solve_frac_of_fp64_peak": flops_per_scen_step * S * n_steps / (ms / 1e3) / 1e9 / FP64_PEAK_GFLOPS,
+           "solve_frac_of_fp64_peak": flops_per_scen_step * S * n_steps / (ms / 1e3) / 1e9 / fp64_peak_gflops(),
            "n_matrix_variants": sim.info("n_matrix_variants"), "scenarios_per_cta": sim.info("scenarios_per_cta"),
            "threads_per_cta": sim.info("batch_threads"), "subsystem_groups": sim.info("batch_groups"),
            "build_prefactor_s": round(build_s, 3), "autotune_s": round(tune_s, 3),
@@ -614,9 +649,9 @@ def size_leg(net, workload, steps, reps=3, n_check=1000, cpu_steps=1000):
            "ctas": sim.info("n_subsystems"), "largest_component": sim.info("max_component_nodes"),
            "largest_cta_nodes": n_max, "time_steps": N, "ms": 1e3 * t, "us_per_step": 1e6 * t / N,
            "node_steps_per_s": net.n_nodes * N / t,
-           "fp64_frac_of_derived_peak": flops * N / t / 1e9 / FP64_PEAK_GFLOPS,
+           "fp64_frac_of_measured_peak": flops * N / t / 1e9 / fp64_peak_gflops(),
            # the largest CTA's dense solve (a packed CTA's zero blocks included: its SM runs them)
-           "critical_path_sm_frac": (2.0 * n_max * n_max) / (t / N) / (FP64_PEAK_GFLOPS / 148 * 1e9),
+           "critical_path_sm_frac": (2.0 * n_max * n_max) / (t / N) / (fp64_peak_gflops() / 148 * 1e9),
            "smem_bytes_per_cta": sim.info("smem_bytes")}
     n_chk = min(n_check, N)
     w = sim.waveforms(n_rows=n_chk)[:, 0, :]
@@ -769,7 +804,9 @@ def run_ours(args):
         if os.path.exists(PROFILE_SUMMARY):
             prof = json.load(open(PROFILE_SUMMARY))
             if prof.get("kernel_source_hash") == kernel_hash():
-                traffic = prof.get("dram_bytes_per_step_n_call")
+                traffic = prof.get("dram_bytes_full_run")
+        peak = fp64_peak_gflops()
+        peaks = measure_peaks()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
@@ -780,14 +817,22 @@ def run_ours(args):
                        "n_subsystems": n_sub, "time_steps_per_bench_step": N_STEPS,
                        "l2": "flushed between timed iterations (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                         "frac": achieved / FP64_PEAK_GFLOPS, "traffic": traffic,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "GFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": "fwd_kernel (+ source_kernel, <0.5% of the time)",
-                         "peak_source": "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz",
+                         "peak_source": ("measured in this run by bench_peaks.cu: FP64 DFMA, 8 independent chains "
+                                         "per thread, best of 148 x {1,2,4,8} CTAs of 256 threads (of measured)"
+                                         if "fp64_dfma_gflops" in peaks else
+                                         "derived: 148 SMs x 2 DFMA/clk x 2 flop x 2.032 GHz (measurement failed)"),
+                         "derived_peak": FP64_PEAK_GFLOPS, "frac_of_derived_peak": achieved / FP64_PEAK_GFLOPS,
+                         "measured_peaks": peaks,
+                         "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum of the fwd_kernel and "
+                                           "source_kernel launches of one full 50,000-step run (profiles/"
+                                           "fwd_kernel_large_scale.json); null if the kernel sources changed since",
                          # the step cannot end before the largest subsystem's dense solve (2 n^2 flop) has run
                          # on its one SM: that SM's share of the FP64 peak against the measured step time
                          "critical_path_sm_frac": (2.0 * n_max * n_max) / (per_launch_s / N_STEPS)
-                                                  / (FP64_PEAK_GFLOPS / 148 * 1e9),
+                                                  / (peak / 148 * 1e9),
                          "critical_path": f"2 n^2 flop of the largest subsystem (n = {n_max}) per step on one SM",
                        "paper_sparse_solve": sparse_solve_flops_per_step(net)},
             "cpu_baseline": cpu_baseline(net, N_STEPS),
@@ -829,9 +874,13 @@ def main():
     ap.add_argument("--leg-warm", type=int, default=500, help="warm-up steps of a lone scenario leg")
     ap.add_argument("--shape", default=None, help="S_t,threads for a lone scenario leg (no autotuning)")
     ap.add_argument("--selftest-ranks", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--peaks", action="store_true", help="print the peaks bench_peaks.cu measures and exit")
     args = ap.parse_args()
     if args.selftest_ranks:
         return run_rank_selftest()
+    if args.peaks:
+        print(json.dumps(measure_peaks()), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "fd_lines", "nonlinear",
