@@ -77,6 +77,16 @@ struct emt_ctx {
   int max_clayers = 0;
   int64_t ring_len = 0, ginv_len = 0, n_lc_total = 0;
   int64_t n_components = 0;
+  // subsystems that factorise their switch states at run time (SubDev::n_cache)
+  bool lazy = false;
+  std::vector<long long> cache_tag0;   // initial tags of every cache slot
+  std::vector<int32_t> cache_next0;    // per subsystem: initial slot to replace next
+  int64_t lazy_work_len = 0;
+  long long* d_cache_tag = nullptr;
+  long long* d_cache_tag0 = nullptr;
+  int32_t* d_cache_next = nullptr;
+  int32_t* d_cache_next0 = nullptr;
+  double* d_lazy_work = nullptr;
   bool forward_narrow = false;   // emt_adjoint: its re-runs share the device with the reverse sweep   // electrical subsystems (components); n_sub counts CTAs, several components each when packed
   int64_t comp_sum_n2 = 0, comp_max_n = 0;   // over the components
   FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0};
@@ -713,6 +723,7 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
           for (int word = 0; word < sd.n_states; ++word) {
             EpochDev E{};
             E.start = 0;
+            E.rs_word = -1;   // the runtime switches are in its switch list
             E.ginv_off = goff;
             goff += (int64_t)sd.n * (sd.n + sd.n_str);
             E.nlz_off = -1;
@@ -1698,11 +1709,15 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
     int64_t goff = 0;
     for (int s = 0; s < S; ++s) {
       SubDev& sd = c->subs[s];
-      if ((int)rs_of[s].size() > kMaxRuntimeSwitches)
-        return bail("subsystem " + std::to_string(s) + " has more than " + std::to_string(kMaxRuntimeSwitches) +
-                    " runtime switches");
+      const int max_rs = scen ? kMaxRuntimeSwitches : kMaxLazySwitches;
+      if ((int)rs_of[s].size() > max_rs)
+        return bail("subsystem " + std::to_string(s) + " has more than " + std::to_string(max_rs) +
+                    " runtime switches" + (scen ? " (in a scenario set)" : ""));
       sd.n_rs = (int)rs_of[s].size();
-      sd.n_states = 1 << sd.n_rs;
+      // up to kMaxRuntimeSwitches every state word is prefactored; above it
+      // the states are factorised on the device when first met
+      const bool lazy = sd.n_rs > kMaxRuntimeSwitches;
+      sd.n_states = lazy ? 1 : 1 << sd.n_rs;
       sd.rs_off = (int)c->rswitches.size();
       int32_t word0 = 0;
       for (int j = 0; j < sd.n_rs; ++j) {
@@ -1713,6 +1728,7 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
         r.kind = d->rs_kind[w];
         r.r_on = d->rs_ron[w];
         r.trip = d->rs_trip_step[w];
+        r.r_off = d->rs_roff[w];
         c->rswitches.push_back(r);
         c->rs_roff.push_back(d->rs_roff[w]);
         if (r.kind == 1 || d->rs_on0[w]) word0 |= 1 << j;
@@ -1729,17 +1745,45 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
       eps.push_back({LLONG_MIN, events.empty() ? 1 : events[0] - 1});
       for (int64_t e : events) eps.push_back({e, e});
       sd.ep_off = (int)c->epochs.size();
-      for (auto& ep : eps)
+      const int64_t mat_len = (int64_t)sd.n * (sd.n + sd.n_str);
+      if (lazy) {   // cache slots: epoch te's initial state in slot te, then spare slots
+        const int n_te = (int)eps.size();
+        sd.n_cache = n_te + kLazyCacheExtra;
+        sd.cache_slot0 = (int)c->cache_tag0.size();
+        sd.cache_goff = goff;
+        goff += (int64_t)sd.n_cache * mat_len;
+        sd.cache_zoff = c->nlz_len;
+        if (sd.n_nl > 0) c->nlz_len += (int64_t)sd.n_cache * sd.n;
+        sd.work_off = c->lazy_work_len;
+        c->lazy_work_len += 2 * (int64_t)sd.n * sd.n;
+        for (int j = 0; j < sd.n_cache; ++j)
+          c->cache_tag0.push_back(j < n_te ? (((long long)j << 32) | (unsigned)word0) : -1ll);
+        c->cache_next0.push_back(n_te % sd.n_cache);
+        c->lazy = true;
+      } else {
+        c->cache_next0.push_back(0);
+      }
+      for (int te = 0; te < (int)eps.size(); ++te) {
+        const auto& ep = eps[te];
         for (int word = 0; word < sd.n_states; ++word) {
           EpochDev E{};
           E.start = ep.first;
-          E.ginv_off = goff;
-          goff += (int64_t)sd.n * (sd.n + sd.n_str);
+          if (lazy) {
+            E.ginv_off = sd.cache_goff + te * mat_len;
+          } else {
+            E.ginv_off = goff;
+            goff += mat_len;
+          }
           E.nlz_off = -1;
           if (sd.n_nl > 0) {
-            E.nlz_off = c->nlz_len;
-            c->nlz_len += sd.n;
+            if (lazy) {
+              E.nlz_off = sd.cache_zoff + (int64_t)te * sd.n;
+            } else {
+              E.nlz_off = c->nlz_len;
+              c->nlz_len += sd.n;
+            }
           }
+          E.rs_word = lazy ? word0 : -1;
           E.sw_off = (int)c->switches.size();
           for (int64_t w : sw_of[s]) {
             if (!switch_closed(d->sw_close_step[w], d->sw_open_step[w], ep.second)) continue;
@@ -1749,7 +1793,7 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
             sw.g = 1.0 / d->sw_r[w];
             c->switches.push_back(sw);
           }
-          for (int j = 0; j < sd.n_rs; ++j) {   // runtime switches: r_on or r_off by the state word
+          for (int j = 0; j < sd.n_rs && !lazy; ++j) {   // runtime switches: r_on or r_off by the state word
             const int64_t w = rs_of[s][j];
             SwitchDev sw{};
             sw.k = d->rs_k[w] >= 0 ? local[d->rs_k[w]] : -1;
@@ -1760,6 +1804,7 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
           E.n_sw = (int)c->switches.size() - E.sw_off;
           c->epochs.push_back(E);
         }
+      }
       sd.n_ep = (int)c->epochs.size() - sd.ep_off;
     }
     c->ginv_len = goff;
@@ -1855,6 +1900,13 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_cstate, 2 * c->cblocks.size());
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_cy, c->cblocks.size());
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_le_prev, c->line_ends.size());
+  if (c->lazy) {
+    UP(d_cache_tag0, cache_tag0)
+    UP(d_cache_tag, cache_tag0)
+    UP(d_cache_next0, cache_next0)
+    UP(d_cache_next, cache_next0)
+    if (e == cudaSuccess) e = c->alloc_zero(&c->d_lazy_work, (size_t)c->lazy_work_len);
+  }
   if (c->batched) {
     UP(d_col_code, b_col_code)
     UP(d_node_sub, b_node_sub)
@@ -1948,6 +2000,18 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   return EMT_OK;
 }
 
+// Subsystems that factorise their states at run time: after a prefactor,
+// the cache holds each epoch's initial state (slot te) and nothing else.
+static cudaError_t reset_matrix_cache(emt_ctx* c, cudaStream_t st) {
+  if (!c->lazy) return cudaSuccess;
+  cudaError_t e = cudaMemcpyAsync(c->d_cache_tag, c->d_cache_tag0, c->cache_tag0.size() * sizeof(long long),
+                                  cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_cache_next, c->d_cache_next0, c->cache_next0.size() * sizeof(int32_t),
+                        cudaMemcpyDeviceToDevice, st);
+  return e;
+}
+
 extern "C" emt_status emt_prefactor(emt_ctx* c) {
   if (!c) return EMT_EINVAL;
   std::vector<int32_t> mat_sub, mat_ep;
@@ -1990,6 +2054,7 @@ extern "C" emt_status emt_prefactor(emt_ctx* c) {
   p.work_g = d_wg;
   p.work_r = d_wr;
   p.status = d_status;
+  p.rs = c->d_rs;
   if (c->batched) {
     p.rm_ptr_br = c->d_rm_ptr_br;
     p.rm_br = c->d_rm_br;
@@ -1997,6 +2062,7 @@ extern "C" emt_status emt_prefactor(emt_ctx* c) {
     p.rm_le = c->d_rm_le;
   }
   if (e == cudaSuccess) e = launch_prefactor(p, std::max(c->lim.n, 1), nullptr);
+  if (e == cudaSuccess) e = reset_matrix_cache(c, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   std::vector<int32_t> status(mat_sub.size(), 0);
   if (e == cudaSuccess && !status.empty())
@@ -2217,6 +2283,14 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
   p.cinj = c->d_cinj;
   p.cstate = c->d_cstate;
   p.cy = c->d_cy;
+  p.ginv_rw = c->d_ginv;
+  p.ginv_lo_rw = c->d_ginv_lo;
+  p.nlz_rw = c->d_nlz;
+  p.nlz_lo_rw = c->d_nlz_lo;
+  p.cache_tag = c->d_cache_tag;
+  p.cache_next = c->d_cache_next;
+  p.lazy_work = c->d_lazy_work;
+  p.sw = c->d_sw;
   for (int64_t done = 0; done < n_steps; done += chunk) {
     const int64_t len = std::min(chunk, n_steps - done);
     SourceParams sp{};
@@ -2232,7 +2306,7 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
     if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n source table");
     p.n0 = c->step + 1;
     p.n_steps = len;
-    e = launch_forward(p, st, !c->forward_narrow);
+    e = launch_forward(p, st, !c->forward_narrow, c->lazy);
     if (e == cudaErrorCooperativeLaunchTooLarge)
       return c->fail(EMT_ERESOURCE, "persistent launch of " + std::to_string(c->n_sub) +
                                         " CTAs cannot be co-resident on this device");
@@ -2283,6 +2357,10 @@ extern "C" emt_status emt_sync(emt_ctx* c, int32_t* info) {
   if (h[0] == EMT_ETIMEOUT)
     return c->fail(EMT_ETIMEOUT, "subsystem " + std::to_string(h[1]) + " timed out at step " + std::to_string(h[3]) +
                                      " waiting for the value of its line end " + std::to_string(h[2]));
+  if (h[0] == EMT_ESINGULAR)
+    return c->fail(EMT_ESINGULAR, "conductance matrix of subsystem " + std::to_string(h[1]) + " in switch epoch " +
+                                      std::to_string(h[3]) + ", runtime-switch state word " + std::to_string(h[2]) +
+                                      " (factorised at run time) is singular");
   if (h[0] != 0) return c->fail((emt_status)h[0], "device error");
   return EMT_OK;
 }
@@ -2591,6 +2669,20 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "n_control_injections") *value = (int64_t)c->cinj.size();
   else if (k == "max_control_layers") *value = c->max_clayers;
   else if (k == "smem_bytes") *value = (int64_t)forward_smem_bytes(c->lim);
+  else if (k == "lazy_subsystems") {   // subsystems whose switch states are factorised at run time
+    int64_t m = 0;
+    for (const SubDev& sd : c->subs) m += sd.n_cache > 0 ? 1 : 0;
+    *value = m;
+  } else if (k == "factorised_states") {   // solve matrices held by their caches (synchronises the device)
+    std::vector<long long> tag(c->cache_tag0.size());
+    cudaDeviceSynchronize();
+    if (!tag.empty() &&
+        cudaMemcpy(tag.data(), c->d_cache_tag, tag.size() * sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return EMT_ECUDA;
+    int64_t m = 0;
+    for (long long t : tag) m += t >= 0 ? 1 : 0;
+    *value = m;
+  }
   else if (k == "ctas_per_sm") {   // co-resident persistent CTAs per SM (occupancy of the single-network kernel)
     FwdLimits fl = c->lim;
     fl.n = std::max(fl.n, 1);
@@ -2643,6 +2735,9 @@ static emt_status adjoint_run(emt_ctx* c, const double* v_target, int64_t n_step
   if (!c->cblocks.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: control blocks have no adjoint");
   if (!c->fdends.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: frequency-dependent lines have no adjoint");
   if (!c->nls.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: nonlinear resistors have no adjoint");
+  if (c->lazy)
+    return c->fail(EMT_EINVAL, "emt_adjoint: a subsystem with more than " + std::to_string(kMaxRuntimeSwitches) +
+                                   " runtime switches (states factorised at run time) has no adjoint");
   if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
   if (n_steps < 1) return c->fail(EMT_EINVAL, "emt_adjoint: n_steps must be >= 1");
   if (n_steps > (int64_t)INT32_MAX - (int64_t)(1 << 21))
@@ -3047,7 +3142,9 @@ extern "C" emt_status emt_prefactor_noalloc(emt_ctx* c, void* stream) {
   p.work_g = work_g;
   p.work_r = work_r;
   p.status = status;
+  p.rs = c->d_rs;
   if (e == cudaSuccess) e = launch_prefactor(p, std::max(c->lim.n, 1), st);
+  if (e == cudaSuccess) e = reset_matrix_cache(c, st);
   int32_t* first = status + n_mats;
   if (e == cudaSuccess) e = cudaMemsetAsync(first, 0x7f, sizeof(int32_t), st);
   if (e == cudaSuccess) {

@@ -126,6 +126,14 @@ struct SubDev {
   int32_t ci_off, n_ci;        // control injections: local block slot per injection in cinj
   int32_t fd_off, n_fd;        // frequency-dependent line ends (FdEndDev list)
   int32_t nl_off, n_nl;        // nonlinear resistor (NlDev list; at most one)
+  // More than kMaxRuntimeSwitches runtime switches: the solve matrix of a
+  // (switch epoch, state word) is factorised by the CTA when the state is
+  // first met (process 3 at run time) into one of n_cache slots, slot j at
+  // ginv offset cache_goff + j n (n + n_str) (its nonlinear column at
+  // cache_zoff + j n), tagged in cache_tag[cache_slot0 + j]; the
+  // factorisation's two n x n workspaces at lazy_work + work_off.
+  int32_t n_cache, cache_slot0;
+  int64_t cache_goff, cache_zoff, work_off;
 };
 
 // A nonlinear resistor solved by the compensation method: odd, piecewise
@@ -163,8 +171,13 @@ struct __align__(16) CtrlDev {
 constexpr int kLayerTypeShift = 24;
 constexpr int kMixedLayer = 15;
 
-// Maximum runtime switches per subsystem (2^k solve matrices each epoch).
+// Runtime switches per subsystem up to which every state word of every
+// epoch is prefactored (2^k solve matrices per epoch); above it, and up to
+// kMaxLazySwitches, states are factorised on the device when first met.
 constexpr int kMaxRuntimeSwitches = 8;
+constexpr int kMaxLazySwitches = 30;
+// Cache slots per such subsystem beyond one per epoch.
+constexpr int kLazyCacheExtra = 64;
 
 // A runtime switch in device form: a two-state resistor whose state in
 // force at step n is decided from step n-1's solution.  Bit `j` (its index
@@ -176,6 +189,7 @@ struct RuntimeSwitchDev {
   int32_t pad;
   double r_on;         // breaker current = (v_k - v_m) / r_on while on
   int64_t trip;        // breaker: first step at which it may open
+  double r_off;        // resistance while off (stamped by run-time factorisation)
 };
 
 // Strong L/C branches.  When a branch's conductance dwarfs the rest of
@@ -196,6 +210,9 @@ struct EpochDev {
   int64_t ginv_off;      // offset of this epoch's n x nc solve matrix
   int32_t sw_off, n_sw;  // closed switches (SwitchDev list)
   int64_t nlz_off;       // offset of its nonlinear resistor's column z (n doubles), or -1
+  int32_t rs_word;       // >= 0: also stamp the subsystem's runtime switches in this state word
+                         // (subsystems factorised at run time); -1: they are in the switch list
+  int32_t pad;
 };
 
 // Per-launch upper bounds that size the forward kernel's shared memory.
@@ -256,6 +273,15 @@ struct FwdParams {
   const NlDev* nl;             // nonlinear resistors (SubDev nl_off / n_nl)
   const double* nlz;           // their columns z per solve matrix entry (EpochDev::nlz_off)
   const float* nlz_lo;         // z minus that rounding, in single precision
+  // run-time factorisation (SubDev::n_cache > 0): the same arrays, writable
+  double* ginv_rw;
+  float* ginv_lo_rw;
+  double* nlz_rw;
+  float* nlz_lo_rw;
+  long long* cache_tag;        // per cache slot: (epoch << 32) | state word, or -1
+  int32_t* cache_next;         // per subsystem: next slot to replace
+  double* lazy_work;
+  const SwitchDev* sw;         // closed switches of each epoch (EpochDev sw_off / n_sw)
 };
 
 constexpr int kFdState = 11;
@@ -277,6 +303,7 @@ struct PrefParams {
   const NlDev* nl;             // nonlinear resistors: their columns z are written to nlz / nlz_lo
   double* nlz;
   float* nlz_lo;
+  const RuntimeSwitchDev* rs;  // runtime switches, stamped by EpochDev::rs_word where that is >= 0
   double* work_g;              // copy of G per matrix, at ep.ginv_off
   double* work_r;              // residual I - G X per matrix, at ep.ginv_off
   int32_t* status;             // per matrix: 0 ok, 1 singular
@@ -498,8 +525,9 @@ cudaError_t launch_companion(BranchDev* br, int64_t n_br, double dt, cudaStream_
 cudaError_t launch_coupled_constants(CoupledEndDev* ce, int64_t n_ce, cudaStream_t st);
 cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st);
 cudaError_t launch_sources(const SourceParams& p, cudaStream_t st);
-// wide = false: the 64-register build only (while another persistent grid shares the device)
-cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide = true);
+// wide = false: the 64-register build only (while another persistent grid shares the device);
+// lazy: some subsystem factorises its switch states at run time (SubDev::n_cache > 0)
+cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide = true, bool lazy = false);
 size_t forward_smem_bytes(const FwdLimits& lim);
 int forward_blocks_per_sm(const FwdLimits& lim);   // resident CTAs per SM (0 on error)
 cudaError_t launch_batch(const BatchParams& p, int threads, cudaStream_t st, BatchGraph* graph);

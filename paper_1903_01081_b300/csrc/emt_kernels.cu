@@ -111,50 +111,78 @@ __device__ __forceinline__ void stamp(double* A, int n, int k, int m, double g) 
   }
 }
 
-__global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
-  extern __shared__ double A[];
-  __shared__ double fcol[kMaxSubsystemNodes];
-  __shared__ int perm[kMaxSubsystemNodes];
-  __shared__ int s_p, s_sing;
-  const int mi = blockIdx.x;
-  const SubDev S = P.sub[P.mat_sub[mi]];
-  const EpochDev E = P.ep[P.mat_ep[mi]];
+// One solve matrix (process 3), by all threads of a CTA: stamp G, invert it
+// in place (Gauss-Jordan, partial pivoting), then a Newton step with the
+// residual summed in twice the working precision, giving G^-1 = X_hi +
+// X_lo; then the strong-branch columns and the nonlinear resistor's column.
+// Used by the prefactor (one CTA per matrix) and by the forward kernel when
+// a subsystem meets a switch state for the first time.
+struct FactorJob {
+  SubDev S;
+  const SwitchDev* sw;                   // closed switches
+  int n_sw;
+  const RuntimeSwitchDev* rs;            // the subsystem's runtime switches, stamped by rs_word if >= 0
+  int rs_word;
+  const BranchDev* br;
+  const LineEndDev* le;
+  const CoupledEndDev* ce;
+  const int32_t* lc_idx;
+  const int32_t* str_slot;
+  const NlDev* nl;
+  int rb0, rb1, rl0, rl1;                // removed branches / line ends (scenario variants)
+  const int32_t* rm_br;
+  const int32_t* rm_le;
+  double* out;                           // X_hi, n x nc (nc = n + strong columns)
+  float* out_lo;                         // X_lo
+  double* nlz;                           // the nonlinear resistor's column (n), or nullptr
+  float* nlz_lo;
+  double* Gw;                            // two n x n workspaces
+  double* Rw;
+};
+
+// A: n x n doubles, fcol: n doubles, perm: n ints, all in shared memory, and
+// two shared ints; returns true on every thread if G is singular.
+__device__ __noinline__ bool factor_cta(const FactorJob& J, double* A, double* fcol, int* perm, int* s_p, int* s_sing) {
+  const SubDev& S = J.S;
   const int n = S.n, T = blockDim.x, tid = threadIdx.x;
   for (int i = tid; i < n * n; i += T) A[i] = 0.0;
   __syncthreads();
   if (tid == 0) {
     // a source end acts as ground in G (its voltage goes to the injection);
     // elements a scenario variant removes are left out
-    const int rb0 = P.rm_ptr_br ? P.rm_ptr_br[mi] : 0, rb1 = P.rm_ptr_br ? P.rm_ptr_br[mi + 1] : 0;
-    const int rl0 = P.rm_ptr_le ? P.rm_ptr_le[mi] : 0, rl1 = P.rm_ptr_le ? P.rm_ptr_le[mi + 1] : 0;
     for (int b = 0; b < S.n_br; ++b) {
       bool removed = false;
-      for (int x = rb0; x < rb1; ++x) removed |= (P.rm_br[x] == S.br_off + b);
+      for (int x = J.rb0; x < J.rb1; ++x) removed |= (J.rm_br[x] == S.br_off + b);
       if (removed) continue;
-      const BranchDev x = P.br[S.br_off + b];
+      const BranchDev x = J.br[S.br_off + b];
       stamp(A, n, x.k >= 0 ? x.k : -1, x.m >= 0 ? x.m : -1, x.g);
     }
     for (int e = 0; e < S.n_le; ++e) {
       bool removed = false;
-      for (int x = rl0; x < rl1; ++x) removed |= (P.rm_le[x] == S.le_off + e);
+      for (int x = J.rl0; x < J.rl1; ++x) removed |= (J.rm_le[x] == S.le_off + e);
       if (removed) continue;
-      const LineEndDev le = P.le[S.le_off + e];
+      const LineEndDev le = J.le[S.le_off + e];
       if (le.node >= 0) A[le.node * n + le.node] += le.y;
     }
     for (int x = 0; x < S.n_ce; ++x) {   // coupled line ends: the 3 x 3 block Y_p
-      const CoupledEndDev& c = P.ce[S.ce_off + x];
+      const CoupledEndDev& c = J.ce[S.ce_off + x];
       for (int p = 0; p < 3; ++p)
         for (int q = 0; q < 3; ++q) A[c.node[p] * n + c.node[q]] += c.yp[3 * p + q];
     }
-    for (int w = 0; w < E.n_sw; ++w) {
-      const SwitchDev sw = P.sw[E.sw_off + w];
+    for (int w = 0; w < J.n_sw; ++w) {
+      const SwitchDev sw = J.sw[w];
       stamp(A, n, sw.k, sw.m, sw.g);
     }
-    s_sing = 0;
+    if (J.rs_word >= 0)   // runtime switches by the state word: r_on or r_off
+      for (int j = 0; j < S.n_rs; ++j) {
+        const RuntimeSwitchDev r = J.rs[S.rs_off + j];
+        stamp(A, n, r.k, r.m, 1.0 / (((J.rs_word >> j) & 1) ? r.r_on : r.r_off));
+      }
+    *s_sing = 0;
   }
   __syncthreads();
-  double* Gw = P.work_g + E.ginv_off;
-  double* Rw = P.work_r + E.ginv_off;
+  double* Gw = J.Gw;
+  double* Rw = J.Rw;
   for (int i = tid; i < n * n; i += T) Gw[i] = A[i];
   // in-place Gauss-Jordan inversion with row pivoting
   for (int k = 0; k < n; ++k) {
@@ -171,14 +199,14 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
         if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
       }
       if (tid == 0) {
-        s_p = arg;
+        *s_p = arg;
         perm[k] = arg;
-        if (!(best > 1e-300) || !isfinite(best)) s_sing = 1;
+        if (!(best > 1e-300) || !isfinite(best)) *s_sing = 1;
       }
     }
     __syncthreads();
-    if (s_sing) break;
-    const int p = s_p;
+    if (*s_sing) break;
+    const int p = *s_p;
     if (p != k)
       for (int j = tid; j < n; j += T) {
         const double t = A[k * n + j];
@@ -199,10 +227,9 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
     }
     __syncthreads();
   }
-  if (s_sing) {
-    if (tid == 0) P.status[mi] = 1;
-    return;
-  }
+  const bool singular = *s_sing != 0;
+  __syncthreads();
+  if (singular) return true;
   // undo the row interchanges as column interchanges, last pivot first
   for (int k = n - 1; k >= 0; --k) {
     const int p = perm[k];
@@ -228,7 +255,7 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
   }
   __syncthreads();
   const int nc = n + S.n_str;
-  double* out = P.ginv + E.ginv_off;
+  double* out = J.out;
   for (int idx = tid; idx < n * n; idx += T) {
     const int i = idx / n, j = idx - i * n;
     double c = 0.0;
@@ -245,7 +272,7 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
     Rw[idx] = __dadd_rn(hi, lo);
   }
   __syncthreads();
-  float* out_lo = P.ginv_lo + E.ginv_off;
+  float* out_lo = J.out_lo;
   for (int idx = tid; idx < n * n; idx += T) {
     const int i = idx / n, j = idx - i * n;
     double c = 0.0;
@@ -257,7 +284,7 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
   // error-free differences, split again into double + single remainder
   for (int idx = tid; idx < n * S.n_str; idx += T) {
     const int i = idx / S.n_str, t = idx - i * S.n_str;
-    const BranchDev b = P.br[P.lc_idx[S.lc_off + P.str_slot[S.str_off + t]]];
+    const BranchDev b = J.br[J.lc_idx[S.lc_off + J.str_slot[S.str_off + t]]];
     double d1, e1;
     two_sum(out[i * nc + b.k], -out[i * nc + b.m], d1, e1);
     const double rest = e1 + ((double)out_lo[i * nc + b.k] - (double)out_lo[i * nc + b.m]);
@@ -267,8 +294,8 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
     out_lo[i * nc + n + t] = (float)e;
   }
   // the nonlinear resistor's column G^-1 (e_k - e_m), formed the same way
-  if (S.n_nl > 0 && E.nlz_off >= 0) {
-    const NlDev& q = P.nl[S.nl_off];
+  if (S.n_nl > 0 && J.nlz != nullptr) {
+    const NlDev& q = J.nl[S.nl_off];
     for (int i = tid; i < n; i += T) {
       const double a = q.k >= 0 ? out[i * nc + q.k] : 0.0, b = q.m >= 0 ? out[i * nc + q.m] : 0.0;
       const double al = q.k >= 0 ? (double)out_lo[i * nc + q.k] : 0.0;
@@ -277,11 +304,47 @@ __global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
       two_sum(a, -b, d1, e1);
       double s, e;
       two_sum(d1, e1 + (al - bl), s, e);
-      P.nlz[E.nlz_off + i] = s;
-      P.nlz_lo[E.nlz_off + i] = (float)e;
+      J.nlz[i] = s;
+      J.nlz_lo[i] = (float)e;
     }
   }
-  if (tid == 0) P.status[mi] = 0;
+  __syncthreads();
+  return false;
+}
+
+__global__ void __launch_bounds__(256) prefactor_kernel(PrefParams P) {
+  extern __shared__ double A[];
+  __shared__ double fcol[kMaxSubsystemNodes];
+  __shared__ int perm[kMaxSubsystemNodes];
+  __shared__ int s_p, s_sing;
+  const int mi = blockIdx.x;
+  FactorJob J;
+  J.S = P.sub[P.mat_sub[mi]];
+  const EpochDev E = P.ep[P.mat_ep[mi]];
+  J.sw = P.sw + E.sw_off;
+  J.n_sw = E.n_sw;
+  J.rs = P.rs;
+  J.rs_word = E.rs_word;
+  J.br = P.br;
+  J.le = P.le;
+  J.ce = P.ce;
+  J.lc_idx = P.lc_idx;
+  J.str_slot = P.str_slot;
+  J.nl = P.nl;
+  J.rb0 = P.rm_ptr_br ? P.rm_ptr_br[mi] : 0;
+  J.rb1 = P.rm_ptr_br ? P.rm_ptr_br[mi + 1] : 0;
+  J.rl0 = P.rm_ptr_le ? P.rm_ptr_le[mi] : 0;
+  J.rl1 = P.rm_ptr_le ? P.rm_ptr_le[mi + 1] : 0;
+  J.rm_br = P.rm_br;
+  J.rm_le = P.rm_le;
+  J.out = P.ginv + E.ginv_off;
+  J.out_lo = P.ginv_lo + E.ginv_off;
+  J.nlz = E.nlz_off >= 0 ? P.nlz + E.nlz_off : nullptr;
+  J.nlz_lo = E.nlz_off >= 0 ? P.nlz_lo + E.nlz_off : nullptr;
+  J.Gw = P.work_g + E.ginv_off;
+  J.Rw = P.work_r + E.ginv_off;
+  const bool singular = factor_cta(J, A, fcol, perm, &s_p, &s_sing);
+  if (threadIdx.x == 0) P.status[mi] = singular ? 1 : 0;
 }
 
 // ------------------------------------------------------------ sources
@@ -625,13 +688,18 @@ __device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int la
 // networks of many subsystems) and at most 128 (two per SM): the second
 // keeps more of the step loop's state in registers and is used whenever its
 // residency holds every CTA.
-template <int kMinBlocks>
+// kLazy: the network has subsystems whose states are factorised at run time
+// (the code for that is compiled only into those instances, so that the
+// step loop of every other network keeps its registers).
+template <int kMinBlocks, bool kLazy>
 __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_abort;
-  __shared__ RuntimeSwitchDev s_rs[kMaxRuntimeSwitches];
-  __shared__ double s_rsi[kMaxRuntimeSwitches];   // breaker currents of the previous step
-  __shared__ int s_rsbit[kMaxRuntimeSwitches];    // states decided for the next step
+  constexpr int kRs = kLazy ? kMaxLazySwitches : kMaxRuntimeSwitches;
+  __shared__ RuntimeSwitchDev s_rs[kRs];
+  __shared__ double s_rsi[kRs];   // breaker currents of the previous step
+  __shared__ int s_rsbit[kRs];    // states decided for the next step
+  __shared__ int s_slot, s_fp, s_fsing;        // run-time factorisation: cache slot, pivot, singular flag
   const FwdSmem L = fwd_smem(P.lim);
   double* gi_buf = reinterpret_cast<double*>(smem_raw + L.gi);
   double* part = reinterpret_cast<double*>(smem_raw + L.part);
@@ -796,27 +864,93 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   // resident, so a switch that goes back and forth reloads nothing.
   const size_t buf_len = (size_t)P.lim.n * (size_t)(P.lim.nc | 1);
   int cur_buf = 0;
-  int tag_cur = te * n_states + word, tag_other = -1;   // solve-matrix entries held by the two buffers
+  int tag_cur = -1, tag_other = -1;   // solve-matrix entries (or cache slots) held by the two buffers
   double* gi = gi_buf;
   float* gilo = gilo_buf;
+  // A subsystem with more runtime switches than are prefactored keeps its
+  // solve matrices in a cache of slots: the slot of (epoch te, state word),
+  // factorised by the CTA into the slot (shared-memory buffer wbuf as the
+  // workspace) when the state is met for the first time; -1 if singular.
+  auto lazy_slot = [&](int te_, int word_, int wbuf, bool& factored) -> int {
+    factored = false;
+    const long long key = ((long long)te_ << 32) | (unsigned)word_;
+    if (tid == 0) {
+      int f = -1;
+      for (int j = 0; j < S.n_cache && f < 0; ++j)
+        if (P.cache_tag[S.cache_slot0 + j] == key) f = j;
+      if (f < 0) {   // replace the next slot in turn
+        f = P.cache_next[sidx];
+        P.cache_next[sidx] = f + 1 == S.n_cache ? 0 : f + 1;
+        P.cache_tag[S.cache_slot0 + f] = -1;
+        s_slot = -1 - f;
+      } else {
+        s_slot = f;
+      }
+    }
+    __syncthreads();
+    int slot = s_slot;
+    if (slot >= 0) return slot;
+    slot = -1 - slot;
+    factored = true;
+    const EpochDev E = P.ep[S.ep_off + te_];
+    FactorJob J;
+    J.S = S;
+    J.sw = P.sw + E.sw_off;
+    J.n_sw = E.n_sw;
+    J.rs = P.rs;
+    J.rs_word = word_;
+    J.br = P.br;
+    J.le = P.le;
+    J.ce = P.ce;
+    J.lc_idx = P.lc_idx;
+    J.str_slot = P.str_slot;
+    J.nl = P.nl;
+    J.rb0 = J.rb1 = J.rl0 = J.rl1 = 0;
+    J.rm_br = J.rm_le = nullptr;
+    J.out = P.ginv_rw + S.cache_goff + (int64_t)slot * n * nc;
+    J.out_lo = P.ginv_lo_rw + S.cache_goff + (int64_t)slot * n * nc;
+    J.nlz = S.n_nl > 0 ? P.nlz_rw + S.cache_zoff + (int64_t)slot * n : nullptr;
+    J.nlz_lo = S.n_nl > 0 ? P.nlz_lo_rw + S.cache_zoff + (int64_t)slot * n : nullptr;
+    J.Gw = P.lazy_work + S.work_off;
+    J.Rw = J.Gw + (size_t)n * n;
+    // workspaces: the buffer the matrix is loaded into next, and the solve's partial sums
+    if (factor_cta(J, gi_buf + wbuf * buf_len, part, reinterpret_cast<int*>(partf), &s_fp, &s_fsing)) {
+      if (tid == 0 && atomicCAS(P.err, 0, 2) == 0) {   // EMT_ESINGULAR, subsystem, -, epoch
+        P.err[1] = sidx;
+        P.err[2] = word_;
+        P.err[3] = te_;
+      }
+      return -1;
+    }
+    if (tid == 0) P.cache_tag[S.cache_slot0 + slot] = key;
+    return slot;
+  };
+  const bool lazy = kLazy && S.n_cache > 0;
   {
-    const int64_t off = P.ep[S.ep_off + tag_cur].ginv_off;
-    for (int i = tid; i < n * nc; i += T) {
-      const int r = i / nc, c = i - r * nc;
-      gi[r * ldg + c] = P.ginv[off + i];
-      gilo[r * ldg + c] = P.ginv_lo[off + i];
+    bool factored;
+    const int entry = lazy ? lazy_slot(te, word, 0, factored) : te * n_states + word;
+    if (entry < 0) {
+      if (tid == 0) s_abort = 1;
+    } else {
+      tag_cur = entry;
+      const int64_t off = lazy ? S.cache_goff + (int64_t)entry * n * nc : P.ep[S.ep_off + entry].ginv_off;
+      for (int i = tid; i < n * nc; i += T) {
+        const int r = i / nc, c = i - r * nc;
+        gi[r * ldg + c] = P.ginv[off + i];
+        gilo[r * ldg + c] = P.ginv_lo[off + i];
+      }
     }
   }
   // nonlinear resistor: its record and the column of the current matrix;
   // its constants are (re)computed before the first compensation after a load
   const int n_nl = S.n_nl;
-  if (n_nl > 0) {
+  if (n_nl > 0 && tag_cur >= 0) {
     NlState* nls = reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls);
     if (tid == 0) {
       nls->q = P.nl[S.nl_off];
       nls->dirty = 1;
     }
-    const int64_t zoff = P.ep[S.ep_off + tag_cur].nlz_off;
+    const int64_t zoff = lazy ? S.cache_zoff + (int64_t)tag_cur * n : P.ep[S.ep_off + tag_cur].nlz_off;
     for (int i = tid; i < n; i += T) {
       nls->z()[i] = P.nlz[zoff + i];
       nls->zl(n)[i] = P.nlz_lo[zoff + i];
@@ -862,11 +996,29 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
       while (te + 1 < n_te && P.ep[S.ep_off + (te + 1) * n_states].start <= step) ++te;
       next_ep_start = (te + 1 < n_te) ? P.ep[S.ep_off + (te + 1) * n_states].start : LLONG_MAX;
       word = new_word;
-      const int entry = te * n_states + word;
+      int entry = te * n_states + word;
+      if (lazy) {
+        // a miss factorises into the buffer loaded next (whose copy is then
+        // stale) and replaces a slot (whose copies are then stale)
+        const int wbuf = P.lim.nbuf > 1 ? (cur_buf ^ 1) : cur_buf;
+        bool factored;
+        entry = lazy_slot(te, word, wbuf, factored);
+        if (entry < 0) {
+          if (tid == 0) s_abort = 1;
+          __syncthreads();
+          break;
+        }
+        if (factored) {
+          if (P.lim.nbuf > 1) tag_other = -1;
+          else tag_cur = -1;
+          if (entry == tag_cur) tag_cur = -1;
+          if (entry == tag_other) tag_other = -1;
+        }
+      }
       if (entry != tag_cur) {
         if (n_nl > 0) {   // the nonlinear resistor's column follows the matrix
           NlState* nls = reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls);
-          const int64_t zoff = P.ep[S.ep_off + entry].nlz_off;
+          const int64_t zoff = lazy ? S.cache_zoff + (int64_t)entry * n : P.ep[S.ep_off + entry].nlz_off;
           for (int i = tid; i < n; i += T) {
             nls->z()[i] = P.nlz[zoff + i];
             nls->zl(n)[i] = P.nlz_lo[zoff + i];
@@ -883,7 +1035,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
         gilo = gilo_buf + cur_buf * buf_len;
         if (entry != tag_cur) {
           tag_cur = entry;
-          const int64_t off = P.ep[S.ep_off + entry].ginv_off;
+          const int64_t off = lazy ? S.cache_goff + (int64_t)entry * n * nc : P.ep[S.ep_off + entry].ginv_off;
           for (int i = tid; i < n * nc; i += T) {
             const int r = i / nc, c = i - r * nc;
             gi[r * ldg + c] = P.ginv[off + i];
@@ -1176,20 +1328,23 @@ size_t forward_smem_bytes(const FwdLimits& lim) { return fwd_smem(lim).bytes; }
 int forward_blocks_per_sm(const FwdLimits& lim) {
   const size_t smem = forward_smem_bytes(lim);
   if (smem > 227 * 1024) return 0;
-  if (cudaFuncSetAttribute(fwd_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(fwd_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<4>, kFwdThreads, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<4, false>, kFwdThreads, smem) != cudaSuccess)
+    return 0;
   return per_sm;
 }
 
-cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide) {
+cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide, bool lazy) {
   const size_t smem = forward_smem_bytes(p.lim);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   // the 128-register build when allowed and its residency holds every CTA, else the 64-register one
-  const void* fns[2] = {(const void*)fwd_kernel<2>, (const void*)fwd_kernel<4>};
+  const void* fns[2] = {lazy ? (const void*)fwd_kernel<2, true> : (const void*)fwd_kernel<2, false>,
+                        lazy ? (const void*)fwd_kernel<4, true> : (const void*)fwd_kernel<4, false>};
   for (int v = wide ? 0 : 1; v < 2; ++v) {
     cudaError_t e = cudaFuncSetAttribute(fns[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -798,6 +798,80 @@ def with_rectifier_loads(base: Network, seed: int = 1006, n_rectifiers: int = 30
     return net
 
 
+def _subsystem_roots(net: Network):
+    """Union-find roots of the subsystems (components over branches,
+    switches and runtime switches; lines cut them)."""
+    parent = list(range(net.n_nodes))
+
+    def find(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+    for k, m in list(zip(net.br_k, net.br_m)) + list(zip(net.rs_k, net.rs_m)) + list(zip(net.sw_k, net.sw_m)):
+        if k >= 0 and m >= 0:
+            a, b = find(int(k)), find(int(m))
+            if a != b:
+                parent[max(a, b)] = min(a, b)
+    return find
+
+
+def with_converter_stations(base: Network, seed: int = 1013, n_stations: int = 10, bridges: int = 2) -> Network:
+    """``base`` plus diode converter stations, each ``bridges`` six-pulse
+    bridges on one three-phase bus (two bridges: 12 diodes in one subsystem).
+
+    Bridge on bus phase nodes (a, b, c): per phase a commutation inductance
+    L ~ U[1, 5] mH from the phase node to a new AC terminal t_p, an upper
+    diode t_p -> P and a lower diode ground -> t_p (r_on 0.01 ohm, r_off
+    1 Mohm, off at the start), each valve with a 500 ohm snubber resistor
+    across it (without one, a valve that opens on the inductance's current
+    leaves a trapezoidal-rule oscillation that makes the valves chatter
+    every step); the DC node P feeds R ~ U[50, 200] ohm and C ~ U[20, 100]
+    uF to ground.  Stations go to the source buses first, then to random
+    buses, one per subsystem."""
+    rng = np.random.default_rng(seed)
+    net = base.copy()
+    find = _subsystem_roots(net)
+    buses = list(net.meta.get("source_bus", [])) + rng.permutation(len(net.meta["bus_nodes"])).tolist()
+    taken, picks = set(), []
+    for bus in buses:
+        r = find(int(net.meta["bus_nodes"][bus][0]))
+        if r not in taken:
+            taken.add(r)
+            picks.append(int(bus))
+        if len(picks) == n_stations:
+            break
+    n = net.n_nodes
+    br = [list(net.br_k), list(net.br_m), list(net.br_kind), list(net.br_value)]
+    rs = {k: list(getattr(net, "rs_" + k)) for k in ("k", "m", "kind", "ron", "roff", "on0", "trip")}
+
+    def diode(a, c):
+        for key, val in (("k", a), ("m", c), ("kind", 0), ("ron", 0.01), ("roff", 1e6), ("on0", 0), ("trip", -1)):
+            rs[key].append(val)
+        br[0].append(a); br[1].append(c); br[2].append(KIND_R); br[3].append(500.0)   # snubber
+    for bus in picks:
+        for _ in range(bridges):
+            dc = n + 3
+            for p, nd in enumerate(net.meta["bus_nodes"][bus]):
+                t = n + p
+                br[0].append(int(nd)); br[1].append(t); br[2].append(KIND_L); br[3].append(rng.uniform(1e-3, 5e-3))
+                diode(t, dc)
+                diode(GROUND, t)
+            for kind, val in ((KIND_R, rng.uniform(50.0, 200.0)), (KIND_C, rng.uniform(20e-6, 100e-6))):
+                br[0].append(dc); br[1].append(GROUND); br[2].append(kind); br[3].append(val)
+            n += 4
+    net.n_nodes = n
+    net.br_k = np.asarray(br[0], np.int32)
+    net.br_m = np.asarray(br[1], np.int32)
+    net.br_kind = np.asarray(br[2], np.uint8)
+    net.br_value = np.asarray(br[3], np.float64)
+    for key, dt in (("k", np.int32), ("m", np.int32), ("kind", np.uint8), ("ron", np.float64), ("roff", np.float64),
+                    ("on0", np.uint8), ("trip", np.int64)):
+        setattr(net, "rs_" + key, np.asarray(rs[key], dt))
+    net.meta = dict(net.meta, converter_stations={"seed": seed, "buses": picks, "bridges": bridges})
+    return net
+
+
 def with_fd_lines(base: Network, seed: int = 1009, fractional: bool = True) -> Network:
     """``base`` with every Bergeron line replaced by a lossy frequency-dependent
     line of the same surge impedance Z_c and travel time (plus U[0, 1) dt when

@@ -113,13 +113,23 @@ def test_runtime_switch_limits():
     b = g.NetworkBuilder()
     b.source(1000.0, 0.0)
     b.branch(g.source_node(0), 0, 0, 1.0)
-    for i in range(9):
+    for i in range(31):
         b.diode(0, i + 1, 0.01, 1e6)
         b.branch(i + 1, g.GROUND, 0, 10.0)
-    net = b.build(50e-6, 10, 10)
+    net = b.build(50e-6, 32, 10)
     with pytest.raises(emt.EmtError) as ei:
         emt.emt_build_network(net)
     assert ei.value.status == emt.EMT_EINVAL and "runtime switches" in str(ei.value)
+    # nine in one subsystem of a scenario set (every state prefactored there)
+    b = g.NetworkBuilder()
+    b.source(1000.0, 0.0)
+    b.branch(g.source_node(0), 0, 0, 1.0)
+    for i in range(9):
+        b.diode(0, i + 1, 0.01, 1e6)
+        b.branch(i + 1, g.GROUND, 0, 10.0)
+    with pytest.raises(emt.EmtError) as ei:
+        emt.emt_build_network(b.build(50e-6, 10, 10), g.Scenarios(n_scenarios=2))
+    assert ei.value.status == emt.EMT_EINVAL and "scenario set" in str(ei.value)
     net = switched_multi()
     ctx = emt.emt_build_network(net)
     emt.emt_prefactor(ctx)
@@ -152,3 +162,68 @@ def test_scenario_set_with_runtime_switches():
     two.sync()
     assert np.array_equal(two.waveforms(), w)
     two.close()
+
+
+def station_network(n_stations=1):
+    base = g.multi_subsystem(41, [3, 5, 4], n_lines=4, n_sources=2, dt=20e-6)
+    return g.with_converter_stations(base, n_stations=n_stations)
+
+
+def test_two_six_pulse_bridges_in_one_subsystem_factorised_at_run_time():
+    """Twelve diodes in one subsystem (two six-pulse bridges): more than the
+    eight whose 2^k states are prefactored, so the CTA factorises each switch
+    state the first time it meets it.  4,000 steps (about 110 valve
+    commutations, 29 distinct states) against the oracle, which factorises G
+    again at every state change.  A second run from the de-energised state
+    finds every state in the cache and gives the same waveforms bit for bit."""
+    net = station_network()
+    N = 4000
+    ref = oracle.simulate(net, N)
+    assert decision_margin(net, ref) > 1e-9
+    st = oracle.runtime_switch_states(net, N)
+    assert len({tuple(r) for r in st}) > 10
+    sim = emt.Simulator(net, n_steps=N)
+    assert sim.info("lazy_subsystems") == 1
+    before = sim.info("factorised_states")
+    sim.run(N)
+    sim.sync()
+    assert sim.info("factorised_states") > before
+    w = sim.waveforms()[:, 0, :]
+    assert rel(w, ref) <= TOL
+    sim.reset()
+    sim.run(N)
+    sim.sync()
+    assert np.array_equal(sim.waveforms()[:, 0, :], w)
+    sim.close()
+
+
+def test_run_time_factorisation_across_launches():
+    net = station_network()
+    N = 3000
+    ref = oracle.simulate(net, N)
+    assert rel(gpu_run(net, N, chunks=(700, 1100, None)), ref) <= TOL
+
+
+def test_converter_stations_on_the_large_network():
+    """Ten two-bridge stations (120 diodes) on the 3,000-node network, one per
+    subsystem: 3,000 steps against the oracle."""
+    net = g.with_converter_stations(g.large_scale(n_steps=3000), n_stations=10)
+    N = 3000
+    ref = oracle.simulate(net, N)
+    assert decision_margin(net, ref) > 1e-9
+    sim = emt.Simulator(net, n_steps=N)
+    assert sim.info("lazy_subsystems") == 10
+    sim.run(N)
+    sim.sync()
+    assert rel(sim.waveforms()[:, 0, :], ref) <= TOL
+    sim.close()
+
+
+def test_adjoint_rejects_states_factorised_at_run_time():
+    net = station_network()
+    ctx = emt.emt_build_network(net)
+    emt.emt_prefactor(ctx)
+    with pytest.raises(emt.EmtError) as ei:
+        emt.emt_adjoint(ctx, np.zeros((10, net.n_nodes)), 10, 0)
+    assert ei.value.status == emt.EMT_EINVAL
+    emt.emt_destroy(ctx)
