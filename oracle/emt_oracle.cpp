@@ -304,8 +304,11 @@ struct Sim {
   std::vector<FLine> fl;
   // nonlinear resistors: the one of each subsystem (or -1) and its column
   // z = G^-1 (e_k - e_m) over the subsystem's nodes, for the current factors
-  std::vector<int> nl_of_sub;
+  std::vector<int> nl_of_sub;                  // the subsystem's nonlinear resistor when it has exactly one, else -1
   std::vector<std::vector<T>> nl_z;
+  std::vector<std::vector<int64_t>> nl_list;   // all nonlinear resistors of each subsystem
+  std::vector<std::vector<T>> gmat;            // unfactorised G of subsystems with several of them
+  std::vector<int> nl_seg;                     // per nonlinear resistor: segment of the last step, sign * (j + 1)
   // control blocks: output of the latest evaluation, and the two states
   // (integral or previous output; previous input)
   std::vector<T> cy, cs0, cs1;
@@ -344,11 +347,15 @@ struct Sim {
     rs_i.assign(net->n_rs, 0.0);
     nl_of_sub.assign(n_sub, -1);
     nl_z.assign(n_sub, {});
+    nl_list.assign(n_sub, {});
+    gmat.assign(n_sub, {});
+    nl_seg.assign(net->n_nl, 1);
     for (int64_t e = 0; e < net->n_nl; ++e) {
       const int a = net->nl_k[e] >= 0 ? net->nl_k[e] : net->nl_m[e];
-      if (nl_of_sub[sub[a]] >= 0) return false;   // at most one per subsystem
-      nl_of_sub[sub[a]] = (int)e;
+      nl_list[sub[a]].push_back(e);
     }
+    for (int s = 0; s < n_sub; ++s)
+      if (nl_list[s].size() == 1) nl_of_sub[s] = (int)nl_list[s][0];
     fl.assign(net->n_fl, FLine{});
     for (int64_t l = 0; l < net->n_fl; ++l) {
       FLine& L = fl[l];
@@ -525,6 +532,7 @@ struct Sim {
           for (int q = 0; q < 3; ++q) G[(size_t)local[nd[p]] * ns + local[nd[q]]] += T(cl[l].yp[3 * p + q]);
       }
     lu[s] = G;
+    if (nl_list[s].size() > 1) gmat[s] = G;
     if (!lu_factor(ns, lu[s], piv[s])) return false;
     if (nl_of_sub[s] >= 0) {   // the nonlinear resistor's column G^-1 (e_k - e_m)
       const int64_t e = nl_of_sub[s];
@@ -558,6 +566,37 @@ struct Sim {
     // last segment's slope): u + r_th (i0 + slope (u - v0)) = |v_th|
     const T u = (x - r_th * T(i0 - slope * v0)) / (T(1.0) + r_th * T(slope));
     return T(sgn) * (T(i0) + T(slope) * (u - T(v0)));
+  }
+
+  // Segment of nonlinear resistor e that holds the voltage u: sign(u) * (j + 1),
+  // j = the number of breakpoints at or below |u| (j = np: past the last one).
+  int nl_segment_of(int64_t e, double u) const {
+    const double* pv = net->nl_v + 8 * e;
+    const int np = net->nl_np[e];
+    const double x = std::fabs(u);
+    int j = 0;
+    while (j < np && x >= pv[j]) ++j;
+    return u < 0.0 ? -(j + 1) : j + 1;
+  }
+
+  // The line i = c0 + slope u of f on segment code sg (see nl_segment_of):
+  // from (v0, i0), the segment's start, with the segment's slope (past the
+  // last breakpoint the last slope); odd: i = sign (i0 + slope (sign u - v0)).
+  void nl_line(int64_t e, int sg, double& slope, double& c0) const {
+    const double* pv = net->nl_v + 8 * e;
+    const double* pi = net->nl_i + 8 * e;
+    const int np = net->nl_np[e];
+    const double sgn = sg < 0 ? -1.0 : 1.0;
+    const int j = (sg < 0 ? -sg : sg) - 1;
+    double v0 = 0.0, i0 = 0.0, sl = 0.0;
+    for (int q = 0; q < np && q <= j; ++q) {   // walk the segments up to j, as nl_current does
+      sl = (pi[q] - i0) / (pv[q] - v0);
+      if (q == j) break;
+      v0 = pv[q];
+      i0 = pi[q];
+    }
+    slope = sl;
+    c0 = sgn * (i0 - sl * v0);
   }
 
   T node_voltage(int32_t x) const {
@@ -637,6 +676,49 @@ struct Sim {
         const T rth = (k >= 0 ? z[local[k]] : T(0.0)) - (m >= 0 ? z[local[m]] : T(0.0));
         const T inl = nl_current(e, vth, rth);
         for (int i = 0; i < ns; ++i) x[i] -= z[i] * inl;
+      } else if (nl_list[s].size() > 1) {
+        // several nonlinear resistors: the piecewise-linear Newton iteration on
+        // the subsystem's nodal equations, from the previous step's segments:
+        // every element stamped as its segment's line i = c0 + slope u, the
+        // system solved, every element moved to the segment its voltage lies
+        // on, until no element moves (f monotone: the solution is unique)
+        bool settled = false;
+        for (int it = 0; it < 64 && !settled; ++it) {
+          std::vector<T> Gs = gmat[s];
+          std::vector<int> ps(ns);
+          for (int i = 0; i < ns; ++i) x[i] = rhs[nodes[s][i]];
+          for (int64_t e : nl_list[s]) {
+            double slope, c0;
+            nl_line(e, nl_seg[e], slope, c0);
+            const int a = net->nl_k[e] >= 0 ? local[net->nl_k[e]] : -1;
+            const int b = net->nl_m[e] >= 0 ? local[net->nl_m[e]] : -1;
+            if (a >= 0) {
+              Gs[(size_t)a * ns + a] += T(slope);
+              x[a] -= T(c0);
+            }
+            if (b >= 0) {
+              Gs[(size_t)b * ns + b] += T(slope);
+              x[b] += T(c0);
+            }
+            if (a >= 0 && b >= 0) {
+              Gs[(size_t)a * ns + b] -= T(slope);
+              Gs[(size_t)b * ns + a] -= T(slope);
+            }
+          }
+          if (!lu_factor(ns, Gs, ps)) return false;
+          lu_solve(ns, Gs, ps, x.data());
+          settled = true;
+          for (int64_t e : nl_list[s]) {
+            const int32_t k = net->nl_k[e], m = net->nl_m[e];
+            const double u = re((k >= 0 ? x[local[k]] : T(0.0)) - (m >= 0 ? x[local[m]] : T(0.0)));
+            const int sg = nl_segment_of(e, u);
+            if (sg != nl_seg[e]) {
+              nl_seg[e] = sg;
+              settled = false;
+            }
+          }
+        }
+        if (!settled) return false;
       }
       for (int i = 0; i < ns; ++i) v[nodes[s][i]] = x[i];
     }

@@ -130,8 +130,12 @@ typedef struct {
    * solved without the element (v0), the element sees the Thevenin source
    * v_th = v0_k - v0_m behind R_th = z_k - z_m, z = G^-1 (e_k - e_m); its
    * current solves i = f(v_th - R_th i) (unique: f monotone, R_th > 0);
-   * then v = v0 - z i.  At most one nonlinear resistor per subsystem.  The
-   * element joins k and m into one subsystem. */
+   * then v = v0 - z i.  A subsystem with several nonlinear resistors is
+   * solved by the piecewise-linear Newton iteration on its nodal equations:
+   * each element stamped as the line of the segment it was on at the last
+   * step (i = c0 + slope u), the system solved, each element moved to the
+   * segment its voltage lies on, until none moves (at most 64 rounds, else
+   * the run fails).  The element joins k and m into one subsystem. */
   int64_t n_nl;
   const int32_t* nl_k;
   const int32_t* nl_m;

@@ -10,8 +10,13 @@ solved by the compensation method against the linear solution).
 * a series-L circuit against a hand-written implicit trapezoidal recursion
   solved by bisection every step;
 * monolithic and partitioned solves agree; invalid descriptions are
-  rejected.
+  rejected;
+* several elements in one subsystem (the piecewise-linear Newton iteration
+  on the nodal equations): on a resistive network every step is a static
+  problem, and each step's solution is the one consistent assignment found
+  by trying every combination of segments.
 """
+import itertools
 import numpy as np
 import pytest
 
@@ -127,10 +132,6 @@ def test_invalid_nonlinear_rejected():
         with pytest.raises(oracle.OracleError):
             oracle.simulate(x, 5)
 
-    sub, _ = oracle.partition(net)
-    same = [x for x in range(net.n_nodes) if sub[x] == sub[net.nl_k[0]] and x != net.nl_k[0]][0]
-    k = net.nl_k.copy(); k[1] = same
-    bad(nl_k=k)                                     # two in one subsystem
     v = net.nl_v.copy(); v[1] = v[0]
     bad(nl_v=v)                                     # breakpoints not increasing
     i = net.nl_i.copy(); i[2] = 0.0
@@ -139,3 +140,103 @@ def test_invalid_nonlinear_rejected():
     bad(nl_k=np.array([-1, net.nl_k[1]], np.int32))  # both ends ground
     with pytest.raises(oracle.OracleError):
         oracle.adjoint(net, 5, np.zeros((5, net.n_nodes)))
+
+
+def three_arrester_ladder(amp=6000.0):
+    """Source -> 2 ohm -> node 0 -> 30 ohm -> node 1 -> 30 ohm -> node 2, 200 ohm
+    loads to ground at each node and an arrester to ground at each node,
+    plus one between nodes 0 and 2: four nonlinear resistors in one
+    subsystem, no storage elements (each step is a static problem)."""
+    vp = [[700.0, 1000.0], [650.0, 900.0], [800.0, 1100.0], [300.0, 500.0]]
+    ip = [[1.0, 40.0], [0.5, 60.0], [2.0, 30.0], [0.2, 20.0]]
+    b = g.NetworkBuilder()
+    b.source(amp, PHI, F)
+    b.branch(g.source_node(0), 0, g.KIND_R, 2.0)
+    b.branch(0, 1, g.KIND_R, 30.0)
+    b.branch(1, 2, g.KIND_R, 30.0)
+    for x in range(3):
+        b.branch(x, g.GROUND, g.KIND_R, 200.0)
+    for (k, m), v_, i_ in zip([(0, g.GROUND), (1, g.GROUND), (2, g.GROUND), (0, 2)], vp, ip):
+        b.nonlinear_resistor(k, m, v_, i_)
+    return b.build(DT, 3), vp, ip
+
+
+def brute_force_step(vs, vp, ip):
+    """Node voltages of the ladder at source voltage vs: every assignment of
+    the four elements to segments (sign x segment) linearised and solved;
+    the assignments whose solution lies on their own segments."""
+    ends = [(0, -1), (1, -1), (2, -1), (0, 2)]
+    G0 = np.zeros((3, 3))
+    def stamp(Gm, k, m, gg):
+        for a in (k, m):
+            if a >= 0:
+                Gm[a, a] += gg
+        if k >= 0 and m >= 0:
+            Gm[k, m] -= gg
+            Gm[m, k] -= gg
+    stamp(G0, 0, -1, 1 / 2.0); stamp(G0, 0, 1, 1 / 30.0); stamp(G0, 1, 2, 1 / 30.0)
+    for x in range(3):
+        stamp(G0, x, -1, 1 / 200.0)
+    segs = []
+    for v_, i_ in zip(vp, ip):
+        pts_v, pts_i = [0.0] + v_, [0.0] + i_
+        lines = []
+        for j in range(3):   # two breakpoints: three segments, the last continued
+            q = min(j, 1)
+            slope = (pts_i[q + 1] - pts_i[q]) / (pts_v[q + 1] - pts_v[q])
+            lo, hi = pts_v[j], (pts_v[j + 1] if j < 2 else np.inf)
+            for sg in (1.0, -1.0):
+                lines.append((sg, lo, hi, slope, sg * (pts_i[j] - slope * pts_v[j])))
+        segs.append(lines)
+    sols = []
+    for combo in itertools.product(*segs):
+        Gm = G0.copy()
+        r = np.array([vs / 2.0, 0.0, 0.0])
+        for (k, m), (sg, lo, hi, slope, c0) in zip(ends, combo):
+            stamp(Gm, k, m, slope)
+            if k >= 0:
+                r[k] -= c0
+            if m >= 0:
+                r[m] += c0
+        x = np.linalg.solve(Gm, r)
+        ok = True
+        for (k, m), (sg, lo, hi, slope, c0) in zip(ends, combo):
+            u = (x[k] if k >= 0 else 0.0) - (x[m] if m >= 0 else 0.0)
+            ok &= (sg * u >= -1e-9 * max(1.0, abs(u))) and lo * (1 - 1e-12) <= abs(u) <= hi * (1 + 1e-12)
+        if ok:
+            sols.append(x)
+    return sols
+
+
+def test_several_in_one_subsystem_match_brute_force():
+    net, vp, ip = three_arrester_ladder()
+    N = 300
+    v = oracle.simulate(net, N)
+    reached = set()
+    for n in range(1, N + 1, 3):
+        sols = brute_force_step(vsrc(n) * 3.0, vp, ip)
+        assert sols, n
+        for x in sols:   # any consistent assignment is the (unique) solution
+            assert np.max(np.abs(x - v[n - 1])) <= 1e-9 * max(1.0, np.max(np.abs(x))), n
+        reached.add(round(float(np.max(np.abs(v[n - 1]))), -2))
+    assert max(reached) > 1000.0        # the elements were driven past their breakpoints
+
+
+def test_several_in_one_subsystem_monolithic_equals_partitioned():
+    base = g.multi_subsystem(43, [4, 5, 3], n_lines=4, n_sources=2, dt=DT)
+    net, vp, ip = base, None, None
+    b_nodes = net.meta["bus_nodes"]
+    sub, _ = oracle.partition(net)
+    # three arresters in the first source bus's subsystem, one in another
+    first = b_nodes[net.meta["source_bus"][0]]
+    others = [x for x in range(net.n_nodes) if sub[x] != sub[first[0]]]
+    bb = g.NetworkBuilder()
+    for x in list(first) + [others[0]]:
+        bb.nonlinear_resistor(int(x), g.GROUND, [v * 0.6 for v in g.ARRESTER_V], g.ARRESTER_I)
+    nl = bb.build(DT, 0)
+    for f_ in ("nl_k", "nl_m", "nl_np", "nl_v", "nl_i"):
+        setattr(net, f_, getattr(nl, f_))
+    N = 2000
+    a = oracle.simulate(net, N)
+    m = oracle.simulate(net, N, monolithic=True)
+    assert np.max(np.abs(a - m)) / np.max(np.abs(m)) <= 1e-12
