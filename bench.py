@@ -38,6 +38,11 @@ two further legs the metric names, reported as extra keys of the line:
       method, against the plain one;
   "controls": the same with 180 converter loads (4,320 layered control
       blocks driving controlled current injections), against the plain one;
+  "converter_stations": the same with 10 two-bridge diode converter stations
+      (12 valves per subsystem, states factorised on the device), against
+      the plain one;
+  "bus_arresters": the same with arresters on all phases of 20 buses (three
+      nonlinear resistors per subsystem), against the plain one;
   "sizes": the same family as 500 subsystems of 6 nodes, and as 500
       subsystems of 6..60 nodes (16,500 nodes, packed several to a CTA).
 
@@ -604,6 +609,40 @@ def nonlinear_leg(steps=None, reps=3):
                        "method; all nodes recorded", steps, reps, active)
 
 
+def station_leg(steps=None, reps=3):
+    """The large-scale network with 10 converter stations of two six-pulse
+    diode bridges each (12 valves in one subsystem: switch states factorised
+    on the device when first met)."""
+    import oracle
+    from paper_1903_01081_b300 import netgen as g
+
+    def states(net, n):
+        st = oracle.runtime_switch_states(net, n)
+        return {"runtime_switches": int(net.n_runtime_switches),
+                "state_changes_in_checked_steps": int(np.sum(st[1:] != st[:-1])),
+                "distinct_network_states_in_checked_steps": len({tuple(r) for r in st})}
+    return variant_leg(g.with_converter_stations(g.large_scale(), n_stations=10),
+                       "large-scale network plus 10 converter stations (two six-pulse diode bridges each, 12 valves "
+                       "with snubbers in one subsystem, commutation inductances, R-C DC loads); switch states "
+                       "factorised on the device the first time they occur; all nodes recorded", steps, reps, states)
+
+
+def bus_arrester_leg(steps=None, reps=3):
+    """The large-scale network with three-phase arrester sets at 20 buses
+    (three nonlinear resistors per subsystem, solved together)."""
+    import oracle
+    from paper_1903_01081_b300 import netgen as g
+
+    def active(net, n):
+        v = oracle.simulate(net, n, rec=net.nl_k)
+        knee = np.asarray(net.nl_v).reshape(-1, 8)[:, 0]
+        return {"nonlinear_resistors": int(net.n_nonlinear),
+                "conducting_in_checked_steps": int(np.sum(np.max(np.abs(v), axis=0) > knee))}
+    return variant_leg(g.with_bus_arresters(g.large_scale(), n_buses=20),
+                       "large-scale network plus surge arresters on all three phases of 20 buses (3 per subsystem, "
+                       "solved together through their Thevenin matrix); all nodes recorded", steps, reps, active)
+
+
 def control_leg(steps=None, reps=3):
     """The large-scale network with 180 power-regulated converter loads, each
     24 layered control blocks driving three controlled current injections."""
@@ -846,7 +885,8 @@ def run_ours(args):
             "parity_rel_err_first_2000_steps": parity,
             **({"scenarios": scenario_legs(cpu=True), "adjoint": adjoint_leg(), "small_network": small_network_leg(), "runtime_switches": runtime_switch_leg(),
                 "coupled_lines": coupled_line_leg(), "fd_lines": fd_line_leg(), "nonlinear": nonlinear_leg(),
-                "controls": control_leg(), "sizes": scale_legs()}
+                "controls": control_leg(), "converter_stations": station_leg(),
+                "bus_arresters": bus_arrester_leg(), "sizes": scale_legs()}
                if args.leg == "all" else {}),
         }
         print(json.dumps(line), flush=True)
@@ -866,7 +906,8 @@ def main():
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines",
                                       "fd_lines", "nonlinear", "controls", "sizes", "control_study",
-                                      "arrester_study", "fd_line_study", "coupled_line_study"],
+                                      "arrester_study", "fd_line_study", "coupled_line_study", "converter_stations",
+                                      "bus_arresters"],
                     default="all",
                     help="all: the JSON line with every leg; single: the single-network leg only; "
                          "n1 / shared_g / adjoint: that leg alone (profiling)")
@@ -884,7 +925,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "fd_lines", "nonlinear",
-                    "controls", "sizes", "control_study", "arrester_study", "fd_line_study", "coupled_line_study"):
+                    "controls", "sizes", "control_study", "arrester_study", "fd_line_study", "coupled_line_study",
+                    "converter_stations", "bus_arresters"):
         return run_leg(args)
     return run_ours(args)
 
@@ -905,6 +947,10 @@ def run_leg(args):
         out = fd_line_leg(args.leg_steps, reps=1)
     elif args.leg == "nonlinear":
         out = nonlinear_leg(args.leg_steps, reps=1)
+    elif args.leg == "converter_stations":
+        out = station_leg(args.leg_steps, reps=1)
+    elif args.leg == "bus_arresters":
+        out = bus_arrester_leg(args.leg_steps, reps=1)
     elif args.leg == "sizes":
         out = scale_legs(args.leg_steps, reps=1)
     elif args.leg in ("control_study", "arrester_study", "fd_line_study", "coupled_line_study"):

@@ -68,7 +68,7 @@ struct emt_ctx {
   std::vector<CoupledEndDev> cends;                    // coupled line ends, grouped by subsystem
   std::vector<int32_t> rs_word0;                       // per subsystem: state word at step 1
   std::vector<FdEndDev> fdends;                        // frequency-dependent line ends, grouped by subsystem
-  std::vector<NlDev> nls;                              // nonlinear resistors, one per subsystem at most
+  std::vector<NlDev> nls;                              // nonlinear resistors, grouped by subsystem
   int64_t nlz_len = 0;                                 // doubles of their columns over all matrix entries
   std::vector<CtrlDev> cblocks;                        // control blocks, grouped by subsystem, by layer
   std::vector<int32_t> clay, cinj;                     // layer starts; block slot per control injection
@@ -80,7 +80,7 @@ struct emt_ctx {
   // subsystems that factorise their switch states at run time (SubDev::n_cache)
   bool lazy = false;
   std::vector<long long> cache_tag0;   // initial tags of every cache slot
-  std::vector<int32_t> cache_next0;    // per subsystem: initial slot to replace next
+  std::vector<int32_t> cache_next0;    // per subsystem: initial slot to replace next; then 0 (factorisations)
   int64_t lazy_work_len = 0;
   long long* d_cache_tag = nullptr;
   long long* d_cache_tag0 = nullptr;
@@ -124,6 +124,7 @@ struct emt_ctx {
   double* d_rs_prev_i = nullptr;
   FdEndDev* d_fd = nullptr;
   NlDev* d_nl = nullptr;
+  int32_t* d_nl_seg = nullptr;                         // per nonlinear resistor: its segment at the last step
   double* d_nlz = nullptr;
   float* d_nlz_lo = nullptr;
   double* d_fd_state = nullptr;
@@ -1514,34 +1515,34 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   // -------- nonlinear resistors (compensation method): at most one per
   // subsystem, the odd characteristic as segments from (0, 0)
   {
-    std::vector<int64_t> nl_of(S, -1);
+    std::vector<std::vector<int64_t>> nl_of(S);
+    const int max_nl = scen ? 1 : kNlMaxPerSub;
     for (int64_t x = 0; x < d->n_nonlin; ++x) {
       const int a = d->nl_k[x] >= 0 ? d->nl_k[x] : d->nl_m[x];
       const int sb = c->sub_of_node[a];
-      if (nl_of[sb] >= 0)
-        return bail("subsystem " + std::to_string(sb) + " has more than one nonlinear resistor (nonlinear resistors " +
-                    std::to_string(nl_of[sb]) + " and " + std::to_string(x) + ")");
-      nl_of[sb] = x;
+      nl_of[sb].push_back(x);
+      if ((int)nl_of[sb].size() > max_nl)
+        return bail("subsystem " + std::to_string(sb) + " has more than " + std::to_string(max_nl) +
+                    " nonlinear resistors" + (scen ? " (in a scenario set)" : ""));
     }
     for (int s = 0; s < S; ++s) {
       SubDev& sd = c->subs[s];
       sd.nl_off = (int)c->nls.size();
-      sd.n_nl = 0;
-      const int64_t x = nl_of[s];
-      if (x < 0) continue;
-      NlDev q{};
-      q.k = d->nl_k[x] >= 0 ? local[d->nl_k[x]] : -1;
-      q.m = d->nl_m[x] >= 0 ? local[d->nl_m[x]] : -1;
-      q.np = d->nl_np[x];
-      for (int j = 0; j < q.np; ++j) {
-        q.bv[j + 1] = d->nl_v[kNlMaxPoints * x + j];
-        q.bi[j + 1] = d->nl_i[kNlMaxPoints * x + j];
+      sd.n_nl = (int)nl_of[s].size();
+      for (int64_t x : nl_of[s]) {
+        NlDev q{};
+        q.k = d->nl_k[x] >= 0 ? local[d->nl_k[x]] : -1;
+        q.m = d->nl_m[x] >= 0 ? local[d->nl_m[x]] : -1;
+        q.np = d->nl_np[x];
+        for (int j = 0; j < q.np; ++j) {
+          q.bv[j + 1] = d->nl_v[kNlMaxPoints * x + j];
+          q.bi[j + 1] = d->nl_i[kNlMaxPoints * x + j];
+        }
+        for (int j = 0; j < q.np; ++j) q.sl[j] = (q.bi[j + 1] - q.bi[j]) / (q.bv[j + 1] - q.bv[j]);
+        q.sl[q.np] = q.sl[q.np - 1];   // past the last point, the last slope
+        c->nls.push_back(q);
       }
-      for (int j = 0; j < q.np; ++j) q.sl[j] = (q.bi[j + 1] - q.bi[j]) / (q.bv[j + 1] - q.bv[j]);
-      q.sl[q.np] = q.sl[q.np - 1];   // past the last point, the last slope
-      c->nls.push_back(q);
-      sd.n_nl = 1;
-      c->lim.nl = 1;
+      c->lim.nl = std::max(c->lim.nl, sd.n_nl);
     }
   }
 
@@ -1753,7 +1754,7 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
         sd.cache_goff = goff;
         goff += (int64_t)sd.n_cache * mat_len;
         sd.cache_zoff = c->nlz_len;
-        if (sd.n_nl > 0) c->nlz_len += (int64_t)sd.n_cache * sd.n;
+        c->nlz_len += (int64_t)sd.n_cache * sd.n_nl * sd.n;
         sd.work_off = c->lazy_work_len;
         c->lazy_work_len += 2 * (int64_t)sd.n * sd.n;
         for (int j = 0; j < sd.n_cache; ++j)
@@ -1775,12 +1776,12 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
             goff += mat_len;
           }
           E.nlz_off = -1;
-          if (sd.n_nl > 0) {
+          if (sd.n_nl > 0) {   // one column per nonlinear resistor
             if (lazy) {
-              E.nlz_off = sd.cache_zoff + (int64_t)te * sd.n;
+              E.nlz_off = sd.cache_zoff + (int64_t)te * sd.n_nl * sd.n;
             } else {
               E.nlz_off = c->nlz_len;
-              c->nlz_len += sd.n;
+              c->nlz_len += (int64_t)sd.n_nl * sd.n;
             }
           }
           E.rs_word = lazy ? word0 : -1;
@@ -1808,6 +1809,7 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
       sd.n_ep = (int)c->epochs.size() - sd.ep_off;
     }
     c->ginv_len = goff;
+    c->cache_next0.push_back(0);   // the count of run-time factorisations
   }
 
   // -------- matvec blocking: a task's n/q FMAs and a node's q-1 adds are
@@ -1879,6 +1881,10 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   UP(d_rs_word, rs_word0)
   UP(d_fd, fdends)
   UP(d_nl, nls)
+  if (e == cudaSuccess && !c->nls.empty()) {
+    const std::vector<int32_t> one(c->nls.size(), 1);
+    e = c->upload(&c->d_nl_seg, one);
+  }
   UP(d_cb, cblocks)
   UP(d_clay, clay)
   UP(d_cinj, cinj)
@@ -2278,6 +2284,7 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
   p.nl = c->d_nl;
   p.nlz = c->d_nlz;
   p.nlz_lo = c->d_nlz_lo;
+  p.nl_seg = c->d_nl_seg;
   p.cb = c->d_cb;
   p.clay = c->d_clay;
   p.cinj = c->d_cinj;
@@ -2306,7 +2313,7 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
     if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n source table");
     p.n0 = c->step + 1;
     p.n_steps = len;
-    e = launch_forward(p, st, !c->forward_narrow, c->lazy);
+    e = launch_forward(p, st, !c->forward_narrow, c->lazy || c->lim.nl > 1);
     if (e == cudaErrorCooperativeLaunchTooLarge)
       return c->fail(EMT_ERESOURCE, "persistent launch of " + std::to_string(c->n_sub) +
                                         " CTAs cannot be co-resident on this device");
@@ -2357,6 +2364,9 @@ extern "C" emt_status emt_sync(emt_ctx* c, int32_t* info) {
   if (h[0] == EMT_ETIMEOUT)
     return c->fail(EMT_ETIMEOUT, "subsystem " + std::to_string(h[1]) + " timed out at step " + std::to_string(h[3]) +
                                      " waiting for the value of its line end " + std::to_string(h[2]));
+  if (h[0] == kErrNoSegments)
+    return c->fail(EMT_ESTATE, "the nonlinear resistors of subsystem " + std::to_string(h[1]) +
+                                   " found no consistent segments at step " + std::to_string(h[3]));
   if (h[0] == EMT_ESINGULAR)
     return c->fail(EMT_ESINGULAR, "conductance matrix of subsystem " + std::to_string(h[1]) + " in switch epoch " +
                                       std::to_string(h[3]) + ", runtime-switch state word " + std::to_string(h[2]) +
@@ -2516,6 +2526,10 @@ extern "C" emt_status emt_reset(emt_ctx* c) {
     e = cudaMemset(c->d_fd_state, 0, kFdState * c->fdends.size() * sizeof(double));
   if (e == cudaSuccess && !c->cblocks.empty()) e = cudaMemset(c->d_cstate, 0, 2 * c->cblocks.size() * sizeof(double));
   if (e == cudaSuccess && !c->cblocks.empty()) e = cudaMemset(c->d_cy, 0, c->cblocks.size() * sizeof(double));
+  if (e == cudaSuccess && !c->nls.empty()) {   // every nonlinear resistor on its first positive segment
+    const std::vector<int32_t> one(c->nls.size(), 1);
+    e = cudaMemcpy(c->d_nl_seg, one.data(), one.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+  }
   if (c->batched) {
     if (e == cudaSuccess) e = cudaMemset(c->d_bh, 0, std::max<size_t>((size_t)c->n_lc_total * c->S, 1) * sizeof(double));
     if (e == cudaSuccess)
@@ -2673,6 +2687,12 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
     int64_t m = 0;
     for (const SubDev& sd : c->subs) m += sd.n_cache > 0 ? 1 : 0;
     *value = m;
+  } else if (k == "runtime_factorisations") {   // switch states factorised by the kernel since the prefactor
+    int32_t v = 0;
+    cudaDeviceSynchronize();
+    if (c->lazy && cudaMemcpy(&v, c->d_cache_next + c->n_sub, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return EMT_ECUDA;
+    *value = v;
   } else if (k == "factorised_states") {   // solve matrices held by their caches (synchronises the device)
     std::vector<long long> tag(c->cache_tag0.size());
     cudaDeviceSynchronize();

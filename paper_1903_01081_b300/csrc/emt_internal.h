@@ -125,7 +125,7 @@ struct SubDev {
   int32_t clay_off, n_clay;    // control layers: n_clay + 1 starts in clay (with the layer's type, see kLayerTypeShift)
   int32_t ci_off, n_ci;        // control injections: local block slot per injection in cinj
   int32_t fd_off, n_fd;        // frequency-dependent line ends (FdEndDev list)
-  int32_t nl_off, n_nl;        // nonlinear resistor (NlDev list; at most one)
+  int32_t nl_off, n_nl;        // nonlinear resistors (NlDev list; at most kNlMaxPerSub)
   // More than kMaxRuntimeSwitches runtime switches: the solve matrix of a
   // (switch epoch, state word) is factorised by the CTA when the state is
   // first met (process 3 at run time) into one of n_cache slots, slot j at
@@ -143,6 +143,14 @@ struct SubDev {
 // (EpochDev::nlz_off); the step solves i = f(v_th - R_th i) against the
 // linear solution, R_th = z_k - z_m, and corrects v by -z i.
 constexpr int kNlMaxPoints = 8;
+// Nonlinear resistors per subsystem (single networks; one in scenario
+// sets).  With several, each solve matrix entry carries one column per
+// element, z_j = G^-1 (e_kj - e_mj) at EpochDev::nlz_off + j n, and the step
+// solves the elements together through the Thevenin matrix R = A^T Z.
+constexpr int kNlMaxPerSub = 4;
+// Device error code: the piecewise-linear iteration of a subsystem's
+// nonlinear resistors found no consistent segments (reported as EMT_ESTATE).
+constexpr int kErrNoSegments = 100;
 struct NlDev {
   int32_t k, m;        // subsystem-local ends, -1 = ground
   int32_t np;          // breakpoints after (0, 0)
@@ -177,7 +185,7 @@ constexpr int kMixedLayer = 15;
 constexpr int kMaxRuntimeSwitches = 8;
 constexpr int kMaxLazySwitches = 30;
 // Cache slots per such subsystem beyond one per epoch.
-constexpr int kLazyCacheExtra = 64;
+constexpr int kLazyCacheExtra = 256;
 
 // A runtime switch in device form: a two-state resistor whose state in
 // force at step n is decided from step n-1's solution.  Bit `j` (its index
@@ -222,7 +230,7 @@ struct FwdLimits {
   int32_t ce;                  // coupled line ends per subsystem
   int32_t cb, clay, ci;        // control blocks, layers + 1 and injections per subsystem
   int32_t fd;                  // frequency-dependent line ends per subsystem
-  int32_t nl;                  // 1 if some subsystem has a nonlinear resistor
+  int32_t nl;                  // most nonlinear resistors in one subsystem
 };
 
 struct FwdParams {
@@ -271,15 +279,16 @@ struct FwdParams {
   const FdEndDev* fd;          // frequency-dependent line ends (SubDev fd_off / n_fd)
   double* fd_state;            // per FD end: s[4], z[4], v(n-1), W(n-1), Hy(n) (11 doubles, carried)
   const NlDev* nl;             // nonlinear resistors (SubDev nl_off / n_nl)
-  const double* nlz;           // their columns z per solve matrix entry (EpochDev::nlz_off)
+  const double* nlz;           // their columns z per solve matrix entry (EpochDev::nlz_off, n per element)
   const float* nlz_lo;         // z minus that rounding, in single precision
+  int32_t* nl_seg;             // per nonlinear resistor: its segment at the last step, sign * (j + 1) (carried)
   // run-time factorisation (SubDev::n_cache > 0): the same arrays, writable
   double* ginv_rw;
   float* ginv_lo_rw;
   double* nlz_rw;
   float* nlz_lo_rw;
   long long* cache_tag;        // per cache slot: (epoch << 32) | state word, or -1
-  int32_t* cache_next;         // per subsystem: next slot to replace
+  int32_t* cache_next;         // per subsystem: next slot to replace; then the count of run-time factorisations
   double* lazy_work;
   const SwitchDev* sw;         // closed switches of each epoch (EpochDev sw_off / n_sw)
 };
@@ -526,8 +535,9 @@ cudaError_t launch_coupled_constants(CoupledEndDev* ce, int64_t n_ce, cudaStream
 cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st);
 cudaError_t launch_sources(const SourceParams& p, cudaStream_t st);
 // wide = false: the 64-register build only (while another persistent grid shares the device);
-// lazy: some subsystem factorises its switch states at run time (SubDev::n_cache > 0)
-cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide = true, bool lazy = false);
+// ext: some subsystem factorises its switch states at run time (SubDev::n_cache > 0) or holds
+// several nonlinear resistors
+cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide = true, bool ext = false);
 size_t forward_smem_bytes(const FwdLimits& lim);
 int forward_blocks_per_sm(const FwdLimits& lim);   // resident CTAs per SM (0 on error)
 cudaError_t launch_batch(const BatchParams& p, int threads, cudaStream_t st, BatchGraph* graph);

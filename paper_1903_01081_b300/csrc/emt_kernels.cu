@@ -293,10 +293,11 @@ __device__ __noinline__ bool factor_cta(const FactorJob& J, double* A, double* f
     out[i * nc + n + t] = s;
     out_lo[i * nc + n + t] = (float)e;
   }
-  // the nonlinear resistor's column G^-1 (e_k - e_m), formed the same way
+  // each nonlinear resistor's column G^-1 (e_k - e_m), formed the same way
   if (S.n_nl > 0 && J.nlz != nullptr) {
-    const NlDev& q = J.nl[S.nl_off];
-    for (int i = tid; i < n; i += T) {
+    for (int idx = tid; idx < n * S.n_nl; idx += T) {
+      const int x = idx / n, i = idx - x * n;
+      const NlDev& q = J.nl[S.nl_off + x];
       const double a = q.k >= 0 ? out[i * nc + q.k] : 0.0, b = q.m >= 0 ? out[i * nc + q.m] : 0.0;
       const double al = q.k >= 0 ? (double)out_lo[i * nc + q.k] : 0.0;
       const double bl = q.m >= 0 ? (double)out_lo[i * nc + q.m] : 0.0;
@@ -304,8 +305,8 @@ __device__ __noinline__ bool factor_cta(const FactorJob& J, double* A, double* f
       two_sum(a, -b, d1, e1);
       double s, e;
       two_sum(d1, e1 + (al - bl), s, e);
-      J.nlz[i] = s;
-      J.nlz_lo[i] = (float)e;
+      J.nlz[idx] = s;
+      J.nlz_lo[idx] = (float)e;
     }
   }
   __syncthreads();
@@ -402,14 +403,25 @@ constexpr int kItemThreads = kFwdThreads - 32;
 // it is used (only CTAs with a nonlinear resistor), so that the step loop of
 // the others keeps no extra pointer live.
 struct NlState {
-  NlDev q;
+  NlDev q[kNlMaxPerSub];
   double c[1 + 3 * (kNlMaxPoints + 1)];
   double inl;
   long long row;
   int dirty;
-  int pad;
+  int m;                                 // elements (several: the fields below)
+  double R[kNlMaxPerSub * kNlMaxPerSub];   // Thevenin matrix R_jl = z_l[k_j] - z_l[m_j]
+  double minv[kNlMaxPerSub * kNlMaxPerSub];  // (I + D R)^-1 for the slopes of minv_key
+  double work[kNlMaxPerSub * kNlMaxPerSub];  // its elimination
+  double cur[kNlMaxPerSub];              // element currents of the step
+  double c0[kNlMaxPerSub], slope[kNlMaxPerSub];   // the current segments' lines
+  double a[kNlMaxPerSub], f[kNlMaxPerSub];        // c = a + B y, u = E y - f for the current segments
+  double B[kNlMaxPerSub * kNlMaxPerSub], E[kNlMaxPerSub * kNlMaxPerSub];
+  int seg[kNlMaxPerSub];                 // segments, sign * (j + 1)
+  int minv_key;                          // segment indices (4 bits each) minv belongs to, -1: none
+  int coef_key;                          // segments with signs (5 bits each) a, B, E, f belong to, -1: none
+  // the columns z_j (m n doubles), then their single-precision remainders
   __device__ double* z() { return reinterpret_cast<double*>(this + 1); }
-  __device__ float* zl(int n) { return reinterpret_cast<float*>(z() + n); }
+  __device__ float* zl(int n, int m = 1) { return reinterpret_cast<float*>(z() + (size_t)m * n); }
 };
 
 // Shared-memory layout of fwd_kernel, from the per-launch limits.  G^-1
@@ -452,7 +464,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.cbr = d16(sizeof(CtrlDev) / 8 * (size_t)L.cb);
   s.cy = d16(2 * (size_t)L.cb + 2);
   s.cs = d16(2 * (size_t)L.cb);
-  s.nls = d(L.nl ? sizeof(NlState) / 8 + (size_t)L.n + ((size_t)L.n + 1) / 2 : 0);
+  s.nls = d(L.nl ? sizeof(NlState) / 8 + (size_t)L.nl * L.n + ((size_t)L.nl * L.n + 1) / 2 : 0);
   s.fdr = d(sizeof(FdEndDev) / 8 * (size_t)L.fd);
   s.fdst = d(kFdState * (size_t)L.fd);
   s.gilo = w(nbuf * (size_t)L.n * ldg);
@@ -615,17 +627,220 @@ __device__ __forceinline__ void compensate(const FwdParams& P, int n, NlState* s
   const float* zl = s->zl(n);
   if (tid == 0) {
     if (s->dirty) {
-      nl_setup(s->q, z, zl, s->c);
+      nl_setup(s->q[0], z, zl, s->c);
       s->dirty = 0;
     }
-    const double vth = (s->q.k >= 0 ? vv[s->q.k] : 0.0) - (s->q.m >= 0 ? vv[s->q.m] : 0.0);
-    s->inl = nl_current(s->q, s->c, vth);
+    const double vth = (s->q[0].k >= 0 ? vv[s->q[0].k] : 0.0) - (s->q[0].m >= 0 ? vv[s->q[0].m] : 0.0);
+    s->inl = nl_current(s->q[0], s->c, vth);
   }
   __syncthreads();
   const double inl = s->inl;
   const long long row = s->row;
   for (int r = tid; r < n; r += T) {
     const double v = fma(-(double)zl[r], inl, fma(-z[r], inl, vv[r]));
+    vv[r] = v;
+    if (row >= 0 && recp[r] >= 0) P.rec[(row - P.rec_row0) * P.n_rec + recp[r]] = v;
+  }
+  __syncthreads();
+}
+
+// Segment of nonlinear resistor q that holds the voltage u: sign * (j + 1),
+// j the number of breakpoints at or below |u| (independent integer compares
+// of the bit patterns, which order non-negative doubles).
+__device__ __forceinline__ int nl_segment_of(const NlDev& q, double u) {
+  const long long bu = __double_as_longlong(u);
+  const long long kx = bu & 0x7fffffffffffffffll;   // |u|
+  int j = 0;
+#pragma unroll
+  for (int p = 1; p <= kNlMaxPoints; ++p)
+    j += (p <= q.np && kx >= __double_as_longlong(q.bv[p])) ? 1 : 0;
+  return bu < 0 ? -(j + 1) : j + 1;
+}
+
+// (I + D R)^-1 of the current segments' slopes D into s->minv (Gauss-Jordan
+// with partial pivoting, on one thread, in the state's shared memory; it
+// runs only when a segment's slope changes).
+__device__ __forceinline__ void nl_invert(NlState* s, int m) {
+  constexpr int W = kNlMaxPerSub;
+  double* M = s->work;
+  double* X = s->minv;
+  for (int j = 0; j < m; ++j)
+    for (int l = 0; l < m; ++l) {
+      M[j * W + l] = fma(s->q[j].sl[abs(s->seg[j]) - 1], s->R[j * W + l], j == l ? 1.0 : 0.0);
+      X[j * W + l] = j == l ? 1.0 : 0.0;
+    }
+  for (int k = 0; k < m; ++k) {
+    int p = k;
+    for (int i = k + 1; i < m; ++i)
+      if (fabs(M[i * W + k]) > fabs(M[p * W + k])) p = i;
+    for (int l = 0; l < m; ++l) {
+      double t = M[k * W + l];
+      M[k * W + l] = M[p * W + l];
+      M[p * W + l] = t;
+      t = X[k * W + l];
+      X[k * W + l] = X[p * W + l];
+      X[p * W + l] = t;
+    }
+    const double inv = 1.0 / M[k * W + k];
+    for (int l = 0; l < m; ++l) {
+      M[k * W + l] *= inv;
+      X[k * W + l] *= inv;
+    }
+    for (int i = 0; i < m; ++i) {
+      if (i == k) continue;
+      const double f = M[i * W + k];
+      for (int l = 0; l < m; ++l) {
+        M[i * W + l] = fma(-f, M[k * W + l], M[i * W + l]);
+        X[i * W + l] = fma(-f, X[k * W + l], X[i * W + l]);
+      }
+    }
+  }
+}
+
+// Several nonlinear resistors in the CTA (m >= 2), the compensation method
+// with the Thevenin matrix R = A^T Z: with each element on a segment's line
+// i = c0 + slope u, the currents solve (I + D R) c = c0 + D y, D =
+// diag(slope), y = A^T v0 (v0 the linear solution), i.e. c = a + B y and
+// the element voltages u = y - R c = E y - f, with M = (I + D R)^-1,
+// a = M c0, B = M D, E = I - R B, f = R a, all fixed while the segments are;
+// each element is moved to the segment its voltage lies on until none
+// moves, starting from the last step's segments; then v -= Z c.  Warp 0,
+// lane j = element j; M is kept while the slopes stay (a sign change keeps
+// them), a, B, E, f while the segments stay.  Every thread of the CTA calls
+// it (two barriers inside).
+__device__ void compensate_multi(const FwdParams& P, int n, int m, NlState* s, double* vv, const int* recp,
+                                 int* seg_g, int sidx, long long step, int* abort_flag) {
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31;
+  const double* z = s->z();
+  const float* zl = s->zl(n, m);
+  constexpr int W = kNlMaxPerSub;
+  if (tid < 32) {
+    if (s->dirty) {   // a newly loaded matrix: its Thevenin matrix
+      if (lane < m * m) {
+        const int j = lane / m, l = lane - j * m;
+        const NlDev& q = s->q[j];
+        const double* zc = z + (size_t)l * n;
+        const float* zlc = zl + (size_t)l * n;
+        const double a = q.k >= 0 ? zc[q.k] + (double)zlc[q.k] : 0.0;
+        const double b = q.m >= 0 ? zc[q.m] + (double)zlc[q.m] : 0.0;
+        s->R[j * W + l] = a - b;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        s->dirty = 0;
+        s->minv_key = -1;
+        s->coef_key = -1;
+      }
+      __syncwarp();
+    }
+    double y = 0.0;
+    if (lane < m) {
+      const NlDev& q = s->q[lane];
+      y = (q.k >= 0 ? vv[q.k] : 0.0) - (q.m >= 0 ? vv[q.m] : 0.0);
+    }
+    double yl[W];   // every element's y on every lane (0 past the m elements)
+#pragma unroll
+    for (int l = 0; l < W; ++l) yl[l] = __shfl_sync(0xffffffffu, y, l);
+    bool settled = false;
+    double cc = 0.0;
+    for (int it = 0; it < 32 && !settled; ++it) {
+      int key = 0, full = 0;
+      for (int j = 0; j < m; ++j) {
+        key |= (abs(s->seg[j]) - 1) << (4 * j);
+        full |= (s->seg[j] + 9) << (5 * j);   // with the signs
+      }
+      if (full != s->coef_key) {   // new segments: M (if the slopes changed), then a, B, E, f
+        if (key != s->minv_key) {
+          if (lane == 0) {
+            nl_invert(s, m);
+            s->minv_key = key;
+          }
+          __syncwarp();
+        }
+        if (lane < m) {
+          const NlDev& q = s->q[lane];
+          const int sg = s->seg[lane], jj = abs(sg) - 1;
+          const double c0 = fma(-q.sl[jj], q.bv[jj], q.bi[jj]);
+          s->c0[lane] = sg < 0 ? -c0 : c0;
+          s->slope[lane] = q.sl[jj];
+        }
+        __syncwarp();
+        if (lane < m) {
+          double a = 0.0;
+          for (int l = 0; l < W; ++l) {
+            if (l < m) a = fma(s->minv[lane * W + l], s->c0[l], a);
+            s->B[lane * W + l] = l < m ? s->minv[lane * W + l] * s->slope[l] : 0.0;
+          }
+          s->a[lane] = a;
+        }
+        __syncwarp();
+        if (lane < m) {
+          double f = 0.0;
+          for (int l = 0; l < W; ++l) {
+            if (l < m) f = fma(s->R[lane * W + l], s->a[l], f);
+            double rb = 0.0;
+            for (int p = 0; p < m; ++p) rb = fma(s->R[lane * W + p], s->B[p * W + l], rb);
+            s->E[lane * W + l] = l < m ? (lane == l ? 1.0 : 0.0) - rb : 0.0;
+          }
+          s->f[lane] = f;
+        }
+        __syncwarp();
+        if (lane == 0) s->coef_key = full;
+        __syncwarp();
+      }
+      // c = a + B y and u = E y - f: two independent dot products per lane
+      double c = 0.0, u = 0.0;
+      if (lane < m) {   // (B and E are zero past the m elements)
+        c = s->a[lane];
+        u = -s->f[lane];
+#pragma unroll
+        for (int l = 0; l < W; ++l) {
+          c = fma(s->B[lane * W + l], yl[l], c);
+          u = fma(s->E[lane * W + l], yl[l], u);
+        }
+      }
+      int sg = 0;
+      bool moved = false;
+      if (lane < m) {
+        sg = nl_segment_of(s->q[lane], u);
+        moved = sg != s->seg[lane];
+      }
+      if (__any_sync(0xffffffffu, moved)) {
+        __syncwarp();
+        if (lane < m) s->seg[lane] = sg;
+        __syncwarp();
+      } else {
+        settled = true;
+        cc = c;
+      }
+    }
+    if (lane < m) {
+      s->cur[lane] = cc;
+      seg_g[lane] = s->seg[lane];
+    }
+    if (!settled && lane == 0) {
+      if (atomicCAS(P.err, 0, kErrNoSegments) == 0) {
+        P.err[1] = sidx;
+        P.err[2] = -1;
+        P.err[3] = (int)step;
+      }
+      *abort_flag = 1;
+    }
+  }
+  __syncthreads();
+  const long long row = s->row;
+  double cur[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) cur[j] = j < m ? s->cur[j] : 0.0;
+  for (int r = tid; r < n; r += T) {   // the remainders' products first (each column's conversion on the integer pipe)
+    double lo = 0.0, hi = vv[r];
+#pragma unroll
+    for (int j = 0; j < W; ++j)
+      if (j < m) {
+        lo = fma(f64_of(zl[(size_t)j * n + r]), cur[j], lo);
+        hi = fma(-z[(size_t)j * n + r], cur[j], hi);
+      }
+    const double v = hi - lo;
     vv[r] = v;
     if (row >= 0 && recp[r] >= 0) P.rec[(row - P.rec_row0) * P.n_rec + recp[r]] = v;
   }
@@ -688,14 +903,15 @@ __device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int la
 // networks of many subsystems) and at most 128 (two per SM): the second
 // keeps more of the step loop's state in registers and is used whenever its
 // residency holds every CTA.
-// kLazy: the network has subsystems whose states are factorised at run time
-// (the code for that is compiled only into those instances, so that the
-// step loop of every other network keeps its registers).
-template <int kMinBlocks, bool kLazy>
+// kExt: the network has subsystems that factorise their switch states at
+// run time or hold several nonlinear resistors (the code for those is
+// compiled only into these instances, so that the step loop of every other
+// network keeps its registers).
+template <int kMinBlocks, bool kExt>
 __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_abort;
-  constexpr int kRs = kLazy ? kMaxLazySwitches : kMaxRuntimeSwitches;
+  constexpr int kRs = kExt ? kMaxLazySwitches : kMaxRuntimeSwitches;
   __shared__ RuntimeSwitchDev s_rs[kRs];
   __shared__ double s_rsi[kRs];   // breaker currents of the previous step
   __shared__ int s_rsbit[kRs];    // states decided for the next step
@@ -909,8 +1125,8 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
     J.rm_br = J.rm_le = nullptr;
     J.out = P.ginv_rw + S.cache_goff + (int64_t)slot * n * nc;
     J.out_lo = P.ginv_lo_rw + S.cache_goff + (int64_t)slot * n * nc;
-    J.nlz = S.n_nl > 0 ? P.nlz_rw + S.cache_zoff + (int64_t)slot * n : nullptr;
-    J.nlz_lo = S.n_nl > 0 ? P.nlz_lo_rw + S.cache_zoff + (int64_t)slot * n : nullptr;
+    J.nlz = S.n_nl > 0 ? P.nlz_rw + S.cache_zoff + (int64_t)slot * S.n_nl * n : nullptr;
+    J.nlz_lo = S.n_nl > 0 ? P.nlz_lo_rw + S.cache_zoff + (int64_t)slot * S.n_nl * n : nullptr;
     J.Gw = P.lazy_work + S.work_off;
     J.Rw = J.Gw + (size_t)n * n;
     // workspaces: the buffer the matrix is loaded into next, and the solve's partial sums
@@ -922,10 +1138,13 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
       }
       return -1;
     }
-    if (tid == 0) P.cache_tag[S.cache_slot0 + slot] = key;
+    if (tid == 0) {
+      P.cache_tag[S.cache_slot0 + slot] = key;
+      atomicAdd(P.cache_next + P.n_sub, 1);   // run-time factorisations so far (the counter after the slots)
+    }
     return slot;
   };
-  const bool lazy = kLazy && S.n_cache > 0;
+  const bool lazy = kExt && S.n_cache > 0;
   {
     bool factored;
     const int entry = lazy ? lazy_slot(te, word, 0, factored) : te * n_states + word;
@@ -946,14 +1165,19 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   const int n_nl = S.n_nl;
   if (n_nl > 0 && tag_cur >= 0) {
     NlState* nls = reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls);
+    for (int x = tid; x < n_nl; x += T) nls->q[x] = P.nl[S.nl_off + x];
+    if (kExt)   // several elements: their segments of the last step
+      for (int x = tid; x < n_nl; x += T) nls->seg[x] = P.nl_seg[S.nl_off + x];
     if (tid == 0) {
-      nls->q = P.nl[S.nl_off];
       nls->dirty = 1;
+      nls->m = n_nl;
+      nls->minv_key = -1;
     }
-    const int64_t zoff = lazy ? S.cache_zoff + (int64_t)tag_cur * n : P.ep[S.ep_off + tag_cur].nlz_off;
-    for (int i = tid; i < n; i += T) {
+    const int64_t zoff =
+        lazy ? S.cache_zoff + (int64_t)tag_cur * n_nl * n : P.ep[S.ep_off + tag_cur].nlz_off;
+    for (int i = tid; i < n_nl * n; i += T) {   // one column per element
       nls->z()[i] = P.nlz[zoff + i];
-      nls->zl(n)[i] = P.nlz_lo[zoff + i];
+      nls->zl(n, n_nl)[i] = P.nlz_lo[zoff + i];
     }
   }
   __syncthreads();
@@ -1016,12 +1240,13 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
         }
       }
       if (entry != tag_cur) {
-        if (n_nl > 0) {   // the nonlinear resistor's column follows the matrix
+        if (n_nl > 0) {   // the nonlinear resistors' columns follow the matrix
           NlState* nls = reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls);
-          const int64_t zoff = lazy ? S.cache_zoff + (int64_t)entry * n : P.ep[S.ep_off + entry].nlz_off;
-          for (int i = tid; i < n; i += T) {
+          const int64_t zoff =
+              lazy ? S.cache_zoff + (int64_t)entry * n_nl * n : P.ep[S.ep_off + entry].nlz_off;
+          for (int i = tid; i < n_nl * n; i += T) {
             nls->z()[i] = P.nlz[zoff + i];
-            nls->zl(n)[i] = P.nlz_lo[zoff + i];
+            nls->zl(n, n_nl)[i] = P.nlz_lo[zoff + i];
           }
           if (tid == 0) nls->dirty = 1;
         }
@@ -1121,7 +1346,13 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
 
     // compensation method: the nonlinear resistor against the linear
     // solution, its current from the Thevenin source, then v -= z i
-    if (n_nl > 0) compensate(P, n, reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls), vv, recp);
+    if (n_nl == 1) {
+      compensate(P, n, reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls), vv, recp);
+    } else if (kExt && n_nl > 1) {
+      compensate_multi(P, n, n_nl, reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls), vv, recp,
+                       P.nl_seg + S.nl_off, sidx, step, &s_abort);
+      if (s_abort) break;
+    }
 
     // process 1: history currents, line outputs, next step's source
     // injections; then the update threads collect next step's line values
@@ -1336,15 +1567,15 @@ int forward_blocks_per_sm(const FwdLimits& lim) {
   return per_sm;
 }
 
-cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide, bool lazy) {
+cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide, bool ext) {
   const size_t smem = forward_smem_bytes(p.lim);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   // the 128-register build when allowed and its residency holds every CTA, else the 64-register one
-  const void* fns[2] = {lazy ? (const void*)fwd_kernel<2, true> : (const void*)fwd_kernel<2, false>,
-                        lazy ? (const void*)fwd_kernel<4, true> : (const void*)fwd_kernel<4, false>};
+  const void* fns[2] = {ext ? (const void*)fwd_kernel<2, true> : (const void*)fwd_kernel<2, false>,
+                        ext ? (const void*)fwd_kernel<4, true> : (const void*)fwd_kernel<4, false>};
   for (int v = wide ? 0 : 1; v < 2; ++v) {
     cudaError_t e = cudaFuncSetAttribute(fns[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

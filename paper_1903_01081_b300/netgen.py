@@ -965,6 +965,36 @@ def with_arresters(base: Network, seed: int = 1010, n_arresters: int = 40, scale
     return net
 
 
+def with_bus_arresters(base: Network, seed: int = 1014, n_buses: int = 20, scale=(0.55, 0.7)) -> Network:
+    """``base`` plus surge arresters on every phase of ``n_buses`` three-phase
+    buses (several nonlinear resistors in one subsystem, solved together):
+    the source buses first, then random buses, one bus per subsystem; the
+    characteristic ``ARRESTER_V/I`` with its voltages scaled by U[scale], low
+    enough that they conduct near the 1 kV peaks."""
+    rng = np.random.default_rng(seed)
+    net = base.copy()
+    find = _subsystem_roots(net)
+    buses = list(net.meta.get("source_bus", [])) + rng.permutation(len(net.meta["bus_nodes"])).tolist()
+    taken, picks = set(), []
+    for bus in buses:
+        r = find(int(net.meta["bus_nodes"][bus][0]))
+        if r not in taken:
+            taken.add(r)
+            picks.append(int(bus))
+        if len(picks) == n_buses:
+            break
+    b = NetworkBuilder()
+    for bus in picks:
+        for x in net.meta["bus_nodes"][bus]:
+            s_ = rng.uniform(*scale)
+            b.nonlinear_resistor(int(x), GROUND, [v * s_ for v in ARRESTER_V], ARRESTER_I)
+    nl = b.build(base.dt, 0)
+    for f in ("nl_k", "nl_m", "nl_np", "nl_v", "nl_i"):
+        setattr(net, f, getattr(nl, f))
+    net.meta = dict(net.meta, bus_arresters={"seed": seed, "buses": picks})
+    return net
+
+
 # control block types (see Network.cb_*)
 CB_CONST, CB_MEAS, CB_GAIN, CB_SUM, CB_MUL, CB_LIMIT, CB_INTEG, CB_LAG, CB_PI = range(9)
 

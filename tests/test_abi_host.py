@@ -182,11 +182,15 @@ def test_rejects_bad_nonlinear():
     assert "breakpoints" in bad(net, nl_v=v)
     assert "1 to 8" in bad(net, nl_np=np.array([9, 6], np.int32))
     assert "ground" in bad(net, nl_k=np.array([-1, net.nl_k[1]], np.int32))
+    # five in one subsystem (four are solved together; one in a scenario set)
     from oracle import partition
     sub, _ = partition(net)
-    same = [x for x in range(net.n_nodes) if sub[x] == sub[net.nl_k[0]] and x != net.nl_k[0]][0]
-    k = net.nl_k.copy(); k[1] = same
-    assert "more than one nonlinear resistor" in bad(net, nl_k=k)
+    same = [x for x in range(net.n_nodes) if sub[x] == sub[net.nl_k[0]]][:5]
+    assert len(same) == 5
+    rep = lambda a: np.repeat(np.asarray(a).reshape(2, -1)[:1], 5, axis=0).reshape(-1)
+    assert "more than 4 nonlinear resistors" in bad(
+        net, nl_k=np.asarray(same, np.int32), nl_m=np.full(5, -1, np.int32), nl_np=np.repeat(net.nl_np[:1], 5),
+        nl_v=rep(net.nl_v), nl_i=rep(net.nl_i))
     # the same checks hold with a scenario set (validated before any device work)
     sc_net, sc = g.n1_contingency(n_scenarios=4, n_buses=24, n_sub=4, n_steps=10)
     arr = g.with_arresters(sc_net, n_arresters=1)

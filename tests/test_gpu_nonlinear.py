@@ -107,3 +107,59 @@ def test_scenario_set_with_arresters():
     two.sync()
     assert np.array_equal(two.waveforms(), w)
     two.close()
+
+
+def test_three_arresters_in_one_subsystem():
+    """Arresters on all three phases of a source bus (their knees low enough
+    to conduct): the three elements are solved together through their
+    Thevenin matrix, against the oracle's piecewise-linear Newton iteration
+    on the nodal equations; 3,000 steps, and the same run in three launches
+    (the segments carry across launches)."""
+    base = g.multi_subsystem(43, [4, 5, 3], n_lines=4, n_sources=2, dt=20e-6)
+    net = g.with_bus_arresters(base, n_buses=1, scale=(0.07, 0.09))   # this bus peaks near 120 V
+    assert net.n_nonlinear == 3
+    N = 3000
+    ref = oracle.simulate(net, N)
+    knees = np.asarray(net.nl_v).reshape(-1, 8)[:, 0]
+    assert np.all(np.max(np.abs(ref[:, net.nl_k]), axis=0) > knees)      # all three conduct
+    assert rel(gpu_run(net, N), ref) <= TOL
+    assert rel(gpu_run(net, N, chunks=[900, 1300, 800]), ref) <= TOL
+
+
+def test_four_elements_resistive_ladder():
+    """Four elements in one resistive subsystem (one between two nodes), the
+    source driving them past their second breakpoints in both signs."""
+    vp = [[700.0, 1000.0], [650.0, 900.0], [800.0, 1100.0], [300.0, 500.0]]
+    ip = [[1.0, 40.0], [0.5, 60.0], [2.0, 30.0], [0.2, 20.0]]
+    b = g.NetworkBuilder()
+    b.source(6000.0, 0.2, 60.0)
+    b.branch(g.source_node(0), 0, g.KIND_R, 2.0)
+    b.branch(0, 1, g.KIND_R, 30.0)
+    b.branch(1, 2, g.KIND_R, 30.0)
+    for x in range(3):
+        b.branch(x, g.GROUND, g.KIND_R, 200.0)
+    for (k, m), v_, i_ in zip([(0, g.GROUND), (1, g.GROUND), (2, g.GROUND), (0, 2)], vp, ip):
+        b.nonlinear_resistor(k, m, v_, i_)
+    net = b.build(20e-6, 3)
+    N = 2000
+    ref = oracle.simulate(net, N)
+    assert np.max(np.abs(ref)) > 1000.0
+    assert rel(gpu_run(net, N), ref) <= TOL
+
+
+def test_bus_arresters_on_the_large_network():
+    """Three-phase arrester sets at 20 buses of the 3,000-node network (three
+    elements per subsystem), 3,000 steps against the oracle."""
+    net = g.with_bus_arresters(g.large_scale(n_steps=3000), n_buses=20)
+    assert net.n_nonlinear == 60
+    N = 3000
+    ref = oracle.simulate(net, N)
+    assert rel(gpu_run(net, N), ref) <= TOL
+
+
+def test_several_per_subsystem_rejected_in_scenario_sets():
+    base = g.multi_subsystem(43, [4, 5, 3], n_lines=4, n_sources=2, dt=20e-6)
+    net = g.with_bus_arresters(base, n_buses=1)
+    with pytest.raises(emt.EmtError) as ei:
+        emt.emt_build_network(net, g.Scenarios(n_scenarios=2))
+    assert ei.value.status == emt.EMT_EINVAL and "scenario set" in str(ei.value)
