@@ -380,6 +380,26 @@ emt_status emt_adjoint(emt_ctx* ctx, const double* v_target, int64_t n_steps, in
 /* Return to the de-energised state at step 0 (keeps G^-1 and recording setup). */
 emt_status emt_reset(emt_ctx* ctx);
 
+/* Checkpoint / resume of a run (the paper runs each step from the previous
+ * one, Sec. III-B; the run state is what one step hands to the next):
+ * write the context's run state -- history currents, line rings and the
+ * values consumed at the last step, runtime-switch words and breaker
+ * currents, frequency-dependent line and control-block states, nonlinear
+ * resistors' segments (per scenario in a scenario set) -- and its step
+ * counter into buf (host memory, `cap` bytes), for emt_load_state into this
+ * or another context built from the same description (and scenario set),
+ * in this process or another.  *size receives the bytes needed; buf = NULL
+ * only queries it; a smaller cap returns EINVAL.  Solve matrices and the
+ * recording are not part of the state.  Synchronous. */
+emt_status emt_save_state(emt_ctx* ctx, void* buf, int64_t cap, int64_t* size);
+
+/* Restore a state written by emt_save_state: the context must be built from
+ * the same network (EINVAL otherwise: the state carries the network's shape)
+ * and prefactored (ESTATE otherwise); the next emt_step_n continues from the
+ * saved step, bitwise as the saving context would have.  Clears a latched
+ * device error.  Synchronous. */
+emt_status emt_load_state(emt_ctx* ctx, const void* buf, int64_t size);
+
 /* Wait for all work of this context; report a latched device error.
  * dev_err_info (may be NULL): [code, subsystem, line end, step]. */
 emt_status emt_sync(emt_ctx* ctx, int32_t* dev_err_info);

@@ -7,6 +7,9 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libemt.so")
+# the checks build: every device-data index into a global array tested against the array's length (a bad one
+# latches an error that emt_sync reports, and the access is kept in bounds); loaded when EMT_CHECKS=1
+CHECKS_LIB_PATH = os.path.join(HERE, "libemt_checks.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -19,29 +22,34 @@ def headers():
                   glob.glob(os.path.join(os.path.dirname(HERE), "include", "*.h")))
 
 
-def needs_build() -> bool:
-    if not os.path.exists(LIB_PATH):
+def needs_build(path: str = LIB_PATH) -> bool:
+    if not os.path.exists(path):
         return True
-    t = os.path.getmtime(LIB_PATH)
+    t = os.path.getmtime(path)
     return any(os.path.getmtime(f) > t for f in sources() + headers())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Build ``libemt.so`` with nvcc if it is missing or stale; return its path."""
-    if not force and not needs_build():
-        return LIB_PATH
+def build(force: bool = False, verbose: bool = False, checks: bool = False) -> str:
+    """Build ``libemt.so`` (``libemt_checks.so`` with checks=True) with nvcc if
+    it is missing or stale; return its path."""
+    path = CHECKS_LIB_PATH if checks else LIB_PATH
+    if not force and not needs_build(path):
+        return path
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = path + f".tmp{os.getpid()}"
     # warnings are errors: one (a host-only constexpr call in __host__ __device__ code) once compiled to
     # device code that silently did nothing
     cmd = [nvcc, "-shared", "-Xcompiler", "-fPIC", ARCH, "-lineinfo", "-O3", "-std=c++17", "-Werror", "all-warnings",
            "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-o", tmp] + sources()
+    if checks:
+        cmd.insert(1, "-DEMT_CHECKS")
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
+    print(build(force=True, checks=True))

@@ -50,6 +50,11 @@ struct AdjSmem {
   size_t bytes;
 };
 
+// doubles of the shared input vector inp
+__host__ __device__ inline size_t adj_inp_len(const AdjLimits& L) {
+  return (size_t)L.lc + L.sb + 2 * ((size_t)L.le + 3 * (size_t)L.ce) + 1;
+}
+
 __host__ __device__ inline AdjSmem adj_smem(const AdjLimits& L) {
   AdjSmem s{};
   size_t o = 0;
@@ -62,7 +67,7 @@ __host__ __device__ inline AdjSmem adj_smem(const AdjLimits& L) {
   s.ww = d(L.n);
   s.vn = d(2 * (size_t)L.n);
   s.ev = d(2 * (size_t)L.n);
-  s.inp = d((size_t)L.lc + L.sb + 2 * ((size_t)L.le + 3 * (size_t)L.ce) + 1);
+  s.inp = d(adj_inp_len(L));
   s.xr = d(2 * (size_t)L.le);
   s.hb = d(L.lc);
   s.lce = d(L.lc);
@@ -115,7 +120,7 @@ __device__ bool collect_adj(const AdjParams& P, int n_le, unsigned tag, int lane
                             const int* ledepth, int* rslot, const double* ley2, double* xr, double* inp_le) {
   bool ok = true;
   for (int e = lane; e < n_le && ok; e += 32) {
-    const unsigned long long* slot = P.ring + 2 * (leown[e] + rslot[e]);
+    const unsigned long long* slot = P.ring + 2 * EMT_CHK(P.err, leown[e] + rslot[e], P.bnd.ring, kChkRingRead);
     double v = 0.0;
     if (!ld_tagged(slot, tag, v)) {
       const unsigned long long t0 = global_ns();
@@ -168,6 +173,8 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_abort;
   const AdjSmem L = adj_smem(P.lim);
+  const int inp_len = (int)adj_inp_len(P.lim);
+  (void)inp_len;
   double* gi = reinterpret_cast<double*>(smem_raw + L.gi);
   double* part = reinterpret_cast<double*>(smem_raw + L.part);
   double* iv = reinterpret_cast<double*>(smem_raw + L.iv);
@@ -297,9 +304,9 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
   for (int r = tid; r < n; r += T) {
     const int o = P.orig_of[S.node_off + r];
     orig[r] = o;
-    const double v = P.tape[(P.n_hi - 1 - P.tape_row0) * nn + S.node_off + r];
+    const double v = P.tape[EMT_CHK(P.err, (P.n_hi - 1 - P.tape_row0) * nn + S.node_off + r, P.bnd.tape, kChkTape)];
     vn[par0 * nv + r] = v;
-    ev[par0 * nv + r] = v - P.target[(P.n_hi - 1) * nn + o];
+    ev[par0 * nv + r] = v - P.target[EMT_CHK(P.err, (P.n_hi - 1) * nn + o, P.bnd.target, kChkTarget)];
   }
   if (tid == 0) {
     inp[zero_slot] = 0.0;
@@ -314,7 +321,8 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
   long long ep_start = P.ep[S.ep_off + te * n_states].start;
   int word = words ? P.word_tape[(P.n_hi - 1 - P.tape_row0) * P.n_sub + sidx] : 0;
   {
-    const int64_t off = P.ep[S.ep_off + te * n_states + word].ginv_off;
+    const int64_t off =
+        EMT_CHK_BLOCK(P.err, P.ep[S.ep_off + te * n_states + word].ginv_off, n * nc, P.bnd.ginv, kChkMatrix);
     for (int i = tid; i < n * nc; i += T) {
       const int r = i / nc, c = i - r * nc;
       gi[r * ldg + c] = P.ginv[off + i];
@@ -361,7 +369,8 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
       while (te > 0 && P.ep[S.ep_off + te * n_states].start > nstep) --te;
       ep_start = P.ep[S.ep_off + te * n_states].start;
       word = w_now;
-      const int64_t off = P.ep[S.ep_off + te * n_states + word].ginv_off;
+      const int64_t off =
+          EMT_CHK_BLOCK(P.err, P.ep[S.ep_off + te * n_states + word].ginv_off, n * nc, P.bnd.ginv, kChkMatrix);
       for (int x = tid; x < n * nc; x += T) {
         const int r = x / nc, c = x - r * nc;
         gi[r * ldg + c] = P.ginv[off + x];
@@ -372,8 +381,8 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
     double vnx = 0.0, tnx = 0.0, snx = 0.0;
     if (more) {
       if (tid < n) {
-        vnx = __ldg(P.tape + (nstep - 2 - P.tape_row0) * nn + S.node_off + tid);
-        tnx = __ldg(P.target + (nstep - 2) * nn + orig[tid]);
+        vnx = __ldg(P.tape + EMT_CHK(P.err, (nstep - 2 - P.tape_row0) * nn + S.node_off + tid, P.bnd.tape, kChkTape));
+        tnx = __ldg(P.target + EMT_CHK(P.err, (nstep - 2) * nn + orig[tid], P.bnd.target, kChkTarget));
       }
       if (src_thread < n_src) snx = __ldg(P.sin_table + (nstep - 2) * P.n_sources + srcg[src_thread]);
     }
@@ -387,10 +396,10 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
         node = ilnode[l];
         cnt = ilcnt[l];
         const int* e4 = ent + 4 * l;
-        s = (signed_entry(inp, (unsigned)e4[0], ie_base, blk_len, parshift) +
-             signed_entry(inp, (unsigned)e4[1], ie_base, blk_len, parshift)) +
-            (signed_entry(inp, (unsigned)e4[2], ie_base, blk_len, parshift) +
-             signed_entry(inp, (unsigned)e4[3], ie_base, blk_len, parshift));
+        s = (signed_entry(inp, (unsigned)e4[0], ie_base, blk_len, parshift, P.err, inp_len) +
+             signed_entry(inp, (unsigned)e4[1], ie_base, blk_len, parshift, P.err, inp_len)) +
+            (signed_entry(inp, (unsigned)e4[2], ie_base, blk_len, parshift, P.err, inp_len) +
+             signed_entry(inp, (unsigned)e4[3], ie_base, blk_len, parshift, P.err, inp_len));
       }
       const int wmax = __reduce_max_sync(0xffffffffu, cnt);
       double acc = s;
@@ -495,7 +504,8 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
             const int* nd = cenode + 3 * c;
             out = -fma(tr[0], ww[nd[0]], fma(tr[1], ww[nd[1]], tr[2] * ww[nd[2]])) - xmode[par * lv + e];
           }
-          st_tagged(P.ring + 2 * (lefar[e] + wslot[e]), (unsigned)(tau + led[e]), out);
+          st_tagged(P.ring + 2 * EMT_CHK(P.err, lefar[e] + wslot[e], P.bnd.ring, kChkRingWrite),
+                    (unsigned)(tau + led[e]), out);
           const int nx = wslot[e] + 1;
           wslot[e] = nx == ledepth[e] ? 0 : nx;
         }
@@ -512,7 +522,8 @@ __global__ void __launch_bounds__(kAdjThreads, 4) adj_kernel(AdjParams P) {
         bool ok = true;
         for (int e = kAdjItemThreads - 1 - tid; e < n_le && ok; e += kAdjItemThreads) {
           double v = 0.0;
-          ok = poll_slot(P, P.ring + 2 * (leown[e] + rslot[e]), tag, sidx, e, v);
+          ok = poll_slot(P, P.ring + 2 * EMT_CHK(P.err, leown[e] + rslot[e], P.bnd.ring, kChkRingRead), tag, sidx,
+                         e, v);
           xr_new[e] = v;
           blk_new[e] = ley2[e] * v;
           const int nx = rslot[e] + 1;

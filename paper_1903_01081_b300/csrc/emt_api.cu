@@ -2222,6 +2222,11 @@ static cudaError_t batch_launch(emt_ctx* c, int64_t n0, int64_t n_steps, cudaStr
   b.n0 = n0;
   b.n_steps = n_steps;
   b.dt = c->dt;
+  b.err = c->d_err;
+  b.bnd.ring = std::max<int64_t>(c->bring_len, 1) * c->S;
+  b.bnd.h = c->n_lc_total * c->S;
+  b.bnd.ginv = c->ginv_len;
+  b.bnd.rec = record ? c->rec_rows * c->S * (int64_t)c->rec_channels.size() : 0;
   return launch_batch(b, c->batch_threads, st, c->use_graph ? &c->graph : nullptr);
 }
 
@@ -2290,6 +2295,12 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
   p.cinj = c->d_cinj;
   p.cstate = c->d_cstate;
   p.cy = c->d_cy;
+  p.bnd.ring = std::max<int64_t>(c->ring_len, 1);
+  p.bnd.ginv = c->ginv_len;
+  p.bnd.rec = rs.rec ? (rs.rows - rs.row0) * rs.n_rec : 0;
+  p.bnd.h = c->n_lc_total;
+  p.bnd.src = c->src_table_steps * std::max<int64_t>(c->n_sources, 1);
+  p.bnd.nlz = c->nlz_len;
   p.ginv_rw = c->d_ginv;
   p.ginv_lo_rw = c->d_ginv_lo;
   p.nlz_rw = c->d_nlz;
@@ -2364,6 +2375,14 @@ extern "C" emt_status emt_sync(emt_ctx* c, int32_t* info) {
   if (h[0] == EMT_ETIMEOUT)
     return c->fail(EMT_ETIMEOUT, "subsystem " + std::to_string(h[1]) + " timed out at step " + std::to_string(h[3]) +
                                      " waiting for the value of its line end " + std::to_string(h[2]));
+  if (h[0] == kErrBounds) {
+    static const char* kSite[] = {"?", "ring read", "ring write", "solve matrix", "record", "history current",
+                                  "source table", "nonlinear column", "adjoint tape", "adjoint target",
+                                  "injection entry"};
+    const int site = (h[1] >= 1 && h[1] <= 10) ? h[1] : 0;
+    return c->fail(EMT_ESTATE, std::string("checks build: ") + kSite[site] + " index " + std::to_string(h[2]) +
+                                   " outside its array of " + std::to_string(h[3]));
+  }
   if (h[0] == kErrNoSegments)
     return c->fail(EMT_ESTATE, "the nonlinear resistors of subsystem " + std::to_string(h[1]) +
                                    " found no consistent segments at step " + std::to_string(h[3]));
@@ -2730,6 +2749,142 @@ extern "C" void emt_destroy(emt_ctx* c) {
   delete c;
 }
 
+// ---------------------------------------------------------------- save / load state
+//
+// The run state of a context -- everything a launch carries to the next:
+// history currents, line rings, the values consumed at the last step,
+// runtime-switch words and breaker currents, frequency-dependent line and
+// control-block states, nonlinear segments (per scenario in a scenario set)
+// -- and the step counter, as a header followed by the arrays in a fixed
+// order.  Solve matrices are not part of it: a context built from the same
+// description and prefactored has the same ones.
+
+namespace {
+
+constexpr uint32_t kStateMagic = 0x53544d45u;   // "EMTS"
+constexpr uint32_t kStateVersion = 1;
+
+struct StateHeader {
+  uint32_t magic, version;
+  int64_t n_nodes, n_sub, S, step, n_arrays, shape;
+};
+
+// (device pointer, bytes) of every state array, in the serialised order
+std::vector<std::pair<void*, size_t>> state_arrays(emt_ctx* c) {
+  std::vector<std::pair<void*, size_t>> a;
+  auto add = [&](void* p, size_t bytes) { a.push_back({bytes ? p : nullptr, p ? bytes : 0}); };
+  if (!c->batched) {
+    add(c->d_h, (size_t)c->n_lc_total * sizeof(double));
+    add(c->d_ring, 2 * (size_t)std::max<int64_t>(c->ring_len, 1) * sizeof(unsigned long long));
+    add(c->d_le_prev, c->line_ends.size() * sizeof(double));
+    add(c->d_rs_word, c->rs_word0.size() * sizeof(int32_t));
+    add(c->d_rs_prev_i, c->rswitches.size() * sizeof(double));
+    add(c->d_fd_state, kFdState * c->fdends.size() * sizeof(double));
+    add(c->d_cstate, 2 * c->cblocks.size() * sizeof(double));
+    add(c->d_cy, c->cblocks.size() * sizeof(double));
+    add(c->d_nl_seg, c->nls.size() * sizeof(int32_t));
+  } else {
+    const size_t S = (size_t)c->S;
+    add(c->d_bh, (size_t)c->n_lc_total * S * sizeof(double));
+    add(c->d_bring, (size_t)std::max<int64_t>(c->bring_len, 1) * S * sizeof(double));
+    add(c->d_bcy, c->d_bcy ? (2 * c->b_cb.size() + 2) * S * sizeof(double) : 0);
+    add(c->d_bcs, c->d_bcs ? 2 * c->b_cb.size() * S * sizeof(double) : 0);
+    add(c->d_bfds, c->d_bfds ? c->b_fd_le.size() * kBatchFdState * S * sizeof(double) : 0);
+    add(c->d_bcim, c->d_bcim ? 3 * c->b_ce_le0.size() * S * sizeof(double) : 0);
+    add(c->d_bcph, c->d_bcph ? 3 * c->b_ce_le0.size() * S * sizeof(double) : 0);
+    add(c->d_bword, c->d_bword ? (size_t)c->n_sub * S * sizeof(int32_t) : 0);
+    add(c->d_brsi, c->d_brsi ? c->rswitches.size() * S * sizeof(double) : 0);
+    add(c->d_bvbase, c->d_bvbase ? (size_t)c->n_sub * S * sizeof(long long) : 0);
+    add(c->d_bnli, c->d_bnli ? c->nls.size() * S * sizeof(double) : 0);
+  }
+  return a;
+}
+
+// FNV-1a over the context's shape (counts and array sizes), so that a state
+// only loads into a context of the same network
+int64_t state_shape(emt_ctx* c, const std::vector<std::pair<void*, size_t>>& a) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t x) {
+    for (int i = 0; i < 8; ++i) {
+      h ^= (x >> (8 * i)) & 0xffu;
+      h *= 1099511628211ull;
+    }
+  };
+  mix((uint64_t)c->n_nodes);
+  mix((uint64_t)c->n_branches);
+  mix((uint64_t)c->n_lines);
+  mix((uint64_t)c->n_sources);
+  mix((uint64_t)c->n_sub);
+  mix((uint64_t)c->S);
+  mix(c->batched ? 1u : 0u);
+  for (const auto& x : a) mix((uint64_t)x.second);
+  return (int64_t)(h >> 1);
+}
+
+}  // namespace
+
+extern "C" emt_status emt_save_state(emt_ctx* c, void* buf, int64_t cap, int64_t* size) {
+  if (!c || !size) return c ? c->fail(EMT_EINVAL, "emt_save_state: size is NULL") : EMT_EINVAL;
+  const auto arrays = state_arrays(c);
+  int64_t need = (int64_t)sizeof(StateHeader);
+  for (const auto& x : arrays) need += (int64_t)(sizeof(uint64_t) + x.second);
+  *size = need;
+  if (!buf) return EMT_OK;   // a size query
+  if (cap < need) return c->fail(EMT_EINVAL, "emt_save_state: buffer of " + std::to_string(cap) + " bytes, " +
+                                                 std::to_string(need) + " needed");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_save_state");
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  StateHeader hd{kStateMagic, kStateVersion, c->n_nodes, c->n_sub, c->S, c->step, (int64_t)arrays.size(),
+                 state_shape(c, arrays)};
+  std::memcpy(out, &hd, sizeof(hd));
+  size_t off = sizeof(hd);
+  for (const auto& x : arrays) {
+    const uint64_t bytes = x.second;
+    std::memcpy(out + off, &bytes, sizeof(bytes));
+    off += sizeof(bytes);
+    if (bytes) {
+      e = cudaMemcpy(out + off, x.first, bytes, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return c->cuda_fail(e, "emt_save_state");
+    }
+    off += bytes;
+  }
+  return EMT_OK;
+}
+
+extern "C" emt_status emt_load_state(emt_ctx* c, const void* buf, int64_t size) {
+  if (!c) return EMT_EINVAL;
+  if (!buf || size < (int64_t)sizeof(StateHeader)) return c->fail(EMT_EINVAL, "emt_load_state: no state in the buffer");
+  const auto arrays = state_arrays(c);
+  StateHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  if (hd.magic != kStateMagic || hd.version != kStateVersion)
+    return c->fail(EMT_EINVAL, "emt_load_state: not a state written by emt_save_state (or another version)");
+  if (hd.n_nodes != c->n_nodes || hd.n_sub != c->n_sub || hd.S != c->S || hd.n_arrays != (int64_t)arrays.size() ||
+      hd.shape != state_shape(c, arrays))
+    return c->fail(EMT_EINVAL, "emt_load_state: the state belongs to a context of another network");
+  if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
+  if (hd.step < 0 || hd.step > (int64_t)INT32_MAX - (int64_t)(1 << 21))
+    return c->fail(EMT_EINVAL, "emt_load_state: step counter out of range");
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  size_t off = sizeof(hd);
+  cudaError_t e = cudaDeviceSynchronize();
+  for (const auto& x : arrays) {
+    uint64_t bytes = 0;
+    if (off + sizeof(bytes) > (size_t)size) return c->fail(EMT_EINVAL, "emt_load_state: truncated state");
+    std::memcpy(&bytes, in + off, sizeof(bytes));
+    off += sizeof(bytes);
+    if (bytes != x.second || off + bytes > (size_t)size) return c->fail(EMT_EINVAL, "emt_load_state: truncated state");
+    if (e == cudaSuccess && bytes) e = cudaMemcpy(x.first, in + off, bytes, cudaMemcpyHostToDevice);
+    off += bytes;
+  }
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, 4 * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_load_state");
+  c->step = hd.step;
+  return EMT_OK;
+}
+
 // ---------------------------------------------------------------- adjoint
 //
 // Forward pass from the de-energised state, saving (h, line rings) before
@@ -2963,6 +3118,10 @@ static emt_status adjoint_run(emt_ctx* c, const double* v_target, int64_t n_step
   a.err = c->d_err;
   a.n_total = N;
   a.wait_budget_ns = c->wait_budget_ns;
+  a.bnd.ring = std::max<int64_t>(c->ring_len, 1);
+  a.bnd.ginv = c->ginv_len;
+  a.bnd.tape = K * nn;
+  a.bnd.target = N * nn;
   // Re-run of segment j from its checkpoint, recording its tape, on `rs`.
   auto rerun = [&](int64_t j, cudaStream_t rs) -> emt_status {
     const int64_t s0 = j * K, len = std::min(K, N - s0);

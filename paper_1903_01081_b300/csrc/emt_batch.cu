@@ -52,12 +52,13 @@ __device__ __forceinline__ double entry_value(const BatchParams& P, uint32_t raw
     else   // a frequency-dependent end's b (4) or Hy (5) of this step
       val = P.fds[((int64_t)idx * kBatchFdState + (kind == 4u ? 11 : 10)) * P.S + sg];
   } else if (kind == 0u) {
-    val = P.h[(int64_t)idx * P.S + sg];
+    val = P.h[EMT_CHK(P.err, (int64_t)idx * P.S + sg, P.bnd.h, kChkHistory)];
   } else if (kind == 1u) {
     val = __ldg(P.sb_g + idx) * vs[__ldg(P.sb_src + idx) * P.S_t + sl];
     if (P.keep_sb && !P.keep_sb[(int64_t)idx * P.S + sg]) val = 0.0;
   } else {
-    val = P.ring[(__ldg(P.le_bring + idx) + ring_slot(step, __ldg(P.le_d1 + idx))) * P.S + sg];
+    val = P.ring[EMT_CHK(P.err, (__ldg(P.le_bring + idx) + ring_slot(step, __ldg(P.le_d1 + idx))) * P.S + sg,
+                         P.bnd.ring, kChkRingRead)];
   }
   // the sign by flipping the sign bit (integer pipe)
   return __longlong_as_double(__double_as_longlong(val) ^ ((long long)(raw & kEntryNeg) << 32));
@@ -120,7 +121,8 @@ __device__ __forceinline__ double batch_nl_current(const BatchParams& P, int e, 
                                                    const double* vv, int node0, int St) {
   const NlDev& q = P.nl[e];
   const int s = __ldg(P.nlinfo + 4 * e), n = __ldg(P.nlinfo + 4 * e + 1), node_off = __ldg(P.nlinfo + 4 * e + 2);
-  const int64_t zoff = cur[(size_t)sl * P.n_sub + s] + (int64_t)n * __ldg(P.sub_nc + s);
+  const int64_t zoff =
+      EMT_CHK_BLOCK(P.err, cur[(size_t)sl * P.n_sub + s] + (int64_t)n * __ldg(P.sub_nc + s), n, P.bnd.ginv, kChkNlColumn);
   const double* z = P.ginv + zoff;
   const float* zl = P.ginv_lo + zoff;
   const double vk = q.k >= 0 ? vv[(size_t)(node_off + q.k - node0) * St + sl] : 0.0;
@@ -139,7 +141,8 @@ __device__ __forceinline__ double batch_nl_current(const BatchParams& P, int e, 
 __device__ __forceinline__ double fd_ring_w(const BatchParams& P, int ge, long long m, int sg) {
   if (m < 1) return 0.0;
   const int depth = __ldg(P.le_d1 + ge) + 1;
-  return P.ring[(__ldg(P.le_bring + ge) + (int64_t)((unsigned long long)m % (unsigned)depth)) * P.S + sg];
+  return P.ring[EMT_CHK(P.err, (__ldg(P.le_bring + ge) + (int64_t)((unsigned long long)m % (unsigned)depth)) * P.S + sg,
+                        P.bnd.ring, kChkRingRead)];
 }
 
 // FD end x at the start of step n (scenario sg): b(n) and the A terms.
@@ -179,7 +182,8 @@ __device__ __forceinline__ void batch_fd_update(const BatchParams& P, int ge, in
   const double yc = fma(r.y0, v, ssum);
   const double w = fma(2.0, yc, -st[11 * S]);
   const int depth = __ldg(P.le_d1 + ge) + 1;
-  P.ring[(__ldg(P.le_bfar + ge) + (int64_t)((unsigned long long)step % (unsigned)depth)) * S + sg] = w;
+  P.ring[EMT_CHK(P.err, (__ldg(P.le_bfar + ge) + (int64_t)((unsigned long long)step % (unsigned)depth)) * S + sg,
+                 P.bnd.ring, kChkRingWrite)] = w;
   st[8 * S] = v;
   st[10 * S] = fma(r.mu_sum, v, lam_s);
 }
@@ -215,7 +219,8 @@ __device__ __forceinline__ void batch_ce_update(const BatchParams& P, int ge, in
   const double vm = fma(r.tinv[3 * j], v[0], fma(r.tinv[3 * j + 1], v[1], r.tinv[3 * j + 2] * v[2]));
   const double out = fma(-__ldg(P.le_y2 + ge), vm, -P.cim[(int64_t)(3 * x + j) * S + sg]);
   const int depth = __ldg(P.le_d1 + ge) + 1;
-  P.ring[(__ldg(P.le_bfar + ge) + (int64_t)((unsigned long long)step % (unsigned)depth)) * S + sg] = out;
+  P.ring[EMT_CHK(P.err, (__ldg(P.le_bfar + ge) + (int64_t)((unsigned long long)step % (unsigned)depth)) * S + sg,
+                 P.bnd.ring, kChkRingWrite)] = out;
 }
 
 // Scenario sg selects variant base `base` for subsystem s: its matrix is
@@ -367,7 +372,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
           if (e0 < e1) acc = entry_value(P, (uint32_t)__ldg(P.bent + e0), sg, sl, step, vs);
           for (int e = e0 + 1; e < e1; ++e) acc += entry_value(P, (uint32_t)__ldg(P.bent + e), sg, sl, step, vs);
         } else {
-          acc = -P.h[(int64_t)(-1 - code) * S + sg];
+          acc = -P.h[EMT_CHK(P.err, (int64_t)(-1 - code) * S + sg, P.bnd.h, kChkHistory)];
         }
         iv[x] = acc;
         ivf[x] = f32_trunc(acc);
@@ -387,7 +392,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
         const int s = __ldg(P.node_sub + node), r = __ldg(P.node_r + node);
         const int nc = __ldg(P.sub_nc + s);
         const int cb = __ldg(P.sub_col_off + s) - G.col0;
-        const int64_t off = cur[(size_t)sl * n_sub + s] + (int64_t)r * nc;
+        const int64_t off =
+            EMT_CHK_BLOCK(P.err, cur[(size_t)sl * n_sub + s] + (int64_t)r * nc, nc, P.bnd.ginv, kChkMatrix);
         const double* row = P.ginv + off;
         const float* rowl = P.ginv_lo + off;
         const double* ivc = iv + (size_t)cb * St + sl;
@@ -416,7 +422,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
         vv[x] = v;
         if (rec_now) {
           const int pos = P.rec_pos[node];
-          if (pos >= 0) P.rec[(rec_row * S + sigma0 + sl) * P.n_rec + pos] = v;
+          if (pos >= 0) P.rec[EMT_CHK(P.err, (rec_row * S + sigma0 + sl) * P.n_rec + pos, P.bnd.rec, kChkRecord)] = v;
         }
       }
       __syncthreads();
@@ -449,11 +455,13 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
           const int r = node - node_off;
           const double i = P.nl_i[(int64_t)e * S + sigma0 + sl];
           double* vp = vv + (size_t)(node - G.node0) * St + sl;
-          const double v = fma(-(double)__ldg(P.ginv_lo + zoff + r), i, fma(-__ldg(P.ginv + zoff + r), i, *vp));
+          const int64_t zr = EMT_CHK(P.err, zoff + r, P.bnd.ginv, kChkNlColumn);
+          const double v = fma(-(double)__ldg(P.ginv_lo + zr), i, fma(-__ldg(P.ginv + zr), i, *vp));
           *vp = v;
           if (rec_now) {
             const int pos = P.rec_pos[node];
-            if (pos >= 0) P.rec[(rec_row * S + sigma0 + sl) * P.n_rec + pos] = v;
+            if (pos >= 0)
+              P.rec[EMT_CHK(P.err, (rec_row * S + sigma0 + sl) * P.n_rec + pos, P.bnd.rec, kChkRecord)] = v;
           }
         }
         __syncthreads();
@@ -504,7 +512,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
           const double vk = nk >= 0 ? vv[(size_t)(nk - G.node0) * St + sl] : (nk == -1 ? 0.0 : vs[(-2 - nk) * St + sl]);
           const double vm = nm >= 0 ? vv[(size_t)(nm - G.node0) * St + sl] : (nm == -1 ? 0.0 : vs[(-2 - nm) * St + sl]);
           const double e = __ldg(P.lc_e + gl);
-          double* hp = P.h + (int64_t)gl * S + sg;
+          double* hp = P.h + EMT_CHK(P.err, (int64_t)gl * S + sg, P.bnd.h, kChkHistory);
           const double hv = *hp;
           *hp = __ldg(P.lc_isl + gl) ? fma(e, vk - vm, hv) : fma(e, vk - vm, -hv);
         } else if (P.le_fd != nullptr && __ldg(P.le_fd + G.le0 + (it - n_lc)) >= 0) {
@@ -516,10 +524,12 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
         } else {
           const int ge = G.le0 + (it - n_lc);
           const int d1 = __ldg(P.le_d1 + ge);
-          const double ie = P.ring[(__ldg(P.le_bring + ge) + ring_slot(step, d1)) * S + sg];
+          const double ie =
+              P.ring[EMT_CHK(P.err, (__ldg(P.le_bring + ge) + ring_slot(step, d1)) * S + sg, P.bnd.ring, kChkRingRead)];
           double out = fma(-__ldg(P.le_y2 + ge), vv[(size_t)(__ldg(P.le_nd + ge) - G.node0) * St + sl], -ie);
           if (P.keep_le && !P.keep_le[(int64_t)ge * S + sg]) out = 0.0;   // removed line
-          P.ring[(__ldg(P.le_bfar + ge) + ring_slot(step + d1 - 1, d1)) * S + sg] = out;
+          P.ring[EMT_CHK(P.err, (__ldg(P.le_bfar + ge) + ring_slot(step + d1 - 1, d1)) * S + sg, P.bnd.ring,
+                         kChkRingWrite)] = out;
         }
       }
       __syncthreads();

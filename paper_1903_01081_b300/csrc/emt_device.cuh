@@ -2,11 +2,45 @@
 #pragma once
 #include <stdint.h>
 
+#include <climits>
+
 #include <cuda_runtime.h>
 
 #include "emt_internal.h"
 
 namespace emt {
+
+// Checks build (compiled with -DEMT_CHECKS; the library libemt_checks.so):
+// every index into a global array whose value comes from device data is
+// tested against the array's length; one outside latches {kErrBounds, site,
+// index, length} in the device error word (emt_sync reports it) and is
+// replaced by 0, so that the access stays in bounds.  Nothing traps.  In the
+// normal build the macros are the index itself.  (kErrBounds: emt_internal.h)
+#ifdef EMT_CHECKS
+__device__ __forceinline__ int64_t chk_index(int32_t* err, int64_t i, int64_t n, int site) {
+  if (i >= 0 && i < n) return i;
+  if (err != nullptr && atomicCAS(err, 0, kErrBounds) == 0) {
+    err[1] = site;
+    err[2] = (int)(i > INT32_MAX ? INT32_MAX : (i < INT32_MIN ? INT32_MIN : i));
+    err[3] = (int)(n > INT32_MAX ? INT32_MAX : n);
+  }
+  return 0;
+}
+// a block [off, off + count) inside [0, n): off, else 0
+__device__ __forceinline__ int64_t chk_block(int32_t* err, int64_t off, int64_t count, int64_t n, int site) {
+  if (off >= 0 && off + count <= n) return off;
+  chk_index(err, off + count - 1, n, site);
+  return 0;
+}
+#define EMT_CHK(err, i, n, site) ::emt::chk_index((err), (int64_t)(i), (int64_t)(n), (site))
+#define EMT_CHK_BLOCK(err, off, count, n, site) ::emt::chk_block((err), (int64_t)(off), (int64_t)(count), (int64_t)(n), (site))
+#else
+#define EMT_CHK(err, i, n, site) (i)
+#define EMT_CHK_BLOCK(err, off, count, n, site) (off)
+#endif
+// sites reported by the checks build
+enum ChkSite { kChkRingRead = 1, kChkRingWrite, kChkMatrix, kChkRecord, kChkHistory, kChkSource, kChkNlColumn,
+               kChkTape, kChkTarget, kChkEntry };
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -87,9 +121,13 @@ __device__ __forceinline__ bool poll_slot(const Params& P, const unsigned long l
 
 // Signed injection entry (see kEntryNeg): the input value with the entry's
 // sign bit applied; line-end entries are shifted to the current parity block.
-__device__ __forceinline__ double signed_entry(const double* inp, unsigned raw, int ie_base, int n_le, int parshift) {
+__device__ __forceinline__ double signed_entry(const double* inp, unsigned raw, int ie_base, int n_le, int parshift,
+                                                int32_t* err, int inp_len) {
   int idx = (int)(raw & ~kEntryNeg);
   if ((unsigned)(idx - ie_base) < (unsigned)n_le) idx += parshift;
+  idx = (int)EMT_CHK(err, idx, inp_len, kChkEntry);
+  (void)err;
+  (void)inp_len;
   const unsigned long long bits =
       (unsigned long long)__double_as_longlong(inp[idx]) ^ ((unsigned long long)(raw & kEntryNeg) << 32);
   return __longlong_as_double((long long)bits);

@@ -151,6 +151,9 @@ constexpr int kNlMaxPerSub = 4;
 // Device error code: the piecewise-linear iteration of a subsystem's
 // nonlinear resistors found no consistent segments (reported as EMT_ESTATE).
 constexpr int kErrNoSegments = 100;
+// Device error code of the checks build: an index outside its array
+// {kErrBounds, site, index, length} (emt_device.cuh; reported as EMT_ESTATE).
+constexpr int kErrBounds = 101;
 struct NlDev {
   int32_t k, m;        // subsystem-local ends, -1 = ground
   int32_t np;          // breakpoints after (0, 0)
@@ -223,6 +226,14 @@ struct EpochDev {
   int32_t pad;
 };
 
+// Lengths of the global arrays a launch indexes with device data, for the
+// checks build (emt_device.cuh): ring slots, solve-matrix entries, record
+// doubles, history slots, source-table doubles, nonlinear columns, tape and
+// target doubles.
+struct Bounds {
+  int64_t ring, ginv, rec, h, src, nlz, tape, target;
+};
+
 // Per-launch upper bounds that size the forward kernel's shared memory.
 struct FwdLimits {
   int32_t n, nc, q, lc, sb, le, src, il, str;
@@ -291,6 +302,7 @@ struct FwdParams {
   int32_t* cache_next;         // per subsystem: next slot to replace; then the count of run-time factorisations
   double* lazy_work;
   const SwitchDev* sw;         // closed switches of each epoch (EpochDev sw_off / n_sw)
+  Bounds bnd;
 };
 
 constexpr int kFdState = 11;
@@ -450,6 +462,8 @@ struct BatchParams {
   int32_t rec_decim, n_rec;
   int64_t n0, n_steps;
   double dt;
+  int32_t* err;                // device error word (the checks build latches there)
+  Bounds bnd;                  // ring: slots of the rings x S; h: L/C slots x S; ginv; rec
 };
 
 // A CUDA graph holding the one multi-scenario launch; its kernel node's
@@ -510,6 +524,7 @@ struct AdjParams {
   int64_t n_total;
   int64_t n_hi, n_steps;
   unsigned long long wait_budget_ns;
+  Bounds bnd;
 };
 
 struct SourceParams {

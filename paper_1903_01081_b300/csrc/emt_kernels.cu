@@ -436,6 +436,11 @@ struct FwdSmem {
   size_t bytes;
 };
 
+// doubles of the shared input vector inp (see kEntryNeg)
+__host__ __device__ inline size_t fwd_inp_len(const FwdLimits& L) {
+  return (size_t)L.lc + L.sb + 2 * ((size_t)L.le + 3 * (size_t)L.ce + L.fd) + 1 + (size_t)L.ci + L.fd;
+}
+
 __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   FwdSmem s{};
   size_t o = 0;
@@ -450,7 +455,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.part = d(n_tasks);
   s.iv = d(L.nc);
   s.vv = d(L.n);
-  s.inp = d((size_t)L.lc + L.sb + 2 * ((size_t)L.le + 3 * (size_t)L.ce + L.fd) + 1 + (size_t)L.ci + L.fd);
+  s.inp = d(fwd_inp_len(L));
   s.vs = d(2 * (size_t)L.src);
   s.lce = d(L.lc);
   s.sbg = d(L.sb);
@@ -639,7 +644,7 @@ __device__ __forceinline__ void compensate(const FwdParams& P, int n, NlState* s
   for (int r = tid; r < n; r += T) {
     const double v = fma(-(double)zl[r], inl, fma(-z[r], inl, vv[r]));
     vv[r] = v;
-    if (row >= 0 && recp[r] >= 0) P.rec[(row - P.rec_row0) * P.n_rec + recp[r]] = v;
+    if (row >= 0 && recp[r] >= 0) P.rec[EMT_CHK(P.err, (row - P.rec_row0) * P.n_rec + recp[r], P.bnd.rec, kChkRecord)] = v;
   }
   __syncthreads();
 }
@@ -842,7 +847,7 @@ __device__ void compensate_multi(const FwdParams& P, int n, int m, NlState* s, d
       }
     const double v = hi - lo;
     vv[r] = v;
-    if (row >= 0 && recp[r] >= 0) P.rec[(row - P.rec_row0) * P.n_rec + recp[r]] = v;
+    if (row >= 0 && recp[r] >= 0) P.rec[EMT_CHK(P.err, (row - P.rec_row0) * P.n_rec + recp[r], P.bnd.rec, kChkRecord)] = v;
   }
   __syncthreads();
 }
@@ -890,7 +895,7 @@ __device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int la
   for (int e = lane; e < n_le && ok; e += 32) {
     const bool fd = F.lefd != nullptr && F.lefd[e] >= 0;
     double v = 0.0;
-    ok = poll_slot(P, P.ring + 2 * (leown[e] + rslot[e]), tag, sidx, e, v);
+    ok = poll_slot(P, P.ring + 2 * EMT_CHK(P.err, leown[e] + rslot[e], P.bnd.ring, kChkRingRead), tag, sidx, e, v);
     ie[e] = v;
     if (ok && fd) fold_fd_end(F, e, v, ie);
     const int nx = rslot[e] + 1;
@@ -917,6 +922,8 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   __shared__ int s_rsbit[kRs];    // states decided for the next step
   __shared__ int s_slot, s_fp, s_fsing;        // run-time factorisation: cache slot, pivot, singular flag
   const FwdSmem L = fwd_smem(P.lim);
+  const int inp_len = (int)fwd_inp_len(P.lim);
+  (void)inp_len;
   double* gi_buf = reinterpret_cast<double*>(smem_raw + L.gi);
   double* part = reinterpret_cast<double*>(smem_raw + L.part);
   double* iv = reinterpret_cast<double*>(smem_raw + L.iv);
@@ -994,7 +1001,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   // ---- prologue: this subsystem's data into shared memory
   for (int x = tid; x < n_lc; x += T) {
     const BranchDev b = P.br[P.lc_idx[S.lc_off + x]];
-    inp[x] = P.h[S.lc_off + x];
+    inp[x] = P.h[EMT_CHK(P.err, S.lc_off + x, P.bnd.h, kChkHistory)];
     lce[x] = b.e;
     lck[x] = b.k;
     lcm[x] = b.m;
@@ -1059,7 +1066,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   }
   for (int x = tid; x < S.n_src; x += T) {
     srcg[x] = P.src_global[S.src_off + x];
-    vs[(P.n0 & 1) * src_vs + x] = P.src_table[P.src_global[S.src_off + x]];
+    vs[(P.n0 & 1) * src_vs + x] = P.src_table[EMT_CHK(P.err, P.src_global[S.src_off + x], P.bnd.src, kChkSource)];
   }
   if (tid == 0) {
     inp[zero_slot] = 0.0;
@@ -1152,7 +1159,9 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
       if (tid == 0) s_abort = 1;
     } else {
       tag_cur = entry;
-      const int64_t off = lazy ? S.cache_goff + (int64_t)entry * n * nc : P.ep[S.ep_off + entry].ginv_off;
+      const int64_t off =
+          EMT_CHK_BLOCK(P.err, lazy ? S.cache_goff + (int64_t)entry * n * nc : P.ep[S.ep_off + entry].ginv_off,
+                        n * nc, P.bnd.ginv, kChkMatrix);
       for (int i = tid; i < n * nc; i += T) {
         const int r = i / nc, c = i - r * nc;
         gi[r * ldg + c] = P.ginv[off + i];
@@ -1174,7 +1183,8 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
       nls->minv_key = -1;
     }
     const int64_t zoff =
-        lazy ? S.cache_zoff + (int64_t)tag_cur * n_nl * n : P.ep[S.ep_off + tag_cur].nlz_off;
+        EMT_CHK_BLOCK(P.err, lazy ? S.cache_zoff + (int64_t)tag_cur * n_nl * n : P.ep[S.ep_off + tag_cur].nlz_off,
+                      n_nl * n, P.bnd.nlz, kChkNlColumn);
     for (int i = tid; i < n_nl * n; i += T) {   // one column per element
       nls->z()[i] = P.nlz[zoff + i];
       nls->zl(n, n_nl)[i] = P.nlz_lo[zoff + i];
@@ -1243,7 +1253,8 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
         if (n_nl > 0) {   // the nonlinear resistors' columns follow the matrix
           NlState* nls = reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls);
           const int64_t zoff =
-              lazy ? S.cache_zoff + (int64_t)entry * n_nl * n : P.ep[S.ep_off + entry].nlz_off;
+              EMT_CHK_BLOCK(P.err, lazy ? S.cache_zoff + (int64_t)entry * n_nl * n : P.ep[S.ep_off + entry].nlz_off,
+                            n_nl * n, P.bnd.nlz, kChkNlColumn);
           for (int i = tid; i < n_nl * n; i += T) {
             nls->z()[i] = P.nlz[zoff + i];
             nls->zl(n, n_nl)[i] = P.nlz_lo[zoff + i];
@@ -1260,7 +1271,9 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
         gilo = gilo_buf + cur_buf * buf_len;
         if (entry != tag_cur) {
           tag_cur = entry;
-          const int64_t off = lazy ? S.cache_goff + (int64_t)entry * n * nc : P.ep[S.ep_off + entry].ginv_off;
+          const int64_t off =
+              EMT_CHK_BLOCK(P.err, lazy ? S.cache_goff + (int64_t)entry * n * nc : P.ep[S.ep_off + entry].ginv_off,
+                            n * nc, P.bnd.ginv, kChkMatrix);
           for (int i = tid; i < n * nc; i += T) {
             const int r = i / nc, c = i - r * nc;
             gi[r * ldg + c] = P.ginv[off + i];
@@ -1272,7 +1285,8 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
     // next step's source voltages: load issued now, stored after process 4
     double vnext = 0.0;
     if (src_thread < S.n_src && step + 1 < n_end)
-      vnext = __ldg(P.src_table + (step + 1 - P.n0) * P.n_sources + srcg[src_thread]);
+      vnext = __ldg(P.src_table + EMT_CHK(P.err, (step + 1 - P.n0) * P.n_sources + srcg[src_thread], P.bnd.src,
+                                          kChkSource));
 
     // process 2: nodal injections; each lane sums four entries, the node's
     // first lane adds its other lanes' sums
@@ -1284,10 +1298,10 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
         node = ilnode[l];
         cnt = ilcnt[l];
         const int* e4 = ent + 4 * l;
-        s = (signed_entry(inp, (unsigned)e4[0], ie_base, blk_len, parshift) +
-             signed_entry(inp, (unsigned)e4[1], ie_base, blk_len, parshift)) +
-            (signed_entry(inp, (unsigned)e4[2], ie_base, blk_len, parshift) +
-             signed_entry(inp, (unsigned)e4[3], ie_base, blk_len, parshift));
+        s = (signed_entry(inp, (unsigned)e4[0], ie_base, blk_len, parshift, P.err, inp_len) +
+             signed_entry(inp, (unsigned)e4[1], ie_base, blk_len, parshift, P.err, inp_len)) +
+            (signed_entry(inp, (unsigned)e4[2], ie_base, blk_len, parshift, P.err, inp_len) +
+             signed_entry(inp, (unsigned)e4[3], ie_base, blk_len, parshift, P.err, inp_len));
       }
       const int wmax = __reduce_max_sync(0xffffffffu, cnt);
       double acc = s;
@@ -1336,7 +1350,8 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
       }
       v += (double)vl;
       vv[r] = v;
-      if (rec_now && recp[r] >= 0) P.rec[(rec_row - P.rec_row0) * P.n_rec + recp[r]] = v;
+      if (rec_now && recp[r] >= 0)
+        P.rec[EMT_CHK(P.err, (rec_row - P.rec_row0) * P.n_rec + recp[r], P.bnd.rec, kChkRecord)] = v;
     }
     if (n_nl > 0 && tid == 0)   // rewritten after the compensation
       reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls)->row = rec_now ? rec_row : -1;
@@ -1432,7 +1447,9 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
             const double vm = fma(tr[0], vv[nd[0]], fma(tr[1], vv[nd[1]], tr[2] * vv[nd[2]]));
             out = fma(-ley2[e], vm, -imode[par * lv + e]);
           }
-          if (writes_lines) st_tagged(P.ring + 2 * (lefar[e] + wslot[e]), (unsigned)(step + led[e]), out);
+          if (writes_lines)
+            st_tagged(P.ring + 2 * EMT_CHK(P.err, lefar[e] + wslot[e], P.bnd.ring, kChkRingWrite),
+                      (unsigned)(step + led[e]), out);
           const int nx = wslot[e] + 1;
           wslot[e] = nx == ledepth[e] ? 0 : nx;
         } else if (it >= it_sb) {
@@ -1454,7 +1471,8 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
         bool ok = true;
         for (int e = item_threads - 1 - tid; e < n_le && ok; e += item_threads) {
           double v = 0.0;
-          ok = poll_slot(P, P.ring + 2 * (leown[e] + rslot[e]), tag, sidx, e, v);
+          ok = poll_slot(P, P.ring + 2 * EMT_CHK(P.err, leown[e] + rslot[e], P.bnd.ring, kChkRingRead), tag, sidx,
+                         e, v);
           ie_next[e] = v;
           const int nx = rslot[e] + 1;
           rslot[e] = nx == ledepth[e] ? 0 : nx;
@@ -1483,7 +1501,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
     __syncthreads();
   }
   if (!s_abort) {
-    for (int b = tid; b < n_lc; b += T) P.h[S.lc_off + b] = inp[b];
+    for (int b = tid; b < n_lc; b += T) P.h[EMT_CHK(P.err, S.lc_off + b, P.bnd.h, kChkHistory)] = inp[b];
     if (P.n_steps > 0)   // the values consumed at the last step, for the next launch's interpolation
       for (int x = tid; x < n_le; x += T)
         P.le_prev[S.le_off + x] = inp[ie_base + (int)((n_end - 1) & 1) * blk_len + x];

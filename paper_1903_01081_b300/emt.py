@@ -76,20 +76,28 @@ class _ScenarioDesc(ctypes.Structure):
 _lib = None
 
 
+def checks_build() -> bool:
+    """EMT_CHECKS=1 in the environment selects the checks build of the library."""
+    return os.environ.get("EMT_CHECKS", "0") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB_PATH
+    return _build.CHECKS_LIB_PATH if checks_build() else _build.LIB_PATH
 
 
 def load_library(build_if_needed: bool = True):
-    """Load libemt.so (building it with nvcc first if missing or stale)."""
+    """Load libemt.so, or libemt_checks.so under EMT_CHECKS=1 (building it
+    with nvcc first if missing or stale)."""
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_needed and _build.needs_build():
-        _build.build()
-    if not os.path.exists(_build.LIB_PATH):
-        raise RuntimeError(f"libemt.so not found at {_build.LIB_PATH}; build it with paper_1903_01081_b300.build.build()")
-    lib = ctypes.CDLL(_build.LIB_PATH)
+    path = library_path()
+    if build_if_needed and _build.needs_build(path):
+        _build.build(checks=checks_build())
+    if not os.path.exists(path):
+        raise RuntimeError(f"{os.path.basename(path)} not found at {path}; build it with "
+                           "paper_1903_01081_b300.build.build()")
+    lib = ctypes.CDLL(path)
     P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
     sig = {
         "emt_build_network": [P, P, P],
@@ -107,6 +115,8 @@ def load_library(build_if_needed: bool = True):
         "emt_adjoint": [P, P, I64, I32, P, P, I32, P],
         "emt_autotune": [P, I64, P],
         "emt_read_controls": [P, P, I64, I32],
+        "emt_save_state": [P, P, I64, P],
+        "emt_load_state": [P, P, I64],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -411,6 +421,22 @@ def emt_autotune(ctx: Ctx, trial_steps: int = 50, stream=None) -> None:
 
 def emt_reset(ctx: Ctx) -> None:
     _check(ctx, load_library().emt_reset(ctx.handle))
+
+
+def emt_save_state(ctx: Ctx) -> np.ndarray:
+    """The context's run state as bytes (include/emt.h)."""
+    lib = load_library()
+    size = ctypes.c_int64(0)
+    _check(ctx, lib.emt_save_state(ctx.handle, None, 0, ctypes.byref(size)))
+    buf = np.empty(size.value, np.uint8)
+    _check(ctx, lib.emt_save_state(ctx.handle, buf.ctypes.data, size.value, ctypes.byref(size)))
+    return buf
+
+
+def emt_load_state(ctx: Ctx, state) -> None:
+    """Restore a state from emt_save_state (include/emt.h)."""
+    buf = np.ascontiguousarray(state, np.uint8)
+    _check(ctx, load_library().emt_load_state(ctx.handle, buf.ctypes.data, buf.size))
 
 
 def emt_sync(ctx: Ctx):

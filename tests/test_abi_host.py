@@ -196,3 +196,25 @@ def test_rejects_bad_nonlinear():
     arr = g.with_arresters(sc_net, n_arresters=1)
     with pytest.raises(emt.EmtError, match="1 to 8"):
         emt.emt_build_network(dataclasses.replace(arr, nl_np=np.array([9], np.int32)), sc)
+
+
+def test_out_of_range_indices_rejected_before_any_launch():
+    """Every index in a description is checked on the host: a node, source,
+    line end or switch end outside its range returns EINVAL from
+    emt_build_network (nothing reaches the device; the checks build only
+    guards indices the kernels compute)."""
+    net = g.multi_subsystem(7, [4, 5], n_lines=2, n_sources=2, dt=20e-6)
+    n = net.n_nodes
+    k = net.br_k.copy(); k[0] = n
+    assert "node" in bad(net, br_k=k)
+    m = net.br_m.copy(); m[1] = -2 - net.n_sources                        # a source that does not exist
+    assert "out of range" in bad(net, br_m=m)
+    lk = net.ln_k.copy(); lk[0] = n + 5
+    bad(net, ln_k=lk)
+    lm = net.ln_m.copy(); lm[0] = -1                                      # a line end at ground
+    bad(net, ln_m=lm)
+    sw = g.NetworkBuilder()
+    sw.source(1.0, 0.0)
+    sw.branch(g.source_node(0), 0, 0, 1.0)
+    sw.switch(0, 7, 0.1, 10)
+    bad(sw.build(20e-6, 1, 20))
