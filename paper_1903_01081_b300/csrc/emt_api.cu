@@ -87,6 +87,11 @@ struct emt_ctx {
   int32_t* d_cache_next = nullptr;
   int32_t* d_cache_next0 = nullptr;
   double* d_lazy_work = nullptr;
+  // one warp per subsystem (emt_small.cu), for networks whose subsystems are all small and hold basic
+  // elements only; opt-in (option warp_per_subsystem): measured no faster than the CTA kernel, whose eight
+  // warps spread a subsystem's FP64 work over all four FP64 pipes of its SM
+  bool small_ok = false;
+  bool use_small = false;
   bool forward_narrow = false;   // emt_adjoint: its re-runs share the device with the reverse sweep   // electrical subsystems (components); n_sub counts CTAs, several components each when packed
   int64_t comp_sum_n2 = 0, comp_max_n = 0;   // over the components
   FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0};
@@ -1837,6 +1842,11 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
     if (forward_smem_bytes(two) <= 200 * 1024) c->lim.nbuf = 2;
   }
 
+  // -------- the warp-per-subsystem kernel serves networks of small subsystems
+  // with R/L/C branches, sources, fixed-time switches and lossless lines only
+  c->small_ok = !scen && S > 0 && c->lim.n <= kSmallMaxNodes && c->lim.ce == 0 && c->lim.fd == 0 &&
+                c->lim.cb == 0 && c->lim.ci == 0 && c->lim.nl == 0 && c->rswitches.empty() && !c->lazy;
+
   // -------- injection-lane range of every internal node
   c->node_l0.assign(N, 0);
   c->node_nl.assign(N, 0);
@@ -2232,7 +2242,8 @@ static cudaError_t batch_launch(emt_ctx* c, int64_t n0, int64_t n_steps, cudaStr
 
 // Single-network forward run of n_steps steps from the context's step.
 static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, const RecSpec& rs) {
-  if (forward_smem_bytes(c->lim) > 227 * 1024)
+  const bool small = c->small_ok && c->use_small;
+  if ((small ? small_smem_bytes(c->lim) : forward_smem_bytes(c->lim)) > 227 * 1024)
     return c->fail(EMT_ERESOURCE, "a subsystem needs more shared memory than one CTA has");
   // source table for one chunk of steps at a time (grow-only buffer)
   const int64_t chunk =
@@ -2324,7 +2335,7 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
     if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n source table");
     p.n0 = c->step + 1;
     p.n_steps = len;
-    e = launch_forward(p, st, !c->forward_narrow, c->lazy || c->lim.nl > 1);
+    e = small ? launch_forward_small(p, st) : launch_forward(p, st, !c->forward_narrow, c->lazy || c->lim.nl > 1);
     if (e == cudaErrorCooperativeLaunchTooLarge)
       return c->fail(EMT_ERESOURCE, "persistent launch of " + std::to_string(c->n_sub) +
                                         " CTAs cannot be co-resident on this device");
@@ -2649,6 +2660,14 @@ extern "C" emt_status emt_set_option(emt_ctx* c, const char* key, int64_t value)
       return c->fail(EMT_EINVAL, "scenarios_per_cta " + std::to_string(value) + " does not fit in shared memory");
     return EMT_OK;
   }
+  if (k == "warp_per_subsystem") {   // 1: networks of small subsystems run one warp per subsystem (emt_small.cu)
+    if (value != 0 && !c->small_ok)
+      return c->fail(EMT_EINVAL, "this network does not fit the warp-per-subsystem kernel (subsystems of at most " +
+                                     std::to_string(kSmallMaxNodes) + " nodes with basic elements only)");
+    cudaDeviceSynchronize();
+    c->use_small = value != 0;
+    return EMT_OK;
+  }
   if (k == "adjoint_overlap") {   // 0: the adjoint re-runs segments on the caller's stream only
     c->overlap_adjoint = value != 0;
     return EMT_OK;
@@ -2702,6 +2721,7 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "n_control_injections") *value = (int64_t)c->cinj.size();
   else if (k == "max_control_layers") *value = c->max_clayers;
   else if (k == "smem_bytes") *value = (int64_t)forward_smem_bytes(c->lim);
+  else if (k == "warp_per_subsystem") *value = c->small_ok && c->use_small ? 1 : 0;
   else if (k == "lazy_subsystems") {   // subsystems whose switch states are factorised at run time
     int64_t m = 0;
     for (const SubDev& sd : c->subs) m += sd.n_cache > 0 ? 1 : 0;

@@ -554,6 +554,10 @@ cudaError_t launch_sources(const SourceParams& p, cudaStream_t st);
 // several nonlinear resistors
 cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide = true, bool ext = false);
 size_t forward_smem_bytes(const FwdLimits& lim);
+// one warp per subsystem (emt_small.cu): subsystems of at most kSmallMaxNodes nodes with basic elements only
+constexpr int kSmallMaxNodes = 32;
+cudaError_t launch_forward_small(const FwdParams& p, cudaStream_t st);
+size_t small_smem_bytes(const FwdLimits& lim);
 int forward_blocks_per_sm(const FwdLimits& lim);   // resident CTAs per SM (0 on error)
 cudaError_t launch_batch(const BatchParams& p, int threads, cudaStream_t st, BatchGraph* graph);
 size_t batch_smem_bytes(int S_t, int n_sources, int n_sub, int max_cols, int max_nodes);

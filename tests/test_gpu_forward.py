@@ -239,3 +239,37 @@ def test_pipelined_read_to_pinned_host_is_bitwise(decim, chunk):
     b.close()
     assert np.array_equal(out.numpy(), want)
     assert rel_err(want[:, 0, :], oracle.simulate(net, N)[decim - 1::decim]) <= TOL
+
+
+@pytest.mark.parametrize("kind", ["single_rlc", "strict_500", "multi"])
+def test_warp_per_subsystem_kernel(kind):
+    """Networks whose subsystems are all small (at most 32 nodes) with basic
+    elements can run one warp per subsystem (option warp_per_subsystem = 1);
+    the same runs on the CTA kernel (the default) and both match the
+    oracle."""
+    if kind == "single_rlc":
+        net, N = g.single_rlc(), 20000                     # the 12-node network, its fault at step 2,000
+    elif kind == "strict_500":
+        net, N = g.large_scale(strict_500=True, n_steps=2000), 2000
+    else:
+        net, N = g.multi_subsystem(17, [2, 4, 3, 5, 1], n_lines=9, n_sources=2, dt=20e-6, delay_range=(1, 3)), 3000
+    ref = oracle.simulate(net, N)
+    for warp in (1, 0):
+        sim = emt.Simulator(net, n_steps=N)
+        assert sim.info("warp_per_subsystem") == 0
+        emt.emt_set_option(sim.ctx, "warp_per_subsystem", warp)
+        assert sim.info("warp_per_subsystem") == warp
+        sim.run(N // 3)
+        sim.run(N - N // 3)
+        sim.sync()
+        w = sim.waveforms()[:, 0, :]
+        sim.close()
+        assert np.max(np.abs(w - ref)) / np.max(np.abs(ref)) <= 1e-10, warp
+
+
+def test_warp_per_subsystem_kernel_is_not_used_for_large_subsystems():
+    sim = emt.Simulator(g.large_scale(n_steps=10), n_steps=10)
+    assert sim.info("warp_per_subsystem") == 0
+    with pytest.raises(emt.EmtError):
+        emt.emt_set_option(sim.ctx, "warp_per_subsystem", 1)
+    sim.close()
