@@ -434,12 +434,68 @@ emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
  * subsystem's control graph),
  * "n_matrix_variants", "scenarios_per_cta", "batch_threads", "batch_groups"
  * (subsystem groups per step of the multi-scenario kernel),
- * "graph_launches", "autotuned". */
+ * "graph_launches", "autotuned", "shard_rank" (-1 unless a shard),
+ * "shard_window" (see emt_set_shard; 0 unless a shard), "shard_ctas" (CTAs
+ * this context runs). */
 emt_status emt_get_info(const emt_ctx* ctx, const char* key, int64_t* value);
 
 /* Internal node order: perm[i] = original node id of internal slot i
  * (n_nodes entries). */
 emt_status emt_get_node_order(const emt_ctx* ctx, int32_t* perm);
+
+/* ---- Shards: one network over several devices (one context per rank) ----
+ *
+ * Subsystems meet only through line rings: the value a line end sends at
+ * step n is consumed at the far end at step n + d, d its travel time in
+ * whole steps (Sec. II-B: the line decouples its two ends).  Every rank
+ * builds a context from the same description (so CTAs and line ends are
+ * numbered alike) and runs only the CTAs it owns.  With D = the smallest d
+ * of a line end whose two sides belong to different ranks, a window of
+ * W <= D steps reads only values sent before it began, so the ranks run
+ * each window independently and, between windows, swap the ring slots the
+ * window wrote for the other side: point to point, 16 bytes per cut line
+ * end and step, no collective.  The result is bitwise that of the whole
+ * network in one context. */
+
+/* CTA of every node: cta[i] for the caller's node i (n_nodes entries,
+ * host memory).  EINVAL for a context built with a scenario set. */
+emt_status emt_get_node_ctas(const emt_ctx* ctx, int32_t* cta);
+
+/* The line ends ("n_line_ends" of them, library order; coupled lines
+ * contribute one per mode and end): the CTA that owns each, the index of
+ * the end at the other side of the line, and its travel time d in whole
+ * steps.  Host arrays of n_line_ends entries, each may be NULL.  EINVAL for
+ * a context built with a scenario set. */
+emt_status emt_get_line_ends(const emt_ctx* ctx, int32_t* cta, int32_t* far_end, int32_t* d);
+
+/* Make ctx a shard: it runs the CTAs c with owner[c] == rank (owner: host
+ * array of "n_ctas" non-negative ranks, the same on every rank); owner =
+ * NULL makes it the whole network again.  Sets "shard_window" (emt_get_info)
+ * to D above (2^31 - 1 if no line is cut).  From then on each emt_step_n
+ * is one window of at most D steps, and the next emt_step_n is refused
+ * (ESTATE) until, for every peer, the window's values were packed
+ * (emt_shard_pack) and the peer's window values unpacked (emt_shard_unpack).
+ * Synchronises the device.  EINVAL: a scenario set, a rank owning no CTA, a
+ * negative owner; the context then runs the whole network.  emt_adjoint is
+ * refused while the context is a shard. */
+emt_status emt_set_shard(emt_ctx* ctx, const int32_t* owner, int32_t rank);
+
+/* The slots the last window wrote for rank `peer` (those its CTAs will
+ * consume), as [cut line end][step of the window] 16-byte records (tag and
+ * value words), cut line ends in ascending library order.  *bytes (may be
+ * NULL) receives the size: 16 x (cut ends towards peer) x (window steps);
+ * buf = NULL only queries it.  buf: device memory of `cap` bytes, 16-byte
+ * aligned.  Enqueued on cuda_stream (NULL: legacy default stream), after the
+ * window's launch when both are on one stream.  0 bytes for a peer that
+ * shares no line with this rank. */
+emt_status emt_shard_pack(emt_ctx* ctx, int32_t peer, void* buf, int64_t cap, int64_t* bytes, void* cuda_stream);
+
+/* Write what rank `peer` packed for this rank after the same window into
+ * this context's rings.  buf: device memory, 16-byte aligned, of exactly the
+ * size the peer's emt_shard_pack reported (EINVAL otherwise).  Enqueued on
+ * cuda_stream: the caller orders it after the buffer's arrival (and before
+ * the next window). */
+emt_status emt_shard_unpack(emt_ctx* ctx, int32_t peer, const void* buf, int64_t bytes, void* cuda_stream);
 
 /* Last error message of ctx (or of the last failed build if ctx == NULL). */
 const char* emt_last_error(const emt_ctx* ctx);

@@ -81,8 +81,15 @@ def _load():
         lib.orc_lu_solve.argtypes = [ctypes.c_int64, P, P, P]
         lib.orc_rs_states.argtypes = [P, ctypes.c_int64, P]
         lib.orc_controls.argtypes = [P, ctypes.c_int64, P]
+        lib.orc_open.argtypes = [P]
+        lib.orc_open.restype = P
+        lib.orc_advance.argtypes = [P, ctypes.c_int64, P, P]
+        lib.orc_line_ends.argtypes = [P, P, P, P]
+        lib.orc_sent.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, P, ctypes.c_int]
+        lib.orc_close.argtypes = [P]
+        lib.orc_close.restype = None
         for f in (lib.orc_run, lib.orc_loss_cs, lib.orc_adjoint, lib.orc_partition, lib.orc_lu_solve,
-                  lib.orc_rs_states, lib.orc_controls):
+                  lib.orc_rs_states, lib.orc_controls, lib.orc_advance, lib.orc_line_ends, lib.orc_sent):
             f.restype = ctypes.c_int
         _lib = lib
     return _lib
@@ -250,3 +257,57 @@ def lu_solve(A, b):
     x = np.zeros_like(b)
     _check(lib.orc_lu_solve(int(A.shape[0]), A.ctypes.data, b.ctypes.data, x.ctypes.data), "orc_lu_solve")
     return x
+
+
+def line_ends(net):
+    """(node, far end, d) of every line end: lines (k, m), coupled lines
+    (end k's modes, end m's modes), frequency-dependent lines (k, m)."""
+    lib = _load()
+    pin = _Pinned(net)
+    n = 2 * pin.net.n_ln + 6 * pin.net.n_cl + 2 * pin.net.n_fl
+    node, far, d = (np.zeros(n, dtype=np.int32) for _ in range(3))
+    if n:
+        _check(lib.orc_line_ends(pin.ref, node.ctypes.data, far.ctypes.data, d.ctypes.data), "orc_line_ends")
+    return node, far, d
+
+
+class Session:
+    """The loop run window by window on a chosen set of subsystems (see
+    orc_advance in emt_oracle.h): the oracle side of a sharded run."""
+
+    def __init__(self, net):
+        lib = _load()
+        self.n_nodes = int(net.n_nodes)
+        self._pin = _Pinned(net)          # the C session points into these arrays
+        self._h = lib.orc_open(self._pin.ref)
+        if not self._h:
+            raise OracleError("orc_open failed (invalid input)")
+        self.step = 0
+
+    def advance(self, n_steps: int, active=None):
+        """Run n_steps more steps; ``active``: per subsystem (orc_partition), truthy = run it.
+        Returns the node voltages [n_steps, n_nodes]."""
+        out = np.zeros((int(n_steps), self.n_nodes), dtype=np.float64)
+        act = None if active is None else _arr(active, np.uint8)
+        _check(_load().orc_advance(self._h, int(n_steps), None if act is None else act.ctypes.data,
+                                   out.ctypes.data if out.size else None), "orc_advance")
+        self.step += int(n_steps)
+        return out
+
+    def sent(self, end: int, n0: int, w: int):
+        vals = np.zeros(int(w), dtype=np.float64)
+        _check(_load().orc_sent(self._h, int(end), int(n0), int(w), vals.ctypes.data if w else None, 0), "orc_sent")
+        return vals
+
+    def set_sent(self, end: int, n0: int, vals):
+        v = _arr(vals, np.float64)
+        _check(_load().orc_sent(self._h, int(end), int(n0), v.size, v.ctypes.data if v.size else None, 1),
+               "orc_sent")
+
+    def close(self):
+        if self._h:
+            _load().orc_close(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

@@ -312,6 +312,8 @@ struct Sim {
   // control blocks: output of the latest evaluation, and the two states
   // (integral or previous output; previous input)
   std::vector<T> cy, cs0, cs1;
+  // subsystems whose processes 3 and 4 run (empty: all); see orc_advance
+  std::vector<char> active;
 
   bool init(const T* br_value, const T* src_amp, bool monolithic) {
     n_nodes = (int)net->n_nodes;
@@ -663,6 +665,7 @@ struct Sim {
     }
     // processes 3 and 4 per subsystem
     for (int s = 0; s < n_sub; ++s) {
+      if (!active.empty() && !active[s]) continue;
       if (!refactor_if_needed(s, n)) return false;
       int ns = (int)nodes[s].size();
       std::vector<T> x(ns);
@@ -1019,3 +1022,133 @@ extern "C" int orc_lu_solve(int64_t n, const double* A, const double* b, double*
   lu_solve<double>((int)n, a, piv, x);
   return 0;
 }
+
+// ---------------------------------------------------------------- sessions
+//
+// A session runs the loop window by window on a chosen set of subsystems.
+// Subsystems meet only through lines, and a line end consumes at step n
+// what the far end sent at step n - d (Sec. II-B: the travel time
+// decouples the two ends), so a part of the network can run a window of
+// up to d steps alone when the values its ends consume come in from
+// wherever the far ends run.  The session exposes those sent values per
+// line end for that exchange.  The other subsystems' processes 3 and 4 do
+// not run; their node voltages stay 0, and what their ends send is wrong
+// until the exchange overwrites it.
+
+struct orc_session {
+  const orc_net* net;
+  Sim<double> sim;
+  std::vector<double> br_value;
+  int64_t n = 0;   // last completed step
+};
+
+namespace {
+
+int64_t n_line_ends(const orc_net* net) { return 2 * net->n_ln + 6 * net->n_cl + 2 * net->n_fl; }
+
+// The storage of the value line end x sent at step m (which must still be
+// held: m within the last d + 1 steps), or nullptr for an unknown end.
+double* sent_slot(orc_session* S, int64_t x, int64_t m) {
+  const orc_net* net = S->net;
+  Sim<double>& sim = S->sim;
+  if (x < 0) return nullptr;
+  if (x < 2 * net->n_ln) {   // end k's value waits in end m's ring, and vice versa, at the slot of step m + d
+    const int64_t l = x / 2, d1 = net->ln_d[l] + 1;
+    auto& ring = (x % 2 == 0) ? sim.ring_m[l] : sim.ring_k[l];
+    return &ring[(m + net->ln_d[l]) % d1];
+  }
+  x -= 2 * net->n_ln;
+  if (x < 6 * net->n_cl) {   // coupled line l, end e, mode j: by sending step
+    const int64_t l = x / 6;
+    const int e = (int)((x % 6) / 3), j = (int)(x % 3);
+    auto& L = sim.cl[l];
+    return &L.c[e][j][m % (L.d[j] + 2)];
+  }
+  x -= 6 * net->n_cl;
+  if (x < 2 * net->n_fl) {   // frequency-dependent line l, end e: by sending step
+    auto& L = sim.fl[x / 2];
+    return &L.w[x % 2][m % (L.d + 3)];
+  }
+  return nullptr;
+}
+
+int64_t end_delay(const orc_net* net, const Sim<double>& sim, int64_t x) {
+  if (x < 2 * net->n_ln) return net->ln_d[x / 2];
+  x -= 2 * net->n_ln;
+  if (x < 6 * net->n_cl) return sim.cl[x / 6].d[x % 3];
+  x -= 6 * net->n_cl;
+  return sim.fl[x / 2].d;
+}
+
+}  // namespace
+
+extern "C" orc_session* orc_open(const orc_net* net) {
+  if (!valid(net)) return nullptr;
+  orc_session* S = new orc_session;
+  S->net = net;
+  S->br_value.assign(net->br_val, net->br_val + net->n_br);
+  S->sim.net = net;
+  if (!S->sim.init(S->br_value.data(), net->src_amp, false)) {
+    delete S;
+    return nullptr;
+  }
+  return S;
+}
+
+extern "C" int orc_advance(orc_session* S, int64_t n_steps, const uint8_t* active, double* v_out) {
+  if (!S || n_steps < 0) return -1;
+  Sim<double>& sim = S->sim;
+  if (active != nullptr && S->net->n_cb > 0) return -1;   // control blocks may join subsystems without a line
+  sim.active.clear();
+  if (active != nullptr)
+    for (int s = 0; s < sim.n_sub; ++s) sim.active.push_back(active[s] ? 1 : 0);
+  for (int64_t k = 0; k < n_steps; ++k) {
+    if (!sim.step(S->n + 1)) return -2;
+    ++S->n;
+    if (v_out)
+      for (int64_t i = 0; i < S->net->n_nodes; ++i) v_out[k * S->net->n_nodes + i] = sim.v[i];
+  }
+  return 0;
+}
+
+extern "C" int orc_line_ends(const orc_net* net, int32_t* node, int32_t* far, int32_t* d) {
+  if (!valid(net)) return -1;
+  int64_t x = 0;
+  for (int64_t l = 0; l < net->n_ln; ++l, x += 2) {
+    node[x] = net->ln_k[l];
+    node[x + 1] = net->ln_m[l];
+    far[x] = (int32_t)(x + 1);
+    far[x + 1] = (int32_t)x;
+    d[x] = d[x + 1] = net->ln_d[l];
+  }
+  for (int64_t l = 0; l < net->n_cl; ++l)
+    for (int e = 0; e < 2; ++e)
+      for (int j = 0; j < 3; ++j, ++x) {
+        node[x] = (e == 0 ? net->cl_k : net->cl_m)[3 * l];
+        far[x] = (int32_t)(x + (e == 0 ? 3 : -3));
+        d[x] = (int32_t)std::floor(net->cl_tau[3 * l + j] / net->dt);
+      }
+  for (int64_t l = 0; l < net->n_fl; ++l, x += 2) {
+    node[x] = net->fl_k[l];
+    node[x + 1] = net->fl_m[l];
+    far[x] = (int32_t)(x + 1);
+    far[x + 1] = (int32_t)x;
+    d[x] = d[x + 1] = (int32_t)std::floor(net->fl_tau[l] / net->dt);
+  }
+  return 0;
+}
+
+extern "C" int orc_sent(orc_session* S, int64_t end, int64_t n0, int64_t w, double* vals, int set) {
+  if (!S || end < 0 || end >= n_line_ends(S->net) || w < 0) return -1;
+  const int64_t d = end_delay(S->net, S->sim, end);
+  // only the last d + 1 steps' values are still held
+  if (n0 < 1 || n0 + w - 1 > S->n || n0 <= S->n - (d + 1)) return -1;
+  for (int64_t j = 0; j < w; ++j) {
+    double* p = sent_slot(S, end, n0 + j);
+    if (set) *p = vals[j];
+    else vals[j] = *p;
+  }
+  return 0;
+}
+
+extern "C" void orc_close(orc_session* S) { delete S; }

@@ -193,6 +193,32 @@ int orc_controls(const orc_net* net, int64_t n_steps, double* y_out);
 /* Subsystem of each unknown node (components over branches and switches). */
 int orc_partition(const orc_net* net, int32_t* sub_of_node, int64_t* n_sub);
 
+/* Sessions: the loop run window by window on a chosen part of the network
+ * (partitioned mode), for checking a sharded run.  Subsystems meet only
+ * through lines, and an end consumes at step n what the far end sent at
+ * step n - d (Sec. II-B: the travel time decouples the two ends), so a part
+ * can run up to d steps alone once the values its ends consume are put in.
+ *   orc_open:      a session at step 0 (net must outlive it); NULL if invalid.
+ *   orc_advance:   n_steps more steps; active[s] != 0 for the subsystems (of
+ *                  orc_partition) whose processes 3 and 4 run, NULL = all;
+ *                  v_out: [n_steps][n_nodes] or NULL.  Networks with control
+ *                  blocks take active = NULL only (-1 otherwise).  An
+ *                  inactive subsystem's voltages stay 0 and what its ends
+ *                  send is wrong until orc_sent overwrites it.
+ *   orc_line_ends: the 2 n_ln + 6 n_cl + 2 n_fl line ends, in the order
+ *                  lines (k, m), coupled lines (end k modes 0-2, end m modes
+ *                  0-2), frequency-dependent lines (k, m): a node of the end,
+ *                  the far end's index, the travel time d in whole steps.
+ *   orc_sent:      the values end `end` sent at steps n0 .. n0+w-1 (set = 0:
+ *                  read into vals; 1: overwrite from vals); those steps must
+ *                  be among the last d + 1 completed ones. */
+typedef struct orc_session orc_session;
+orc_session* orc_open(const orc_net* net);
+int orc_advance(orc_session* s, int64_t n_steps, const uint8_t* active, double* v_out);
+int orc_line_ends(const orc_net* net, int32_t* node, int32_t* far, int32_t* d);
+int orc_sent(orc_session* s, int64_t end, int64_t n0, int64_t w, double* vals, int set);
+void orc_close(orc_session* s);
+
 /* Dense LU with partial pivoting: solve A x = b, A row-major n x n. */
 int orc_lu_solve(int64_t n, const double* A, const double* b, double* x);
 

@@ -231,6 +231,21 @@ struct emt_ctx {
   int32_t *d_bce_le0 = nullptr, *d_ble_ce = nullptr, *d_bce_node = nullptr;
   double *d_ble_f = nullptr, *d_bcim = nullptr, *d_bcph = nullptr;
 
+  // shard of the network this context runs (emt_set_shard): the CTAs it
+  // owns, and per peer rank the line ends whose sent values cross over
+  // (ascending library order, so that both sides list them alike)
+  bool sharded = false;
+  int32_t shard_rank = -1;
+  int32_t shard_window = 0;                 // largest window: min d over the cut line ends
+  std::vector<int32_t> shard_active;        // CTAs run here
+  std::map<int32_t, std::vector<int32_t>> shard_send, shard_recv;
+  std::map<int32_t, int64_t> shard_send_off, shard_recv_off;   // offsets into d_shard_ends
+  std::set<int32_t> shard_to_pack, shard_to_unpack;         // peers the last window still owes
+  int64_t win_n0 = 0, win_w = 0;            // steps of the last window
+  int32_t* d_shard_active = nullptr;
+  SubDev* d_shard_sub = nullptr;            // their descriptions, in that order
+  int32_t* d_shard_ends = nullptr;
+
   std::vector<void*> allocations;
 
   emt_status fail(emt_status st, const std::string& msg) {
@@ -2241,6 +2256,13 @@ static cudaError_t batch_launch(emt_ctx* c, int64_t n0, int64_t n_steps, cudaStr
 }
 
 // Single-network forward run of n_steps steps from the context's step.
+// A sharded context forgets its last window (after a reset or a loaded state).
+static void shard_clear_window(emt_ctx* c) {
+  c->shard_to_pack.clear();
+  c->shard_to_unpack.clear();
+  c->win_n0 = c->win_w = 0;
+}
+
 static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, const RecSpec& rs) {
   const bool small = c->small_ok && c->use_small;
   if ((small ? small_smem_bytes(c->lim) : forward_smem_bytes(c->lim)) > 227 * 1024)
@@ -2320,6 +2342,11 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
   p.cache_next = c->d_cache_next;
   p.lazy_work = c->d_lazy_work;
   p.sw = c->d_sw;
+  if (c->sharded) {
+    p.sub = c->d_shard_sub;
+    p.active = c->d_shard_active;
+    p.n_active = (int32_t)c->shard_active.size();
+  }
   for (int64_t done = 0; done < n_steps; done += chunk) {
     const int64_t len = std::min(chunk, n_steps - done);
     SourceParams sp{};
@@ -2356,6 +2383,17 @@ extern "C" emt_status emt_step_n(emt_ctx* c, int64_t n_steps, void* stream) {
     return c->fail(EMT_EINVAL, "step counter would exceed 2^31 - 2^21");
   if (!c->rec_channels.empty() && (c->step + n_steps) / c->rec_decim > c->rec_rows)
     return c->fail(EMT_EINVAL, "recording capacity exceeded: raise max_rows in emt_set_recording");
+  if (c->sharded) {
+    if (n_steps > c->shard_window)
+      return c->fail(EMT_EINVAL, "a shard advances at most " + std::to_string(c->shard_window) +
+                                     " steps (its shortest cut line) between exchanges, not " + std::to_string(n_steps));
+    if (!c->shard_to_pack.empty())
+      return c->fail(EMT_ESTATE, "the last window's line values for rank " + std::to_string(*c->shard_to_pack.begin()) +
+                                     " are not packed (emt_shard_pack)");
+    if (!c->shard_to_unpack.empty())
+      return c->fail(EMT_ESTATE, "the last window's line values from rank " +
+                                     std::to_string(*c->shard_to_unpack.begin()) + " are not unpacked (emt_shard_unpack)");
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (c->batched) {
     cudaError_t e = batch_launch(c, c->step + 1, n_steps, st, !c->rec_channels.empty());
@@ -2372,7 +2410,15 @@ extern "C" emt_status emt_step_n(emt_ctx* c, int64_t n_steps, void* stream) {
     rs.decim = c->rec_decim;
     rs.rows = c->rec_rows;
   }
-  return forward_steps(c, n_steps, st, rs);
+  const int64_t n0 = c->step + 1;
+  const emt_status r = forward_steps(c, n_steps, st, rs);
+  if (r == EMT_OK && c->sharded) {   // the window just enqueued: its sent values go out, the peers' come in
+    c->win_n0 = n0;
+    c->win_w = n_steps;
+    for (auto& kv : c->shard_send) c->shard_to_pack.insert(kv.first);
+    for (auto& kv : c->shard_recv) c->shard_to_unpack.insert(kv.first);
+  }
+  return r;
 }
 
 extern "C" emt_status emt_sync(emt_ctx* c, int32_t* info) {
@@ -2540,6 +2586,7 @@ extern "C" emt_status emt_read_controls(emt_ctx* c, double* y, int64_t n, int32_
 
 extern "C" emt_status emt_reset(emt_ctx* c) {
   if (!c) return EMT_EINVAL;
+  shard_clear_window(c);
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemset(c->d_h, 0, std::max<int64_t>(c->n_lc_total, 1) * sizeof(double));
   if (e == cudaSuccess)
@@ -2721,6 +2768,9 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "n_control_injections") *value = (int64_t)c->cinj.size();
   else if (k == "max_control_layers") *value = c->max_clayers;
   else if (k == "smem_bytes") *value = (int64_t)forward_smem_bytes(c->lim);
+  else if (k == "shard_rank") *value = c->sharded ? c->shard_rank : -1;
+  else if (k == "shard_window") *value = c->sharded ? c->shard_window : 0;
+  else if (k == "shard_ctas") *value = c->sharded ? (int64_t)c->shard_active.size() : c->n_sub;
   else if (k == "warp_per_subsystem") *value = c->small_ok && c->use_small ? 1 : 0;
   else if (k == "lazy_subsystems") {   // subsystems whose switch states are factorised at run time
     int64_t m = 0;
@@ -2756,6 +2806,158 @@ extern "C" emt_status emt_get_node_order(const emt_ctx* c, int32_t* perm) {
   if (!c || !perm) return EMT_EINVAL;
   for (int64_t i = 0; i < c->n_nodes; ++i) perm[i] = c->original_of[i];
   return EMT_OK;
+}
+
+// ---------------------------------------------------------------- shards
+//
+// Subsystems meet only through line rings, and a value sent at step n is
+// consumed at step n + d (Sec. II-B: the line's travel time decouples its
+// two ends).  A shard runs the CTAs one rank owns; with every cut line end
+// at least D steps long, a window of W <= D steps reads only values sent
+// before the window began, so each rank runs its window alone and the
+// ranks swap, between windows, the slots the window wrote for the other
+// side.
+
+static std::vector<int32_t> far_ends(const emt_ctx* c) {
+  std::map<int64_t, int32_t> by_own;
+  for (size_t e = 0; e < c->line_ends.size(); ++e) by_own[c->line_ends[e].own_ring] = (int32_t)e;
+  std::vector<int32_t> far(c->line_ends.size(), -1);
+  for (size_t e = 0; e < c->line_ends.size(); ++e) {
+    auto it = by_own.find(c->line_ends[e].far_ring);
+    if (it != by_own.end()) far[e] = it->second;
+  }
+  return far;
+}
+
+static std::vector<int32_t> cta_of_line_end(const emt_ctx* c) {
+  std::vector<int32_t> cta(c->line_ends.size(), -1);
+  for (int s = 0; s < c->n_sub; ++s)
+    for (int x = 0; x < c->subs[s].n_le; ++x) cta[c->subs[s].le_off + x] = s;
+  return cta;
+}
+
+extern "C" emt_status emt_get_node_ctas(const emt_ctx* c, int32_t* cta) {
+  if (!c || !cta) return EMT_EINVAL;
+  if (c->batched) return const_cast<emt_ctx*>(c)->fail(EMT_EINVAL, "emt_get_node_ctas: a scenario set's CTAs hold scenarios, not subsystems");
+  for (int64_t i = 0; i < c->n_nodes; ++i) cta[i] = c->sub_of_node[i];
+  return EMT_OK;
+}
+
+extern "C" emt_status emt_get_line_ends(const emt_ctx* c, int32_t* cta, int32_t* far_end, int32_t* d) {
+  if (!c) return EMT_EINVAL;
+  if (c->batched) return const_cast<emt_ctx*>(c)->fail(EMT_EINVAL, "emt_get_line_ends: not for a context built with a scenario set");
+  const std::vector<int32_t> own = cta_of_line_end(c), far = far_ends(c);
+  for (size_t e = 0; e < c->line_ends.size(); ++e) {
+    if (cta) cta[e] = own[e];
+    if (far_end) far_end[e] = far[e];
+    if (d) d[e] = c->line_ends[e].d;
+  }
+  return EMT_OK;
+}
+
+extern "C" emt_status emt_set_shard(emt_ctx* c, const int32_t* owner, int32_t rank) {
+  if (!c) return EMT_EINVAL;
+  if (c->batched) return c->fail(EMT_EINVAL, "emt_set_shard: a context built with a scenario set is not sharded");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_set_shard");
+  c->release(c->d_shard_active);
+  c->release(c->d_shard_ends);
+  c->release(c->d_shard_sub);
+  c->d_shard_active = c->d_shard_ends = nullptr;
+  c->d_shard_sub = nullptr;
+  c->sharded = false;
+  c->shard_rank = -1;
+  c->shard_window = 0;
+  c->shard_active.clear();
+  c->shard_send.clear();
+  c->shard_recv.clear();
+  c->shard_send_off.clear();
+  c->shard_recv_off.clear();
+  shard_clear_window(c);
+  if (owner == nullptr) return EMT_OK;   // the whole network again
+  if (rank < 0) return c->fail(EMT_EINVAL, "emt_set_shard: rank < 0");
+  for (int s = 0; s < c->n_sub; ++s) {
+    if (owner[s] < 0) return c->fail(EMT_EINVAL, "emt_set_shard: CTA " + std::to_string(s) + " has a negative owner");
+    if (owner[s] == rank) c->shard_active.push_back(s);
+  }
+  if (c->shard_active.empty()) return c->fail(EMT_EINVAL, "emt_set_shard: rank " + std::to_string(rank) + " owns no CTA");
+  const std::vector<int32_t> own = cta_of_line_end(c), far = far_ends(c);
+  int64_t window = INT32_MAX;
+  for (size_t x = 0; x < c->line_ends.size(); ++x) {
+    if (far[x] < 0) return c->fail(EMT_ESTATE, "emt_set_shard: line end without a far end");
+    const int32_t a = owner[own[x]], b = owner[own[far[x]]];
+    if (a == b) continue;
+    window = std::min<int64_t>(window, c->line_ends[x].d);
+    if (a == rank) c->shard_send[b].push_back((int32_t)x);   // sent here, consumed at rank b
+    if (b == rank) c->shard_recv[a].push_back((int32_t)x);   // sent at rank a, consumed here
+  }
+  std::vector<int32_t> all;
+  for (auto& kv : c->shard_send) {
+    c->shard_send_off[kv.first] = (int64_t)all.size();
+    all.insert(all.end(), kv.second.begin(), kv.second.end());
+  }
+  for (auto& kv : c->shard_recv) {
+    c->shard_recv_off[kv.first] = (int64_t)all.size();
+    all.insert(all.end(), kv.second.begin(), kv.second.end());
+  }
+  std::vector<SubDev> ssub;
+  for (int32_t s : c->shard_active) ssub.push_back(c->subs[s]);
+  e = c->upload(&c->d_shard_active, c->shard_active);
+  if (e == cudaSuccess) e = c->upload(&c->d_shard_sub, ssub);
+  if (e == cudaSuccess) e = c->upload(&c->d_shard_ends, all);
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_set_shard");
+  c->sharded = true;
+  c->shard_rank = rank;
+  c->shard_window = (int32_t)window;
+  return EMT_OK;
+}
+
+static emt_status shard_copy(emt_ctx* c, int32_t peer, void* buf, int64_t bytes, void* stream, bool pack) {
+  const char* fn = pack ? "emt_shard_pack" : "emt_shard_unpack";
+  if (!c->sharded) return c->fail(EMT_ESTATE, std::string(fn) + ": the context is not a shard (emt_set_shard)");
+  const auto& lists = pack ? c->shard_send : c->shard_recv;
+  auto it = lists.find(peer);
+  const int64_t n_ends = it == lists.end() ? 0 : (int64_t)it->second.size();
+  const int64_t need = n_ends * c->win_w * 16;
+  if (buf == nullptr && pack) return EMT_OK;   // size query only (the caller read *bytes)
+  if (bytes != need)
+    return c->fail(EMT_EINVAL, std::string(fn) + ": the window's buffer for rank " + std::to_string(peer) + " holds " +
+                                   std::to_string(need) + " bytes, not " + std::to_string(bytes));
+  if (need > 0) {
+    if ((reinterpret_cast<uintptr_t>(buf) & 15u) != 0)
+      return c->fail(EMT_EINVAL, std::string(fn) + ": buffer not 16-byte aligned");
+    RingCopyParams p{};
+    p.le = c->d_le;
+    p.ends = c->d_shard_ends + (pack ? c->shard_send_off[peer] : c->shard_recv_off[peer]);
+    p.n_ends = (int32_t)n_ends;
+    p.w = (int32_t)c->win_w;
+    p.n0 = c->win_n0;
+    p.ring = c->d_ring;
+    p.buf = static_cast<unsigned long long*>(buf);
+    p.pack = pack ? 1 : 0;
+    cudaError_t e = launch_ring_copy(p, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return c->cuda_fail(e, fn);
+    c->launches += 1;
+  }
+  (pack ? c->shard_to_pack : c->shard_to_unpack).erase(peer);
+  return EMT_OK;
+}
+
+extern "C" emt_status emt_shard_pack(emt_ctx* c, int32_t peer, void* buf, int64_t cap, int64_t* bytes, void* stream) {
+  if (!c) return EMT_EINVAL;
+  if (!c->sharded) return c->fail(EMT_ESTATE, "emt_shard_pack: the context is not a shard (emt_set_shard)");
+  auto it = c->shard_send.find(peer);
+  const int64_t need = (it == c->shard_send.end() ? 0 : (int64_t)it->second.size()) * c->win_w * 16;
+  if (bytes) *bytes = need;
+  if (buf == nullptr) return EMT_OK;
+  if (cap < need) return c->fail(EMT_EINVAL, "emt_shard_pack: buffer of " + std::to_string(cap) + " bytes, " +
+                                                 std::to_string(need) + " needed");
+  return shard_copy(c, peer, buf, need, stream, true);
+}
+
+extern "C" emt_status emt_shard_unpack(emt_ctx* c, int32_t peer, const void* buf, int64_t bytes, void* stream) {
+  if (!c) return EMT_EINVAL;
+  return shard_copy(c, peer, const_cast<void*>(buf), bytes, stream, false);
 }
 
 extern "C" const char* emt_last_error(const emt_ctx* c) { return c ? c->err.c_str() : g_build_error.c_str(); }
@@ -2902,6 +3104,7 @@ extern "C" emt_status emt_load_state(emt_ctx* c, const void* buf, int64_t size) 
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return c->cuda_fail(e, "emt_load_state");
   c->step = hd.step;
+  shard_clear_window(c);
   return EMT_OK;
 }
 
@@ -2927,6 +3130,7 @@ extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_
 static emt_status adjoint_run(emt_ctx* c, const double* v_target, int64_t n_steps, int32_t ckpt_every,
                               double* grad, double* loss, int32_t on_device, void* stream) {
   if (c->batched) return c->fail(EMT_EINVAL, "emt_adjoint: a context built with a scenario set has no adjoint");
+  if (c->sharded) return c->fail(EMT_EINVAL, "emt_adjoint: runs the whole network; clear the shard (emt_set_shard NULL)");
   if (!c->cblocks.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: control blocks have no adjoint");
   if (!c->fdends.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: frequency-dependent lines have no adjoint");
   if (!c->nls.empty()) return c->fail(EMT_EINVAL, "emt_adjoint: nonlinear resistors have no adjoint");

@@ -246,6 +246,11 @@ struct FwdLimits {
 
 struct FwdParams {
   int32_t n_sub;
+  // a shard of the network (the other subsystems run elsewhere and meet it only
+  // through line rings): CTA (or warp) i runs sub[i], subsystem active[i] of the
+  // network, i < n_active; nullptr: all n_sub, active[i] = i
+  const int32_t* active;
+  int32_t n_active;
   FwdLimits lim;
   const SubDev* sub;
   const EpochDev* ep;
@@ -545,6 +550,22 @@ struct RingInitParams {
 
 // kernels / launchers (emt_kernels.cu)
 cudaError_t launch_ring_init(const RingInitParams& p, cudaStream_t st);
+
+// Ring slots a shard exchanges: for each listed line end e and j < w, the
+// slot its far ring holds for step n0 + d_e + j (the value e sent at step
+// n0 + j), slot far_ring + (n0 + d + j) mod depth; 16 bytes (tag and value
+// words) each.  pack = 1: ring -> buf[i w + j]; 0: buf -> ring.
+struct RingCopyParams {
+  const LineEndDev* le;
+  const int32_t* ends;
+  int32_t n_ends;
+  int32_t w;
+  int64_t n0;
+  unsigned long long* ring;
+  unsigned long long* buf;
+  int32_t pack;
+};
+cudaError_t launch_ring_copy(const RingCopyParams& p, cudaStream_t st);
 cudaError_t launch_companion(BranchDev* br, int64_t n_br, double dt, cudaStream_t st);
 cudaError_t launch_coupled_constants(CoupledEndDev* ce, int64_t n_ce, cudaStream_t st);
 cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st);

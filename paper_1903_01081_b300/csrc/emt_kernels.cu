@@ -377,6 +377,23 @@ __global__ void ring_init_kernel(RingInitParams P) {
   }
 }
 
+// Between the windows of a sharded run: copy the slots a window wrote for
+// remote readers (pack) or write them into this context's copy of the
+// rings (unpack).  No kernel of the run is in flight at either point, so
+// plain 16-byte accesses suffice.
+__global__ void ring_copy_kernel(RingCopyParams P) {
+  const int64_t total = (int64_t)P.n_ends * P.w;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = i / P.w, j = i - x * P.w;
+    const LineEndDev L = P.le[P.ends[x]];
+    const int64_t slot = L.far_ring + (P.n0 + L.d + j) % L.depth;
+    ulonglong2* r = reinterpret_cast<ulonglong2*>(P.ring) + slot;
+    ulonglong2* b = reinterpret_cast<ulonglong2*>(P.buf) + i;
+    if (P.pack) *b = *r;
+    else *r = *b;
+  }
+}
+
 // ------------------------------------------------------------ forward
 //
 // On B300 a warp issues at most one FP64 instruction per ~64 cycles however
@@ -971,8 +988,14 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   int* lefd = reinterpret_cast<int*>(smem_raw + L.lefd);            // per line end: FD end or -1
   int* cecnt = reinterpret_cast<int*>(smem_raw + L.cecnt);          // per coupled end: modes collected this step
 
-  const int sidx = blockIdx.x;
-  const SubDev S = P.sub[sidx];
+  // the subsystem this CTA runs: its description P.sub[blockIdx.x], its index in
+  // the network sidx0 (kept in shared memory: a register held through the step
+  // loop would cost the narrow instance a spill)
+  __shared__ int s_sidx;
+  const int sidx0 = P.active != nullptr ? P.active[blockIdx.x] : (int)blockIdx.x;
+  s_sidx = sidx0;   // every thread stores the same value and reads back its own store
+  const SubDev S = P.sub[blockIdx.x];
+#define SIDX (*(volatile int*)&s_sidx)
   const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = S.n, Q = S.q, n_str = S.n_str, nc = n + n_str, ldg = nc | 1;
   const int blk = (nc + Q - 1) / Q;   // columns per matvec task
@@ -990,7 +1013,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   const int item_threads = n_cb > 0 ? kItemThreads - 32 : kItemThreads;
   const int lv = P.lim.le;
   const int src_vs = P.lim.src;
-  const bool writes_lines = sidx != P.hold_sub;
+  const bool writes_lines = sidx0 != P.hold_sub;
   const int src_thread = T - 1 - tid;
   // update items: L/C branches, then line ends, then source branches, each
   // block starting on a warp boundary so that a warp runs one kind
@@ -1074,7 +1097,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   }
   // solve matrix: switch epoch te (by step) and runtime-switch state word
   const int n_rs = S.n_rs, n_states = S.n_states, n_te = S.n_ep / n_states;
-  int word = n_rs > 0 ? P.rs_word[sidx] : 0;
+  int word = n_rs > 0 ? P.rs_word[SIDX] : 0;
   for (int x = tid; x < n_rs; x += T) {
     s_rs[x] = P.rs[S.rs_off + x];
     s_rsi[x] = P.rs_prev_i[S.rs_off + x];
@@ -1102,8 +1125,8 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
       for (int j = 0; j < S.n_cache && f < 0; ++j)
         if (P.cache_tag[S.cache_slot0 + j] == key) f = j;
       if (f < 0) {   // replace the next slot in turn
-        f = P.cache_next[sidx];
-        P.cache_next[sidx] = f + 1 == S.n_cache ? 0 : f + 1;
+        f = P.cache_next[SIDX];
+        P.cache_next[SIDX] = f + 1 == S.n_cache ? 0 : f + 1;
         P.cache_tag[S.cache_slot0 + f] = -1;
         s_slot = -1 - f;
       } else {
@@ -1139,7 +1162,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
     // workspaces: the buffer the matrix is loaded into next, and the solve's partial sums
     if (factor_cta(J, gi_buf + wbuf * buf_len, part, reinterpret_cast<int*>(partf), &s_fp, &s_fsing)) {
       if (tid == 0 && atomicCAS(P.err, 0, 2) == 0) {   // EMT_ESINGULAR, subsystem, -, epoch
-        P.err[1] = sidx;
+        P.err[1] = SIDX;
         P.err[2] = word_;
         P.err[3] = te_;
       }
@@ -1201,7 +1224,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   if (warp == kPollWarp && n_le > 0) {
     const int p0 = (int)(P.n0 & 1);
     const FdFold F{n_fd > 0 ? lefd : nullptr, fdr, fdst, lef, inp + ie_base + (p0 ^ 1) * blk_len, fd_base};
-    const bool ok = collect_lines(P, n_le, (unsigned)P.n0, lane, sidx, leown, ledepth, rslot,
+    const bool ok = collect_lines(P, n_le, (unsigned)P.n0, lane, SIDX, leown, ledepth, rslot,
                                   inp + ie_base + p0 * blk_len, F);
     if (!ok && lane == 0) s_abort = 1;
     if (n_ce > 0)
@@ -1225,7 +1248,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
     // runtime-switch states decided from the previous step's solution
     int new_word = 0;
     for (int j = 0; j < n_rs; ++j) new_word |= s_rsbit[j] << j;
-    if (P.word_tape != nullptr && tid == 0) P.word_tape[(step - 1 - P.word_row0) * P.n_sub + sidx] = new_word;
+    if (P.word_tape != nullptr && tid == 0) P.word_tape[(step - 1 - P.word_row0) * P.n_sub + SIDX] = new_word;
     if (step >= next_ep_start || new_word != word) {
       while (te + 1 < n_te && P.ep[S.ep_off + (te + 1) * n_states].start <= step) ++te;
       next_ep_start = (te + 1 < n_te) ? P.ep[S.ep_off + (te + 1) * n_states].start : LLONG_MAX;
@@ -1365,7 +1388,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
       compensate(P, n, reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls), vv, recp);
     } else if (kExt && n_nl > 1) {
       compensate_multi(P, n, n_nl, reinterpret_cast<NlState*>(smem_raw + fwd_smem(P.lim).nls), vv, recp,
-                       P.nl_seg + S.nl_off, sidx, step, &s_abort);
+                       P.nl_seg + S.nl_off, SIDX, step, &s_abort);
       if (s_abort) break;
     }
 
@@ -1471,7 +1494,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
         bool ok = true;
         for (int e = item_threads - 1 - tid; e < n_le && ok; e += item_threads) {
           double v = 0.0;
-          ok = poll_slot(P, P.ring + 2 * EMT_CHK(P.err, leown[e] + rslot[e], P.bnd.ring, kChkRingRead), tag, sidx,
+          ok = poll_slot(P, P.ring + 2 * EMT_CHK(P.err, leown[e] + rslot[e], P.bnd.ring, kChkRingRead), tag, SIDX,
                          e, v);
           ie_next[e] = v;
           const int nx = rslot[e] + 1;
@@ -1517,7 +1540,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
     if (n_rs > 0 && tid == 0) {
       int w = 0;
       for (int j = 0; j < n_rs; ++j) w |= s_rsbit[j] << j;
-      P.rs_word[sidx] = w;
+      P.rs_word[SIDX] = w;
     }
   }
 }
@@ -1536,9 +1559,20 @@ __global__ void gather_kernel(const double* rec, int32_t n_rec, int64_t n_scen_r
 
 }  // namespace
 
+#undef SIDX
+
 cudaError_t launch_ring_init(const RingInitParams& p, cudaStream_t st) {
   if (p.n_le <= 0) return cudaSuccess;
   ring_init_kernel<<<(unsigned)p.n_le, 64, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ring_copy(const RingCopyParams& p, cudaStream_t st) {
+  const int64_t total = (int64_t)p.n_ends * p.w;
+  if (total <= 0) return cudaSuccess;
+  const int th = 256;
+  const int64_t blocks = std::min<int64_t>((total + th - 1) / th, 148 * 8);
+  ring_copy_kernel<<<(unsigned)blocks, th, 0, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -1600,11 +1634,12 @@ cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide, bool 
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[v], kFwdThreads, smem);
     if (e != cudaSuccess) return e;
-    if ((long long)per_sm * n_sm < p.n_sub) continue;
+    const int grid = p.active != nullptr ? p.n_active : p.n_sub;
+    if ((long long)per_sm * n_sm < grid) continue;
     FwdParams arg = p;
     void* args[] = {&arg};
     // cooperative launch: all CTAs co-resident, so every ring wait can end
-    return cudaLaunchCooperativeKernel(fns[v], dim3(p.n_sub), dim3(kFwdThreads), args, smem, st);
+    return cudaLaunchCooperativeKernel(fns[v], dim3(grid), dim3(kFwdThreads), args, smem, st);
   }
   return cudaErrorCooperativeLaunchTooLarge;
 }

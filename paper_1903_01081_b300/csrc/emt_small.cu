@@ -85,8 +85,9 @@ __global__ void __launch_bounds__(32 * kSmallWarps) fwd_small_kernel(FwdParams P
   extern __shared__ __align__(16) unsigned char smem_all[];
   const SmallSmem L = small_smem(P.lim);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sidx = blockIdx.x * kSmallWarps + warp;
-  if (sidx >= P.n_sub) return;   // (no CTA barrier in this kernel: a warp past the last subsystem just leaves)
+  const int wi = blockIdx.x * kSmallWarps + warp;
+  if (wi >= (P.active != nullptr ? P.n_active : P.n_sub)) return;   // (no CTA barrier here: a spare warp leaves)
+  const int sidx = P.active != nullptr ? P.active[wi] : wi;
   unsigned char* sm = smem_all + (size_t)warp * L.bytes;
   double* gi = reinterpret_cast<double*>(sm + L.gi);
   double* iv = reinterpret_cast<double*>(sm + L.iv);
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(32 * kSmallWarps) fwd_small_kernel(FwdParams P
   int* srcg = reinterpret_cast<int*>(sm + L.srcg);
   int* recp = reinterpret_cast<int*>(sm + L.recp);
 
-  const SubDev S = P.sub[sidx];
+  const SubDev S = P.sub[wi];
   const int n = S.n, n_str = S.n_str, nc = n + n_str, ldg = nc | 1;
   const int n_lc = S.n_lc, n_sb = S.n_sb, n_le = S.n_le, n_il = S.n_il, n_src = S.n_src;
   const int ie_base = n_lc + n_sb, zero_slot = ie_base + 2 * n_le;
@@ -344,7 +345,7 @@ cudaError_t launch_forward_small(const FwdParams& p, cudaStream_t st) {
   int dev = 0, n_sm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = (p.n_sub + kSmallWarps - 1) / kSmallWarps;
+  const int grid = ((p.active != nullptr ? p.n_active : p.n_sub) + kSmallWarps - 1) / kSmallWarps;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_small_kernel, 32 * kSmallWarps, smem);
   if (e != cudaSuccess) return e;
   if ((long long)per_sm * n_sm < grid) return cudaErrorCooperativeLaunchTooLarge;

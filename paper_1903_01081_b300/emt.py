@@ -117,6 +117,11 @@ def load_library(build_if_needed: bool = True):
         "emt_read_controls": [P, P, I64, I32],
         "emt_save_state": [P, P, I64, P],
         "emt_load_state": [P, P, I64],
+        "emt_get_node_ctas": [P, P],
+        "emt_get_line_ends": [P, P, P, P],
+        "emt_set_shard": [P, P, I32],
+        "emt_shard_pack": [P, I32, P, I64, P, P],
+        "emt_shard_unpack": [P, I32, P, I64, P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -459,6 +464,52 @@ def emt_get_node_order(ctx: Ctx) -> np.ndarray:
     perm = np.zeros(ctx.n_nodes, dtype=np.int32)
     _check(ctx, load_library().emt_get_node_order(ctx.handle, perm.ctypes.data if perm.size else None))
     return perm
+
+
+def emt_get_node_ctas(ctx: Ctx) -> np.ndarray:
+    """CTA of every node, in the caller's node order (include/emt.h)."""
+    cta = np.zeros(ctx.n_nodes, dtype=np.int32)
+    _check(ctx, load_library().emt_get_node_ctas(ctx.handle, cta.ctypes.data if cta.size else None))
+    return cta
+
+
+def emt_get_line_ends(ctx: Ctx):
+    """(cta, far_end, d) of every line end, library order (include/emt.h)."""
+    n = emt_get_info(ctx, "n_line_ends")
+    cta, far, d = (np.zeros(n, dtype=np.int32) for _ in range(3))
+    ptr = (lambda a: a.ctypes.data if a.size else None)
+    _check(ctx, load_library().emt_get_line_ends(ctx.handle, ptr(cta), ptr(far), ptr(d)))
+    return cta, far, d
+
+
+def emt_set_shard(ctx: Ctx, owner, rank: int) -> None:
+    """Run only the CTAs with owner[c] == rank (owner None: all of them)."""
+    if owner is None:
+        _check(ctx, load_library().emt_set_shard(ctx.handle, None, int(rank)))
+        return
+    own = _arr(owner, np.int32)
+    if own.size != emt_get_info(ctx, "n_ctas"):
+        raise ValueError("owner needs one rank per CTA")
+    _check(ctx, load_library().emt_set_shard(ctx.handle, own.ctypes.data, int(rank)))
+
+
+def emt_shard_pack(ctx: Ctx, peer: int, out=None, stream=None) -> int:
+    """Pack the last window's slots for rank ``peer`` into ``out`` (a CUDA
+    uint8 torch tensor of at least that many bytes); out None: the size only."""
+    lib = load_library()
+    size = ctypes.c_int64(0)
+    if out is None:
+        _check(ctx, lib.emt_shard_pack(ctx.handle, int(peer), None, 0, ctypes.byref(size), None))
+        return size.value
+    _check(ctx, lib.emt_shard_pack(ctx.handle, int(peer), out.data_ptr(), out.numel() * out.element_size(),
+                                   ctypes.byref(size), _stream_handle(stream)))
+    return size.value
+
+
+def emt_shard_unpack(ctx: Ctx, peer: int, buf, n_bytes: int, stream=None) -> None:
+    """Write rank ``peer``'s packed slots (a CUDA tensor, ``n_bytes`` bytes) into the rings."""
+    _check(ctx, load_library().emt_shard_unpack(ctx.handle, int(peer), buf.data_ptr() if n_bytes else None,
+                                                int(n_bytes), _stream_handle(stream)))
 
 
 def emt_last_error(ctx: Optional[Ctx] = None) -> str:
