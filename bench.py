@@ -705,6 +705,58 @@ def size_leg(net, workload, steps, reps=3, n_check=1000, cpu_steps=1000):
     return out
 
 
+def phases_leg(steps=None):
+    """clock64 cycles per phase of every step of the single-network kernel
+    (the phase-clock build, EMT_PHASES=1; this function re-runs bench.py
+    under it when needed) for the 12-node RLC network, the strict 500 x 6
+    reading and the large-scale network: per step, the mean over CTAs and
+    the CTA with the most own work (injection + solve + node voltages +
+    updates), beside the event-timed microseconds per step."""
+    from paper_1903_01081_b300 import emt, netgen as g
+    if not emt.phases_build():
+        cmd = [sys.executable, os.path.abspath(__file__), "--leg", "phases"]
+        if steps:
+            cmd += ["--leg-steps", str(steps)]
+        r = subprocess.run(cmd, capture_output=True, text=True, env=dict(os.environ, EMT_PHASES="1"))
+        if r.returncode != 0:
+            raise RuntimeError("phase-clock run failed: " + r.stderr[-2000:])
+        return json.loads([x for x in r.stdout.splitlines() if x.startswith("{")][-1])["phases"]
+    import torch
+    N = steps or 20000
+    cases = (("single_rlc_12_nodes", g.single_rlc()), ("strict_500x6", g.large_scale(strict_500=True)),
+             ("large_scale_3000_nodes", g.large_scale()))
+    names = emt.PHASES
+    out = {}
+    for tag, net in cases:
+        n = min(N, net.n_steps) if tag == "single_rlc_12_nodes" else N
+        sim = emt.Simulator(net, n_steps=n)
+        stream = torch.cuda.current_stream()
+        sim.run(min(n, 2000), stream)          # warm-up launch
+        sim.sync()
+        sim.reset()
+        emt.emt_phase_clocks(sim.ctx, reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.run(n, stream)
+        e1.record(stream)
+        sim.sync()
+        ms = e0.elapsed_time(e1)
+        ph = emt.emt_phase_clocks(sim.ctx).astype(np.float64)
+        steps_run = ph[:, 6]
+        per = ph[:, :6] / steps_run[:, None]
+        own = per[:, 0] + per[:, 1] + per[:, 2] + per[:, 3]
+        crit = int(np.argmax(own))
+        cyc_per_step = float(np.max(ph[:, 7] / steps_run))   # the slowest CTA's (independent subsystems end apart)
+        out[tag] = {"ctas": int(ph.shape[0]), "largest_cta_nodes": sim.info("max_subsystem_nodes"),
+                    "steps": n, "us_per_step_events": 1e3 * ms / n,
+                    "cycles_per_step_span": cyc_per_step,
+                    "sm_mhz_implied": cyc_per_step / (1e3 * ms / n),
+                    "mean_over_ctas": {k: round(float(v), 1) for k, v in zip(names[:6], per.mean(axis=0))},
+                    "critical_cta": {"cta": crit, **{k: round(float(v), 1) for k, v in zip(names[:6], per[crit])}}}
+        sim.close()
+    return out
+
+
 def scale_legs(steps=None, reps=3):
     """The large-scale family at two other sizes: the strict reading of
     500 subsystems of 6 nodes (3,000 nodes), and 500 subsystems of 6..60
@@ -907,7 +959,7 @@ def main():
     ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines",
                                       "fd_lines", "nonlinear", "controls", "sizes", "control_study",
                                       "arrester_study", "fd_line_study", "coupled_line_study", "converter_stations",
-                                      "bus_arresters"],
+                                      "bus_arresters", "phases"],
                     default="all",
                     help="all: the JSON line with every leg; single: the single-network leg only; "
                          "n1 / shared_g / adjoint: that leg alone (profiling)")
@@ -926,7 +978,7 @@ def main():
         return run_reference(args)
     if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "fd_lines", "nonlinear",
                     "controls", "sizes", "control_study", "arrester_study", "fd_line_study", "coupled_line_study",
-                    "converter_stations", "bus_arresters"):
+                    "converter_stations", "bus_arresters", "phases"):
         return run_leg(args)
     return run_ours(args)
 
@@ -953,6 +1005,8 @@ def run_leg(args):
         out = bus_arrester_leg(args.leg_steps, reps=1)
     elif args.leg == "sizes":
         out = scale_legs(args.leg_steps, reps=1)
+    elif args.leg == "phases":
+        out = {"phases": phases_leg(args.leg_steps)}
     elif args.leg in ("control_study", "arrester_study", "fd_line_study", "coupled_line_study"):
         shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
         which = {"control_study": "controls", "arrester_study": "arresters", "fd_line_study": "fd",

@@ -412,7 +412,13 @@ emt_status emt_sync(emt_ctx* ctx, int32_t* dev_err_info);
  * a second stream while the reverse sweep of segment j runs, when both
  * persistent grids fit on the device together; 0: one stream),
  * "debug_hold_lines" (that subsystem never sends line values; -1 none;
- * for failure-path tests).  EINVAL for an unknown key. */
+ * for failure-path tests), "warp_per_subsystem" (1: one warp per subsystem,
+ * for networks of subsystems of at most 32 nodes with basic elements),
+ * "state_space" (the step of each subsystem as one product y = M x with M
+ * from G^-1, for networks whose subsystems hold basic elements only --
+ * R/L/C branches, sources, fixed-time switches, lossless lines: 0 off,
+ * 1 auto (default: while every subsystem's M has at most 2,048 entries),
+ * 2 on).  EINVAL for an unknown key. */
 emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
 
 /* Read-only facts: "n_subsystems", "n_ctas" (the CTAs of the persistent
@@ -434,7 +440,8 @@ emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
  * subsystem's control graph),
  * "n_matrix_variants", "scenarios_per_cta", "batch_threads", "batch_groups"
  * (subsystem groups per step of the multi-scenario kernel),
- * "graph_launches", "autotuned", "shard_rank" (-1 unless a shard),
+ * "graph_launches", "autotuned", "state_space" (1 while the state-space
+ * form runs emt_step_n), "warp_per_subsystem", "shard_rank" (-1 unless a shard),
  * "shard_window" (see emt_set_shard; 0 unless a shard), "shard_ctas" (CTAs
  * this context runs). */
 emt_status emt_get_info(const emt_ctx* ctx, const char* key, int64_t* value);
@@ -496,6 +503,22 @@ emt_status emt_shard_pack(emt_ctx* ctx, int32_t peer, void* buf, int64_t cap, in
  * cuda_stream: the caller orders it after the buffer's arrival (and before
  * the next window). */
 emt_status emt_shard_unpack(emt_ctx* ctx, int32_t peer, const void* buf, int64_t bytes, void* cuda_stream);
+
+/* Per-phase cycle counts of the single-network kernel, from the phase-clock
+ * build of the library (compiled with -DEMT_PHASE_CLOCKS; libemt_phases.so):
+ * out[c * 8 + k] for every CTA c < n_ctas (host memory), summed over all
+ * steps of all launches since the last reset, as clock64 cycles seen by the
+ * CTA's thread 0:
+ *   k = 0 process 2 (nodal injections), 1 process 4 (the solve's partial
+ *   sums), 2 node voltages and the compensation method, 3 thread 0's own
+ *   process-1 updates, 4 the wait of the thread that polls the CTA's first
+ *   line end (its own count), 5 from thread 0's updates to the end-of-step
+ *   barrier (the other updates and the line-value polls), 6 steps, 7 the
+ *   cycles from the first step's start to the last step's end of the last
+ *   launch.
+ * out may be NULL; reset != 0 zeroes the counters afterwards.  Synchronises
+ * the device.  EINVAL in the normal build or with more than 2048 CTAs. */
+emt_status emt_phase_clocks(emt_ctx* ctx, uint64_t* out, int32_t reset);
 
 /* Last error message of ctx (or of the last failed build if ctx == NULL). */
 const char* emt_last_error(const emt_ctx* ctx);

@@ -10,6 +10,9 @@ LIB_PATH = os.path.join(HERE, "libemt.so")
 # the checks build: every device-data index into a global array tested against the array's length (a bad one
 # latches an error that emt_sync reports, and the access is kept in bounds); loaded when EMT_CHECKS=1
 CHECKS_LIB_PATH = os.path.join(HERE, "libemt_checks.so")
+# the phase-clock build: clock64 cycles per phase of every step of the single-network kernel, read by
+# emt_phase_clocks (bench.py --leg phases); loaded when EMT_PHASES=1
+PHASES_LIB_PATH = os.path.join(HERE, "libemt_phases.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -29,10 +32,11 @@ def needs_build(path: str = LIB_PATH) -> bool:
     return any(os.path.getmtime(f) > t for f in sources() + headers())
 
 
-def build(force: bool = False, verbose: bool = False, checks: bool = False) -> str:
-    """Build ``libemt.so`` (``libemt_checks.so`` with checks=True) with nvcc if
-    it is missing or stale; return its path."""
-    path = CHECKS_LIB_PATH if checks else LIB_PATH
+def build(force: bool = False, verbose: bool = False, checks: bool = False, phases: bool = False) -> str:
+    """Build ``libemt.so`` (``libemt_checks.so`` with checks=True,
+    ``libemt_phases.so`` with phases=True) with nvcc if it is missing or
+    stale; return its path."""
+    path = CHECKS_LIB_PATH if checks else (PHASES_LIB_PATH if phases else LIB_PATH)
     if not force and not needs_build(path):
         return path
     nvcc = os.environ.get("NVCC", "nvcc")
@@ -43,6 +47,8 @@ def build(force: bool = False, verbose: bool = False, checks: bool = False) -> s
            "-cudart", "shared", "-Xlinker", "-rpath,/usr/local/cuda/lib64", "-o", tmp] + sources()
     if checks:
         cmd.insert(1, "-DEMT_CHECKS")
+    if phases:
+        cmd.insert(1, "-DEMT_PHASE_CLOCKS")
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)
@@ -53,3 +59,4 @@ def build(force: bool = False, verbose: bool = False, checks: bool = False) -> s
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
     print(build(force=True, checks=True))
+    print(build(force=True, phases=True))

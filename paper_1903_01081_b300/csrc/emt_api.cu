@@ -31,6 +31,11 @@ const double kTwoPi = 2.0 * 3.14159265358979323846;
 // subsystem (double + single-precision parts).
 const double kSolveSmemBytes = 150.0 * 1024;
 
+// The state-space form runs by default while every subsystem's M has at
+// most this many entries: beyond, its product's work outgrows what the
+// shorter chain saves against the CTA kernel.
+const int64_t kSsAutoEntries = 2048;
+
 // Source-voltage table budget per chunk of a launch (doubles): 32 MiB.
 const int64_t kSourceTableDoubles = 4 << 20;
 
@@ -92,6 +97,20 @@ struct emt_ctx {
   // warps spread a subsystem's FP64 work over all four FP64 pipes of its SM
   bool small_ok = false;
   bool use_small = false;
+  // state-space form (emt_ss.cu): eligible networks (ss_ok) run it unless the option state_space is 0;
+  // auto (1) only while every subsystem's M is at most kSsAutoEntries, 2 forces it
+  bool ss_ok = false;
+  int ss_mode = 1;
+  int64_t ss_len = 0, ss_max_entries = 0;
+  int ss_rows = 0, ss_cols = 0, ss_ln = 0;
+  std::vector<SsSubDev> ss;
+  std::vector<int32_t> ss_lnode, ss_lptr, ss_lend;
+  SsSubDev* d_ss = nullptr;
+  double* d_ss_m = nullptr;
+  float* d_ss_mlo = nullptr;
+  int32_t* d_ss_lnode = nullptr;
+  int32_t* d_ss_lptr = nullptr;
+  int32_t* d_ss_lend = nullptr;
   bool forward_narrow = false;   // emt_adjoint: its re-runs share the device with the reverse sweep   // electrical subsystems (components); n_sub counts CTAs, several components each when packed
   int64_t comp_sum_n2 = 0, comp_max_n = 0;   // over the components
   FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0};
@@ -1832,13 +1851,23 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
     c->cache_next0.push_back(0);   // the count of run-time factorisations
   }
 
-  // -------- matvec blocking: a task's n/q FMAs and a node's q-1 adds are
-  // both FP64 instructions on one warp, so q ~ sqrt(n), within the CTA
+  // -------- matvec blocking: n q tasks (at most one per thread) of
+  // ceil(nc / q) dependent FMAs, then a node's q - 1 adds: q minimises that
+  // chain of FP64 instructions (ties: nearest sqrt(nc))
   for (int s = 0; s < S; ++s) {
     SubDev& sd = c->subs[s];
-    const int n = std::max(sd.n, 1);
-    const int q = (int)std::lround(std::sqrt((double)(n + sd.n_str)));
-    sd.q = std::max(1, std::min(q, kFwdThreads / n));
+    const int n = std::max(sd.n, 1), ncol = std::max(sd.n + sd.n_str, 1);
+    int q = 1;
+    long best = LONG_MAX;
+    const double root = std::sqrt((double)ncol);
+    for (int t = 1; t <= std::min(std::min(32, ncol), std::max(1, kFwdThreads / n)); ++t) {
+      const long chain = (ncol + t - 1) / t + (t - 1);
+      if (chain < best || (chain == best && std::fabs(t - root) < std::fabs(q - root))) {
+        best = chain;
+        q = t;
+      }
+    }
+    sd.q = q;
     c->lim.q = std::max(c->lim.q, sd.q);
     // every task runs the same number of columns (zero columns pad the
     // last block), so that no warp diverges inside the FMA loop
@@ -1861,6 +1890,65 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   // with R/L/C branches, sources, fixed-time switches and lossless lines only
   c->small_ok = !scen && S > 0 && c->lim.n <= kSmallMaxNodes && c->lim.ce == 0 && c->lim.fd == 0 &&
                 c->lim.cb == 0 && c->lim.ci == 0 && c->lim.nl == 0 && c->rswitches.empty() && !c->lazy;
+
+  // -------- the state-space form (emt_ss.cu): the same element set; per
+  // subsystem M's shape, its line-end nodes, and Q lanes per row of the
+  // product chosen against a model of the step: its chain (ceil(cols/Q)
+  // FMAs, log2 Q shuffle-adds, one add, the line outputs of a node) and the
+  // FP64 instructions of the CTAs one SM holds, on its four pipes
+  c->ss_ok = !scen && S > 0 && c->lim.ce == 0 && c->lim.fd == 0 && c->lim.cb == 0 && c->lim.ci == 0 &&
+             c->lim.nl == 0 && c->rswitches.empty() && !c->lazy;
+  if (c->ss_ok) {
+    int n_sm = 148;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device);
+    const int cps = (S + n_sm - 1) / std::max(n_sm, 1);
+    c->ss.assign(S, SsSubDev{});
+    c->ss_lend.assign(c->line_ends.size(), 0);
+    int64_t off = 0;
+    for (int s = 0; s < S && c->ss_ok; ++s) {
+      const SubDev& sd = c->subs[s];
+      std::map<int, std::vector<int>> by_node;   // ends grouped by their node, nodes ascending
+      for (int x = 0; x < sd.n_le; ++x) by_node[c->line_ends[sd.le_off + x].node].push_back(x);
+      SsSubDev& Q = c->ss[s];
+      Q.n_ln = (int32_t)by_node.size();
+      Q.ln_off = (int32_t)c->ss_lnode.size();
+      Q.ptr_off = (int32_t)c->ss_lptr.size();
+      int pos = 0, most = 0;
+      for (const auto& kv : by_node) {
+        c->ss_lnode.push_back(kv.first);
+        c->ss_lptr.push_back(pos);
+        for (int x : kv.second) c->ss_lend[sd.le_off + pos++] = x;
+        most = std::max(most, (int)kv.second.size());
+      }
+      c->ss_lptr.push_back(pos);
+      Q.rows = sd.n_lc + sd.n;
+      Q.cols = sd.n_lc + sd.n_src + Q.n_ln;
+      if (Q.rows > kSsThreads - 32 || Q.cols < 1) {
+        c->ss_ok = false;
+        break;
+      }
+      double best = 1e300;
+      for (int qq = 1, lg = 0; qq <= 32 && Q.rows * qq <= kSsThreads - 32; qq *= 2, ++lg) {
+        const double chain = (Q.cols + qq - 1) / qq + lg + 1 + (most + qq - 1) / qq;
+        const double warps = (Q.rows * qq + 31) / 32;
+        const double cost = std::max(chain, cps * warps * chain / 4.0);
+        if (cost < best) {
+          best = cost;
+          Q.q = qq;
+        }
+      }
+      Q.m_off = off;
+      off += (int64_t)sd.n_ep * Q.rows * Q.cols;
+      c->ss_rows = std::max(c->ss_rows, Q.rows);
+      c->ss_cols = std::max(c->ss_cols, Q.cols);
+      c->ss_ln = std::max(c->ss_ln, Q.n_ln);
+      c->ss_max_entries = std::max<int64_t>(c->ss_max_entries, (int64_t)Q.rows * Q.cols);
+    }
+    c->ss_len = off;
+    if (c->ss_ok && ss_smem_bytes(c->ss_rows, c->ss_cols, std::max(c->lim.n, 1), c->lim.le, c->lim.src, c->ss_ln) *
+                            (size_t)cps > 220 * 1024)
+      c->ss_ok = false;
+  }
 
   // -------- injection-lane range of every internal node
   c->node_l0.assign(N, 0);
@@ -1931,6 +2019,14 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_cstate, 2 * c->cblocks.size());
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_cy, c->cblocks.size());
   if (e == cudaSuccess) e = c->alloc_zero(&c->d_le_prev, c->line_ends.size());
+  if (c->ss_ok) {
+    UP(d_ss, ss)
+    UP(d_ss_lnode, ss_lnode)
+    UP(d_ss_lptr, ss_lptr)
+    UP(d_ss_lend, ss_lend)
+    if (e == cudaSuccess) e = c->alloc_zero(&c->d_ss_m, (size_t)c->ss_len);
+    if (e == cudaSuccess) e = c->alloc_zero(&c->d_ss_mlo, (size_t)c->ss_len);
+  }
   if (c->lazy) {
     UP(d_cache_tag0, cache_tag0)
     UP(d_cache_tag, cache_tag0)
@@ -2033,6 +2129,28 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
 
 // Subsystems that factorise their states at run time: after a prefactor,
 // the cache holds each epoch's initial state (slot te) and nothing else.
+// M of every (subsystem, epoch) of the state-space form, from the G^-1
+// just prefactored (emt_ss.cu).
+static cudaError_t build_state_space(emt_ctx* c, cudaStream_t st) {
+  if (!c->ss_ok) return cudaSuccess;
+  FwdParams p{};
+  p.n_sub = c->n_sub;
+  p.sub = c->d_sub;
+  p.ep = c->d_ep;
+  p.ginv = c->d_ginv;
+  p.ginv_lo = c->d_ginv_lo;
+  p.br = c->d_br;
+  p.lc_idx = c->d_lc_idx;
+  p.sb_idx = c->d_sb_idx;
+  p.le = c->d_le;
+  p.str_slot = c->d_str_slot;
+  p.ss = c->d_ss;
+  p.ss_m = c->d_ss_m;
+  p.ss_mlo = c->d_ss_mlo;
+  p.ss_lnode = c->d_ss_lnode;
+  return launch_ss_build(p, st);
+}
+
 static cudaError_t reset_matrix_cache(emt_ctx* c, cudaStream_t st) {
   if (!c->lazy) return cudaSuccess;
   cudaError_t e = cudaMemcpyAsync(c->d_cache_tag, c->d_cache_tag0, c->cache_tag0.size() * sizeof(long long),
@@ -2094,6 +2212,7 @@ extern "C" emt_status emt_prefactor(emt_ctx* c) {
   }
   if (e == cudaSuccess) e = launch_prefactor(p, std::max(c->lim.n, 1), nullptr);
   if (e == cudaSuccess) e = reset_matrix_cache(c, nullptr);
+  if (e == cudaSuccess) e = build_state_space(c, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   std::vector<int32_t> status(mat_sub.size(), 0);
   if (e == cudaSuccess && !status.empty())
@@ -2263,9 +2382,15 @@ static void shard_clear_window(emt_ctx* c) {
   c->win_n0 = c->win_w = 0;
 }
 
+static bool state_space_runs(const emt_ctx* c) {
+  return c->ss_ok && !(c->small_ok && c->use_small) &&
+         (c->ss_mode == 2 || (c->ss_mode == 1 && c->ss_max_entries <= kSsAutoEntries));
+}
+
 static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, const RecSpec& rs) {
   const bool small = c->small_ok && c->use_small;
-  if ((small ? small_smem_bytes(c->lim) : forward_smem_bytes(c->lim)) > 227 * 1024)
+  const bool ssf = state_space_runs(c);
+  if (!ssf && (small ? small_smem_bytes(c->lim) : forward_smem_bytes(c->lim)) > 227 * 1024)
     return c->fail(EMT_ERESOURCE, "a subsystem needs more shared memory than one CTA has");
   // source table for one chunk of steps at a time (grow-only buffer)
   const int64_t chunk =
@@ -2342,6 +2467,16 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
   p.cache_next = c->d_cache_next;
   p.lazy_work = c->d_lazy_work;
   p.sw = c->d_sw;
+  p.ss = c->d_ss;
+  p.ss_m = c->d_ss_m;
+  p.ss_mlo = c->d_ss_mlo;
+  p.ss_lnode = c->d_ss_lnode;
+  p.ss_lptr = c->d_ss_lptr;
+  p.ss_lend = c->d_ss_lend;
+  p.ss_rows = c->ss_rows;
+  p.ss_cols = c->ss_cols;
+  p.ss_ln = c->ss_ln;
+  p.bnd.ssm = std::max<int64_t>(c->ss_len, 1);
   if (c->sharded) {
     p.sub = c->d_shard_sub;
     p.active = c->d_shard_active;
@@ -2362,7 +2497,9 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
     if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n source table");
     p.n0 = c->step + 1;
     p.n_steps = len;
-    e = small ? launch_forward_small(p, st) : launch_forward(p, st, !c->forward_narrow, c->lazy || c->lim.nl > 1);
+    e = ssf     ? launch_forward_ss(p, st)
+        : small ? launch_forward_small(p, st)
+                : launch_forward(p, st, !c->forward_narrow, c->lazy || c->lim.nl > 1);
     if (e == cudaErrorCooperativeLaunchTooLarge)
       return c->fail(EMT_ERESOURCE, "persistent launch of " + std::to_string(c->n_sub) +
                                         " CTAs cannot be co-resident on this device");
@@ -2715,6 +2852,15 @@ extern "C" emt_status emt_set_option(emt_ctx* c, const char* key, int64_t value)
     c->use_small = value != 0;
     return EMT_OK;
   }
+  if (k == "state_space") {   // 0 off, 1 auto (default), 2 on: the state-space form (emt_ss.cu)
+    if (value < 0 || value > 2) return c->fail(EMT_EINVAL, "state_space is 0, 1 or 2");
+    if (value == 2 && !c->ss_ok)
+      return c->fail(EMT_EINVAL, "this network does not fit the state-space form (subsystems of basic elements "
+                                 "whose M has at most " + std::to_string(kSsThreads - 32) + " rows)");
+    cudaDeviceSynchronize();
+    c->ss_mode = (int)value;
+    return EMT_OK;
+  }
   if (k == "adjoint_overlap") {   // 0: the adjoint re-runs segments on the caller's stream only
     c->overlap_adjoint = value != 0;
     return EMT_OK;
@@ -2771,6 +2917,7 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "shard_rank") *value = c->sharded ? c->shard_rank : -1;
   else if (k == "shard_window") *value = c->sharded ? c->shard_window : 0;
   else if (k == "shard_ctas") *value = c->sharded ? (int64_t)c->shard_active.size() : c->n_sub;
+  else if (k == "state_space") *value = state_space_runs(c) ? 1 : 0;
   else if (k == "warp_per_subsystem") *value = c->small_ok && c->use_small ? 1 : 0;
   else if (k == "lazy_subsystems") {   // subsystems whose switch states are factorised at run time
     int64_t m = 0;
@@ -2958,6 +3105,16 @@ extern "C" emt_status emt_shard_pack(emt_ctx* c, int32_t peer, void* buf, int64_
 extern "C" emt_status emt_shard_unpack(emt_ctx* c, int32_t peer, const void* buf, int64_t bytes, void* stream) {
   if (!c) return EMT_EINVAL;
   return shard_copy(c, peer, const_cast<void*>(buf), bytes, stream, false);
+}
+
+extern "C" emt_status emt_phase_clocks(emt_ctx* c, uint64_t* out, int32_t reset) {
+  if (!c) return EMT_EINVAL;
+  if (c->n_sub > kPhaseCtas)
+    return c->fail(EMT_EINVAL, "emt_phase_clocks: more than " + std::to_string(kPhaseCtas) + " CTAs");
+  cudaError_t e = phase_clocks(reinterpret_cast<unsigned long long*>(out), c->n_sub, reset != 0);
+  if (e == cudaErrorNotSupported) return c->fail(EMT_EINVAL, "emt_phase_clocks: not the phase-clock build");
+  if (e != cudaSuccess) return c->cuda_fail(e, "emt_phase_clocks");
+  return EMT_OK;
 }
 
 extern "C" const char* emt_last_error(const emt_ctx* c) { return c ? c->err.c_str() : g_build_error.c_str(); }
@@ -3548,6 +3705,7 @@ extern "C" emt_status emt_prefactor_noalloc(emt_ctx* c, void* stream) {
   p.rs = c->d_rs;
   if (e == cudaSuccess) e = launch_prefactor(p, std::max(c->lim.n, 1), st);
   if (e == cudaSuccess) e = reset_matrix_cache(c, st);
+  if (e == cudaSuccess) e = build_state_space(c, st);
   int32_t* first = status + n_mats;
   if (e == cudaSuccess) e = cudaMemsetAsync(first, 0x7f, sizeof(int32_t), st);
   if (e == cudaSuccess) {

@@ -231,7 +231,27 @@ struct EpochDev {
 // doubles, history slots, source-table doubles, nonlinear columns, tape and
 // target doubles.
 struct Bounds {
-  int64_t ring, ginv, rec, h, src, nlz, tape, target;
+  int64_t ring, ginv, rec, h, src, nlz, tape, target, ssm;
+};
+
+// The step of one subsystem in state-space form (emt_ss.cu).  With
+// x(n) = [h(n-1) | v_src(n) | J(n)] -- the history currents of its L/C
+// slots, its sources' voltages, and per node with line ends the sum J of
+// the values they consume -- both the node voltages v(n) and the new
+// history currents h(n) are linear in x(n): y(n) = [h(n) | v(n)] = M x(n)
+// (processes 2 and 4, v = G^-1 i, and process 1's h from v, in one
+// matrix).  The values the line ends send follow from v directly, c_e =
+// -(2/Z) v_node - I_e.  M per switch epoch, rows x cols, row-major at m_off
+// + epoch rows cols in FwdParams::ss_m (ss_mlo: its single-precision
+// remainder).  Used for networks of small subsystems with the basic
+// elements only, where the step's chain of dependent FP64 operations, not
+// its work, sets the time.
+struct SsSubDev {
+  int32_t rows, cols;   // rows = n_lc + n; cols = n_lc + n_src + n_ln
+  int32_t q;            // lanes per row of the matvec (a power of two <= 32)
+  int32_t n_ln;         // nodes with line ends: ss_lnode[ln_off + j], their ends ss_lend[ss_lptr[ptr_off + j] ..]
+  int32_t ln_off, ptr_off;
+  int64_t m_off;
 };
 
 // Per-launch upper bounds that size the forward kernel's shared memory.
@@ -307,6 +327,14 @@ struct FwdParams {
   int32_t* cache_next;         // per subsystem: next slot to replace; then the count of run-time factorisations
   double* lazy_work;
   const SwitchDev* sw;         // closed switches of each epoch (EpochDev sw_off / n_sw)
+  // state-space form (SsSubDev): per subsystem of the network, M and its remainder, the largest rows / cols
+  const SsSubDev* ss;
+  const double* ss_m;
+  const float* ss_mlo;
+  const int32_t* ss_lnode;     // local node of each line-end node slot
+  const int32_t* ss_lptr;      // per slot: first position in ss_lend (n_ln + 1 per subsystem, from S.le_off)
+  const int32_t* ss_lend;      // subsystem-local line ends grouped by node (n_le per subsystem, at S.le_off)
+  int32_t ss_rows, ss_cols, ss_ln;   // maxima over subsystems (shared-memory layout)
   Bounds bnd;
 };
 
@@ -566,6 +594,18 @@ struct RingCopyParams {
   int32_t pack;
 };
 cudaError_t launch_ring_copy(const RingCopyParams& p, cudaStream_t st);
+
+// Phase-clock build: per CTA, clock64 cycles summed over steps of
+//   0 injection, 1 solve, 2 node voltages and compensation, 3 thread 0's
+//   updates, 4 the wait of the thread polling line end 0, 5 thread 0 from
+//   its updates to the end-of-step barrier (others' updates and polls),
+//   6 steps, 7 cycles from the first step's start to the last step's end
+//   (of the last launch);
+// copied for CTAs 0 .. n-1 (n <= kPhaseCtas) into out, zeroed if reset.
+// cudaErrorNotSupported in the normal build.
+constexpr int kPhaseCtas = 2048;
+constexpr int kPhaseCount = 8;
+cudaError_t phase_clocks(unsigned long long* out, int n, bool reset);
 cudaError_t launch_companion(BranchDev* br, int64_t n_br, double dt, cudaStream_t st);
 cudaError_t launch_coupled_constants(CoupledEndDev* ce, int64_t n_ce, cudaStream_t st);
 cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st);
@@ -579,6 +619,15 @@ size_t forward_smem_bytes(const FwdLimits& lim);
 constexpr int kSmallMaxNodes = 32;
 cudaError_t launch_forward_small(const FwdParams& p, cudaStream_t st);
 size_t small_smem_bytes(const FwdLimits& lim);
+
+// State-space form (emt_ss.cu): build M of every (subsystem, epoch) from the
+// prefactored G^-1 (P's sub, ep, ginv, ginv_lo, br, lc_idx, sb_idx, le,
+// str_slot, ss, ss_m, ss_mlo are used; one CTA per subsystem), and run steps
+// with it (a cooperative launch of one CTA per subsystem, as launch_forward).
+cudaError_t launch_ss_build(const FwdParams& p, cudaStream_t st);
+cudaError_t launch_forward_ss(const FwdParams& p, cudaStream_t st);
+size_t ss_smem_bytes(int rows, int cols, int n, int le, int src, int ln);
+constexpr int kSsThreads = 256;
 int forward_blocks_per_sm(const FwdLimits& lim);   // resident CTAs per SM (0 on error)
 cudaError_t launch_batch(const BatchParams& p, int threads, cudaStream_t st, BatchGraph* graph);
 size_t batch_smem_bytes(int S_t, int n_sources, int n_sub, int max_cols, int max_nodes);

@@ -394,6 +394,31 @@ __global__ void ring_copy_kernel(RingCopyParams P) {
   }
 }
 
+// ------------------------------------------------------------ phase clocks
+//
+// The phase-clock build (compiled with -DEMT_PHASE_CLOCKS, the library
+// libemt_phases.so): thread 0 of every CTA of fwd_kernel adds the clock64
+// cycles of each phase of each step to per-CTA counters, and the thread
+// that polls the CTA's first line end adds the cycles of its wait; read by
+// emt_phase_clocks.  In the normal build the marks compile to nothing.
+#ifdef EMT_PHASE_CLOCKS
+__device__ unsigned long long g_phase[kPhaseCtas][kPhaseCount];
+// (32-bit clocks and shared-memory sums: the instrumented kernel keeps the
+// register budget of the normal one)
+#define PH_DECL                                                   \
+  __shared__ unsigned long long s_ph[kPhaseCount];                \
+  __shared__ unsigned s_ph_first;                                 \
+  unsigned ph_t0 = 0, ph_t1 = 0;                                  \
+  if (threadIdx.x < kPhaseCount) s_ph[threadIdx.x] = 0;
+#define PH_MARK(t) const unsigned t = (unsigned)clock();
+#define PH_ADD(k, a, b) \
+  if (threadIdx.x == 0) s_ph[k] += (unsigned)((b) - (a));
+#else
+#define PH_DECL
+#define PH_MARK(t)
+#define PH_ADD(k, a, b)
+#endif
+
 // ------------------------------------------------------------ forward
 //
 // On B300 a warp issues at most one FP64 instruction per ~64 cycles however
@@ -1014,6 +1039,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   const int lv = P.lim.le;
   const int src_vs = P.lim.src;
   const bool writes_lines = sidx0 != P.hold_sub;
+  PH_DECL
   const int src_thread = T - 1 - tid;
   // update items: L/C branches, then line ends, then source branches, each
   // block starting on a warp boundary so that a warp runs one kind
@@ -1311,6 +1337,10 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
       vnext = __ldg(P.src_table + EMT_CHK(P.err, (step + 1 - P.n0) * P.n_sources + srcg[src_thread], P.bnd.src,
                                           kChkSource));
 
+    PH_MARK(c0)
+#ifdef EMT_PHASE_CLOCKS
+    if (step == P.n0 && tid == 0) s_ph_first = c0;
+#endif
     // process 2: nodal injections; each lane sums four entries, the node's
     // first lane adds its other lanes' sums
     for (int base = 0; base < n_il; base += T) {
@@ -1334,10 +1364,11 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
       }
       if (cnt > 0) {
         iv[node] = acc;
-        ivf[node] = (float)acc;
+        ivf[node] = f32_trunc(acc);   // (the X_lo chain's operand: truncation on the integer pipe)
       }
     }
     __syncthreads();
+    PH_MARK(c1)
 
     // process 4: v = (X_hi + X_lo) i; task (r, q) runs one FMA chain over
     // the contiguous column block q (the warp issue rate, not the FMA
@@ -1360,6 +1391,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
     }
     if (src_thread < S.n_src) vs[(par ^ 1) * src_vs + src_thread] = vnext;
     __syncthreads();
+    PH_MARK(c2)
 
     // node voltages
     const bool rec_now = P.rec != nullptr && dec == 0 && rec_row < P.rec_rows;
@@ -1371,7 +1403,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
         v += part[r * Q + q];
         vl += partf[r * Q + q];
       }
-      v += (double)vl;
+      v += f64_of(vl);
       vv[r] = v;
       if (rec_now && recp[r] >= 0)
         P.rec[EMT_CHK(P.err, (rec_row - P.rec_row0) * P.n_rec + recp[r], P.bnd.rec, kChkRecord)] = v;
@@ -1391,6 +1423,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
                        P.nl_seg + S.nl_off, SIDX, step, &s_abort);
       if (s_abort) break;
     }
+    PH_MARK(c3)
 
     // process 1: history currents, line outputs, next step's source
     // injections; then the update threads collect next step's line values
@@ -1439,7 +1472,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
           const int t = lcstr[it];
           if (t >= 0) {   // strong branch: its current drives the extra matvec column
             iv[n + t] = -hn;
-            ivf[n + t] = (float)(-hn);
+            ivf[n + t] = f32_trunc(-hn);
           }
         } else if (it >= it_le && it < it_le + n_le) {
           const int e = it - it_le;
@@ -1480,6 +1513,9 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
           inp[n_lc + x] = sbg[x] * vs_next[sbsrc[x]];
         }
       }
+#ifdef EMT_PHASE_CLOCKS
+      ph_t0 = (unsigned)clock();
+#endif
       // next step's ring values: one update thread per line end, counted
       // from the last thread (the first threads hold the update items), so
       // that all waits run at once and the folds spread over several warps.
@@ -1520,9 +1556,32 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
         }
         if (!ok) s_abort = 1;
       }
+#ifdef EMT_PHASE_CLOCKS
+      ph_t1 = (unsigned)clock();
+      if (tid == item_threads - 1) s_ph[4] += ph_t1 - ph_t0;   // the wait of line end 0's poll thread
+#endif
     }
     __syncthreads();
+    PH_MARK(c5)
+    PH_ADD(0, c0, c1)
+    PH_ADD(1, c1, c2)
+    PH_ADD(2, c2, c3)
+    PH_ADD(3, c3, ph_t0)
+    PH_ADD(5, ph_t1, c5)
+#ifdef EMT_PHASE_CLOCKS
+    if (tid == 0) {
+      s_ph[6] += 1;
+      s_ph[7] = (unsigned)(c5 - s_ph_first);
+    }
+#endif
   }
+#ifdef EMT_PHASE_CLOCKS
+  __syncthreads();
+  if (SIDX < kPhaseCtas && tid < kPhaseCount) {
+    if (tid == 7) g_phase[SIDX][7] = s_ph[7];   // the last launch's span
+    else atomicAdd(&g_phase[SIDX][tid], s_ph[tid]);
+  }
+#endif
   if (!s_abort) {
     for (int b = tid; b < n_lc; b += T) P.h[EMT_CHK(P.err, S.lc_off + b, P.bnd.h, kChkHistory)] = inp[b];
     if (P.n_steps > 0)   // the values consumed at the last step, for the next launch's interpolation
@@ -1565,6 +1624,26 @@ cudaError_t launch_ring_init(const RingInitParams& p, cudaStream_t st) {
   if (p.n_le <= 0) return cudaSuccess;
   ring_init_kernel<<<(unsigned)p.n_le, 64, 0, st>>>(p);
   return cudaGetLastError();
+}
+
+cudaError_t phase_clocks(unsigned long long* out, int n, bool reset) {
+#ifdef EMT_PHASE_CLOCKS
+  const size_t bytes = (size_t)std::min(n, kPhaseCtas) * kPhaseCount * sizeof(unsigned long long);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && out != nullptr && bytes > 0) e = cudaMemcpyFromSymbol(out, g_phase, bytes);
+  if (e == cudaSuccess && reset) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_phase);
+    if (e == cudaSuccess) e = cudaMemset(p, 0, sizeof(g_phase));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  return e;
+#else
+  (void)out;
+  (void)n;
+  (void)reset;
+  return cudaErrorNotSupported;
+#endif
 }
 
 cudaError_t launch_ring_copy(const RingCopyParams& p, cudaStream_t st) {

@@ -81,8 +81,15 @@ def checks_build() -> bool:
     return os.environ.get("EMT_CHECKS", "0") == "1"
 
 
+def phases_build() -> bool:
+    """EMT_PHASES=1 in the environment selects the phase-clock build of the library."""
+    return os.environ.get("EMT_PHASES", "0") == "1"
+
+
 def library_path() -> str:
-    return _build.CHECKS_LIB_PATH if checks_build() else _build.LIB_PATH
+    if checks_build():
+        return _build.CHECKS_LIB_PATH
+    return _build.PHASES_LIB_PATH if phases_build() else _build.LIB_PATH
 
 
 def load_library(build_if_needed: bool = True):
@@ -93,7 +100,7 @@ def load_library(build_if_needed: bool = True):
         return _lib
     path = library_path()
     if build_if_needed and _build.needs_build(path):
-        _build.build(checks=checks_build())
+        _build.build(checks=checks_build(), phases=phases_build() and not checks_build())
     if not os.path.exists(path):
         raise RuntimeError(f"{os.path.basename(path)} not found at {path}; build it with "
                            "paper_1903_01081_b300.build.build()")
@@ -122,6 +129,7 @@ def load_library(build_if_needed: bool = True):
         "emt_set_shard": [P, P, I32],
         "emt_shard_pack": [P, I32, P, I64, P, P],
         "emt_shard_unpack": [P, I32, P, I64, P],
+        "emt_phase_clocks": [P, P, I32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -510,6 +518,17 @@ def emt_shard_unpack(ctx: Ctx, peer: int, buf, n_bytes: int, stream=None) -> Non
     """Write rank ``peer``'s packed slots (a CUDA tensor, ``n_bytes`` bytes) into the rings."""
     _check(ctx, load_library().emt_shard_unpack(ctx.handle, int(peer), buf.data_ptr() if n_bytes else None,
                                                 int(n_bytes), _stream_handle(stream)))
+
+
+PHASES = ("injection", "solve", "node_voltages", "updates", "poll_wait_line_end0", "updates_polls_barrier",
+          "steps", "cycles_last_launch")
+
+
+def emt_phase_clocks(ctx: Ctx, reset: bool = False) -> np.ndarray:
+    """Per-CTA phase cycle counts [n_ctas, 8] (phase-clock build only; see include/emt.h)."""
+    out = np.zeros((emt_get_info(ctx, "n_ctas"), len(PHASES)), dtype=np.uint64)
+    _check(ctx, load_library().emt_phase_clocks(ctx.handle, out.ctypes.data if out.size else None, int(reset)))
+    return out
 
 
 def emt_last_error(ctx: Optional[Ctx] = None) -> str:
