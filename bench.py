@@ -725,11 +725,12 @@ def phases_leg(steps=None):
     N = steps or 20000
     cases = (("single_rlc_12_nodes", g.single_rlc()), ("strict_500x6", g.large_scale(strict_500=True)),
              ("large_scale_3000_nodes", g.large_scale()))
-    names = emt.PHASES
     out = {}
-    for tag, net in cases:
-        n = min(N, net.n_steps) if tag == "single_rlc_12_nodes" else N
-        sim = emt.Simulator(net, n_steps=n)
+    runs = [(tag, net, 0) for tag, net in cases] + [(tag + "_state_space", net, 2) for tag, net in cases[:2]]
+    for tag, net, ss in runs:
+        names = emt.PHASES if ss == 0 else emt.SS_PHASES
+        n = min(N, net.n_steps) if tag.startswith("single_rlc") else N
+        sim = emt.Simulator(net, n_steps=n, options={"state_space": ss})
         stream = torch.cuda.current_stream()
         sim.run(min(n, 2000), stream)          # warm-up launch
         sim.sync()
@@ -744,15 +745,16 @@ def phases_leg(steps=None):
         ph = emt.emt_phase_clocks(sim.ctx).astype(np.float64)
         steps_run = ph[:, 6]
         per = ph[:, :6] / steps_run[:, None]
-        own = per[:, 0] + per[:, 1] + per[:, 2] + per[:, 3]
+        own = per[:, 0] + per[:, 1] + per[:, 2] + per[:, 3] if ss == 0 else per[:, 0]
         crit = int(np.argmax(own))
         cyc_per_step = float(np.max(ph[:, 7] / steps_run))   # the slowest CTA's (independent subsystems end apart)
         out[tag] = {"ctas": int(ph.shape[0]), "largest_cta_nodes": sim.info("max_subsystem_nodes"),
                     "steps": n, "us_per_step_events": 1e3 * ms / n,
                     "cycles_per_step_span": cyc_per_step,
                     "sm_mhz_implied": cyc_per_step / (1e3 * ms / n),
-                    "mean_over_ctas": {k: round(float(v), 1) for k, v in zip(names[:6], per.mean(axis=0))},
-                    "critical_cta": {"cta": crit, **{k: round(float(v), 1) for k, v in zip(names[:6], per[crit])}}}
+                    "kernel": "fwd_kernel (CTA per subsystem)" if ss == 0 else "fwd_ss_kernel (state-space form)",
+                    "mean_over_ctas": {k: round(float(v), 1) for k, v in zip(names[:6], per.mean(axis=0)) if k},
+                    "critical_cta": {"cta": crit, **{k: round(float(v), 1) for k, v in zip(names[:6], per[crit]) if k}}}
         sim.close()
     return out
 

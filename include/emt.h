@@ -516,6 +516,10 @@ emt_status emt_shard_unpack(emt_ctx* ctx, int32_t peer, const void* buf, int64_t
  *   barrier (the other updates and the line-value polls), 6 steps, 7 the
  *   cycles from the first step's start to the last step's end of the last
  *   launch.
+ * While the state-space form runs (option "state_space"), its kernel's
+ * counters instead: k = 0 thread 0's rows of the product, 1 the collection
+ * of the next step's line values and source voltages (the poll warp's lane
+ * 0), 2 thread 0 from its rows to the end-of-step barrier, 6 and 7 as above.
  * out may be NULL; reset != 0 zeroes the counters afterwards.  Synchronises
  * the device.  EINVAL in the normal build or with more than 2048 CTAs. */
 emt_status emt_phase_clocks(emt_ctx* ctx, uint64_t* out, int32_t reset);

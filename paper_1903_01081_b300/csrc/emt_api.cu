@@ -100,6 +100,7 @@ struct emt_ctx {
   // state-space form (emt_ss.cu): eligible networks (ss_ok) run it unless the option state_space is 0;
   // auto (1) only while every subsystem's M is at most kSsAutoEntries, 2 forces it
   bool ss_ok = false;
+  bool ss_compact = false;   // every subsystem takes the compact step (several CTAs to an SM)
   int ss_mode = 1;
   int64_t ss_len = 0, ss_max_entries = 0;
   int ss_rows = 0, ss_cols = 0, ss_ln = 0;
@@ -1904,6 +1905,7 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
     const int cps = (S + n_sm - 1) / std::max(n_sm, 1);
     c->ss.assign(S, SsSubDev{});
     c->ss_lend.assign(c->line_ends.size(), 0);
+    c->ss_compact = cps > 1 && c->lim.n <= 32;
     int64_t off = 0;
     for (int s = 0; s < S && c->ss_ok; ++s) {
       const SubDev& sd = c->subs[s];
@@ -1921,20 +1923,27 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
         most = std::max(most, (int)kv.second.size());
       }
       c->ss_lptr.push_back(pos);
-      Q.rows = sd.n_lc + sd.n;
+      // several CTAs to an SM: the compact step (one warp, M's node rows only)
+      Q.compact = c->ss_compact ? 1 : 0;
+      Q.rows = Q.compact ? sd.n : sd.n_lc + sd.n;
       Q.cols = sd.n_lc + sd.n_src + Q.n_ln;
       if (Q.rows > kSsThreads - 32 || Q.cols < 1) {
         c->ss_ok = false;
         break;
       }
-      double best = 1e300;
-      for (int qq = 1, lg = 0; qq <= 32 && Q.rows * qq <= kSsThreads - 32; qq *= 2, ++lg) {
-        const double chain = (Q.cols + qq - 1) / qq + lg + 1 + (most + qq - 1) / qq;
-        const double warps = (Q.rows * qq + 31) / 32;
-        const double cost = std::max(chain, cps * warps * chain / 4.0);
-        if (cost < best) {
-          best = cost;
-          Q.q = qq;
+      if (Q.compact) {   // the most lanes per row that one warp holds
+        Q.q = 1;
+        while (Q.q < 32 && sd.n * Q.q * 2 <= 32 && Q.q < Q.cols) Q.q *= 2;
+      } else {
+        double best = 1e300;
+        for (int qq = 1, lg = 0; qq <= 32 && Q.rows * qq <= kSsThreads - 32; qq *= 2, ++lg) {
+          const double chain = (Q.cols + qq - 1) / qq + lg + 1 + (most + qq - 1) / qq;
+          const double warps = (Q.rows * qq + 31) / 32;
+          const double cost = std::max(chain, cps * warps * chain / 4.0);
+          if (cost < best) {
+            best = cost;
+            Q.q = qq;
+          }
         }
       }
       Q.m_off = off;
@@ -1945,7 +1954,8 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
       c->ss_max_entries = std::max<int64_t>(c->ss_max_entries, (int64_t)Q.rows * Q.cols);
     }
     c->ss_len = off;
-    if (c->ss_ok && ss_smem_bytes(c->ss_rows, c->ss_cols, std::max(c->lim.n, 1), c->lim.le, c->lim.src, c->ss_ln) *
+    if (c->ss_ok && ss_smem_bytes(c->ss_rows, c->ss_cols, std::max(c->lim.n, 1), c->lim.le, c->lim.src, c->ss_ln,
+                                  c->lim.lc) *
                             (size_t)cps > 220 * 1024)
       c->ss_ok = false;
   }
@@ -2497,7 +2507,7 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
     if (e != cudaSuccess) return c->cuda_fail(e, "emt_step_n source table");
     p.n0 = c->step + 1;
     p.n_steps = len;
-    e = ssf     ? launch_forward_ss(p, st)
+    e = ssf     ? launch_forward_ss(p, c->ss_compact, st)
         : small ? launch_forward_small(p, st)
                 : launch_forward(p, st, !c->forward_narrow, c->lazy || c->lim.nl > 1);
     if (e == cudaErrorCooperativeLaunchTooLarge)
@@ -3111,7 +3121,8 @@ extern "C" emt_status emt_phase_clocks(emt_ctx* c, uint64_t* out, int32_t reset)
   if (!c) return EMT_EINVAL;
   if (c->n_sub > kPhaseCtas)
     return c->fail(EMT_EINVAL, "emt_phase_clocks: more than " + std::to_string(kPhaseCtas) + " CTAs");
-  cudaError_t e = phase_clocks(reinterpret_cast<unsigned long long*>(out), c->n_sub, reset != 0);
+  cudaError_t e = state_space_runs(c) ? ss_phase_clocks(reinterpret_cast<unsigned long long*>(out), c->n_sub, reset != 0)
+                                      : phase_clocks(reinterpret_cast<unsigned long long*>(out), c->n_sub, reset != 0);
   if (e == cudaErrorNotSupported) return c->fail(EMT_EINVAL, "emt_phase_clocks: not the phase-clock build");
   if (e != cudaSuccess) return c->cuda_fail(e, "emt_phase_clocks");
   return EMT_OK;

@@ -92,6 +92,19 @@ __device__ __forceinline__ double f64_of(float f) {
                                           ((unsigned long long)(u & 0x7fffffu) << 29)));
 }
 
+// A tagged slot's two words, loaded without looking at them (so that several
+// slots' loads can be in flight at once), and the check of such a pair.
+__device__ __forceinline__ void ld_tagged_raw(const unsigned long long* p, unsigned long long& w0,
+                                              unsigned long long& w1) {
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(w0), "=l"(w1) : "l"(p) : "memory");
+}
+
+__device__ __forceinline__ bool tagged_value(unsigned long long w0, unsigned long long w1, unsigned tag, double& v) {
+  if ((unsigned)(w0 >> 32) != tag || (unsigned)(w1 >> 32) != tag) return false;
+  v = __longlong_as_double((long long)((w1 << 32) | (w0 & 0xffffffffull)));
+  return true;
+}
+
 // Wait for a ring slot to carry `tag` and return its value.  Bounded: on
 // exceeding the time budget (or seeing another CTA's error) it latches an
 // error {5, subsystem, line end, tag} and returns false.  Params: the

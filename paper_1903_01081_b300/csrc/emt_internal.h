@@ -247,10 +247,14 @@ struct Bounds {
 // elements only, where the step's chain of dependent FP64 operations, not
 // its work, sets the time.
 struct SsSubDev {
-  int32_t rows, cols;   // rows = n_lc + n; cols = n_lc + n_src + n_ln
+  int32_t rows, cols;   // rows = n_lc + n (compact: n); cols = n_lc + n_src + n_ln
   int32_t q;            // lanes per row of the matvec (a power of two <= 32)
   int32_t n_ln;         // nodes with line ends: ss_lnode[ln_off + j], their ends ss_lend[ss_lptr[ptr_off + j] ..]
   int32_t ln_off, ptr_off;
+  // compact: M holds the node-voltage rows only, and one warp runs the whole
+  // step (v, then h and the line outputs from v): fewer FP64 instructions,
+  // for SMs that hold several CTAs
+  int32_t compact, pad;
   int64_t m_off;
 };
 
@@ -606,6 +610,9 @@ cudaError_t launch_ring_copy(const RingCopyParams& p, cudaStream_t st);
 constexpr int kPhaseCtas = 2048;
 constexpr int kPhaseCount = 8;
 cudaError_t phase_clocks(unsigned long long* out, int n, bool reset);
+// the same for the state-space kernel (emt_ss.cu): 0 thread 0's product rows,
+// 1 the poll warp's collection, 2 thread 0 from its rows to the barrier, 6, 7 as above
+cudaError_t ss_phase_clocks(unsigned long long* out, int n, bool reset);
 cudaError_t launch_companion(BranchDev* br, int64_t n_br, double dt, cudaStream_t st);
 cudaError_t launch_coupled_constants(CoupledEndDev* ce, int64_t n_ce, cudaStream_t st);
 cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st);
@@ -625,8 +632,8 @@ size_t small_smem_bytes(const FwdLimits& lim);
 // str_slot, ss, ss_m, ss_mlo are used; one CTA per subsystem), and run steps
 // with it (a cooperative launch of one CTA per subsystem, as launch_forward).
 cudaError_t launch_ss_build(const FwdParams& p, cudaStream_t st);
-cudaError_t launch_forward_ss(const FwdParams& p, cudaStream_t st);
-size_t ss_smem_bytes(int rows, int cols, int n, int le, int src, int ln);
+cudaError_t launch_forward_ss(const FwdParams& p, bool compact, cudaStream_t st);
+size_t ss_smem_bytes(int rows, int cols, int n, int le, int src, int ln, int lc);
 constexpr int kSsThreads = 256;
 int forward_blocks_per_sm(const FwdLimits& lim);   // resident CTAs per SM (0 on error)
 cudaError_t launch_batch(const BatchParams& p, int threads, cudaStream_t st, BatchGraph* graph);

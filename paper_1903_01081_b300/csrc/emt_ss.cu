@@ -39,6 +39,15 @@ namespace {
 
 constexpr int kSsPollWarp = kSsThreads / 32 - 1;
 
+// Phase-clock build (-DEMT_PHASE_CLOCKS): per CTA, clock cycles per step of
+// 0 thread 0's part of the product, 1 the poll warp's collection of the next
+// step's values (its lane 0), 2 thread 0 from its rows to the end-of-step
+// barrier; 6 steps, 7 the last launch's span (see phase_clocks).
+#ifdef EMT_PHASE_CLOCKS
+__device__ unsigned long long g_ss_phase[kPhaseCtas][kPhaseCount];
+#endif
+constexpr int kSsPrefetch = 4;   // ring slots a poll lane has in flight at once
+
 // ---------------------------------------------------------------- double-double
 
 struct DD {
@@ -103,6 +112,7 @@ struct Build {
     return dd_neg(x(r, P.ss_lnode[Q.ln_off + col]));
   }
   __device__ DD entry(int row, int col) const {
+    if (Q.compact) return xa(row, col);   // node voltages only
     if (row < S.n_lc) {   // h_b(n) = +-h_b(n-1) + e_b (v_k - v_m), a source end's voltage taken directly
       const BranchDev b = P.br[P.lc_idx[S.lc_off + row]];
       DD acc{0.0, 0.0};
@@ -140,12 +150,13 @@ __global__ void ss_build_kernel(FwdParams P) {
 // ---------------------------------------------------------------- the step
 
 struct SsSmem {
-  size_t mh, x, ie, ley2, leown, lefar;                                        // 8-byte
-  size_t ml, xf, ledepth, led, rslot, wslot, lend, lnode, lptr, js, recp, srcg;   // 4-byte
+  size_t mh, x, ie, ley2, leown, lefar, vv, lce;                                      // 8-byte
+  size_t ml, xf, ledepth, led, rslot, wslot, lend, lnode, lptr, js, recp, srcg, lenode, lck, lcm,
+      lckind;                                                                         // 4-byte
   size_t bytes;
 };
 
-__host__ __device__ inline SsSmem ss_smem(int rows, int cols, int n, int le, int src, int ln) {
+__host__ __device__ inline SsSmem ss_smem(int rows, int cols, int n, int le, int src, int ln, int lc) {
   SsSmem s{};
   size_t o = 0;
   auto d = [&](size_t c) { size_t r = o; o += c * 8; return r; };
@@ -157,6 +168,8 @@ __host__ __device__ inline SsSmem ss_smem(int rows, int cols, int n, int le, int
   s.ley2 = d(le);
   s.leown = d(le);
   s.lefar = d(le);
+  s.vv = d(n);
+  s.lce = d(lc);
   s.ml = w((size_t)rows * ldm);
   s.xf = w(2 * (size_t)cols);
   s.ledepth = w(le);
@@ -169,14 +182,20 @@ __host__ __device__ inline SsSmem ss_smem(int rows, int cols, int n, int le, int
   s.js = w(n);
   s.recp = w(n);
   s.srcg = w(src);
+  s.lenode = w(le);
+  s.lck = w(lc);
+  s.lcm = w(lc);
+  s.lckind = w(lc);
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
 }
 
+// kCompact: every subsystem's step is the compact one (SsSubDev::compact)
+template <bool kCompact>
 __global__ void __launch_bounds__(kSsThreads, 4) fwd_ss_kernel(FwdParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_abort;
-  const SsSmem L = ss_smem(P.ss_rows, P.ss_cols, P.lim.n, P.lim.le, P.lim.src, P.ss_ln);
+  const SsSmem L = ss_smem(P.ss_rows, P.ss_cols, P.lim.n, P.lim.le, P.lim.src, P.ss_ln, P.lim.lc);
   double* mh = reinterpret_cast<double*>(smem_raw + L.mh);
   double* xb = reinterpret_cast<double*>(smem_raw + L.x);
   double* ieb = reinterpret_cast<double*>(smem_raw + L.ie);
@@ -195,6 +214,12 @@ __global__ void __launch_bounds__(kSsThreads, 4) fwd_ss_kernel(FwdParams P) {
   int* js = reinterpret_cast<int*>(smem_raw + L.js);
   int* recp = reinterpret_cast<int*>(smem_raw + L.recp);
   int* srcg = reinterpret_cast<int*>(smem_raw + L.srcg);
+  double* vv = reinterpret_cast<double*>(smem_raw + L.vv);
+  double* lce = reinterpret_cast<double*>(smem_raw + L.lce);
+  int* lenode = reinterpret_cast<int*>(smem_raw + L.lenode);
+  int* lck = reinterpret_cast<int*>(smem_raw + L.lck);
+  int* lcm = reinterpret_cast<int*>(smem_raw + L.lcm);
+  int* lckind = reinterpret_cast<int*>(smem_raw + L.lckind);
 
   const int sidx = P.active != nullptr ? P.active[blockIdx.x] : (int)blockIdx.x;
   const SubDev S = P.sub[blockIdx.x];
@@ -206,12 +231,27 @@ __global__ void __launch_bounds__(kSsThreads, 4) fwd_ss_kernel(FwdParams P) {
   const bool writes_lines = sidx != P.hold_sub;
 
   // ---- prologue: element data, the run state at step n0, the epoch's M
-  if (tid == 0) s_abort = 0;
+  // The CTAs one SM holds take their product's first warp on different SM
+  // sub-partitions (a warp runs on sub-partition (hardware slot mod 4); a CTA
+  // of 8 warps takes 8 consecutive slots, so its slot / 8 tells the CTAs
+  // apart), so that their FP64 instructions do not queue on one pipe.
+  __shared__ int s_rot;
+  if (tid == 0) {
+    unsigned wid;
+    asm volatile("mov.u32 %0, %%warpid;" : "=r"(wid));
+    s_rot = (int)((wid >> 3) & 3u);
+    s_abort = 0;
+  }
   const int p0 = (int)(P.n0 & 1);
   for (int b = tid; b < n_lc; b += kSsThreads) {
     const double h = P.h[EMT_CHK(P.err, S.lc_off + b, P.bnd.h, kChkHistory)];
     xb[p0 * cols + b] = h;
     xfb[p0 * cols + b] = f32_trunc(h);
+    const BranchDev br = P.br[P.lc_idx[S.lc_off + b]];
+    lce[b] = br.e;
+    lck[b] = br.k;
+    lcm[b] = br.m;
+    lckind[b] = br.kind;
   }
   for (int e = tid; e < n_le; e += kSsThreads) {
     const LineEndDev le = P.le[S.le_off + e];
@@ -223,6 +263,7 @@ __global__ void __launch_bounds__(kSsThreads, 4) fwd_ss_kernel(FwdParams P) {
     rslot[e] = (int)(P.n0 % le.depth);
     wslot[e] = (int)((P.n0 + le.d) % le.depth);
     lend[e] = P.ss_lend[S.le_off + e];
+    lenode[e] = le.node;
   }
   for (int j = tid; j < n_ln; j += kSsThreads) lnode[j] = P.ss_lnode[Q.ln_off + j];
   for (int j = tid; j <= n_ln; j += kSsThreads) lptr[j] = P.ss_lptr[Q.ptr_off + j];
@@ -254,19 +295,42 @@ __global__ void __launch_bounds__(kSsThreads, 4) fwd_ss_kernel(FwdParams P) {
 
   // the poll warp: step m's line values into ie / J of parity m & 1 (and
   // step m's source voltages when `src`); false if a wait ran out
+  // (every load of a lane -- its source voltage, its line ends' slots, up to
+  // kSsPrefetch of them -- is issued before any is looked at, so that their
+  // L2 round trips overlap; a slot not yet written is then waited for)
   auto collect = [&](long long m, bool src) -> bool {
     const int pm = (int)(m & 1);
+    const bool has_src = src && lane < n_src;
+    double sv = 0.0;
+    if (has_src) sv = __ldg(P.src_table + EMT_CHK(P.err, (m - P.n0) * P.n_sources + srcg[lane], P.bnd.src, kChkSource));
     bool ok = true;
-    for (int e = lane; e < n_le && ok; e += 32) {
-      double v = 0.0;
-      ok = poll_slot(P, P.ring + 2 * EMT_CHK(P.err, leown[e] + rslot[e], P.bnd.ring, kChkRingRead), (unsigned)m, sidx,
-                     e, v);
-      ieb[pm * n_le + e] = v;
-      const int nx = rslot[e] + 1;
-      rslot[e] = nx == ledepth[e] ? 0 : nx;
+    for (int e0 = lane; e0 < n_le && ok; e0 += 32 * kSsPrefetch) {
+      unsigned long long w[kSsPrefetch][2];
+#pragma unroll
+      for (int k = 0; k < kSsPrefetch; ++k) {
+        const int e = e0 + 32 * k;
+        if (e < n_le) ld_tagged_raw(P.ring + 2 * EMT_CHK(P.err, leown[e] + rslot[e], P.bnd.ring, kChkRingRead), w[k][0], w[k][1]);
+      }
+#pragma unroll
+      for (int k = 0; k < kSsPrefetch; ++k) {
+        const int e = e0 + 32 * k;
+        if (e < n_le && ok) {
+          double v = 0.0;
+          if (!tagged_value(w[k][0], w[k][1], (unsigned)m, v))
+            ok = poll_slot(P, P.ring + 2 * EMT_CHK(P.err, leown[e] + rslot[e], P.bnd.ring, kChkRingRead), (unsigned)m,
+                           sidx, e, v);
+          ieb[pm * n_le + e] = v;
+          const int nx = rslot[e] + 1;
+          rslot[e] = nx == ledepth[e] ? 0 : nx;
+        }
+      }
+    }
+    if (has_src) {
+      xb[pm * cols + vs0 + lane] = sv;
+      xfb[pm * cols + vs0 + lane] = f32_trunc(sv);
     }
     if (src)
-      for (int s = lane; s < n_src; s += 32) {
+      for (int s = lane + 32; s < n_src; s += 32) {
         const double v =
             __ldg(P.src_table + EMT_CHK(P.err, (m - P.n0) * P.n_sources + srcg[s], P.bnd.src, kChkSource));
         xb[pm * cols + vs0 + s] = v;
@@ -289,10 +353,21 @@ __global__ void __launch_bounds__(kSsThreads, 4) fwd_ss_kernel(FwdParams P) {
   __syncthreads();
 
   const int rpw = 32 / qn;   // rows per warp
+  const int tw = (warp - s_rot + kSsPollWarp) % kSsPollWarp;   // this warp's place in the product
   const int rq = lane / qn, q = lane & (qn - 1);
   const long long n_end = P.n0 + P.n_steps;
+#ifdef EMT_PHASE_CLOCKS
+  __shared__ unsigned long long s_ph[kPhaseCount];
+  __shared__ unsigned s_first;
+  if (tid < kPhaseCount) s_ph[tid] = 0;
+  __syncthreads();
+#endif
   for (long long step = P.n0; step < n_end && !s_abort; ++step) {
     const int par = (int)(step & 1);
+#ifdef EMT_PHASE_CLOCKS
+    const unsigned c0 = (unsigned)clock();
+    if (step == P.n0 && tid == 0) s_first = c0;
+#endif
     if (step >= next_ep_start) {   // a switch event: the next epoch's M
       while (te + 1 < n_te && P.ep[S.ep_off + te + 1].start <= step) ++te;
       next_ep_start = (te + 1 < n_te) ? P.ep[S.ep_off + te + 1].start : LLONG_MAX;
@@ -305,10 +380,54 @@ __global__ void __launch_bounds__(kSsThreads, 4) fwd_ss_kernel(FwdParams P) {
     float* xfn = xfb + (par ^ 1) * cols;
     const double* iec = ieb + par * n_le;
     const bool rec_now = P.rec != nullptr && dec == 0 && rec_row < P.rec_rows;
-    if (warp < kSsPollWarp) {
+    if (kCompact && warp < kSsPollWarp) {
+      // one warp: v = M x (n rows of Q lanes), then from v the line outputs
+      // and the history currents, as processes 1 of the CTA kernel
+      if (tw == 0) {
+        const int r = rq;
+        double a = 0.0;
+        float b = 0.f;
+        if (r < n) {
+          const double* row = mh + r * ldm;
+          const float* rowl = ml + r * ldm;
+#pragma unroll 4
+          for (int j = q; j < cols; j += qn) {
+            a = fma(row[j], xc[j], a);
+            b = fmaf(rowl[j], xfc[j], b);
+          }
+        }
+        for (int o = qn >> 1; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (r < n && q == 0) {
+          const double y = a + f64_of(b);
+          vv[r] = y;
+          if (rec_now && recp[r] >= 0)
+            P.rec[EMT_CHK(P.err, (rec_row - P.rec_row0) * P.n_rec + recp[r], P.bnd.rec, kChkRecord)] = y;
+        }
+        __syncwarp();
+        for (int e = lane; e < n_le; e += 32) {
+          const double c = fma(-ley2[e], vv[lenode[e]], -iec[e]);
+          if (writes_lines)
+            st_tagged(P.ring + 2 * EMT_CHK(P.err, lefar[e] + wslot[e], P.bnd.ring, kChkRingWrite),
+                      (unsigned)(step + led[e]), c);
+          const int nx = wslot[e] + 1;
+          wslot[e] = nx == ledepth[e] ? 0 : nx;
+        }
+        for (int b2 = lane; b2 < n_lc; b2 += 32) {
+          const int k = lck[b2], m = lcm[b2];
+          const double vk = k >= 0 ? vv[k] : (k == -1 ? 0.0 : xc[vs0 - 2 - k]);
+          const double vm = m >= 0 ? vv[m] : (m == -1 ? 0.0 : xc[vs0 - 2 - m]);
+          const double hn = lckind[b2] == 1 ? fma(lce[b2], vk - vm, xc[b2]) : fma(lce[b2], vk - vm, -xc[b2]);
+          xn[b2] = hn;
+          xfn[b2] = f32_trunc(hn);
+        }
+      }
+    } else if (!kCompact && warp < kSsPollWarp) {
       // y = M x: lane (row, q) over the columns q, q + Q, ...; a butterfly
       // leaves the row's sum in all Q lanes
-      for (int r0 = warp * rpw; r0 < rows; r0 += kSsPollWarp * rpw) {
+      for (int r0 = tw * rpw; r0 < rows; r0 += kSsPollWarp * rpw) {
         const int r = r0 + rq;
         double a = 0.0;
         float b = 0.f;
@@ -352,11 +471,33 @@ __global__ void __launch_bounds__(kSsThreads, 4) fwd_ss_kernel(FwdParams P) {
       }
     } else if (step + 1 < n_end) {   // meanwhile: the next step's line values and source voltages
       if (!collect(step + 1, true) && lane == 0) s_abort = 1;
+#ifdef EMT_PHASE_CLOCKS
+      if (lane == 0) s_ph[1] += (unsigned)clock() - c0;
+#endif
     }
+#ifdef EMT_PHASE_CLOCKS
+    const unsigned c1 = (unsigned)clock();
+#endif
     if (dec == 0) ++rec_row;
     if (++dec == decim) dec = 0;
     __syncthreads();
+#ifdef EMT_PHASE_CLOCKS
+    if (tid == 0) {
+      const unsigned c2 = (unsigned)clock();
+      s_ph[0] += c1 - c0;
+      s_ph[2] += c2 - c1;
+      s_ph[6] += 1;
+      s_ph[7] = c2 - s_first;
+    }
+#endif
   }
+#ifdef EMT_PHASE_CLOCKS
+  __syncthreads();
+  if (sidx < kPhaseCtas && tid < kPhaseCount) {
+    if (tid == 7) g_ss_phase[sidx][7] = s_ph[7];
+    else atomicAdd(&g_ss_phase[sidx][tid], s_ph[tid]);
+  }
+#endif
   if (!s_abort) {
     const int pe = (int)(n_end & 1);
     for (int b = tid; b < n_lc; b += kSsThreads) P.h[EMT_CHK(P.err, S.lc_off + b, P.bnd.h, kChkHistory)] = xb[pe * cols + b];
@@ -367,8 +508,28 @@ __global__ void __launch_bounds__(kSsThreads, 4) fwd_ss_kernel(FwdParams P) {
 
 }  // namespace
 
-size_t ss_smem_bytes(int rows, int cols, int n, int le, int src, int ln) {
-  return ss_smem(rows, cols, n, le, src, ln).bytes;
+cudaError_t ss_phase_clocks(unsigned long long* out, int n, bool reset) {
+#ifdef EMT_PHASE_CLOCKS
+  const size_t bytes = (size_t)std::min(n, kPhaseCtas) * kPhaseCount * sizeof(unsigned long long);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && out != nullptr && bytes > 0) e = cudaMemcpyFromSymbol(out, g_ss_phase, bytes);
+  if (e == cudaSuccess && reset) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_ss_phase);
+    if (e == cudaSuccess) e = cudaMemset(p, 0, sizeof(g_ss_phase));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  return e;
+#else
+  (void)out;
+  (void)n;
+  (void)reset;
+  return cudaErrorNotSupported;
+#endif
+}
+
+size_t ss_smem_bytes(int rows, int cols, int n, int le, int src, int ln, int lc) {
+  return ss_smem(rows, cols, n, le, src, ln, lc).bytes;
 }
 
 cudaError_t launch_ss_build(const FwdParams& p, cudaStream_t st) {
@@ -377,22 +538,23 @@ cudaError_t launch_ss_build(const FwdParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_forward_ss(const FwdParams& p, cudaStream_t st) {
-  const size_t smem = ss_smem_bytes(p.ss_rows, p.ss_cols, p.lim.n, p.lim.le, p.lim.src, p.ss_ln);
+cudaError_t launch_forward_ss(const FwdParams& p, bool compact, cudaStream_t st) {
+  const void* fn = compact ? (const void*)fwd_ss_kernel<true> : (const void*)fwd_ss_kernel<false>;
+  const size_t smem = ss_smem_bytes(p.ss_rows, p.ss_cols, p.lim.n, p.lim.le, p.lim.src, p.ss_ln, p.lim.lc);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(fwd_ss_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, n_sm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   const int grid = p.active != nullptr ? p.n_active : p.n_sub;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_ss_kernel, kSsThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kSsThreads, smem);
   if (e != cudaSuccess) return e;
   if ((long long)per_sm * n_sm < grid) return cudaErrorCooperativeLaunchTooLarge;
   FwdParams arg = p;
   void* args[] = {&arg};
   // cooperative launch: all CTAs co-resident, so every ring wait can end
-  return cudaLaunchCooperativeKernel((const void*)fwd_ss_kernel, dim3(grid), dim3(kSsThreads), args, smem, st);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kSsThreads), args, smem, st);
 }
 
 }  // namespace emt

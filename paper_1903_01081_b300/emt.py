@@ -524,6 +524,10 @@ PHASES = ("injection", "solve", "node_voltages", "updates", "poll_wait_line_end0
           "steps", "cycles_last_launch")
 
 
+SS_PHASES = ("product_rows_thread0", "collect_next_values", "rows_to_barrier_thread0", "", "", "", "steps",
+             "cycles_last_launch")
+
+
 def emt_phase_clocks(ctx: Ctx, reset: bool = False) -> np.ndarray:
     """Per-CTA phase cycle counts [n_ctas, 8] (phase-clock build only; see include/emt.h)."""
     out = np.zeros((emt_get_info(ctx, "n_ctas"), len(PHASES)), dtype=np.uint64)
