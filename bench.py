@@ -759,6 +759,42 @@ def phases_leg(steps=None):
     return out
 
 
+def shared_g_digit_leg(steps=None):
+    """The shared-G study (4,096 scenarios, 3,000 nodes) at fixed launch
+    shapes with the solve in FP64 and in digit form on the tensor cores
+    (option digit_solve): scenario-steps/s of 100 steps each."""
+    import torch
+    from paper_1903_01081_b300 import emt, netgen as g
+    net, sc = g.shared_g(n_scenarios=4096)
+    N = steps or 100
+    out = []
+    for St, th in ((8, 512), (16, 512), (28, 512), (28, 1024)):
+        for digit in (0, 1):
+            if digit and th > 512:
+                continue
+            ctx = emt.emt_build_network(net, sc)
+            emt.emt_prefactor(ctx)
+            emt.emt_set_option(ctx, "scenarios_per_cta", St)
+            emt.emt_set_option(ctx, "batch_threads", th)
+            emt.emt_set_option(ctx, "digit_solve", digit)
+            stream = torch.cuda.current_stream()
+            emt.emt_step_n(ctx, 10, stream)
+            emt.emt_sync(ctx)
+            emt.emt_reset(ctx)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            emt.emt_step_n(ctx, N, stream)
+            e1.record(stream)
+            emt.emt_sync(ctx)
+            ms = e0.elapsed_time(e1)
+            out.append({"scenarios_per_cta": St, "threads": th, "digit_solve": digit,
+                        "groups": emt.emt_get_info(ctx, "batch_groups"),
+                        "scenario_steps_per_s": 4096 * N / (ms / 1e3)})
+            emt.emt_destroy(ctx)
+    return {"workload": "shared-G study, 4,096 scenarios of the 3,000-node network, fixed launch shapes",
+            "runs": out}
+
+
 def scale_legs(steps=None, reps=3):
     """The large-scale family at two other sizes: the strict reading of
     500 subsystems of 6 nodes (3,000 nodes), and 500 subsystems of 6..60
@@ -961,7 +997,7 @@ def main():
     ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines",
                                       "fd_lines", "nonlinear", "controls", "sizes", "control_study",
                                       "arrester_study", "fd_line_study", "coupled_line_study", "converter_stations",
-                                      "bus_arresters", "phases"],
+                                      "bus_arresters", "phases", "shared_g_digit"],
                     default="all",
                     help="all: the JSON line with every leg; single: the single-network leg only; "
                          "n1 / shared_g / adjoint: that leg alone (profiling)")
@@ -980,7 +1016,7 @@ def main():
         return run_reference(args)
     if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "fd_lines", "nonlinear",
                     "controls", "sizes", "control_study", "arrester_study", "fd_line_study", "coupled_line_study",
-                    "converter_stations", "bus_arresters", "phases"):
+                    "converter_stations", "bus_arresters", "phases", "shared_g_digit"):
         return run_leg(args)
     return run_ours(args)
 
@@ -1009,6 +1045,8 @@ def run_leg(args):
         out = scale_legs(args.leg_steps, reps=1)
     elif args.leg == "phases":
         out = {"phases": phases_leg(args.leg_steps)}
+    elif args.leg == "shared_g_digit":
+        out = shared_g_digit_leg(args.leg_steps)
     elif args.leg in ("control_study", "arrester_study", "fd_line_study", "coupled_line_study"):
         shape = tuple(int(x) for x in args.shape.split(",")) if args.shape else None
         which = {"control_study": "controls", "arrester_study": "arresters", "fd_line_study": "fd",

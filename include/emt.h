@@ -418,7 +418,11 @@ emt_status emt_sync(emt_ctx* ctx, int32_t* dev_err_info);
  * from G^-1, for networks whose subsystems hold basic elements only --
  * R/L/C branches, sources, fixed-time switches, lossless lines: 0 off,
  * 1 auto (default: while every subsystem's M has at most 2,048 entries),
- * 2 on).  EINVAL for an unknown key. */
+ * 2 on), "digit_solve" (scenario sets: 1 runs process 4 of each subsystem
+ * whose solve matrix a whole scenario tile shares as exact base-256 digit
+ * products on the bf16 tensor cores, one rounding per entry; default 0: it
+ * measured slower than the FP64 solve; at most 512 threads per CTA while on).
+ * EINVAL for an unknown key. */
 emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
 
 /* Read-only facts: "n_subsystems", "n_ctas" (the CTAs of the persistent
@@ -440,7 +444,8 @@ emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
  * subsystem's control graph),
  * "n_matrix_variants", "scenarios_per_cta", "batch_threads", "batch_groups"
  * (subsystem groups per step of the multi-scenario kernel),
- * "graph_launches", "autotuned", "state_space" (1 while the state-space
+ * "graph_launches", "autotuned", "digit_solve" (1 while on), "digit_matrices"
+ * (solve matrices held in digit form), "state_space" (1 while the state-space
  * form runs emt_step_n), "warp_per_subsystem", "shard_rank" (-1 unless a shard),
  * "shard_window" (see emt_set_shard; 0 unless a shard), "shard_ctas" (CTAs
  * this context runs). */

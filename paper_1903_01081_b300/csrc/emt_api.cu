@@ -211,6 +211,17 @@ struct emt_ctx {
   BatchGroupDev* d_grp = nullptr;
   BatchGraph graph;
   bool use_graph = true;
+  // digit form of the multi-scenario solve (emt_batch.cu): matrices that
+  // whole tiles share, in digit form; option digit_solve
+  bool use_digit = false;
+  int dig_words = 0, dig_grp = 0;                     // table words and most subsystems of a group, current S_t
+  int64_t dig_len = 0;
+  std::vector<int32_t> dig_ptr, dig_sub_n, dig_node0, dig_mat_n, dig_mat_nc;
+  std::vector<int64_t> dig_key, dig_val, dig_mat_goff;
+  uint32_t* d_dig = nullptr;
+  int32_t *d_dig_ptr = nullptr, *d_sub_node0 = nullptr, *d_sub_n = nullptr, *d_dig_mat_n = nullptr,
+          *d_dig_mat_nc = nullptr;
+  int64_t *d_dig_key = nullptr, *d_dig_val = nullptr, *d_dig_mat_goff = nullptr;
   bool tuned = false;
   int64_t* d_le_bring = nullptr;
   int64_t* d_le_bfar = nullptr;
@@ -561,70 +572,106 @@ cudaError_t reset_batch_words(emt_ctx* c) {
   return cudaMemcpy(c->d_bword, w.data(), w.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
 }
 
+// Shared memory a subsystem adds to its group in the digit form: its entry
+// of the selections, and, with a digit matrix, its injection exponents and
+// its digit table for tiles of S_t scenarios (0 with the digit form off).
+size_t batch_dig_bytes(const emt_ctx* c, int s, int S_t) {
+  if (!c->use_digit || c->dig_key.empty()) return 0;
+  const int ts = 16 * ((S_t + 15) / 16);
+  if (c->dig_ptr[s + 1] == c->dig_ptr[s]) return 8;
+  return 8 + (size_t)ts * 4 + (size_t)dig_table_words(c->subs[s].n + c->subs[s].n_str, ts) * 4;
+}
+
 bool batch_configure(emt_ctx* c, int S_t, bool upload) {
-  const size_t fixed = batch_smem_bytes(S_t, (int)c->n_sources, c->n_sub, 0, 0);
+  const bool dig = c->use_digit && !c->dig_key.empty();
+  const size_t fixed = batch_smem_bytes(S_t, (int)c->n_sources, c->n_sub, 0, 0) + (dig ? 16 : 0);
   if (fixed >= 227 * 1024) return false;
-  const size_t budget = 227 * 1024 - fixed - 16;
+  size_t budget = 227 * 1024 - fixed - 16;
+  int dig_grp = 0, dig_words = 0;   // digit form: most subsystems of a group, largest table of a group
   std::vector<BatchGroupDev> groups;
   std::vector<int32_t> lay, list;   // control layers per group (see BatchGroupDev)
   int max_cols = 0, max_nodes = 0;
-  int s0 = 0;
-  while (s0 < c->n_sub) {
-    int s1 = s0, cols = 0, nodes = 0;
-    while (s1 < c->n_sub) {
-      const SubDev& sd = c->subs[s1];
-      const int nc2 = cols + sd.n + sd.n_str, n2 = nodes + sd.n;
-      if (((size_t)nc2 * 12 + (size_t)n2 * 8) * S_t > budget) break;
-      cols = nc2;
-      nodes = n2;
-      ++s1;
-    }
-    if (s1 == s0) return false;
-    const SubDev& a = c->subs[s0];
-    const SubDev& b = c->subs[s1 - 1];
-    BatchGroupDev G{};
-    // control layers: layer l of the group = layer l of each of its subsystems
-    G.lay0 = (int)lay.size();
-    for (int s = s0; s < s1; ++s) G.n_lay = std::max(G.n_lay, c->subs[s].n_clay);
-    for (int l = 0; l < G.n_lay; ++l) {
-      lay.push_back((int32_t)list.size());
-      for (int s = s0; s < s1; ++s) {
-        const SubDev& sd = c->subs[s];
-        if (l >= sd.n_clay) continue;
-        constexpr int kSlotMask = (1 << kLayerTypeShift) - 1;
-        const int j0 = c->clay[sd.clay_off + l] & kSlotMask, j1 = c->clay[sd.clay_off + l + 1] & kSlotMask;
-        for (int j = j0; j < j1; ++j) list.push_back(sd.cb_off + j);
+  // (with the digit form the largest columns, nodes, members and tables may
+  // come from different groups: the budget shrinks until their sum fits)
+  for (int attempt = 0;; ++attempt) {
+    groups.clear();
+    lay.clear();
+    list.clear();
+    max_cols = max_nodes = dig_grp = dig_words = 0;
+    int s0 = 0;
+    while (s0 < c->n_sub) {
+      int s1 = s0, cols = 0, nodes = 0;
+      size_t dbytes = 0;
+      while (s1 < c->n_sub) {
+        const SubDev& sd = c->subs[s1];
+        const int nc2 = cols + sd.n + sd.n_str, n2 = nodes + sd.n;
+        const size_t d2 = dbytes + batch_dig_bytes(c, s1, S_t);
+        if (((size_t)nc2 * 12 + (size_t)n2 * 8) * S_t + d2 > budget) break;
+        cols = nc2;
+        nodes = n2;
+        dbytes = d2;
+        ++s1;
       }
+      if (dig && s1 > s0) {
+        int words = 0;
+        for (int s = s0; s < s1; ++s)
+          if (c->dig_ptr[s + 1] > c->dig_ptr[s])
+            words += dig_table_words(c->subs[s].n + c->subs[s].n_str, 16 * ((S_t + 15) / 16));
+        dig_words = std::max(dig_words, words);
+        dig_grp = std::max(dig_grp, s1 - s0);
+      }
+      if (s1 == s0) return false;
+      const SubDev& a = c->subs[s0];
+      const SubDev& b = c->subs[s1 - 1];
+      BatchGroupDev G{};
+      // control layers: layer l of the group = layer l of each of its subsystems
+      G.lay0 = (int)lay.size();
+      for (int s = s0; s < s1; ++s) G.n_lay = std::max(G.n_lay, c->subs[s].n_clay);
+      for (int l = 0; l < G.n_lay; ++l) {
+        lay.push_back((int32_t)list.size());
+        for (int s = s0; s < s1; ++s) {
+          const SubDev& sd = c->subs[s];
+          if (l >= sd.n_clay) continue;
+          constexpr int kSlotMask = (1 << kLayerTypeShift) - 1;
+          const int j0 = c->clay[sd.clay_off + l] & kSlotMask, j1 = c->clay[sd.clay_off + l + 1] & kSlotMask;
+          for (int j = j0; j < j1; ++j) list.push_back(sd.cb_off + j);
+        }
+      }
+      lay.push_back((int32_t)list.size());
+      // nonlinear resistors of the group's subsystems and their correction pairs
+      G.nl0 = a.nl_off;
+      G.nl1 = b.nl_off + b.n_nl;
+      G.fd0 = a.fd_off;
+      G.fd1 = b.fd_off + b.n_fd;
+      G.ce0 = a.ce_off;
+      G.ce1 = b.ce_off + b.n_ce;
+      G.sub0 = s0;
+      G.sub1 = s1;
+      G.nlc0 = G.nlc1 = 0;
+      for (int s = 0, pos = 0; s < s1; ++s) {
+        const SubDev& sd = c->subs[s];
+        if (s == s0) G.nlc0 = pos;
+        pos += sd.n_nl * sd.n;
+        G.nlc1 = pos;
+      }
+      G.node0 = a.node_off;
+      G.node1 = b.node_off + b.n;
+      G.col0 = c->b_sub_col_off[s0];
+      G.col1 = c->b_sub_col_off[s1 - 1] + b.n + b.n_str;
+      G.lc0 = a.lc_off;
+      G.lc1 = b.lc_off + b.n_lc;
+      G.le0 = a.le_off;
+      G.le1 = b.le_off + b.n_le;
+      groups.push_back(G);
+      max_cols = std::max(max_cols, cols);
+      max_nodes = std::max(max_nodes, nodes);
+      s0 = s1;
     }
-    lay.push_back((int32_t)list.size());
-    // nonlinear resistors of the group's subsystems and their correction pairs
-    G.nl0 = a.nl_off;
-    G.nl1 = b.nl_off + b.n_nl;
-    G.fd0 = a.fd_off;
-    G.fd1 = b.fd_off + b.n_fd;
-    G.ce0 = a.ce_off;
-    G.ce1 = b.ce_off + b.n_ce;
-    G.sub0 = s0;
-    G.sub1 = s1;
-    G.nlc0 = G.nlc1 = 0;
-    for (int s = 0, pos = 0; s < s1; ++s) {
-      const SubDev& sd = c->subs[s];
-      if (s == s0) G.nlc0 = pos;
-      pos += sd.n_nl * sd.n;
-      G.nlc1 = pos;
-    }
-    G.node0 = a.node_off;
-    G.node1 = b.node_off + b.n;
-    G.col0 = c->b_sub_col_off[s0];
-    G.col1 = c->b_sub_col_off[s1 - 1] + b.n + b.n_str;
-    G.lc0 = a.lc_off;
-    G.lc1 = b.lc_off + b.n_lc;
-    G.le0 = a.le_off;
-    G.le1 = b.le_off + b.n_le;
-    groups.push_back(G);
-    max_cols = std::max(max_cols, cols);
-    max_nodes = std::max(max_nodes, nodes);
-    s0 = s1;
+    const size_t total = batch_smem_bytes(S_t, (int)c->n_sources, c->n_sub, max_cols, max_nodes,
+                                          dig ? std::max(dig_words, 1) : 0, dig_grp);
+    if (total <= 227 * 1024) break;
+    if (!dig || attempt >= 8 || total - 227 * 1024 >= budget) return false;
+    budget -= total - 227 * 1024;
   }
   if (!upload) return true;
   if (c->d_grp) {
@@ -646,6 +693,8 @@ bool batch_configure(emt_ctx* c, int S_t, bool upload) {
   c->max_cols = std::max(max_cols, 1);
   c->max_nodes = std::max(max_nodes, 1);
   c->S_t = S_t;
+  c->dig_words = dig ? std::max(dig_words, 1) : 0;
+  c->dig_grp = dig_grp;
   return true;
 }
 
@@ -906,6 +955,45 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
       c->b_ev_off.push_back(x[2]);
     }
     c->b_ev_ptr.push_back((int64_t)c->b_ev_step.size());
+  }
+  // digit form: the matrices (of at most kDigRows rows and kDigCols columns)
+  // that at least 16 scenarios (or all) select, so that whole tiles share them
+  {
+    const int64_t nvar = (int64_t)c->epochs.size() - c->n_base_epochs;
+    std::vector<int64_t> users(nvar, 0), last(nvar, -1);
+    for (int64_t q = 0; q < S; ++q)
+      for (int k = 0; k < nsub; ++k)
+        for (int64_t x = c->msel_ptr[q * nsub + k]; x < c->msel_ptr[q * nsub + k + 1]; ++x) {
+          const int64_t v = c->msel_mat[x] - c->n_base_epochs;
+          if (last[v] != q) {
+            last[v] = q;
+            ++users[v];
+          }
+        }
+    std::vector<std::vector<int64_t>> mats(nsub);   // epoch entries per subsystem
+    for (int64_t v = 0; v < nvar; ++v) {   // (selections name a variant's first state matrix; its others follow)
+      const int k = c->var_sub[v];
+      const SubDev& sd = c->subs[k];
+      if (users[v] < std::min<int64_t>(16, S) || sd.n > kDigRows || sd.n + sd.n_str > kDigCols) continue;
+      for (int w = 0; w < sd.n_states && v + w < nvar; ++w) mats[k].push_back(c->n_base_epochs + v + w);
+    }
+    c->dig_ptr.assign(1, 0);
+    int64_t doff = 0;
+    for (int k = 0; k < nsub; ++k) {
+      const SubDev& sd = c->subs[k];
+      for (int64_t e : mats[k]) {
+        c->dig_key.push_back(c->epochs[e].ginv_off);
+        c->dig_val.push_back(doff);
+        c->dig_mat_goff.push_back(c->epochs[e].ginv_off);
+        c->dig_mat_n.push_back(sd.n);
+        c->dig_mat_nc.push_back(sd.n + sd.n_str);
+        doff += (dig_matrix_words(sd.n, sd.n + sd.n_str) + 3) & ~(int64_t)3;   // 16-byte aligned fragments
+      }
+      c->dig_ptr.push_back((int32_t)c->dig_key.size());
+      c->dig_sub_n.push_back(sd.n);
+      c->dig_node0.push_back(sd.node_off);
+    }
+    c->dig_len = doff;
   }
   // runtime switches: per subsystem (first switch, count, matrix stride,
   // first internal node); states are per scenario
@@ -2063,6 +2151,15 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
     UP(d_ev_step, b_ev_step)
     UP(d_ev_sub, b_ev_sub)
     UP(d_ev_off, b_ev_off)
+    UP(d_dig_ptr, dig_ptr)
+    UP(d_dig_key, dig_key)
+    UP(d_dig_val, dig_val)
+    UP(d_sub_node0, dig_node0)
+    UP(d_sub_n, dig_sub_n)
+    UP(d_dig_mat_goff, dig_mat_goff)
+    UP(d_dig_mat_n, dig_mat_n)
+    UP(d_dig_mat_nc, dig_mat_nc)
+    if (e == cudaSuccess) e = c->alloc_zero(&c->d_dig, (size_t)std::max<int64_t>(c->dig_len, 1));
     if (e == cudaSuccess) e = c->upload(&c->d_le_bring, c->le_bring);
     if (e == cudaSuccess) e = c->upload(&c->d_le_bfar, c->le_bfar);
     if (e == cudaSuccess) e = c->upload(&c->d_bsrc_amp, c->bsrc_amp);
@@ -2223,6 +2320,9 @@ extern "C" emt_status emt_prefactor(emt_ctx* c) {
   if (e == cudaSuccess) e = launch_prefactor(p, std::max(c->lim.n, 1), nullptr);
   if (e == cudaSuccess) e = reset_matrix_cache(c, nullptr);
   if (e == cudaSuccess) e = build_state_space(c, nullptr);
+  if (e == cudaSuccess && c->batched)   // the shared matrices in digit form
+    e = launch_batch_digits(c->d_ginv, c->d_ginv_lo, c->d_dig_mat_goff, c->d_dig_mat_n, c->d_dig_mat_nc, c->d_dig_val,
+                            (int)c->dig_key.size(), c->d_dig, nullptr);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   std::vector<int32_t> status(mat_sub.size(), 0);
   if (e == cudaSuccess && !status.empty())
@@ -2381,6 +2481,16 @@ static cudaError_t batch_launch(emt_ctx* c, int64_t n0, int64_t n_steps, cudaStr
   b.bnd.h = c->n_lc_total * c->S;
   b.bnd.ginv = c->ginv_len;
   b.bnd.rec = record ? c->rec_rows * c->S * (int64_t)c->rec_channels.size() : 0;
+  if (c->use_digit && c->dig_words > 0) {
+    b.dig = c->d_dig;
+    b.dig_ptr = c->d_dig_ptr;
+    b.dig_key = c->d_dig_key;
+    b.dig_val = c->d_dig_val;
+    b.sub_node0 = c->d_sub_node0;
+    b.sub_n = c->d_sub_n;
+    b.dig_words = c->dig_words;
+    b.dig_grp = std::max(c->dig_grp, 1);
+  }
   return launch_batch(b, c->batch_threads, st, c->use_graph ? &c->graph : nullptr);
 }
 
@@ -2800,6 +2910,7 @@ extern "C" emt_status emt_autotune(emt_ctx* c, int64_t trial_steps, void* stream
   for (int St : cand) {
     if (!batch_configure(c, St, true)) continue;
     for (int th : threads) {
+      if (th > batch_max_threads(c->use_digit && c->dig_words > 0)) continue;
       c->batch_threads = th;
       emt_status rs = emt_reset(c);
       if (rs != EMT_OK) return rs;
@@ -2844,9 +2955,9 @@ extern "C" emt_status emt_set_option(emt_ctx* c, const char* key, int64_t value)
   if (k == "scenarios_per_cta" || k == "batch_threads") {
     if (!c->batched) return c->fail(EMT_EINVAL, k + " applies to a context built with a scenario set");
     if (k == "batch_threads") {
-      if (value < 32 || value > batch_max_threads() || value % 32)
-        return c->fail(EMT_EINVAL, "batch_threads must be a multiple of 32 in [32, " +
-                                       std::to_string(batch_max_threads()) + "]");
+      const int most = batch_max_threads(c->use_digit && c->dig_words > 0);
+      if (value < 32 || value > most || value % 32)
+        return c->fail(EMT_EINVAL, "batch_threads must be a multiple of 32 in [32, " + std::to_string(most) + "]");
       c->batch_threads = (int)value;
       return EMT_OK;
     }
@@ -2860,6 +2971,20 @@ extern "C" emt_status emt_set_option(emt_ctx* c, const char* key, int64_t value)
                                      std::to_string(kSmallMaxNodes) + " nodes with basic elements only)");
     cudaDeviceSynchronize();
     c->use_small = value != 0;
+    return EMT_OK;
+  }
+  if (k == "digit_solve") {   // 1: the multi-scenario solve of shared matrices on the tensor cores (digit form)
+    if (!c->batched) return c->fail(EMT_EINVAL, "digit_solve applies to a context built with a scenario set");
+    cudaDeviceSynchronize();
+    c->use_digit = value != 0;
+    if (c->use_digit) c->batch_threads = std::min(c->batch_threads, batch_max_threads(true));
+    if (!batch_configure(c, c->S_t, true)) {
+      c->use_digit = false;
+      batch_configure(c, c->S_t, true);
+      return c->fail(EMT_EINVAL, "digit_solve: the digit table does not fit next to scenarios_per_cta " +
+                                     std::to_string(c->S_t));
+    }
+    c->tuned = false;
     return EMT_OK;
   }
   if (k == "state_space") {   // 0 off, 1 auto (default), 2 on: the state-space form (emt_ss.cu)
@@ -2928,6 +3053,8 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "shard_window") *value = c->sharded ? c->shard_window : 0;
   else if (k == "shard_ctas") *value = c->sharded ? (int64_t)c->shard_active.size() : c->n_sub;
   else if (k == "state_space") *value = state_space_runs(c) ? 1 : 0;
+  else if (k == "digit_solve") *value = c->batched && c->use_digit && c->dig_words > 0 ? 1 : 0;
+  else if (k == "digit_matrices") *value = (int64_t)c->dig_key.size();
   else if (k == "warp_per_subsystem") *value = c->small_ok && c->use_small ? 1 : 0;
   else if (k == "lazy_subsystems") {   // subsystems whose switch states are factorised at run time
     int64_t m = 0;

@@ -28,12 +28,73 @@
 
 #include "emt_internal.h"
 #include "emt_device.cuh"
+#include "emt_digits.cuh"
 
 namespace emt {
 
 namespace {
 
 constexpr int kBatchMaxThreads = 1024;
+// the digit-form instance takes at most 512 threads (128 registers each: its
+// tensor-core loop keeps two accumulator chains and the 64-bit sums live)
+constexpr int kBatchDigitThreads = 512;
+
+// ---------------------------------------------------------------- digit form
+//
+// For a subsystem whose solve matrix X every scenario of the tile shares,
+// process 4 over the tile, V = X [i^(1) .. i^(S_t)], is a dense product; it
+// runs exactly on the bf16 tensor cores in the digit form of emt_digits.cuh
+// (62-bit fixed point, balanced base-256 digits, exact fp32 sums of digit
+// products, one rounding to double).  mma.m16n8k16 with M = 16 scenarios
+// (the injection digits b, from a shared-memory table), N = 8 rows of X
+// (its digits a, prepared once per matrix), K = 16 solve columns; the
+// pairs with a + b = u go to one fp32 accumulator (at most 8 pairs of 64
+// columns: below 2^23, exact), turned into integers per u.
+
+__device__ __forceinline__ void dg_mma(float* d, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                       unsigned b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ long long dg_shl64(int x, int sh) {
+  return (long long)((unsigned long long)(long long)x << sh);
+}
+
+// One CTA per matrix: each row as 62-bit fixed point against its own scale
+// (X_hi + X_lo), split into digits, written in the B-fragment order
+// (dig_matrix_words), then the row exponents.  Padding stays zero.
+__global__ void __launch_bounds__(256) batch_digits_kernel(const double* ginv, const float* ginv_lo,
+                                                           const int64_t* mat_goff, const int32_t* mat_n,
+                                                           const int32_t* mat_nc, const int64_t* mat_doff,
+                                                           uint32_t* dig) {
+  __shared__ unsigned s_em[kDigRows];
+  const int mi = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+  const int n = mat_n[mi], nc = mat_nc[mi], r8n = (n + 7) / 8, ks = (nc + 15) / 16;
+  const double* xh = ginv + mat_goff[mi];
+  const float* xl = ginv_lo + mat_goff[mi];
+  uint32_t* out = dig + mat_doff[mi];
+  int* ex = reinterpret_cast<int*>(out + (int64_t)8 * r8n * ks * 64);
+  for (int r = tid; r < 8 * r8n; r += T) {
+    unsigned em = 1;
+    for (int k = 0; r < n && k < nc; ++k)
+      em = max(em, max(dg_expo(xh[r * nc + k]), dg_expo((double)xl[r * nc + k])));
+    if (r < n) s_em[r] = em;
+    ex[r] = (int)em;
+  }
+  __syncthreads();
+  unsigned short* o16 = reinterpret_cast<unsigned short*>(out);
+  for (int idx = tid; idx < n * nc; idx += T) {
+    const int r = idx / nc, k = idx - r * nc;
+    const long long np = dg_fixed(xh[idx], s_em[r]) + dg_fixed((double)xl[idx], s_em[r]) + kDigitBias;
+    const int R8 = r >> 3, g = r & 7, st = k >> 4, kk = k & 15, t = (kk & 7) >> 1, half = kk >> 3, el = kk & 1;
+    for (int a = 0; a < kDigits; ++a) {
+      const int64_t word = ((int64_t)(a * r8n + R8) * ks + st) * 64 + 2 * (4 * g + t) + half;
+      o16[2 * word + el] = (unsigned short)dg_digit_bf16(np, a);
+    }
+  }
+}
 
 // Ring slot of step `step` in a ring of depth d1 (steps stay below 2^31).
 __device__ __forceinline__ int64_t ring_slot(long long step, int d1) { return (int64_t)((unsigned)step % (unsigned)d1); }
@@ -270,7 +331,10 @@ __device__ __forceinline__ void batch_rs_decide(const BatchParams& P, long long*
   }
 }
 
-__global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams P) {
+// kDigit: the instance with the digit-form solve (P.dig set); the other keeps
+// the FP64 kernel's registers free of it
+template <bool kDigit>
+__global__ void __launch_bounds__(kDigit ? kBatchDigitThreads : kBatchMaxThreads, 1) batch_kernel(BatchParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int St = P.S_t;
   const int sigma0 = blockIdx.x * St;
@@ -287,6 +351,13 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
   double* vv = iv + (size_t)P.max_cols * St;                             // [max_nodes][St]
   float* ivf = reinterpret_cast<float*>(vv + (size_t)P.max_nodes * St);  // [max_cols][St]
   double* wsc = reinterpret_cast<double*>(ivf + (((size_t)P.max_cols * St + 1) & ~(size_t)1));   // [n_sources][2]
+  // digit form: per subsystem of the group its digit matrix (or -1), the
+  // injection exponents of a batch [dig_grp][TS], the digit table
+  const int TS = 16 * ((St + 15) / 16);
+  long long* dsel = reinterpret_cast<long long*>(wsc + 2 * (size_t)P.n_sources);   // [dig_grp]
+  int* dem = reinterpret_cast<int*>(dsel + P.dig_grp);
+  uint32_t* dtab = reinterpret_cast<uint32_t*>(
+      (reinterpret_cast<uintptr_t>(dem + (P.dig != nullptr ? P.dig_grp * TS : 0)) + 15) & ~(uintptr_t)15);
 
   // solve matrices in force at the first step
   for (int sl = tid; sl < n_here; sl += T) {
@@ -377,6 +448,20 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
         iv[x] = acc;
         ivf[x] = f32_trunc(acc);
       }
+      // digit form: a subsystem whose matrix the whole tile shares, and that
+      // matrix in digit form
+      if (kDigit)
+        for (int j = tid; j < G.sub1 - G.sub0; j += T) {
+          const int s = G.sub0 + j;
+          const long long c0 = cur[s];
+          bool same = true;
+          for (int sl = 1; sl < n_here && same; ++sl) same = cur[(size_t)sl * n_sub + s] == c0;
+          long long d = -1;
+          if (same)
+            for (int x = __ldg(P.dig_ptr + s); x < __ldg(P.dig_ptr + s + 1); ++x)
+              if (__ldg(P.dig_key + x) == c0) d = __ldg(P.dig_val + x);
+          dsel[j] = d;
+        }
       __syncthreads();
 
       // process 4: v = (X_hi + X_lo) [i; -h_strong], each scenario with its
@@ -390,6 +475,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
         if (sl >= n_here) continue;
         const int node = G.node0 + k;
         const int s = __ldg(P.node_sub + node), r = __ldg(P.node_r + node);
+        if (kDigit && dsel[s - G.sub0] >= 0) continue;   // (the digit form below)
         const int nc = __ldg(P.sub_nc + s);
         const int cb = __ldg(P.sub_col_off + s) - G.col0;
         const int64_t off =
@@ -423,6 +509,124 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
         if (rec_now) {
           const int pos = P.rec_pos[node];
           if (pos >= 0) P.rec[EMT_CHK(P.err, (rec_row * S + sigma0 + sl) * P.n_rec + pos, P.bnd.rec, kChkRecord)] = v;
+        }
+      }
+      // the digit-form subsystems, in batches whose injection digits fit the table
+      if (kDigit) {
+        const int warp = tid >> 5, lane = tid & 31, n_warps = T >> 5, g = lane >> 2, t = lane & 3;
+        for (int jb0 = 0; jb0 < G.sub1 - G.sub0;) {
+          // the batch [jb0, jb1): the digit subsystems whose tables fit dig_words (all of the group's, as sized)
+          int jb1 = jb0, used = 0, cnt = 0;
+          for (; jb1 < G.sub1 - G.sub0; ++jb1) {
+            if (dsel[jb1] < 0) continue;
+            const int w = dig_table_words(__ldg(P.sub_nc + G.sub0 + jb1), TS);
+            if (used + w > P.dig_words) break;
+            used += w;
+            ++cnt;
+          }
+          if (cnt == 0) {   // (every digit subsystem's table fits by construction; a step past one never loops)
+            jb0 = jb1 + (jb1 < G.sub1 - G.sub0 ? 1 : 0);
+            continue;
+          }
+          // injection digits: a warp per (subsystem, scenario): its scale (largest exponent), then the table
+          for (int it = warp; it < cnt * n_here; it += n_warps) {
+            int jj = it / n_here, sl = it - jj * n_here, j = jb0, off = 0;
+            for (;; ++j) {   // the jj-th digit subsystem of the batch, and its table offset
+              if (dsel[j] < 0) continue;
+              if (jj == 0) break;
+              off += dig_table_words(__ldg(P.sub_nc + G.sub0 + j), TS);
+              --jj;
+            }
+            const int s = G.sub0 + j, nc = __ldg(P.sub_nc + s), ks = (nc + 15) >> 4, sw = 8 * ks + 4;
+            const double* ivc = iv + (size_t)(__ldg(P.sub_col_off + s) - G.col0) * St + sl;
+            unsigned em = 1;
+            for (int k = lane; k < nc; k += 32) em = max(em, dg_expo(ivc[(size_t)k * St]));
+            em = max(__reduce_max_sync(0xffffffffu, em), 1u);
+            uint32_t* tab = dtab + off;
+            for (int kw = lane; kw < 8 * ks; kw += 32) {
+              const int k = 2 * kw;
+              const double x0 = k < nc ? ivc[(size_t)k * St] : 0.0, x1 = k + 1 < nc ? ivc[(size_t)(k + 1) * St] : 0.0;
+              const long long n0 = dg_fixed(x0, em) + kDigitBias, n1 = dg_fixed(x1, em) + kDigitBias;
+#pragma unroll
+              for (int b = 0; b < kDigits; ++b)
+                tab[(b * TS + sl) * sw + kw] = dg_digit_bf16(n0, b) | (dg_digit_bf16(n1, b) << 16);
+            }
+            if (lane == 0) dem[it - (it / n_here) * n_here + (it / n_here) * TS] = (int)em;
+          }
+          __syncthreads();
+          // products: a warp per (subsystem, 16 scenarios, 8 rows)
+          int n_task = 0;
+          for (int j = jb0; j < jb1; ++j)
+            if (dsel[j] >= 0) n_task += (TS / 16) * ((__ldg(P.sub_n + G.sub0 + j) + 7) >> 3);
+          for (int it = warp; it < n_task; it += n_warps) {
+            int rem = it, j = jb0, jj = 0, off = 0, ntile = 0;
+            for (;; ++j) {
+              if (dsel[j] < 0) continue;
+              ntile = (TS / 16) * ((__ldg(P.sub_n + G.sub0 + j) + 7) >> 3);
+              if (rem < ntile) break;
+              rem -= ntile;
+              off += dig_table_words(__ldg(P.sub_nc + G.sub0 + j), TS);
+              ++jj;
+            }
+            const int s = G.sub0 + j, n = __ldg(P.sub_n + s), nc = __ldg(P.sub_nc + s);
+            const int ks = (nc + 15) >> 4, sw = 8 * ks + 4, r8n = (n + 7) >> 3;
+            const int stile = rem / r8n, R8 = rem - stile * r8n;
+            const uint32_t* dm = P.dig + dsel[j];
+            const uint32_t* tab = dtab + off + (16 * stile + g) * sw + t;
+            long long ta[4] = {0, 0, 0, 0}, tb[4] = {0, 0, 0, 0};
+            for (int u = kDigitGroupLo; u <= 2 * kDigits - 2; ++u) {
+              // pairs (a, u - a) two at a time on two accumulators, so that two MMA chains are in flight
+              float e0[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f};
+              const int a_hi = min(kDigits - 1, u);
+              for (int a = max(0, u - (kDigits - 1)); a <= a_hi; a += 2) {
+                const bool two = a + 1 <= a_hi;
+                const uint32_t* tA = tab + (u - a) * TS * sw;
+                const uint32_t* tB = tab + (u - a - (two ? 1 : 0)) * TS * sw;
+                const uint2* fA = reinterpret_cast<const uint2*>(dm) + ((size_t)(a * r8n + R8) * ks) * 32 + lane;
+                const uint2* fB = fA + (size_t)r8n * ks * 32;
+                for (int st = 0; st < ks; ++st) {
+                  const uint2 bA = __ldg(fA + st * 32);
+                  dg_mma(e0, tA[8 * st], tA[8 * sw + 8 * st], tA[8 * st + 4], tA[8 * sw + 8 * st + 4], bA.x, bA.y);
+                  if (two) {
+                    const uint2 bB = __ldg(fB + st * 32);
+                    dg_mma(e1, tB[8 * st], tB[8 * sw + 8 * st], tB[8 * st + 4], tB[8 * sw + 8 * st + 4], bB.x, bB.y);
+                  }
+                }
+                if (ks > 4) {   // more than 64 columns: each pair's sums leave the accumulators at once
+#pragma unroll
+                  for (int c = 0; c < 4; ++c) {
+                    const int q = dg_acc_int(e0[c]) + dg_acc_int(e1[c]);
+                    if (u >= 11) ta[c] += dg_shl64(q, 8 * (u - 11));
+                    else tb[c] += dg_shl64(q, 8 * (u - kDigitGroupLo));
+                    e0[c] = e1[c] = 0.f;
+                  }
+                }
+              }
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const int q = dg_acc_int(e0[c]) + dg_acc_int(e1[c]);
+                if (u >= 11) ta[c] += dg_shl64(q, 8 * (u - 11));
+                else tb[c] += dg_shl64(q, 8 * (u - kDigitGroupLo));
+              }
+            }
+            const int* ex = reinterpret_cast<const int*>(dm + (size_t)8 * r8n * ks * 64);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const int sl = 16 * stile + g + (c >= 2 ? 8 : 0), r = 8 * R8 + 2 * t + (c & 1);
+              if (sl < n_here && r < n) {
+                const double v = dg_to_double(ta[c], tb[c], __ldg(ex + r) + dem[jj * TS + sl] - 2120);
+                const int node = __ldg(P.sub_node0 + s) + r;
+                vv[(size_t)(node - G.node0) * St + sl] = v;
+                if (rec_now) {
+                  const int pos = P.rec_pos[node];
+                  if (pos >= 0)
+                    P.rec[EMT_CHK(P.err, (rec_row * S + sigma0 + sl) * P.n_rec + pos, P.bnd.rec, kChkRecord)] = v;
+                }
+              }
+            }
+          }
+          jb0 = jb1;
+          if (jb0 < G.sub1 - G.sub0) __syncthreads();   // (the table is refilled by the next batch)
         }
       }
       __syncthreads();
@@ -578,11 +782,23 @@ cudaError_t launch_slot_constants(const BranchDev* br, const int32_t* lc_idx, in
   return cudaGetLastError();
 }
 
-int batch_max_threads() { return kBatchMaxThreads; }
+int batch_max_threads(bool digit) { return digit ? kBatchDigitThreads : kBatchMaxThreads; }
 
-size_t batch_smem_bytes(int S_t, int n_sources, int n_sub, int max_cols, int max_nodes) {
-  return (size_t)n_sources * S_t * 8 + (size_t)S_t * n_sub * 8 + (size_t)S_t * 8 + (size_t)max_nodes * S_t * 8 +
-         (((size_t)max_cols * S_t + 1) & ~(size_t)1) * 12 + (size_t)n_sources * 16;
+size_t batch_smem_bytes(int S_t, int n_sources, int n_sub, int max_cols, int max_nodes, int dig_words,
+                        int dig_grp) {
+  size_t b = (size_t)n_sources * S_t * 8 + (size_t)S_t * n_sub * 8 + (size_t)S_t * 8 + (size_t)max_nodes * S_t * 8 +
+             (((size_t)max_cols * S_t + 1) & ~(size_t)1) * 12 + (size_t)n_sources * 16;
+  if (dig_words > 0)   // digit form: dsel, the batch's exponents, 16-byte alignment, the table
+    b += (size_t)dig_grp * 8 + (size_t)dig_grp * 16 * ((S_t + 15) / 16) * 4 + 16 + (size_t)dig_words * 4;
+  return b;
+}
+
+cudaError_t launch_batch_digits(const double* ginv, const float* ginv_lo, const int64_t* mat_goff,
+                                const int32_t* mat_n, const int32_t* mat_nc, const int64_t* mat_doff, int n_mats,
+                                uint32_t* dig, cudaStream_t st) {
+  if (n_mats <= 0) return cudaSuccess;
+  batch_digits_kernel<<<n_mats, 256, 0, st>>>(ginv, ginv_lo, mat_goff, mat_n, mat_nc, mat_doff, dig);
+  return cudaGetLastError();
 }
 
 void batch_graph_destroy(BatchGraph* g) {
@@ -598,24 +814,29 @@ void batch_graph_destroy(BatchGraph* g) {
 // launch goes through a CUDA graph that is built once per launch shape and
 // whose kernel node gets this call's arguments.
 cudaError_t launch_batch(const BatchParams& p, int threads, cudaStream_t st, BatchGraph* graph) {
-  const size_t smem = batch_smem_bytes(p.S_t, p.n_sources, p.n_sub, p.max_cols, p.max_nodes);
-  if (smem > 227 * 1024 || threads < 32 || threads > kBatchMaxThreads || threads % 32) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem =
+      batch_smem_bytes(p.S_t, p.n_sources, p.n_sub, p.max_cols, p.max_nodes, p.dig ? p.dig_words : 0, p.dig_grp);
+  if (smem > 227 * 1024 || threads < 32 || threads > (p.dig != nullptr ? kBatchDigitThreads : kBatchMaxThreads) ||
+      threads % 32)
+    return cudaErrorInvalidValue;
+  const void* fn = p.dig != nullptr ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int grid = (p.S + p.S_t - 1) / p.S_t;
   if (!graph) {
-    batch_kernel<<<grid, threads, smem, st>>>(p);
+    if (p.dig != nullptr) batch_kernel<true><<<grid, threads, smem, st>>>(p);
+    else batch_kernel<false><<<grid, threads, smem, st>>>(p);
     return cudaGetLastError();
   }
   BatchParams arg = p;
   void* args[] = {&arg};
   cudaKernelNodeParams kp{};
-  kp.func = (void*)batch_kernel;
+  kp.func = const_cast<void*>(fn);
   kp.gridDim = dim3(grid);
   kp.blockDim = dim3(threads);
   kp.sharedMemBytes = (unsigned)smem;
   kp.kernelParams = args;
-  if (graph->exec && (graph->grid != grid || graph->threads != threads || graph->smem != smem))
+  if (graph->exec && (graph->grid != grid || graph->threads != threads || graph->smem != smem || graph->func != fn))
     batch_graph_destroy(graph);
   if (!graph->exec) {
     e = cudaGraphCreate(&graph->graph, 0);
@@ -628,6 +849,7 @@ cudaError_t launch_batch(const BatchParams& p, int threads, cudaStream_t st, Bat
     graph->grid = grid;
     graph->threads = threads;
     graph->smem = smem;
+    graph->func = fn;
   } else {
     e = cudaGraphExecKernelNodeSetParams(graph->exec, graph->node, &kp);
     if (e != cudaSuccess) return e;

@@ -501,7 +501,39 @@ struct BatchParams {
   double dt;
   int32_t* err;                // device error word (the checks build latches there)
   Bounds bnd;                  // ring: slots of the rings x S; h: L/C slots x S; ginv; rec
+  // Digit form of the solve on the bf16 tensor cores (emt_digits.cuh) for a
+  // subsystem whose matrix all scenarios of a tile share: per subsystem s its
+  // matrices in digit form, dig_key[x] = ginv offset, dig_val[x] = word
+  // offset in dig (x in dig_ptr[s] .. dig_ptr[s + 1]); per subsystem its
+  // first internal node and rows; dig_words: the shared-memory digit table's
+  // words, dig_grp: the most subsystems of a group (nullptr dig: off).
+  const uint32_t* dig;
+  const int32_t* dig_ptr;
+  const int64_t* dig_key;
+  const int64_t* dig_val;
+  const int32_t* sub_node0;
+  const int32_t* sub_n;
+  int32_t dig_words, dig_grp;
 };
+
+// Digit matrices of the multi-scenario solve: B fragments of
+// mma.m16n8k16 (k = solve column, n = row of X): fragment (a, R8, s) for
+// digit a, rows 8 R8 .. 8 R8 + 7, columns 16 s .. 16 s + 15 at word
+// ((a R8n + R8) ks + s) 64 + 2 lane (lane 4g + t: row 8 R8 + g, columns
+// 16 s + 2t, +1 in the first word, + 8, + 9 in the second), then the 8 R8n
+// row exponents.  Subsystems of at most kDigRows rows and kDigCols columns.
+constexpr int kDigRows = 64;
+constexpr int kDigCols = 128;
+__host__ __device__ inline int64_t dig_matrix_words(int n, int nc) {
+  const int r8 = (n + 7) / 8, ks = (nc + 15) / 16;
+  return (int64_t)8 * r8 * ks * 64 + 8 * r8;
+}
+// shared-memory table words of one subsystem's injection digits for a tile
+// of ts scenario rows (a multiple of 16): 8 digits x ts rows x (8 ks + 4)
+__host__ __device__ inline int dig_table_words(int nc, int ts) { return 8 * ts * (8 * ((nc + 15) / 16) + 4); }
+cudaError_t launch_batch_digits(const double* ginv, const float* ginv_lo, const int64_t* mat_goff,
+                                const int32_t* mat_n, const int32_t* mat_nc, const int64_t* mat_doff, int n_mats,
+                                uint32_t* dig, cudaStream_t st);
 
 // A CUDA graph holding the one multi-scenario launch; its kernel node's
 // arguments are updated per call.
@@ -511,6 +543,7 @@ struct BatchGraph {
   cudaGraphNode_t node = nullptr;
   int grid = 0, threads = 0;
   size_t smem = 0;
+  const void* func = nullptr;   // the kernel instance of the node
   int64_t launches = 0;
 };
 
@@ -637,8 +670,9 @@ size_t ss_smem_bytes(int rows, int cols, int n, int le, int src, int ln, int lc)
 constexpr int kSsThreads = 256;
 int forward_blocks_per_sm(const FwdLimits& lim);   // resident CTAs per SM (0 on error)
 cudaError_t launch_batch(const BatchParams& p, int threads, cudaStream_t st, BatchGraph* graph);
-size_t batch_smem_bytes(int S_t, int n_sources, int n_sub, int max_cols, int max_nodes);
-int batch_max_threads();
+size_t batch_smem_bytes(int S_t, int n_sources, int n_sub, int max_cols, int max_nodes, int dig_words = 0,
+                        int dig_grp = 0);
+int batch_max_threads(bool digit);   // most threads of a multi-scenario CTA (the digit-form instance: fewer)
 void batch_graph_destroy(BatchGraph* graph);
 cudaError_t launch_source_coefficients(const double* amp, const double* phase, int64_t count, double* ac, double* as,
                                        cudaStream_t st);
