@@ -322,6 +322,9 @@ def scenario_leg(name, net, sc, n_steps, n_check, rec_channels, decim, tune_step
            "solve_frac_of_fp64_peak": flops_per_scen_step * S * n_steps / (ms / 1e3) / 1e9 / fp64_peak_gflops(),
            "n_matrix_variants": sim.info("n_matrix_variants"), "scenarios_per_cta": sim.info("scenarios_per_cta"),
            "threads_per_cta": sim.info("batch_threads"), "subsystem_groups": sim.info("batch_groups"),
+           "solve_form": ("tensor cores (tcgen05 digit form) for the shared matrices of at least "
+                          f"{sim.info('digit_min_rows')} rows, FP64 for the rest" if sim.info("digit_solve")
+                          else "FP64"),
            "build_prefactor_s": round(build_s, 3), "autotune_s": round(tune_s, 3),
            "autotune_trial_steps": tune_steps, "kernel_launches": 1, "launch": "one CUDA-graph launch",
            "parity_rel_err_sampled": worst, "parity_scenarios": check,
@@ -768,15 +771,25 @@ def shared_g_digit_leg(steps=None):
     net, sc = g.shared_g(n_scenarios=4096)
     N = steps or 100
     out = []
-    for St, th in ((8, 512), (16, 512), (28, 512), (28, 1024)):
-        for digit in (0, 1):
-            if digit and th > 512:
-                continue
+    for St, th in ((16, 1024), (28, 512), (28, 1024), (None, None)):
+        for digit in (0, 1, 2):   # 2: the digit form for every shared matrix (digit_min_rows 1)
             ctx = emt.emt_build_network(net, sc)
             emt.emt_prefactor(ctx)
-            emt.emt_set_option(ctx, "scenarios_per_cta", St)
-            emt.emt_set_option(ctx, "batch_threads", th)
-            emt.emt_set_option(ctx, "digit_solve", digit)
+            emt.emt_set_option(ctx, "digit_solve", min(digit, 1))
+            if digit == 2:
+                emt.emt_set_option(ctx, "digit_min_rows", 1)
+            tuned = St is None
+            try:
+                if tuned:   # the autotuner's pick for this form
+                    emt.emt_autotune(ctx, 20)
+                    St, th = emt.emt_get_info(ctx, "scenarios_per_cta"), emt.emt_get_info(ctx, "batch_threads")
+                else:
+                    emt.emt_set_option(ctx, "scenarios_per_cta", St)
+                    emt.emt_set_option(ctx, "batch_threads", th)
+            except emt.EmtError as e:   # (a shape whose tables do not fit in shared memory)
+                out.append({"scenarios_per_cta": St, "threads": th, "digit_solve": digit, "error": str(e)})
+                emt.emt_destroy(ctx)
+                continue
             stream = torch.cuda.current_stream()
             emt.emt_step_n(ctx, 10, stream)
             emt.emt_sync(ctx)
@@ -787,10 +800,12 @@ def shared_g_digit_leg(steps=None):
             e1.record(stream)
             emt.emt_sync(ctx)
             ms = e0.elapsed_time(e1)
-            out.append({"scenarios_per_cta": St, "threads": th, "digit_solve": digit,
+            out.append({"scenarios_per_cta": St, "threads": th, "digit_solve": digit, "autotuned": tuned,
                         "groups": emt.emt_get_info(ctx, "batch_groups"),
                         "scenario_steps_per_s": 4096 * N / (ms / 1e3)})
             emt.emt_destroy(ctx)
+            if tuned:
+                St = th = None
     return {"workload": "shared-G study, 4,096 scenarios of the 3,000-node network, fixed launch shapes",
             "runs": out}
 

@@ -337,7 +337,10 @@ emt_status emt_read_controls(emt_ctx* ctx, double* y, int64_t n, int32_t on_devi
  * scenarios per CTA S_t (about k CTAs per SM for k = 1..6, and the powers
  * of two up to 32, where the subsystem groups fit in shared memory) and
  * 256, 512 or 1024 threads per CTA, run `trial_steps` steps from the
- * de-energised state on `cuda_stream` and keep the fastest.  Resets the
+ * de-energised state on `cuda_stream` and keep the fastest; unless
+ * "digit_solve" was set, both forms of the solve are timed (FP64, and the
+ * tensor-core digit form when a solve matrix qualifies) and the faster
+ * one is kept (emt_get_info "digit_solve" reports it).  Resets the
  * context to step 0 afterwards.  A context without a scenario set has no
  * tunable shape (EMT_OK, nothing changes).  The chosen shape is reported by
  * emt_get_info ("scenarios_per_cta", "batch_threads"); it can also be set
@@ -419,9 +422,14 @@ emt_status emt_sync(emt_ctx* ctx, int32_t* dev_err_info);
  * R/L/C branches, sources, fixed-time switches, lossless lines: 0 off,
  * 1 auto (default: while every subsystem's M has at most 2,048 entries),
  * 2 on), "digit_solve" (scenario sets: 1 runs process 4 of each subsystem
- * whose solve matrix a whole scenario tile shares as exact base-256 digit
- * products on the bf16 tensor cores, one rounding per entry; default 0: it
- * measured slower than the FP64 solve; at most 512 threads per CTA while on).
+ * whose solve matrix a whole scenario tile shares, of at most 64 rows and
+ * 128 columns, as exact base-256 digit products on the tensor cores
+ * (tcgen05.mma, bf16 -> f32 accumulators in tensor memory), one rounding
+ * per entry; 0 keeps the FP64 solve; unset (default) the FP64 solve runs
+ * until emt_autotune picks the faster form; while on: at most 32 scenarios
+ * and at least 128 threads per CTA, and one CTA per SM), "digit_min_rows"
+ * (default 24: subsystems of fewer rows keep the FP64 solve in the digit
+ * form, where a small product costs more on the tensor cores than in FP64).
  * EINVAL for an unknown key. */
 emt_status emt_set_option(emt_ctx* ctx, const char* key, int64_t value);
 

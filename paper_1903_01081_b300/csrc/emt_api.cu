@@ -193,12 +193,12 @@ struct emt_ctx {
   std::vector<int32_t> var_sub;                        // subsystem of each variant matrix
   std::vector<int32_t> rm_ptr_br, rm_br, rm_ptr_le, rm_le;
   // flat per-slot arrays of the multi-scenario kernel (see BatchParams)
-  std::vector<int32_t> b_col_code, b_node_sub, b_node_r, b_sub_nc, b_sub_col_off, b_ent_ptr, b_bent;
+  std::vector<int32_t> b_col_code, b_col_sub, b_node_sub, b_node_r, b_sub_nc, b_sub_col_off, b_ent_ptr, b_bent;
   std::vector<int32_t> b_lc_nk, b_lc_nm, b_sb_src, b_le_nd, b_le_d1, b_ev_sub;
   std::vector<double> b_lc_e, b_sb_g, b_le_y2;
   std::vector<int8_t> b_lc_isl;
   std::vector<int64_t> b_ev_ptr, b_ev_step, b_ev_off;
-  int32_t *d_col_code = nullptr, *d_node_sub = nullptr, *d_node_r = nullptr, *d_sub_nc = nullptr,
+  int32_t *d_col_code = nullptr, *d_col_sub = nullptr, *d_node_sub = nullptr, *d_node_r = nullptr, *d_sub_nc = nullptr,
           *d_sub_col_off = nullptr, *d_ent_ptr = nullptr, *d_bent = nullptr, *d_lc_nk = nullptr,
           *d_lc_nm = nullptr, *d_sb_src = nullptr, *d_le_nd = nullptr, *d_le_d1 = nullptr, *d_ev_sub = nullptr;
   double *d_lc_e = nullptr, *d_sb_g = nullptr, *d_le_y2 = nullptr, *d_src_ac = nullptr, *d_src_as = nullptr;
@@ -214,7 +214,10 @@ struct emt_ctx {
   // digit form of the multi-scenario solve (emt_batch.cu): matrices that
   // whole tiles share, in digit form; option digit_solve
   bool use_digit = false;
-  int dig_words = 0, dig_grp = 0;                     // table words and most subsystems of a group, current S_t
+  bool digit_auto = true;   // digit_solve not set: emt_autotune times both forms and keeps the faster
+  int dig_min_rows = 24;   // option digit_min_rows: smaller subsystems keep the FP64 solve
+  bool dig_on = false;                                // the digit form runs (current configuration)
+  int dig_grp = 0;                                    // most subsystems of a group (current S_t)
   int64_t dig_len = 0;
   std::vector<int32_t> dig_ptr, dig_sub_n, dig_node0, dig_mat_n, dig_mat_nc;
   std::vector<int64_t> dig_key, dig_val, dig_mat_goff;
@@ -573,21 +576,22 @@ cudaError_t reset_batch_words(emt_ctx* c) {
 }
 
 // Shared memory a subsystem adds to its group in the digit form: its entry
-// of the selections, and, with a digit matrix, its injection exponents and
-// its digit table for tiles of S_t scenarios (0 with the digit form off).
+// of the selections (0 with the digit form off).
 size_t batch_dig_bytes(const emt_ctx* c, int s, int S_t) {
-  if (!c->use_digit || c->dig_key.empty()) return 0;
-  const int ts = 16 * ((S_t + 15) / 16);
-  if (c->dig_ptr[s + 1] == c->dig_ptr[s]) return 8;
-  return 8 + (size_t)ts * 4 + (size_t)dig_table_words(c->subs[s].n + c->subs[s].n_str, ts) * 4;
+  (void)s;
+  (void)S_t;
+  return c->use_digit && !c->dig_key.empty() ? 8 + 16 + 4 * kDigMaxTile : 0;   // dsel, dmeta, exponents
 }
 
 bool batch_configure(emt_ctx* c, int S_t, bool upload) {
   const bool dig = c->use_digit && !c->dig_key.empty();
-  const size_t fixed = batch_smem_bytes(S_t, (int)c->n_sources, c->n_sub, 0, 0) + (dig ? 16 : 0);
+  if (dig && S_t > kDigMaxTile) return false;   // (the digit table holds at most 32 scenario rows)
+  // the digit form's fixed part: the tile's exponents, alignment, one matrix's planes and the digit table
+  const size_t fixed = batch_smem_bytes(S_t, (int)c->n_sources, c->n_sub, 0, 0, dig, 0) +
+                       (dig ? kBatchDigitStaticSmem : 0);
   if (fixed >= 227 * 1024) return false;
   size_t budget = 227 * 1024 - fixed - 16;
-  int dig_grp = 0, dig_words = 0;   // digit form: most subsystems of a group, largest table of a group
+  int dig_grp = 0;   // digit form: most subsystems of a group
   std::vector<BatchGroupDev> groups;
   std::vector<int32_t> lay, list;   // control layers per group (see BatchGroupDev)
   int max_cols = 0, max_nodes = 0;
@@ -597,7 +601,7 @@ bool batch_configure(emt_ctx* c, int S_t, bool upload) {
     groups.clear();
     lay.clear();
     list.clear();
-    max_cols = max_nodes = dig_grp = dig_words = 0;
+    max_cols = max_nodes = dig_grp = 0;
     int s0 = 0;
     while (s0 < c->n_sub) {
       int s1 = s0, cols = 0, nodes = 0;
@@ -612,14 +616,7 @@ bool batch_configure(emt_ctx* c, int S_t, bool upload) {
         dbytes = d2;
         ++s1;
       }
-      if (dig && s1 > s0) {
-        int words = 0;
-        for (int s = s0; s < s1; ++s)
-          if (c->dig_ptr[s + 1] > c->dig_ptr[s])
-            words += dig_table_words(c->subs[s].n + c->subs[s].n_str, 16 * ((S_t + 15) / 16));
-        dig_words = std::max(dig_words, words);
-        dig_grp = std::max(dig_grp, s1 - s0);
-      }
+      if (dig && s1 > s0) dig_grp = std::max(dig_grp, s1 - s0);
       if (s1 == s0) return false;
       const SubDev& a = c->subs[s0];
       const SubDev& b = c->subs[s1 - 1];
@@ -668,10 +665,11 @@ bool batch_configure(emt_ctx* c, int S_t, bool upload) {
       s0 = s1;
     }
     const size_t total = batch_smem_bytes(S_t, (int)c->n_sources, c->n_sub, max_cols, max_nodes,
-                                          dig ? std::max(dig_words, 1) : 0, dig_grp);
-    if (total <= 227 * 1024) break;
-    if (!dig || attempt >= 8 || total - 227 * 1024 >= budget) return false;
-    budget -= total - 227 * 1024;
+                                          dig, dig_grp);
+    const size_t limit = 227 * 1024 - (dig ? kBatchDigitStaticSmem : 0);
+    if (total <= limit) break;
+    if (!dig || attempt >= 8 || total - limit >= budget) return false;
+    budget -= total - limit;
   }
   if (!upload) return true;
   if (c->d_grp) {
@@ -693,7 +691,7 @@ bool batch_configure(emt_ctx* c, int S_t, bool upload) {
   c->max_cols = std::max(max_cols, 1);
   c->max_nodes = std::max(max_nodes, 1);
   c->S_t = S_t;
-  c->dig_words = dig ? std::max(dig_words, 1) : 0;
+  c->dig_on = dig;
   c->dig_grp = dig_grp;
   return true;
 }
@@ -889,6 +887,7 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
     c->b_sub_nc.push_back(nc);
     if (col + nc > INT32_MAX / 2) return "too many solve columns";
     c->b_sub_col_off.push_back((int32_t)col);
+    c->b_col_sub.insert(c->b_col_sub.end(), (size_t)nc, (int32_t)q);
     const int ie_base = sd.n_lc + sd.n_sb;
     for (int k = 0; k < sd.n; ++k) {
       c->b_col_code.push_back(sd.node_off + k);
@@ -987,7 +986,7 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
         c->dig_mat_goff.push_back(c->epochs[e].ginv_off);
         c->dig_mat_n.push_back(sd.n);
         c->dig_mat_nc.push_back(sd.n + sd.n_str);
-        doff += (dig_matrix_words(sd.n, sd.n + sd.n_str) + 3) & ~(int64_t)3;   // 16-byte aligned fragments
+        doff += (dig_matrix_words(sd.n + sd.n_str) + 3) & ~(int64_t)3;   // 16-byte aligned chunks
       }
       c->dig_ptr.push_back((int32_t)c->dig_key.size());
       c->dig_sub_n.push_back(sd.n);
@@ -2134,6 +2133,7 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   }
   if (c->batched) {
     UP(d_col_code, b_col_code)
+    UP(d_col_sub, b_col_sub)
     UP(d_node_sub, b_node_sub)
     UP(d_node_r, b_node_r)
     UP(d_sub_nc, b_sub_nc)
@@ -2412,6 +2412,7 @@ static cudaError_t batch_launch(emt_ctx* c, int64_t n0, int64_t n_steps, cudaStr
   b.ginv = c->d_ginv;
   b.ginv_lo = c->d_ginv_lo;
   b.col_code = c->d_col_code;
+  b.col_sub = c->d_col_sub;
   b.node_sub = c->d_node_sub;
   b.node_r = c->d_node_r;
   b.sub_nc = c->d_sub_nc;
@@ -2481,15 +2482,15 @@ static cudaError_t batch_launch(emt_ctx* c, int64_t n0, int64_t n_steps, cudaStr
   b.bnd.h = c->n_lc_total * c->S;
   b.bnd.ginv = c->ginv_len;
   b.bnd.rec = record ? c->rec_rows * c->S * (int64_t)c->rec_channels.size() : 0;
-  if (c->use_digit && c->dig_words > 0) {
+  if (c->use_digit && c->dig_on) {
     b.dig = c->d_dig;
     b.dig_ptr = c->d_dig_ptr;
     b.dig_key = c->d_dig_key;
     b.dig_val = c->d_dig_val;
     b.sub_node0 = c->d_sub_node0;
     b.sub_n = c->d_sub_n;
-    b.dig_words = c->dig_words;
     b.dig_grp = std::max(c->dig_grp, 1);
+    b.dig_min_rows = c->dig_min_rows;
   }
   return launch_batch(b, c->batch_threads, st, c->use_graph ? &c->graph : nullptr);
 }
@@ -2700,6 +2701,10 @@ extern "C" emt_status emt_sync(emt_ctx* c, int32_t* info) {
   if (h[0] == kErrNoSegments)
     return c->fail(EMT_ESTATE, "the nonlinear resistors of subsystem " + std::to_string(h[1]) +
                                    " found no consistent segments at step " + std::to_string(h[3]));
+  if (h[0] == kErrTensorWait)
+    return c->fail(EMT_ESTATE, std::string("tensor-core solve of subsystem ") + std::to_string(h[1]) + " at step " +
+                                   std::to_string(h[3]) + ": the wait for its " +
+                                   (h[2] == 0 ? "staged digit planes" : "products") + " ran out of time");
   if (h[0] == EMT_ESINGULAR)
     return c->fail(EMT_ESINGULAR, "conductance matrix of subsystem " + std::to_string(h[1]) + " in switch epoch " +
                                       std::to_string(h[3]) + ", runtime-switch state word " + std::to_string(h[2]) +
@@ -2907,10 +2912,17 @@ extern "C" emt_status emt_autotune(emt_ctx* c, int64_t trial_steps, void* stream
   cudaEventCreate(&e1);
   float best_ms = 1e30f;
   int best_st = c->S_t, best_th = c->batch_threads;
+  bool best_digit = c->use_digit;
+  // the solve form: the one set by digit_solve, else both (FP64, and the digit form when a matrix qualifies)
+  std::vector<bool> forms{c->use_digit};
+  if (c->digit_auto && !c->dig_key.empty()) forms = {false, true};
+  for (bool form : forms)
   for (int St : cand) {
+    c->use_digit = form;
     if (!batch_configure(c, St, true)) continue;
     for (int th : threads) {
-      if (th > batch_max_threads(c->use_digit && c->dig_words > 0)) continue;
+      const bool dg = c->use_digit && c->dig_on;
+      if (th > batch_max_threads(dg) || th < batch_min_threads(dg)) continue;
       c->batch_threads = th;
       emt_status rs = emt_reset(c);
       if (rs != EMT_OK) return rs;
@@ -2929,11 +2941,13 @@ extern "C" emt_status emt_autotune(emt_ctx* c, int64_t trial_steps, void* stream
         best_ms = ms;
         best_st = St;
         best_th = th;
+        best_digit = form;
       }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  c->use_digit = best_digit;
   if (!batch_configure(c, best_st, true)) return c->fail(EMT_ERESOURCE, "emt_autotune: no launch shape fits");
   c->batch_threads = best_th;
   c->tuned = true;
@@ -2955,9 +2969,11 @@ extern "C" emt_status emt_set_option(emt_ctx* c, const char* key, int64_t value)
   if (k == "scenarios_per_cta" || k == "batch_threads") {
     if (!c->batched) return c->fail(EMT_EINVAL, k + " applies to a context built with a scenario set");
     if (k == "batch_threads") {
-      const int most = batch_max_threads(c->use_digit && c->dig_words > 0);
-      if (value < 32 || value > most || value % 32)
-        return c->fail(EMT_EINVAL, "batch_threads must be a multiple of 32 in [32, " + std::to_string(most) + "]");
+      const bool dg = c->use_digit && c->dig_on;
+      const int most = batch_max_threads(dg), fewest = batch_min_threads(dg);
+      if (value < fewest || value > most || value % 32)
+        return c->fail(EMT_EINVAL, "batch_threads must be a multiple of 32 in [" + std::to_string(fewest) + ", " +
+                                       std::to_string(most) + "]");
       c->batch_threads = (int)value;
       return EMT_OK;
     }
@@ -2977,13 +2993,23 @@ extern "C" emt_status emt_set_option(emt_ctx* c, const char* key, int64_t value)
     if (!c->batched) return c->fail(EMT_EINVAL, "digit_solve applies to a context built with a scenario set");
     cudaDeviceSynchronize();
     c->use_digit = value != 0;
-    if (c->use_digit) c->batch_threads = std::min(c->batch_threads, batch_max_threads(true));
+    c->digit_auto = false;   // (the autotuner keeps the form set here)
+    if (c->use_digit)
+      c->batch_threads = std::max(std::min(c->batch_threads, batch_max_threads(true)), batch_min_threads(true));
     if (!batch_configure(c, c->S_t, true)) {
       c->use_digit = false;
       batch_configure(c, c->S_t, true);
-      return c->fail(EMT_EINVAL, "digit_solve: the digit table does not fit next to scenarios_per_cta " +
-                                     std::to_string(c->S_t));
+      return c->fail(EMT_EINVAL, "digit_solve: scenarios_per_cta " + std::to_string(c->S_t) +
+                                     " is above 32, or the digit planes and table do not fit in shared memory "
+                                     "beside it");
     }
+    c->tuned = false;
+    return EMT_OK;
+  }
+  if (k == "digit_min_rows") {   // the digit form takes subsystems of at least this many rows (default 24)
+    if (value < 1 || value > kDigRows)
+      return c->fail(EMT_EINVAL, "digit_min_rows must be in [1, " + std::to_string(kDigRows) + "]");
+    c->dig_min_rows = (int)value;
     c->tuned = false;
     return EMT_OK;
   }
@@ -3053,8 +3079,9 @@ extern "C" emt_status emt_get_info(const emt_ctx* c, const char* key, int64_t* v
   else if (k == "shard_window") *value = c->sharded ? c->shard_window : 0;
   else if (k == "shard_ctas") *value = c->sharded ? (int64_t)c->shard_active.size() : c->n_sub;
   else if (k == "state_space") *value = state_space_runs(c) ? 1 : 0;
-  else if (k == "digit_solve") *value = c->batched && c->use_digit && c->dig_words > 0 ? 1 : 0;
+  else if (k == "digit_solve") *value = c->batched && c->use_digit && c->dig_on ? 1 : 0;
   else if (k == "digit_matrices") *value = (int64_t)c->dig_key.size();
+  else if (k == "digit_min_rows") *value = c->dig_min_rows;
   else if (k == "warp_per_subsystem") *value = c->small_ok && c->use_small ? 1 : 0;
   else if (k == "lazy_subsystems") {   // subsystems whose switch states are factorised at run time
     int64_t m = 0;

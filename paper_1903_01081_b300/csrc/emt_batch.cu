@@ -35,27 +35,142 @@ namespace emt {
 namespace {
 
 constexpr int kBatchMaxThreads = 1024;
-// the digit-form instance takes at most 512 threads (128 registers each: its
-// tensor-core loop keeps two accumulator chains and the 64-bit sums live)
-constexpr int kBatchDigitThreads = 512;
+// the digit-form instance: at least four warps (one per TMEM lane quarter)
+constexpr int kBatchDigitMinThreads = 128;
 
 // ---------------------------------------------------------------- digit form
 //
 // For a subsystem whose solve matrix X every scenario of the tile shares,
 // process 4 over the tile, V = X [i^(1) .. i^(S_t)], is a dense product; it
-// runs exactly on the bf16 tensor cores in the digit form of emt_digits.cuh
+// runs exactly on the tensor cores in the digit form of emt_digits.cuh
 // (62-bit fixed point, balanced base-256 digits, exact fp32 sums of digit
-// products, one rounding to double).  mma.m16n8k16 with M = 16 scenarios
-// (the injection digits b, from a shared-memory table), N = 8 rows of X
-// (its digits a, prepared once per matrix), K = 16 solve columns; the
-// pairs with a + b = u go to one fp32 accumulator (at most 8 pairs of 64
-// columns: below 2^23, exact), turned into integers per u.
+// products, one rounding to double), with tcgen05.mma (bf16 x bf16 -> f32,
+// accumulators in tensor memory), per chunk of up to 64 columns of X:
+//
+//   A (M = 128 rows, K-major) = digit planes 2p (rows 0..63) and 2p + 1
+//     (rows 64..127) of X, rows past n zero, one operand per pair p;
+//   B (N rows, K-major) = the injection digit table, row (b, sc) = digit b
+//     of scenario sc's injection (TS rows per digit plane b, TS = 16 or 32);
+//   D (lane, column (s - 5) TS + sc) = the sum over the pairs of the MMAs
+//     into block s of X_a[row] . I_b[sc] with a + b = s (upper 64 lanes,
+//     even a) or a + b = s + 1 (lower 64 lanes, odd a).
+//
+// For pair p the B operand starts at table plane s0 - 2p, so the N blocks of
+// one MMA are the injection planes b = s - 2p of consecutive blocks s, and
+// one accumulator of 9 TS columns (s = 5 .. 13) collects every digit pair
+// with a + b >= 6 (the pairs the digit form keeps, and a few dropped ones
+// that land in lanes and blocks nobody reads): 4 MMAs per 16 columns of X.
+// Each accumulator entry sums at most 4 pairs x 128 columns of products
+// below 2^14: exact in fp32.  A lane's groups are turned into an exact
+// integer partial sum; the even-plane and odd-plane lanes of a row swap
+// their partials through shared memory and each finishes half the columns
+// with one rounding.  The X planes come into shared memory by one bulk copy
+// (TMA engine) per chunk, issued as soon as the previous products are done;
+// the MMAs are issued by one thread and signal an mbarrier.
 
-__device__ __forceinline__ void dg_mma(float* d, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
-                                       unsigned b1) {
-  asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+// Every wait of this phase has a time budget; past it the kernel latches
+// {kErrTensorWait, subsystem, what, step} and leaves (reported by emt_sync).
+constexpr unsigned long long kTensorWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor of tcgen05.mma, K-major without swizzle:
+// start address, lbo = bytes between the two 8-column halves of a
+// 16-column K slice, sbo = bytes between consecutive 8-row groups, the
+// descriptor version 1 (bits 46-47), layout 0 (no swizzle).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: f32 accumulator (bits 4-5 = 1), bf16
+// A and B (bits 7-9, 10-12 = 1), both K-major, N / 8 at bit 17, M / 16 at
+// bit 24.
+__device__ __forceinline__ uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, int acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// the MMAs issued so far by this thread arrive on the mbarrier when done
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tc_ld2(uint32_t taddr, uint32_t& a, uint32_t& b) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(a), "=r"(b) : "r"(taddr) : "memory");
+}
+
+__device__ __forceinline__ void tc_ld4(uint32_t taddr, uint32_t& a, uint32_t& b, uint32_t& c, uint32_t& d) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(a), "=r"(b), "=r"(c), "=r"(d)
+               : "r"(taddr)
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Bounded wait for the mbarrier's phase `parity` to complete.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned spins = 0;; ++spins) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((spins & 15u) == 15u && global_ns() - t0 > kTensorWaitNs) return false;
+  }
+}
+
+// One bulk copy global -> shared (16-byte aligned, a multiple of 16 bytes)
+// completing on the mbarrier, which expects that many bytes.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+// Exact integer value of an fp32 accumulator entry (an integer, |x| <= 2^24):
+// 1.5 2^23 + x has a unit last place for |x| < 2^22 (one add on the FP32
+// pipe); the rare larger ones take the conversion instruction.
+__device__ __forceinline__ int acc_int(uint32_t bits) {
+  const float x = __uint_as_float(bits);
+  if (fabsf(x) < 4194304.0f) return __float_as_int(x + 12582912.0f) - 0x4B400000;
+  return __float2int_rn(x);
+}
+
+// bf16 pair (digit of n0' in the low half, of n1' in the high half) of the
+// byte `sel` of w0 and w1 (32-bit halves of N' = N + kDigitBias), as
+// dg_digit_bf16: the byte u, exact in float as (2^23 + u) - (2^23 + 128),
+// keeps all its bits in the high half of the float.
+__device__ __forceinline__ uint32_t digit_pair(uint32_t w0, uint32_t w1, int sel) {
+  const uint32_t s = 0x7540u | (uint32_t)sel;   // bytes: u, 0, 0, 0x4B
+  const float f0 = __uint_as_float(__byte_perm(w0, 0x4B000000u, s)) - 8388736.0f;
+  const float f1 = __uint_as_float(__byte_perm(w1, 0x4B000000u, s)) - 8388736.0f;
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
+}
+
+// c + a b as one 64-bit multiply-add of 32-bit signed operands
+__device__ __forceinline__ long long mad_wide(int a, int b, long long c) {
+  long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
 }
 
 __device__ __forceinline__ long long dg_shl64(int x, int sh) {
@@ -63,43 +178,55 @@ __device__ __forceinline__ long long dg_shl64(int x, int sh) {
 }
 
 // One CTA per matrix: each row as 62-bit fixed point against its own scale
-// (X_hi + X_lo), split into digits, written in the B-fragment order
-// (dig_matrix_words), then the row exponents.  Padding stays zero.
+// (X_hi + X_lo), split into digits, written in the chunked operand layout of
+// the digit matrices (dig_matrix_words), then the row exponents.  Padding
+// rows and columns get zero digits.
 __global__ void __launch_bounds__(256) batch_digits_kernel(const double* ginv, const float* ginv_lo,
                                                            const int64_t* mat_goff, const int32_t* mat_n,
                                                            const int32_t* mat_nc, const int64_t* mat_doff,
                                                            uint32_t* dig) {
   __shared__ unsigned s_em[kDigRows];
   const int mi = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
-  const int n = mat_n[mi], nc = mat_nc[mi], r8n = (n + 7) / 8, ks = (nc + 15) / 16;
+  const int n = mat_n[mi], nc = mat_nc[mi], kp = dig_cols_pad(nc);
   const double* xh = ginv + mat_goff[mi];
   const float* xl = ginv_lo + mat_goff[mi];
   uint32_t* out = dig + mat_doff[mi];
-  int* ex = reinterpret_cast<int*>(out + (int64_t)8 * r8n * ks * 64);
-  for (int r = tid; r < 8 * r8n; r += T) {
+  int* ex = reinterpret_cast<int*>(out + dig_planes_bytes(nc) / 4);
+  for (int r = tid; r < kDigRows; r += T) {
     unsigned em = 1;
     for (int k = 0; r < n && k < nc; ++k)
       em = max(em, max(dg_expo(xh[r * nc + k]), dg_expo((double)xl[r * nc + k])));
-    if (r < n) s_em[r] = em;
+    s_em[r] = em;
     ex[r] = (int)em;
   }
   __syncthreads();
   unsigned short* o16 = reinterpret_cast<unsigned short*>(out);
-  for (int idx = tid; idx < n * nc; idx += T) {
-    const int r = idx / nc, k = idx - r * nc;
-    const long long np = dg_fixed(xh[idx], s_em[r]) + dg_fixed((double)xl[idx], s_em[r]) + kDigitBias;
-    const int R8 = r >> 3, g = r & 7, st = k >> 4, kk = k & 15, t = (kk & 7) >> 1, half = kk >> 3, el = kk & 1;
-    for (int a = 0; a < kDigits; ++a) {
-      const int64_t word = ((int64_t)(a * r8n + R8) * ks + st) * 64 + 2 * (4 * g + t) + half;
-      o16[2 * word + el] = (unsigned short)dg_digit_bf16(np, a);
-    }
+  for (int idx = tid; idx < kDigRows * kp; idx += T) {
+    const int r = idx / kp, k = idx - r * kp;
+    long long np = kDigitBias;
+    if (r < n && k < nc) np += dg_fixed(xh[r * nc + k], s_em[r]) + dg_fixed((double)xl[r * nc + k], s_em[r]);
+    const int c = k / kDigChunk, kc = dig_chunk_cols(kp, c), kk = k - kDigChunk * c;
+    // chunk c, then plane a of 64 rows x kc columns in 8 x 8 core matrices
+    const int64_t el = (int64_t)c * (kDigChunkBytes / 2) + (int64_t)((r >> 3) * (kc >> 3) + (kk >> 3)) * 64 +
+                       (r & 7) * 8 + (kk & 7);
+    for (int a = 0; a < kDigits; ++a) o16[el + (int64_t)a * kDigRows * kc] = (unsigned short)dg_digit_bf16(np, a);
   }
 }
 
 // Ring slot of step `step` in a ring of depth d1 (steps stay below 2^31).
 __device__ __forceinline__ int64_t ring_slot(long long step, int d1) { return (int64_t)((unsigned)step % (unsigned)d1); }
 
+// v_src(t_n) of source src in scenario sg from the step's sin/cos pair of
+// its frequency (wsc): (A cos phase) sin(omega t) + (A sin phase) cos(omega t)
+__device__ __forceinline__ double source_value(const BatchParams& P, int src, int sg, const double* wsc) {
+  const int64_t q = (int64_t)sg * P.n_sources + src;
+  return fma(__ldg(P.src_ac + q), wsc[2 * src], __ldg(P.src_as + q) * wsc[2 * src + 1]);
+}
+
 // Signed value of one batched injection entry for scenario sg (tile lane sl).
+// kTab: source voltages from the tile's table vs [n_sources][S_t]; else
+// formed from the sin/cos pairs in vs (the digit-form instance keeps no table).
+template <bool kTab>
 __device__ __forceinline__ double entry_value(const BatchParams& P, uint32_t raw, int sg, int sl, long long step,
                                               const double* vs) {
   const uint32_t kind = (raw >> kBentKindShift) & 7u;
@@ -115,7 +242,7 @@ __device__ __forceinline__ double entry_value(const BatchParams& P, uint32_t raw
   } else if (kind == 0u) {
     val = P.h[EMT_CHK(P.err, (int64_t)idx * P.S + sg, P.bnd.h, kChkHistory)];
   } else if (kind == 1u) {
-    val = __ldg(P.sb_g + idx) * vs[__ldg(P.sb_src + idx) * P.S_t + sl];
+    val = __ldg(P.sb_g + idx) * (kTab ? vs[__ldg(P.sb_src + idx) * P.S_t + sl] : source_value(P, __ldg(P.sb_src + idx), sg, vs));
     if (P.keep_sb && !P.keep_sb[(int64_t)idx * P.S + sg]) val = 0.0;
   } else {
     val = P.ring[EMT_CHK(P.err, (__ldg(P.le_bring + idx) + ring_slot(step, __ldg(P.le_d1 + idx))) * P.S + sg,
@@ -334,7 +461,7 @@ __device__ __forceinline__ void batch_rs_decide(const BatchParams& P, long long*
 // kDigit: the instance with the digit-form solve (P.dig set); the other keeps
 // the FP64 kernel's registers free of it
 template <bool kDigit>
-__global__ void __launch_bounds__(kDigit ? kBatchDigitThreads : kBatchMaxThreads, 1) batch_kernel(BatchParams P) {
+__global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int St = P.S_t;
   const int sigma0 = blockIdx.x * St;
@@ -344,20 +471,53 @@ __global__ void __launch_bounds__(kDigit ? kBatchDigitThreads : kBatchMaxThreads
   // item x = tid + i T of a phase is (x / St, x % St); both advance by
   // (T / St, T % St) per iteration, so no phase loop divides
   const int q0 = tid / St, r0 = tid - q0 * St, dq = T / St, dr = T - dq * St;
-  double* vs = reinterpret_cast<double*>(smem_raw);                      // [n_sources][St]
-  long long* cur = reinterpret_cast<long long*>(vs + (size_t)P.n_sources * St);   // [St][n_sub] matrix offsets
+  double* vs = reinterpret_cast<double*>(smem_raw);   // [n_sources][St] (none in the digit-form instance)
+  long long* cur = reinterpret_cast<long long*>(vs + (kDigit ? 0 : (size_t)P.n_sources * St));   // [St][n_sub] offsets
   long long* evn = cur + (size_t)St * n_sub;                             // [St] next selection event
   double* iv = reinterpret_cast<double*>(evn + St);                      // [max_cols][St]
   double* vv = iv + (size_t)P.max_cols * St;                             // [max_nodes][St]
   float* ivf = reinterpret_cast<float*>(vv + (size_t)P.max_nodes * St);  // [max_cols][St]
   double* wsc = reinterpret_cast<double*>(ivf + (((size_t)P.max_cols * St + 1) & ~(size_t)1));   // [n_sources][2]
-  // digit form: per subsystem of the group its digit matrix (or -1), the
-  // injection exponents of a batch [dig_grp][TS], the digit table
-  const int TS = 16 * ((St + 15) / 16);
+  // digit form: per subsystem of the group its digit matrix (or -1) and
+  // {rows, columns, first column in the group, first node}, the injection
+  // exponents of the tile [TS], then (128-byte aligned) one staged chunk of
+  // digit planes and the chunk's injection digit table (also the scratch of
+  // the accumulator read-back)
+  const int TS = dig_tile_rows(St);
   long long* dsel = reinterpret_cast<long long*>(wsc + 2 * (size_t)P.n_sources);   // [dig_grp]
-  int* dem = reinterpret_cast<int*>(dsel + P.dig_grp);
-  uint32_t* dtab = reinterpret_cast<uint32_t*>(
-      (reinterpret_cast<uintptr_t>(dem + (P.dig != nullptr ? P.dig_grp * TS : 0)) + 15) & ~(uintptr_t)15);
+  int4* dmeta = reinterpret_cast<int4*>((reinterpret_cast<uintptr_t>(dsel + P.dig_grp) + 15) & ~(uintptr_t)15);
+  // injection exponents [dig_grp][kDigMaxTile]: the largest biased exponent of each subsystem's
+  // injections per scenario, gathered by the injection phase (atomicMax), cleared after the digit phase
+  int* dexp = reinterpret_cast<int*>(dmeta + P.dig_grp);
+  unsigned char* dA = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(dexp + (kDigit ? P.dig_grp * kDigMaxTile : 0)) + 127) & ~(uintptr_t)127);
+  unsigned char* dB = dA + (kDigit ? kDigChunkBytes : 0);
+  __shared__ __align__(8) unsigned long long s_mbar[2];   // [0]: digit planes landed, [1]: products done
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int warp = tid >> 5, lane = tid & 31;
+  // tensor memory: 9 TS accumulator columns (a power of two >= 32 is allocated)
+  const uint32_t tmem_cols = 9 * TS > 256 ? 512u : 256u;
+  uint32_t par_a = 0, par_m = 0;   // mbarrier phases (par_a: thread 0 only)
+  int pending_a = -1;              // thread 0: the group-local subsystem whose planes are being loaded
+  bool mma_stuck = false;          // products committed whose completion was not seen
+  if (kDigit) {
+    if (tid == 0) {
+      s_abort = 0;
+      mbar_init(smem_addr(&s_mbar[0]));
+      mbar_init(smem_addr(&s_mbar[1]));
+    }
+    for (int x = tid; x < P.dig_grp * kDigMaxTile; x += T) dexp[x] = 0;
+    if (warp == 0) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&s_tmem)),
+                   "r"(tmem_cols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
 
   // solve matrices in force at the first step
   for (int sl = tid; sl < n_here; sl += T) {
@@ -371,6 +531,7 @@ __global__ void __launch_bounds__(kDigit ? kBatchDigitThreads : kBatchMaxThreads
   const int decim = P.rec_decim > 0 ? P.rec_decim : 1;
   const long long n_end = P.n0 + P.n_steps;
   for (long long step = P.n0; step < n_end; ++step) {
+    if (kDigit && s_abort) break;
     const double t = (double)step * P.dt;
     // switch events of this step
     for (int sl = tid; sl < n_here; sl += T) {
@@ -392,21 +553,24 @@ __global__ void __launch_bounds__(kDigit ? kBatchDigitThreads : kBatchMaxThreads
       wsc[2 * x + 1] = cs;
     }
     __syncthreads();
-    for (int x = tid, src = q0, sl = r0; x < P.n_sources * St; x += T, src += dq, sl += dr) {
-      if (sl >= St) {
-        sl -= St;
-        ++src;
+    if (!kDigit) {   // (the digit-form instance forms each source value where it is used)
+      for (int x = tid, src = q0, sl = r0; x < P.n_sources * St; x += T, src += dq, sl += dr) {
+        if (sl >= St) {
+          sl -= St;
+          ++src;
+        }
+        if (sl < n_here) {
+          const int64_t q = (int64_t)(sigma0 + sl) * P.n_sources + src;
+          vs[x] = fma(__ldg(P.src_ac + q), wsc[2 * src], __ldg(P.src_as + q) * wsc[2 * src + 1]);
+        }
       }
-      if (sl < n_here) {
-        const int64_t q = (int64_t)(sigma0 + sl) * P.n_sources + src;
-        vs[x] = fma(__ldg(P.src_ac + q), wsc[2 * src], __ldg(P.src_as + q) * wsc[2 * src + 1]);
-      }
+      __syncthreads();
     }
-    __syncthreads();
     const bool rec_now = P.rec != nullptr && step % decim == 0 && step / decim - 1 < P.rec_rows;
     const long long rec_row = step / decim - 1;
 
     for (int g = 0; g < P.n_groups; ++g) {
+      if (kDigit && s_abort) break;
       const BatchGroupDev G = P.grp[g];
 
       // frequency-dependent ends: W(n) interpolated from the far end's w of
@@ -440,13 +604,16 @@ __global__ void __launch_bounds__(kDigit ? kBatchDigitThreads : kBatchMaxThreads
         double acc = 0.0;
         if (code >= 0) {
           const int e0 = __ldg(P.ent_ptr + code), e1 = __ldg(P.ent_ptr + code + 1);
-          if (e0 < e1) acc = entry_value(P, (uint32_t)__ldg(P.bent + e0), sg, sl, step, vs);
-          for (int e = e0 + 1; e < e1; ++e) acc += entry_value(P, (uint32_t)__ldg(P.bent + e), sg, sl, step, vs);
+          if (e0 < e1) acc = entry_value<!kDigit>(P, (uint32_t)__ldg(P.bent + e0), sg, sl, step, kDigit ? wsc : vs);
+          for (int e = e0 + 1; e < e1; ++e)
+            acc += entry_value<!kDigit>(P, (uint32_t)__ldg(P.bent + e), sg, sl, step, kDigit ? wsc : vs);
         } else {
           acc = -P.h[EMT_CHK(P.err, (int64_t)(-1 - code) * S + sg, P.bnd.h, kChkHistory)];
         }
         iv[x] = acc;
         ivf[x] = f32_trunc(acc);
+        if (kDigit)   // the subsystem's injection exponent for this scenario (digit form)
+          atomicMax(dexp + (__ldg(P.col_sub + G.col0 + c) - G.sub0) * kDigMaxTile + sl, (int)dg_expo(acc));
       }
       // digit form: a subsystem whose matrix the whole tile shares, and that
       // matrix in digit form
@@ -457,10 +624,12 @@ __global__ void __launch_bounds__(kDigit ? kBatchDigitThreads : kBatchMaxThreads
           bool same = true;
           for (int sl = 1; sl < n_here && same; ++sl) same = cur[(size_t)sl * n_sub + s] == c0;
           long long d = -1;
-          if (same)
+          if (same && __ldg(P.sub_n + s) >= P.dig_min_rows)
             for (int x = __ldg(P.dig_ptr + s); x < __ldg(P.dig_ptr + s + 1); ++x)
               if (__ldg(P.dig_key + x) == c0) d = __ldg(P.dig_val + x);
           dsel[j] = d;
+          dmeta[j] = make_int4(__ldg(P.sub_n + s), __ldg(P.sub_nc + s), __ldg(P.sub_col_off + s) - G.col0,
+                               __ldg(P.sub_node0 + s));
         }
       __syncthreads();
 
@@ -511,125 +680,209 @@ __global__ void __launch_bounds__(kDigit ? kBatchDigitThreads : kBatchMaxThreads
           if (pos >= 0) P.rec[EMT_CHK(P.err, (rec_row * S + sigma0 + sl) * P.n_rec + pos, P.bnd.rec, kChkRecord)] = v;
         }
       }
-      // the digit-form subsystems, in batches whose injection digits fit the table
+      // the digit-form subsystems, one after another on the tensor cores
       if (kDigit) {
-        const int warp = tid >> 5, lane = tid & 31, n_warps = T >> 5, g = lane >> 2, t = lane & 3;
-        for (int jb0 = 0; jb0 < G.sub1 - G.sub0;) {
-          // the batch [jb0, jb1): the digit subsystems whose tables fit dig_words (all of the group's, as sized)
-          int jb1 = jb0, used = 0, cnt = 0;
-          for (; jb1 < G.sub1 - G.sub0; ++jb1) {
-            if (dsel[jb1] < 0) continue;
-            const int w = dig_table_words(__ldg(P.sub_nc + G.sub0 + jb1), TS);
-            if (used + w > P.dig_words) break;
-            used += w;
-            ++cnt;
-          }
-          if (cnt == 0) {   // (every digit subsystem's table fits by construction; a step past one never loops)
-            jb0 = jb1 + (jb1 < G.sub1 - G.sub0 ? 1 : 0);
-            continue;
-          }
-          // injection digits: a warp per (subsystem, scenario): its scale (largest exponent), then the table
-          for (int it = warp; it < cnt * n_here; it += n_warps) {
-            int jj = it / n_here, sl = it - jj * n_here, j = jb0, off = 0;
-            for (;; ++j) {   // the jj-th digit subsystem of the batch, and its table offset
-              if (dsel[j] < 0) continue;
-              if (jj == 0) break;
-              off += dig_table_words(__ldg(P.sub_nc + G.sub0 + j), TS);
-              --jj;
+        const int nwq = (T >> 5) >> 2, q = warp & 3, wj = warp >> 2;   // warps per TMEM lane quarter
+        const int cpw = TS / nwq;                                      // scenario columns per warp (>= 2)
+        const int n_g = G.sub1 - G.sub0;
+        for (int j = 0; j < n_g; ++j) {
+          if (dsel[j] < 0) continue;
+          const int4 md = dmeta[j];   // rows, columns, first column in the group, first node
+          const int s = G.sub0 + j, n = md.x, nc = md.y, kp = dig_cols_pad(nc);
+          const int n_chunks = (kp + kDigChunk - 1) / kDigChunk;
+          const unsigned char* dm = reinterpret_cast<const unsigned char*>(P.dig + dsel[j]);
+          const double* ivc = iv + (size_t)md.z * St;
+          const int* dem = dexp + j * kDigMaxTile;   // this subsystem's injection exponents
+          bool done = true;
+          for (int c = 0; c < n_chunks; ++c) {
+            const int kc = dig_chunk_cols(kp, c);
+            // this chunk's planes (unless asked for when the last products finished)
+            if (tid == 0 && pending_a != 4 * j + c) {
+              bulk_load(smem_addr(dA), dm + (size_t)c * kDigChunkBytes, (uint32_t)(16 * kDigRows * kc),
+                        smem_addr(&s_mbar[0]));
+              pending_a = 4 * j + c;
             }
-            const int s = G.sub0 + j, nc = __ldg(P.sub_nc + s), ks = (nc + 15) >> 4, sw = 8 * ks + 4;
-            const double* ivc = iv + (size_t)(__ldg(P.sub_col_off + s) - G.col0) * St + sl;
-            unsigned em = 1;
-            for (int k = lane; k < nc; k += 32) em = max(em, dg_expo(ivc[(size_t)k * St]));
-            em = max(__reduce_max_sync(0xffffffffu, em), 1u);
-            uint32_t* tab = dtab + off;
-            for (int kw = lane; kw < 8 * ks; kw += 32) {
-              const int k = 2 * kw;
-              const double x0 = k < nc ? ivc[(size_t)k * St] : 0.0, x1 = k + 1 < nc ? ivc[(size_t)(k + 1) * St] : 0.0;
-              const long long n0 = dg_fixed(x0, em) + kDigitBias, n1 = dg_fixed(x1, em) + kDigitBias;
+            // the digit table of the chunk: a warp writes one 128-byte row of core matrices (8
+            // scenarios x 8 columns), a lane two columns of one scenario
+            for (int x = tid; x < TS * (kc >> 1); x += T) {
+              const int rest = x >> 5, kblk = rest % (kc >> 3);
+              const int sc = 8 * (rest / (kc >> 3)) + ((x >> 2) & 7), k2 = 8 * kblk + 2 * (x & 3);
+              const int k = kDigChunk * c + k2;
+              long long n0 = kDigitBias, n1 = kDigitBias;
+              if (sc < n_here) {
+                const unsigned em = (unsigned)max(dem[sc], 1);
+                if (k < nc) n0 += dg_fixed(ivc[(size_t)k * St + sc], em);
+                if (k + 1 < nc) n1 += dg_fixed(ivc[(size_t)(k + 1) * St + sc], em);
+              }
+              uint32_t* w = reinterpret_cast<uint32_t*>(
+                  dB + ((size_t)((sc >> 3) * (kc >> 3) + kblk) * 128 + (sc & 7) * 16 + (k2 & 7) * 2));
+              const size_t plane_words = (size_t)TS * kc / 2;
+              const uint32_t lo0 = (uint32_t)n0, lo1 = (uint32_t)n1;
+              const uint32_t hi0 = (uint32_t)((unsigned long long)n0 >> 32), hi1 = (uint32_t)((unsigned long long)n1 >> 32);
 #pragma unroll
-              for (int b = 0; b < kDigits; ++b)
-                tab[(b * TS + sl) * sw + kw] = dg_digit_bf16(n0, b) | (dg_digit_bf16(n1, b) << 16);
+              for (int b = 0; b < 4; ++b) w[b * plane_words] = digit_pair(lo0, lo1, b);
+#pragma unroll
+              for (int b = 4; b < 7; ++b) w[b * plane_words] = digit_pair(hi0, hi1, b - 4);
+              w[7 * plane_words] = digit_pair(hi0 ^ 0x80000000u, hi1 ^ 0x80000000u, 3);   // (the signed top digit)
             }
-            if (lane == 0) dem[it - (it / n_here) * n_here + (it / n_here) * TS] = (int)em;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+            __syncthreads();
+            // products: thread 0 waits for the planes, issues the MMAs and commits
+            if (tid == 0) {
+              tc_fence_after();
+              const bool ok = mbar_wait(smem_addr(&s_mbar[0]), par_a);
+              if (ok) {
+                par_a ^= 1u;
+                pending_a = -1;
+                const uint32_t a0 = smem_addr(dA), b0 = smem_addr(dB), sbo = (uint32_t)(kc >> 3) * 128;
+                const uint32_t pair_a = (uint32_t)(4 * kDigRows * kc), plane_b = (uint32_t)(2 * TS * kc);
+                // pair p: planes 2p (lanes 0..63) and 2p + 1 (lanes 64..127) against the injection
+                // planes b = s - 2p of the accumulator blocks s0 .. s1 (block s: TS columns from
+                // (s - 5) TS): block s holds group s in the upper lanes and group s + 1 in the lower ones
+                auto mma = [&](int kk, int p, int s0, int s1, int acc) {
+                  tc_mma(s_tmem + (uint32_t)((s0 - 5) * TS), tc_desc(a0 + p * pair_a + kk * 256, 128, sbo),
+                         tc_desc(b0 + (s0 - 2 * p) * plane_b + kk * 256, 128, sbo),
+                         tc_idesc(128, (s1 - s0 + 1) * TS), acc);
+                };
+                for (int kk = 0; kk < (kc >> 4); ++kk) {
+                  if (c == 0 && kk == 0) {   // the first products write every accumulator column
+                    mma(0, 2, 5, 11, 0);
+                    mma(0, 3, 12, 13, 0);
+                    mma(0, 3, 6, 11, 1);
+                  } else {
+                    mma(kk, 2, 5, 11, 1);
+                    mma(kk, 3, 6, 13, 1);
+                  }
+                  mma(kk, 0, 5, 7, 1);
+                  mma(kk, 1, 5, 9, 1);
+                }
+                tc_commit(smem_addr(&s_mbar[1]));
+              } else {
+                if (atomicCAS(P.err, 0, kErrTensorWait) == 0) {
+                  P.err[1] = s;
+                  P.err[2] = 0;
+                  P.err[3] = (int)step;
+                }
+                s_abort = 1;
+              }
+            }
+            __syncthreads();
+            if (s_abort) break;
+            const bool ok_m = mbar_wait(smem_addr(&s_mbar[1]), par_m);
+            if (ok_m) par_m ^= 1u;
+            else mma_stuck = true;
+            done = !__syncthreads_or(!ok_m);   // (the same verdict in every thread)
+            tc_fence_after();
+            if (!done) {
+              if (tid == 0 && atomicCAS(P.err, 0, kErrTensorWait) == 0) {
+                P.err[1] = s;
+                P.err[2] = 1;
+                P.err[3] = (int)step;
+              }
+              s_abort = 1;
+              break;
+            }
+            // the planes of the next chunk, or of the next digit subsystem, now that these are read
+            if (tid == 0 && done) {
+              if (c + 1 < n_chunks) {
+                bulk_load(smem_addr(dA), dm + (size_t)(c + 1) * kDigChunkBytes,
+                          (uint32_t)(16 * kDigRows * dig_chunk_cols(kp, c + 1)), smem_addr(&s_mbar[0]));
+                pending_a = 4 * j + c + 1;
+              } else {
+                int jn = j + 1;
+                while (jn < n_g && dsel[jn] < 0) ++jn;
+                if (jn < n_g) {
+                  bulk_load(smem_addr(dA), P.dig + dsel[jn],
+                            (uint32_t)(16 * kDigRows * dig_chunk_cols(dig_cols_pad(dmeta[jn].y), 0)),
+                            smem_addr(&s_mbar[0]));
+                  pending_a = 4 * jn;
+                }
+              }
+            }
           }
-          __syncthreads();
-          // products: a warp per (subsystem, 16 scenarios, 8 rows)
-          int n_task = 0;
-          for (int j = jb0; j < jb1; ++j)
-            if (dsel[j] >= 0) n_task += (TS / 16) * ((__ldg(P.sub_n + G.sub0 + j) + 7) >> 3);
-          for (int it = warp; it < n_task; it += n_warps) {
-            int rem = it, j = jb0, jj = 0, off = 0, ntile = 0;
-            for (;; ++j) {
-              if (dsel[j] < 0) continue;
-              ntile = (TS / 16) * ((__ldg(P.sub_n + G.sub0 + j) + 7) >> 3);
-              if (rem < ntile) break;
-              rem -= ntile;
-              off += dig_table_words(__ldg(P.sub_nc + G.sub0 + j), TS);
-              ++jj;
-            }
-            const int s = G.sub0 + j, n = __ldg(P.sub_n + s), nc = __ldg(P.sub_nc + s);
-            const int ks = (nc + 15) >> 4, sw = 8 * ks + 4, r8n = (n + 7) >> 3;
-            const int stile = rem / r8n, R8 = rem - stile * r8n;
-            const uint32_t* dm = P.dig + dsel[j];
-            const uint32_t* tab = dtab + off + (16 * stile + g) * sw + t;
-            long long ta[4] = {0, 0, 0, 0}, tb[4] = {0, 0, 0, 0};
-            for (int u = kDigitGroupLo; u <= 2 * kDigits - 2; ++u) {
-              // pairs (a, u - a) two at a time on two accumulators, so that two MMA chains are in flight
-              float e0[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f};
-              const int a_hi = min(kDigits - 1, u);
-              for (int a = max(0, u - (kDigits - 1)); a <= a_hi; a += 2) {
-                const bool two = a + 1 <= a_hi;
-                const uint32_t* tA = tab + (u - a) * TS * sw;
-                const uint32_t* tB = tab + (u - a - (two ? 1 : 0)) * TS * sw;
-                const uint2* fA = reinterpret_cast<const uint2*>(dm) + ((size_t)(a * r8n + R8) * ks) * 32 + lane;
-                const uint2* fB = fA + (size_t)r8n * ks * 32;
-                for (int st = 0; st < ks; ++st) {
-                  const uint2 bA = __ldg(fA + st * 32);
-                  dg_mma(e0, tA[8 * st], tA[8 * sw + 8 * st], tA[8 * st + 4], tA[8 * sw + 8 * st + 4], bA.x, bA.y);
-                  if (two) {
-                    const uint2 bB = __ldg(fB + st * 32);
-                    dg_mma(e1, tB[8 * st], tB[8 * sw + 8 * st], tB[8 * st + 4], tB[8 * sw + 8 * st + 4], bB.x, bB.y);
+          if (s_abort) break;
+          // V from the accumulators.  Lane quarter q holds the rows 32 (q & 1) .. + 31 of the even
+          // (q < 2) or the odd (q >= 2) digit planes; each warp takes cpw consecutive scenario columns,
+          // two at a time: each lane forms its partial sum T_half = sum over its groups of G 256^(g - 6)
+          // (as ta 2^40 + tb) for both, the upper lanes finish the first column of a pair and the lower
+          // lanes the second, after swapping partial sums through the scratch (the digit table, dead
+          // now); one rounding to double per entry.
+          {
+            const int half = q >> 1, r = 32 * (q & 1) + lane;
+            const bool act = 32 * (q & 1) < n;   // (warp-uniform)
+            longlong2* scr = reinterpret_cast<longlong2*>(dB);   // [64 rows][TS]
+            const int ex = __ldg(reinterpret_cast<const int*>(dm + dig_planes_bytes(nc)) + r);
+            const uint32_t lane_base = s_tmem + ((uint32_t)(32 * q) << 16);
+            for (int sc0 = wj * cpw; sc0 < (wj + 1) * cpw; sc0 += 4) {   // rounds of two column pairs
+              long long own_a[2] = {0, 0}, own_b[2] = {0, 0};
+              if (act) {
+                // the round's columns of the nine blocks in one batch of loads (x4: four columns, or
+                // x2 when the warp has two), one wait
+                const bool quad = sc0 + 4 <= (wj + 1) * cpw;   // (warp-uniform)
+                uint32_t xv[4][9];
+#pragma unroll
+                for (int u = 0; u < 9; ++u) {
+                  if (quad) tc_ld4(lane_base + (uint32_t)(u * TS + sc0), xv[0][u], xv[1][u], xv[2][u], xv[3][u]);
+                  else tc_ld2(lane_base + (uint32_t)(u * TS + sc0), xv[0][u], xv[1][u]);
+                }
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                  if (pr == 1 && !quad) break;
+                  const int sc = sc0 + 2 * pr;
+                  long long ta0 = 0, tb0 = 0, ta1 = 0, tb1 = 0;
+#pragma unroll
+                  for (int u = 0; u < 9; ++u) {
+                    const int g = u + 5 + half;   // the digit group of block u in these lanes
+                    if (g < kDigitGroupLo) continue;
+                    const int g0 = acc_int(xv[2 * pr][u]), g1 = acc_int(xv[2 * pr + 1][u]);
+                    if (g >= 11) {
+                      ta0 = mad_wide(g0, 1 << (8 * (g - 11)), ta0);
+                      ta1 = mad_wide(g1, 1 << (8 * (g - 11)), ta1);
+                    } else if (g < 10) {
+                      tb0 = mad_wide(g0, 1 << (8 * (g - kDigitGroupLo)), tb0);
+                      tb1 = mad_wide(g1, 1 << (8 * (g - kDigitGroupLo)), tb1);
+                    } else {   // (2^32: into the high word)
+                      tb0 += dg_shl64(g0, 32);
+                      tb1 += dg_shl64(g1, 32);
+                    }
+                  }
+                  // the column this lane finishes keeps its partial; the other one goes to the scratch
+                  own_a[pr] = half ? ta1 : ta0;
+                  own_b[pr] = half ? tb1 : tb0;
+                  scr[r * TS + sc + (half ^ 1)] = make_longlong2(half ? ta0 : ta1, half ? tb0 : tb1);
+                }
+              }
+              __syncthreads();
+              if (act) {
+#pragma unroll
+                for (int pr = 0; pr < 2; ++pr) {
+                  const int oc = sc0 + 2 * pr + half;   // the column this lane finishes
+                  if (sc0 + 2 * pr < (wj + 1) * cpw && oc < n_here && r < n) {
+                    const longlong2 o = scr[r * TS + oc];
+                    const double v = dg_to_double(own_a[pr] + o.x, own_b[pr] + o.y, ex + max(dem[oc], 1) - 2120);
+                    const int node = md.w + r;
+                    vv[(size_t)(node - G.node0) * St + oc] = v;
+                    if (rec_now) {
+                      const int pos = P.rec_pos[node];
+                      if (pos >= 0)
+                        P.rec[EMT_CHK(P.err, (rec_row * S + sigma0 + oc) * P.n_rec + pos, P.bnd.rec, kChkRecord)] = v;
+                    }
                   }
                 }
-                if (ks > 4) {   // more than 64 columns: each pair's sums leave the accumulators at once
-#pragma unroll
-                  for (int c = 0; c < 4; ++c) {
-                    const int q = dg_acc_int(e0[c]) + dg_acc_int(e1[c]);
-                    if (u >= 11) ta[c] += dg_shl64(q, 8 * (u - 11));
-                    else tb[c] += dg_shl64(q, 8 * (u - kDigitGroupLo));
-                    e0[c] = e1[c] = 0.f;
-                  }
-                }
               }
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const int q = dg_acc_int(e0[c]) + dg_acc_int(e1[c]);
-                if (u >= 11) ta[c] += dg_shl64(q, 8 * (u - 11));
-                else tb[c] += dg_shl64(q, 8 * (u - kDigitGroupLo));
-              }
-            }
-            const int* ex = reinterpret_cast<const int*>(dm + (size_t)8 * r8n * ks * 64);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              const int sl = 16 * stile + g + (c >= 2 ? 8 : 0), r = 8 * R8 + 2 * t + (c & 1);
-              if (sl < n_here && r < n) {
-                const double v = dg_to_double(ta[c], tb[c], __ldg(ex + r) + dem[jj * TS + sl] - 2120);
-                const int node = __ldg(P.sub_node0 + s) + r;
-                vv[(size_t)(node - G.node0) * St + sl] = v;
-                if (rec_now) {
-                  const int pos = P.rec_pos[node];
-                  if (pos >= 0)
-                    P.rec[EMT_CHK(P.err, (rec_row * S + sigma0 + sl) * P.n_rec + pos, P.bnd.rec, kChkRecord)] = v;
-                }
-              }
+              tc_fence_before();
+              __syncthreads();
             }
           }
-          jb0 = jb1;
-          if (jb0 < G.sub1 - G.sub0) __syncthreads();   // (the table is refilled by the next batch)
         }
       }
       __syncthreads();
+      if (kDigit) {
+        if (s_abort) break;
+        for (int x = tid; x < (G.sub1 - G.sub0) * kDigMaxTile; x += T) dexp[x] = 0;   // (read again next group)
+      }
 
       // compensation method: each nonlinear resistor against its
       // subsystem's linear solution, per scenario (its current from the
@@ -713,8 +966,12 @@ __global__ void __launch_bounds__(kDigit ? kBatchDigitThreads : kBatchMaxThreads
           const int gl = G.lc0 + it;
           if (P.keep_lc && !P.keep_lc[(int64_t)gl * S + sg]) continue;   // removed: h stays 0
           const int nk = __ldg(P.lc_nk + gl), nm = __ldg(P.lc_nm + gl);
-          const double vk = nk >= 0 ? vv[(size_t)(nk - G.node0) * St + sl] : (nk == -1 ? 0.0 : vs[(-2 - nk) * St + sl]);
-          const double vm = nm >= 0 ? vv[(size_t)(nm - G.node0) * St + sl] : (nm == -1 ? 0.0 : vs[(-2 - nm) * St + sl]);
+          const double vk = nk >= 0    ? vv[(size_t)(nk - G.node0) * St + sl]
+                            : nk == -1 ? 0.0
+                                       : (kDigit ? source_value(P, -2 - nk, sg, wsc) : vs[(-2 - nk) * St + sl]);
+          const double vm = nm >= 0    ? vv[(size_t)(nm - G.node0) * St + sl]
+                            : nm == -1 ? 0.0
+                                       : (kDigit ? source_value(P, -2 - nm, sg, wsc) : vs[(-2 - nm) * St + sl]);
           const double e = __ldg(P.lc_e + gl);
           double* hp = P.h + EMT_CHK(P.err, (int64_t)gl * S + sg, P.bnd.h, kChkHistory);
           const double hv = *hp;
@@ -738,6 +995,15 @@ __global__ void __launch_bounds__(kDigit ? kBatchDigitThreads : kBatchMaxThreads
       }
       __syncthreads();
     }
+  }
+  if (kDigit) {
+    // (after a wait that ran out: the copy or products still in flight get one more bounded wait)
+    if (tid == 0 && pending_a >= 0) mbar_wait(smem_addr(&s_mbar[0]), par_a);
+    if (tid == 0 && mma_stuck) mbar_wait(smem_addr(&s_mbar[1]), par_m);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(tmem_cols) : "memory");
   }
 }
 
@@ -782,14 +1048,20 @@ cudaError_t launch_slot_constants(const BranchDev* br, const int32_t* lc_idx, in
   return cudaGetLastError();
 }
 
-int batch_max_threads(bool digit) { return digit ? kBatchDigitThreads : kBatchMaxThreads; }
+int batch_max_threads(bool digit) {
+  (void)digit;
+  return kBatchMaxThreads;
+}
+int batch_min_threads(bool digit) { return digit ? kBatchDigitMinThreads : 32; }
 
-size_t batch_smem_bytes(int S_t, int n_sources, int n_sub, int max_cols, int max_nodes, int dig_words,
-                        int dig_grp) {
-  size_t b = (size_t)n_sources * S_t * 8 + (size_t)S_t * n_sub * 8 + (size_t)S_t * 8 + (size_t)max_nodes * S_t * 8 +
-             (((size_t)max_cols * S_t + 1) & ~(size_t)1) * 12 + (size_t)n_sources * 16;
-  if (dig_words > 0)   // digit form: dsel, the batch's exponents, 16-byte alignment, the table
-    b += (size_t)dig_grp * 8 + (size_t)dig_grp * 16 * ((S_t + 15) / 16) * 4 + 16 + (size_t)dig_words * 4;
+size_t batch_smem_bytes(int S_t, int n_sources, int n_sub, int max_cols, int max_nodes, bool digit, int dig_grp) {
+  // (the digit-form instance keeps no per-scenario source table)
+  size_t b = (digit ? 0 : (size_t)n_sources * S_t * 8) + (size_t)S_t * n_sub * 8 + (size_t)S_t * 8 +
+             (size_t)max_nodes * S_t * 8 + (((size_t)max_cols * S_t + 1) & ~(size_t)1) * 12 + (size_t)n_sources * 16;
+  if (digit)   // digit form: dsel, (16-byte aligned) dmeta and the exponents per subsystem of a group,
+               // 128-byte alignment, one chunk's planes, the chunk's digit table
+    b += (size_t)dig_grp * (24 + 4 * kDigMaxTile) + 16 + 128 + (size_t)kDigChunkBytes +
+         (size_t)dig_table_bytes(dig_tile_rows(S_t));
   return b;
 }
 
@@ -814,11 +1086,13 @@ void batch_graph_destroy(BatchGraph* g) {
 // launch goes through a CUDA graph that is built once per launch shape and
 // whose kernel node gets this call's arguments.
 cudaError_t launch_batch(const BatchParams& p, int threads, cudaStream_t st, BatchGraph* graph) {
-  const size_t smem =
-      batch_smem_bytes(p.S_t, p.n_sources, p.n_sub, p.max_cols, p.max_nodes, p.dig ? p.dig_words : 0, p.dig_grp);
-  if (smem > 227 * 1024 || threads < 32 || threads > (p.dig != nullptr ? kBatchDigitThreads : kBatchMaxThreads) ||
-      threads % 32)
+  size_t smem = batch_smem_bytes(p.S_t, p.n_sources, p.n_sub, p.max_cols, p.max_nodes, p.dig != nullptr, p.dig_grp);
+  if (smem > 227 * 1024 - (p.dig != nullptr ? kBatchDigitStaticSmem : 0) ||
+      threads < batch_min_threads(p.dig != nullptr) || threads > kBatchMaxThreads ||
+      threads % 32 || (p.dig != nullptr && p.S_t > kDigMaxTile))
     return cudaErrorInvalidValue;
+  // the digit form holds all 512 columns of tensor memory: one CTA per SM
+  if (p.dig != nullptr) smem = std::max<size_t>(smem, 116 * 1024);
   const void* fn = p.dig != nullptr ? (const void*)batch_kernel<true> : (const void*)batch_kernel<false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -154,6 +154,10 @@ constexpr int kErrNoSegments = 100;
 // Device error code of the checks build: an index outside its array
 // {kErrBounds, site, index, length} (emt_device.cuh; reported as EMT_ESTATE).
 constexpr int kErrBounds = 101;
+// Device error code of the multi-scenario kernel's tensor-core solve: a
+// wait for the staged digit planes (what = 0) or for the products (1) ran
+// past its budget {kErrTensorWait, subsystem, what, step} (EMT_ESTATE).
+constexpr int kErrTensorWait = 102;
 struct NlDev {
   int32_t k, m;        // subsystem-local ends, -1 = ground
   int32_t np;          // breakpoints after (0, 0)
@@ -418,6 +422,7 @@ struct BatchParams {
   const double* ginv;
   const float* ginv_lo;
   const int32_t* col_code;     // per global column: internal node, or -1 - L/C slot of a strong branch
+  const int32_t* col_sub;      // per global column: its subsystem
   const int32_t* node_sub;     // per internal node: subsystem
   const int32_t* node_r;       // per internal node: row within its subsystem
   const int32_t* sub_nc;       // per subsystem: solve columns n + n_str
@@ -501,36 +506,51 @@ struct BatchParams {
   double dt;
   int32_t* err;                // device error word (the checks build latches there)
   Bounds bnd;                  // ring: slots of the rings x S; h: L/C slots x S; ginv; rec
-  // Digit form of the solve on the bf16 tensor cores (emt_digits.cuh) for a
-  // subsystem whose matrix all scenarios of a tile share: per subsystem s its
-  // matrices in digit form, dig_key[x] = ginv offset, dig_val[x] = word
-  // offset in dig (x in dig_ptr[s] .. dig_ptr[s + 1]); per subsystem its
-  // first internal node and rows; dig_words: the shared-memory digit table's
-  // words, dig_grp: the most subsystems of a group (nullptr dig: off).
+  // Digit form of the solve on the tensor cores (tcgen05, emt_digits.cuh)
+  // for a subsystem whose matrix all scenarios of a tile share: per subsystem
+  // s its matrices in digit form, dig_key[x] = ginv offset, dig_val[x] =
+  // word offset in dig (x in dig_ptr[s] .. dig_ptr[s + 1]); per subsystem its
+  // first internal node and rows; dig_grp: the most subsystems of a group
+  // (nullptr dig: off).
   const uint32_t* dig;
   const int32_t* dig_ptr;
   const int64_t* dig_key;
   const int64_t* dig_val;
   const int32_t* sub_node0;
   const int32_t* sub_n;
-  int32_t dig_words, dig_grp;
+  int32_t dig_grp;
+  int32_t dig_min_rows;        // subsystems of fewer rows keep the FP64 solve (cheaper below ~24 rows)
 };
 
-// Digit matrices of the multi-scenario solve: B fragments of
-// mma.m16n8k16 (k = solve column, n = row of X): fragment (a, R8, s) for
-// digit a, rows 8 R8 .. 8 R8 + 7, columns 16 s .. 16 s + 15 at word
-// ((a R8n + R8) ks + s) 64 + 2 lane (lane 4g + t: row 8 R8 + g, columns
-// 16 s + 2t, +1 in the first word, + 8, + 9 in the second), then the 8 R8n
-// row exponents.  Subsystems of at most kDigRows rows and kDigCols columns.
+// Digit matrices of the multi-scenario solve, in the shared-memory operand
+// layout of tcgen05.mma (K-major, no swizzle: core matrices of 8 rows x 8
+// bf16, 128 contiguous bytes, row i of a core matrix at byte 16 i), in
+// chunks of 64 columns (kp = nc rounded up to 16; chunk c holds the kc =
+// min(64, kp - 64 c) columns from 64 c, one bulk copy each): chunk c at byte
+// 65536 c, in it digit plane a (8 planes) of 64 rows (rows past n are zero),
+// element (a, r, k) at byte
+//   2 a 64 kc + ((r / 8) (kc / 8) + (k - 64 c) / 8) 128 + (r % 8) 16 + (k % 8) 2,
+// so that planes 2p and 2p + 1 form one 128-row operand; after the chunks
+// the 64 row exponents (int32).  Subsystems of at most kDigRows rows and
+// kDigCols columns.
 constexpr int kDigRows = 64;
 constexpr int kDigCols = 128;
-__host__ __device__ inline int64_t dig_matrix_words(int n, int nc) {
-  const int r8 = (n + 7) / 8, ks = (nc + 15) / 16;
-  return (int64_t)8 * r8 * ks * 64 + 8 * r8;
-}
-// shared-memory table words of one subsystem's injection digits for a tile
-// of ts scenario rows (a multiple of 16): 8 digits x ts rows x (8 ks + 4)
-__host__ __device__ inline int dig_table_words(int nc, int ts) { return 8 * ts * (8 * ((nc + 15) / 16) + 4); }
+constexpr int kDigChunk = 64;                         // columns of one staged chunk
+constexpr int kDigChunkBytes = 16 * kDigRows * kDigChunk;   // 64 KiB: the shared-memory staging of a chunk
+__host__ __device__ inline int dig_cols_pad(int nc) { return (nc + 15) & ~15; }
+__host__ __device__ inline int dig_chunk_cols(int kp, int c) { return kp - kDigChunk * c < kDigChunk ? kp - kDigChunk * c : kDigChunk; }
+// bytes of the digit planes of all chunks (the row exponents follow)
+__host__ __device__ inline int64_t dig_planes_bytes(int nc) { return (int64_t)16 * kDigRows * dig_cols_pad(nc); }
+__host__ __device__ inline int64_t dig_matrix_words(int nc) { return dig_planes_bytes(nc) / 4 + kDigRows; }
+// Scenario rows of the injection digit table of a tile (the tcgen05 N
+// blocks): 16 or 32, so that the digit groups of one MMA fit its at most
+// 256 accumulator columns
+__host__ __device__ inline int dig_tile_rows(int S_t) { return S_t <= 16 ? 16 : 32; }
+constexpr int kDigMaxTile = 32;
+// shared-memory bytes of the injection digit table of one chunk for a tile
+// (8 planes x ts rows x 64 bf16), also the scratch of the accumulator
+// read-back (64 rows x ts scenarios x 16 bytes)
+__host__ __device__ inline int dig_table_bytes(int ts) { return 16 * ts * kDigChunk; }
 cudaError_t launch_batch_digits(const double* ginv, const float* ginv_lo, const int64_t* mat_goff,
                                 const int32_t* mat_n, const int32_t* mat_nc, const int64_t* mat_doff, int n_mats,
                                 uint32_t* dig, cudaStream_t st);
@@ -670,9 +690,13 @@ size_t ss_smem_bytes(int rows, int cols, int n, int le, int src, int ln, int lc)
 constexpr int kSsThreads = 256;
 int forward_blocks_per_sm(const FwdLimits& lim);   // resident CTAs per SM (0 on error)
 cudaError_t launch_batch(const BatchParams& p, int threads, cudaStream_t st, BatchGraph* graph);
-size_t batch_smem_bytes(int S_t, int n_sources, int n_sub, int max_cols, int max_nodes, int dig_words = 0,
+size_t batch_smem_bytes(int S_t, int n_sources, int n_sub, int max_cols, int max_nodes, bool digit = false,
                         int dig_grp = 0);
-int batch_max_threads(bool digit);   // most threads of a multi-scenario CTA (the digit-form instance: fewer)
+int batch_max_threads(bool digit);   // most threads of a multi-scenario CTA
+int batch_min_threads(bool digit);   // fewest (the digit form: a warp per TMEM lane quarter)
+// static shared memory the digit-form instance of the multi-scenario kernel
+// keeps beside its dynamic shared memory (mbarriers, the TMEM address)
+constexpr int kBatchDigitStaticSmem = 256;
 void batch_graph_destroy(BatchGraph* graph);
 cudaError_t launch_source_coefficients(const double* amp, const double* phase, int64_t count, double* ac, double* as,
                                        cudaStream_t st);

@@ -23,13 +23,17 @@ def rel_err(a, b):
     return np.max(np.abs(a - b)) / np.max(np.abs(b))
 
 
-def run(net, sc, n_steps, digit, decim=1, shape=None):
+def run(net, sc, n_steps, digit, decim=1, shape=None, min_rows=1):
+    """min_rows=1: every shared matrix in digit form (the default leaves
+    subsystems below 24 rows on the FP64 path)."""
     ctx = emt.emt_build_network(net, sc)
     emt.emt_prefactor(ctx)
     if shape:
         emt.emt_set_option(ctx, "scenarios_per_cta", shape[0])
         emt.emt_set_option(ctx, "batch_threads", shape[1])
     emt.emt_set_option(ctx, "digit_solve", digit)
+    if min_rows is not None:
+        emt.emt_set_option(ctx, "digit_min_rows", min_rows)
     info = {k: emt.emt_get_info(ctx, k) for k in ("digit_solve", "digit_matrices", "scenarios_per_cta")}
     emt.emt_set_recording(ctx, None, decim, n_steps // decim)
     emt.emt_step_n(ctx, n_steps)
@@ -80,11 +84,23 @@ def test_shared_g_full_length_sampled_scenarios():
     64 scenarios; four compared with the oracle at every 10th step."""
     net, sc = g.shared_g(n_scenarios=64)
     N = net.n_steps
-    got, info = run(net, sc, N, 1, decim=10)
+    got, info = run(net, sc, N, 1, decim=10, min_rows=None)   # the default split between the two paths
     assert info["digit_solve"] == 1
     for s in (0, 21, 42, 63):
         ref = oracle.simulate(sc.expand(net, s), N)[9::10]
         assert rel_err(got[:, s, :], ref) <= TOL, s
+
+
+def test_min_rows_option_range():
+    base = g.multi_subsystem(91, [3, 5, 2, 4, 6], n_lines=9, n_sources=3, dt=20e-6, n_series_extra=2)
+    net, sc = g.shared_g(seed=92, n_scenarios=40, n_steps=100, fault_step=50, base=base)
+    ctx = emt.emt_build_network(net, sc)
+    assert emt.emt_get_info(ctx, "digit_min_rows") == 24
+    for bad in (0, 65):
+        with pytest.raises(emt.EmtError) as ei:
+            emt.emt_set_option(ctx, "digit_min_rows", bad)
+        assert ei.value.status == emt.EMT_EINVAL
+    emt.emt_destroy(ctx)
 
 
 def test_option_is_for_scenario_sets_only():
