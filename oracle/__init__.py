@@ -65,6 +65,7 @@ class _Net(ctypes.Structure):
         ("cb_in1", ctypes.c_void_p), ("cb_node", ctypes.c_void_p), ("cb_p0", ctypes.c_void_p),
         ("cb_p1", ctypes.c_void_p),
         ("n_ci", ctypes.c_int64), ("ci_block", ctypes.c_void_p), ("ci_node", ctypes.c_void_p),
+        ("n_fg", ctypes.c_int64), ("fg_line", ctypes.c_void_p), ("fg_tv", ctypes.c_void_p),
     ]
 
 
@@ -154,6 +155,8 @@ class _Pinned:
         n.cb_p0, n.cb_p1 = p(rs("cb_p0", np.float64), np.float64), p(rs("cb_p1", np.float64), np.float64)
         n.n_ci = int(len(rs("ci_block", np.int32)))
         n.ci_block, n.ci_node = p(rs("ci_block", np.int32), np.int32), p(rs("ci_node", np.int32), np.int32)
+        n.n_fg = int(len(rs("fg_line", np.int32))) // 3
+        n.fg_line, n.fg_tv = p(rs("fg_line", np.int32), np.int32), p(rs("fg_tv", np.float64), np.float64)
         self.net = n
 
     @property

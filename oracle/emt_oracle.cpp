@@ -209,6 +209,17 @@ bool valid(const orc_net* net) {
     if (net->ci_block[c] < 0 || net->ci_block[c] >= net->n_cb || net->ci_node[c] < 0 ||
         net->ci_node[c] >= net->n_nodes)
       return false;
+  if (net->n_fg < 0) return false;
+  std::vector<char> grouped(net->n_fl > 0 ? net->n_fl : 0, 0);
+  for (int64_t g = 0; g < net->n_fg; ++g) {
+    for (int j = 0; j < 3; ++j) {
+      const int32_t l = net->fg_line[3 * g + j];
+      if (l < 0 || l >= net->n_fl || grouped[l]) return false;
+      grouped[l] = 1;
+    }
+    double inv[9];
+    if (!invert3(net->fg_tv + 9 * g, inv)) return false;
+  }
   return true;
 }
 
@@ -236,6 +247,11 @@ void components(const orc_net* net, std::vector<int>& sub, int& n_sub) {
     for (int p = 1; p < 3; ++p) {
       join(net->cl_k[3 * l], net->cl_k[3 * l + p]);
       join(net->cl_m[3 * l], net->cl_m[3 * l + p]);
+    }
+  for (int64_t g = 0; g < net->n_fg; ++g)   // a group end's three phase nodes are coupled
+    for (int p = 1; p < 3; ++p) {
+      join(net->fl_k[net->fg_line[3 * g]], net->fl_k[net->fg_line[3 * g + p]]);
+      join(net->fl_m[net->fg_line[3 * g]], net->fl_m[net->fg_line[3 * g + p]]);
     }
   sub.assign(n, -1);
   n_sub = 0;
@@ -302,6 +318,13 @@ struct Sim {
     std::vector<T> w[2];
   };
   std::vector<FLine> fl;
+  // frequency-dependent line groups: T_v^-1 and T_i of each; per line its
+  // group (or -1) and mode
+  struct FGroup {
+    double tinv[9], ti[9];
+  };
+  std::vector<FGroup> fg;
+  std::vector<int> fl_grp, fl_mode;
   // nonlinear resistors: the one of each subsystem (or -1) and its column
   // z = G^-1 (e_k - e_m) over the subsystem's nodes, for the current factors
   std::vector<int> nl_of_sub;                  // the subsystem's nonlinear resistor when it has exactly one, else -1
@@ -384,6 +407,19 @@ struct Sim {
         for (int i = 0; i < 4; ++i) L.s[e][i] = L.z[e][i] = T(0.0);
         L.vprev[e] = L.wprev[e] = L.b[e] = T(0.0);
         L.w[e].assign(L.d + 3, T(0.0));
+      }
+    }
+    fg.assign(net->n_fg, FGroup{});
+    fl_grp.assign(net->n_fl, -1);
+    fl_mode.assign(net->n_fl, 0);
+    for (int64_t gi = 0; gi < net->n_fg; ++gi) {
+      FGroup& G = fg[gi];
+      invert3(net->fg_tv + 9 * gi, G.tinv);
+      for (int p = 0; p < 3; ++p)
+        for (int j = 0; j < 3; ++j) G.ti[3 * p + j] = G.tinv[3 * j + p];   // T_i = (T_v^-1)^T
+      for (int j = 0; j < 3; ++j) {
+        fl_grp[net->fg_line[3 * gi + j]] = (int)gi;
+        fl_mode[net->fg_line[3 * gi + j]] = j;
       }
     }
     cy.assign(net->n_cb, T(0.0));
@@ -517,9 +553,24 @@ struct Sim {
       if (sub[net->ln_k[l]] == s) G[(size_t)local[net->ln_k[l]] * ns + local[net->ln_k[l]]] += y;
       if (sub[net->ln_m[l]] == s) G[(size_t)local[net->ln_m[l]] * ns + local[net->ln_m[l]]] += y;
     }
-    for (int64_t l = 0; l < net->n_fl; ++l)
+    for (int64_t l = 0; l < net->n_fl; ++l) {
+      if (fl_grp[l] >= 0) continue;   // (groups below)
       for (int32_t x : {net->fl_k[l], net->fl_m[l]})
         if (sub[x] == s) G[(size_t)local[x] * ns + local[x]] += T(fl[l].geq);
+    }
+    for (int64_t gi = 0; gi < net->n_fg; ++gi)   // each end: T_i diag(G_eq) T_v^-1 over its phase nodes
+      for (int e = 0; e < 2; ++e) {
+        const FGroup& F = fg[gi];
+        int32_t nd[3];
+        for (int p = 0; p < 3; ++p) nd[p] = e == 0 ? net->fl_k[net->fg_line[3 * gi + p]] : net->fl_m[net->fg_line[3 * gi + p]];
+        if (sub[nd[0]] != s) continue;
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) {
+            double acc = 0.0;
+            for (int j = 0; j < 3; ++j) acc += F.ti[3 * p + j] * fl[net->fg_line[3 * gi + j]].geq * F.tinv[3 * j + q];
+            G[(size_t)local[nd[p]] * ns + local[nd[q]]] += T(acc);
+          }
+      }
     for (int64_t w = 0; w < net->n_sw; ++w)
       if (st[w]) stamp(net->sw_k[w], net->sw_m[w], T(1.0) / T(net->sw_r[w]));
     for (int64_t w = 0; w < net->n_rs; ++w) {
@@ -626,6 +677,7 @@ struct Sim {
     for (int64_t c = 0; c < net->n_ci; ++c) rhs[net->ci_node[c]] += cy[net->ci_block[c]];   // y(n-1)
     // frequency-dependent lines: the far end's interpolated w, A's terms,
     // and the history current each end draws
+    std::vector<T> fhist(2 * (size_t)net->n_fl, T(0.0));   // per line and end: the history current drawn
     for (int64_t l = 0; l < net->n_fl; ++l) {
       FLine& L = fl[l];
       for (int e = 0; e < 2; ++e) {
@@ -639,9 +691,19 @@ struct Sim {
         L.b[e] = b;
         T hist = -b;
         for (int i = 0; i < L.ny; ++i) hist += T(L.lam_y[i]) * L.s[e][i] + T(L.mu_y[i]) * L.vprev[e];
-        rhs[e == 0 ? net->fl_k[l] : net->fl_m[l]] -= hist;
+        fhist[2 * l + e] = hist;
+        if (fl_grp[l] < 0) rhs[e == 0 ? net->fl_k[l] : net->fl_m[l]] -= hist;
       }
     }
+    // line groups: the modal history currents enter the phase nodes as T_i hist_mode
+    for (int64_t gi = 0; gi < net->n_fg; ++gi)
+      for (int e = 0; e < 2; ++e)
+        for (int p = 0; p < 3; ++p) {
+          const int32_t lp = net->fg_line[3 * gi + p];
+          T ip = T(0.0);
+          for (int j = 0; j < 3; ++j) ip += T(fg[gi].ti[3 * p + j]) * fhist[2 * net->fg_line[3 * gi + j] + e];
+          rhs[e == 0 ? net->fl_k[lp] : net->fl_m[lp]] -= ip;
+        }
     for (int64_t l = 0; l < net->n_ln; ++l) {
       int64_t d1 = net->ln_d[l] + 1;
       rhs[net->ln_k[l]] -= ring_k[l][n % d1];
@@ -755,7 +817,15 @@ struct Sim {
     for (int64_t l = 0; l < net->n_fl; ++l) {
       FLine& L = fl[l];
       for (int e = 0; e < 2; ++e) {
-        const T ve = v[e == 0 ? net->fl_k[l] : net->fl_m[l]];
+        T ve = v[e == 0 ? net->fl_k[l] : net->fl_m[l]];
+        if (fl_grp[l] >= 0) {   // a mode: the modal voltage (T_v^-1 v_phase)_j
+          const int gi = fl_grp[l], j = fl_mode[l];
+          ve = T(0.0);
+          for (int p = 0; p < 3; ++p) {
+            const int32_t lp = net->fg_line[3 * gi + p];
+            ve += T(fg[gi].tinv[3 * j + p]) * v[e == 0 ? net->fl_k[lp] : net->fl_m[lp]];
+          }
+        }
         T yc = T(L.y0) * ve;
         for (int i = 0; i < L.ny; ++i) {
           L.s[e][i] = T(L.lam_y[i]) * L.s[e][i] + T(L.mu_y[i]) * (ve + L.vprev[e]);

@@ -152,6 +152,19 @@ typedef struct {
   int64_t n_ci;
   const int32_t* ci_block;
   const int32_t* ci_node;
+  /* Frequency-dependent line groups (n_fg may be 0): three of the
+   * frequency-dependent lines above carry the modes of one three-phase line.
+   * fg_line[3 g + j] is the line of mode j; its end nodes are phase j's
+   * nodes at each end (the three end-k nodes lie in one subsystem, as do the
+   * three end-m nodes); fg_tv[9 g + 3 p + j]: T_v, phase voltages = T_v modal
+   * voltages (modal currents: T_i = T_v^-T).  Mode j's equations act on modal
+   * quantities: its Y_c on the modal voltage (T_v^-1 v_phase)_j, its w and b
+   * as for one conductor; each end draws the phase currents T_i i_mode, i.e.
+   * it stamps T_i diag(G_eq) T_v^-1 and draws T_i times the modal history
+   * currents.  A line belongs to at most one group. */
+  int64_t n_fg;
+  const int32_t* fg_line;
+  const double* fg_tv;
 } orc_net;
 
 /* Run n_steps steps from the de-energised state.

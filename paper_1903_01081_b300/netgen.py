@@ -115,6 +115,12 @@ class Network:
     cb_p1: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
     ci_block: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
     ci_node: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    # frequency-dependent line groups: fg_line[3 g + j] is the frequency-
+    # dependent line carrying mode j of a three-phase line (its ends are
+    # phase j's nodes), fg_tv[9 g + 3 p + j] the group's T_v (phase voltages
+    # = T_v modal voltages; modal currents T_i = T_v^-T)
+    fg_line: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    fg_tv: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float64))
     n_steps: int = 0            # suggested run length
     meta: dict = field(default_factory=dict)
 
@@ -1102,3 +1108,64 @@ def with_coupled_lines(base: Network, seed: int = 1007) -> Network:
     net.cl_tau = np.asarray(cl_tau, np.float64)
     net.meta = dict(net.meta, coupled_lines={"seed": seed, "lines": L})
     return net
+
+
+def fd_groups_from_coupled(cnet: Network, seed: int = 1011, lossless: bool = False,
+                           same_modes: bool = False) -> Network:
+    """The coupled lines of ``cnet`` as frequency-dependent line groups: mode j
+    of each becomes a frequency-dependent line between phase j's nodes with
+    the mode's Z_c and travel time, grouped with the line's T_v.  Lossless:
+    Y_c = 1/Z_j, A = e^{-s tau_j} (the coupled Bergeron line itself);
+    otherwise each mode gets poles drawn as in ``with_fd_lines`` (Y_c(0) =
+    (1 + delta)/Z_j, DC transmission exp(-U[0.02, 0.2])).  ``same_modes``:
+    every mode of a line takes mode 1's impedance, travel time and poles (with
+    an orthogonal T_v the phases then decouple into three equal lines)."""
+    rng = np.random.default_rng(seed)
+    net = cnet.copy()
+    L = len(cnet.cl_z) // 3
+    n = 3 * L
+    fl_k, fl_m = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    tau, y0, a0 = np.zeros(n), np.zeros(n), np.zeros(n)
+    ny, na = np.zeros(n, np.int32), np.zeros(n, np.int32)
+    yq, yc, ap, ar = np.zeros((n, 4)), np.zeros((n, 4)), np.zeros((n, 4)), np.zeros((n, 4))
+    for l in range(L):
+        for j in range(3):
+            x, src = 3 * l + j, 3 * l + (1 if same_modes else j)
+            fl_k[x], fl_m[x] = cnet.cl_k[x], cnet.cl_m[x]
+            z = float(cnet.cl_z[src])
+            tau[x], y0[x] = float(cnet.cl_tau[src]), 1.0 / z
+            if lossless:
+                a0[x] = 1.0
+                continue
+            if same_modes and j != 1:
+                continue   # (copied from mode 1 below)
+            q = -rng.uniform(1e3, 1e5)
+            ny[x], yq[x, 0], yc[x, 0] = 1, q, -q * rng.uniform(0.05, 0.3) / z
+            dc = np.exp(-rng.uniform(0.02, 0.2))
+            w1 = rng.uniform(0.0, 1.0)
+            p1, p2 = -rng.uniform(2e3, 2e4), -rng.uniform(2e4, 2e5)
+            na[x], ap[x, :2] = 2, (p1, p2)
+            ar[x, :2] = -p1 * w1 * dc, -p2 * (1.0 - w1) * dc
+        if same_modes and not lossless:
+            for j in (0, 2):
+                x, src = 3 * l + j, 3 * l + 1
+                ny[x], na[x], a0[x] = ny[src], na[src], a0[src]
+                yq[x], yc[x], ap[x], ar[x] = yq[src], yc[src], ap[src], ar[src]
+    net.fl_k, net.fl_m, net.fl_tau, net.fl_y0, net.fl_a0 = fl_k, fl_m, tau, y0, a0
+    net.fl_ny, net.fl_na = ny, na
+    net.fl_yq, net.fl_yc, net.fl_ap, net.fl_ar = yq.reshape(-1), yc.reshape(-1), ap.reshape(-1), ar.reshape(-1)
+    net.fg_line = np.arange(n, dtype=np.int32)
+    net.fg_tv = np.asarray(cnet.cl_tv, np.float64).copy()
+    for f in ("cl_k", "cl_m", "cl_tv", "cl_z", "cl_tau"):
+        setattr(net, f, np.zeros(0, getattr(cnet, f).dtype))
+    net.meta = dict(net.meta, fd_line_groups={"seed": seed, "groups": L, "lossless": lossless,
+                                              "same_modes": same_modes})
+    return net
+
+
+def with_fd_line_groups(base: Network, seed: int = 1011) -> Network:
+    """``base`` with every three-phase line a frequency-dependent line group:
+    Clarke modes with the impedances and travel times of ``with_coupled_lines``
+    (zero-sequence mode slower and of higher impedance, fractional travel
+    times), each mode lossy as in ``with_fd_lines``."""
+    return fd_groups_from_coupled(with_coupled_lines(base, seed=seed), seed=seed + 1)
