@@ -32,6 +32,8 @@ two further legs the metric names, reported as extra keys of the line:
       and 10 current-zero breakers, against the same network without them;
   "coupled_lines": the large-scale network with its three-phase lines as
       coupled modal lines with interpolated travel times, against the plain one;
+  "fd_line_groups": the same with its three-phase lines as frequency-dependent
+      line groups (Clarke modes, each a lossy frequency-dependent line);
   "fd_lines": the same with its line conductors as lossy frequency-dependent
       lines, against the plain one;
   "nonlinear": the same with 40 surge arresters solved by the compensation
@@ -596,6 +598,17 @@ def fd_line_leg(steps=None, reps=3):
                        "dt; all nodes recorded", steps, reps)
 
 
+def fd_group_leg(steps=None, reps=3):
+    """The large-scale network with its 700 three-phase lines as frequency-
+    dependent line groups: Clarke modes, each mode a lossy frequency-dependent
+    line with its own impedance, travel time and poles."""
+    from paper_1903_01081_b300 import netgen as g
+    return variant_leg(g.with_fd_line_groups(g.large_scale()),
+                       "large-scale network with its 700 three-phase lines as frequency-dependent line groups: "
+                       "Clarke modes (zero sequence slower, of higher impedance), each mode Y_c = 1/Z + one pole, "
+                       "A = e^{-s tau} x two poles, fractional travel times; all nodes recorded", steps, reps)
+
+
 def nonlinear_leg(steps=None, reps=3):
     """The large-scale network with 40 surge arresters (odd piecewise-linear
     resistors solved by the compensation method, one per subsystem)."""
@@ -989,7 +1002,8 @@ def run_ours(args):
             "clocks": clocks.summary(),
             "parity_rel_err_first_2000_steps": parity,
             **({"scenarios": scenario_legs(cpu=True), "adjoint": adjoint_leg(), "small_network": small_network_leg(), "runtime_switches": runtime_switch_leg(),
-                "coupled_lines": coupled_line_leg(), "fd_lines": fd_line_leg(), "nonlinear": nonlinear_leg(),
+                "coupled_lines": coupled_line_leg(), "fd_lines": fd_line_leg(),
+                "fd_line_groups": fd_group_leg(), "nonlinear": nonlinear_leg(),
                 "controls": control_leg(), "converter_stations": station_leg(),
                 "bus_arresters": bus_arrester_leg(), "sizes": scale_legs()}
                if args.leg == "all" else {}),
@@ -1010,7 +1024,7 @@ def main():
     ap.add_argument("--time-steps", type=int, default=N_STEPS)
     ap.add_argument("--skip-extras", action="store_true")
     ap.add_argument("--leg", choices=["all", "single", "n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines",
-                                      "fd_lines", "nonlinear", "controls", "sizes", "control_study",
+                                      "fd_lines", "fd_line_groups", "nonlinear", "controls", "sizes", "control_study",
                                       "arrester_study", "fd_line_study", "coupled_line_study", "converter_stations",
                                       "bus_arresters", "phases", "shared_g_digit"],
                     default="all",
@@ -1029,7 +1043,8 @@ def main():
         return 0
     if args.impl == "reference":
         return run_reference(args)
-    if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "fd_lines", "nonlinear",
+    if args.leg in ("n1", "shared_g", "adjoint", "runtime_switches", "coupled_lines", "fd_lines", "fd_line_groups",
+                    "nonlinear",
                     "controls", "sizes", "control_study", "arrester_study", "fd_line_study", "coupled_line_study",
                     "converter_stations", "bus_arresters", "phases", "shared_g_digit"):
         return run_leg(args)
@@ -1050,6 +1065,8 @@ def run_leg(args):
         out = control_leg(args.leg_steps, reps=1)
     elif args.leg == "fd_lines":
         out = fd_line_leg(args.leg_steps, reps=1)
+    elif args.leg == "fd_line_groups":
+        out = fd_group_leg(args.leg_steps, reps=1)
     elif args.leg == "nonlinear":
         out = nonlinear_leg(args.leg_steps, reps=1)
     elif args.leg == "converter_stations":

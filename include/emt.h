@@ -201,6 +201,20 @@ typedef struct {
   const int32_t* nl_np;
   const double* nl_v;
   const double* nl_i;
+  /* Frequency-dependent line groups (n_fdgroups may be 0; appended here so
+   * that descriptions without them keep their layout): three of the
+   * frequency-dependent lines above carry the modes of one three-phase line.
+   * fg_line[3 g + j] is the line of mode j, whose ends are phase j's nodes
+   * (the three end-k nodes lie in one subsystem, as do the end-m ones);
+   * fg_tv[9 g + 3 p + j]: T_v, phase voltages = T_v modal voltages (modal
+   * currents: T_i = T_v^-T).  Mode j's Y_c acts on the modal voltage
+   * (T_v^-1 v_phase)_j, its w and b as for one conductor; each end stamps
+   * T_i diag(G_eq) T_v^-1 and draws T_i times the modal history currents.
+   * A line belongs to at most one group.  Single networks only (a scenario
+   * set with groups returns EINVAL); not supported by emt_adjoint. */
+  int64_t n_fdgroups;
+  const int32_t* fg_line;
+  const double* fg_tv;
 } emt_network_desc;
 
 /* Optional per-scenario overrides of one base network (the paper's

@@ -447,6 +447,24 @@ std::string validate(const emt_network_desc* d) {
         return nm + ": poles must be finite and < 0";
     if (!(geq > 0.0)) return nm + ": its end conductance y0 + sum mu must be > 0";
   }
+  if (d->n_fdgroups < 0) return "negative count";
+  if (d->n_fdgroups && (!d->fg_line || !d->fg_tv)) return "frequency-dependent line group array is NULL";
+  {
+    std::vector<char> grouped((size_t)std::max<int64_t>(d->n_fdlines, 0), 0);
+    for (int64_t gi = 0; gi < d->n_fdgroups; ++gi) {
+      const std::string nm = "frequency-dependent line group " + std::to_string(gi);
+      for (int j = 0; j < 3; ++j) {
+        const int32_t l = d->fg_line[3 * gi + j];
+        if (l < 0 || l >= d->n_fdlines) return nm + ": line index out of range";
+        if (grouped[l]) return nm + ": line " + std::to_string(l) + " is in a group twice";
+        grouped[l] = 1;
+      }
+      for (int k = 0; k < 9; ++k)
+        if (!std::isfinite(d->fg_tv[9 * gi + k])) return nm + ": T_v must be finite";
+      double inv[9];
+      if (!invert3_host(d->fg_tv + 9 * gi, inv)) return nm + ": T_v must be invertible";
+    }
+  }
   if (d->n_cblocks < 0 || d->n_cinj < 0) return "negative count";
   if (d->n_cblocks && (!d->cb_type || !d->cb_in0 || !d->cb_in1 || !d->cb_node || !d->cb_p0 || !d->cb_p1))
     return "control block array is NULL";
@@ -1213,7 +1231,8 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
     return EMT_EINVAL;
   }
   if (scen) {
-    const std::string sm = validate_scenarios(d, scen);
+    std::string sm = validate_scenarios(d, scen);
+    if (sm.empty() && d->n_fdgroups > 0) sm = "frequency-dependent line groups are not supported in scenario sets";
     if (!sm.empty()) {
       g_build_error = sm;
       return EMT_EINVAL;
@@ -1250,6 +1269,11 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
     for (int p = 1; p < 3; ++p) {
       join(d->cl_k[3 * l], d->cl_k[3 * l + p]);
       join(d->cl_m[3 * l], d->cl_m[3 * l + p]);
+    }
+  for (int64_t gi = 0; gi < d->n_fdgroups; ++gi)   // and those of a frequency-dependent line group
+    for (int p = 1; p < 3; ++p) {
+      join(d->fl_k[d->fg_line[3 * gi]], d->fl_k[d->fg_line[3 * gi + p]]);
+      join(d->fl_m[d->fg_line[3 * gi]], d->fl_m[d->fg_line[3 * gi + p]]);
     }
   if (scen && scen->sw_ptr)   // scenario switches may join nodes too
     for (int64_t w = 0; w < scen->sw_ptr[scen->n_scenarios]; ++w) join(scen->sw_k[w], scen->sw_m[w]);
@@ -1459,9 +1483,18 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   std::vector<std::vector<int64_t>> cends_of(S);   // coupled ends (2 l + e) per subsystem
   for (int64_t x = 0; x < 2 * d->n_clines; ++x)
     cends_of[c->sub_of_node[(x & 1) ? d->cl_m[3 * (x >> 1)] : d->cl_k[3 * (x >> 1)]]].push_back(x);
-  std::vector<std::vector<int64_t>> fends_of(S);   // frequency-dependent ends (2 l + e) per subsystem
+  // frequency-dependent line groups: per line its group (or -1); group ends (2 g + e) per subsystem
+  std::vector<int64_t> fg_of_line((size_t)d->n_fdlines, -1);
+  for (int64_t gi = 0; gi < d->n_fdgroups; ++gi)
+    for (int j = 0; j < 3; ++j) fg_of_line[d->fg_line[3 * gi + j]] = gi;
+  std::vector<std::vector<int64_t>> gends_of(S);
+  for (int64_t x = 0; x < 2 * d->n_fdgroups; ++x) {
+    const int32_t l0 = d->fg_line[3 * (x >> 1)];
+    gends_of[c->sub_of_node[(x & 1) ? d->fl_m[l0] : d->fl_k[l0]]].push_back(x);
+  }
+  std::vector<std::vector<int64_t>> fends_of(S);   // frequency-dependent ends (2 l + e) of lines in no group
   for (int64_t x = 0; x < 2 * d->n_fdlines; ++x)
-    fends_of[c->sub_of_node[(x & 1) ? d->fl_m[x >> 1] : d->fl_k[x >> 1]]].push_back(x);
+    if (fg_of_line[x >> 1] < 0) fends_of[c->sub_of_node[(x & 1) ? d->fl_m[x >> 1] : d->fl_k[x >> 1]]].push_back(x);
   std::vector<std::vector<int64_t>> ends_of(S);
   std::vector<int64_t> le_of_end(2 * d->n_lines, -1);
   for (int64_t e = 0; e < 2 * d->n_lines; ++e) {
@@ -1494,6 +1527,31 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
         if (it == dmin.end() || it->second > le.d) dmin[fs] = le.d;
       }
     }
+    // the discretised pole terms of frequency-dependent line l; its end conductance in geq
+    auto fd_record = [&](int64_t l, double& geq) {
+      const double dt = d->dt;
+      FdEndDev r{};
+      r.ny = d->fl_ny[l];
+      r.na = d->fl_na[l];
+      r.y0 = d->fl_y0[l];
+      r.a0 = d->fl_a0[l];
+      geq = r.y0;
+      for (int i = 0; i < r.ny; ++i) {
+        const double q = d->fl_yq[4 * l + i], den = 1.0 - q * dt / 2.0;
+        r.lam_y[i] = (1.0 + q * dt / 2.0) / den;
+        r.mu_y[i] = d->fl_yc[4 * l + i] * (dt / 2.0) / den;
+        r.mu_sum += r.mu_y[i];
+        geq += r.mu_y[i];
+      }
+      for (int i = 0; i < r.na; ++i) {
+        const double p = d->fl_ap[4 * l + i], den = 1.0 - p * dt / 2.0;
+        r.lam_a[i] = (1.0 + p * dt / 2.0) / den;
+        r.mu_a[i] = d->fl_ar[4 * l + i] * (dt / 2.0) / den;
+      }
+      return r;
+    };
+    // frequency-dependent records of this subsystem: those of group modes (below), then of lone lines
+    sd.fd_off = (int)c->fdends.size();
     // coupled line ends: a record each, then its three modes as line ends
     sd.ce_off = (int)c->cends.size();
     for (int64_t x : cends_of[s]) {
@@ -1528,33 +1586,56 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
         }
       }
     }
+    // frequency-dependent line group ends: a coupled end (T_v, modal 1 / G_eq, so that it stamps
+    // T_i diag(G_eq) T_v^-1) whose three modes are frequency-dependent line ends on modal quantities
+    for (int64_t x : gends_of[s]) {
+      const int64_t gi = x >> 1;
+      const int e = (int)(x & 1);
+      CoupledEndDev ce{};
+      ce.le0 = (int)c->line_ends.size() - sd.le_off;
+      for (int k = 0; k < 9; ++k) ce.tv[k] = d->fg_tv[9 * gi + k];
+      const int ce_local = (int)c->cends.size() - sd.ce_off;
+      for (int j = 0; j < 3; ++j) {
+        const int64_t l = d->fg_line[3 * gi + j];
+        ce.node[j] = local[e ? d->fl_m[l] : d->fl_k[l]];
+        double geq = 0.0;
+        FdEndDev r = fd_record(l, geq);
+        ce.z[j] = 1.0 / geq;
+        const double steps = d->fl_tau[l] / d->dt;
+        r.le = (int)c->line_ends.size() - sd.le_off;
+        LineEndDev le{};
+        le.node = -1;
+        le.ce = ce_local;
+        le.mode = j;
+        le.fd = (int)c->fdends.size() - sd.fd_off;
+        le.d = (int32_t)std::floor(steps);
+        le.depth = 2 * le.d;
+        le.f = steps - (double)le.d;
+        r.omf = 1.0 - le.f;
+        le.y = 0.0;
+        le.y2 = 0.0;
+        le.own_ring = fl_ring[2 * l + e];
+        le.far_ring = fl_ring[2 * l + 1 - e];
+        c->fdends.push_back(r);
+        c->line_ends.push_back(le);
+        const int fs = c->sub_of_node[e ? d->fl_k[l] : d->fl_m[l]];
+        if (fs != s) {
+          auto it = dmin.find(fs);
+          if (it == dmin.end() || it->second > le.d) dmin[fs] = le.d;
+        }
+      }
+      c->cends.push_back(ce);
+    }
     sd.n_ce = (int)c->cends.size() - sd.ce_off;
     c->lim.ce = std::max(c->lim.ce, sd.n_ce);
     // frequency-dependent line ends: a line end each (the ring carries w)
     // and a record with the discretised pole terms
-    sd.fd_off = (int)c->fdends.size();
     for (int64_t x : fends_of[s]) {
       const int64_t l = x >> 1;
       const int e = (int)(x & 1);
       const double dt = d->dt, steps = d->fl_tau[l] / dt;
-      FdEndDev r{};
-      r.ny = d->fl_ny[l];
-      r.na = d->fl_na[l];
-      r.y0 = d->fl_y0[l];
-      r.a0 = d->fl_a0[l];
-      double geq = r.y0;
-      for (int i = 0; i < r.ny; ++i) {
-        const double q = d->fl_yq[4 * l + i], den = 1.0 - q * dt / 2.0;
-        r.lam_y[i] = (1.0 + q * dt / 2.0) / den;
-        r.mu_y[i] = d->fl_yc[4 * l + i] * (dt / 2.0) / den;
-        r.mu_sum += r.mu_y[i];
-        geq += r.mu_y[i];
-      }
-      for (int i = 0; i < r.na; ++i) {
-        const double p = d->fl_ap[4 * l + i], den = 1.0 - p * dt / 2.0;
-        r.lam_a[i] = (1.0 + p * dt / 2.0) / den;
-        r.mu_a[i] = d->fl_ar[4 * l + i] * (dt / 2.0) / den;
-      }
+      double geq = 0.0;
+      FdEndDev r = fd_record(l, geq);
       r.le = (int)c->line_ends.size() - sd.le_off;
       LineEndDev le{};
       le.node = local[e ? d->fl_m[l] : d->fl_k[l]];
@@ -1776,7 +1857,12 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
     for (int x = 0; x < sd.n_ci; ++x)   // controlled currents enter their nodes
       el[ci_nodes_of[s][x]].push_back((int32_t)(zero + 1 + x));
     for (int x = 0; x < sd.n_fd; ++x) {   // FD ends draw Hy - b
-      const int node = c->line_ends[sd.le_off + c->fdends[sd.fd_off + x].le].node;
+      const LineEndDev& le = c->line_ends[sd.le_off + c->fdends[sd.fd_off + x].le];
+      if (le.ce >= 0) {   // a group mode: its Hy slot carries phase `mode`'s T_i Hy; b enters the phase slots
+        el[c->cends[sd.ce_off + le.ce].node[le.mode]].push_back((int32_t)(kEntryNeg | (uint32_t)(zero + 1 + sd.n_ci + x)));
+        continue;
+      }
+      const int node = le.node;
       el[node].push_back((int32_t)(ie_base + sd.n_le + 3 * sd.n_ce + x));
       el[node].push_back((int32_t)(kEntryNeg | (uint32_t)(zero + 1 + sd.n_ci + x)));
     }

@@ -474,7 +474,7 @@ struct FwdSmem {
       fdst, nls;                                                                           // 8-byte
   size_t gilo, ivf, partf;                                                                 // float
   size_t lck, lcm, lckind, lcstr, sbsrc, lenode, ledepth, led, rslot, wslot, ent, ilnode, ilcnt, srcg, recp,
-      lece, lemode, cele0, cenode, clay, cinj, lefd, cecnt;                                // int
+      lece, lemode, cele0, cenode, clay, cinj, lefd, cecnt, cecnt2;                        // int
   size_t bytes;
 };
 
@@ -540,6 +540,7 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
   s.cinj = w(L.ci);
   s.lefd = w(L.le);
   s.cecnt = w(L.ce);
+  s.cecnt2 = w(L.ce);
   s.bytes = (o + 15) & ~(size_t)15;
   return s;
 }
@@ -551,9 +552,12 @@ __host__ __device__ inline FwdSmem fwd_smem(const FwdLimits& L) {
 // (blk_old), then the phase-domain history currents T_i I_mode of each
 // coupled end into the phase slots that follow the n_le line-end slots.
 __device__ void fold_modes(int lane, int n_le, int n_ce, const int* lece, const double* lef, const double* blk_old,
-                           double* blk_new, double* imode_new, const int* cele0, const double* ceti) {
+                           double* blk_new, double* imode_new, const int* cele0, const double* ceti, const int* lefd,
+                           int fd_base) {
   for (int e = lane; e < n_le; e += 32)
-    if (lece[e] >= 0) imode_new[e] = fma(lef[e], blk_old[e], (1.0 - lef[e]) * blk_new[e]);
+    if (lece[e] >= 0)   // (a mode of a frequency-dependent line group: -b, already folded on arrival)
+      imode_new[e] = lefd != nullptr && lefd[e] >= 0 ? -blk_new[fd_base + lefd[e]]
+                                                     : fma(lef[e], blk_old[e], (1.0 - lef[e]) * blk_new[e]);
   __syncwarp();
   for (int x = lane; x < 3 * n_ce; x += 32) {
     const int c = x / 3, p = x - 3 * c;
@@ -1082,6 +1086,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   for (int c = tid; c < n_ce; c += T) {
     const CoupledEndDev& ce = P.ce[S.ce_off + c];
     cecnt[c] = 0;
+    reinterpret_cast<int*>(smem_raw + L.cecnt2)[c] = 0;
     cele0[c] = ce.le0;
     for (int k = 0; k < 3; ++k) cenode[3 * c + k] = ce.node[k];
     for (int k = 0; k < 9; ++k) {
@@ -1241,6 +1246,17 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   }
   __syncthreads();
   for (int x = tid; x < n_sb; x += T) inp[n_lc + x] = sbg[x] * vs[(P.n0 & 1) * src_vs + sbsrc[x]];
+  // frequency-dependent line groups: the modes' Hy (kept modal in the state) into the phase slots, T_i Hy
+  for (int c = tid; c < (n_fd > 0 ? n_ce : 0); c += T) {
+    const int e0 = cele0[c];
+    if (lefd[e0] < 0) continue;   // (a coupled Bergeron end)
+    const double h0 = fdst[kFdState * lefd[e0] + 10], h1 = fdst[kFdState * lefd[e0 + 1] + 10],
+                 h2 = fdst[kFdState * lefd[e0 + 2] + 10];
+    for (int p = 0; p < 3; ++p) {
+      const double* ti = ceti + 9 * c + 3 * p;
+      inp[hy_base + lefd[e0 + p]] = fma(ti[0], h0, fma(ti[1], h1, ti[2] * h2));
+    }
+  }
   for (int t = tid; t < n_str; t += T) {
     const int x = P.str_slot[S.str_off + t];
     lcstr[x] = t;
@@ -1255,7 +1271,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
     if (!ok && lane == 0) s_abort = 1;
     if (n_ce > 0)
       fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + (p0 ^ 1) * blk_len, inp + ie_base + p0 * blk_len,
-                 imode + p0 * lv, cele0, ceti);
+                 imode + p0 * lv, cele0, ceti, n_fd > 0 ? lefd : nullptr, fd_base);
   }
   // control layer starts 0..31 in the control warp's registers (lane l)
   int lay_reg = 0;
@@ -1481,7 +1497,15 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
           if (fx >= 0) {   // frequency-dependent end: Y_c's terms of v, then w = 2 yc - b
             const FdEndDev& r = fdr[fx];
             double* sx = fdst + kFdState * fx;
-            const double v = vv[lenode[e]], vsum = v + sx[8];
+            double v;
+            if (c >= 0) {   // a mode of a line group: the modal voltage (T_v^-1 v_phase)_mode
+              const double* tr = cetinv + 9 * c + 3 * lemode[e];
+              const int* nd = cenode + 3 * c;
+              v = fma(tr[0], vv[nd[0]], fma(tr[1], vv[nd[1]], tr[2] * vv[nd[2]]));
+            } else {
+              v = vv[lenode[e]];
+            }
+            const double vsum = v + sx[8];
             double ssum = 0.0, lam_s = 0.0;
             for (int i = 0; i < r.ny; ++i) {
               const double si = fma(r.lam_y[i], sx[i], r.mu_y[i] * vsum);
@@ -1494,7 +1518,24 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
             sx[8] = v;
             const double hy = fma(r.mu_sum, v, lam_s);   // Hy(n+1)
             sx[10] = hy;
-            inp[hy_base + fx] = hy;
+            if (c < 0) {
+              inp[hy_base + fx] = hy;
+            } else {   // the last of its end's three modes puts T_i Hy_mode into the phase slots
+              __threadfence_block();
+              int* cnt2 = reinterpret_cast<int*>(smem_raw + fwd_smem(P.lim).cecnt2);
+              if (atomicAdd(&cnt2[c], 1) == 2) {
+                __threadfence_block();
+                cnt2[c] = 0;
+                const int e0 = cele0[c];
+                const volatile double* st = fdst;
+                const double h0 = st[kFdState * lefd[e0] + 10], h1 = st[kFdState * lefd[e0 + 1] + 10],
+                             h2 = st[kFdState * lefd[e0 + 2] + 10];
+                for (int p = 0; p < 3; ++p) {
+                  const double* ti = ceti + 9 * c + 3 * p;
+                  inp[hy_base + lefd[e0 + p]] = fma(ti[0], h0, fma(ti[1], h1, ti[2] * h2));
+                }
+              }
+            }
           } else if (c < 0) {
             out = fma(-ley2[e], vv[lenode[e]], -ie_cur[e]);
           } else {   // a mode: c_j = -(2/Z_j) (T_v^-1 v_p)_j - I_mode_j(n)
@@ -1538,7 +1579,12 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
           if (!ok) break;
           const int c = lece[e];
           if (c >= 0) {   // a mode: its interpolated history; the third of its end's modes forms T_i I_mode
-            imode_next[e] = fma(lef[e], ie_old[e], (1.0 - lef[e]) * v);
+            if (F.lefd != nullptr && F.lefd[e] >= 0) {   // a line group's mode: b folded now, -b its history
+              fold_fd_end(F, e, v, ie_next);
+              imode_next[e] = -ie_next[F.b_base + F.lefd[e]];
+            } else {
+              imode_next[e] = fma(lef[e], ie_old[e], (1.0 - lef[e]) * v);
+            }
             __threadfence_block();
             if (atomicAdd(&cecnt[c], 1) == 2) {
               __threadfence_block();

@@ -58,6 +58,7 @@ class _NetworkDesc(ctypes.Structure):
         ("fl_na", ctypes.c_void_p), ("fl_ap", ctypes.c_void_p), ("fl_ar", ctypes.c_void_p),
         ("n_nonlin", ctypes.c_int64), ("nl_k", ctypes.c_void_p), ("nl_m", ctypes.c_void_p),
         ("nl_np", ctypes.c_void_p), ("nl_v", ctypes.c_void_p), ("nl_i", ctypes.c_void_p),
+        ("n_fdgroups", ctypes.c_int64), ("fg_line", ctypes.c_void_p), ("fg_tv", ctypes.c_void_p),
     ]
 
 
@@ -220,6 +221,8 @@ def network_desc(net, keep: list) -> _NetworkDesc:
     d.nl_k, d.nl_m = p(rs("nl_k", np.int32), np.int32), p(rs("nl_m", np.int32), np.int32)
     d.nl_np = p(rs("nl_np", np.int32), np.int32)
     d.nl_v, d.nl_i = p(rs("nl_v", np.float64), np.float64), p(rs("nl_i", np.float64), np.float64)
+    d.n_fdgroups = int(len(rs("fg_line", np.int32))) // 3
+    d.fg_line, d.fg_tv = p(rs("fg_line", np.int32), np.int32), p(rs("fg_tv", np.float64), np.float64)
     return d
 
 

@@ -1,0 +1,71 @@
+"""Frequency-dependent line groups on the GPU (three frequency-dependent
+conductors as the modes of one three-phase line through T_v): each end is a
+coupled end whose modes run the frequency-dependent line equations on modal
+quantities.  Held to the oracle at a peak-normalised 1e-10, also across
+launches (the modal histories are folded into the phase slots when a launch
+starts) and over the full 50,000 steps of the large-scale network."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_01081_b300 import emt, netgen as g
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def rel_err(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+def base_net():
+    return g.multi_subsystem(161, [3, 4, 2, 3, 5], n_lines=8, n_sources=2, dt=20e-6)
+
+
+def gpu_run(net, chunks):
+    sim = emt.Simulator(net, n_steps=sum(chunks))
+    for n in chunks:
+        sim.run(n)
+    sim.sync()
+    w = sim.waveforms()[:, 0, :]
+    sim.close()
+    return w
+
+
+def test_small_network_matches_the_oracle_across_launches():
+    net = g.with_fd_line_groups(base_net())
+    N = 4000
+    ref = oracle.simulate(net, N)
+    assert rel_err(gpu_run(net, [N]), ref) <= TOL
+    assert rel_err(gpu_run(net, [1, 1499, 2500]), ref) <= TOL
+
+
+def test_lossless_groups_are_the_coupled_line():
+    cnet = g.with_coupled_lines(base_net(), seed=3)
+    net = g.fd_groups_from_coupled(cnet, lossless=True)
+    N = 3000
+    got = gpu_run(net, [N])
+    assert rel_err(got, oracle.simulate(net, N)) <= TOL
+    assert rel_err(got, gpu_run(cnet, [N])) <= TOL
+
+
+def test_large_scale_network_full_length():
+    net = g.with_fd_line_groups(g.large_scale())
+    N = net.n_steps
+    got = gpu_run(net, [N])
+    ref = oracle.simulate(net, N)
+    assert rel_err(got, ref) <= TOL
+
+
+def test_groups_are_refused_in_scenario_sets_and_by_the_adjoint():
+    net = g.with_fd_line_groups(base_net())
+    base, sc = g.shared_g(seed=92, n_scenarios=4, n_steps=100, fault_step=50, base=net)
+    with pytest.raises(emt.EmtError) as ei:
+        emt.emt_build_network(base, sc)
+    assert ei.value.status == emt.EMT_EINVAL
+    ctx = emt.emt_build_network(net)
+    emt.emt_prefactor(ctx)
+    with pytest.raises(emt.EmtError) as ei:
+        emt.emt_adjoint(ctx, np.zeros((10, net.n_nodes)), 10, 0)
+    assert ei.value.status == emt.EMT_EINVAL
+    emt.emt_destroy(ctx)
