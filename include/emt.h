@@ -210,8 +210,8 @@ typedef struct {
    * currents: T_i = T_v^-T).  Mode j's Y_c acts on the modal voltage
    * (T_v^-1 v_phase)_j, its w and b as for one conductor; each end stamps
    * T_i diag(G_eq) T_v^-1 and draws T_i times the modal history currents.
-   * A line belongs to at most one group.  Single networks only (a scenario
-   * set with groups returns EINVAL); not supported by emt_adjoint. */
+   * A line belongs to at most one group.  Scenario sets take them; not
+   * supported by emt_adjoint. */
   int64_t n_fdgroups;
   const int32_t* fg_line;
   const double* fg_tv;

@@ -926,8 +926,12 @@ std::string build_scenarios(emt_ctx* c, const emt_network_desc* d, const emt_sce
           else if (idx < fdb0) code = (6u << kBentKindShift) | (uint32_t)(3 * sd.ce_off + idx - cph0);
           else if (idx < ie_base + blk) code = (4u << kBentKindShift) | (uint32_t)(sd.fd_off + idx - fdb0);
           else if (idx > zero && idx <= zero + sd.n_ci) code = (3u << kBentKindShift) | (uint32_t)(sd.ci_off + idx - zero - 1);
-          else if (idx > zero + sd.n_ci && idx <= zero + sd.n_ci + sd.n_fd)
-            code = (5u << kBentKindShift) | (uint32_t)(sd.fd_off + idx - zero - 1 - sd.n_ci);
+          else if (idx > zero + sd.n_ci && idx <= zero + sd.n_ci + sd.n_fd) {
+            const int fx = sd.fd_off + idx - zero - 1 - sd.n_ci;
+            // (a line group's modes: their Hy enters the phase history currents of the coupled fold)
+            if (c->line_ends[sd.le_off + c->fdends[fx].le].ce >= 0) continue;
+            code = (5u << kBentKindShift) | (uint32_t)fx;
+          }
           else continue;
           c->b_bent.push_back((int32_t)(code | (raw & kEntryNeg)));
         }
@@ -1231,8 +1235,7 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
     return EMT_EINVAL;
   }
   if (scen) {
-    std::string sm = validate_scenarios(d, scen);
-    if (sm.empty() && d->n_fdgroups > 0) sm = "frequency-dependent line groups are not supported in scenario sets";
+    const std::string sm = validate_scenarios(d, scen);
     if (!sm.empty()) {
       g_build_error = sm;
       return EMT_EINVAL;

@@ -384,6 +384,19 @@ __device__ __forceinline__ void batch_ce_fold(const BatchParams& P, int x, int s
   const int64_t S = P.S;
   const int ge0 = __ldg(P.ce_le0 + x);
   double im[3];
+  if (P.le_fd != nullptr && __ldg(P.le_fd + ge0) >= 0) {
+    // a frequency-dependent line group's end: each mode's b(n) folded here, its modal history
+    // Hy(n) - b(n) (Hy from the last step's update), then the phase history currents T_i (Hy - b)
+    for (int j = 0; j < 3; ++j) {
+      const int fx = __ldg(P.le_fd + ge0 + j);
+      batch_fd_fold(P, fx, sg, step);
+      const double* st = P.fds + (int64_t)fx * kBatchFdState * S + sg;
+      im[j] = st[10 * S] - st[11 * S];
+    }
+    for (int p = 0; p < 3; ++p)
+      P.cph[(int64_t)(3 * x + p) * S + sg] = fma(r.ti[3 * p], im[0], fma(r.ti[3 * p + 1], im[1], r.ti[3 * p + 2] * im[2]));
+    return;
+  }
   for (int j = 0; j < 3; ++j) {
     const int ge = ge0 + j, d = __ldg(P.le_d1 + ge) - 1;
     const double f = __ldg(P.le_f + ge);
@@ -585,8 +598,12 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
             ++j;
           }
           if (sl >= n_here) continue;
-          if (j < n_fdg) batch_fd_fold(P, G.fd0 + j, sigma0 + sl, step);
-          else batch_ce_fold(P, G.ce0 + j - n_fdg, sigma0 + sl, step);
+          if (j < n_fdg) {   // (a line group's modes are folded with their coupled end)
+            if (P.le_ce == nullptr || __ldg(P.le_ce + __ldg(P.fd_le + G.fd0 + j)) < 0)
+              batch_fd_fold(P, G.fd0 + j, sigma0 + sl, step);
+          } else {
+            batch_ce_fold(P, G.ce0 + j - n_fdg, sigma0 + sl, step);
+          }
         }
         __syncthreads();
       }
@@ -978,7 +995,18 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) batch_kernel(BatchParams 
           *hp = __ldg(P.lc_isl + gl) ? fma(e, vk - vm, hv) : fma(e, vk - vm, -hv);
         } else if (P.le_fd != nullptr && __ldg(P.le_fd + G.le0 + (it - n_lc)) >= 0) {
           const int ge = G.le0 + (it - n_lc);
-          batch_fd_update(P, ge, __ldg(P.le_fd + ge), sg, step, vv[(size_t)(__ldg(P.le_nd + ge) - G.node0) * St + sl]);
+          const int x = P.le_ce != nullptr ? __ldg(P.le_ce + ge) : -1;
+          double v;
+          if (x >= 0) {   // a line group's mode: its modal voltage (T_v^-1 v_phase)_j
+            const CoupledEndDev& r = P.ce[x];
+            const int j = ge - __ldg(P.ce_le0 + x);
+            double vp[3];
+            for (int p = 0; p < 3; ++p) vp[p] = vv[(size_t)(__ldg(P.ce_node + 3 * x + p) - G.node0) * St + sl];
+            v = fma(r.tinv[3 * j], vp[0], fma(r.tinv[3 * j + 1], vp[1], r.tinv[3 * j + 2] * vp[2]));
+          } else {
+            v = vv[(size_t)(__ldg(P.le_nd + ge) - G.node0) * St + sl];
+          }
+          batch_fd_update(P, ge, __ldg(P.le_fd + ge), sg, step, v);
         } else if (P.le_ce != nullptr && __ldg(P.le_ce + G.le0 + (it - n_lc)) >= 0) {
           const int ge = G.le0 + (it - n_lc);
           batch_ce_update(P, ge, __ldg(P.le_ce + ge), sg, sl, step, vv, G.node0, St);
