@@ -15,9 +15,22 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/emt.h"
 #include "emt_internal.h"
+
+namespace {
+// An NVTX range over one call of the C ABI, so that a timeline tool shows
+// which entry point issued which launches (header-only NVTX: no cost
+// without a tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
 
 using namespace emt;
 
@@ -1197,6 +1210,7 @@ static int64_t forward_capacity(const emt_ctx* c) {
 // largest component step by step until the packed network fits.  Scenario
 // sets are not packed.
 extern "C" emt_status emt_build_network(const emt_network_desc* d, const emt_scenario_desc* scen, emt_ctx** out) {
+  NvtxRange nvtx_range("emt_build_network");
   emt_status st = build_network(d, scen, out, 0, 1.0, 1.0);
   if (st != EMT_OK || scen) return st;
   int64_t target = forward_capacity(*out);
@@ -2358,6 +2372,7 @@ static cudaError_t reset_matrix_cache(emt_ctx* c, cudaStream_t st) {
 }
 
 extern "C" emt_status emt_prefactor(emt_ctx* c) {
+  NvtxRange nvtx_range("emt_prefactor");
   if (!c) return EMT_EINVAL;
   std::vector<int32_t> mat_sub, mat_ep;
   if (c->batched) {
@@ -2722,6 +2737,7 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
 
 
 extern "C" emt_status emt_step_n(emt_ctx* c, int64_t n_steps, void* stream) {
+  NvtxRange nvtx_range("emt_step_n");
   if (!c) return EMT_EINVAL;
   if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
   if (n_steps < 0) return c->fail(EMT_EINVAL, "n_steps < 0");
@@ -2818,6 +2834,7 @@ static const double* contiguous_rows(const emt_ctx* c, const std::vector<int32_t
 extern "C" emt_status emt_read_waveforms(emt_ctx* c, const int32_t* channels, int64_t n_ch, int64_t step0,
                                          int64_t n_rows, int64_t scen0, int64_t n_scen, double* out,
                                          int32_t out_on_device) {
+  NvtxRange nvtx_range("emt_read_waveforms");
   if (!c) return EMT_EINVAL;
   if (n_ch < 0 || n_rows < 0 || n_scen < 0) return c->fail(EMT_EINVAL, "negative count");
   if (n_ch == 0 || n_rows == 0 || n_scen == 0) return EMT_OK;
@@ -2867,6 +2884,7 @@ extern "C" emt_status emt_read_waveforms(emt_ctx* c, const int32_t* channels, in
 extern "C" emt_status emt_read_waveforms_async(emt_ctx* c, const int32_t* channels, int64_t n_ch, int64_t step0,
                                                int64_t n_rows, int64_t scen0, int64_t n_scen, double* out,
                                                int32_t out_on_device, void* cuda_stream) {
+  NvtxRange nvtx_range("emt_read_waveforms_async");
   if (!c) return EMT_EINVAL;
   if (n_ch < 0 || n_rows < 0 || n_scen < 0) return c->fail(EMT_EINVAL, "negative count");
   if (n_ch == 0 || n_rows == 0 || n_scen == 0) return EMT_OK;
@@ -2978,6 +2996,7 @@ extern "C" emt_status emt_reset(emt_ctx* c) {
 }
 
 extern "C" emt_status emt_autotune(emt_ctx* c, int64_t trial_steps, void* stream) {
+  NvtxRange nvtx_range("emt_autotune");
   if (!c) return EMT_EINVAL;
   if (trial_steps < 1) return c->fail(EMT_EINVAL, "emt_autotune: trial_steps must be >= 1");
   if (!c->prefactored) return c->fail(EMT_ESTATE, "emt_prefactor has not run");
@@ -3531,6 +3550,7 @@ static emt_status adjoint_run(emt_ctx* c, const double* v_target, int64_t n_step
 
 extern "C" emt_status emt_adjoint(emt_ctx* c, const double* v_target, int64_t n_steps, int32_t ckpt_every,
                                   double* grad, double* loss, int32_t on_device, void* stream) {
+  NvtxRange nvtx_range("emt_adjoint");
   if (!c) return EMT_EINVAL;
   c->forward_narrow = true;   // the re-runs may share the device with the reverse sweep
   const emt_status st = adjoint_run(c, v_target, n_steps, ckpt_every, grad, loss, on_device, stream);
