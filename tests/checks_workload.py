@@ -2,7 +2,8 @@
 runs of the large-scale network, of a network with every feature, of
 converter stations (states factorised at run time), of arrester sets
 (several nonlinear resistors per subsystem) and of the 500 x 6-node network
-(the 64-register build), a scenario set and an adjoint gradient.
+(the 64-register build), frequency-dependent line groups, scenario sets
+(one with the shared-matrix solve on the tensor cores) and an adjoint gradient.
 
     python tests/checks_workload.py OUT.npz
 
@@ -20,8 +21,8 @@ sys.path.insert(0, HERE)
 from paper_1903_01081_b300 import emt, netgen as g  # noqa: E402
 
 
-def forward(net, N, sc=None):
-    sim = emt.Simulator(net, sc, n_steps=N)
+def forward(net, N, sc=None, options=None):
+    sim = emt.Simulator(net, sc, n_steps=N, options=options)
     sim.run(N)
     status = 0
     try:
@@ -48,8 +49,15 @@ def run_all():
     net, sc = g.n1_contingency(seed=77, n_scenarios=12, n_buses=40, n_sub=8, n_lines=12, n_sources=3,
                                n_steps=600, fault_step=300, target_branches=240)
     cases["n1"] = (net, 600, sc)
-    for name, (net, N, sc) in cases.items():
-        w, status = forward(net, N, sc)
+    cases["fd_groups"] = (g.with_fd_line_groups(g.multi_subsystem(161, [3, 4, 2, 3, 5], n_lines=8, n_sources=2,
+                                                                    dt=20e-6)), 1500, None)
+    # the shared-matrix solve on the tensor cores (every shared matrix in digit form)
+    sg_base = g.multi_subsystem(91, [3, 5, 2, 4, 6], n_lines=9, n_sources=3, dt=20e-6, n_series_extra=2)
+    net, sc = g.shared_g(seed=92, n_scenarios=40, n_steps=600, fault_step=200, base=sg_base)
+    cases["shared_g_tcgen05"] = (net, 600, sc, {"digit_solve": 1, "digit_min_rows": 1})
+    for name, case in cases.items():
+        net, N, sc = case[:3]
+        w, status = forward(net, N, sc, case[3] if len(case) > 3 else None)
         out[name] = w
         out[name + "_status"] = np.array([status])
     # adjoint gradient of a small network

@@ -26,7 +26,7 @@ def test_checks_build_latches_nothing_and_changes_nothing(tmp_path):
     chk = run(True, str(tmp_path / "checks.npz"))
     ref = run(False, str(tmp_path / "normal.npz"))
     names = [k for k in ref.files if not k.endswith("_status")]
-    assert len(names) == 7
+    assert len(names) == 9
     for k in names:
         assert int(chk[k + "_status"][0]) == 0, k
         assert int(ref[k + "_status"][0]) == 0, k
