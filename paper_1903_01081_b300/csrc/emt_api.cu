@@ -125,7 +125,8 @@ struct emt_ctx {
   int32_t* d_ss_lnode = nullptr;
   int32_t* d_ss_lptr = nullptr;
   int32_t* d_ss_lend = nullptr;
-  bool forward_narrow = false;   // emt_adjoint: its re-runs share the device with the reverse sweep   // electrical subsystems (components); n_sub counts CTAs, several components each when packed
+  bool forward_narrow = false;   // emt_adjoint: its re-runs share the device with the reverse sweep
+  bool fd_groups = false;        // frequency-dependent line groups (their code is in the kExt kernel builds)
   int64_t comp_sum_n2 = 0, comp_max_n = 0;   // over the components
   FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0};
 
@@ -1504,6 +1505,7 @@ static emt_status build_network(const emt_network_desc* d, const emt_scenario_de
   std::vector<int64_t> fg_of_line((size_t)d->n_fdlines, -1);
   for (int64_t gi = 0; gi < d->n_fdgroups; ++gi)
     for (int j = 0; j < 3; ++j) fg_of_line[d->fg_line[3 * gi + j]] = gi;
+  c->fd_groups = d->n_fdgroups > 0;
   std::vector<std::vector<int64_t>> gends_of(S);
   for (int64_t x = 0; x < 2 * d->n_fdgroups; ++x) {
     const int32_t l0 = d->fg_line[3 * (x >> 1)];
@@ -2724,7 +2726,7 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
     p.n_steps = len;
     e = ssf     ? launch_forward_ss(p, c->ss_compact, st)
         : small ? launch_forward_small(p, st)
-                : launch_forward(p, st, !c->forward_narrow, c->lazy || c->lim.nl > 1);
+                : launch_forward(p, st, !c->forward_narrow, c->lazy || c->lim.nl > 1 || c->fd_groups);
     if (e == cudaErrorCooperativeLaunchTooLarge)
       return c->fail(EMT_ERESOURCE, "persistent launch of " + std::to_string(c->n_sub) +
                                         " CTAs cannot be co-resident on this device");
