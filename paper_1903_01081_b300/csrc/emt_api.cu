@@ -126,7 +126,7 @@ struct emt_ctx {
   int32_t* d_ss_lptr = nullptr;
   int32_t* d_ss_lend = nullptr;
   bool forward_narrow = false;   // emt_adjoint: its re-runs share the device with the reverse sweep
-  bool fd_groups = false;        // frequency-dependent line groups (their code is in the kExt kernel builds)
+  bool fd_groups = false;        // frequency-dependent line groups (their code is in kernel builds of their own)
   int64_t comp_sum_n2 = 0, comp_max_n = 0;   // over the components
   FwdLimits lim{0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0};
 
@@ -2726,7 +2726,7 @@ static emt_status forward_steps(emt_ctx* c, int64_t n_steps, cudaStream_t st, co
     p.n_steps = len;
     e = ssf     ? launch_forward_ss(p, c->ss_compact, st)
         : small ? launch_forward_small(p, st)
-                : launch_forward(p, st, !c->forward_narrow, c->lazy || c->lim.nl > 1 || c->fd_groups);
+                : launch_forward(p, st, !c->forward_narrow, c->lazy || c->lim.nl > 1, c->fd_groups);
     if (e == cudaErrorCooperativeLaunchTooLarge)
       return c->fail(EMT_ERESOURCE, "persistent launch of " + std::to_string(c->n_sub) +
                                         " CTAs cannot be co-resident on this device");

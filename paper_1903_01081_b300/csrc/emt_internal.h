@@ -672,8 +672,9 @@ cudaError_t launch_prefactor(const PrefParams& p, int max_n, cudaStream_t st);
 cudaError_t launch_sources(const SourceParams& p, cudaStream_t st);
 // wide = false: the 64-register build only (while another persistent grid shares the device);
 // ext: some subsystem factorises its switch states at run time (SubDev::n_cache > 0) or holds
-// several nonlinear resistors, or the network has frequency-dependent line groups
-cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide = true, bool ext = false);
+// several nonlinear resistors; grp: the network has frequency-dependent line groups
+cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide = true, bool ext = false,
+                           bool grp = false);
 size_t forward_smem_bytes(const FwdLimits& lim);
 // one warp per subsystem (emt_small.cu): subsystems of at most kSmallMaxNodes nodes with basic elements only
 constexpr int kSmallMaxNodes = 32;

@@ -955,11 +955,11 @@ __device__ bool collect_lines(const FwdParams& P, int n_le, unsigned tag, int la
 // keeps more of the step loop's state in registers and is used whenever its
 // residency holds every CTA.
 // kExt: the network has subsystems that factorise their switch states at
-// run time or hold several nonlinear resistors, or has frequency-dependent
-// line groups (the code for those is compiled only into these instances, so
-// that the step loop of every other network keeps its registers and its
-// schedule).
-template <int kMinBlocks, bool kExt>
+// run time or hold several nonlinear resistors; kGrp: it has
+// frequency-dependent line groups (the code for each is compiled only into
+// the instances that need it, so that the step loop of every other network
+// keeps its registers and its schedule).
+template <int kMinBlocks, bool kExt, bool kGrp>
 __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_abort;
@@ -1248,7 +1248,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
   __syncthreads();
   for (int x = tid; x < n_sb; x += T) inp[n_lc + x] = sbg[x] * vs[(P.n0 & 1) * src_vs + sbsrc[x]];
   // frequency-dependent line groups: the modes' Hy (kept modal in the state) into the phase slots, T_i Hy
-  for (int c = tid; c < (kExt && n_fd > 0 ? n_ce : 0); c += T) {
+  for (int c = tid; c < (kGrp && n_fd > 0 ? n_ce : 0); c += T) {
     const int e0 = cele0[c];
     if (lefd[e0] < 0) continue;   // (a coupled Bergeron end)
     const double h0 = fdst[kFdState * lefd[e0] + 10], h1 = fdst[kFdState * lefd[e0 + 1] + 10],
@@ -1272,7 +1272,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
     if (!ok && lane == 0) s_abort = 1;
     if (n_ce > 0)
       fold_modes(lane, n_le, n_ce, lece, lef, inp + ie_base + (p0 ^ 1) * blk_len, inp + ie_base + p0 * blk_len,
-                 imode + p0 * lv, cele0, ceti, kExt && n_fd > 0 ? lefd : nullptr, fd_base);
+                 imode + p0 * lv, cele0, ceti, kGrp && n_fd > 0 ? lefd : nullptr, fd_base);
   }
   // control layer starts 0..31 in the control warp's registers (lane l)
   int lay_reg = 0;
@@ -1499,7 +1499,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
             const FdEndDev& r = fdr[fx];
             double* sx = fdst + kFdState * fx;
             double v;
-            if (kExt && c >= 0) {   // a mode of a line group: the modal voltage (T_v^-1 v_phase)_mode
+            if (kGrp && c >= 0) {   // a mode of a line group: the modal voltage (T_v^-1 v_phase)_mode
               const double* tr = cetinv + 9 * c + 3 * lemode[e];
               const int* nd = cenode + 3 * c;
               v = fma(tr[0], vv[nd[0]], fma(tr[1], vv[nd[1]], tr[2] * vv[nd[2]]));
@@ -1519,7 +1519,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
             sx[8] = v;
             const double hy = fma(r.mu_sum, v, lam_s);   // Hy(n+1)
             sx[10] = hy;
-            if (!kExt || c < 0) {
+            if (!kGrp || c < 0) {
               inp[hy_base + fx] = hy;
             } else {   // the last of its end's three modes puts T_i Hy_mode into the phase slots
               __threadfence_block();
@@ -1580,7 +1580,7 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
           if (!ok) break;
           const int c = lece[e];
           if (c >= 0) {   // a mode: its interpolated history; the third of its end's modes forms T_i I_mode
-            if (kExt && F.lefd != nullptr && F.lefd[e] >= 0) {   // a line group's mode: b folded now, -b its history
+            if (kGrp && F.lefd != nullptr && F.lefd[e] >= 0) {   // a line group's mode: b folded now, -b its history
               fold_fd_end(F, e, v, ie_next);
               imode_next[e] = -ie_next[F.b_base + F.lefd[e]];
             } else {
@@ -1737,23 +1737,26 @@ size_t forward_smem_bytes(const FwdLimits& lim) { return fwd_smem(lim).bytes; }
 int forward_blocks_per_sm(const FwdLimits& lim) {
   const size_t smem = forward_smem_bytes(lim);
   if (smem > 227 * 1024) return 0;
-  if (cudaFuncSetAttribute(fwd_kernel<4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (cudaFuncSetAttribute(fwd_kernel<4, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<4, false>, kFwdThreads, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd_kernel<4, false, false>, kFwdThreads, smem) != cudaSuccess)
     return 0;
   return per_sm;
 }
 
-cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide, bool ext) {
+cudaError_t launch_forward(const FwdParams& p, cudaStream_t st, bool wide, bool ext, bool grp) {
   const size_t smem = forward_smem_bytes(p.lim);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   // the 128-register build when allowed and its residency holds every CTA, else the 64-register one
-  const void* fns[2] = {ext ? (const void*)fwd_kernel<2, true> : (const void*)fwd_kernel<2, false>,
-                        ext ? (const void*)fwd_kernel<4, true> : (const void*)fwd_kernel<4, false>};
+  const void* fns[2] = {
+      ext ? (grp ? (const void*)fwd_kernel<2, true, true> : (const void*)fwd_kernel<2, true, false>)
+          : (grp ? (const void*)fwd_kernel<2, false, true> : (const void*)fwd_kernel<2, false, false>),
+      ext ? (grp ? (const void*)fwd_kernel<4, true, true> : (const void*)fwd_kernel<4, true, false>)
+          : (grp ? (const void*)fwd_kernel<4, false, true> : (const void*)fwd_kernel<4, false, false>)};
   for (int v = wide ? 0 : 1; v < 2; ++v) {
     cudaError_t e = cudaFuncSetAttribute(fns[v], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
