@@ -3,8 +3,8 @@ conductors as the modes of one three-phase line through T_v): each end is a
 coupled end whose modes run the frequency-dependent line equations on modal
 quantities.  Held to the oracle at a peak-normalised 1e-10, also across
 launches (the modal histories are folded into the phase slots when a launch
-starts), over the full 50,000 steps of the large-scale network, and in a
-scenario set."""
+starts), over the full 50,000 steps of the large-scale network, together
+with the extended kernel code, and in a scenario set."""
 import numpy as np
 import pytest
 
@@ -81,6 +81,25 @@ def test_scenario_set_with_line_groups():
     two.sync()
     assert np.array_equal(two.waveforms(), w)
     two.close()
+
+
+def test_groups_with_run_time_factorisation_and_arrester_sets():
+    """Line groups on a network that also needs the extended kernel code
+    (converter stations whose subsystems are factorised at run time, and
+    three-phase arrester sets: several nonlinear resistors per subsystem):
+    the kernel build that carries both, across launches, against the oracle."""
+    base = g.with_converter_stations(g.large_scale(n_steps=3000), n_stations=10)
+    net = g.with_fd_line_groups(g.with_bus_arresters(base, n_buses=20))
+    N = 3000
+    ref = oracle.simulate(net, N)
+    sim = emt.Simulator(net, n_steps=N)
+    sim.run(1000)
+    sim.run(N - 1000)
+    sim.sync()
+    assert sim.info("lazy_subsystems") == 10
+    got = sim.waveforms()[:, 0, :]
+    sim.close()
+    assert rel_err(got, ref) <= TOL
 
 
 def test_groups_are_refused_by_the_adjoint():
