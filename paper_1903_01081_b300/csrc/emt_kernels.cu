@@ -1478,6 +1478,15 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
       }
       const double* ie_cur = inp + ie_base + parshift;
       const double* vs_next = vs + (par ^ 1) * src_vs;
+      // the next step's slot of this thread's first line end, loaded now so
+      // that its L2 round trip overlaps the update items (checked after them;
+      // a slot written later, by a one-step line, is polled as before).  Not
+      // in the line-group builds, whose longer collection it slowed (5.72
+      // against 5.54 us per step).
+      const int e_pre = kGrp ? -1 : item_threads - 1 - tid;
+      unsigned long long pw0 = 0, pw1 = 0;
+      if (e_pre >= 0 && e_pre < n_le && step + 1 < n_end)
+        ld_tagged_raw(P.ring + 2 * EMT_CHK(P.err, leown[e_pre] + rslot[e_pre], P.bnd.ring, kChkRingRead), pw0, pw1);
       for (int it = tid; it < it_end; it += item_threads) {
         if (it < n_lc) {
           const int k = lck[it], m = lcm[it];
@@ -1572,8 +1581,9 @@ __global__ void __launch_bounds__(kFwdThreads, kMinBlocks) fwd_kernel(FwdParams 
         bool ok = true;
         for (int e = item_threads - 1 - tid; e < n_le && ok; e += item_threads) {
           double v = 0.0;
-          ok = poll_slot(P, P.ring + 2 * EMT_CHK(P.err, leown[e] + rslot[e], P.bnd.ring, kChkRingRead), tag, SIDX,
-                         e, v);
+          if (e != e_pre || !tagged_value(pw0, pw1, tag, v))
+            ok = poll_slot(P, P.ring + 2 * EMT_CHK(P.err, leown[e] + rslot[e], P.bnd.ring, kChkRingRead), tag, SIDX,
+                           e, v);
           ie_next[e] = v;
           const int nx = rslot[e] + 1;
           rslot[e] = nx == ledepth[e] ? 0 : nx;
